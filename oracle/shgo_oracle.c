@@ -1,0 +1,486 @@
+/*
+ * Plain CPU oracle for nuclear-attraction integrals over contracted real solid-harmonic
+ * Gaussian orbitals (SHGOs).  TEST INFRASTRUCTURE ONLY: it is called by the tests, by the
+ * smoke check and by the CPU-baseline leg of the benchmark, never by the library.
+ *
+ * It deliberately does NOT follow the paper's SHGO route.  It evaluates the plain definition
+ *
+ *     V_ab = sum_C Z_C < phi_a | 1/|r - C| | phi_b >                         (operator of Eq. 11)
+ *
+ * over the orbitals of Eq. 1 by the Cartesian route that the paper lists as its comparison
+ * (Table 1, first column): Boys function -> Hermite Coulomb integrals -> Hermite expansion
+ * coefficients -> Cartesian integrals -> primitive contraction -> solid harmonics.  The
+ * Cartesian integrals follow McMurchie and Davidson (J. Comput. Phys. 26, 218 (1978)), in the
+ * notation of Helgaker, Jorgensen and Olsen, "Molecular Electronic-Structure Theory", ch. 9.
+ *
+ * Conventions (readings of the paper, all stated in the design notes):
+ *  - Solid harmonics are Racah-normalised, Condon-Shortley phase (Eq. 2); the output uses the
+ *    real combination S_l0 = Y_l^0, S_{l,m>0} = (-1)^m sqrt2 Re Y_l^m,
+ *    S_{l,-m} = (-1)^m sqrt2 Im Y_l^m, so S_11 = x, S_1,-1 = y, S_10 = z.
+ *  - N(l, alpha) of Eq. 1 normalises each primitive; the contracted function is then
+ *    renormalised to <phi|phi> = 1, using this file's own Cartesian overlap integrals.
+ *  - V carries no minus sign.  Functions are ordered shell by shell, m = -l..l.
+ *
+ * The scalar type is `real`: double by default, long double when compiled with
+ * -DORACLE_LONG_DOUBLE (80-bit on x86-64, IEEE binary128 on aarch64).  All public entry
+ * points take and return double.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifdef ORACLE_LONG_DOUBLE
+typedef long double real;
+#define RX(f) f##l
+#define RPI 3.141592653589793238462643383279502884L
+#else
+typedef double real;
+#define RX(f) f
+#define RPI 3.141592653589793238462643383279502884
+#endif
+
+#define ORACLE_LMAX 10 /* largest shell l accepted (the library's limit is 8) */
+
+/* ------------------------------------------------------------------------------------------ */
+/* Boys function  F_n(T) = int_0^1 u^{2n} exp(-T u^2) du   (the third factor after Eq. 12).   */
+/*                                                                                            */
+/* T below the switch: the convergent series                                                  */
+/*     F_n(T) = exp(-T) sum_{i>=0} (2T)^i / [(2n+1)(2n+3)...(2n+2i+1)]                        */
+/* evaluated for n = nmax, then the downward recursion F_n = (2T F_{n+1} + exp(-T))/(2n+1).   */
+/* T at or above it: F_0 = sqrt(pi/T) erf(sqrt T)/2 and the upward recursion                  */
+/*     F_{n+1} = ((2n+1) F_n - exp(-T)) / (2T),                                               */
+/* which loses nothing while 2n+1 < 2T.                                                        */
+/* ------------------------------------------------------------------------------------------ */
+static void boys_r(int nmax, real T, real* F) {
+  const real ex = RX(exp)(-T);
+  const real tsw = (real)(2 * nmax + 40);
+  if (T < tsw) {
+    real term = (real)1 / (real)(2 * nmax + 1);
+    real sum = term;
+    for (int i = 1; i < 100000; ++i) {
+      term *= (2 * T) / (real)(2 * nmax + 2 * i + 1);
+      sum += term;
+      if (term < sum * (real)1e-40) break;
+    }
+    F[nmax] = ex * sum;
+    for (int n = nmax - 1; n >= 0; --n) F[n] = (2 * T * F[n + 1] + ex) / (real)(2 * n + 1);
+  } else {
+    const real st = RX(sqrt)(T);
+    F[0] = RX(sqrt)(RPI) * RX(erf)(st) / (2 * st);
+    for (int n = 0; n < nmax; ++n) F[n + 1] = ((real)(2 * n + 1) * F[n] - ex) / (2 * T);
+  }
+}
+
+void oracle_boys(int nmax, double T, double* F) {
+  real Fr[64];
+  if (nmax < 0 || nmax > 60) return;
+  boys_r(nmax, (real)T, Fr);
+  for (int n = 0; n <= nmax; ++n) F[n] = (double)Fr[n];
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Cartesian components of degree l, ordered i = l..0, j = l-i..0, k = l-i-j (x^i y^j z^k).   */
+/* ------------------------------------------------------------------------------------------ */
+static int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+static int cart_index(int l, int i, int j) {
+  /* position of (i, j, l-i-j) in the order above */
+  int idx = 0;
+  for (int ii = l; ii > i; --ii) idx += l - ii + 1;
+  return idx + (l - i - j);
+}
+
+static real factorial_r(int n) {
+  real f = 1;
+  for (int i = 2; i <= n; ++i) f *= (real)i;
+  return f;
+}
+
+static real binom_r(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  return factorial_r(n) / (factorial_r(k) * factorial_r(n - k));
+}
+
+/*
+ * Cartesian expansion of the real Racah-normalised solid harmonic S_lm (Eq. 2 with the real
+ * combination above).  Written out from the textbook closed form
+ *     S_{l,|m|}  = sqrt((2 - d_m0) (l-|m|)!/(l+|m|)!) Pi_l^|m|(z, r) Re (x + i y)^|m|
+ *     S_{l,-|m|} = sqrt( 2        (l-|m|)!/(l+|m|)!) Pi_l^|m|(z, r) Im (x + i y)^|m|
+ *     Pi_l^m(z, r) = sum_k (-1)^k 2^-l C(l,k) C(2l-2k,l) (l-2k)!/(l-2k-m)! r^{2k} z^{l-2k-m}
+ * with r^{2k} = (x^2 + y^2 + z^2)^k expanded by the multinomial theorem.
+ * coef[(m + l) * ncart(l) + c] multiplies Cartesian component c.
+ */
+static void solid_harmonic_cart(int l, real* coef) {
+  const int nc = ncart(l);
+  memset(coef, 0, sizeof(real) * (size_t)(2 * l + 1) * nc);
+  for (int m = -l; m <= l; ++m) {
+    const int am = m < 0 ? -m : m;
+    const real norm = RX(sqrt)((m == 0 ? (real)1 : (real)2) * factorial_r(l - am) / factorial_r(l + am));
+    real* row = coef + (size_t)(m + l) * nc;
+    for (int k = 0; 2 * k <= l - am; ++k) {
+      const real pik = ((k & 1) ? -1 : 1) * RX(pow)((real)2, (real)(-l)) * binom_r(l, k) *
+                       binom_r(2 * l - 2 * k, l) * factorial_r(l - 2 * k) / factorial_r(l - 2 * k - am);
+      /* (x + i y)^am: term C(am, q) x^{am-q} (i y)^q; real part for q even, imaginary for q odd */
+      for (int q = 0; q <= am; ++q) {
+        real xy;
+        if (m >= 0) {
+          if (q & 1) continue;
+          xy = binom_r(am, q) * ((q / 2) & 1 ? -1 : 1);
+        } else {
+          if (!(q & 1)) continue;
+          xy = binom_r(am, q) * (((q - 1) / 2) & 1 ? -1 : 1);
+        }
+        /* multinomial expansion of (x^2+y^2+z^2)^k */
+        for (int a = 0; a <= k; ++a)
+          for (int b = 0; a + b <= k; ++b) {
+            const int c = k - a - b;
+            const real mult = factorial_r(k) / (factorial_r(a) * factorial_r(b) * factorial_r(c));
+            const int px = am - q + 2 * a, py = q + 2 * b;
+            row[cart_index(l, px, py)] += norm * pik * xy * mult;
+          }
+      }
+    }
+  }
+}
+
+int oracle_solid_harmonic_cart(int l, double* coef) {
+  if (l < 0 || l > ORACLE_LMAX) return -1;
+  const int n = (2 * l + 1) * ncart(l);
+  real* c = (real*)malloc(sizeof(real) * (size_t)n);
+  if (!c) return -2;
+  solid_harmonic_cart(l, c);
+  for (int i = 0; i < n; ++i) coef[i] = (double)c[i];
+  free(c);
+  return 0;
+}
+
+/* Evaluate S_lm at npts points from the Cartesian expansion above: out[p * (2l+1) + m + l]. */
+int oracle_solid_harmonic(int l, long npts, const double* xyz, double* out) {
+  if (l < 0 || l > ORACLE_LMAX) return -1;
+  const int nc = ncart(l);
+  real* c = (real*)malloc(sizeof(real) * (size_t)(2 * l + 1) * nc);
+  if (!c) return -2;
+  solid_harmonic_cart(l, c);
+  for (long p = 0; p < npts; ++p) {
+    const real x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
+    for (int m = 0; m < 2 * l + 1; ++m) {
+      real s = 0;
+      for (int i = l; i >= 0; --i)
+        for (int j = l - i; j >= 0; --j) {
+          const int k = l - i - j;
+          s += c[(size_t)m * nc + cart_index(l, i, j)] * RX(pow)(x, (real)i) * RX(pow)(y, (real)j) *
+               RX(pow)(z, (real)k);
+        }
+      out[p * (2 * l + 1) + m] = (double)s;
+    }
+  }
+  free(c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* McMurchie-Davidson building blocks.                                                       */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Hermite expansion coefficients of one Cartesian direction:
+ *   E^{00}_0 = exp(-mu X_AB^2)
+ *   E^{i+1,j}_t = E^{ij}_{t-1}/(2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
+ *   E^{i,j+1}_t = E^{ij}_{t-1}/(2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1}
+ * Stored E[(i * (jmax+1) + j) * (tdim) + t], tdim = imax + jmax + 1. */
+static void hermite_E(int imax, int jmax, real p, real XPA, real XPB, real E00, real* E) {
+  const int tdim = imax + jmax + 1;
+#define EIDX(i, j, t) (((i) * (jmax + 1) + (j)) * tdim + (t))
+  memset(E, 0, sizeof(real) * (size_t)(imax + 1) * (jmax + 1) * tdim);
+  E[EIDX(0, 0, 0)] = E00;
+  const real h = (real)1 / (2 * p);
+  for (int i = 0; i <= imax; ++i) {
+    if (i > 0) {
+      for (int t = 0; t <= i; ++t) {
+        real v = XPA * E[EIDX(i - 1, 0, t)];
+        if (t > 0) v += h * E[EIDX(i - 1, 0, t - 1)];
+        if (t + 1 <= i - 1) v += (real)(t + 1) * E[EIDX(i - 1, 0, t + 1)];
+        E[EIDX(i, 0, t)] = v;
+      }
+    }
+    for (int j = 1; j <= jmax; ++j) {
+      for (int t = 0; t <= i + j; ++t) {
+        real v = 0;
+        if (t <= i + j - 1) v += XPB * E[EIDX(i, j - 1, t)];
+        if (t > 0) v += h * E[EIDX(i, j - 1, t - 1)];
+        if (t + 1 <= i + j - 1) v += (real)(t + 1) * E[EIDX(i, j - 1, t + 1)];
+        E[EIDX(i, j, t)] = v;
+      }
+    }
+  }
+#undef EIDX
+}
+
+/* Hermite Coulomb integrals R^0_{tuv}(p, P - C) for t + u + v <= L:
+ *   R^n_{000} = (-2p)^n F_n(p |PC|^2)
+ *   R^n_{t+1,u,v} = t R^{n+1}_{t-1,u,v} + X_PC R^{n+1}_{t,u,v}   (and likewise in y, z)
+ * work holds (L+1)^4 reals; out[(t * (L+1) + u) * (L+1) + v] receives R^0_{tuv}. */
+static void hermite_R(int L, real p, real XPC, real YPC, real ZPC, real* work, real* out) {
+  const int d = L + 1;
+#define RIDX(n, t, u, v) ((((n) * d + (t)) * d + (u)) * d + (v))
+  real F[80];
+  boys_r(L, p * (XPC * XPC + YPC * YPC + ZPC * ZPC), F);
+  real m2p = 1;
+  for (int n = 0; n <= L; ++n) {
+    work[RIDX(n, 0, 0, 0)] = m2p * F[n];
+    m2p *= -2 * p;
+  }
+  for (int n = L - 1; n >= 0; --n) {
+    for (int s = 1; s <= L - n; ++s)
+      for (int t = s; t >= 0; --t)
+        for (int u = s - t; u >= 0; --u) {
+          const int v = s - t - u;
+          real r;
+          if (t > 0) {
+            r = XPC * work[RIDX(n + 1, t - 1, u, v)];
+            if (t > 1) r += (real)(t - 1) * work[RIDX(n + 1, t - 2, u, v)];
+          } else if (u > 0) {
+            r = YPC * work[RIDX(n + 1, t, u - 1, v)];
+            if (u > 1) r += (real)(u - 1) * work[RIDX(n + 1, t, u - 2, v)];
+          } else {
+            r = ZPC * work[RIDX(n + 1, t, u, v - 1)];
+            if (v > 1) r += (real)(v - 1) * work[RIDX(n + 1, t, u, v - 2)];
+          }
+          work[RIDX(n, t, u, v)] = r;
+        }
+  }
+  for (int t = 0; t <= L; ++t)
+    for (int u = 0; u + t <= L; ++u)
+      for (int v = 0; v + u + t <= L; ++v) out[(t * d + u) * d + v] = work[RIDX(0, t, u, v)];
+#undef RIDX
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Basis handling.                                                                            */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int l, nprim;
+  const double* alpha;
+  real coef[64]; /* contraction coefficient x primitive normalisation x contracted renormalisation */
+  real A[3];
+} shell_t;
+
+/* N(l, alpha)^-2 = pi^{3/2} (2l-1)!! / (2^l (2 alpha)^{l + 3/2})   (normalisation of Eq. 1) */
+static real prim_norm(int l, real a) {
+  real dfact = 1;
+  for (int k = 2 * l - 1; k > 1; k -= 2) dfact *= (real)k;
+  const real n2 = RX(pow)(RPI, (real)1.5) * dfact / (RX(pow)((real)2, (real)l) * RX(pow)(2 * a, (real)l + (real)1.5));
+  return 1 / RX(sqrt)(n2);
+}
+
+/* Cartesian overlap block of two contracted shells, transformed to real solid harmonics:
+ * out[ma * (2lb+1) + mb].  (pi/p)^{3/2} E^{ij}_0 E^{kl}_0 E^{mn}_0 per primitive pair. */
+static void overlap_block(const shell_t* a, const shell_t* b, const real* ca, const real* cb, real* out) {
+  const int la = a->l, lb = b->l, nca = ncart(la), ncb = ncart(lb);
+  const int tdim = la + lb + 1;
+  real* Ex = (real*)malloc(sizeof(real) * 3 * (size_t)(la + 1) * (lb + 1) * tdim);
+  real* Ey = Ex + (size_t)(la + 1) * (lb + 1) * tdim;
+  real* Ez = Ey + (size_t)(la + 1) * (lb + 1) * tdim;
+  real* Sc = (real*)calloc((size_t)nca * ncb, sizeof(real));
+  for (int i = 0; i < a->nprim; ++i)
+    for (int j = 0; j < b->nprim; ++j) {
+      const real al = a->alpha[i], be = b->alpha[j], p = al + be, mu = al * be / p;
+      real P[3], E00[3];
+      for (int c = 0; c < 3; ++c) {
+        P[c] = (al * a->A[c] + be * b->A[c]) / p;
+        const real X = a->A[c] - b->A[c];
+        E00[c] = RX(exp)(-mu * X * X);
+      }
+      hermite_E(la, lb, p, P[0] - a->A[0], P[0] - b->A[0], E00[0], Ex);
+      hermite_E(la, lb, p, P[1] - a->A[1], P[1] - b->A[1], E00[1], Ey);
+      hermite_E(la, lb, p, P[2] - a->A[2], P[2] - b->A[2], E00[2], Ez);
+      const real pre = a->coef[i] * b->coef[j] * RX(pow)(RPI / p, (real)1.5);
+      for (int ix = la; ix >= 0; --ix)
+        for (int iy = la - ix; iy >= 0; --iy) {
+          const int iz = la - ix - iy, ia = cart_index(la, ix, iy);
+          for (int jx = lb; jx >= 0; --jx)
+            for (int jy = lb - jx; jy >= 0; --jy) {
+              const int jz = lb - jx - jy, ib = cart_index(lb, jx, jy);
+              Sc[ia * ncb + ib] += pre * Ex[(ix * (lb + 1) + jx) * tdim] * Ey[(iy * (lb + 1) + jy) * tdim] *
+                                   Ez[(iz * (lb + 1) + jz) * tdim];
+            }
+        }
+    }
+  for (int ma = 0; ma < 2 * la + 1; ++ma)
+    for (int mb = 0; mb < 2 * lb + 1; ++mb) {
+      real s = 0;
+      for (int ia = 0; ia < nca; ++ia)
+        for (int ib = 0; ib < ncb; ++ib) s += ca[ma * nca + ia] * cb[mb * ncb + ib] * Sc[ia * ncb + ib];
+      out[ma * (2 * lb + 1) + mb] = s;
+    }
+  free(Sc);
+  free(Ex);
+}
+
+/* Fill the shells: coef = c_i N(l, alpha_i) / sqrt(<phi|phi>), the self-overlap taken from
+ * overlap_block (the m = -l diagonal element; all 2l+1 agree). */
+static int setup_shells(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
+                        const double* xyz, shell_t* sh, real** cart) {
+  long off = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    if (l[s] < 0 || l[s] > ORACLE_LMAX || nprim[s] < 1 || nprim[s] > 64) return -1;
+    sh[s].l = l[s];
+    sh[s].nprim = nprim[s];
+    sh[s].alpha = exps + off;
+    for (int c = 0; c < 3; ++c) sh[s].A[c] = xyz[3 * s + c];
+    for (int i = 0; i < nprim[s]; ++i) sh[s].coef[i] = (real)coefs[off + i] * prim_norm(l[s], exps[off + i]);
+    off += nprim[s];
+  }
+  for (int s = 0; s < n_shells; ++s) {
+    const int ll = sh[s].l, nb = 2 * ll + 1;
+    real* blk = (real*)malloc(sizeof(real) * (size_t)nb * nb);
+    overlap_block(&sh[s], &sh[s], cart[ll], cart[ll], blk);
+    const real scale = 1 / RX(sqrt)(blk[0]);
+    for (int i = 0; i < sh[s].nprim; ++i) sh[s].coef[i] *= scale;
+    free(blk);
+  }
+  return 0;
+}
+
+/* Nuclear-attraction block of one shell pair: out[ma * (2lb+1) + mb] =
+ *   sum_C Z_C <a, ma | 1/|r-C| | b, mb>.
+ * Per primitive pair: R^0_tuv is summed over nuclei weighted by Z_C (the operator of Eq. 11 is
+ * the sum of the nuclear potentials), then contracted with E^x_t E^y_u E^z_v and (2 pi / p). */
+static void nuclear_block(const shell_t* a, const shell_t* b, const real* ca, const real* cb, long nC,
+                          const double* C, const double* Z, real* out) {
+  const int la = a->l, lb = b->l, L = la + lb, nca = ncart(la), ncb = ncart(lb);
+  const int tdim = L + 1, d = L + 1;
+  real* Ex = (real*)malloc(sizeof(real) * 3 * (size_t)(la + 1) * (lb + 1) * tdim);
+  real* Ey = Ex + (size_t)(la + 1) * (lb + 1) * tdim;
+  real* Ez = Ey + (size_t)(la + 1) * (lb + 1) * tdim;
+  real* work = (real*)malloc(sizeof(real) * (size_t)d * d * d * d);
+  real* Rc = (real*)malloc(sizeof(real) * (size_t)d * d * d);
+  real* Rs = (real*)malloc(sizeof(real) * (size_t)d * d * d);
+  real* Vc = (real*)calloc((size_t)nca * ncb, sizeof(real));
+  for (int i = 0; i < a->nprim; ++i)
+    for (int j = 0; j < b->nprim; ++j) {
+      const real al = a->alpha[i], be = b->alpha[j], p = al + be, mu = al * be / p;
+      real P[3], E00[3];
+      for (int c = 0; c < 3; ++c) {
+        P[c] = (al * a->A[c] + be * b->A[c]) / p;
+        const real X = a->A[c] - b->A[c];
+        E00[c] = RX(exp)(-mu * X * X);
+      }
+      hermite_E(la, lb, p, P[0] - a->A[0], P[0] - b->A[0], E00[0], Ex);
+      hermite_E(la, lb, p, P[1] - a->A[1], P[1] - b->A[1], E00[1], Ey);
+      hermite_E(la, lb, p, P[2] - a->A[2], P[2] - b->A[2], E00[2], Ez);
+      memset(Rs, 0, sizeof(real) * (size_t)d * d * d);
+      for (long c = 0; c < nC; ++c) {
+        hermite_R(L, p, P[0] - (real)C[3 * c], P[1] - (real)C[3 * c + 1], P[2] - (real)C[3 * c + 2], work, Rc);
+        for (int t = 0; t <= L; ++t)
+          for (int u = 0; u + t <= L; ++u)
+            for (int v = 0; v + u + t <= L; ++v) Rs[(t * d + u) * d + v] += (real)Z[c] * Rc[(t * d + u) * d + v];
+      }
+      const real pre = a->coef[i] * b->coef[j] * 2 * RPI / p;
+      for (int ix = la; ix >= 0; --ix)
+        for (int iy = la - ix; iy >= 0; --iy) {
+          const int iz = la - ix - iy, ia = cart_index(la, ix, iy);
+          for (int jx = lb; jx >= 0; --jx)
+            for (int jy = lb - jx; jy >= 0; --jy) {
+              const int jz = lb - jx - jy, ib = cart_index(lb, jx, jy);
+              const real* ex = Ex + (ix * (lb + 1) + jx) * tdim;
+              const real* ey = Ey + (iy * (lb + 1) + jy) * tdim;
+              const real* ez = Ez + (iz * (lb + 1) + jz) * tdim;
+              real s = 0;
+              for (int t = 0; t <= ix + jx; ++t)
+                for (int u = 0; u <= iy + jy; ++u)
+                  for (int v = 0; v <= iz + jz; ++v) s += ex[t] * ey[u] * ez[v] * Rs[(t * d + u) * d + v];
+              Vc[ia * ncb + ib] += pre * s;
+            }
+        }
+    }
+  for (int ma = 0; ma < 2 * la + 1; ++ma)
+    for (int mb = 0; mb < 2 * lb + 1; ++mb) {
+      real s = 0;
+      for (int ia = 0; ia < nca; ++ia)
+        for (int ib = 0; ib < ncb; ++ib) s += ca[ma * nca + ia] * cb[mb * ncb + ib] * Vc[ia * ncb + ib];
+      out[ma * (2 * lb + 1) + mb] = s;
+    }
+  free(Vc);
+  free(Rs);
+  free(Rc);
+  free(work);
+  free(Ex);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Public entry points.                                                                       */
+/* ------------------------------------------------------------------------------------------ */
+typedef enum { OP_OVERLAP = 0, OP_NUCLEAR = 1 } op_t;
+
+static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, const double* exps,
+                        const double* coefs, const double* xyz, long nC, const double* C, const double* Z,
+                        double* out, int n_threads) {
+  if (n_shells < 0) return -1;
+  shell_t* sh = (shell_t*)calloc((size_t)(n_shells > 0 ? n_shells : 1), sizeof(shell_t));
+  real* cart[ORACLE_LMAX + 1];
+  for (int ll = 0; ll <= ORACLE_LMAX; ++ll) {
+    cart[ll] = (real*)malloc(sizeof(real) * (size_t)(2 * ll + 1) * ncart(ll));
+    solid_harmonic_cart(ll, cart[ll]);
+  }
+  int rc = setup_shells(n_shells, l, nprim, exps, coefs, xyz, sh, cart);
+  long* off = (long*)malloc(sizeof(long) * (size_t)(n_shells + 1));
+  off[0] = 0;
+  for (int s = 0; s < n_shells; ++s) off[s + 1] = off[s] + (rc == 0 ? 2 * sh[s].l + 1 : 0);
+  const long nbf = off[n_shells];
+  if (rc == 0) {
+    const long npairs = (long)n_shells * (n_shells + 1) / 2;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (long q = 0; q < npairs; ++q) {
+      /* q enumerates pairs a >= b */
+      long a = (long)((sqrt(8.0 * (double)q + 1.0) - 1.0) / 2.0);
+      while (a * (a + 1) / 2 > q) --a;
+      while ((a + 1) * (a + 2) / 2 <= q) ++a;
+      const long b = q - a * (a + 1) / 2;
+      const int na = 2 * sh[a].l + 1, nb = 2 * sh[b].l + 1;
+      real* blk = (real*)malloc(sizeof(real) * (size_t)na * nb);
+      if (op == OP_OVERLAP)
+        overlap_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], blk);
+      else
+        nuclear_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], nC, C, Z, blk);
+      for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) {
+          out[(off[a] + i) * nbf + off[b] + j] = (double)blk[i * nb + j];
+          out[(off[b] + j) * nbf + off[a] + i] = (double)blk[i * nb + j];
+        }
+      free(blk);
+    }
+  }
+  free(off);
+  for (int ll = 0; ll <= ORACLE_LMAX; ++ll) free(cart[ll]);
+  free(sh);
+  return rc;
+}
+
+/* V_ab = sum_C Z_C <phi_a | 1/|r - C| | phi_b>, written to out (nbf x nbf, row-major, both
+ * triangles).  Shell s has l[s], nprim[s] primitives whose exponents and coefficients follow
+ * those of shell s-1 in exps/coefs, and centre xyz[3s..3s+2] (bohr).  Returns 0, or -1 on bad
+ * input.  n_threads > 0 sets the OpenMP thread count (shell pairs are independent). */
+int oracle_nuclear_attraction(int n_shells, const int* l, const int* nprim, const double* exps,
+                              const double* coefs, const double* xyz, long n_centers, const double* centers,
+                              const double* charges, double* out, int n_threads) {
+  return one_electron(OP_NUCLEAR, n_shells, l, nprim, exps, coefs, xyz, n_centers, centers, charges, out,
+                      n_threads);
+}
+
+/* S_ab = <phi_a | phi_b> (Eq. 4) over the same basis; same layout and conventions. */
+int oracle_overlap(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
+                   const double* xyz, double* out, int n_threads) {
+  return one_electron(OP_OVERLAP, n_shells, l, nprim, exps, coefs, xyz, 0, NULL, NULL, out, n_threads);
+}
+
+/* Primitive normalisation N(l, alpha) of Eq. 1, as used above. */
+double oracle_prim_norm(int l, double alpha) { return (double)prim_norm(l, alpha); }
+
+int oracle_real_bits(void) { return (int)(sizeof(real) * 8); }

@@ -1,0 +1,274 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: closed forms (Eq. 5 product,
+the s-s Boys form, F_0 = sqrt(pi/T) erf(sqrt T)/2), scipy's special functions and spherical
+harmonics, brute-force 3-D quadrature, and invariances of the exact integral (hermiticity,
+translation, rotation covariance by fitted Wigner-D blocks, linearity in the charges, far field).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import oracle
+from paper_2404_16245_gb300 import workloads as W
+from tests import refmath as RM
+
+
+# ---------------------------------------------------------------- Boys function (after Eq. 12)
+@pytest.mark.parametrize("T", [1e-12, 1e-6, 0.01, 0.5, 3.0, 11.0, 29.9, 30.1, 47.0, 60.0, 150.0, 2e3, 1e6])
+def test_boys_f0_closed_form(T):
+    ref = math.sqrt(math.pi / T) * math.erf(math.sqrt(T)) / 2
+    assert oracle.boys(0, T)[0] == pytest.approx(ref, rel=2e-15)
+
+
+def test_boys_zero_argument():
+    F = oracle.boys(20, 0.0)
+    assert np.allclose(F, 1.0 / (2 * np.arange(21) + 1), rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 12, 16, 20])
+@pytest.mark.parametrize("T", [0.2, 1.7, 6.0, 19.0, 35.0, 55.0, 80.0, 300.0])
+def test_boys_quadrature(n, T):
+    # definition F_n(T) = int_0^1 u^{2n} exp(-T u^2) du by composite Gauss-Legendre
+    u, w = [], []
+    edges = np.linspace(0, 1, 41)
+    for a, b in zip(edges[:-1], edges[1:]):
+        x, ww = RM.gauss_legendre(40, a, b)
+        u.append(x)
+        w.append(ww)
+    u = np.concatenate(u)
+    w = np.concatenate(w)
+    ref = np.sum(w * u ** (2 * n) * np.exp(-T * u * u))
+    assert oracle.boys(n, T)[n] == pytest.approx(ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("T", [0.5, 4.0, 25.0, 41.0, 120.0])
+def test_boys_incomplete_gamma(T):
+    F = oracle.boys(16, T)
+    for n in range(17):
+        ref = sp.gamma(n + 0.5) * sp.gammainc(n + 0.5, T) / (2 * T ** (n + 0.5))
+        assert F[n] == pytest.approx(ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("T", [0.01, 2.0, 33.0, 40.0, 77.0])
+def test_boys_recursion_identity(T):
+    F = oracle.boys(18, T)
+    n = np.arange(18)
+    lhs = 2 * T * F[1:]
+    rhs = (2 * n + 1) * F[:-1] - math.exp(-T)
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-300)
+
+
+# ---------------------------------------------------------------- solid harmonics (Eq. 2)
+@pytest.mark.parametrize("l", range(0, 11))
+def test_solid_harmonics_match_scipy(l):
+    rng = np.random.default_rng(100 + l)
+    pts = rng.normal(size=(40, 3)) * 1.3
+    got = oracle.solid_harmonic(l, pts)
+    ref = RM.solid_harmonics_scipy(l, pts)
+    scale = np.max(np.abs(ref)) + 1e-300
+    assert np.max(np.abs(got - ref)) <= 1e-13 * scale
+
+
+def test_solid_harmonics_low_order_explicit():
+    x, y, z = 0.3, -1.1, 0.7
+    S1 = oracle.solid_harmonic(1, [[x, y, z]])[0]
+    assert np.allclose(S1, [y, z, x], rtol=0, atol=1e-15)
+    S2 = oracle.solid_harmonic(2, [[x, y, z]])[0]
+    r2 = x * x + y * y + z * z
+    ref = [math.sqrt(3) * x * y, math.sqrt(3) * y * z, z * z - 0.5 * (x * x + y * y), math.sqrt(3) * x * z,
+           math.sqrt(3) / 2 * (x * x - y * y)]
+    assert np.allclose(S2, ref, rtol=0, atol=1e-15)
+    assert abs(ref[2] - (1.5 * z * z - 0.5 * r2)) < 1e-15
+
+
+# ---------------------------------------------------------------- normalisation (Eq. 1, Eq. 10)
+@pytest.mark.parametrize("l", range(0, 9))
+def test_primitive_norm_radial_quadrature(l):
+    for a in (0.05, 1.0, 37.0):
+        assert oracle.prim_norm(l, a) == pytest.approx(RM.radial_norm(l, a), rel=1e-12)
+
+
+def test_self_overlap_is_identity_per_shell():
+    basis = W.random_basis(7, 18, 8, max_prim=5)
+    S = oracle.overlap(basis)
+    off = np.concatenate([[0], np.cumsum(2 * basis["l"] + 1)])
+    for s in range(len(basis["l"])):
+        blk = S[off[s]:off[s + 1], off[s]:off[s + 1]]
+        assert np.allclose(blk, np.eye(len(blk)), rtol=0, atol=1e-12)
+
+
+def test_overlap_eq10_prefactor_one_centre():
+    # Eq. 10 with a = b keeps only l1 = la = lb, where the epsilon factors are 1: the overlap of
+    # two unnormalised primitives is 4 pi (pi/2)^{1/2} (2l-1)!!/[2p]^{l+3/2}, the Racah-normalised
+    # angular integral 4 pi/(2l+1) times the radial moment int r^{2l+2} e^{-p r^2} dr
+    for l in range(0, 7):
+        a, b = 0.8, 2.3
+        basis = W.make_basis([l, l], [1, 1], [a, b], [1.0, 1.0], [[0, 0, 0], [0, 0, 0]])
+        S = oracle.overlap(basis)
+        n = 2 * l + 1
+        p = a + b
+        dfact = float(np.prod(np.arange(2 * l - 1, 0, -2))) if l > 0 else 1.0
+        eq10 = 4 * math.pi * math.sqrt(math.pi / 2) * dfact / (2 * p) ** (l + 1.5)
+        ref = eq10 * RM.radial_norm(l, a) * RM.radial_norm(l, b)
+        assert np.allclose(np.diag(S[:n, n:]), ref, rtol=1e-12)
+
+
+def test_overlap_brute_force():
+    basis = W.make_basis([1, 2], [2, 1], [0.9, 2.5, 1.4], [0.6, 0.4, 1.0], [[0, 0, 0], [0.4, -0.3, 0.8]])
+    S = oracle.overlap(basis)
+    # raw-normalised functions on a product grid about the first centre; renormalise numerically
+    pts, w = RM.sphere_grid(60, 9.0, 40, 80, np.zeros(3))
+    rho = np.linalg.norm(pts, axis=1)
+    w = w * rho  # int f d^3r: restore the power of rho removed for 1/r kernels
+    f0 = RM.shell_values(basis, 0, pts, [1.0, 1.0])
+    n0 = np.sqrt(np.sum(w * f0[:, 0] ** 2))
+    pts1, w1 = RM.sphere_grid(60, 9.0, 40, 80, basis["xyz"][1])
+    w1 = w1 * np.linalg.norm(pts1 - basis["xyz"][1], axis=1)
+    n1 = np.sqrt(np.sum(w1 * RM.shell_values(basis, 1, pts1, [1.0, 1.0])[:, 0] ** 2))
+    fa = RM.shell_values(basis, 0, pts, [1 / n0, 1 / n1])
+    fb = RM.shell_values(basis, 1, pts, [1 / n0, 1 / n1])
+    ref = np.einsum("p,pi,pj->ij", w, fa, fb)
+    assert np.allclose(S[:3, 3:], ref, rtol=0, atol=2e-11)
+
+
+# ---------------------------------------------------------------- nuclear attraction
+def test_ss_closed_form():
+    # (2 pi / p) K_AB F_0(p |PC|^2) with K_AB and P of the Gaussian product rule (Eq. 5)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        a, b = np.exp(rng.uniform(-2, 3, 2))
+        A, B, C = rng.uniform(-2, 2, (3, 3))
+        Z = 3.0
+        basis = W.make_basis([0, 0], [1, 1], [a, b], [1, 1], [A, B])
+        V = oracle.nuclear_attraction(basis, C[None], [Z])
+        p = a + b
+        P = (a * A + b * B) / p
+        K = math.exp(-a * b / p * np.sum((A - B) ** 2))
+        T = p * np.sum((P - C) ** 2)
+        F0 = math.sqrt(math.pi / T) * math.erf(math.sqrt(T)) / 2
+        N = lambda x: (2 * x / math.pi) ** 0.75
+        assert V[0, 1] == pytest.approx(Z * 2 * math.pi / p * K * F0 * N(a) * N(b), rel=1e-13)
+
+
+def _brute_force_V(basis, centers, charges, n_rho=56, n_theta=48, n_phi=96, rho_max=10.0):
+    n = len(basis["l"])
+    # numerical contracted normalisation of every shell
+    norms = []
+    for s in range(n):
+        pts, w = RM.sphere_grid(n_rho, rho_max, n_theta, n_phi, basis["xyz"][s])
+        w = w * np.linalg.norm(pts - basis["xyz"][s], axis=1)
+        f = RM.shell_values(basis, s, pts, np.ones(n))
+        norms.append(1.0 / math.sqrt(np.sum(w * f[:, 0] ** 2)))
+    nb = W.nbf(basis)
+    V = np.zeros((nb, nb))
+    off = np.concatenate([[0], np.cumsum(2 * basis["l"] + 1)])
+    for C, Z in zip(centers, charges):
+        pts, w = RM.sphere_grid(n_rho, rho_max, n_theta, n_phi, C)
+        F = np.concatenate([RM.shell_values(basis, s, pts, norms) for s in range(n)], axis=1)
+        V += Z * np.einsum("p,pi,pj->ij", w, F, F)
+    return V
+
+
+def test_brute_force_small_mixed():
+    basis = W.make_basis([0, 1, 2, 1], [2, 1, 2, 1], [1.2, 0.4, 0.9, 1.5, 0.6, 2.0], [0.7, 0.5, 1.0, 0.3, 0.8, 1.0],
+                         [[0, 0, 0], [0.0, 0.0, 0.0], [0.9, -0.4, 0.5], [-0.6, 0.7, -0.2]])
+    centers = np.array([[0.3, -0.5, 0.8], [-0.4, 0.2, -0.3]])
+    charges = np.array([2.0, 1.0])
+    V = oracle.nuclear_attraction(basis, centers, charges)
+    ref = _brute_force_V(basis, centers, charges)
+    assert np.max(np.abs(V - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+def test_brute_force_one_centre_l3():
+    # both shells at P = 0, nucleus at (0.3, -0.5, 0.8): the one-centre integral of Eq. 11's last
+    # line, including the coupled terms with L < l1 + l2 (l1 = 3, l2 = 2)
+    basis = W.make_basis([3, 2], [1, 1], [0.6, 0.7], [1, 1], [[0, 0, 0], [0, 0, 0]])
+    centers = np.array([[0.3, -0.5, 0.8]])
+    V = oracle.nuclear_attraction(basis, centers, [1.0])
+    ref = _brute_force_V(basis, centers, [1.0], n_rho=64, n_theta=56, n_phi=112)
+    assert np.max(np.abs(V - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+def test_hermitian():
+    basis, pos, Z = W.config1()
+    V = oracle.nuclear_attraction(basis, pos, Z)
+    assert np.array_equal(V, V.T)
+
+
+def test_translation_invariance():
+    basis = W.random_basis(11, 10, 5, max_prim=3)
+    C, Z = W.random_nuclei(12, 3)
+    V = oracle.nuclear_attraction(basis, C, Z)
+    shift = np.array([3.7, -11.2, 0.45])
+    b2 = dict(basis)
+    b2["xyz"] = basis["xyz"] + shift
+    V2 = oracle.nuclear_attraction(b2, C + shift, Z)
+    assert np.max(np.abs(V - V2)) < 1e-12 * np.max(np.abs(V))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_rotation_covariance(seed):
+    basis = W.random_basis(20 + seed, 9, 6, max_prim=2)
+    C, Z = W.random_nuclei(30 + seed, 3)
+    R = RM.rotation_matrix(seed)
+    V = oracle.nuclear_attraction(basis, C, Z)
+    b2 = dict(basis)
+    b2["xyz"] = basis["xyz"] @ R.T
+    V2 = oracle.nuclear_attraction(b2, C @ R.T, Z)
+    off = np.concatenate([[0], np.cumsum(2 * basis["l"] + 1)])
+    D = [RM.wigner_real(int(l), R) for l in basis["l"]]
+    for a in range(len(basis["l"])):
+        for b in range(len(basis["l"])):
+            blk = V[off[a]:off[a + 1], off[b]:off[b + 1]]
+            blk2 = V2[off[a]:off[a + 1], off[b]:off[b + 1]]
+            assert np.allclose(D[a] @ blk @ D[b].T, blk2, rtol=0, atol=1e-11 * np.max(np.abs(V)))
+
+
+def test_linear_in_charges_and_additive_over_nuclei():
+    basis = W.random_basis(5, 8, 4, max_prim=3)
+    C, Z = W.random_nuclei(6, 4)
+    V = oracle.nuclear_attraction(basis, C, Z)
+    parts = sum(oracle.nuclear_attraction(basis, C[i:i + 1], [1.0]) * Z[i] for i in range(4))
+    assert np.allclose(V, parts, rtol=1e-13, atol=1e-14)
+
+
+def test_far_field_limit():
+    # V_ab -> Z S_ab / |C| as |C| -> infinity (monopole of the product distribution)
+    basis = W.random_basis(8, 8, 4, max_prim=3, box=1.0)
+    S = oracle.overlap(basis)
+    R = 1e6
+    C = np.array([[R, 0.3 * R, -0.2 * R]])
+    dist = np.linalg.norm(C[0] - basis["xyz"].mean(axis=0))
+    V = oracle.nuclear_attraction(basis, C, [2.0])
+    assert np.allclose(V * dist / 2.0, S, rtol=0, atol=1e-5)
+
+
+def test_degenerate_geometries():
+    # nucleus at the product centre and coincident shell centres are valid inputs
+    basis = W.make_basis([2, 2], [1, 1], [1.0, 1.0], [1, 1], [[0.5, 0.5, 0.5], [0.5, 0.5, 0.5]])
+    V = oracle.nuclear_attraction(basis, np.array([[0.5, 0.5, 0.5]]), [1.0])
+    assert np.all(np.isfinite(V))
+    ref = _brute_force_V(basis, np.array([[0.5, 0.5, 0.5]]), [1.0])
+    assert np.max(np.abs(V - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("la,lb", [(8, 8), (8, 5), (7, 7), (6, 3)])
+def test_double_oracle_certified_by_extended_precision(la, lb):
+    # the double build against the same code in long double (80-bit x86 / binary128 aarch64)
+    tri = W.config5(12, replica=9)
+    worst = 0.0
+    for basis, C, Z in tri:
+        b = dict(basis)
+        b["l"] = np.array([la, lb], dtype=np.int32)
+        V = oracle.nuclear_attraction(b, C, Z)
+        Vl = oracle.nuclear_attraction(b, C, Z, precision="ld")
+        scale = np.max(np.abs(Vl))
+        if scale == 0:
+            continue
+        err = np.abs(V - Vl) / (1e-13 + 1e-11 * np.abs(Vl))
+        worst = max(worst, float(np.max(err)))
+    assert oracle.real_bits("ld") > 64
+    assert worst <= 1.0
