@@ -1,0 +1,335 @@
+"""Benchmark: SHGO nuclear-attraction shell-triples/s on GB300.
+
+Workload (one step): the full nuclear-attraction matrix V of one molecule of the high-l FP64
+configuration: 32 atoms in a 20 bohr cube, Z ~ U{1..10}, one uncontracted shell per l = 0..6 on
+every atom (224 shells, 1568 functions, 25,200 shell pairs), all 32 nuclei -> 806,400
+shell-triples per step.  Steps cycle over seeded replicas of that distribution, all resident in
+HBM before timing.  Between steps L2 is flushed by writing a 256 MiB buffer (outside the step
+events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl shgo|reference]
+
+--impl reference times the plain CPU oracle (the Cartesian McMurchie-Davidson route) on the host
+cores on the same workload, each step one replica's full V.  Under torchrun (N > 1) every rank
+runs its own replicas (no collective on the data path; "replicas only") and rank 0 prints one
+JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SHGO nuclear-attraction shell-triples/s per (la,lb); speedup vs plain @1e-10"
+UNIT = "shell-triples/s"
+WORKLOAD = "high-l FP64: 32 atoms / 20 bohr cube, one uncontracted shell per l=0..6 per atom, 32 nuclei"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (recipe table); a DFMA probe measured 1.20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "power_w_median": statistics.median(power) if power else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_rate(replicas, seconds: float, threads: int):
+    """Oracle throughput on whole replicas (full V each) until `seconds` of wall time are used."""
+    import oracle
+    oracle.build()
+    done = 0
+    triples = 0
+    t0 = time.perf_counter()
+    while True:
+        basis, C, Z = replicas[done % len(replicas)]
+        oracle.nuclear_attraction(basis, C, Z, threads=threads)
+        n = len(basis["l"])
+        triples += n * (n + 1) // 2 * len(Z)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return triples / el, done, el
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_2404_16245_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    replicas = [W.config2(replica=r) for r in range(4)]
+    import oracle
+    oracle.build()
+    for _ in range(max(0, args.warmup)):
+        b, C, Z = replicas[0]
+        oracle.nuclear_attraction(b, C, Z, threads=threads)
+    times = []
+    triples = 0
+    for k in range(args.steps):
+        b, C, Z = replicas[k % len(replicas)]
+        t0 = time.perf_counter()
+        oracle.nuclear_attraction(b, C, Z, threads=threads)
+        times.append(time.perf_counter() - t0)
+        n = len(b["l"])
+        triples += n * (n + 1) // 2 * len(Z)
+    total = sum(times)
+    value = triples / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps, each one replica's full V (806,400 shell-triples)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_shgo(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    R = args.replicas
+    reps = [W.config2(replica=rank * R + r) for r in range(R)]
+    bases = [shgo.Basis(b) for b, _, _ in reps]
+    cents = [torch.tensor(C, device=dev) for _, C, _ in reps]
+    chgs = [torch.tensor(Z, device=dev) for _, _, Z in reps]
+    outs = [torch.empty((B.nbf, B.nbf), dtype=torch.float64, device=dev) for B in bases]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(k):
+        i = k % R
+        shgo.shgo_nuclear_attraction(bases[i].handle, cents[i].shape[0], cents[i].data_ptr(), chgs[i].data_ptr(),
+                                     outs[i].data_ptr(), stream)
+
+    flops, trip = shgo.shgo_basis_flops(bases[0].handle, cents[0].shape[0])
+    triples_per_step = float(trip[0])
+    launches_per_step = shgo.shgo_basis_launches(bases[0].handle)
+
+    for k in range(max(3, args.warmup)):
+        step(k)
+    torch.cuda.synchronize()
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev_s[k].record(stream)
+        step(k)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
+    tot_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(tot_ms, op=dist.ReduceOp.MAX)
+    ms_per_step = float(tot_ms.item()) / args.steps
+    value = ws * triples_per_step / (ms_per_step / 1e3)
+
+    # dominant kernel: live phase timings (CUDA events on the launching stream)
+    ph = np.zeros(2)
+    nrep = max(3, min(R, 8))
+    for i in range(nrep):
+        flush.zero_()
+        a, b = shgo.shgo_nuclear_attraction_timed(bases[i % R].handle, cents[i % R].shape[0],
+                                                  cents[i % R].data_ptr(), chgs[i % R].data_ptr(),
+                                                  outs[i % R].data_ptr(), stream)
+        ph += (a, b)
+    ph /= nrep
+    names = ["k_coupling_block", "k_pair_block"]
+    dom = int(np.argmax(ph))
+    achieved = flops[dom] / (ph[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); DFMA probe measured 1.20",
+                "phase_ms": [float(ph[0]), float(ph[1])], "phase_tflops": [float(flops[0] / ph[0] / 1e9),
+                                                                           float(flops[1] / ph[1] / 1e9)],
+                "algorithmic_flops_per_step": [float(flops[0]), float(flops[1])]}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin_C = [torch.tensor(C).pin_memory() for _, C, _ in reps]
+        pin_Z = [torch.tensor(Z).pin_memory() for _, _, Z in reps]
+        pin_V = [torch.empty((B.nbf, B.nbf), dtype=torch.float64).pin_memory() for B in bases]
+        dC = [torch.empty_like(c, device=dev) for c in pin_C]
+        dZ = [torch.empty_like(z, device=dev) for z in pin_Z]
+        ksteps = max(3, min(args.steps, 10))
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(ksteps):
+            i = k % R
+            b = reps[i][0]
+            Bh = shgo.Basis(b)  # host arrays -> library-owned device buffers
+            dC[i].copy_(pin_C[i], non_blocking=True)
+            dZ[i].copy_(pin_Z[i], non_blocking=True)
+            shgo.shgo_nuclear_attraction(Bh.handle, dC[i].shape[0], dC[i].data_ptr(), dZ[i].data_ptr(),
+                                         outs[i].data_ptr(), stream)
+            pin_V[i].copy_(outs[i], non_blocking=True)
+            torch.cuda.synchronize()
+            Bh.close()
+            h2d += sum(b[key].nbytes for key in ("l", "nprim", "exps", "coefs", "xyz")) + pin_C[i].nbytes + pin_Z[i].nbytes
+            d2h += pin_V[i].nbytes
+        el = time.perf_counter() - t0
+        e2e = {"value": ws * triples_per_step * ksteps / el, "unit": UNIT, "h2d_bytes_per_step": h2d // ksteps,
+               "d2h_bytes_per_step": d2h // ksteps, "steps": ksteps,
+               "note": "basis upload + pinned H2D of nuclei + kernels + D2H of V, wall clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, done, el = oracle_rate(reps, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{done} full replicas of the benchmark workload in {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shell_triples_per_step": triples_per_step, "replicas": R,
+                       "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write, outside step events)",
+                       "wall_s_timed_region": wall},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    for B in bases:
+        B.close()
+    return 0
+
+
+def run_profile_case() -> int:
+    """Small fixed case for ncu captures: one warm and one measured V of the benchmark workload."""
+    import torch
+
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+    b, C, Z = W.config2()
+    B = shgo.Basis(b)
+    Cd = torch.tensor(C, device="cuda")
+    Zd = torch.tensor(Z, device="cuda")
+    for _ in range(2):
+        V = shgo.nuclear_attraction(B, Cd, Zd)
+    torch.cuda.synchronize()
+    print("profile case ok", tuple(V.shape))
+    B.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", action="store_true", help="one warm + one measured call, for ncu")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="shgo", choices=["shgo", "reference"])
+    ap.add_argument("--replicas", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case()
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, ws, rank)
+        return run_shgo(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

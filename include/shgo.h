@@ -1,0 +1,149 @@
+/*
+ * shgo.h - C ABI of the GB300 (sm_103a) library for nuclear-attraction integrals over
+ * contracted solid-harmonic Gaussian orbitals (SHGOs), evaluated the way arXiv 2404.16245
+ * describes: Gaussian product (Eq. 5), translation of both orbitals to the product centre P
+ * by the solid-harmonic addition theorem (Eqs. 7-8, "vector uncoupling"), coupling of the two
+ * harmonics at P (Clebsch-Gordan product rule, Supp. Eq. 4) and Boys functions (Eq. 12 and the
+ * text after it), then contraction over primitives and nuclei (Eq. 11).
+ *
+ * Conventions shared by every entry point:
+ *  - Lengths in bohr.  Orbitals follow Eq. 1 with Racah-normalised real solid harmonics
+ *    (Eq. 2, Condon-Shortley phase): S_l0 = Y_l^0, S_{l,m>0} = (-1)^m sqrt2 Re Y_l^m,
+ *    S_{l,-m} = (-1)^m sqrt2 Im Y_l^m, so S_11 = x, S_1,-1 = y, S_10 = z.
+ *  - Coefficients multiply normalised primitives (N(l, alpha) of Eq. 1); each contracted
+ *    function is renormalised to <phi|phi> = 1.
+ *  - Function order: shells in input order, m = -l..l inside a shell.
+ *  - V_ab = + sum_C Z_C <phi_a | 1/|r - C| | phi_b>  (no minus sign).
+ *  - Device pointers are caller-owned CUDA device memory on the basis's device.  Calls that take
+ *    a stream are asynchronous and stream-ordered (stream = a cudaStream_t, NULL = the legacy
+ *    default stream).  Errors found before any launch are returned synchronously and the
+ *    outputs are left untouched; a CUDA error is returned as SHGO_ERR_CUDA.
+ *  - Failing calls leave a message for shgo_last_error() (thread-local).
+ */
+#ifndef SHGO_H
+#define SHGO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SHGO_OK = 0,
+  SHGO_ERR_INVALID_ARG = 1,   /* NULL pointer, negative count, non-finite or non-positive exponent */
+  SHGO_ERR_UNSUPPORTED_L = 2, /* a shell with l > SHGO_LMAX */
+  SHGO_ERR_OOM = 3,           /* device or host allocation failed */
+  SHGO_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  SHGO_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+  SHGO_ERR_NUMERIC = 6        /* non-finite values detected */
+} shgo_status;
+
+#define SHGO_LMAX 8
+
+typedef enum {
+  SHGO_PREC_FP64 = 0,     /* every step in FP64 */
+  SHGO_PREC_FP32_BULK = 1 /* FP32 nucleus sums and coupling with compensated sums; FP64 Boys */
+} shgo_precision;
+
+typedef struct {
+  int32_t precision; /* a shgo_precision value */
+  int32_t device;    /* CUDA device ordinal, -1 = the current device */
+} shgo_options;
+
+/* Opaque basis: host copies of the shells, their normalised contraction coefficients, the
+ * class-sorted shell-pair lists and the device buffers built from them.  Library-owned. */
+typedef struct shgo_basis shgo_basis;
+
+/* Nuclear positions: n rows of (x, y, z), device pointer, row-major, bohr. */
+typedef struct {
+  int64_t n;
+  const double* xyz;
+} shgo_centers;
+
+/*
+ * Build a basis of n_shells contracted shells (Eq. 1).
+ *   l[s]          angular momentum of shell s, 0 <= l[s] <= SHGO_LMAX          (host)
+ *   n_prim[s]     primitives of shell s, 1..64                                   (host)
+ *   exponents     sum(n_prim) Gaussian exponents alpha > 0, shell after shell    (host)
+ *   coefs         sum(n_prim) contraction coefficients of normalised primitives  (host)
+ *   shell_xyz     n_shells x 3 centres a (bohr)                                  (host)
+ *   opt           NULL = FP64 on the current device
+ * The host arrays are copied; the caller keeps ownership.  On success *out receives a handle to
+ * release with shgo_free().  Device memory for the pair lists, tables and the per-primitive-pair
+ * coupling buffer is allocated here, on the selected device.
+ */
+shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
+                              const double* coefs, const double* shell_xyz, const shgo_options* opt,
+                              shgo_basis** out);
+
+/* Number of basis functions sum(2 l + 1) and of unique shell pairs n(n+1)/2. */
+int64_t shgo_basis_nbf(const shgo_basis* basis);
+int64_t shgo_basis_npairs(const shgo_basis* basis);
+
+/*
+ * V_ab = sum_C Z_C <phi_a|1/|r - C||phi_b> for every basis function pair (Eq. 11 with the one-
+ * centre integral of Eq. 12 in its coupled form).
+ *   centers   n nuclei, device [n][3] (n = 0 gives V = 0)
+ *   charges   device [n], Z_C
+ *   out       device [nbf][nbf] row-major FP64, fully overwritten (both triangles)
+ *   stream    cudaStream_t the kernels are queued on
+ * Asynchronous.  Not reentrant for one basis: calls on the same basis must be ordered (they
+ * share the basis's coupling buffer).
+ */
+shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers* centers, const double* charges,
+                                    double* out, void* stream);
+
+/* Same computation as shgo_nuclear_attraction, with CUDA events recorded on `stream` around
+ * the two kernel phases; blocks until they complete and writes their device durations (ms):
+ * phase_ms[0] = primitive-pair coupling blocks (Gaussian product, Boys, S_LM(C - P), nucleus
+ * sums), phase_ms[1] = shell-pair blocks (Gaunt coupling, primitive contraction, translation,
+ * write).  For measurement; the arithmetic and launches are those of the plain call. */
+shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_centers* centers,
+                                          const double* charges, double* out, void* stream, double* phase_ms);
+
+/* Algorithmic FP64 operation counts (an FMA counts 2) of one shgo_nuclear_attraction call with
+ * n_centers nuclei, per kernel phase as in shgo_nuclear_attraction_timed:
+ *   flops[0]  per primitive-pair x nucleus: geometry, Boys (tabulated Taylor + recursion), the
+ *             radial factors, S_LM(C - P) by recursion, and 2 per entry of R[L,M,k];
+ *   flops[1]  per primitive pair: 2 per Gaunt term + 4 per W entry; per shell pair: building
+ *             T_A, T_B and the two dense products T_A W T_B^T.
+ * triples[0] receives the shell-triples (unique shell pairs x nuclei), triples[1] the primitive
+ * triples (primitive pairs x nuclei). */
+shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples);
+
+/* Number of kernel launches one shgo_nuclear_attraction call on this basis makes (n > 0). */
+int64_t shgo_basis_launches(const shgo_basis* basis);
+
+/* Release a basis and its device memory (synchronises its device).  NULL-safe. */
+void shgo_free(shgo_basis* basis);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* shgo_last_error(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * Host-side views of the library's own tables and scalar algorithms, for testing them against
+ * the mathematics without a GPU.  None of these is used on the device path.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Real solid harmonics S_lm(r), m = -l..l, of Eq. 2 by the library's recursion:
+ * out[p * (2l+1) + m + l] for the npts points xyz[3p..3p+2].  l <= 2 * SHGO_LMAX. */
+shgo_status shgo_host_solid_harmonics(int32_t l, int64_t npts, const double* xyz, double* out);
+
+/* Real coupling coefficient G with S_{l1 m1}(r) S_{l2 m2}(r) = sum_{L,M} G r^{l1+l2-L} S_{LM}(r)
+ * (the Clebsch-Gordan product rule behind Supp. Eq. 4, mapped to real harmonics).  l1, l2 <= 8. */
+double shgo_host_gaunt(int32_t l1, int32_t m1, int32_t l2, int32_t m2, int32_t L, int32_t M);
+
+/* Real translation coefficient E with S_{la,ma}(x + y) = sum E S_{l1,m1}(x) S_{la-l1,nu}(y):
+ * the addition theorem of Eq. 7 with the vector-coupling coefficients of Eq. 8, mapped to real
+ * harmonics.  la <= 8. */
+double shgo_host_translation(int32_t la, int32_t ma, int32_t l1, int32_t m1, int32_t nu);
+
+/* F_n(T), n = 0..nmax (nmax <= 2 * SHGO_LMAX + 1), by the device algorithm (tabulated Taylor
+ * expansion and downward recursion below T = 40, asymptotic start and upward recursion above). */
+shgo_status shgo_host_boys(int32_t nmax, double T, double* F);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHGO_H */

@@ -1,0 +1,335 @@
+// C ABI of the library: argument checks, primitive normalisation (Eq. 1), class-sorted shell
+// and primitive-pair lists, device buffers, and the host-side table views.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "shgo_internal.h"
+#include "shgo_math.h"
+
+using namespace shgo;
+
+namespace {
+thread_local std::string g_last_error;
+
+shgo_status fail(shgo_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+// N(l, alpha)^-2 = int S_lm^2 e^{-2 alpha r^2} d^3r = pi^{3/2} (2l-1)!! / (2^l (2 alpha)^{l+3/2})
+double prim_norm(int l, double alpha) {
+  long double df = 1;
+  for (int k = 2 * l - 1; k > 1; k -= 2) df *= k;
+  const long double n2 = std::pow(3.14159265358979323846264338327950288L, 1.5L) * df /
+                         (std::pow(2.0L, (long double)l) * std::pow(2.0L * alpha, (long double)l + 1.5L));
+  return (double)(1.0L / std::sqrt(n2));
+}
+}  // namespace
+
+struct shgo_basis {
+  int device = 0;
+  int n_shells = 0;
+  int64_t nbf = 0;
+  int64_t npairs = 0;
+  std::vector<ClassWork> work;
+  DeviceBasis d;
+  const DeviceTables* tabs = nullptr;
+  std::vector<void*> allocations;
+};
+
+namespace {
+template <typename T>
+shgo_status dev_upload(shgo_basis* b, T** dst, const std::vector<T>& src, std::string* err) {
+  const size_t bytes = sizeof(T) * (src.empty() ? 1 : src.size());
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+  }
+  b->allocations.push_back(*dst);
+  if (!src.empty()) {
+    e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      *err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+      return SHGO_ERR_CUDA;
+    }
+  }
+  return SHGO_OK;
+}
+
+void release(shgo_basis* b) {
+  if (!b) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  for (void* p : b->allocations) cudaFree(p);
+  cudaSetDevice(prev);
+  delete b;
+}
+}  // namespace
+
+extern "C" {
+
+const char* shgo_last_error(void) { return g_last_error.c_str(); }
+
+shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
+                              const double* coefs, const double* shell_xyz, const shgo_options* opt,
+                              shgo_basis** out) {
+  g_last_error.clear();
+  if (!out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_shells < 0) return fail(SHGO_ERR_INVALID_ARG, "n_shells < 0");
+  if (n_shells > 0 && (!l || !n_prim || !exponents || !coefs || !shell_xyz))
+    return fail(SHGO_ERR_INVALID_ARG, "NULL basis array");
+  if (opt && opt->precision != SHGO_PREC_FP64 && opt->precision != SHGO_PREC_FP32_BULK)
+    return fail(SHGO_ERR_INVALID_ARG, "unknown precision mode");
+  int64_t nprim_total = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    if (l[s] < 0) return fail(SHGO_ERR_INVALID_ARG, "negative l in shell " + std::to_string(s));
+    if (l[s] > kLmax) return fail(SHGO_ERR_UNSUPPORTED_L, "l > 8 in shell " + std::to_string(s));
+    if (n_prim[s] < 1 || n_prim[s] > 64)
+      return fail(SHGO_ERR_INVALID_ARG, "n_prim outside 1..64 in shell " + std::to_string(s));
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(shell_xyz[3 * s + c])) return fail(SHGO_ERR_INVALID_ARG, "non-finite shell centre");
+    nprim_total += n_prim[s];
+  }
+  for (int64_t i = 0; i < nprim_total; ++i) {
+    if (!(exponents[i] > 0) || !std::isfinite(exponents[i]))
+      return fail(SHGO_ERR_INVALID_ARG, "exponent must be finite and > 0");
+    if (!std::isfinite(coefs[i])) return fail(SHGO_ERR_INVALID_ARG, "non-finite contraction coefficient");
+  }
+  int device = 0;
+  if (opt && opt->device >= 0) {
+    device = opt->device;
+  } else if (cudaGetDevice(&device) != cudaSuccess) {
+    return fail(SHGO_ERR_CUDA, "no CUDA device");
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return fail(SHGO_ERR_CUDA, "cudaSetDevice failed");
+
+  auto* b = new shgo_basis();
+  b->device = device;
+  b->n_shells = n_shells;
+  std::string err;
+
+  // primitive offsets, normalised coefficients (Eq. 1 normalisation, contracted renormalisation)
+  std::vector<int> poff(n_shells + 1, 0);
+  for (int s = 0; s < n_shells; ++s) poff[s + 1] = poff[s] + n_prim[s];
+  std::vector<double> pexp(exponents, exponents + nprim_total), pcoef(nprim_total);
+  for (int s = 0; s < n_shells; ++s) {
+    const int ls = l[s];
+    for (int i = 0; i < n_prim[s]; ++i) pcoef[poff[s] + i] = coefs[poff[s] + i] * prim_norm(ls, exponents[poff[s] + i]);
+    // <phi|phi> = sum_ij d_i d_j (2 sqrt(a_i a_j)/(a_i + a_j))^{l+3/2} / (N_i N_j) with d = c N
+    long double self = 0;
+    for (int i = 0; i < n_prim[s]; ++i)
+      for (int j = 0; j < n_prim[s]; ++j) {
+        const long double ai = exponents[poff[s] + i], aj = exponents[poff[s] + j];
+        const long double ov = std::pow(2 * std::sqrt(ai * aj) / (ai + aj), (long double)ls + 1.5L);
+        self += (long double)coefs[poff[s] + i] * coefs[poff[s] + j] * ov;
+      }
+    if (!(self > 0)) {
+      release(b);
+      return fail(SHGO_ERR_NUMERIC, "contracted shell " + std::to_string(s) + " has zero norm");
+    }
+    const double scale = (double)(1.0L / std::sqrt(self));
+    for (int i = 0; i < n_prim[s]; ++i) pcoef[poff[s] + i] *= scale;
+  }
+  std::vector<int64_t> foff(n_shells + 1, 0);
+  for (int s = 0; s < n_shells; ++s) foff[s + 1] = foff[s] + 2 * l[s] + 1;
+  b->nbf = foff[n_shells];
+
+  // class-sorted pairs (la >= lb), and their primitive pairs
+  std::vector<std::vector<int>> by_l(kLmax + 1);
+  for (int s = 0; s < n_shells; ++s) by_l[l[s]].push_back(s);
+  std::vector<int> pa, pb;
+  std::vector<int64_t> ppoff;
+  std::vector<int> pp_pair, pp_ij;
+  int64_t ppcount = 0;
+  for (int la = 0; la <= kLmax; ++la)
+    for (int lb = 0; lb <= la; ++lb) {
+      ClassWork w{la, lb, 0, (int)pa.size(), 0, ppcount};
+      for (size_t x = 0; x < by_l[la].size(); ++x) {
+        const size_t ylim = (la == lb) ? x + 1 : by_l[lb].size();
+        for (size_t y = 0; y < ylim; ++y) {
+          const int sa = by_l[la][x], sb = by_l[lb][y];
+          pa.push_back(sa);
+          pb.push_back(sb);
+          ppoff.push_back(ppcount);
+          for (int i = 0; i < n_prim[sa]; ++i)
+            for (int j = 0; j < n_prim[sb]; ++j) {
+              pp_pair.push_back((int)pa.size() - 1);
+              pp_ij.push_back((i << 8) | j);
+            }
+          ppcount += (int64_t)n_prim[sa] * n_prim[sb];
+          ++w.npairs;
+        }
+      }
+      w.npp = ppcount - w.pp_base;
+      if (w.npairs > 0) b->work.push_back(w);
+    }
+  b->npairs = (int64_t)pa.size();
+  int64_t rlen = 0;
+  for (const auto& w : b->work) rlen += w.npp * n_r(w.la + w.lb);
+
+  std::vector<double> xyz(shell_xyz, shell_xyz + 3 * (size_t)n_shells);
+  std::vector<int> lv(l, l + n_shells), npv(n_prim, n_prim + n_shells);
+  std::vector<int> poffv(poff.begin(), poff.end() - (n_shells >= 0 ? 1 : 0));
+  shgo_status st = SHGO_OK;
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_xyz, xyz, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_l, lv, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_nprim, npv, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_poff, poffv, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_foff, foff, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.prim_exp, pexp, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.prim_coef, pcoef, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_a, pa, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_b, pb, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_ppoff, ppoff, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_pair, pp_pair, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_ij, pp_ij, &err);
+  if (st == SHGO_OK) {
+    b->d.rbuf_len = rlen;
+    cudaError_t e = cudaMalloc((void**)&b->d.rbuf, sizeof(double) * (size_t)(rlen > 0 ? rlen : 1));
+    if (e != cudaSuccess) {
+      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+      err = std::string("cudaMalloc coupling buffer: ") + cudaGetErrorString(e);
+    } else {
+      b->allocations.push_back(b->d.rbuf);
+    }
+  }
+  if (st == SHGO_OK) st = device_tables(device, &b->tabs, &err);
+  if (st != SHGO_OK) {
+    release(b);
+    return fail(st, err);
+  }
+  *out = b;
+  return SHGO_OK;
+}
+
+int64_t shgo_basis_nbf(const shgo_basis* basis) { return basis ? basis->nbf : -1; }
+int64_t shgo_basis_npairs(const shgo_basis* basis) { return basis ? basis->npairs : -1; }
+
+shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers* centers, const double* charges,
+                                    double* out, void* stream) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (!centers || centers->n < 0) return fail(SHGO_ERR_INVALID_ARG, "centers is NULL or negative count");
+  if (centers->n > 0 && (!centers->xyz || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
+  if (basis->nbf > 0 && !out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  std::string err;
+  const shgo_status st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
+                                                   centers->xyz, charges, out, (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+
+shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_centers* centers,
+                                          const double* charges, double* out, void* stream, double* phase_ms) {
+  g_last_error.clear();
+  if (!basis || !phase_ms) return fail(SHGO_ERR_INVALID_ARG, "basis or phase_ms is NULL");
+  if (!centers || centers->n < 0) return fail(SHGO_ERR_INVALID_ARG, "centers is NULL or negative count");
+  if (centers->n > 0 && (!centers->xyz || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
+  if (basis->nbf > 0 && !out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) cudaEventCreate(&e);
+  std::string err;
+  shgo_status st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
+                                             centers->xyz, charges, out, (cudaStream_t)stream, &err, ev);
+  if (st == SHGO_OK) {
+    cudaError_t e = cudaEventSynchronize(ev[2]);
+    float t0 = 0, t1 = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    if (e != cudaSuccess) {
+      st = SHGO_ERR_CUDA;
+      err = cudaGetErrorString(e);
+    }
+    phase_ms[0] = t0;
+    phase_ms[1] = t1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+
+int64_t shgo_basis_launches(const shgo_basis* basis) { return basis ? launches_per_call(basis->work, basis->nbf) : -1; }
+
+shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples) {
+  if (!basis || !flops || !triples || n_centers < 0) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  const Tables& t = tables_host();
+  double f0 = 0, f1 = 0, st = 0, pt = 0;
+  for (const auto& w : basis->work) {
+    const int la = w.la, lb = w.lb, lam = la + lb;
+    const double nB = n_beta(lam), nR = n_r(lam);
+    // per primitive triple
+    double s_lm = lam >= 2 ? 5.0 : 0.0;
+    for (int l = 1; l < lam; ++l) s_lm += 8.0 * l + 8.0;
+    const double boys = 4.0 * kBoysK + 1 + 3.0 * lam;
+    const double per_triple = 9 + boys + (lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
+    f0 += per_triple * (double)w.npp * (double)n_centers + nR * (double)w.npp;
+    // per primitive pair: coupling
+    const int cid = class_id(la, lb);
+    const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
+    const double terms = t.g_rowptr[t.g_rowbase[cid] + nW];
+    f1 += (2.0 * terms + 4.0 * nW) * (double)w.npp;
+    // per shell pair: translation matrices and the two products
+    double ta = 0, tb = 0;
+    for (int l1 = 0; l1 <= la; ++l1) ta += (2.0 * l1 + 1) * 2.0 * (2 * (la - l1) + 1);
+    for (int l2 = 0; l2 <= lb; ++l2) tb += (2.0 * l2 + 1) * 2.0 * (2 * (lb - l2) + 1);
+    const double na = 2 * la + 1, nb = 2 * lb + 1;
+    f1 += (na * ta + nb * tb + 2.0 * nWa * nb * nWb + 2.0 * na * nb * nWa) * (double)w.npairs;
+    st += (double)w.npairs * (double)n_centers;
+    pt += (double)w.npp * (double)n_centers;
+  }
+  flops[0] = f0;
+  flops[1] = f1;
+  triples[0] = st;
+  triples[1] = pt;
+  return SHGO_OK;
+}
+
+void shgo_free(shgo_basis* basis) { release(basis); }
+
+shgo_status shgo_host_solid_harmonics(int32_t l, int64_t npts, const double* xyz, double* out) {
+  if (l < 0 || l > kHarmMax || npts < 0 || (npts > 0 && (!xyz || !out)))
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  const HarmCoef& hc = harm_coef_host();
+  std::vector<double> buf(n_harm(l));
+  for (int64_t p = 0; p < npts; ++p) {
+    solid_harmonics(l, xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], buf.data(), 1, hc.a, hc.b, hc.c);
+    for (int m = -l; m <= l; ++m) out[p * (2 * l + 1) + m + l] = buf[harm_index(l, m)];
+  }
+  return SHGO_OK;
+}
+
+double shgo_host_gaunt(int32_t l1, int32_t m1, int32_t l2, int32_t m2, int32_t L, int32_t M) {
+  if (l1 < 0 || l2 < 0 || l1 > kLmax || l2 > kLmax || L < 0) return 0.0;
+  return gaunt_real(l1, m1, l2, m2, L, M);
+}
+
+double shgo_host_translation(int32_t la, int32_t ma, int32_t l1, int32_t m1, int32_t nu) {
+  if (la < 0 || la > kLmax) return 0.0;
+  return translation_real(la, ma, l1, m1, nu);
+}
+
+shgo_status shgo_host_boys(int32_t nmax, double T, double* F) {
+  if (nmax < 0 || nmax > kLamMax + 1 || !F || !(T >= 0) || !std::isfinite(T))
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  boys_host(nmax, T, F);
+  return SHGO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the host API, the table builder and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/shgo.h"
+
+namespace shgo {
+
+constexpr int kLmax = SHGO_LMAX;          // largest shell l
+constexpr int kLamMax = 2 * kLmax;         // largest la + lb
+constexpr int kHarmMax = kLamMax;          // largest l of S_lm(C - P)
+
+// Boys grid: T_g = g * h for g = 0..kBoysNg-1, h = 1/16, up to T = kBoysTsw.  Row g holds
+// exp(-T_g) followed by F_n(T_g), n = 0..kBoysNmax.  A value is the Taylor expansion about the
+// nearest T_g with kBoysK + 1 terms (|T - T_g| <= 1/32).
+constexpr int kBoysK = 7;
+constexpr double kBoysInvH = 16.0;
+constexpr double kBoysTsw = 40.0;
+constexpr int kBoysNg = 641;
+constexpr int kBoysNmax = kLamMax + 1 + kBoysK;  // 24: F_{Lambda+1} may be needed by the expansion
+constexpr int kBoysStride = kBoysNmax + 2;       // exp slot + orders 0..kBoysNmax
+
+// Sizes of the per-primitive-pair layouts for Lambda = la + lb.
+__host__ __device__ inline int n_harm(int lam) { return (lam + 1) * (lam + 1); }
+__host__ __device__ inline int kmax_of(int lam, int L) { return (lam - L) >> 1; }
+__host__ __device__ inline int n_beta(int lam) {
+  int n = 0;
+  for (int L = 0; L <= lam; ++L) n += kmax_of(lam, L) + 1;
+  return n;
+}
+__host__ __device__ inline int n_r(int lam) { return (lam + 1) * (lam + 2) * (lam + 3) / 6; }
+__host__ __device__ inline int harm_index(int l, int m) { return l * l + l + m; }
+
+// Coefficients of the real solid-harmonic recursion (Racah normalisation):
+//   S_{l+1,l+1}  = c_l (x S_{l,l} - y S_{l,-l})          (l >= 1; S_11 = x)
+//   S_{l+1,-l-1} = c_l (y S_{l,l} + x S_{l,-l})          (l >= 1; S_1-1 = y)
+//   S_{l+1,m}    = a_lm z S_{l,m} - b_lm r^2 S_{l-1,m}    (|m| <= l)
+// with c_l = sqrt((2l+1)/(2l+2)), a_lm = (2l+1)/sqrt((l+m+1)(l-m+1)),
+// b_lm = sqrt((l+m)(l-m)/((l+m+1)(l-m+1))).
+struct HarmCoef {
+  double a[(kHarmMax + 1) * (kHarmMax + 1)];
+  double b[(kHarmMax + 1) * (kHarmMax + 1)];
+  double c[kHarmMax + 1];
+};
+const HarmCoef& harm_coef_host();
+
+// Host tables, built once per process (long double arithmetic, stored as double).
+struct Tables {
+  std::vector<double> boys;  // [kBoysNg][kBoysStride]
+  // Real translation tensors: for la, entry (ma, l1, m1, nu) at etab[eoff[la] + ...] with the
+  // index ((ma + la) * (la+1)^2 + l1^2 + l1 + m1) * (2 la + 1) + (nu + la - l1) ... packed densely
+  // per (ma, l1 m1) over nu = -(la-l1)..(la-l1): see translation_index().
+  std::vector<double> etab;
+  std::vector<int> eoff;  // [kLmax + 2]
+  // Gaunt programs per class (la >= lb): CSR over W entries (l1 m1, l2 m2), row-major with
+  // (lb+1)^2 columns; each term is (R index for Lambda = la+lb, coefficient).
+  std::vector<int> g_rowptr;  // concatenated, class c rows at g_rowbase[c] .. + nW + 1
+  std::vector<int> g_ridx;
+  std::vector<double> g_coef;
+  std::vector<int> g_rowbase;  // [n classes]
+  std::vector<int> g_termbase; // [n classes]
+  // R layout per Lambda: packed (harm index | beta index << 12 | k << 24) for entry e.
+  std::vector<int> rmap;
+  std::vector<int> rmap_off;  // [kLamMax + 2]
+};
+const Tables& tables_host();
+
+inline int class_id(int la, int lb) { return la * (la + 1) / 2 + lb; }  // la >= lb
+constexpr int kNumClasses = (kLmax + 1) * (kLmax + 2) / 2;
+
+// Offset inside the la block of etab for (ma, l1, m1); nu runs over 2(la - l1) + 1 values.
+int translation_offset(int la, int ma, int l1, int m1);
+
+double gaunt_real(int l1, int m1, int l2, int m2, int L, int M);
+double translation_real(int la, int ma, int l1, int m1, int nu);
+void boys_host(int nmax, double T, double* F);
+
+// Device copies of the tables (one set per device, created on first use).
+struct DeviceTables {
+  double* boys = nullptr;
+  double* etab = nullptr;
+  int* eoff = nullptr;
+  int* g_rowptr = nullptr;
+  int* g_ridx = nullptr;
+  double* g_coef = nullptr;
+  int* rmap = nullptr;
+};
+shgo_status device_tables(int device, const DeviceTables** out, std::string* err);
+
+// Kernel launchers (shgo_kernels.cu).
+struct ClassWork {
+  int la, lb;
+  int npairs;      // shell pairs in this class
+  int pair_base;   // first pair of the class in the pair arrays
+  int64_t npp;     // primitive pairs of the class
+  int64_t pp_base; // first primitive pair of the class in the primitive-pair arrays
+};
+
+struct DeviceBasis {
+  // shells
+  double* shell_xyz = nullptr;  // [n_shells][3]
+  int* shell_l = nullptr;
+  int* shell_nprim = nullptr;
+  int* shell_poff = nullptr;    // first primitive
+  int64_t* shell_foff = nullptr;  // first function
+  double* prim_exp = nullptr;
+  double* prim_coef = nullptr;  // normalised contraction coefficient
+  // pairs, class-sorted; pair_a has l >= pair_b's l
+  int* pair_a = nullptr;
+  int* pair_b = nullptr;
+  int64_t* pair_ppoff = nullptr;  // first primitive pair of the pair
+  // primitive pairs, class-sorted: owning pair, i (prim of a), j (prim of b)
+  int* pp_pair = nullptr;
+  int* pp_ij = nullptr;          // i << 8 | j
+  int64_t* pp_roff = nullptr;    // offset of the pair's coupling block in rbuf
+  double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
+  int64_t rbuf_len = 0;
+};
+
+shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
+                                      const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
+                                      const double* centers, const double* charges, double* out,
+                                      cudaStream_t stream, std::string* err, cudaEvent_t* events = nullptr);
+int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
+
+}  // namespace shgo

@@ -1,0 +1,416 @@
+// CUDA kernels (sm_103a, FP64) of the SHGO nuclear-attraction path.
+//
+//  k_coupling_block  (S1 + S2): one warp per primitive pair (alpha_i on a, beta_j on b).
+//      Gaussian product (Eq. 5): p, P.  Then, for every nucleus C (one lane per nucleus,
+//      chunks of 32 or 16): d = C - P, T = p |d|^2, Boys F_0..F_Lambda(T), the radial factors
+//      beta_{L,k}(T) = sum_j k!/j! T^j F_{L+j}(T) scaled by Z_C, and the real solid harmonics
+//      S_LM(d); the lanes stage them in shared memory and then contract over the nuclei of the
+//      chunk, each lane owning entries of
+//          R[L,M,k] = sum_C Z_C S_LM(C - P) beta_{L,k}(T_C),
+//      which is stored as R' = 2 pi p^{-(k+1)} R (the one-centre integral of Eq. 12 in coupled
+//      form, before the Gaunt coupling).
+//  k_pair_block      (S3 + S4 + S5): one warp per shell pair.  Couples R' of each primitive
+//      pair with the real Gaunt coefficients into W[l1 m1][l2 m2], scales by c_i c_j K_AB
+//      (beta/p)^{la-l1} (alpha/p)^{lb-l2} and sums over primitive pairs (Eq. 11); then the
+//      translation ("vector uncoupling", Eq. 7) V = T_A W T_B^T with
+//      T_A[ma][l1 m1] = sum_nu E^{la}(ma; l1 m1; nu) S_{la-l1,nu}(b - a) and T_B likewise with
+//      a - b; writes the block and its transpose into V.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "shgo_internal.h"
+#include "shgo_math.h"
+
+namespace shgo {
+
+__constant__ HarmCoef c_harm;
+__constant__ BoysConst c_boys;
+__constant__ int c_lof[(kLmax + 1) * (kLmax + 1)];  // l of a packed harmonic index (l <= 8)
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ int odd_pad(int n) { return n | 1; }
+
+// Shared-memory bytes of one warp of k_coupling_block.
+__host__ __device__ inline size_t coupling_smem_per_warp(int lam, int nch) {
+  const int rs = (n_harm(lam) + n_beta(lam)) | 1;
+  return sizeof(double) * ((size_t)nch * rs + n_r(lam) + 16);
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int64_t pp_base, int64_t rbase,
+                                                       const int* __restrict__ pp_pair,
+                                                       const int* __restrict__ pp_ij, const int* __restrict__ pair_a,
+                                                       const int* __restrict__ pair_b,
+                                                       const double* __restrict__ shell_xyz,
+                                                       const int* __restrict__ shell_poff,
+                                                       const int* __restrict__ shell_nprim,
+                                                       const double* __restrict__ prim_exp, int64_t ncenters,
+                                                       const double* __restrict__ centers,
+                                                       const double* __restrict__ charges,
+                                                       const double* __restrict__ boys_tab,
+                                                       const int* __restrict__ rmap, double* __restrict__ rbuf) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int nS = n_harm(lam), nB = n_beta(lam), nR = n_r(lam);
+  const int rs = odd_pad(nS + nB);
+  double* rows = smem;
+  double* racc = smem + (size_t)NCH * rs;
+  double* scl = racc + nR;
+  for (int64_t w = blockIdx.x; w < npp; w += gridDim.x) {
+    const int64_t q = pp_base + w;
+    const int pr = pp_pair[q];
+    const int ij = pp_ij[q];
+    const int a = pair_a[pr], b = pair_b[pr];
+    const double ea = prim_exp[shell_poff[a] + (ij >> 8)];
+    const double eb = prim_exp[shell_poff[b] + (ij & 255)];
+    const double p = ea + eb;
+    const double rp = 1.0 / p;
+    const double Px = (ea * shell_xyz[3 * a] + eb * shell_xyz[3 * b]) * rp;
+    const double Py = (ea * shell_xyz[3 * a + 1] + eb * shell_xyz[3 * b + 1]) * rp;
+    const double Pz = (ea * shell_xyz[3 * a + 2] + eb * shell_xyz[3 * b + 2]) * rp;
+    for (int e = lane; e < nR; e += 32) racc[e] = 0.0;
+    for (int64_t c0 = 0; c0 < ncenters; c0 += NCH) {
+      __syncwarp();
+      if (lane < NCH) {
+        double* row = rows + (size_t)lane * rs;
+        const int64_t c = c0 + lane;
+        double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
+        if (c < ncenters) {
+          dx = centers[3 * c] - Px;
+          dy = centers[3 * c + 1] - Py;
+          dz = centers[3 * c + 2] - Pz;
+          z = charges[c];
+        }
+        const double T = p * (dx * dx + dy * dy + dz * dz);
+        boys_eval(lam, T, row, 1, boys_tab, c_boys);
+        // Z F_n, and T^k / k! behind it
+        for (int n = 0; n <= lam; ++n) row[n] *= z;
+        double* tk = row + lam + 1;
+        tk[0] = 1.0;
+        for (int k = 1; k <= (lam >> 1); ++k) tk[k] = tk[k - 1] * T * c_boys.inv_int[k];
+        // beta_{L,k} / k! = sum_j T^j/j! Z F_{L+j}  (running sum over k)
+        double* brow = row + nS;
+        int bo = 0;
+        for (int L = 0; L <= lam; ++L) {
+          const int km = (lam - L) >> 1;
+          double acc = row[L];
+          brow[bo] = acc;
+          for (int k = 1; k <= km; ++k) {
+            acc = fma(tk[k], row[L + k], acc);
+            brow[bo + k] = acc;
+          }
+          bo += km + 1;
+        }
+        solid_harmonics(lam, dx, dy, dz, row, 1, c_harm.a, c_harm.b, c_harm.c);
+      }
+      __syncwarp();
+      const int* rm = rmap;
+      for (int e = lane; e < nR; e += 32) {
+        const int code = __ldg(rm + e);
+        const int si = code & 0xfff, bi = nS + ((code >> 12) & 0xfff);
+        double acc = racc[e];
+#pragma unroll 8
+        for (int c = 0; c < NCH; ++c) acc = fma(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], acc);
+        racc[e] = acc;
+      }
+    }
+    // scale 2 pi k! p^{-(k+1)}
+    if (lane <= (lam >> 1)) {
+      double s = kTwoPi * rp;
+      for (int k = 1; k <= lane; ++k) s *= double(k) * rp;
+      scl[lane] = s;
+    }
+    __syncwarp();
+    double* out = rbuf + rbase + w * (int64_t)nR;
+    for (int e = lane; e < nR; e += 32) out[e] = racc[e] * scl[(__ldg(rmap + e) >> 24) & 0xff];
+    __syncwarp();
+  }
+}
+
+// Shared-memory bytes of one warp of k_pair_block.
+__host__ __device__ inline size_t pair_smem(int la, int lb) {
+  const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1);
+  const int lm = la > lb ? la : lb;
+  return sizeof(double) * ((size_t)nWa * nWb + (2 * la + 1) * nWa + (2 * lb + 1) * nWb + nWa * (2 * lb + 1) +
+                           (lm + 1) * (lm + 1) + la + 1 + lb + 1 + 8);
+}
+
+__device__ __forceinline__ int translation_offset_dev(int la, int ma, int l1, int m1) {
+  int per_ma = 0, below = 0;
+  for (int k = 0; k <= la; ++k) {
+    const int t = (2 * k + 1) * (2 * (la - k) + 1);
+    per_ma += t;
+    if (k < l1) below += t;
+  }
+  return (ma + la) * per_ma + below + (m1 + l1) * (2 * (la - l1) + 1);
+}
+
+__global__ void __launch_bounds__(32) k_pair_block(int la, int lb, int npairs, int pair_base, int64_t pp_base,
+                                                   int64_t rbase, const int* __restrict__ pair_a,
+                                                   const int* __restrict__ pair_b,
+                                                   const int64_t* __restrict__ pair_ppoff,
+                                                   const double* __restrict__ shell_xyz,
+                                                   const int* __restrict__ shell_poff,
+                                                   const int* __restrict__ shell_nprim,
+                                                   const int64_t* __restrict__ shell_foff,
+                                                   const double* __restrict__ prim_exp,
+                                                   const double* __restrict__ prim_coef,
+                                                   const double* __restrict__ etab, const int* __restrict__ eoff,
+                                                   const int* __restrict__ g_rowptr, const int* __restrict__ g_ridx,
+                                                   const double* __restrict__ g_coef, const double* __restrict__ rbuf,
+                                                   int64_t nbf, double* __restrict__ out) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31;
+  const int lam = la + lb;
+  const int nR = n_r(lam);
+  const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
+  const int na = 2 * la + 1, nb = 2 * lb + 1;
+  const int lm = la > lb ? la : lb;
+  double* W = smem;
+  double* TA = W + nW;
+  double* TB = TA + na * nWa;
+  double* X = TB + nb * nWb;
+  double* Sab = X + nWa * nb;
+  double* fa = Sab + (lm + 1) * (lm + 1);
+  double* fb = fa + la + 1;
+  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
+    const int pr = pair_base + w;
+    const int a = pair_a[pr], b = pair_b[pr];
+    const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
+    const double Bx = shell_xyz[3 * b], By = shell_xyz[3 * b + 1], Bz = shell_xyz[3 * b + 2];
+    const double ABx = Bx - Ax, ABy = By - Ay, ABz = Bz - Az;
+    const double ab2 = ABx * ABx + ABy * ABy + ABz * ABz;
+    __syncwarp();
+    if (lane == 0) solid_harmonics(lm, ABx, ABy, ABz, Sab, 1, c_harm.a, c_harm.b, c_harm.c);
+    for (int e = lane; e < nW; e += 32) W[e] = 0.0;
+    __syncwarp();
+    // translation matrices (Eq. 7 with Eq. 8 coefficients, real basis)
+    for (int e = lane; e < na * nWa; e += 32) {
+      const int ma = e / nWa - la, i1 = e % nWa, l1 = c_lof[i1], m1 = i1 - l1 * l1 - l1, lr = la - l1;
+      const double* ev = etab + eoff[la] + translation_offset_dev(la, ma, l1, m1);
+      double s = 0.0;
+      for (int nu = -lr; nu <= lr; ++nu) s = fma(ev[nu + lr], Sab[lr * lr + lr + nu], s);
+      TA[e] = s;
+    }
+    for (int e = lane; e < nb * nWb; e += 32) {
+      const int mb = e / nWb - lb, i2 = e % nWb, l2 = c_lof[i2], m2 = i2 - l2 * l2 - l2, lr = lb - l2;
+      const double* ev = etab + eoff[lb] + translation_offset_dev(lb, mb, l2, m2);
+      double s = 0.0;
+      for (int nu = -lr; nu <= lr; ++nu) s = fma(ev[nu + lr], Sab[lr * lr + lr + nu], s);
+      TB[e] = (lr & 1) ? -s : s;  // S_l(a - b) = (-1)^l S_l(b - a)
+    }
+    // coupling and primitive contraction
+    const int npa = shell_nprim[a], npb = shell_nprim[b];
+    const int64_t q0 = pair_ppoff[pr];
+    for (int ij = 0; ij < npa * npb; ++ij) {
+      const int i = ij / npb, j = ij % npb;
+      const double ea = prim_exp[shell_poff[a] + i], eb = prim_exp[shell_poff[b] + j];
+      const double p = ea + eb, rp = 1.0 / p;
+      const double pref = prim_coef[shell_poff[a] + i] * prim_coef[shell_poff[b] + j] * exp(-ea * eb * rp * ab2);
+      __syncwarp();
+      if (lane <= la) {
+        double v = 1.0;
+        const double r = eb * rp;
+        for (int k = 0; k < la - lane; ++k) v *= r;
+        fa[lane] = v;
+      }
+      if (lane <= lb) {
+        double v = 1.0;
+        const double r = ea * rp;
+        for (int k = 0; k < lb - lane; ++k) v *= r;
+        fb[lane] = v;
+      }
+      __syncwarp();
+      if (pref == 0.0) continue;
+      const double* R = rbuf + rbase + (q0 + ij - pp_base) * (int64_t)nR;
+      for (int e = lane; e < nW; e += 32) {
+        const int i1 = e / nWb, i2 = e % nWb;
+        const int t0 = g_rowptr[e], t1 = g_rowptr[e + 1];
+        double acc = 0.0;
+        for (int t = t0; t < t1; ++t) acc = fma(g_coef[t], R[g_ridx[t]], acc);
+        W[e] = fma(pref * fa[c_lof[i1]] * fb[c_lof[i2]], acc, W[e]);
+      }
+    }
+    __syncwarp();
+    // X = W T_B^T, V = T_A X
+    for (int e = lane; e < nWa * nb; e += 32) {
+      const int i1 = e / nb, mb = e % nb;
+      const double* wr = W + i1 * nWb;
+      const double* tb = TB + mb * nWb;
+      double s = 0.0;
+      for (int i2 = 0; i2 < nWb; ++i2) s = fma(wr[i2], tb[i2], s);
+      X[e] = s;
+    }
+    __syncwarp();
+    const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
+    for (int e = lane; e < na * nb; e += 32) {
+      const int ma = e / nb, mb = e % nb;
+      double s = 0.0;
+      if (a == b && ma > mb) {
+        // diagonal shell block: use the upper triangle for both halves (exact symmetry)
+        const double* ta = TA + mb * nWa;
+        for (int i1 = 0; i1 < nWa; ++i1) s = fma(ta[i1], X[i1 * nb + ma], s);
+      } else {
+        const double* ta = TA + ma * nWa;
+        for (int i1 = 0; i1 < nWa; ++i1) s = fma(ta[i1], X[i1 * nb + mb], s);
+      }
+      out[(fa0 + ma) * nbf + fb0 + mb] = s;
+      if (a != b) out[(fb0 + mb) * nbf + fa0 + ma] = s;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Device tables
+// ---------------------------------------------------------------------------------------------
+namespace {
+std::mutex g_tab_mu;
+DeviceTables g_tabs[64];
+bool g_tab_ok[64] = {};
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (src.empty() ? 1 : src.size()));
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+}  // namespace
+
+shgo_status device_tables(int device, const DeviceTables** out, std::string* err) {
+  if (device < 0 || device >= 64) {
+    *err = "device ordinal out of range";
+    return SHGO_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  if (g_tab_ok[device]) {
+    *out = &g_tabs[device];
+    return SHGO_OK;
+  }
+  const Tables& t = tables_host();
+  DeviceTables d;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = upload(&d.boys, t.boys);
+  if (e == cudaSuccess) e = upload(&d.etab, t.etab);
+  if (e == cudaSuccess) e = upload(&d.eoff, t.eoff);
+  if (e == cudaSuccess) e = upload(&d.g_rowptr, t.g_rowptr);
+  if (e == cudaSuccess) e = upload(&d.g_ridx, t.g_ridx);
+  if (e == cudaSuccess) e = upload(&d.g_coef, t.g_coef);
+  if (e == cudaSuccess) e = upload(&d.rmap, t.rmap);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
+  if (e == cudaSuccess) {
+    int lof[(kLmax + 1) * (kLmax + 1)];
+    for (int l = 0; l <= kLmax; ++l)
+      for (int m = -l; m <= l; ++m) lof[harm_index(l, m)] = l;
+    e = cudaMemcpyToSymbol(c_lof, lof, sizeof(lof));
+  }
+  if (e != cudaSuccess) {
+    *err = std::string("uploading tables: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+  }
+  g_tabs[device] = d;
+  g_tab_ok[device] = true;
+  *out = &g_tabs[device];
+  return SHGO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launch
+// ---------------------------------------------------------------------------------------------
+static int grid_cap(int64_t n, int per_sm) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+  }
+  const int64_t cap = (int64_t)nsm * per_sm;
+  return (int)(n < cap ? n : cap);
+}
+
+shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
+                                      const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
+                                      const double* centers, const double* charges, double* out,
+                                      cudaStream_t stream, std::string* err, cudaEvent_t* events) {
+  if (events) cudaEventRecord(events[0], stream);
+  if (nbf == 0 || ncenters == 0) {
+    if (events) cudaEventRecord(events[1], stream);
+  }
+  if (nbf == 0) {
+    if (events) cudaEventRecord(events[2], stream);
+    return SHGO_OK;
+  }
+  if (ncenters == 0) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nbf * (size_t)nbf, stream);
+    if (events) cudaEventRecord(events[2], stream);
+    if (e != cudaSuccess) {
+      *err = cudaGetErrorString(e);
+      return SHGO_ERR_CUDA;
+    }
+    return SHGO_OK;
+  }
+  const Tables& th = tables_host();
+  int64_t rbase = 0;
+  std::vector<int64_t> rbases(work.size());
+  for (size_t c = 0; c < work.size(); ++c) {
+    rbases[c] = rbase;
+    rbase += work[c].npp * n_r(work[c].la + work[c].lb);
+  }
+  for (size_t c = 0; c < work.size(); ++c) {
+    const ClassWork& w = work[c];
+    if (w.npp == 0) continue;
+    const int lam = w.la + w.lb;
+    const int nch = lam <= 12 ? 32 : 16;
+    const size_t sm = coupling_smem_per_warp(lam, nch);
+    const int* rmap = dt.rmap + th.rmap_off[lam];
+    if (nch == 32) {
+      cudaFuncSetAttribute(k_coupling_block<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, stream>>>(
+          lam, w.npp, w.pp_base, rbases[c], db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
+          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+    } else {
+      cudaFuncSetAttribute(k_coupling_block<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, stream>>>(
+          lam, w.npp, w.pp_base, rbases[c], db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
+          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+    }
+  }
+  if (events) cudaEventRecord(events[1], stream);
+  for (size_t c = 0; c < work.size(); ++c) {
+    const ClassWork& w = work[c];
+    if (w.npairs == 0) continue;
+    const int cid = class_id(w.la, w.lb);
+    const size_t sm = pair_smem(w.la, w.lb);
+    cudaFuncSetAttribute(k_pair_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pair_block<<<grid_cap(w.npairs, 8), 32, sm, stream>>>(
+        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbases[c], db.pair_a, db.pair_b, db.pair_ppoff, db.shell_xyz,
+        db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
+        dt.g_rowptr + th.g_rowbase[cid], dt.g_ridx + th.g_termbase[cid], dt.g_coef + th.g_termbase[cid], db.rbuf,
+        nbf, out);
+  }
+  if (events) cudaEventRecord(events[2], stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = std::string("kernel launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return SHGO_OK;
+}
+
+int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf) {
+  int64_t n = 0;
+  for (const auto& w : work) n += (w.npp > 0 ? 1 : 0) + (w.npairs > 0 ? 1 : 0);
+  return nbf == 0 ? 0 : n;
+}
+
+}  // namespace shgo

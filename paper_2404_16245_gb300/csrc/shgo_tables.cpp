@@ -1,0 +1,271 @@
+// Host construction of the constant tables: recursion coefficients of the real solid
+// harmonics, the real translation tensors (addition theorem, Eqs. 7-8), the real coupling
+// (Gaunt) programs (Clebsch-Gordan product rule, Supp. Eq. 4), the packed layout of the
+// per-primitive-pair coupling block, and the Boys grid.  Built once per process in long double.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+
+#include "shgo_internal.h"
+#include "shgo_math.h"
+
+namespace shgo {
+
+using ld = long double;
+using cld = std::complex<long double>;
+
+namespace {
+
+ld fact(int n) {
+  ld f = 1;
+  for (int i = 2; i <= n; ++i) f *= (ld)i;
+  return f;
+}
+
+ld binom(int n, int k) {
+  if (n < 0 || k < 0 || k > n) return 0;
+  return fact(n) / (fact(k) * fact(n - k));
+}
+
+// Clebsch-Gordan coefficient <j1 m1 j2 m2 | J M> by Racah's closed formula.
+ld clebsch_gordan(int j1, int m1, int j2, int m2, int J, int M) {
+  if (M != m1 + m2 || J < std::abs(j1 - j2) || J > j1 + j2) return 0;
+  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(M) > J) return 0;
+  const ld pre = std::sqrt((ld)(2 * J + 1) * fact(j1 + j2 - J) * fact(j1 - j2 + J) * fact(-j1 + j2 + J) /
+                           fact(j1 + j2 + J + 1)) *
+                 std::sqrt(fact(j1 + m1) * fact(j1 - m1) * fact(j2 + m2) * fact(j2 - m2) * fact(J + M) * fact(J - M));
+  ld sum = 0;
+  for (int k = 0; k <= j1 + j2 - J; ++k) {
+    const int d1 = j1 + j2 - J - k, d2 = j1 - m1 - k, d3 = j2 + m2 - k, d4 = J - j2 + m1 + k, d5 = J - j1 - m2 + k;
+    if (d1 < 0 || d2 < 0 || d3 < 0 || d4 < 0 || d5 < 0) continue;
+    const ld term = 1 / (fact(k) * fact(d1) * fact(d2) * fact(d3) * fact(d4) * fact(d5));
+    sum += (k & 1) ? -term : term;
+  }
+  return pre * sum;
+}
+
+// Unitary map from complex to real harmonics: S_{l,m} = sum_m' U[m][m'] Y_l^{m'} with
+//   S_l0 = Y_l^0,  S_{l,m>0} = ((-1)^m Y^m + Y^-m)/sqrt2,  S_{l,-m} = ((-1)^m Y^m - Y^-m)/(i sqrt2).
+cld umap(int m, int mp) {
+  const ld r2 = std::sqrt((ld)0.5);
+  if (m == 0) return mp == 0 ? cld(1, 0) : cld(0, 0);
+  if (m > 0) {
+    const ld sg = (m & 1) ? -1 : 1;
+    if (mp == m) return cld(sg * r2, 0);
+    if (mp == -m) return cld(r2, 0);
+    return cld(0, 0);
+  }
+  const int mu = -m;
+  const ld sg = (mu & 1) ? -1 : 1;
+  if (mp == mu) return cld(0, -sg * r2);
+  if (mp == -mu) return cld(0, r2);
+  return cld(0, 0);
+}
+
+// The two complex indices that a real index m couples to (m and -m; one when m = 0).
+int partners(int m, int* out) {
+  if (m == 0) {
+    out[0] = 0;
+    return 1;
+  }
+  out[0] = std::abs(m);
+  out[1] = -std::abs(m);
+  return 2;
+}
+
+// Vector-coupling coefficient of Eq. 8: eps_{l1 l2 m1 m2} = sqrt(C(l1+m1, l2+m2) C(l1-m1, l2-m2)).
+ld epsilon(int l1, int l2, int m1, int m2) { return std::sqrt(binom(l1 + m1, l2 + m2) * binom(l1 - m1, l2 - m2)); }
+
+}  // namespace
+
+double gaunt_real(int l1, int m1, int l2, int m2, int L, int M) {
+  if (std::abs(m1) > l1 || std::abs(m2) > l2 || std::abs(M) > L) return 0;
+  if (((l1 + l2 + L) & 1) || L < std::abs(l1 - l2) || L > l1 + l2) return 0;
+  const ld cg0 = clebsch_gordan(l1, 0, l2, 0, L, 0);
+  int p1[2], p2[2];
+  const int n1 = partners(m1, p1), n2 = partners(m2, p2);
+  cld acc(0, 0);
+  for (int a = 0; a < n1; ++a)
+    for (int b = 0; b < n2; ++b) {
+      const int Mp = p1[a] + p2[b];
+      if (std::abs(Mp) > L) continue;
+      const ld cg = clebsch_gordan(l1, p1[a], l2, p2[b], L, Mp);
+      acc += umap(m1, p1[a]) * umap(m2, p2[b]) * cg0 * cg * std::conj(umap(M, Mp));
+    }
+  return (double)acc.real();
+}
+
+double translation_real(int la, int ma, int l1, int m1, int nu) {
+  const int lr = la - l1;
+  if (l1 < 0 || lr < 0 || std::abs(ma) > la || std::abs(m1) > l1 || std::abs(nu) > lr) return 0;
+  int pa[2], p1[2], pr[2];
+  const int na = partners(ma, pa), n1 = partners(m1, p1), nr = partners(nu, pr);
+  cld acc(0, 0);
+  for (int a = 0; a < na; ++a)
+    for (int b = 0; b < n1; ++b)
+      for (int c = 0; c < nr; ++c) {
+        if (pa[a] != p1[b] + pr[c]) continue;
+        acc += umap(ma, pa[a]) * epsilon(la, l1, pa[a], p1[b]) * std::conj(umap(m1, p1[b])) * std::conj(umap(nu, pr[c]));
+      }
+  return (double)acc.real();
+}
+
+int translation_offset(int la, int ma, int l1, int m1) {
+  // Within the la block: (ma, l1, m1) in order, each followed by 2(la-l1)+1 nu values.
+  int off = 0;
+  const int per_ma = [&] {
+    int s = 0;
+    for (int k = 0; k <= la; ++k) s += (2 * k + 1) * (2 * (la - k) + 1);
+    return s;
+  }();
+  off += (ma + la) * per_ma;
+  for (int k = 0; k < l1; ++k) off += (2 * k + 1) * (2 * (la - k) + 1);
+  off += (m1 + l1) * (2 * (la - l1) + 1);
+  return off;
+}
+
+const HarmCoef& harm_coef_host() {
+  static HarmCoef hc;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    std::memset(&hc, 0, sizeof(hc));
+    for (int l = 0; l <= kHarmMax; ++l) {
+      hc.c[l] = (double)std::sqrt((ld)(2 * l + 1) / (ld)(2 * l + 2));
+      for (int m = -l; m <= l; ++m) {
+        const int k = harm_index(l, m);
+        hc.a[k] = (double)((ld)(2 * l + 1) / std::sqrt((ld)(l + m + 1) * (ld)(l - m + 1)));
+        hc.b[k] = (double)std::sqrt((ld)(l + m) * (ld)(l - m) / ((ld)(l + m + 1) * (ld)(l - m + 1)));
+      }
+    }
+  });
+  return hc;
+}
+
+const BoysConst& boys_const_host() {
+  static BoysConst bc;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int k = 0; k <= kBoysK; ++k) bc.inv_fact[k] = (double)(1 / fact(k));
+    for (int n = 0; n < kBoysNmax + 2; ++n) bc.inv_odd[n] = (double)(1 / (ld)(2 * n + 1));
+    bc.inv_int[0] = 0.0;
+    for (int k = 1; k < kLamMax + 2; ++k) bc.inv_int[k] = (double)(1 / (ld)k);
+  });
+  return bc;
+}
+
+namespace {
+
+// F_n(T_g) for n = 0..nmax by the series F_nmax(T) = exp(-T) sum_i (2T)^i/[(2nmax+1)...(2nmax+2i+1)]
+// followed by downward recursion, all in long double.
+void boys_grid_row(ld T, int nmax, ld* F, ld* ex) {
+  *ex = std::exp(-T);
+  ld term = 1 / (ld)(2 * nmax + 1), sum = term;
+  for (int i = 1; i < 4000; ++i) {
+    term *= 2 * T / (ld)(2 * nmax + 2 * i + 1);
+    sum += term;
+    if (term < sum * (ld)1e-36) break;
+  }
+  F[nmax] = *ex * sum;
+  for (int n = nmax - 1; n >= 0; --n) F[n] = (2 * T * F[n + 1] + *ex) / (ld)(2 * n + 1);
+}
+
+void build_tables(Tables& t) {
+  // Boys grid
+  t.boys.assign((size_t)kBoysNg * kBoysStride, 0.0);
+  for (int g = 0; g < kBoysNg; ++g) {
+    ld F[kBoysNmax + 1], ex;
+    boys_grid_row((ld)g / (ld)kBoysInvH, kBoysNmax, F, &ex);
+    t.boys[(size_t)g * kBoysStride] = (double)ex;
+    for (int n = 0; n <= kBoysNmax; ++n) t.boys[(size_t)g * kBoysStride + 1 + n] = (double)F[n];
+  }
+  // Translation tensors
+  t.eoff.assign(kLmax + 2, 0);
+  for (int la = 0; la <= kLmax; ++la) {
+    int per_ma = 0;
+    for (int k = 0; k <= la; ++k) per_ma += (2 * k + 1) * (2 * (la - k) + 1);
+    t.eoff[la + 1] = t.eoff[la] + (2 * la + 1) * per_ma;
+  }
+  t.etab.assign(t.eoff[kLmax + 1], 0.0);
+  for (int la = 0; la <= kLmax; ++la)
+    for (int ma = -la; ma <= la; ++ma)
+      for (int l1 = 0; l1 <= la; ++l1)
+        for (int m1 = -l1; m1 <= l1; ++m1) {
+          const int base = t.eoff[la] + translation_offset(la, ma, l1, m1);
+          for (int nu = -(la - l1); nu <= la - l1; ++nu)
+            t.etab[base + nu + (la - l1)] = translation_real(la, ma, l1, m1, nu);
+        }
+  // Packed R layout per Lambda: harm index | beta index << 12 | k << 24
+  t.rmap_off.assign(kLamMax + 2, 0);
+  for (int lam = 0; lam <= kLamMax; ++lam) t.rmap_off[lam + 1] = t.rmap_off[lam] + n_r(lam);
+  t.rmap.assign(t.rmap_off[kLamMax + 1], 0);
+  for (int lam = 0; lam <= kLamMax; ++lam) {
+    int e = t.rmap_off[lam], boff = 0;
+    for (int L = 0; L <= lam; ++L) {
+      const int km = kmax_of(lam, L);
+      for (int M = -L; M <= L; ++M)
+        for (int k = 0; k <= km; ++k) t.rmap[e++] = harm_index(L, M) | ((boff + k) << 12) | (k << 24);
+      boff += km + 1;
+    }
+  }
+  // Gaunt programs per class
+  std::vector<std::vector<std::pair<int, double>>> terms;  // per (i1, i2) over all l <= kLmax
+  const int nh = (kLmax + 1) * (kLmax + 1);
+  terms.resize((size_t)nh * nh);
+  for (int l1 = 0; l1 <= kLmax; ++l1)
+    for (int m1 = -l1; m1 <= l1; ++m1)
+      for (int l2 = 0; l2 <= kLmax; ++l2)
+        for (int m2 = -l2; m2 <= l2; ++m2) {
+          auto& v = terms[(size_t)harm_index(l1, m1) * nh + harm_index(l2, m2)];
+          for (int L = std::abs(l1 - l2); L <= l1 + l2; L += 2)
+            for (int M = -L; M <= L; ++M) {
+              const double g = gaunt_real(l1, m1, l2, m2, L, M);
+              if (std::fabs(g) > 1e-15) v.push_back({harm_index(L, M) | (((l1 + l2 - L) / 2) << 12), g});
+            }
+        }
+  t.g_rowbase.assign(kNumClasses, 0);
+  t.g_termbase.assign(kNumClasses, 0);
+  t.g_rowptr.clear();
+  t.g_ridx.clear();
+  t.g_coef.clear();
+  for (int la = 0; la <= kLmax; ++la)
+    for (int lb = 0; lb <= la; ++lb) {
+      const int cid = class_id(la, lb), lam = la + lb;
+      t.g_rowbase[cid] = (int)t.g_rowptr.size();
+      t.g_termbase[cid] = (int)t.g_ridx.size();
+      // R index of (L, M, k) in the Lambda layout
+      auto ridx = [&](int L, int M, int k) {
+        int off = 0;
+        for (int Lp = 0; Lp < L; ++Lp) off += (2 * Lp + 1) * (kmax_of(lam, Lp) + 1);
+        return off + (M + L) * (kmax_of(lam, L) + 1) + k;
+      };
+      int local = 0;
+      for (int i1 = 0; i1 < (la + 1) * (la + 1); ++i1)
+        for (int i2 = 0; i2 < (lb + 1) * (lb + 1); ++i2) {
+          t.g_rowptr.push_back(local);
+          for (const auto& tm : terms[(size_t)i1 * nh + i2]) {
+            const int hi = tm.first & 0xfff, k = tm.first >> 12;
+            int L = 0;
+            while ((L + 1) * (L + 1) <= hi) ++L;
+            const int M = hi - L * L - L;
+            t.g_ridx.push_back(ridx(L, M, k));
+            t.g_coef.push_back(tm.second);
+            ++local;
+          }
+        }
+      t.g_rowptr.push_back(local);
+    }
+}
+
+}  // namespace
+
+const Tables& tables_host() {
+  static Tables t;
+  static std::once_flag once;
+  std::call_once(once, [] { build_tables(t); });
+  return t;
+}
+
+void boys_host(int nmax, double T, double* F) { boys_eval(nmax, T, F, 1, tables_host().boys.data(), boys_const_host()); }
+
+}  // namespace shgo

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libshgo.so (the C ABI declared in include/shgo.h).
+
+Argument marshalling only: every step of the integral path runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  Importing this module loads the library and fails
+loudly if it has not been built (``__graft_entry__.build()`` or ``python -m
+paper_2404_16245_gb300.build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SHGO_OK = 0
+SHGO_PREC_FP64 = 0
+SHGO_PREC_FP32_BULK = 1
+LMAX = 8
+
+_STATUS = {0: "SHGO_OK", 1: "SHGO_ERR_INVALID_ARG", 2: "SHGO_ERR_UNSUPPORTED_L", 3: "SHGO_ERR_OOM",
+           4: "SHGO_ERR_CUDA", 5: "SHGO_ERR_TIMEOUT", 6: "SHGO_ERR_NUMERIC"}
+
+
+class ShgoError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class shgo_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class shgo_centers(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("xyz", ctypes.c_void_p)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libshgo.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.shgo_basis_create.argtypes = [ctypes.c_int32, i32p, i32p, f64p, f64p, f64p, ctypes.POINTER(shgo_options),
+                                      ctypes.POINTER(ctypes.c_void_p)]
+    lib.shgo_basis_create.restype = ctypes.c_int
+    lib.shgo_basis_nbf.argtypes = [ctypes.c_void_p]
+    lib.shgo_basis_nbf.restype = ctypes.c_int64
+    lib.shgo_basis_npairs.argtypes = [ctypes.c_void_p]
+    lib.shgo_basis_npairs.restype = ctypes.c_int64
+    lib.shgo_nuclear_attraction.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_nuclear_attraction.restype = ctypes.c_int
+    lib.shgo_nuclear_attraction_timed.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p, f64p]
+    lib.shgo_nuclear_attraction_timed.restype = ctypes.c_int
+    lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
+    lib.shgo_basis_flops.restype = ctypes.c_int
+    lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
+    lib.shgo_basis_launches.restype = ctypes.c_int64
+    lib.shgo_free.argtypes = [ctypes.c_void_p]
+    lib.shgo_free.restype = None
+    lib.shgo_last_error.argtypes = []
+    lib.shgo_last_error.restype = ctypes.c_char_p
+    lib.shgo_host_solid_harmonics.argtypes = [ctypes.c_int32, ctypes.c_int64, f64p, f64p]
+    lib.shgo_host_solid_harmonics.restype = ctypes.c_int
+    lib.shgo_host_gaunt.argtypes = [ctypes.c_int32] * 6
+    lib.shgo_host_gaunt.restype = ctypes.c_double
+    lib.shgo_host_translation.argtypes = [ctypes.c_int32] * 5
+    lib.shgo_host_translation.restype = ctypes.c_double
+    lib.shgo_host_boys.argtypes = [ctypes.c_int32, ctypes.c_double, f64p]
+    lib.shgo_host_boys.restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int) -> None:
+    if status != SHGO_OK:
+        raise ShgoError(status, _lib.shgo_last_error().decode())
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    return ctypes.c_void_p(int(handle) if handle else 0)
+
+
+# ------------------------------------------------------------------ C-ABI names
+def shgo_basis_create(n_shells, l, n_prim, exponents, coefs, shell_xyz, precision=SHGO_PREC_FP64, device=-1):
+    """Returns an opaque handle (int).  Host arrays are copied by the library."""
+    l = np.ascontiguousarray(l, dtype=np.int32)
+    n_prim = np.ascontiguousarray(n_prim, dtype=np.int32)
+    exponents = np.ascontiguousarray(exponents, dtype=np.float64)
+    coefs = np.ascontiguousarray(coefs, dtype=np.float64)
+    shell_xyz = np.ascontiguousarray(shell_xyz, dtype=np.float64).reshape(-1)
+    opt = shgo_options(int(precision), int(device))
+    handle = ctypes.c_void_p()
+    _check(_lib.shgo_basis_create(int(n_shells), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32),
+                                  _ptr(exponents, ctypes.c_double), _ptr(coefs, ctypes.c_double),
+                                  _ptr(shell_xyz, ctypes.c_double), ctypes.byref(opt), ctypes.byref(handle)))
+    return handle.value
+
+
+def shgo_nuclear_attraction(basis, n_centers, centers_ptr, charges_ptr, out_ptr, stream=None):
+    """Raw call: device pointers as ints, stream a torch.cuda.Stream, a raw handle or None."""
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    _check(_lib.shgo_nuclear_attraction(ctypes.c_void_p(basis), ctypes.byref(c),
+                                        ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0),
+                                        ctypes.c_void_p(int(out_ptr) if out_ptr else 0), _stream_handle(stream)))
+
+
+def shgo_nuclear_attraction_timed(basis, n_centers, centers_ptr, charges_ptr, out_ptr, stream=None):
+    """As shgo_nuclear_attraction; blocks and returns the two phase durations in ms."""
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    ms = np.zeros(2)
+    _check(_lib.shgo_nuclear_attraction_timed(ctypes.c_void_p(basis), ctypes.byref(c),
+                                              ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0),
+                                              ctypes.c_void_p(int(out_ptr) if out_ptr else 0), _stream_handle(stream),
+                                              _ptr(ms, ctypes.c_double)))
+    return float(ms[0]), float(ms[1])
+
+
+def shgo_basis_flops(basis, n_centers: int):
+    """(flops per phase [2], (shell triples, primitive triples)) of one call with n_centers nuclei."""
+    f = np.zeros(2)
+    t = np.zeros(2)
+    _check(_lib.shgo_basis_flops(ctypes.c_void_p(basis), int(n_centers), _ptr(f, ctypes.c_double),
+                                 _ptr(t, ctypes.c_double)))
+    return f, t
+
+
+def shgo_basis_launches(basis) -> int:
+    return int(_lib.shgo_basis_launches(ctypes.c_void_p(basis)))
+
+
+def shgo_free(basis) -> None:
+    _lib.shgo_free(ctypes.c_void_p(basis))
+
+
+def shgo_basis_nbf(basis) -> int:
+    return int(_lib.shgo_basis_nbf(ctypes.c_void_p(basis)))
+
+
+def shgo_basis_npairs(basis) -> int:
+    return int(_lib.shgo_basis_npairs(ctypes.c_void_p(basis)))
+
+
+# ------------------------------------------------------------------ convenience wrappers
+class Basis:
+    """Owns a shgo_basis handle built from a basis dict (see workloads.py)."""
+
+    def __init__(self, basis: dict, precision: int = SHGO_PREC_FP64, device: int = -1):
+        self.handle = shgo_basis_create(len(basis["l"]), basis["l"], basis["nprim"], basis["exps"], basis["coefs"],
+                                        basis["xyz"], precision, device)
+        self.nbf = shgo_basis_nbf(self.handle)
+        self.npairs = shgo_basis_npairs(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            shgo_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nuclear_attraction(basis: Basis, centers, charges, out=None, stream=None):
+    """V (nbf x nbf, FP64, device tensor).  centers [n, 3] and charges [n] are CUDA float64 tensors."""
+    import torch
+    if not (centers.is_cuda and charges.is_cuda):
+        raise ValueError("centers and charges must be CUDA tensors")
+    if centers.dtype != torch.float64 or charges.dtype != torch.float64:
+        raise ValueError("centers and charges must be float64")
+    centers = centers.contiguous()
+    charges = charges.contiguous()
+    if out is None:
+        out = torch.empty((basis.nbf, basis.nbf), dtype=torch.float64, device=centers.device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != (basis.nbf, basis.nbf):
+        raise ValueError("out must be a contiguous float64 [nbf, nbf] tensor")
+    n = centers.shape[0] if centers.numel() else 0
+    shgo_nuclear_attraction(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
+                            out.data_ptr(), stream)
+    return out
+
+
+def host_solid_harmonics(l: int, xyz) -> np.ndarray:
+    pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((pts.shape[0], 2 * l + 1))
+    _check(_lib.shgo_host_solid_harmonics(int(l), pts.shape[0], _ptr(pts, ctypes.c_double), _ptr(out, ctypes.c_double)))
+    return out
+
+
+def host_gaunt(l1, m1, l2, m2, L, M) -> float:
+    return float(_lib.shgo_host_gaunt(l1, m1, l2, m2, L, M))
+
+
+def host_translation(la, ma, l1, m1, nu) -> float:
+    return float(_lib.shgo_host_translation(la, ma, l1, m1, nu))
+
+
+def host_boys(nmax: int, T: float) -> np.ndarray:
+    F = np.zeros(nmax + 1)
+    _check(_lib.shgo_host_boys(int(nmax), float(T), _ptr(F, ctypes.c_double)))
+    return F

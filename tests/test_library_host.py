@@ -1,0 +1,214 @@
+"""CPU checks of the library's host side (no GPU): the C ABI exports, the real solid-harmonic
+recursion, the coupling (Gaunt) and translation (Eq. 7-8) tables, and the Boys scheme the kernels
+use.  A numpy restatement of the corrected method built from those tables is compared with the
+oracle, which pins the readings of Eqs. 7, 11 and 12 before any kernel runs."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import oracle
+from paper_2404_16245_gb300 import workloads as W
+from tests import refmath as RM
+
+shgo = pytest.importorskip("paper_2404_16245_gb300.shgo", reason="libshgo.so not built")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_abi_exports_every_declared_symbol():
+    import ctypes
+    lib = ctypes.CDLL(shgo._build.LIB)
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(shgo_[a-z0-9_]+)\s*\(", txt)
+    assert "shgo_basis_create" in names and "shgo_nuclear_attraction" in names and "shgo_free" in names
+    for n in set(names):
+        assert hasattr(lib, n), n
+
+
+def test_invalid_arguments_are_rejected_without_gpu_work():
+    with pytest.raises(shgo.ShgoError) as e:
+        shgo.shgo_basis_create(1, [9], [1], [1.0], [1.0], [0.0, 0.0, 0.0])
+    assert e.value.status == 2
+    with pytest.raises(shgo.ShgoError) as e:
+        shgo.shgo_basis_create(1, [1], [1], [-1.0], [1.0], [0.0, 0.0, 0.0])
+    assert e.value.status == 1
+    with pytest.raises(shgo.ShgoError):
+        shgo.shgo_basis_create(1, [1], [0], [], [], [0.0, 0.0, 0.0])
+
+
+@pytest.mark.parametrize("l", range(0, 17))
+def test_host_harmonic_recursion_matches_scipy(l):
+    rng = np.random.default_rng(l)
+    pts = rng.normal(size=(30, 3))
+    got = shgo.host_solid_harmonics(l, pts)
+    ref = RM.solid_harmonics_scipy(l, pts)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("l1,l2", [(0, 0), (1, 1), (2, 1), (3, 3), (4, 2), (5, 5), (8, 7), (8, 8)])
+def test_gaunt_product_rule(l1, l2):
+    # S_{l1 m1} S_{l2 m2} = sum_{L,M} G r^{l1+l2-L} S_{LM} at random points (Supp. Eq. 4 product rule)
+    rng = np.random.default_rng(10 * l1 + l2)
+    pts = rng.normal(size=(12, 3))
+    r = np.linalg.norm(pts, axis=1)
+    S1 = RM.solid_harmonics_scipy(l1, pts)
+    S2 = RM.solid_harmonics_scipy(l2, pts)
+    SL = {L: RM.solid_harmonics_scipy(L, pts) for L in range(abs(l1 - l2), l1 + l2 + 1)}
+    for m1 in range(-l1, l1 + 1):
+        for m2 in range(-l2, l2 + 1):
+            rhs = np.zeros(len(pts))
+            for L in range(abs(l1 - l2), l1 + l2 + 1, 2):
+                for M in range(-L, L + 1):
+                    g = shgo.host_gaunt(l1, m1, l2, m2, L, M)
+                    if g:
+                        rhs += g * r ** (l1 + l2 - L) * SL[L][:, M + L]
+            lhs = S1[:, m1 + l1] * S2[:, m2 + l2]
+            assert np.allclose(lhs, rhs, rtol=1e-11, atol=1e-11 * np.max(np.abs(lhs) + 1))
+
+
+@pytest.mark.parametrize("la", range(0, 9))
+def test_translation_addition_theorem(la):
+    # S_{la,ma}(x + y) = sum_{l1,m1,nu} E S_{l1,m1}(x) S_{la-l1,nu}(y)   (Eqs. 7-8, real basis)
+    rng = np.random.default_rng(50 + la)
+    x = rng.normal(size=(10, 3))
+    y = rng.normal(size=(10, 3))
+    lhs = RM.solid_harmonics_scipy(la, x + y)
+    Sx = {l: RM.solid_harmonics_scipy(l, x) for l in range(la + 1)}
+    Sy = {l: RM.solid_harmonics_scipy(l, y) for l in range(la + 1)}
+    for ma in range(-la, la + 1):
+        rhs = np.zeros(len(x))
+        for l1 in range(la + 1):
+            lr = la - l1
+            for m1 in range(-l1, l1 + 1):
+                for nu in range(-lr, lr + 1):
+                    e = shgo.host_translation(la, ma, l1, m1, nu)
+                    if e:
+                        rhs += e * Sx[l1][:, m1 + l1] * Sy[lr][:, nu + lr]
+        assert np.allclose(lhs[:, ma + la], rhs, rtol=1e-11, atol=1e-11 * (1 + np.max(np.abs(lhs))))
+
+
+@pytest.mark.parametrize("T", [0.0, 1e-9, 0.01, 0.03124, 0.5, 3.3, 17.0, 39.97, 40.0, 55.5, 300.0, 1e5])
+def test_boys_scheme(T):
+    F = shgo.host_boys(17, T)
+    for n in range(18):
+        if T == 0:
+            ref = 1.0 / (2 * n + 1)
+        else:
+            ref = sp.gamma(n + 0.5) * sp.gammainc(n + 0.5, T) / (2 * T ** (n + 0.5))
+            if T < 1e-6:
+                ref = 1.0 / (2 * n + 1) - T / (2 * n + 3)
+        assert F[n] == pytest.approx(ref, rel=5e-14, abs=1e-300)
+
+
+# ----------------------------------------------------------------- numpy model of the method
+def _rlayout(lam):
+    idx = {}
+    e = 0
+    for L in range(lam + 1):
+        km = (lam - L) // 2
+        for M in range(-L, L + 1):
+            for k in range(km + 1):
+                idx[(L, M, k)] = e
+                e += 1
+    return idx
+
+
+def method_block(la, lb, A, B, alphas, betas, ca, cb, C, Z):
+    """V block of one shell pair by Eq. 11 with the coupled one-centre integral (corrected Eq. 12)
+    and the shift vectors b-a / a-b.  ca/cb are coefficients of normalised primitives already
+    scaled for the contracted normalisation."""
+    lam = la + lb
+    AB = B - A
+    V = np.zeros((2 * la + 1, 2 * lb + 1))
+    Sab = {l: shgo.host_solid_harmonics(l, AB[None])[0] for l in range(max(la, lb) + 1)}
+    TA = np.zeros((2 * la + 1, (la + 1) ** 2))
+    TB = np.zeros((2 * lb + 1, (lb + 1) ** 2))
+    for ma in range(-la, la + 1):
+        for l1 in range(la + 1):
+            for m1 in range(-l1, l1 + 1):
+                TA[ma + la, l1 * l1 + l1 + m1] = sum(shgo.host_translation(la, ma, l1, m1, nu) * Sab[la - l1][nu + la - l1]
+                                                     for nu in range(-(la - l1), la - l1 + 1))
+    for mb in range(-lb, lb + 1):
+        for l2 in range(lb + 1):
+            for m2 in range(-l2, l2 + 1):
+                TB[mb + lb, l2 * l2 + l2 + m2] = (-1) ** (lb - l2) * sum(
+                    shgo.host_translation(lb, mb, l2, m2, nu) * Sab[lb - l2][nu + lb - l2] for nu in range(-(lb - l2), lb - l2 + 1))
+    Wt = np.zeros(((la + 1) ** 2, (lb + 1) ** 2))
+    for i, a in enumerate(alphas):
+        for j, b in enumerate(betas):
+            p = a + b
+            P = (a * A + b * B) / p
+            K = math.exp(-a * b / p * AB @ AB)
+            R = {}
+            for Cc, Zc in zip(C, Z):
+                d = Cc - P
+                s = d @ d
+                T = p * s
+                F = shgo.host_boys(lam, T)
+                SL = {L: shgo.host_solid_harmonics(L, d[None])[0] for L in range(lam + 1)}
+                for L in range(lam + 1):
+                    for k in range((lam - L) // 2 + 1):
+                        beta = sum(math.factorial(k) / math.factorial(jj) * T ** jj * F[L + jj] for jj in range(k + 1))
+                        for M in range(-L, L + 1):
+                            R[(L, M, k)] = R.get((L, M, k), 0.0) + Zc * SL[L][M + L] * beta
+            for l1 in range(la + 1):
+                for m1 in range(-l1, l1 + 1):
+                    for l2 in range(lb + 1):
+                        for m2 in range(-l2, l2 + 1):
+                            acc = 0.0
+                            for L in range(abs(l1 - l2), l1 + l2 + 1, 2):
+                                k = (l1 + l2 - L) // 2
+                                for M in range(-L, L + 1):
+                                    g = shgo.host_gaunt(l1, m1, l2, m2, L, M)
+                                    if g:
+                                        acc += g * 2 * math.pi * p ** (-(k + 1)) * R[(L, M, k)]
+                            Wt[l1 * l1 + l1 + m1, l2 * l2 + l2 + m2] += (
+                                ca[i] * cb[j] * K * (b / p) ** (la - l1) * (a / p) ** (lb - l2) * acc)
+    return TA @ Wt @ TB.T
+
+
+def _norm_coefs(l, exps, coefs):
+    d = np.array([c * oracle.prim_norm(l, e) for c, e in zip(coefs, exps)])
+    basis = W.make_basis([l], [len(exps)], exps, coefs, [[0, 0, 0]])
+    S = oracle.overlap(basis)
+    return d  # oracle renormalises internally; the ratio is applied below
+
+
+@pytest.mark.parametrize("la,lb", [(0, 0), (1, 0), (1, 1), (2, 1), (2, 2), (3, 2), (4, 3)])
+def test_method_model_matches_oracle(la, lb):
+    rng = np.random.default_rng(100 * la + lb)
+    A = rng.uniform(-1, 1, 3)
+    B = rng.uniform(-1, 1, 3) + np.array([0.7, 0.0, -0.4])
+    alphas = np.exp(rng.uniform(-1, 1.5, 2))
+    betas = np.exp(rng.uniform(-1, 1.5, 2))
+    ca = rng.uniform(0.2, 1.0, 2)
+    cb = rng.uniform(0.2, 1.0, 2)
+    C = rng.uniform(-1.5, 1.5, (2, 3))
+    Z = np.array([2.0, 5.0])
+    basis = W.make_basis([la, lb], [2, 2], np.concatenate([alphas, betas]), np.concatenate([ca, cb]), [A, B])
+    Vo = oracle.nuclear_attraction(basis, C, Z)[: 2 * la + 1, 2 * la + 1:]
+
+    def contracted(l, ex, co):
+        d = np.array([c * oracle.prim_norm(l, e) for c, e in zip(co, ex)])
+        self = sum(co[i] * co[j] * (2 * math.sqrt(ex[i] * ex[j]) / (ex[i] + ex[j])) ** (l + 1.5)
+                   for i in range(len(ex)) for j in range(len(ex)))
+        return d / math.sqrt(self)
+
+    Vm = method_block(la, lb, A, B, alphas, betas, contracted(la, alphas, ca), contracted(lb, betas, cb), C, Z)
+    assert np.max(np.abs(Vm - Vo)) <= 1e-12 * max(1.0, np.max(np.abs(Vo)))
+
+
+def test_printed_eq12_differs_from_the_coupled_form():
+    # Eq. 12 as printed keeps only L = l1 + l2; for l1 = l2 = 1, m = 0 and C = P it gives 0,
+    # while the integrand z^2 e^{-p r^2}/r is positive: the coupled form is required.
+    basis = W.make_basis([1, 1], [1, 1], [0.6, 0.7], [1, 1], [[0, 0, 0], [0, 0, 0]])
+    V = oracle.nuclear_attraction(basis, np.zeros((1, 3)), [1.0])
+    assert V[1, 4] > 0.1  # (m = 0, m = 0) block element
