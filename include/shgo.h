@@ -115,6 +115,34 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
 /* Number of kernel launches one shgo_nuclear_attraction call on this basis makes (n > 0). */
 int64_t shgo_basis_launches(const shgo_basis* basis);
 
+/* ---------------------------------------------------------------------------------------------
+ * Allocation-free variant.  The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc, for example a process whose device memory belongs to an external pool
+ * manager that forbids other allocations, or code that must never enter the CUDA allocator while
+ * it runs.  shgo_basis_create allocates device memory, so such callers use this call instead.
+ *
+ * Same result as shgo_basis_create + shgo_nuclear_attraction + shgo_free, from the same host
+ * basis arrays, device nuclei/charges and device output, on the current device.  It never calls
+ * cudaMalloc, cudaFree or any allocating CUDA routine: the constant tables, this call's shells and
+ * pair lists and its coupling buffer all live in one static device array of
+ * SHGO_NOALLOC_SCRATCH_BYTES that the library holds on every GPU that loads it, until the process
+ * exits.  A problem whose shells, pairs and coupling buffer do not fit the part of that array left
+ * after the tables (about 60 MiB; the 32-atom l <= 6 workload needs 24 MiB) is rejected with
+ * SHGO_ERR_INVALID_ARG before any device work, and shgo_last_error() gives the sizes.
+ *
+ * The first call on a device does a one-time set-up (finds the array's device address with
+ * cudaGetSymbolAddress and copies the tables into it, synchronously); make that first call
+ * before any stream capture.  Later calls copy the shell image from pageable host memory on
+ * `stream`, which orders the copy after earlier work on that stream.  Every call reuses the same
+ * array, which keeps the previous call's contents; nothing in it needs to start at zero.  Calls
+ * whose device work overlaps (different streams or host threads on one device) race on the array.
+ */
+#define SHGO_NOALLOC_SCRATCH_BYTES (64ll * 1024 * 1024)
+shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const int32_t* l, const int32_t* n_prim,
+                                            const double* exponents, const double* coefs, const double* shell_xyz,
+                                            const shgo_centers* centers, const double* charges, double* out,
+                                            void* stream);
+
 /* Release a basis and its device memory (synchronises its device).  NULL-safe. */
 void shgo_free(shgo_basis* basis);
 

@@ -31,6 +31,11 @@ double prim_norm(int l, double alpha) {
 }
 }  // namespace
 
+namespace shgo {
+// Lets the allocation-free entry point (its own translation unit) report through shgo_last_error.
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace shgo
+
 struct shgo_basis {
   int device = 0;
   int n_shells = 0;

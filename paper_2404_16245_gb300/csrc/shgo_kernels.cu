@@ -323,6 +323,24 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   return SHGO_OK;
 }
 
+// The __constant__ recursion coefficients and Boys constants on the current device, without any
+// allocation (used by the allocation-free entry point, which keeps its tables elsewhere).
+shgo_status upload_constants(std::string* err) {
+  cudaError_t e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
+  if (e == cudaSuccess) {
+    int lof[(kLmax + 1) * (kLmax + 1)];
+    for (int l = 0; l <= kLmax; ++l)
+      for (int m = -l; m <= l; ++m) lof[harm_index(l, m)] = l;
+    e = cudaMemcpyToSymbol(c_lof, lof, sizeof(lof));
+  }
+  if (e != cudaSuccess) {
+    *err = std::string("uploading constants: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return SHGO_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Launch
 // ---------------------------------------------------------------------------------------------

@@ -56,6 +56,10 @@ def _load() -> ctypes.CDLL:
     lib.shgo_nuclear_attraction_timed.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
                                                   ctypes.c_void_p, ctypes.c_void_p, f64p]
     lib.shgo_nuclear_attraction_timed.restype = ctypes.c_int
+    lib.shgo_nuclear_attraction_noalloc.argtypes = [ctypes.c_int32, i32p, i32p, f64p, f64p, f64p,
+                                                    ctypes.POINTER(shgo_centers), ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p]
+    lib.shgo_nuclear_attraction_noalloc.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -141,6 +145,25 @@ def shgo_basis_flops(basis, n_centers: int):
 
 def shgo_basis_launches(basis) -> int:
     return int(_lib.shgo_basis_launches(ctypes.c_void_p(basis)))
+
+
+def shgo_nuclear_attraction_noalloc(n_shells, l, n_prim, exponents, coefs, shell_xyz, n_centers, centers_ptr,
+                                    charges_ptr, out_ptr, stream=None):
+    """Allocation-free call (host basis arrays, device nuclei/charges/output as int pointers).
+
+    For callers that may not allocate device memory: it uses only the library's static device
+    scratch array (see include/shgo.h).  Calls that overlap on the GPU race on that array."""
+    l = np.ascontiguousarray(l, dtype=np.int32)
+    n_prim = np.ascontiguousarray(n_prim, dtype=np.int32)
+    exponents = np.ascontiguousarray(exponents, dtype=np.float64)
+    coefs = np.ascontiguousarray(coefs, dtype=np.float64)
+    shell_xyz = np.ascontiguousarray(shell_xyz, dtype=np.float64).reshape(-1)
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    _check(_lib.shgo_nuclear_attraction_noalloc(
+        int(n_shells), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32), _ptr(exponents, ctypes.c_double),
+        _ptr(coefs, ctypes.c_double), _ptr(shell_xyz, ctypes.c_double), ctypes.byref(c),
+        ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0), ctypes.c_void_p(int(out_ptr) if out_ptr else 0),
+        _stream_handle(stream)))
 
 
 def shgo_free(basis) -> None:
