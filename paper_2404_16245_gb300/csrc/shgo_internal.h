@@ -49,6 +49,13 @@ struct HarmCoef {
 };
 const HarmCoef& harm_coef_host();
 
+// One term of a Gaunt program: 16 bytes, loaded with one vector load.
+struct __align__(16) GTerm {
+  double coef;
+  int ridx;
+  int pad;
+};
+
 // Host tables, built once per process (long double arithmetic, stored as double).
 struct Tables {
   std::vector<double> boys;  // [kBoysNg][kBoysStride]
@@ -57,11 +64,13 @@ struct Tables {
   // per (ma, l1 m1) over nu = -(la-l1)..(la-l1): see translation_index().
   std::vector<double> etab;
   std::vector<int> eoff;  // [kLmax + 2]
-  // Gaunt programs per class (la >= lb): CSR over W entries (l1 m1, l2 m2), row-major with
-  // (lb+1)^2 columns; each term is (R index for Lambda = la+lb, coefficient).
-  std::vector<int> g_rowptr;  // concatenated, class c rows at g_rowbase[c] .. + nW + 1
-  std::vector<int> g_ridx;
-  std::vector<double> g_coef;
+  // Gaunt programs per class (la >= lb): one row per W entry (l1 m1, l2 m2), rows sorted by
+  // decreasing term count so that neighbouring threads run loops of equal length.  Row r has
+  // g_rowinfo[r] = W index (row-major, (lb+1)^2 columns) | l1 << 16 | l2 << 20 and terms
+  // g_rowptr[r] .. g_rowptr[r+1] (local to the class) of (coefficient, R' index for Lambda = la+lb).
+  std::vector<int> g_rowinfo;
+  std::vector<int> g_rowptr;   // concatenated, class c rows at g_rowbase[c] .. + nW + 1
+  std::vector<GTerm> g_terms;
   std::vector<int> g_rowbase;  // [n classes]
   std::vector<int> g_termbase; // [n classes]
   // R layout per Lambda: packed (harm index | beta index << 12 | k << 24) for entry e.
@@ -85,9 +94,9 @@ struct DeviceTables {
   double* boys = nullptr;
   double* etab = nullptr;
   int* eoff = nullptr;
+  int* g_rowinfo = nullptr;
   int* g_rowptr = nullptr;
-  int* g_ridx = nullptr;
-  double* g_coef = nullptr;
+  GTerm* g_terms = nullptr;
   int* rmap = nullptr;
 };
 shgo_status device_tables(int device, const DeviceTables** out, std::string* err);
@@ -125,7 +134,8 @@ struct DeviceBasis {
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
                                       const double* centers, const double* charges, double* out,
-                                      cudaStream_t stream, std::string* err, cudaEvent_t* events = nullptr);
+                                      cudaStream_t stream, std::string* err, cudaEvent_t* events = nullptr,
+                                      bool concurrent = true);
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
 
 }  // namespace shgo

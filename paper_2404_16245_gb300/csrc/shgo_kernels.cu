@@ -17,6 +17,7 @@
 //      a - b; writes the block and its transpose into V.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -133,12 +134,18 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
   }
 }
 
-// Shared-memory bytes of one warp of k_pair_block.
+// Shared-memory bytes of one block of k_pair_block.
 __host__ __device__ inline size_t pair_smem(int la, int lb) {
   const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1);
   const int lm = la > lb ? la : lb;
   return sizeof(double) * ((size_t)nWa * nWb + (2 * la + 1) * nWa + (2 * lb + 1) * nWb + nWa * (2 * lb + 1) +
-                           (lm + 1) * (lm + 1) + la + 1 + lb + 1 + 8);
+                           (lm + 1) * (lm + 1) + (la + 1) * (lb + 1) + n_r(la + lb) + 8);
+}
+
+// Threads per block of k_pair_block for a class: enough to cover the W entries of large classes.
+__host__ __device__ inline int pair_threads(int la, int lb) {
+  const int nW = (la + 1) * (la + 1) * (lb + 1) * (lb + 1);
+  return nW >= 1024 ? 128 : (nW >= 256 ? 64 : 32);
 }
 
 __device__ __forceinline__ int translation_offset_dev(int la, int ma, int l1, int m1) {
@@ -151,22 +158,24 @@ __device__ __forceinline__ int translation_offset_dev(int la, int ma, int l1, in
   return (ma + la) * per_ma + below + (m1 + l1) * (2 * (la - l1) + 1);
 }
 
-__global__ void __launch_bounds__(32) k_pair_block(int la, int lb, int npairs, int pair_base, int64_t pp_base,
-                                                   int64_t rbase, const int* __restrict__ pair_a,
-                                                   const int* __restrict__ pair_b,
-                                                   const int64_t* __restrict__ pair_ppoff,
-                                                   const double* __restrict__ shell_xyz,
-                                                   const int* __restrict__ shell_poff,
-                                                   const int* __restrict__ shell_nprim,
-                                                   const int64_t* __restrict__ shell_foff,
-                                                   const double* __restrict__ prim_exp,
-                                                   const double* __restrict__ prim_coef,
-                                                   const double* __restrict__ etab, const int* __restrict__ eoff,
-                                                   const int* __restrict__ g_rowptr, const int* __restrict__ g_ridx,
-                                                   const double* __restrict__ g_coef, const double* __restrict__ rbuf,
-                                                   int64_t nbf, double* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, int pair_base, int64_t pp_base,
+                                                    int64_t rbase, const int* __restrict__ pair_a,
+                                                    const int* __restrict__ pair_b,
+                                                    const int64_t* __restrict__ pair_ppoff,
+                                                    const double* __restrict__ shell_xyz,
+                                                    const int* __restrict__ shell_poff,
+                                                    const int* __restrict__ shell_nprim,
+                                                    const int64_t* __restrict__ shell_foff,
+                                                    const double* __restrict__ prim_exp,
+                                                    const double* __restrict__ prim_coef,
+                                                    const double* __restrict__ etab, const int* __restrict__ eoff,
+                                                    const int* __restrict__ g_rowinfo,
+                                                    const int* __restrict__ g_rowptr,
+                                                    const GTerm* __restrict__ g_terms,
+                                                    const double* __restrict__ rbuf, int64_t nbf,
+                                                    double* __restrict__ out) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, nth = blockDim.x;
   const int lam = la + lb;
   const int nR = n_r(lam);
   const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
@@ -177,8 +186,8 @@ __global__ void __launch_bounds__(32) k_pair_block(int la, int lb, int npairs, i
   double* TB = TA + na * nWa;
   double* X = TB + nb * nWb;
   double* Sab = X + nWa * nb;
-  double* fa = Sab + (lm + 1) * (lm + 1);
-  double* fb = fa + la + 1;
+  double* fab = Sab + (lm + 1) * (lm + 1);
+  double* Rs = fab + (la + 1) * (lb + 1);
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
@@ -186,26 +195,26 @@ __global__ void __launch_bounds__(32) k_pair_block(int la, int lb, int npairs, i
     const double Bx = shell_xyz[3 * b], By = shell_xyz[3 * b + 1], Bz = shell_xyz[3 * b + 2];
     const double ABx = Bx - Ax, ABy = By - Ay, ABz = Bz - Az;
     const double ab2 = ABx * ABx + ABy * ABy + ABz * ABz;
-    __syncwarp();
-    if (lane == 0) solid_harmonics(lm, ABx, ABy, ABz, Sab, 1, c_harm.a, c_harm.b, c_harm.c);
-    for (int e = lane; e < nW; e += 32) W[e] = 0.0;
-    __syncwarp();
+    __syncthreads();
+    if (tid == 0) solid_harmonics(lm, ABx, ABy, ABz, Sab, 1, c_harm.a, c_harm.b, c_harm.c);
+    for (int e = tid; e < nW; e += nth) W[e] = 0.0;
+    __syncthreads();
     // translation matrices (Eq. 7 with Eq. 8 coefficients, real basis)
-    for (int e = lane; e < na * nWa; e += 32) {
+    for (int e = tid; e < na * nWa; e += nth) {
       const int ma = e / nWa - la, i1 = e % nWa, l1 = c_lof[i1], m1 = i1 - l1 * l1 - l1, lr = la - l1;
       const double* ev = etab + eoff[la] + translation_offset_dev(la, ma, l1, m1);
       double s = 0.0;
       for (int nu = -lr; nu <= lr; ++nu) s = fma(ev[nu + lr], Sab[lr * lr + lr + nu], s);
       TA[e] = s;
     }
-    for (int e = lane; e < nb * nWb; e += 32) {
+    for (int e = tid; e < nb * nWb; e += nth) {
       const int mb = e / nWb - lb, i2 = e % nWb, l2 = c_lof[i2], m2 = i2 - l2 * l2 - l2, lr = lb - l2;
       const double* ev = etab + eoff[lb] + translation_offset_dev(lb, mb, l2, m2);
       double s = 0.0;
       for (int nu = -lr; nu <= lr; ++nu) s = fma(ev[nu + lr], Sab[lr * lr + lr + nu], s);
       TB[e] = (lr & 1) ? -s : s;  // S_l(a - b) = (-1)^l S_l(b - a)
     }
-    // coupling and primitive contraction
+    // coupling (Gaunt) and primitive contraction
     const int npa = shell_nprim[a], npb = shell_nprim[b];
     const int64_t q0 = pair_ppoff[pr];
     for (int ij = 0; ij < npa * npb; ++ij) {
@@ -213,33 +222,35 @@ __global__ void __launch_bounds__(32) k_pair_block(int la, int lb, int npairs, i
       const double ea = prim_exp[shell_poff[a] + i], eb = prim_exp[shell_poff[b] + j];
       const double p = ea + eb, rp = 1.0 / p;
       const double pref = prim_coef[shell_poff[a] + i] * prim_coef[shell_poff[b] + j] * exp(-ea * eb * rp * ab2);
-      __syncwarp();
-      if (lane <= la) {
-        double v = 1.0;
-        const double r = eb * rp;
-        for (int k = 0; k < la - lane; ++k) v *= r;
-        fa[lane] = v;
-      }
-      if (lane <= lb) {
-        double v = 1.0;
-        const double r = ea * rp;
-        for (int k = 0; k < lb - lane; ++k) v *= r;
-        fb[lane] = v;
-      }
-      __syncwarp();
-      if (pref == 0.0) continue;
+      if (pref == 0.0) continue;  // uniform over the block
+      __syncthreads();            // the previous primitive pair is done with Rs and fab
       const double* R = rbuf + rbase + (q0 + ij - pp_base) * (int64_t)nR;
-      for (int e = lane; e < nW; e += 32) {
-        const int i1 = e / nWb, i2 = e % nWb;
-        const int t0 = g_rowptr[e], t1 = g_rowptr[e + 1];
+      for (int e = tid; e < nR; e += nth) Rs[e] = R[e];
+      if (tid < (la + 1) * (lb + 1)) {
+        const int l1 = tid / (lb + 1), l2 = tid % (lb + 1);
+        double v = pref;
+        const double ra = eb * rp, rb = ea * rp;
+        for (int k = 0; k < la - l1; ++k) v *= ra;
+        for (int k = 0; k < lb - l2; ++k) v *= rb;
+        fab[tid] = v;
+      }
+      __syncthreads();
+      for (int r = tid; r < nW; r += nth) {
+        const int info = g_rowinfo[r];
+        const int t0 = g_rowptr[r], t1 = g_rowptr[r + 1];
         double acc = 0.0;
-        for (int t = t0; t < t1; ++t) acc = fma(g_coef[t], R[g_ridx[t]], acc);
-        W[e] = fma(pref * fa[c_lof[i1]] * fb[c_lof[i2]], acc, W[e]);
+#pragma unroll 4
+        for (int t = t0; t < t1; ++t) {
+          const GTerm g = g_terms[t];
+          acc = fma(g.coef, Rs[g.ridx], acc);
+        }
+        const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
+        W[e] = fma(fab[l1 * (lb + 1) + l2], acc, W[e]);
       }
     }
-    __syncwarp();
+    __syncthreads();
     // X = W T_B^T, V = T_A X
-    for (int e = lane; e < nWa * nb; e += 32) {
+    for (int e = tid; e < nWa * nb; e += nth) {
       const int i1 = e / nb, mb = e % nb;
       const double* wr = W + i1 * nWb;
       const double* tb = TB + mb * nWb;
@@ -247,9 +258,9 @@ __global__ void __launch_bounds__(32) k_pair_block(int la, int lb, int npairs, i
       for (int i2 = 0; i2 < nWb; ++i2) s = fma(wr[i2], tb[i2], s);
       X[e] = s;
     }
-    __syncwarp();
+    __syncthreads();
     const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
-    for (int e = lane; e < na * nb; e += 32) {
+    for (int e = tid; e < na * nb; e += nth) {
       const int ma = e / nb, mb = e % nb;
       double s = 0.0;
       if (a == b && ma > mb) {
@@ -301,9 +312,9 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.boys, t.boys);
   if (e == cudaSuccess) e = upload(&d.etab, t.etab);
   if (e == cudaSuccess) e = upload(&d.eoff, t.eoff);
+  if (e == cudaSuccess) e = upload(&d.g_rowinfo, t.g_rowinfo);
   if (e == cudaSuccess) e = upload(&d.g_rowptr, t.g_rowptr);
-  if (e == cudaSuccess) e = upload(&d.g_ridx, t.g_ridx);
-  if (e == cudaSuccess) e = upload(&d.g_coef, t.g_coef);
+  if (e == cudaSuccess) e = upload(&d.g_terms, t.g_terms);
   if (e == cudaSuccess) e = upload(&d.rmap, t.rmap);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
@@ -356,10 +367,115 @@ static int grid_cap(int64_t n, int per_sm) {
   return (int)(n < cap ? n : cap);
 }
 
+namespace {
+constexpr int kPoolStreams = 8;
+std::mutex g_pool_mu;
+cudaStream_t g_pool[64][kPoolStreams];
+bool g_pool_ok[64] = {};
+bool g_attr_ok[64] = {};
+
+// Per-device pool of non-blocking streams on which the classes of one call run concurrently.
+cudaError_t stream_pool(cudaStream_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool_ok[dev]) {
+    for (int i = 0; i < kPoolStreams; ++i) {
+      e = cudaStreamCreateWithFlags(&g_pool[dev][i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    g_pool_ok[dev] = true;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+// Dynamic shared-memory limits, once per device.
+void set_kernel_attributes() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_attr_ok[dev]) return;
+  const int lim = 227 * 1024;
+  cudaFuncSetAttribute(k_coupling_block<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_coupling_block<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_pair_block, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  g_attr_ok[dev] = true;
+}
+
+struct Launcher {
+  const DeviceBasis& db;
+  const DeviceTables& dt;
+  const Tables& th;
+  int64_t nbf, ncenters;
+  const double* centers;
+  const double* charges;
+  double* out;
+
+  void coupling(const ClassWork& w, int64_t rbase, cudaStream_t s) const {
+    if (w.npp == 0) return;
+    const int lam = w.la + w.lb;
+    const int nch = lam <= 12 ? 32 : 16;
+    const size_t sm = coupling_smem_per_warp(lam, nch);
+    const int* rmap = dt.rmap + th.rmap_off[lam];
+    if (nch == 32)
+      k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, s>>>(
+          lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
+          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+    else
+      k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, s>>>(
+          lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
+          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+  }
+  void pair(const ClassWork& w, int64_t rbase, cudaStream_t s) const {
+    if (w.npairs == 0) return;
+    const int cid = class_id(w.la, w.lb);
+    const size_t sm = pair_smem(w.la, w.lb);
+    k_pair_block<<<grid_cap(w.npairs, 16), pair_threads(w.la, w.lb), sm, s>>>(
+        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_xyz,
+        db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
+        dt.g_rowinfo + th.g_rowbase[cid], dt.g_rowptr + th.g_rowbase[cid], dt.g_terms + th.g_termbase[cid], db.rbuf,
+        nbf, out);
+  }
+};
+
+// Fork the work of `order` over the pool streams after the work already queued on `stream`, and
+// make `stream` wait for all of it.  phase: 0 = coupling only, 1 = pair blocks only, 2 = both.
+cudaError_t run_concurrent(const Launcher& L, const std::vector<ClassWork>& work, const std::vector<int64_t>& rbases,
+                           const std::vector<int>& order, int phase, cudaStream_t stream) {
+  cudaStream_t* pool = nullptr;
+  cudaError_t e = stream_pool(&pool);
+  if (e != cudaSuccess) return e;
+  const int ns = (int)std::min<size_t>(order.size(), (size_t)kPoolStreams);
+  cudaEvent_t fork;
+  e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(fork, stream);
+  for (int i = 0; i < ns; ++i) cudaStreamWaitEvent(pool[i], fork, 0);
+  for (size_t k = 0; k < order.size(); ++k) {
+    const int c = order[k];
+    cudaStream_t s = pool[k % ns];
+    if (phase != 1) L.coupling(work[c], rbases[c], s);
+    if (phase != 0) L.pair(work[c], rbases[c], s);
+  }
+  for (int i = 0; i < ns; ++i) {
+    cudaEvent_t join;
+    e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    cudaEventRecord(join, pool[i]);
+    cudaStreamWaitEvent(stream, join, 0);
+    cudaEventDestroy(join);
+  }
+  cudaEventDestroy(fork);
+  return e;
+}
+}  // namespace
+
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
                                       const double* centers, const double* charges, double* out,
-                                      cudaStream_t stream, std::string* err, cudaEvent_t* events) {
+                                      cudaStream_t stream, std::string* err, cudaEvent_t* events, bool concurrent) {
   if (events) cudaEventRecord(events[0], stream);
   if (nbf == 0 || ncenters == 0) {
     if (events) cudaEventRecord(events[1], stream);
@@ -377,47 +493,41 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
     }
     return SHGO_OK;
   }
+  set_kernel_attributes();
   const Tables& th = tables_host();
-  int64_t rbase = 0;
   std::vector<int64_t> rbases(work.size());
+  int64_t rbase = 0;
   for (size_t c = 0; c < work.size(); ++c) {
     rbases[c] = rbase;
     rbase += work[c].npp * n_r(work[c].la + work[c].lb);
   }
-  for (size_t c = 0; c < work.size(); ++c) {
-    const ClassWork& w = work[c];
-    if (w.npp == 0) continue;
-    const int lam = w.la + w.lb;
-    const int nch = lam <= 12 ? 32 : 16;
-    const size_t sm = coupling_smem_per_warp(lam, nch);
-    const int* rmap = dt.rmap + th.rmap_off[lam];
-    if (nch == 32) {
-      cudaFuncSetAttribute(k_coupling_block<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, stream>>>(
-          lam, w.npp, w.pp_base, rbases[c], db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+  const Launcher L{db, dt, th, nbf, ncenters, centers, charges, out};
+  cudaError_t e = cudaSuccess;
+  if (!concurrent) {
+    for (size_t c = 0; c < work.size(); ++c) L.coupling(work[c], rbases[c], stream);
+    if (events) cudaEventRecord(events[1], stream);
+    for (size_t c = 0; c < work.size(); ++c) L.pair(work[c], rbases[c], stream);
+  } else {
+    // classes by decreasing estimated cost, dealt round-robin over the pool streams
+    std::vector<int> order(work.size());
+    std::vector<double> cost(work.size());
+    for (size_t c = 0; c < work.size(); ++c) {
+      order[c] = (int)c;
+      const int lam = work[c].la + work[c].lb;
+      const double nW = (double)(work[c].la + 1) * (work[c].la + 1) * (work[c].lb + 1) * (work[c].lb + 1);
+      cost[c] = (double)work[c].npp * ((double)ncenters * n_r(lam) + 8.0 * nW) + (double)work[c].npairs * 30.0 * nW;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    if (events) {
+      e = run_concurrent(L, work, rbases, order, 0, stream);
+      cudaEventRecord(events[1], stream);
+      if (e == cudaSuccess) e = run_concurrent(L, work, rbases, order, 1, stream);
     } else {
-      cudaFuncSetAttribute(k_coupling_block<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, stream>>>(
-          lam, w.npp, w.pp_base, rbases[c], db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+      e = run_concurrent(L, work, rbases, order, 2, stream);
     }
   }
-  if (events) cudaEventRecord(events[1], stream);
-  for (size_t c = 0; c < work.size(); ++c) {
-    const ClassWork& w = work[c];
-    if (w.npairs == 0) continue;
-    const int cid = class_id(w.la, w.lb);
-    const size_t sm = pair_smem(w.la, w.lb);
-    cudaFuncSetAttribute(k_pair_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_pair_block<<<grid_cap(w.npairs, 8), 32, sm, stream>>>(
-        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbases[c], db.pair_a, db.pair_b, db.pair_ppoff, db.shell_xyz,
-        db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
-        dt.g_rowptr + th.g_rowbase[cid], dt.g_ridx + th.g_termbase[cid], dt.g_coef + th.g_termbase[cid], db.rbuf,
-        nbf, out);
-  }
   if (events) cudaEventRecord(events[2], stream);
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("kernel launch: ") + cudaGetErrorString(e);
     return SHGO_ERR_CUDA;

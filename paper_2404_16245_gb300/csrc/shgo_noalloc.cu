@@ -75,9 +75,9 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   const size_t o_boys = pk.add(t.boys.size() * sizeof(double));
   const size_t o_etab = pk.add(t.etab.size() * sizeof(double));
   const size_t o_eoff = pk.add(t.eoff.size() * sizeof(int));
+  const size_t o_rowinfo = pk.add(t.g_rowinfo.size() * sizeof(int));
   const size_t o_rowptr = pk.add(t.g_rowptr.size() * sizeof(int));
-  const size_t o_ridx = pk.add(t.g_ridx.size() * sizeof(int));
-  const size_t o_coef = pk.add(t.g_coef.size() * sizeof(double));
+  const size_t o_terms = pk.add(t.g_terms.size() * sizeof(GTerm));
   const size_t o_rmap = pk.add(t.rmap.size() * sizeof(int));
   if (pk.used > kNoallocScratchBytes) {
     *err = "constant tables do not fit the static scratch";
@@ -90,9 +90,9 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   } pieces[] = {{o_boys, t.boys.data(), t.boys.size() * sizeof(double)},
                 {o_etab, t.etab.data(), t.etab.size() * sizeof(double)},
                 {o_eoff, t.eoff.data(), t.eoff.size() * sizeof(int)},
+                {o_rowinfo, t.g_rowinfo.data(), t.g_rowinfo.size() * sizeof(int)},
                 {o_rowptr, t.g_rowptr.data(), t.g_rowptr.size() * sizeof(int)},
-                {o_ridx, t.g_ridx.data(), t.g_ridx.size() * sizeof(int)},
-                {o_coef, t.g_coef.data(), t.g_coef.size() * sizeof(double)},
+                {o_terms, t.g_terms.data(), t.g_terms.size() * sizeof(GTerm)},
                 {o_rmap, t.rmap.data(), t.rmap.size() * sizeof(int)}};
   for (const Piece& p : pieces) {
     e = cudaMemcpy(d.base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
@@ -106,9 +106,9 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   d.tabs.boys = reinterpret_cast<double*>(d.base + o_boys);
   d.tabs.etab = reinterpret_cast<double*>(d.base + o_etab);
   d.tabs.eoff = reinterpret_cast<int*>(d.base + o_eoff);
+  d.tabs.g_rowinfo = reinterpret_cast<int*>(d.base + o_rowinfo);
   d.tabs.g_rowptr = reinterpret_cast<int*>(d.base + o_rowptr);
-  d.tabs.g_ridx = reinterpret_cast<int*>(d.base + o_ridx);
-  d.tabs.g_coef = reinterpret_cast<double*>(d.base + o_coef);
+  d.tabs.g_terms = reinterpret_cast<GTerm*>(d.base + o_terms);
   d.tabs.rmap = reinterpret_cast<int*>(d.base + o_rmap);
   d.tables_end = pk.used;
   d.ready = true;
@@ -302,7 +302,8 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   db.pp_ij = reinterpret_cast<int*>(region + o_ppij);
   db.rbuf = reinterpret_cast<double*>(region + o_rbuf);
   db.rbuf_len = rlen;
-  st = launch_nuclear_attraction(db, nd->tabs, work, nbf, centers->n, centers->xyz, charges, out, s, &err);
+  st = launch_nuclear_attraction(db, nd->tabs, work, nbf, centers->n, centers->xyz, charges, out, s, &err, nullptr,
+                                 /*concurrent=*/false);
   if (st != SHGO_OK) return noalloc_fail(st, err);
   return SHGO_OK;
 }

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 
 #include "shgo_internal.h"
@@ -225,35 +226,45 @@ void build_tables(Tables& t) {
         }
   t.g_rowbase.assign(kNumClasses, 0);
   t.g_termbase.assign(kNumClasses, 0);
+  t.g_rowinfo.clear();
   t.g_rowptr.clear();
-  t.g_ridx.clear();
-  t.g_coef.clear();
+  t.g_terms.clear();
   for (int la = 0; la <= kLmax; ++la)
     for (int lb = 0; lb <= la; ++lb) {
       const int cid = class_id(la, lb), lam = la + lb;
       t.g_rowbase[cid] = (int)t.g_rowptr.size();
-      t.g_termbase[cid] = (int)t.g_ridx.size();
+      t.g_termbase[cid] = (int)t.g_terms.size();
       // R index of (L, M, k) in the Lambda layout
       auto ridx = [&](int L, int M, int k) {
         int off = 0;
         for (int Lp = 0; Lp < L; ++Lp) off += (2 * Lp + 1) * (kmax_of(lam, Lp) + 1);
         return off + (M + L) * (kmax_of(lam, L) + 1) + k;
       };
-      int local = 0;
+      const int nWb = (lb + 1) * (lb + 1);
+      std::vector<int> order;
       for (int i1 = 0; i1 < (la + 1) * (la + 1); ++i1)
-        for (int i2 = 0; i2 < (lb + 1) * (lb + 1); ++i2) {
-          t.g_rowptr.push_back(local);
-          for (const auto& tm : terms[(size_t)i1 * nh + i2]) {
-            const int hi = tm.first & 0xfff, k = tm.first >> 12;
-            int L = 0;
-            while ((L + 1) * (L + 1) <= hi) ++L;
-            const int M = hi - L * L - L;
-            t.g_ridx.push_back(ridx(L, M, k));
-            t.g_coef.push_back(tm.second);
-            ++local;
-          }
+        for (int i2 = 0; i2 < nWb; ++i2) order.push_back(i1 * nWb + i2);
+      auto count = [&](int e) { return (int)terms[(size_t)(e / nWb) * nh + (e % nWb)].size(); };
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count(x) > count(y); });
+      int local = 0;
+      for (int e : order) {
+        const int i1 = e / nWb, i2 = e % nWb;
+        int l1 = 0, l2 = 0;
+        while ((l1 + 1) * (l1 + 1) <= i1) ++l1;
+        while ((l2 + 1) * (l2 + 1) <= i2) ++l2;
+        t.g_rowinfo.push_back(e | (l1 << 16) | (l2 << 20));
+        t.g_rowptr.push_back(local);
+        for (const auto& tm : terms[(size_t)i1 * nh + i2]) {
+          const int hi = tm.first & 0xfff, k = tm.first >> 12;
+          int L = 0;
+          while ((L + 1) * (L + 1) <= hi) ++L;
+          const int M = hi - L * L - L;
+          t.g_terms.push_back(GTerm{tm.second, ridx(L, M, k), 0});
+          ++local;
         }
+      }
       t.g_rowptr.push_back(local);
+      t.g_rowinfo.push_back(0);  // keeps g_rowinfo aligned with g_rowptr (nW + 1 entries per class)
     }
 }
 
