@@ -178,6 +178,8 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
       if (w.npairs > 0) b->work.push_back(w);
     }
   b->npairs = (int64_t)pa.size();
+  std::vector<double> prot(9 * pa.size());
+  for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
   int64_t rlen = 0;
   for (const auto& w : b->work) rlen += w.npp * n_r(w.la + w.lb);
 
@@ -195,6 +197,7 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_a, pa, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_b, pb, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_ppoff, ppoff, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_rot, prot, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_pair, pp_pair, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_ij, pp_ij, &err);
   if (st == SHGO_OK) {
@@ -290,12 +293,20 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
     const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
     const double terms = t.g_rowptr[t.g_rowbase[cid] + nW];
     f1 += (2.0 * terms + 4.0 * nW) * (double)w.npp;
-    // per shell pair: translation matrices and the two products
-    double ta = 0, tb = 0;
-    for (int l1 = 0; l1 <= la; ++l1) ta += (2.0 * l1 + 1) * 2.0 * (2 * (la - l1) + 1);
-    for (int l2 = 0; l2 <= lb; ++l2) tb += (2.0 * l2 + 1) * 2.0 * (2 * (lb - l2) + 1);
+    // per shell pair: real rotation matrices up to max(la, lb), the translation along the pair axis
+    // (diagonal in m) and the rotation of the block back to the molecular frame
+    const int lm = std::max(la, lb);
+    double rot = 0;
+    for (int l = 1; l < lm; ++l)
+      for (int M = -(l + 1); M <= l + 1; ++M) {
+        const int q = rot_index(l, M);
+        rot += 2.0 * (t.rot_ptr[q + 1] - t.rot_ptr[q]) * (2 * l + 3);
+      }
     const double na = 2 * la + 1, nb = 2 * lb + 1;
-    f1 += (na * ta + nb * tb + 2.0 * nWa * nb * nWb + 2.0 * na * nb * nWa) * (double)w.npairs;
+    double zt = 0, vt = 0;
+    for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
+    for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
+    f1 += (rot + zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
     st += (double)w.npairs * (double)n_centers;
     pt += (double)w.npp * (double)n_centers;
   }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -76,8 +77,18 @@ struct Tables {
   // R layout per Lambda: packed (harm index | beta index << 12 | k << 24) for entry e.
   std::vector<int> rmap;
   std::vector<int> rmap_off;  // [kLamMax + 2]
+  // Real rotation matrices D^{l+1} from D^l (S_lm(R y) = sum_m' D^l[m][m'] S_lm'(y)): the
+  // harmonic part of u_c S_{l,m'}(u) for a Cartesian component c is sum_M G(1 m(c), l m'; l+1 M)
+  // S_{l+1,M}.  For l = 0..kLmax-1 and M = -(l+1)..l+1 the list rot_terms[rot_ptr[q] .. rot_ptr[q+1]]
+  // (q = l^2 + 2l + M + l + 1 ... see rot_index()) holds (G, Cartesian component c, m').
+  std::vector<int> rot_ptr;
+  std::vector<GTerm> rot_terms;
 };
 const Tables& tables_host();
+
+// Index of the (l -> l+1, M) list of the rotation recursion: lists for l = 0.. are stored one after
+// the other, 2l + 3 of them per l.
+__host__ __device__ inline int rot_index(int l, int M) { return l * (l + 2) + M + l + 1; }
 
 inline int class_id(int la, int lb) { return la * (la + 1) / 2 + lb; }  // la >= lb
 constexpr int kNumClasses = (kLmax + 1) * (kLmax + 2) / 2;
@@ -98,6 +109,8 @@ struct DeviceTables {
   int* g_rowptr = nullptr;
   GTerm* g_terms = nullptr;
   int* rmap = nullptr;
+  int* rot_ptr = nullptr;
+  GTerm* rot_terms = nullptr;
 };
 shgo_status device_tables(int device, const DeviceTables** out, std::string* err);
 
@@ -123,6 +136,7 @@ struct DeviceBasis {
   int* pair_a = nullptr;
   int* pair_b = nullptr;
   int64_t* pair_ppoff = nullptr;  // first primitive pair of the pair
+  double* pair_rot = nullptr;     // per pair, 3x3 row-major Q with Q (b - a)/|b - a| = z (identity if a = b)
   // primitive pairs, class-sorted: owning pair, i (prim of a), j (prim of b)
   int* pp_pair = nullptr;
   int* pp_ij = nullptr;          // i << 8 | j
@@ -130,6 +144,32 @@ struct DeviceBasis {
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
 };
+
+// Frame of a shell pair: rows (e1, e2, n) of a rotation Q with Q n = z for n = (B - A)/|B - A|,
+// e1 perpendicular to n along the axis least aligned with it, e2 = n x e1 (det Q = +1).
+// Q is the identity when A = B.
+inline void pair_frame(const double* A, const double* B, double* Q) {
+  const double d[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  for (int k = 0; k < 9; ++k) Q[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  if (!(r2 > 0.0)) return;
+  const double r = std::sqrt(r2);
+  const double n[3] = {d[0] / r, d[1] / r, d[2] / r};
+  int ax = 0;
+  for (int k = 1; k < 3; ++k)
+    if (std::fabs(n[k]) < std::fabs(n[ax])) ax = k;
+  double u[3] = {0, 0, 0};
+  u[ax] = 1.0;
+  double e1[3] = {u[1] * n[2] - u[2] * n[1], u[2] * n[0] - u[0] * n[2], u[0] * n[1] - u[1] * n[0]};
+  const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (double& v : e1) v /= l1;
+  const double e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+  for (int k = 0; k < 3; ++k) {
+    Q[k] = e1[k];
+    Q[3 + k] = e2[k];
+    Q[6 + k] = n[k];
+  }
+}
 
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,

@@ -55,7 +55,9 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
                                                        const double* __restrict__ centers,
                                                        const double* __restrict__ charges,
                                                        const double* __restrict__ boys_tab,
-                                                       const int* __restrict__ rmap, double* __restrict__ rbuf) {
+                                                       const int* __restrict__ rmap,
+                                                       const double* __restrict__ pair_rot,
+                                                       double* __restrict__ rbuf) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
   const int nS = n_harm(lam), nB = n_beta(lam), nR = n_r(lam);
@@ -75,6 +77,10 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
     const double Px = (ea * shell_xyz[3 * a] + eb * shell_xyz[3 * b]) * rp;
     const double Py = (ea * shell_xyz[3 * a + 1] + eb * shell_xyz[3 * b + 1]) * rp;
     const double Pz = (ea * shell_xyz[3 * a + 2] + eb * shell_xyz[3 * b + 2]) * rp;
+    // frame of the pair: Q (b - a) is along z, so the translation of Eq. 7 is diagonal in m
+    double Q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Q[k] = pair_rot[9 * pr + k];
     for (int e = lane; e < nR; e += 32) racc[e] = 0.0;
     for (int64_t c0 = 0; c0 < ncenters; c0 += NCH) {
       __syncwarp();
@@ -83,9 +89,10 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
         const int64_t c = c0 + lane;
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
         if (c < ncenters) {
-          dx = centers[3 * c] - Px;
-          dy = centers[3 * c + 1] - Py;
-          dz = centers[3 * c + 2] - Pz;
+          const double ux = centers[3 * c] - Px, uy = centers[3 * c + 1] - Py, uz = centers[3 * c + 2] - Pz;
+          dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
+          dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
+          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz;
           z = charges[c];
         }
         const double T = p * (dx * dx + dy * dy + dz * dz);
@@ -115,10 +122,16 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
       for (int e = lane; e < nR; e += 32) {
         const int code = __ldg(rm + e);
         const int si = code & 0xfff, bi = nS + ((code >> 12) & 0xfff);
-        double acc = racc[e];
-#pragma unroll 8
-        for (int c = 0; c < NCH; ++c) acc = fma(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], acc);
-        racc[e] = acc;
+        // four independent partial sums over the nuclei of the chunk
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+        for (int c = 0; c < NCH; c += 4) {
+          a0 = fma(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], a0);
+          a1 = fma(rows[(size_t)(c + 1) * rs + si], rows[(size_t)(c + 1) * rs + bi], a1);
+          a2 = fma(rows[(size_t)(c + 2) * rs + si], rows[(size_t)(c + 2) * rs + bi], a2);
+          a3 = fma(rows[(size_t)(c + 3) * rs + si], rows[(size_t)(c + 3) * rs + bi], a3);
+        }
+        racc[e] += (a0 + a1) + (a2 + a3);
       }
     }
     // scale 2 pi k! p^{-(k+1)}
@@ -134,12 +147,16 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
   }
 }
 
+// Doubles in D^0 .. D^{l-1} (real rotation matrices stored one after the other).
+__host__ __device__ inline int rot_doff(int l) { return l * (2 * l - 1) * (2 * l + 1) / 3; }
+
 // Shared-memory bytes of one block of k_pair_block.
 __host__ __device__ inline size_t pair_smem(int la, int lb) {
   const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1);
+  const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb;
-  return sizeof(double) * ((size_t)nWa * nWb + (2 * la + 1) * nWa + (2 * lb + 1) * nWb + nWa * (2 * lb + 1) +
-                           (lm + 1) * (lm + 1) + (la + 1) * (lb + 1) + n_r(la + lb) + 8);
+  return sizeof(double) * ((size_t)nWa * nWb + rot_doff(lm + 1) + (la + 1) * na + (lb + 1) * nb + nWa * nb +
+                           2 * na * nb + (la + 1) * (lb + 1) + n_r(la + lb) + 16);
 }
 
 // Threads per block of k_pair_block for a class: enough to cover the W entries of large classes.
@@ -162,6 +179,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     int64_t rbase, const int* __restrict__ pair_a,
                                                     const int* __restrict__ pair_b,
                                                     const int64_t* __restrict__ pair_ppoff,
+                                                    const double* __restrict__ pair_rot,
                                                     const double* __restrict__ shell_xyz,
                                                     const int* __restrict__ shell_poff,
                                                     const int* __restrict__ shell_nprim,
@@ -172,6 +190,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     const int* __restrict__ g_rowinfo,
                                                     const int* __restrict__ g_rowptr,
                                                     const GTerm* __restrict__ g_terms,
+                                                    const int* __restrict__ rot_ptr,
+                                                    const GTerm* __restrict__ rot_terms,
                                                     const double* __restrict__ rbuf, int64_t nbf,
                                                     double* __restrict__ out) {
   extern __shared__ double smem[];
@@ -182,39 +202,86 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb;
   double* W = smem;
-  double* TA = W + nW;
-  double* TB = TA + na * nWa;
-  double* X = TB + nb * nWb;
-  double* Sab = X + nWa * nb;
-  double* fab = Sab + (lm + 1) * (lm + 1);
-  double* Rs = fab + (la + 1) * (lb + 1);
+  double* Dm = W + nW;                     // D^l for l <= lm, D = D(Q^T)
+  double* tA = Dm + rot_doff(lm + 1);      // [l1][ma]
+  double* tB = tA + (la + 1) * na;         // [l2][mb]
+  double* Zb = tB + (lb + 1) * nb;         // [l1 m1][mb]
+  double* Vp = Zb + nWa * nb;              // [ma][mb] in the pair frame, later the final block
+  double* Yb = Vp + na * nb;               // [ma][mb]
+  double* fab = Yb + na * nb;              // [l1][l2]
+  double* Rs = fab + (la + 1) * (lb + 1);  // coupling block of one primitive pair
+  double* Rq = Rs + nR;                    // R = Q^T, row-major
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
-    const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double Bx = shell_xyz[3 * b], By = shell_xyz[3 * b + 1], Bz = shell_xyz[3 * b + 2];
-    const double ABx = Bx - Ax, ABy = By - Ay, ABz = Bz - Az;
+    const double ABx = shell_xyz[3 * b] - shell_xyz[3 * a], ABy = shell_xyz[3 * b + 1] - shell_xyz[3 * a + 1],
+                 ABz = shell_xyz[3 * b + 2] - shell_xyz[3 * a + 2];
     const double ab2 = ABx * ABx + ABy * ABy + ABz * ABz;
+    const double dist = sqrt(ab2);
     __syncthreads();
-    if (tid == 0) solid_harmonics(lm, ABx, ABy, ABz, Sab, 1, c_harm.a, c_harm.b, c_harm.c);
+    if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
     for (int e = tid; e < nW; e += nth) W[e] = 0.0;
+    // translation along z (Eq. 7 with Eq. 8 coefficients, real basis): only nu = 0 survives,
+    // t_A(l1, ma) = E^{la}(ma; l1 ma; 0) |b-a|^{la-l1}, t_B(l2, mb) = E^{lb}(mb; l2 mb; 0) (-|b-a|)^{lb-l2}
+    for (int e = tid; e < (la + 1) * na; e += nth) {
+      const int l1 = e / na, ma = e % na - la, lr = la - l1;
+      double v = 0.0;
+      if (l1 >= (ma < 0 ? -ma : ma)) {
+        v = etab[eoff[la] + translation_offset_dev(la, ma, l1, ma) + lr];
+        for (int k = 0; k < lr; ++k) v *= dist;
+      }
+      tA[e] = v;
+    }
+    for (int e = tid; e < (lb + 1) * nb; e += nth) {
+      const int l2 = e / nb, mb = e % nb - lb, lr = lb - l2;
+      double v = 0.0;
+      if (l2 >= (mb < 0 ? -mb : mb)) {
+        v = etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr];
+        for (int k = 0; k < lr; ++k) v *= -dist;
+      }
+      tB[e] = v;
+    }
     __syncthreads();
-    // translation matrices (Eq. 7 with Eq. 8 coefficients, real basis)
-    for (int e = tid; e < na * nWa; e += nth) {
-      const int ma = e / nWa - la, i1 = e % nWa, l1 = c_lof[i1], m1 = i1 - l1 * l1 - l1, lr = la - l1;
-      const double* ev = etab + eoff[la] + translation_offset_dev(la, ma, l1, m1);
-      double s = 0.0;
-      for (int nu = -lr; nu <= lr; ++nu) s = fma(ev[nu + lr], Sab[lr * lr + lr + nu], s);
-      TA[e] = s;
+    // real rotation matrices D^l(R), R = Q^T: D^0 = 1, D^1 from R, then D^{l+1} from D^l through the
+    // harmonic part of u_c S_{l,m'}(u) (Gaunt product rule with one factor of degree 1)
+    if (tid == 0) Dm[0] = 1.0;
+    if (lm >= 1 && tid < 9) {
+      const int m = tid / 3 - 1, c = tid % 3;  // row m, Cartesian column c (x, y, z)
+      const int crow = m == -1 ? 1 : (m == 0 ? 2 : 0);
+      const int mp = c == 0 ? 1 : (c == 1 ? -1 : 0);
+      Dm[1 + (m + 1) * 3 + (mp + 1)] = Rq[crow * 3 + c];
     }
-    for (int e = tid; e < nb * nWb; e += nth) {
-      const int mb = e / nWb - lb, i2 = e % nWb, l2 = c_lof[i2], m2 = i2 - l2 * l2 - l2, lr = lb - l2;
-      const double* ev = etab + eoff[lb] + translation_offset_dev(lb, mb, l2, m2);
-      double s = 0.0;
-      for (int nu = -lr; nu <= lr; ++nu) s = fma(ev[nu + lr], Sab[lr * lr + lr + nu], s);
-      TB[e] = (lr & 1) ? -s : s;  // S_l(a - b) = (-1)^l S_l(b - a)
+    for (int l = 1; l < lm; ++l) {
+      __syncthreads();
+      const double* Dl = Dm + rot_doff(l);
+      double* Dn = Dm + rot_doff(l + 1);
+      const int n1 = 2 * l + 3;
+      for (int e = tid; e < n1 * n1; e += nth) {
+        const int m = e / n1 - (l + 1), M = e % n1 - (l + 1);
+        const int q = rot_index(l, M);
+        double s = 0.0;
+        if (m >= -l && m <= l) {
+          for (int t = rot_ptr[q]; t < rot_ptr[q + 1]; ++t) {
+            const GTerm g = rot_terms[t];
+            s = fma(g.coef * Rq[6 + g.ridx], Dl[(m + l) * (2 * l + 1) + g.pad + l], s);
+          }
+          s *= c_harm.a[harm_index(l, m)];
+        } else {
+          const double* top = Dl + (2 * l) * (2 * l + 1);  // row m = l
+          const double* bot = Dl;                          // row m = -l
+          for (int t = rot_ptr[q]; t < rot_ptr[q + 1]; ++t) {
+            const GTerm g = rot_terms[t];
+            const double rx = Rq[g.ridx], ry = Rq[3 + g.ridx];
+            const double v = (m > 0) ? (rx * top[g.pad + l] - ry * bot[g.pad + l])
+                                     : (ry * top[g.pad + l] + rx * bot[g.pad + l]);
+            s = fma(g.coef, v, s);
+          }
+          s *= c_harm.c[l];
+        }
+        Dn[e] = s;
+      }
     }
-    // coupling (Gaunt) and primitive contraction
+    // coupling (Gaunt) and primitive contraction, in the pair frame
     const int npa = shell_nprim[a], npb = shell_nprim[b];
     const int64_t q0 = pair_ppoff[pr];
     for (int ij = 0; ij < npa * npb; ++ij) {
@@ -238,41 +305,62 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       for (int r = tid; r < nW; r += nth) {
         const int info = g_rowinfo[r];
         const int t0 = g_rowptr[r], t1 = g_rowptr[r + 1];
-        double acc = 0.0;
-#pragma unroll 4
-        for (int t = t0; t < t1; ++t) {
-          const GTerm g = g_terms[t];
-          acc = fma(g.coef, Rs[g.ridx], acc);
+        double acc0 = 0.0, acc1 = 0.0;
+        int t = t0;
+        for (; t + 1 < t1; t += 2) {
+          const GTerm g0 = g_terms[t], g1 = g_terms[t + 1];
+          acc0 = fma(g0.coef, Rs[g0.ridx], acc0);
+          acc1 = fma(g1.coef, Rs[g1.ridx], acc1);
         }
+        if (t < t1) {
+          const GTerm g0 = g_terms[t];
+          acc0 = fma(g0.coef, Rs[g0.ridx], acc0);
+        }
+        const double acc = acc0 + acc1;
         const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
         W[e] = fma(fab[l1 * (lb + 1) + l2], acc, W[e]);
       }
     }
     __syncthreads();
-    // X = W T_B^T, V = T_A X
+    // V' = t_A W t_B (diagonal in m), first over l2
     for (int e = tid; e < nWa * nb; e += nth) {
-      const int i1 = e / nb, mb = e % nb;
-      const double* wr = W + i1 * nWb;
-      const double* tb = TB + mb * nWb;
+      const int i1 = e / nb, mb = e % nb - lb, amb = mb < 0 ? -mb : mb;
       double s = 0.0;
-      for (int i2 = 0; i2 < nWb; ++i2) s = fma(wr[i2], tb[i2], s);
-      X[e] = s;
+      for (int l2 = amb; l2 <= lb; ++l2) s = fma(tB[l2 * nb + mb + lb], W[i1 * nWb + l2 * l2 + l2 + mb], s);
+      Zb[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb - la, mb = e % nb, ama = ma < 0 ? -ma : ma;
+      double s = 0.0;
+      for (int l1 = ama; l1 <= la; ++l1) s = fma(tA[l1 * na + ma + la], Zb[(l1 * l1 + l1 + ma) * nb + mb], s);
+      Vp[e] = s;
+    }
+    __syncthreads();
+    // back to the molecular frame: V = D^{la} V' (D^{lb})^T
+    const double* Da = Dm + rot_doff(la);
+    const double* Db = Dm + rot_doff(lb);
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      double s = 0.0;
+      for (int k = 0; k < nb; ++k) s = fma(Vp[ma * nb + k], Db[mb * nb + k], s);
+      Yb[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      double s = 0.0;
+      for (int k = 0; k < na; ++k) s = fma(Da[ma * na + k], Yb[k * nb + mb], s);
+      Vp[e] = s;
     }
     __syncthreads();
     const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
     for (int e = tid; e < na * nb; e += nth) {
       const int ma = e / nb, mb = e % nb;
-      double s = 0.0;
-      if (a == b && ma > mb) {
-        // diagonal shell block: use the upper triangle for both halves (exact symmetry)
-        const double* ta = TA + mb * nWa;
-        for (int i1 = 0; i1 < nWa; ++i1) s = fma(ta[i1], X[i1 * nb + ma], s);
-      } else {
-        const double* ta = TA + ma * nWa;
-        for (int i1 = 0; i1 < nWa; ++i1) s = fma(ta[i1], X[i1 * nb + mb], s);
-      }
-      out[(fa0 + ma) * nbf + fb0 + mb] = s;
-      if (a != b) out[(fb0 + mb) * nbf + fa0 + ma] = s;
+      // diagonal shell block: the upper triangle serves both halves (exact symmetry)
+      const double v = (a == b && ma > mb) ? Vp[mb * nb + ma] : Vp[e];
+      out[(fa0 + ma) * nbf + fb0 + mb] = v;
+      if (a != b) out[(fb0 + mb) * nbf + fa0 + ma] = v;
     }
   }
 }
@@ -316,6 +404,8 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.g_rowptr, t.g_rowptr);
   if (e == cudaSuccess) e = upload(&d.g_terms, t.g_terms);
   if (e == cudaSuccess) e = upload(&d.rmap, t.rmap);
+  if (e == cudaSuccess) e = upload(&d.rot_ptr, t.rot_ptr);
+  if (e == cudaSuccess) e = upload(&d.rot_terms, t.rot_terms);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
   if (e == cudaSuccess) {
@@ -422,21 +512,21 @@ struct Launcher {
     if (nch == 32)
       k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
     else
       k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.rbuf);
+          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
   }
   void pair(const ClassWork& w, int64_t rbase, cudaStream_t s) const {
     if (w.npairs == 0) return;
     const int cid = class_id(w.la, w.lb);
     const size_t sm = pair_smem(w.la, w.lb);
     k_pair_block<<<grid_cap(w.npairs, 16), pair_threads(w.la, w.lb), sm, s>>>(
-        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_xyz,
-        db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
-        dt.g_rowinfo + th.g_rowbase[cid], dt.g_rowptr + th.g_rowbase[cid], dt.g_terms + th.g_termbase[cid], db.rbuf,
-        nbf, out);
+        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_rot,
+        db.shell_xyz, db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
+        dt.g_rowinfo + th.g_rowbase[cid], dt.g_rowptr + th.g_rowbase[cid], dt.g_terms + th.g_termbase[cid],
+        dt.rot_ptr, dt.rot_terms, db.rbuf, nbf, out);
   }
 };
 

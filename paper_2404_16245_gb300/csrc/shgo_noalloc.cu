@@ -79,6 +79,8 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   const size_t o_rowptr = pk.add(t.g_rowptr.size() * sizeof(int));
   const size_t o_terms = pk.add(t.g_terms.size() * sizeof(GTerm));
   const size_t o_rmap = pk.add(t.rmap.size() * sizeof(int));
+  const size_t o_rotptr = pk.add(t.rot_ptr.size() * sizeof(int));
+  const size_t o_rotterms = pk.add(t.rot_terms.size() * sizeof(GTerm));
   if (pk.used > kNoallocScratchBytes) {
     *err = "constant tables do not fit the static scratch";
     return SHGO_ERR_OOM;
@@ -93,7 +95,9 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
                 {o_rowinfo, t.g_rowinfo.data(), t.g_rowinfo.size() * sizeof(int)},
                 {o_rowptr, t.g_rowptr.data(), t.g_rowptr.size() * sizeof(int)},
                 {o_terms, t.g_terms.data(), t.g_terms.size() * sizeof(GTerm)},
-                {o_rmap, t.rmap.data(), t.rmap.size() * sizeof(int)}};
+                {o_rmap, t.rmap.data(), t.rmap.size() * sizeof(int)},
+                {o_rotptr, t.rot_ptr.data(), t.rot_ptr.size() * sizeof(int)},
+                {o_rotterms, t.rot_terms.data(), t.rot_terms.size() * sizeof(GTerm)}};
   for (const Piece& p : pieces) {
     e = cudaMemcpy(d.base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -110,6 +114,8 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   d.tabs.g_rowptr = reinterpret_cast<int*>(d.base + o_rowptr);
   d.tabs.g_terms = reinterpret_cast<GTerm*>(d.base + o_terms);
   d.tabs.rmap = reinterpret_cast<int*>(d.base + o_rmap);
+  d.tabs.rot_ptr = reinterpret_cast<int*>(d.base + o_rotptr);
+  d.tabs.rot_terms = reinterpret_cast<GTerm*>(d.base + o_rotterms);
   d.tables_end = pk.used;
   d.ready = true;
   *out = &d;
@@ -193,6 +199,7 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   const size_t o_pa = pk.add(sizeof(int) * (size_t)npairs);
   const size_t o_pb = pk.add(sizeof(int) * (size_t)npairs);
   const size_t o_ppoff = pk.add(sizeof(int64_t) * (size_t)npairs);
+  const size_t o_prot = pk.add(sizeof(double) * 9 * (size_t)npairs);
   const size_t o_pppair = pk.add(sizeof(int) * (size_t)npp);
   const size_t o_ppij = pk.add(sizeof(int) * (size_t)npp);
   const size_t host_bytes = pk.used;
@@ -278,6 +285,11 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   put(o_pa, pa.data(), sizeof(int) * pa.size());
   put(o_pb, pb.data(), sizeof(int) * pb.size());
   put(o_ppoff, ppoff.data(), sizeof(int64_t) * ppoff.size());
+  {
+    std::vector<double> prot(9 * pa.size());
+    for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
+    put(o_prot, prot.data(), sizeof(double) * prot.size());
+  }
   put(o_pppair, pp_pair.data(), sizeof(int) * pp_pair.size());
   put(o_ppij, pp_ij.data(), sizeof(int) * pp_ij.size());
 
@@ -298,6 +310,7 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   db.pair_a = reinterpret_cast<int*>(region + o_pa);
   db.pair_b = reinterpret_cast<int*>(region + o_pb);
   db.pair_ppoff = reinterpret_cast<int64_t*>(region + o_ppoff);
+  db.pair_rot = reinterpret_cast<double*>(region + o_prot);
   db.pp_pair = reinterpret_cast<int*>(region + o_pppair);
   db.pp_ij = reinterpret_cast<int*>(region + o_ppij);
   db.rbuf = reinterpret_cast<double*>(region + o_rbuf);

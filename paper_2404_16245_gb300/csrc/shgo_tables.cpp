@@ -209,6 +209,23 @@ void build_tables(Tables& t) {
       boff += km + 1;
     }
   }
+  // Rotation recursion lists: Cartesian component c = 0, 1, 2 (x, y, z) is S_{1, m(c)} with
+  // m(x) = 1, m(y) = -1, m(z) = 0.
+  t.rot_ptr.clear();
+  t.rot_terms.clear();
+  {
+    const int mc[3] = {1, -1, 0};
+    for (int l = 0; l < kLmax; ++l)
+      for (int M = -(l + 1); M <= l + 1; ++M) {
+        t.rot_ptr.push_back((int)t.rot_terms.size());
+        for (int c = 0; c < 3; ++c)
+          for (int mp = -l; mp <= l; ++mp) {
+            const double g = gaunt_real(1, mc[c], l, mp, l + 1, M);
+            if (std::fabs(g) > 1e-15) t.rot_terms.push_back(GTerm{g, c, mp});
+          }
+      }
+    t.rot_ptr.push_back((int)t.rot_terms.size());
+  }
   // Gaunt programs per class
   std::vector<std::vector<std::pair<int, double>>> terms;  // per (i1, i2) over all l <= kLmax
   const int nh = (kLmax + 1) * (kLmax + 1);
