@@ -165,7 +165,8 @@ def run_shgo(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     R = args.replicas
     reps = [W.config2(replica=rank * R + r) for r in range(R)]
-    bases = [shgo.Basis(b) for b, _, _ in reps]
+    prec = {"fp64": shgo.SHGO_PREC_FP64, "fp32": shgo.SHGO_PREC_FP32_BULK}[args.precision]
+    bases = [shgo.Basis(b, precision=prec) for b, _, _ in reps]
     cents = [torch.tensor(C, device=dev) for _, C, _ in reps]
     chgs = [torch.tensor(Z, device=dev) for _, _, Z in reps]
     outs = [torch.empty((B.nbf, B.nbf), dtype=torch.float64, device=dev) for B in bases]
@@ -244,7 +245,7 @@ def run_shgo(args, ws, rank, local):
         for k in range(ksteps):
             i = k % R
             b = reps[i][0]
-            Bh = shgo.Basis(b)  # host arrays -> library-owned device buffers
+            Bh = shgo.Basis(b, precision=prec)  # host arrays -> library-owned device buffers
             dC[i].copy_(pin_C[i], non_blocking=True)
             dZ[i].copy_(pin_Z[i], non_blocking=True)
             shgo.shgo_nuclear_attraction(Bh.handle, dC[i].shape[0], dC[i].data_ptr(), dZ[i].data_ptr(),
@@ -270,8 +271,9 @@ def run_shgo(args, ws, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "shell_triples_per_step": triples_per_step, "replicas": R,
+                       "precision": args.precision,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write, outside step events)",
                        "wall_s_timed_region": wall},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
@@ -280,6 +282,69 @@ def run_shgo(args, ws, rank, local):
         print(json.dumps(line), flush=True)
     for B in bases:
         B.close()
+    return 0
+
+
+def run_precision_sweep(n_triples: int, n_oracle: int) -> int:
+    """Precision sweep over independent primitive triples (la, lb <= 8, exponents log-uniform
+    [0.01, 1000], |AB|, |PC| <= 15): per (la, lb) class, the block-normwise error of FP32-bulk and
+    FP32-plain against the FP64 GPU path, and of the FP64 GPU path against the oracle (double and
+    extended) on the first n_oracle triples.  Prints one JSON line."""
+    import torch
+
+    import oracle
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+
+    def gpu(basis, Cd, Zd, prec):
+        B = shgo.Basis(basis, precision=prec)
+        V = shgo.nuclear_attraction(B, Cd, Zd)
+        out = V.cpu().numpy()
+        B.close()
+        return out
+
+    def err(g, r):
+        # blocks below the normal double range (|y| < 1e-290: K_AB underflow) carry no relative accuracy
+        s = np.max(np.abs(r))
+        return float(np.max(np.abs(g - r)) / s) if s > 1e-290 else None
+
+    stats: dict = {}
+    for t, (basis, C, Z) in enumerate(W.config5(n_triples, replica=0)):
+        la, lb = int(basis["l"][0]), int(basis["l"][1])
+        key = f"{max(la, lb)},{min(la, lb)}"
+        na = 2 * la + 1
+        Cd = torch.tensor(C, device="cuda")
+        Zd = torch.tensor(Z, device="cuda")
+        v64 = gpu(basis, Cd, Zd, shgo.SHGO_PREC_FP64)[:na, na:]
+        vb = gpu(basis, Cd, Zd, shgo.SHGO_PREC_FP32_BULK)[:na, na:]
+        vp = gpu(basis, Cd, Zd, shgo.SHGO_PREC_FP32_PLAIN)[:na, na:]
+        st = stats.setdefault(key, {"n": 0, "bulk": [], "plain": [], "fp64_vs_oracle": [], "oracle_f64_vs_ld": []})
+        st["n"] += 1
+        for name, val in (("bulk", err(vb, v64)), ("plain", err(vp, v64))):
+            if val is not None:
+                st[name].append(val)
+        if t < n_oracle:
+            ld = oracle.nuclear_attraction(basis, C, Z, precision="ld")[:na, na:]
+            d = oracle.nuclear_attraction(basis, C, Z)[:na, na:]
+            for name, val in (("fp64_vs_oracle", err(v64, ld)), ("oracle_f64_vs_ld", err(d, ld))):
+                if val is not None:
+                    st[name].append(val)
+    out = {}
+    for key, st in sorted(stats.items()):
+        row = {"n": st["n"]}
+        for name in ("bulk", "plain", "fp64_vs_oracle", "oracle_f64_vs_ld"):
+            if st[name]:
+                row[name] = {"max": max(st[name]), "median": float(np.median(st[name]))}
+        out[key] = row
+    allb = [e for st in stats.values() for e in st["bulk"]]
+    allp = [e for st in stats.values() for e in st["plain"]]
+    allo = [e for st in stats.values() for e in st["fp64_vs_oracle"]]
+    print(json.dumps({"precision_sweep": {"triples": n_triples, "oracle_triples": n_oracle,
+                                          "measure": "per block max|x-y| / max|y|",
+                                          "bulk_max": max(allb), "bulk_median": float(np.median(allb)),
+                                          "plain_max": max(allp), "plain_median": float(np.median(allp)),
+                                          "fp64_vs_extended_oracle_max": max(allo) if allo else None,
+                                          "per_class": out}}), flush=True)
     return 0
 
 
@@ -304,17 +369,24 @@ def run_profile_case() -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", action="store_true", help="one warm + one measured call, for ncu")
+    ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
+                    help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
+    ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="shgo", choices=["shgo", "reference"])
     ap.add_argument("--replicas", type=int, default=8)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="fp32 = FP32-bulk nucleus loop (FP64 Boys, coupling and translation)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case()
+    if args.precision_sweep:
+        return run_precision_sweep(args.precision_sweep, args.sweep_oracle)
     ws, rank, local = _dist()
     if ws > 1:
         import torch

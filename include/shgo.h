@@ -42,8 +42,11 @@ typedef enum {
 #define SHGO_LMAX 8
 
 typedef enum {
-  SHGO_PREC_FP64 = 0,     /* every step in FP64 */
-  SHGO_PREC_FP32_BULK = 1 /* FP32 nucleus sums and coupling with compensated sums; FP64 Boys */
+  SHGO_PREC_FP64 = 0,      /* every step in FP64 */
+  SHGO_PREC_FP32_BULK = 1, /* nucleus loop in FP32 (solid harmonics, radial factors, nucleus sums with
+                              compensated two-sum accumulation); geometry, T and the Boys function in
+                              FP64; Gaunt coupling, contraction and translation in FP64 */
+  SHGO_PREC_FP32_PLAIN = 2 /* as SHGO_PREC_FP32_BULK without the compensation (for error studies) */
 } shgo_precision;
 
 typedef struct {

@@ -92,7 +92,8 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   if (n_shells < 0) return fail(SHGO_ERR_INVALID_ARG, "n_shells < 0");
   if (n_shells > 0 && (!l || !n_prim || !exponents || !coefs || !shell_xyz))
     return fail(SHGO_ERR_INVALID_ARG, "NULL basis array");
-  if (opt && opt->precision != SHGO_PREC_FP64 && opt->precision != SHGO_PREC_FP32_BULK)
+  if (opt && opt->precision != SHGO_PREC_FP64 && opt->precision != SHGO_PREC_FP32_BULK &&
+      opt->precision != SHGO_PREC_FP32_PLAIN)
     return fail(SHGO_ERR_INVALID_ARG, "unknown precision mode");
   int64_t nprim_total = 0;
   for (int s = 0; s < n_shells; ++s) {
@@ -120,6 +121,7 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   auto* b = new shgo_basis();
   b->device = device;
   b->n_shells = n_shells;
+  b->d.precision = opt ? opt->precision : SHGO_PREC_FP64;
   std::string err;
 
   // primitive offsets, normalised coefficients (Eq. 1 normalisation, contracted renormalisation)

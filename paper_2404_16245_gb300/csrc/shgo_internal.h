@@ -143,6 +143,7 @@ struct DeviceBasis {
   int64_t* pp_roff = nullptr;    // offset of the pair's coupling block in rbuf
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
+  int precision = SHGO_PREC_FP64;  // a shgo_precision value
 };
 
 // Frame of a shell pair: rows (e1, e2, n) of a rotation Q with Q n = z for n = (B - A)/|B - A|,

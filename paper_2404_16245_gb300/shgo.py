@@ -17,6 +17,7 @@ from . import build as _build
 SHGO_OK = 0
 SHGO_PREC_FP64 = 0
 SHGO_PREC_FP32_BULK = 1
+SHGO_PREC_FP32_PLAIN = 2
 LMAX = 8
 
 _STATUS = {0: "SHGO_OK", 1: "SHGO_ERR_INVALID_ARG", 2: "SHGO_ERR_UNSUPPORTED_L", 3: "SHGO_ERR_OOM",
