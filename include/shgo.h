@@ -146,6 +146,36 @@ shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const int32_t* l, 
                                             const shgo_centers* centers, const double* charges, double* out,
                                             void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many independent molecules in one call.  The shells of molecule m are the next
+ * mol_nshells[m] shells of the arrays (same layout as shgo_basis_create); its nuclei are the next
+ * mol_ncenters[m] rows of `centers`/`charges` at call time.  Pairs never cross molecules.  All
+ * molecules' shell pairs of one (la, lb) class are computed by one launch per kernel, the classes
+ * concurrently.  Release with shgo_free.
+ * ------------------------------------------------------------------------------------------- */
+shgo_status shgo_batch_create(int32_t n_mol, const int32_t* mol_nshells, const int64_t* mol_ncenters, int32_t n_shells,
+                              const int32_t* l, const int32_t* n_prim, const double* exponents, const double* coefs,
+                              const double* shell_xyz, const shgo_options* opt, shgo_basis** out);
+
+/* Per molecule (host arrays of n_mol): its number of functions and the offset (in doubles) of its
+ * row-major nbf_m x nbf_m block V_m in the batched output. */
+shgo_status shgo_batch_layout(const shgo_basis* batch, int64_t* mol_nbf, int64_t* mol_out_offset);
+
+/* Doubles of the batched output (sum of nbf_m^2), or -1 if `batch` is not a batch. */
+int64_t shgo_batch_out_size(const shgo_basis* batch);
+
+/* V_m for every molecule (Eq. 11 per molecule with its own nuclei).  centers [sum n_c][3] and
+ * charges [sum n_c] are device arrays in molecule order; out is a device array of
+ * shgo_batch_out_size doubles, fully overwritten.
+ * The first call on a batch tunes, per (la, lb) class, the nucleus-chunk size of the coupling
+ * kernel and the threads per block of the pair kernel by timing them on this work (it
+ * synchronises `stream`; its output is exact).  The next call captures the whole launch sequence
+ * into a CUDA graph on an internal stream; later calls with the same centers/charges/out pointers
+ * replay it with one cudaGraphLaunch on `stream` (new pointers re-capture).  Calls on one batch
+ * must be ordered, and batched calls on one device should come from one host thread at a time. */
+shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* centers, const double* charges,
+                                            double* out, void* stream);
+
 /* Release a basis and its device memory (synchronises its device).  NULL-safe. */
 void shgo_free(shgo_basis* basis);
 

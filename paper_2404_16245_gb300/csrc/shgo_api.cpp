@@ -45,6 +45,19 @@ struct shgo_basis {
   DeviceBasis d;
   const DeviceTables* tabs = nullptr;
   std::vector<void*> allocations;
+  // batches (shgo_batch_create): per molecule basis size, offset of its V block, nuclei
+  bool batch = false;
+  int n_mol = 1;
+  std::vector<int64_t> mol_nbf, mol_out, mol_c0, mol_nc;
+  int64_t out_size = 0, total_centers = 0;
+  std::vector<double> class_pair_cent, class_pp_cent;  // per class: sum over pairs / primitive pairs of nuclei
+  int* pair_mol = nullptr;
+  int64_t *mol_c0_d = nullptr, *mol_nc_d = nullptr, *mol_out_d = nullptr, *mol_ld_d = nullptr;
+  std::vector<ClassTune> tune;
+  bool tuned = false;
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -73,6 +86,8 @@ void release(shgo_basis* b) {
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   for (void* p : b->allocations) cudaFree(p);
   cudaSetDevice(prev);
   delete b;
@@ -83,9 +98,15 @@ extern "C" {
 
 const char* shgo_last_error(void) { return g_last_error.c_str(); }
 
-shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
-                              const double* coefs, const double* shell_xyz, const shgo_options* opt,
-                              shgo_basis** out) {
+}  // extern "C"
+
+namespace {
+
+// Shells of n_mol molecules (consecutive runs of mol_nshells shells; n_mol = 0 means one molecule
+// whose nuclei are given per call), validated, normalised and turned into class-sorted pair lists.
+shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
+                        const double* coefs, const double* shell_xyz, const shgo_options* opt, int32_t n_mol,
+                        const int32_t* mol_nshells, const int64_t* mol_ncenters, shgo_basis** out) {
   g_last_error.clear();
   if (!out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -95,6 +116,17 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   if (opt && opt->precision != SHGO_PREC_FP64 && opt->precision != SHGO_PREC_FP32_BULK &&
       opt->precision != SHGO_PREC_FP32_PLAIN)
     return fail(SHGO_ERR_INVALID_ARG, "unknown precision mode");
+  const bool batch = n_mol > 0;
+  if (n_mol < 0) return fail(SHGO_ERR_INVALID_ARG, "n_mol < 0");
+  if (batch) {
+    if (!mol_nshells || !mol_ncenters) return fail(SHGO_ERR_INVALID_ARG, "NULL molecule arrays");
+    int64_t tot = 0;
+    for (int m = 0; m < n_mol; ++m) {
+      if (mol_nshells[m] < 0 || mol_ncenters[m] < 0) return fail(SHGO_ERR_INVALID_ARG, "negative molecule size");
+      tot += mol_nshells[m];
+    }
+    if (tot != n_shells) return fail(SHGO_ERR_INVALID_ARG, "molecule shell counts do not add up to n_shells");
+  }
   int64_t nprim_total = 0;
   for (int s = 0; s < n_shells; ++s) {
     if (l[s] < 0) return fail(SHGO_ERR_INVALID_ARG, "negative l in shell " + std::to_string(s));
@@ -122,7 +154,20 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   b->device = device;
   b->n_shells = n_shells;
   b->d.precision = opt ? opt->precision : SHGO_PREC_FP64;
+  b->batch = batch;
+  const int nm = batch ? n_mol : 1;
+  b->n_mol = nm;
   std::string err;
+
+  // molecule of each shell
+  std::vector<int> shell_mol(n_shells, 0), mol_s0(nm + 1, 0);
+  if (batch) {
+    for (int m = 0; m < nm; ++m) mol_s0[m + 1] = mol_s0[m] + mol_nshells[m];
+    for (int m = 0; m < nm; ++m)
+      for (int s = mol_s0[m]; s < mol_s0[m + 1]; ++s) shell_mol[s] = m;
+  } else {
+    mol_s0[1] = n_shells;
+  }
 
   // primitive offsets, normalised coefficients (Eq. 1 normalisation, contracted renormalisation)
   std::vector<int> poff(n_shells + 1, 0);
@@ -146,38 +191,70 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
     const double scale = (double)(1.0L / std::sqrt(self));
     for (int i = 0; i < n_prim[s]; ++i) pcoef[poff[s] + i] *= scale;
   }
+  // function offsets inside each molecule's V block
   std::vector<int64_t> foff(n_shells + 1, 0);
-  for (int s = 0; s < n_shells; ++s) foff[s + 1] = foff[s] + 2 * l[s] + 1;
-  b->nbf = foff[n_shells];
+  b->mol_nbf.assign(nm, 0);
+  for (int s = 0; s < n_shells; ++s) {
+    foff[s] = b->mol_nbf[shell_mol[s]];
+    b->mol_nbf[shell_mol[s]] += 2 * l[s] + 1;
+  }
+  foff[n_shells] = 0;
+  b->mol_out.assign(nm, 0);
+  b->mol_c0.assign(nm, 0);
+  b->mol_nc.assign(nm, 0);
+  int64_t acc_out = 0, acc_c = 0;
+  for (int m = 0; m < nm; ++m) {
+    b->mol_out[m] = acc_out;
+    acc_out += b->mol_nbf[m] * b->mol_nbf[m];
+    b->mol_c0[m] = acc_c;
+    b->mol_nc[m] = batch ? mol_ncenters[m] : 0;
+    acc_c += b->mol_nc[m];
+  }
+  b->out_size = acc_out;
+  b->total_centers = acc_c;
+  b->nbf = batch ? 0 : b->mol_nbf[0];
+  for (int m = 0; m < nm; ++m) b->nbf = batch ? b->nbf + b->mol_nbf[m] : b->nbf;
 
-  // class-sorted pairs (la >= lb), and their primitive pairs
-  std::vector<std::vector<int>> by_l(kLmax + 1);
-  for (int s = 0; s < n_shells; ++s) by_l[l[s]].push_back(s);
-  std::vector<int> pa, pb;
+  // class-sorted pairs (la >= lb), molecule after molecule inside a class, and their primitive pairs
+  std::vector<std::vector<std::vector<int>>> by_l(nm, std::vector<std::vector<int>>(kLmax + 1));
+  for (int s = 0; s < n_shells; ++s) by_l[shell_mol[s]][l[s]].push_back(s);
+  std::vector<int> pa, pb, pmol;
   std::vector<int64_t> ppoff;
   std::vector<int> pp_pair, pp_ij;
   int64_t ppcount = 0;
   for (int la = 0; la <= kLmax; ++la)
     for (int lb = 0; lb <= la; ++lb) {
       ClassWork w{la, lb, 0, (int)pa.size(), 0, ppcount};
-      for (size_t x = 0; x < by_l[la].size(); ++x) {
-        const size_t ylim = (la == lb) ? x + 1 : by_l[lb].size();
-        for (size_t y = 0; y < ylim; ++y) {
-          const int sa = by_l[la][x], sb = by_l[lb][y];
-          pa.push_back(sa);
-          pb.push_back(sb);
-          ppoff.push_back(ppcount);
-          for (int i = 0; i < n_prim[sa]; ++i)
-            for (int j = 0; j < n_prim[sb]; ++j) {
-              pp_pair.push_back((int)pa.size() - 1);
-              pp_ij.push_back((i << 8) | j);
-            }
-          ppcount += (int64_t)n_prim[sa] * n_prim[sb];
-          ++w.npairs;
+      double pc = 0, ppc = 0;
+      for (int m = 0; m < nm; ++m) {
+        const auto& A = by_l[m][la];
+        const auto& B = by_l[m][lb];
+        for (size_t x = 0; x < A.size(); ++x) {
+          const size_t ylim = (la == lb) ? x + 1 : B.size();
+          for (size_t y = 0; y < ylim; ++y) {
+            const int sa = A[x], sb = B[y];
+            pa.push_back(sa);
+            pb.push_back(sb);
+            pmol.push_back(m);
+            ppoff.push_back(ppcount);
+            for (int i = 0; i < n_prim[sa]; ++i)
+              for (int j = 0; j < n_prim[sb]; ++j) {
+                pp_pair.push_back((int)pa.size() - 1);
+                pp_ij.push_back((i << 8) | j);
+              }
+            ppcount += (int64_t)n_prim[sa] * n_prim[sb];
+            ++w.npairs;
+            pc += (double)b->mol_nc[m];
+            ppc += (double)b->mol_nc[m] * n_prim[sa] * n_prim[sb];
+          }
         }
       }
       w.npp = ppcount - w.pp_base;
-      if (w.npairs > 0) b->work.push_back(w);
+      if (w.npairs > 0) {
+        b->work.push_back(w);
+        b->class_pair_cent.push_back(pc);
+        b->class_pp_cent.push_back(ppc);
+      }
     }
   b->npairs = (int64_t)pa.size();
   std::vector<double> prot(9 * pa.size());
@@ -187,7 +264,7 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
 
   std::vector<double> xyz(shell_xyz, shell_xyz + 3 * (size_t)n_shells);
   std::vector<int> lv(l, l + n_shells), npv(n_prim, n_prim + n_shells);
-  std::vector<int> poffv(poff.begin(), poff.end() - (n_shells >= 0 ? 1 : 0));
+  std::vector<int> poffv(poff.begin(), poff.end() - 1);
   shgo_status st = SHGO_OK;
   if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_xyz, xyz, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_l, lv, &err);
@@ -202,6 +279,17 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_rot, prot, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_pair, pp_pair, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_ij, pp_ij, &err);
+  if (batch) {
+    if (st == SHGO_OK) st = dev_upload(b, &b->pair_mol, pmol, &err);
+    if (st == SHGO_OK) st = dev_upload(b, &b->mol_c0_d, b->mol_c0, &err);
+    if (st == SHGO_OK) st = dev_upload(b, &b->mol_nc_d, b->mol_nc, &err);
+    if (st == SHGO_OK) st = dev_upload(b, &b->mol_out_d, b->mol_out, &err);
+    if (st == SHGO_OK) st = dev_upload(b, &b->mol_ld_d, b->mol_nbf, &err);
+    if (st == SHGO_OK && cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      st = SHGO_ERR_CUDA;
+      err = "cannot create the capture stream";
+    }
+  }
   if (st == SHGO_OK) {
     b->d.rbuf_len = rlen;
     cudaError_t e = cudaMalloc((void**)&b->d.rbuf, sizeof(double) * (size_t)(rlen > 0 ? rlen : 1));
@@ -218,6 +306,102 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
     return fail(st, err);
   }
   *out = b;
+  return SHGO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
+                              const double* coefs, const double* shell_xyz, const shgo_options* opt,
+                              shgo_basis** out) {
+  return build_basis(n_shells, l, n_prim, exponents, coefs, shell_xyz, opt, 0, nullptr, nullptr, out);
+}
+
+shgo_status shgo_batch_create(int32_t n_mol, const int32_t* mol_nshells, const int64_t* mol_ncenters, int32_t n_shells,
+                              const int32_t* l, const int32_t* n_prim, const double* exponents, const double* coefs,
+                              const double* shell_xyz, const shgo_options* opt, shgo_basis** out) {
+  if (n_mol < 1) {
+    g_last_error = "n_mol must be >= 1";
+    return SHGO_ERR_INVALID_ARG;
+  }
+  return build_basis(n_shells, l, n_prim, exponents, coefs, shell_xyz, opt, n_mol, mol_nshells, mol_ncenters, out);
+}
+
+shgo_status shgo_batch_layout(const shgo_basis* batch, int64_t* mol_nbf, int64_t* mol_out_offset) {
+  if (!batch || !batch->batch) return fail(SHGO_ERR_INVALID_ARG, "not a batch");
+  for (int m = 0; m < batch->n_mol; ++m) {
+    if (mol_nbf) mol_nbf[m] = batch->mol_nbf[m];
+    if (mol_out_offset) mol_out_offset[m] = batch->mol_out[m];
+  }
+  return SHGO_OK;
+}
+
+int64_t shgo_batch_out_size(const shgo_basis* batch) { return batch && batch->batch ? batch->out_size : -1; }
+
+shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* centers, const double* charges,
+                                            double* out, void* stream) {
+  g_last_error.clear();
+  if (!batch || !batch->batch) return fail(SHGO_ERR_INVALID_ARG, "not a batch");
+  if (batch->total_centers > 0 && (!centers || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
+  if (batch->out_size > 0 && !out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  if (batch->work.empty()) return SHGO_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != batch->device) cudaSetDevice(batch->device);
+  MolView mv;
+  mv.pair_mol = batch->pair_mol;
+  mv.c0 = batch->mol_c0_d;
+  mv.nc = batch->mol_nc_d;
+  mv.out_off = batch->mol_out_d;
+  mv.ld = batch->mol_ld_d;
+  mv.ncenters = batch->total_centers;
+  const double npp_cent = batch->npairs > 0 ? (double)batch->total_centers / batch->n_mol : 0.0;
+  std::string err;
+  shgo_status st = SHGO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!batch->tuned) {
+    // first call: tune the launch shape of every class on the real work (its output is exact)
+    st = autotune_batched(batch->d, *batch->tabs, batch->work, mv, centers, charges, out, &batch->tune, s, &err);
+    if (st == SHGO_OK) batch->tuned = true;
+  } else {
+    const void* key[3] = {centers, charges, out};
+    if (!batch->graph || std::memcmp(key, batch->graph_key, sizeof(key)) != 0) {
+      // capture the whole batch (all classes, both kernels, fork/join over the stream pool) once
+      if (batch->graph) {
+        cudaGraphExecDestroy(batch->graph);
+        batch->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(batch->capture_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        st = launch_batched(batch->d, *batch->tabs, batch->work, mv, npp_cent, centers, charges, out, &batch->tune,
+                            batch->capture_stream, &err);
+        e = cudaStreamEndCapture(batch->capture_stream, &g);
+      }
+      if (e == cudaSuccess && st == SHGO_OK) e = cudaGraphInstantiate(&batch->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess || st != SHGO_OK) {
+        if (st == SHGO_OK) {
+          st = SHGO_ERR_CUDA;
+          err = std::string("graph capture: ") + cudaGetErrorString(e);
+        }
+        batch->graph = nullptr;
+      } else {
+        std::memcpy(batch->graph_key, key, sizeof(key));
+      }
+    }
+    if (st == SHGO_OK) {
+      const cudaError_t e = cudaGraphLaunch(batch->graph, s);
+      if (e != cudaSuccess) {
+        st = SHGO_ERR_CUDA;
+        err = std::string("graph launch: ") + cudaGetErrorString(e);
+      }
+    }
+  }
+  if (prev != batch->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;
 }
 
@@ -281,7 +465,11 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
   if (!basis || !flops || !triples || n_centers < 0) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
   const Tables& t = tables_host();
   double f0 = 0, f1 = 0, st = 0, pt = 0;
-  for (const auto& w : basis->work) {
+  for (size_t wi = 0; wi < basis->work.size(); ++wi) {
+    const ClassWork& w = basis->work[wi];
+    // nuclei seen by the class: per call for one molecule, per molecule for a batch
+    const double pair_cent = basis->batch ? basis->class_pair_cent[wi] : (double)w.npairs * (double)n_centers;
+    const double pp_cent = basis->batch ? basis->class_pp_cent[wi] : (double)w.npp * (double)n_centers;
     const int la = w.la, lb = w.lb, lam = la + lb;
     const double nB = n_beta(lam), nR = n_r(lam);
     // per primitive triple
@@ -289,7 +477,7 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
     for (int l = 1; l < lam; ++l) s_lm += 8.0 * l + 8.0;
     const double boys = 4.0 * kBoysK + 1 + 3.0 * lam;
     const double per_triple = 9 + boys + (lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
-    f0 += per_triple * (double)w.npp * (double)n_centers + nR * (double)w.npp;
+    f0 += per_triple * pp_cent + nR * (double)w.npp;
     // per primitive pair: coupling
     const int cid = class_id(la, lb);
     const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
@@ -309,8 +497,8 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
     for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
     for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
     f1 += (rot + zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
-    st += (double)w.npairs * (double)n_centers;
-    pt += (double)w.npp * (double)n_centers;
+    st += pair_cent;
+    pt += pp_cent;
   }
   flops[0] = f0;
   flops[1] = f1;

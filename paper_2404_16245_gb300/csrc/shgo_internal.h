@@ -114,6 +114,41 @@ struct DeviceTables {
 };
 shgo_status device_tables(int device, const DeviceTables** out, std::string* err);
 
+// Molecules of a batch, seen from the kernels: pair -> molecule, and per molecule its first
+// nucleus, nucleus count, offset of its V block in the output and its basis size (the leading
+// dimension of that block).  pair_mol == nullptr means one molecule with the scalar fields.
+struct MolView {
+  const int* pair_mol = nullptr;
+  const int64_t* c0 = nullptr;
+  const int64_t* nc = nullptr;
+  const int64_t* out_off = nullptr;
+  const int64_t* ld = nullptr;
+  int64_t ncenters = 0;
+  int64_t nbf = 0;
+};
+
+__device__ __forceinline__ void mol_centers(const MolView& mv, int pr, int64_t& c_begin, int64_t& n) {
+  if (mv.pair_mol) {
+    const int m = mv.pair_mol[pr];
+    c_begin = mv.c0[m];
+    n = mv.nc[m];
+  } else {
+    c_begin = 0;
+    n = mv.ncenters;
+  }
+}
+
+__device__ __forceinline__ void mol_output(const MolView& mv, int pr, int64_t& base, int64_t& ld) {
+  if (mv.pair_mol) {
+    const int m = mv.pair_mol[pr];
+    base = mv.out_off[m];
+    ld = mv.ld[m];
+  } else {
+    base = 0;
+    ld = mv.nbf;
+  }
+}
+
 // Kernel launchers (shgo_kernels.cu).
 struct ClassWork {
   int la, lb;
@@ -178,5 +213,22 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
                                       cudaStream_t stream, std::string* err, cudaEvent_t* events = nullptr,
                                       bool concurrent = true);
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
+
+// Launch shape of one class: nucleus chunk of the coupling kernel (16 or 32) and threads per
+// block of the pair kernel (32, 64 or 128); 0 = the default rule.
+struct ClassTune {
+  int nch = 0;
+  int threads = 0;
+};
+
+// All molecules of a batch: one launch per class and kernel, classes concurrent on the pool.
+shgo_status launch_batched(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                           const MolView& mv, double nuclei_per_pair, const double* centers, const double* charges,
+                           double* out, const std::vector<ClassTune>* tune, cudaStream_t stream, std::string* err);
+
+// Times the candidate shapes of every class on the real work (synchronises the stream).
+shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                             const MolView& mv, const double* centers, const double* charges, double* out,
+                             std::vector<ClassTune>* tune, cudaStream_t stream, std::string* err);
 
 }  // namespace shgo

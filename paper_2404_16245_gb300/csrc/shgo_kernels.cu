@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
                                                        const double* __restrict__ shell_xyz,
                                                        const int* __restrict__ shell_poff,
                                                        const int* __restrict__ shell_nprim,
-                                                       const double* __restrict__ prim_exp, int64_t ncenters,
+                                                       const double* __restrict__ prim_exp, MolView mv,
                                                        const double* __restrict__ centers,
                                                        const double* __restrict__ charges,
                                                        const double* __restrict__ boys_tab,
@@ -74,25 +74,29 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
     const double eb = prim_exp[shell_poff[b] + (ij & 255)];
     const double p = ea + eb;
     const double rp = 1.0 / p;
-    const double Px = (ea * shell_xyz[3 * a] + eb * shell_xyz[3 * b]) * rp;
-    const double Py = (ea * shell_xyz[3 * a + 1] + eb * shell_xyz[3 * b + 1]) * rp;
-    const double Pz = (ea * shell_xyz[3 * a + 2] + eb * shell_xyz[3 * b + 2]) * rp;
+    // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
+    // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
+    const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
+    const double ABx = shell_xyz[3 * b] - Ax, ABy = shell_xyz[3 * b + 1] - Ay, ABz = shell_xyz[3 * b + 2] - Az;
+    const double shift = eb * rp * sqrt(ABx * ABx + ABy * ABy + ABz * ABz);  // |P - A|, along z in the pair frame
     // frame of the pair: Q (b - a) is along z, so the translation of Eq. 7 is diagonal in m
     double Q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q[k] = pair_rot[9 * pr + k];
     for (int e = lane; e < nR; e += 32) racc[e] = 0.0;
-    for (int64_t c0 = 0; c0 < ncenters; c0 += NCH) {
+    int64_t cbeg, ncen;
+    mol_centers(mv, pr, cbeg, ncen);
+    for (int64_t c0 = 0; c0 < ncen; c0 += NCH) {
       __syncwarp();
       if (lane < NCH) {
         double* row = rows + (size_t)lane * rs;
-        const int64_t c = c0 + lane;
+        const int64_t c = cbeg + c0 + lane;
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
-        if (c < ncenters) {
-          const double ux = centers[3 * c] - Px, uy = centers[3 * c + 1] - Py, uz = centers[3 * c + 2] - Pz;
+        if (c0 + lane < ncen) {
+          const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;
           dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
           dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
-          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz;
+          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - shift;
           z = charges[c];
         }
         const double T = p * (dx * dx + dy * dy + dz * dz);
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
                                                            const int* __restrict__ pair_b,
                                                            const double* __restrict__ shell_xyz,
                                                            const int* __restrict__ shell_poff,
-                                                           const double* __restrict__ prim_exp, int64_t ncenters,
+                                                           const double* __restrict__ prim_exp, MolView mv,
                                                            const double* __restrict__ centers,
                                                            const double* __restrict__ charges,
                                                            const double* __restrict__ boys_tab,
@@ -203,26 +207,30 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
     const double eb = prim_exp[shell_poff[b] + (ij & 255)];
     const double p = ea + eb;
     const double rp = 1.0 / p;
-    const double Px = (ea * shell_xyz[3 * a] + eb * shell_xyz[3 * b]) * rp;
-    const double Py = (ea * shell_xyz[3 * a + 1] + eb * shell_xyz[3 * b + 1]) * rp;
-    const double Pz = (ea * shell_xyz[3 * a + 2] + eb * shell_xyz[3 * b + 2]) * rp;
+    // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
+    // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
+    const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
+    const double ABx = shell_xyz[3 * b] - Ax, ABy = shell_xyz[3 * b + 1] - Ay, ABz = shell_xyz[3 * b + 2] - Az;
+    const double shift = eb * rp * sqrt(ABx * ABx + ABy * ABy + ABz * ABz);  // |P - A|, along z in the pair frame
     const double sp = sqrt(p);
     double Q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q[k] = pair_rot[9 * pr + k];
     for (int e = lane; e < nR; e += 32) racc[e] = make_float2(0.f, 0.f);
-    for (int64_t c0 = 0; c0 < ncenters; c0 += NCH) {
+    int64_t cbeg, ncen;
+    mol_centers(mv, pr, cbeg, ncen);
+    for (int64_t c0 = 0; c0 < ncen; c0 += NCH) {
       __syncwarp();
       if (lane < NCH) {
         float* row = rows + (size_t)lane * rs;
         double* F = fscr + (size_t)lane * (lam + 2);
-        const int64_t c = c0 + lane;
+        const int64_t c = cbeg + c0 + lane;
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
-        if (c < ncenters) {
-          const double ux = centers[3 * c] - Px, uy = centers[3 * c + 1] - Py, uz = centers[3 * c + 2] - Pz;
+        if (c0 + lane < ncen) {
+          const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;
           dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
           dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
-          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz;
+          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - shift;
           z = charges[c];
         }
         const double r2 = dx * dx + dy * dy + dz * dz;
@@ -350,7 +358,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     const GTerm* __restrict__ g_terms,
                                                     const int* __restrict__ rot_ptr,
                                                     const GTerm* __restrict__ rot_terms,
-                                                    const double* __restrict__ rbuf, int64_t nbf,
+                                                    const double* __restrict__ rbuf, MolView mv,
                                                     double* __restrict__ out) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -513,12 +521,15 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
     }
     __syncthreads();
     const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
+    int64_t obase, ld;
+    mol_output(mv, pr, obase, ld);
+    double* o = out + obase;
     for (int e = tid; e < na * nb; e += nth) {
       const int ma = e / nb, mb = e % nb;
       // diagonal shell block: the upper triangle serves both halves (exact symmetry)
       const double v = (a == b && ma > mb) ? Vp[mb * nb + ma] : Vp[e];
-      out[(fa0 + ma) * nbf + fb0 + mb] = v;
-      if (a != b) out[(fb0 + mb) * nbf + fa0 + ma] = v;
+      o[(fa0 + ma) * ld + fb0 + mb] = v;
+      if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = v;
     }
   }
 }
@@ -660,23 +671,33 @@ struct Launcher {
   const DeviceBasis& db;
   const DeviceTables& dt;
   const Tables& th;
-  int64_t nbf, ncenters;
+  MolView mv;
   const double* centers;
   const double* charges;
   double* out;
+  const std::vector<ClassTune>* tune;  // per entry of `work`, or nullptr for the default shapes
 
-  void coupling(const ClassWork& w, int64_t rbase, cudaStream_t s) const {
+  int nch_of(size_t c, int lam) const {
+    if (tune && (*tune)[c].nch) return (*tune)[c].nch;
+    return lam <= 12 ? 32 : 16;
+  }
+  int threads_of(size_t c, int la, int lb) const {
+    if (tune && (*tune)[c].threads) return (*tune)[c].threads;
+    return pair_threads(la, lb);
+  }
+
+  void coupling(const std::vector<ClassWork>& work, size_t c, int64_t rbase, cudaStream_t s) const {
+    const ClassWork& w = work[c];
     if (w.npp == 0) return;
     const int lam = w.la + w.lb;
-    const int nch = lam <= 12 ? 32 : 16;
-    const size_t sm = coupling_smem_per_warp(lam, nch);
+    const int nch = nch_of(c, lam);
     const int* rmap = dt.rmap + th.rmap_off[lam];
     if (db.precision != SHGO_PREC_FP64) {
       const size_t sm32 = coupling_smem_f32(lam, nch);
       const int grid = grid_cap(w.npp, 16);
 #define SHGO_F32_ARGS                                                                                              \
   lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.prim_exp, \
-      ncenters, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf
+      mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf
       const bool comp = db.precision == SHGO_PREC_FP32_BULK;
       if (nch == 32 && comp)
         k_coupling_block_f32<32, true><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
@@ -689,24 +710,26 @@ struct Launcher {
 #undef SHGO_F32_ARGS
       return;
     }
+    const size_t sm = coupling_smem_per_warp(lam, nch);
     if (nch == 32)
       k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
+          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
     else
       k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, ncenters, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
+          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
   }
-  void pair(const ClassWork& w, int64_t rbase, cudaStream_t s) const {
+  void pair(const std::vector<ClassWork>& work, size_t c, int64_t rbase, cudaStream_t s) const {
+    const ClassWork& w = work[c];
     if (w.npairs == 0) return;
     const int cid = class_id(w.la, w.lb);
     const size_t sm = pair_smem(w.la, w.lb);
-    k_pair_block<<<grid_cap(w.npairs, 16), pair_threads(w.la, w.lb), sm, s>>>(
+    k_pair_block<<<grid_cap(w.npairs, 16), threads_of(c, w.la, w.lb), sm, s>>>(
         w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_rot,
         db.shell_xyz, db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
         dt.g_rowinfo + th.g_rowbase[cid], dt.g_rowptr + th.g_rowbase[cid], dt.g_terms + th.g_termbase[cid],
-        dt.rot_ptr, dt.rot_terms, db.rbuf, nbf, out);
+        dt.rot_ptr, dt.rot_terms, db.rbuf, mv, out);
   }
 };
 
@@ -718,6 +741,7 @@ cudaError_t run_concurrent(const Launcher& L, const std::vector<ClassWork>& work
   cudaError_t e = stream_pool(&pool);
   if (e != cudaSuccess) return e;
   const int ns = (int)std::min<size_t>(order.size(), (size_t)kPoolStreams);
+  if (ns == 0) return cudaSuccess;
   cudaEvent_t fork;
   e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
   if (e != cudaSuccess) return e;
@@ -726,8 +750,8 @@ cudaError_t run_concurrent(const Launcher& L, const std::vector<ClassWork>& work
   for (size_t k = 0; k < order.size(); ++k) {
     const int c = order[k];
     cudaStream_t s = pool[k % ns];
-    if (phase != 1) L.coupling(work[c], rbases[c], s);
-    if (phase != 0) L.pair(work[c], rbases[c], s);
+    if (phase != 1) L.coupling(work, c, rbases[c], s);
+    if (phase != 0) L.pair(work, c, rbases[c], s);
   }
   for (int i = 0; i < ns; ++i) {
     cudaEvent_t join;
@@ -739,6 +763,39 @@ cudaError_t run_concurrent(const Launcher& L, const std::vector<ClassWork>& work
   }
   cudaEventDestroy(fork);
   return e;
+}
+
+std::vector<int64_t> class_rbases(const std::vector<ClassWork>& work) {
+  std::vector<int64_t> rbases(work.size());
+  int64_t rbase = 0;
+  for (size_t c = 0; c < work.size(); ++c) {
+    rbases[c] = rbase;
+    rbase += work[c].npp * n_r(work[c].la + work[c].lb);
+  }
+  return rbases;
+}
+
+// Classes by decreasing estimated cost (dealt round-robin over the pool streams).
+std::vector<int> class_order(const std::vector<ClassWork>& work, double nuclei_per_pair) {
+  std::vector<int> order(work.size());
+  std::vector<double> cost(work.size());
+  for (size_t c = 0; c < work.size(); ++c) {
+    order[c] = (int)c;
+    const int lam = work[c].la + work[c].lb;
+    const double nW = (double)(work[c].la + 1) * (work[c].la + 1) * (work[c].lb + 1) * (work[c].lb + 1);
+    cost[c] = (double)work[c].npp * (nuclei_per_pair * n_r(lam) + 8.0 * nW) + (double)work[c].npairs * 30.0 * nW;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  return order;
+}
+
+shgo_status launch_error(std::string* err) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *err = std::string("kernel launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return SHGO_OK;
 }
 }  // namespace
 
@@ -765,29 +822,18 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
   }
   set_kernel_attributes();
   const Tables& th = tables_host();
-  std::vector<int64_t> rbases(work.size());
-  int64_t rbase = 0;
-  for (size_t c = 0; c < work.size(); ++c) {
-    rbases[c] = rbase;
-    rbase += work[c].npp * n_r(work[c].la + work[c].lb);
-  }
-  const Launcher L{db, dt, th, nbf, ncenters, centers, charges, out};
+  const std::vector<int64_t> rbases = class_rbases(work);
+  MolView mv;
+  mv.ncenters = ncenters;
+  mv.nbf = nbf;
+  const Launcher L{db, dt, th, mv, centers, charges, out, nullptr};
   cudaError_t e = cudaSuccess;
   if (!concurrent) {
-    for (size_t c = 0; c < work.size(); ++c) L.coupling(work[c], rbases[c], stream);
+    for (size_t c = 0; c < work.size(); ++c) L.coupling(work, c, rbases[c], stream);
     if (events) cudaEventRecord(events[1], stream);
-    for (size_t c = 0; c < work.size(); ++c) L.pair(work[c], rbases[c], stream);
+    for (size_t c = 0; c < work.size(); ++c) L.pair(work, c, rbases[c], stream);
   } else {
-    // classes by decreasing estimated cost, dealt round-robin over the pool streams
-    std::vector<int> order(work.size());
-    std::vector<double> cost(work.size());
-    for (size_t c = 0; c < work.size(); ++c) {
-      order[c] = (int)c;
-      const int lam = work[c].la + work[c].lb;
-      const double nW = (double)(work[c].la + 1) * (work[c].la + 1) * (work[c].lb + 1) * (work[c].lb + 1);
-      cost[c] = (double)work[c].npp * ((double)ncenters * n_r(lam) + 8.0 * nW) + (double)work[c].npairs * 30.0 * nW;
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    const std::vector<int> order = class_order(work, (double)ncenters);
     if (events) {
       e = run_concurrent(L, work, rbases, order, 0, stream);
       cudaEventRecord(events[1], stream);
@@ -797,12 +843,84 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
     }
   }
   if (events) cudaEventRecord(events[2], stream);
-  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("kernel launch: ") + cudaGetErrorString(e);
     return SHGO_ERR_CUDA;
   }
-  return SHGO_OK;
+  return launch_error(err);
+}
+
+shgo_status launch_batched(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                           const MolView& mv, double nuclei_per_pair, const double* centers, const double* charges,
+                           double* out, const std::vector<ClassTune>* tune, cudaStream_t stream, std::string* err) {
+  if (work.empty()) return SHGO_OK;
+  set_kernel_attributes();
+  const Tables& th = tables_host();
+  const std::vector<int64_t> rbases = class_rbases(work);
+  const Launcher L{db, dt, th, mv, centers, charges, out, tune};
+  const cudaError_t e = run_concurrent(L, work, rbases, class_order(work, nuclei_per_pair), 2, stream);
+  if (e != cudaSuccess) {
+    *err = std::string("kernel launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return launch_error(err);
+}
+
+shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                             const MolView& mv, const double* centers, const double* charges, double* out,
+                             std::vector<ClassTune>* tune, cudaStream_t stream, std::string* err) {
+  // Each candidate shape of a class runs the class's real work once (the output is rewritten by
+  // every candidate, so the call's result stays exact); the fastest by CUDA events is kept.
+  set_kernel_attributes();
+  const Tables& th = tables_host();
+  const std::vector<int64_t> rbases = class_rbases(work);
+  tune->assign(work.size(), ClassTune{});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_it = [&](auto&& fn) {
+    cudaEventRecord(e0, stream);
+    fn();
+    cudaEventRecord(e1, stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  for (size_t c = 0; c < work.size(); ++c) {
+    const ClassWork& w = work[c];
+    std::vector<ClassTune> trial(work.size());
+    const Launcher L{db, dt, th, mv, centers, charges, out, &trial};
+    float best = 1e30f;
+    int best_nch = 32;
+    for (int nch : {16, 32}) {
+      trial[c].nch = nch;
+      L.coupling(work, c, rbases[c], stream);  // warm
+      const float ms = time_it([&] { L.coupling(work, c, rbases[c], stream); });
+      if (ms < best) {
+        best = ms;
+        best_nch = nch;
+      }
+    }
+    trial[c].nch = best_nch;
+    L.coupling(work, c, rbases[c], stream);  // the kept shape leaves its coupling block in place
+    (*tune)[c].nch = best_nch;
+    best = 1e30f;
+    int best_thr = pair_threads(w.la, w.lb);
+    for (int thr : {32, 64, 128}) {
+      trial[c].threads = thr;
+      L.pair(work, c, rbases[c], stream);  // warm
+      const float ms = time_it([&] { L.pair(work, c, rbases[c], stream); });
+      if (ms < best) {
+        best = ms;
+        best_thr = thr;
+      }
+    }
+    (*tune)[c].threads = best_thr;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return launch_error(err);
 }
 
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf) {

@@ -61,6 +61,17 @@ def _load() -> ctypes.CDLL:
                                                     ctypes.POINTER(shgo_centers), ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p]
     lib.shgo_nuclear_attraction_noalloc.restype = ctypes.c_int
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.shgo_batch_create.argtypes = [ctypes.c_int32, i32p, i64p, ctypes.c_int32, i32p, i32p, f64p, f64p, f64p,
+                                      ctypes.POINTER(shgo_options), ctypes.POINTER(ctypes.c_void_p)]
+    lib.shgo_batch_create.restype = ctypes.c_int
+    lib.shgo_batch_layout.argtypes = [ctypes.c_void_p, i64p, i64p]
+    lib.shgo_batch_layout.restype = ctypes.c_int
+    lib.shgo_batch_out_size.argtypes = [ctypes.c_void_p]
+    lib.shgo_batch_out_size.restype = ctypes.c_int64
+    lib.shgo_nuclear_attraction_batched.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_nuclear_attraction_batched.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -239,3 +250,67 @@ def host_boys(nmax: int, T: float) -> np.ndarray:
     F = np.zeros(nmax + 1)
     _check(_lib.shgo_host_boys(int(nmax), float(T), _ptr(F, ctypes.c_double)))
     return F
+
+
+# ------------------------------------------------------------------ batches of molecules
+class Batch:
+    """Owns a batch handle (shgo_batch_create) over a list of (basis dict, n_nuclei)."""
+
+    def __init__(self, molecules, precision: int = SHGO_PREC_FP64, device: int = -1):
+        mol_nshells = np.array([len(b["l"]) for b, _ in molecules], dtype=np.int32)
+        mol_ncent = np.array([int(n) for _, n in molecules], dtype=np.int64)
+        l = np.ascontiguousarray(np.concatenate([b["l"] for b, _ in molecules]), dtype=np.int32)
+        nprim = np.ascontiguousarray(np.concatenate([b["nprim"] for b, _ in molecules]), dtype=np.int32)
+        exps = np.ascontiguousarray(np.concatenate([b["exps"] for b, _ in molecules]), dtype=np.float64)
+        coefs = np.ascontiguousarray(np.concatenate([b["coefs"] for b, _ in molecules]), dtype=np.float64)
+        xyz = np.ascontiguousarray(np.concatenate([b["xyz"] for b, _ in molecules]), dtype=np.float64).reshape(-1)
+        opt = shgo_options(int(precision), int(device))
+        handle = ctypes.c_void_p()
+        _check(_lib.shgo_batch_create(len(molecules), _ptr(mol_nshells, ctypes.c_int32), _ptr(mol_ncent, ctypes.c_int64),
+                                      len(l), _ptr(l, ctypes.c_int32), _ptr(nprim, ctypes.c_int32),
+                                      _ptr(exps, ctypes.c_double), _ptr(coefs, ctypes.c_double),
+                                      _ptr(xyz, ctypes.c_double), ctypes.byref(opt), ctypes.byref(handle)))
+        self.handle = handle.value
+        self.n_mol = len(molecules)
+        self.mol_nbf = np.zeros(self.n_mol, dtype=np.int64)
+        self.mol_off = np.zeros(self.n_mol, dtype=np.int64)
+        _check(_lib.shgo_batch_layout(ctypes.c_void_p(self.handle), _ptr(self.mol_nbf, ctypes.c_int64),
+                                      _ptr(self.mol_off, ctypes.c_int64)))
+        self.out_size = int(_lib.shgo_batch_out_size(ctypes.c_void_p(self.handle)))
+        self.n_centers = int(mol_ncent.sum())
+
+    def block(self, out, m):
+        """V of molecule m as an (nbf_m, nbf_m) view of the batched output."""
+        n = int(self.mol_nbf[m])
+        o = int(self.mol_off[m])
+        return out[o:o + n * n].reshape(n, n)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            shgo_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def shgo_nuclear_attraction_batched(batch, centers_ptr, charges_ptr, out_ptr, stream=None):
+    _check(_lib.shgo_nuclear_attraction_batched(ctypes.c_void_p(batch), ctypes.c_void_p(int(centers_ptr) or 0),
+                                                ctypes.c_void_p(int(charges_ptr) or 0),
+                                                ctypes.c_void_p(int(out_ptr) or 0), _stream_handle(stream)))
+
+
+def nuclear_attraction_batched(batch: Batch, centers, charges, out=None, stream=None):
+    """All molecules' V blocks, concatenated (see Batch.block).  centers [sum n, 3], charges [sum n]
+    are CUDA float64 tensors in molecule order."""
+    import torch
+    centers = centers.contiguous()
+    charges = charges.contiguous()
+    if out is None:
+        out = torch.empty(max(batch.out_size, 1), dtype=torch.float64, device=centers.device)
+    shgo_nuclear_attraction_batched(batch.handle, centers.data_ptr() if centers.numel() else 0,
+                                    charges.data_ptr() if charges.numel() else 0, out.data_ptr(), stream)
+    return out
