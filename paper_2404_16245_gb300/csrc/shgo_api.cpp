@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -55,6 +56,7 @@ struct shgo_basis {
   int64_t *mol_c0_d = nullptr, *mol_nc_d = nullptr, *mol_out_d = nullptr, *mol_ld_d = nullptr;
   std::vector<ClassTune> tune;
   bool tuned = false;
+  std::vector<int64_t> h_ppoff;  // per pair first primitive pair, plus the total
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[3] = {nullptr, nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
@@ -259,8 +261,21 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   b->npairs = (int64_t)pa.size();
   std::vector<double> prot(9 * pa.size());
   for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
-  int64_t rlen = 0;
+  int64_t rlen = 0, max_pair_r = 0;
   for (const auto& w : b->work) rlen += w.npp * n_r(w.la + w.lb);
+  b->h_ppoff.assign(ppoff.begin(), ppoff.end());
+  b->h_ppoff.push_back(ppcount);
+  for (const auto& w : b->work)
+    for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q)
+      max_pair_r = std::max(max_pair_r, (b->h_ppoff[q + 1] - b->h_ppoff[q]) * (int64_t)n_r(w.la + w.lb));
+  int64_t cap = kRbufCapDoubles;
+  if (const char* env = std::getenv("SHGO_RBUF_CAP_DOUBLES")) cap = std::max<int64_t>(1, std::atoll(env));
+  if (rlen > cap) {
+    // bounded buffer: one region per pool stream, classes processed in chunks of shell pairs
+    b->d.region = std::max(cap / kPoolStreamsPublic, max_pair_r);
+    rlen = b->d.region * kPoolStreamsPublic;
+  }
+  b->d.h_ppoff = b->h_ppoff.data();
 
   std::vector<double> xyz(shell_xyz, shell_xyz + 3 * (size_t)n_shells);
   std::vector<int> lv(l, l + n_shells), npv(n_prim, n_prim + n_shells);

@@ -179,7 +179,16 @@ struct DeviceBasis {
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
   int precision = SHGO_PREC_FP64;  // a shgo_precision value
+  // Bounded coupling buffer: region > 0 means rbuf holds one region of `region` doubles per pool
+  // stream and each class runs in chunks of whole shell pairs that fit its stream's region;
+  // h_ppoff (host, npairs + 1) gives the primitive-pair offsets used to cut the chunks.
+  int64_t region = 0;
+  const int64_t* h_ppoff = nullptr;
 };
+
+// Coupling-buffer cap (doubles) above which a basis switches to per-stream regions (2 GiB).
+constexpr int64_t kRbufCapDoubles = (int64_t)1 << 28;
+constexpr int kPoolStreamsPublic = 8;
 
 // Frame of a shell pair: rows (e1, e2, n) of a rotation Q with Q n = z for n = (B - A)/|B - A|,
 // e1 perpendicular to n along the axis least aligned with it, e2 = n x e1 (det Q = +1).

@@ -37,6 +37,19 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 __device__ __forceinline__ int odd_pad(int n) { return n | 1; }
 
+// |B - A|^2 and K_AB = exp(-alpha beta/(alpha + beta) |B - A|^2) of Eq. 5, with every operation
+// rounded explicitly so that the coupling and pair kernels agree bit for bit on which primitive
+// pairs have K_AB == 0 (the coupling kernel skips those, the pair kernel never reads them).
+__device__ __forceinline__ double pair_ab2(const double* __restrict__ xyz, int a, int b) {
+  const double dx = __dsub_rn(xyz[3 * b], xyz[3 * a]);
+  const double dy = __dsub_rn(xyz[3 * b + 1], xyz[3 * a + 1]);
+  const double dz = __dsub_rn(xyz[3 * b + 2], xyz[3 * a + 2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+__device__ __forceinline__ double prim_kab(double ea, double eb, double ab2) {
+  return exp(-__dmul_rn(__ddiv_rn(__dmul_rn(ea, eb), __dadd_rn(ea, eb)), ab2));
+}
+
 // Shared-memory bytes of one warp of k_coupling_block.
 __host__ __device__ inline size_t coupling_smem_per_warp(int lam, int nch) {
   const int rs = (n_harm(lam) + n_beta(lam)) | 1;
@@ -78,7 +91,11 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
     const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
     const double ABx = shell_xyz[3 * b] - Ax, ABy = shell_xyz[3 * b + 1] - Ay, ABz = shell_xyz[3 * b + 2] - Az;
-    const double shift = eb * rp * sqrt(ABx * ABx + ABy * ABy + ABz * ABz);  // |P - A|, along z in the pair frame
+    const double ab2 = pair_ab2(shell_xyz, a, b);
+    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
+    // skips such primitive pairs, so their coupling block is not needed
+    if (prim_kab(ea, eb, ab2) == 0.0) continue;
+    const double shift = eb * rp * sqrt(ab2);  // |P - A|, along z in the pair frame
     // frame of the pair: Q (b - a) is along z, so the translation of Eq. 7 is diagonal in m
     double Q[9];
 #pragma unroll
@@ -211,7 +228,11 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
     const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
     const double ABx = shell_xyz[3 * b] - Ax, ABy = shell_xyz[3 * b + 1] - Ay, ABz = shell_xyz[3 * b + 2] - Az;
-    const double shift = eb * rp * sqrt(ABx * ABx + ABy * ABy + ABz * ABz);  // |P - A|, along z in the pair frame
+    const double ab2 = pair_ab2(shell_xyz, a, b);
+    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
+    // skips such primitive pairs, so their coupling block is not needed
+    if (prim_kab(ea, eb, ab2) == 0.0) continue;
+    const double shift = eb * rp * sqrt(ab2);  // |P - A|, along z in the pair frame
     const double sp = sqrt(p);
     double Q[9];
 #pragma unroll
@@ -383,6 +404,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
     const double ABx = shell_xyz[3 * b] - shell_xyz[3 * a], ABy = shell_xyz[3 * b + 1] - shell_xyz[3 * a + 1],
                  ABz = shell_xyz[3 * b + 2] - shell_xyz[3 * a + 2];
     const double ab2 = ABx * ABx + ABy * ABy + ABz * ABz;
+    const double ab2_exact = pair_ab2(shell_xyz, a, b);
     const double dist = sqrt(ab2);
     __syncthreads();
     if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
@@ -454,8 +476,9 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       const int i = ij / npb, j = ij % npb;
       const double ea = prim_exp[shell_poff[a] + i], eb = prim_exp[shell_poff[b] + j];
       const double p = ea + eb, rp = 1.0 / p;
-      const double pref = prim_coef[shell_poff[a] + i] * prim_coef[shell_poff[b] + j] * exp(-ea * eb * rp * ab2);
-      if (pref == 0.0) continue;  // uniform over the block
+      const double kab = prim_kab(ea, eb, ab2_exact);
+      if (kab == 0.0) continue;  // uniform over the block; the coupling kernel skipped this pair too
+      const double pref = prim_coef[shell_poff[a] + i] * prim_coef[shell_poff[b] + j] * kab;
       __syncthreads();            // the previous primitive pair is done with Rs and fab
       const double* R = rbuf + rbase + (q0 + ij - pp_base) * (int64_t)nR;
       for (int e = tid; e < nR; e += nth) Rs[e] = R[e];
@@ -686,8 +709,7 @@ struct Launcher {
     return pair_threads(la, lb);
   }
 
-  void coupling(const std::vector<ClassWork>& work, size_t c, int64_t rbase, cudaStream_t s) const {
-    const ClassWork& w = work[c];
+  void coupling(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
     if (w.npp == 0) return;
     const int lam = w.la + w.lb;
     const int nch = nch_of(c, lam);
@@ -720,8 +742,7 @@ struct Launcher {
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
           db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
   }
-  void pair(const std::vector<ClassWork>& work, size_t c, int64_t rbase, cudaStream_t s) const {
-    const ClassWork& w = work[c];
+  void pair(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
     if (w.npairs == 0) return;
     const int cid = class_id(w.la, w.lb);
     const size_t sm = pair_smem(w.la, w.lb);
@@ -733,8 +754,30 @@ struct Launcher {
   }
 };
 
+// Pieces of a class whose coupling blocks fit `region` doubles, cut between shell pairs.
+std::vector<ClassWork> class_chunks(const ClassWork& w, const int64_t* ppoff, int64_t region) {
+  std::vector<ClassWork> out;
+  const int64_t nR = n_r(w.la + w.lb);
+  int q = w.pair_base;
+  const int qend = w.pair_base + w.npairs;
+  while (q < qend) {
+    ClassWork ch{w.la, w.lb, 0, q, 0, ppoff[q]};
+    int64_t used = 0;
+    while (q < qend && (ch.npairs == 0 || used + (ppoff[q + 1] - ppoff[q]) * nR <= region)) {
+      used += (ppoff[q + 1] - ppoff[q]) * nR;
+      ++ch.npairs;
+      ++q;
+    }
+    ch.npp = ppoff[q] - ch.pp_base;
+    out.push_back(ch);
+  }
+  return out;
+}
+
 // Fork the work of `order` over the pool streams after the work already queued on `stream`, and
 // make `stream` wait for all of it.  phase: 0 = coupling only, 1 = pair blocks only, 2 = both.
+// With a bounded coupling buffer (db.region > 0) stream i uses region i and runs each of its
+// classes chunk by chunk (both kernels per chunk; phase must be 2).
 cudaError_t run_concurrent(const Launcher& L, const std::vector<ClassWork>& work, const std::vector<int64_t>& rbases,
                            const std::vector<int>& order, int phase, cudaStream_t stream) {
   cudaStream_t* pool = nullptr;
@@ -750,8 +793,16 @@ cudaError_t run_concurrent(const Launcher& L, const std::vector<ClassWork>& work
   for (size_t k = 0; k < order.size(); ++k) {
     const int c = order[k];
     cudaStream_t s = pool[k % ns];
-    if (phase != 1) L.coupling(work, c, rbases[c], s);
-    if (phase != 0) L.pair(work, c, rbases[c], s);
+    if (L.db.region > 0) {
+      const int64_t rb = (int64_t)(k % ns) * L.db.region;
+      for (const ClassWork& ch : class_chunks(work[c], L.db.h_ppoff, L.db.region)) {
+        L.coupling(ch, c, rb, s);
+        L.pair(ch, c, rb, s);
+      }
+      continue;
+    }
+    if (phase != 1) L.coupling(work[c], c, rbases[c], s);
+    if (phase != 0) L.pair(work[c], c, rbases[c], s);
   }
   for (int i = 0; i < ns; ++i) {
     cudaEvent_t join;
@@ -828,10 +879,14 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
   mv.nbf = nbf;
   const Launcher L{db, dt, th, mv, centers, charges, out, nullptr};
   cudaError_t e = cudaSuccess;
+  if (events && db.region > 0) {
+    *err = "phase timing needs the whole coupling buffer; this basis uses bounded regions";
+    return SHGO_ERR_INVALID_ARG;
+  }
   if (!concurrent) {
-    for (size_t c = 0; c < work.size(); ++c) L.coupling(work, c, rbases[c], stream);
+    for (size_t c = 0; c < work.size(); ++c) L.coupling(work[c], c, rbases[c], stream);
     if (events) cudaEventRecord(events[1], stream);
-    for (size_t c = 0; c < work.size(); ++c) L.pair(work, c, rbases[c], stream);
+    for (size_t c = 0; c < work.size(); ++c) L.pair(work[c], c, rbases[c], stream);
   } else {
     const std::vector<int> order = class_order(work, (double)ncenters);
     if (events) {
@@ -889,34 +944,43 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
   };
   for (size_t c = 0; c < work.size(); ++c) {
     const ClassWork& w = work[c];
+    const std::vector<ClassWork> chunks =
+        db.region > 0 ? class_chunks(w, db.h_ppoff, db.region) : std::vector<ClassWork>{w};
+    const int64_t rb = db.region > 0 ? 0 : rbases[c];
+    const ClassWork& first = chunks[0];
     std::vector<ClassTune> trial(work.size());
     const Launcher L{db, dt, th, mv, centers, charges, out, &trial};
     float best = 1e30f;
     int best_nch = 32;
     for (int nch : {16, 32}) {
       trial[c].nch = nch;
-      L.coupling(work, c, rbases[c], stream);  // warm
-      const float ms = time_it([&] { L.coupling(work, c, rbases[c], stream); });
+      L.coupling(first, c, rb, stream);  // warm
+      const float ms = time_it([&] { L.coupling(first, c, rb, stream); });
       if (ms < best) {
         best = ms;
         best_nch = nch;
       }
     }
     trial[c].nch = best_nch;
-    L.coupling(work, c, rbases[c], stream);  // the kept shape leaves its coupling block in place
+    L.coupling(first, c, rb, stream);  // the kept shape leaves its coupling block in place
     (*tune)[c].nch = best_nch;
     best = 1e30f;
     int best_thr = pair_threads(w.la, w.lb);
     for (int thr : {32, 64, 128}) {
       trial[c].threads = thr;
-      L.pair(work, c, rbases[c], stream);  // warm
-      const float ms = time_it([&] { L.pair(work, c, rbases[c], stream); });
+      L.pair(first, c, rb, stream);  // warm
+      const float ms = time_it([&] { L.pair(first, c, rb, stream); });
       if (ms < best) {
         best = ms;
         best_thr = thr;
       }
     }
     (*tune)[c].threads = best_thr;
+    trial[c].threads = best_thr;
+    for (size_t k = 0; k < chunks.size(); ++k) {  // the whole class with the kept shapes
+      if (k > 0) L.coupling(chunks[k], c, rb, stream);
+      L.pair(chunks[k], c, rb, stream);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -93,3 +93,28 @@ def test_batched_molecule_without_nuclei_and_mixed_sizes():
         b, Cm, Zm = mols[m]
         parity.check(batch.block(o, m), oracle.nuclear_attraction(b, Cm, Zm, precision="ld"), what=f"mol {m}")
     batch.close()
+
+
+def test_bounded_coupling_buffer_chunks_match(monkeypatch):
+    # a tiny cap forces per-stream regions and many chunks per class; results must not change
+    from paper_2404_16245_gb300 import shgo
+    basis, C, Z = W.config2(n_atoms=10)
+    Cd = torch.tensor(C, device="cuda")
+    Zd = torch.tensor(Z, device="cuda")
+    B = shgo.Basis(basis)
+    ref = shgo.nuclear_attraction(B, Cd, Zd).cpu().numpy()
+    B.close()
+    monkeypatch.setenv("SHGO_RBUF_CAP_DOUBLES", "20000")
+    B2 = shgo.Basis(basis)
+    got = shgo.nuclear_attraction(B2, Cd, Zd).cpu().numpy()
+    B2.close()
+    assert np.array_equal(got, ref)
+    mols = small_molecules(21, 5)
+    batch = shgo.Batch([(b, len(Zm)) for b, _, Zm in mols])
+    Cb = torch.tensor(np.concatenate([c for _, c, _ in mols]), device="cuda")
+    Zb = torch.tensor(np.concatenate([z for _, _, z in mols]), device="cuda")
+    outs = [shgo.nuclear_attraction_batched(batch, Cb, Zb).cpu().numpy() for _ in range(3)]
+    for m, (b, Cm, Zm) in enumerate(mols):
+        parity.check(batch.block(outs[-1], m), oracle.nuclear_attraction(b, Cm, Zm, precision="ld"), what=f"m{m}")
+    assert np.array_equal(outs[1], outs[2])
+    batch.close()
