@@ -11,6 +11,7 @@
 
 #include "shgo_internal.h"
 #include "shgo_math.h"
+#include "../../include/shgo_mlp.h"
 
 using namespace shgo;
 
@@ -57,6 +58,14 @@ struct shgo_basis {
   std::vector<ClassTune> tune;
   bool tuned = false;
   std::vector<int64_t> h_ppoff;  // per pair first primitive pair, plus the total
+  std::vector<int> h_pair_a, h_pair_b, h_pair_mol;
+  // screening state (shgo_screen_build)
+  uint8_t* scr_mask = nullptr;
+  int64_t* scr_mask_off = nullptr;
+  int64_t* scr_counts = nullptr;
+  int64_t* scr_clist_off = nullptr;
+  int* scr_clist = nullptr;
+  int64_t scr_ntrip = 0, scr_ncenters = -1;
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[3] = {nullptr, nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
@@ -89,6 +98,11 @@ void release(shgo_basis* b) {
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->scr_mask);
+  cudaFree(b->scr_mask_off);
+  cudaFree(b->scr_counts);
+  cudaFree(b->scr_clist_off);
+  cudaFree(b->scr_clist);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   for (void* p : b->allocations) cudaFree(p);
   cudaSetDevice(prev);
@@ -259,6 +273,9 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
       }
     }
   b->npairs = (int64_t)pa.size();
+  b->h_pair_a = pa;
+  b->h_pair_b = pb;
+  b->h_pair_mol = pmol;
   std::vector<double> prot(9 * pa.size());
   for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
   int64_t rlen = 0, max_pair_r = 0;
@@ -550,6 +567,136 @@ shgo_status shgo_host_boys(int32_t nmax, double T, double* F) {
   if (nmax < 0 || nmax > kLamMax + 1 || !F || !(T >= 0) || !std::isfinite(T))
     return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
   boys_host(nmax, T, F);
+  return SHGO_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Learned screening (include/shgo_mlp.h)
+// ---------------------------------------------------------------------------------------------
+static ScreenBasis screen_view(const shgo_basis* b, int64_t n_centers) {
+  ScreenBasis sb;
+  sb.shell_xyz = b->d.shell_xyz;
+  sb.shell_l = b->d.shell_l;
+  sb.shell_nprim = b->d.shell_nprim;
+  sb.shell_poff = b->d.shell_poff;
+  sb.prim_exp = b->d.prim_exp;
+  sb.prim_coef = b->d.prim_coef;
+  sb.pair_a = b->d.pair_a;
+  sb.pair_b = b->d.pair_b;
+  sb.pair_mol = b->batch ? b->pair_mol : nullptr;
+  sb.mol_c0 = b->batch ? b->mol_c0_d : nullptr;
+  sb.mol_nc = b->batch ? b->mol_nc_d : nullptr;
+  sb.ncenters = n_centers;
+  sb.mask_off = b->scr_mask_off;
+  sb.clist_off = b->scr_clist_off;
+  return sb;
+}
+
+shgo_status shgo_pair_shells(const shgo_basis* basis, int32_t* shell_a, int32_t* shell_b) {
+  if (!basis || !shell_a || !shell_b) return fail(SHGO_ERR_INVALID_ARG, "NULL argument");
+  for (int64_t q = 0; q < basis->npairs; ++q) {
+    shell_a[q] = basis->h_pair_a[q];
+    shell_b[q] = basis->h_pair_b[q];
+  }
+  return SHGO_OK;
+}
+
+shgo_status shgo_screen_features(const shgo_basis* basis, const double* centers, const double* charges,
+                                 const int32_t* triples, int64_t n, float* X, void* stream) {
+  if (!basis || n < 0 || (n > 0 && (!centers || !charges || !triples || !X)))
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  return launch_screen_features(screen_view(basis, 0), centers, charges, triples, n, X, (cudaStream_t)stream);
+}
+
+shgo_status shgo_screen_build(shgo_basis* basis, const shgo_mlp* mlp, const double* centers, const double* charges,
+                              int64_t n_centers, double log10_threshold, double log10_margin, int64_t* kept,
+                              int64_t* skipped) {
+  g_last_error.clear();
+  if (!basis || !mlp) return fail(SHGO_ERR_INVALID_ARG, "NULL basis or network");
+  const int64_t nc_total = basis->batch ? basis->total_centers : n_centers;
+  if (nc_total < 0 || (nc_total > 0 && (!centers || !charges))) return fail(SHGO_ERR_INVALID_ARG, "bad nuclei");
+  cudaFree(basis->scr_mask);
+  cudaFree(basis->scr_mask_off);
+  cudaFree(basis->scr_counts);
+  cudaFree(basis->scr_clist_off);
+  cudaFree(basis->scr_clist);
+  basis->scr_mask = nullptr;
+  basis->scr_mask_off = basis->scr_counts = basis->scr_clist_off = nullptr;
+  basis->scr_clist = nullptr;
+  const int64_t np = basis->npairs;
+  std::vector<int64_t> moff(np + 1, 0);
+  for (int64_t q = 0; q < np; ++q)
+    moff[q + 1] = moff[q] + (basis->batch ? basis->mol_nc[basis->h_pair_mol[q]] : n_centers);
+  const int64_t ntrip = moff[np];
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc((void**)&basis->scr_mask_off, sizeof(int64_t) * (np + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&basis->scr_counts, sizeof(int64_t) * (np + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&basis->scr_clist_off, sizeof(int64_t) * (np + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&basis->scr_mask, ntrip > 0 ? ntrip : 1);
+  if (e == cudaSuccess) e = cudaMemcpy(basis->scr_mask_off, moff.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA, cudaGetErrorString(e));
+  const float cut = (float)(log10_threshold - log10_margin);
+  ScreenBasis sb = screen_view(basis, n_centers);
+  shgo_status st = launch_screen_pairs(sb, np, centers, charges, mlp, cut, 0, basis->scr_mask, basis->scr_counts,
+                                       nullptr, 0);
+  if (st != SHGO_OK) return st;
+  std::vector<int64_t> counts(np), coff(np + 1, 0);
+  if (np > 0 && cudaMemcpy(counts.data(), basis->scr_counts, sizeof(int64_t) * np, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(SHGO_ERR_CUDA, "screen counts copy failed");
+  for (int64_t q = 0; q < np; ++q) coff[q + 1] = coff[q] + counts[q];
+  e = cudaMemcpy(basis->scr_clist_off, coff.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&basis->scr_clist, sizeof(int) * (coff[np] > 0 ? coff[np] : 1));
+  if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA, cudaGetErrorString(e));
+  sb.clist_off = basis->scr_clist_off;
+  st = launch_screen_pairs(sb, np, centers, charges, mlp, cut, 1, basis->scr_mask, basis->scr_counts,
+                           basis->scr_clist, 0);
+  if (st != SHGO_OK) return st;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(SHGO_ERR_CUDA, cudaGetErrorString(e));
+  basis->scr_ntrip = ntrip;
+  basis->scr_ncenters = n_centers;
+  if (kept) *kept = coff[np];
+  if (skipped) *skipped = ntrip - coff[np];
+  return SHGO_OK;
+}
+
+shgo_status shgo_screen_mask(const shgo_basis* basis, uint8_t* mask) {
+  if (!basis || !mask || !basis->scr_mask) return fail(SHGO_ERR_INVALID_ARG, "no screening built");
+  if (basis->scr_ntrip > 0 &&
+      cudaMemcpy(mask, basis->scr_mask, (size_t)basis->scr_ntrip, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(SHGO_ERR_CUDA, "mask copy failed");
+  return SHGO_OK;
+}
+
+shgo_status shgo_nuclear_attraction_screened(shgo_basis* basis, const double* centers, const double* charges,
+                                             int64_t n_centers, double* out, void* stream) {
+  g_last_error.clear();
+  if (!basis || !basis->scr_clist) return fail(SHGO_ERR_INVALID_ARG, "no screening built for this basis");
+  if (!basis->batch && n_centers != basis->scr_ncenters)
+    return fail(SHGO_ERR_INVALID_ARG, "nucleus count differs from the screening build");
+  if (!out && (basis->batch ? basis->out_size : basis->nbf) > 0) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  MolView mv;
+  if (basis->batch) {
+    mv.pair_mol = basis->pair_mol;
+    mv.c0 = basis->mol_c0_d;
+    mv.nc = basis->mol_nc_d;
+    mv.out_off = basis->mol_out_d;
+    mv.ld = basis->mol_ld_d;
+  }
+  mv.ncenters = basis->batch ? basis->total_centers : n_centers;
+  mv.nbf = basis->nbf;
+  mv.clist = basis->scr_clist;
+  mv.clist_off = basis->scr_clist_off;
+  const double per_pair = basis->npairs > 0 ? (double)basis->scr_ntrip / (double)basis->npairs : 0.0;
+  std::string err;
+  const shgo_status st = launch_batched(basis->d, *basis->tabs, basis->work, mv, per_pair, centers, charges, out,
+                                        basis->tuned ? &basis->tune : nullptr, (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;
 }
 

@@ -125,10 +125,16 @@ struct MolView {
   const int64_t* ld = nullptr;
   int64_t ncenters = 0;
   int64_t nbf = 0;
+  // Screening: when set, the nuclei of pair pr are centers[clist[clist_off[pr] .. clist_off[pr + 1])]
+  const int* clist = nullptr;
+  const int64_t* clist_off = nullptr;
 };
 
 __device__ __forceinline__ void mol_centers(const MolView& mv, int pr, int64_t& c_begin, int64_t& n) {
-  if (mv.pair_mol) {
+  if (mv.clist) {
+    c_begin = mv.clist_off[pr];
+    n = mv.clist_off[pr + 1] - c_begin;
+  } else if (mv.pair_mol) {
     const int m = mv.pair_mol[pr];
     c_begin = mv.c0[m];
     n = mv.nc[m];
@@ -137,6 +143,9 @@ __device__ __forceinline__ void mol_centers(const MolView& mv, int pr, int64_t& 
     n = mv.ncenters;
   }
 }
+
+// Index into centers/charges of the k-th nucleus slot returned by mol_centers.
+__device__ __forceinline__ int64_t mol_center_index(const MolView& mv, int64_t k) { return mv.clist ? mv.clist[k] : k; }
 
 __device__ __forceinline__ void mol_output(const MolView& mv, int pr, int64_t& base, int64_t& ld) {
   if (mv.pair_mol) {
@@ -240,4 +249,33 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
                              const MolView& mv, const double* centers, const double* charges, double* out,
                              std::vector<ClassTune>* tune, cudaStream_t stream, std::string* err);
 
+struct ScreenBasis;
+shgo_status launch_screen_features(const ScreenBasis& sb, const double* centers, const double* charges,
+                                   const int* triples, int64_t n, float* X, cudaStream_t s);
+
+// Device view of a basis for the screening kernels.
+struct ScreenBasis {
+  const double* shell_xyz = nullptr;
+  const int* shell_l = nullptr;
+  const int* shell_nprim = nullptr;
+  const int* shell_poff = nullptr;
+  const double* prim_exp = nullptr;
+  const double* prim_coef = nullptr;
+  const int* pair_a = nullptr;
+  const int* pair_b = nullptr;
+  const int* pair_mol = nullptr;       // batch: molecule of each pair
+  const int64_t* mol_c0 = nullptr;
+  const int64_t* mol_nc = nullptr;
+  int64_t ncenters = 0;                // one molecule: nuclei of the call
+  const int64_t* mask_off = nullptr;   // per pair, first triple of the pair in the mask
+  const int64_t* clist_off = nullptr;  // per pair (+1), first kept nucleus in the list
+};
+
+}  // namespace shgo
+
+struct shgo_mlp;
+namespace shgo {
+shgo_status launch_screen_pairs(const ScreenBasis& sb, int64_t npairs, const double* centers, const double* charges,
+                                const shgo_mlp* mlp, float cut, int pass, uint8_t* mask, int64_t* counts,
+                                int* clist, cudaStream_t s);
 }  // namespace shgo

@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
     // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
     const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double ABx = shell_xyz[3 * b] - Ax, ABy = shell_xyz[3 * b + 1] - Ay, ABz = shell_xyz[3 * b + 2] - Az;
     const double ab2 = pair_ab2(shell_xyz, a, b);
     // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
     // skips such primitive pairs, so their coupling block is not needed
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
       __syncwarp();
       if (lane < NCH) {
         double* row = rows + (size_t)lane * rs;
-        const int64_t c = cbeg + c0 + lane;
+        const int64_t c = mol_center_index(mv, cbeg + c0 + lane);
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
         if (c0 + lane < ncen) {
           const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;
@@ -227,7 +226,6 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
     // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
     const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double ABx = shell_xyz[3 * b] - Ax, ABy = shell_xyz[3 * b + 1] - Ay, ABz = shell_xyz[3 * b + 2] - Az;
     const double ab2 = pair_ab2(shell_xyz, a, b);
     // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
     // skips such primitive pairs, so their coupling block is not needed
@@ -245,7 +243,7 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
       if (lane < NCH) {
         float* row = rows + (size_t)lane * rs;
         double* F = fscr + (size_t)lane * (lam + 2);
-        const int64_t c = cbeg + c0 + lane;
+        const int64_t c = mol_center_index(mv, cbeg + c0 + lane);
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
         if (c0 + lane < ncen) {
           const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;

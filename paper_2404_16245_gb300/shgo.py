@@ -314,3 +314,171 @@ def nuclear_attraction_batched(batch: Batch, centers, charges, out=None, stream=
     shgo_nuclear_attraction_batched(batch.handle, centers.data_ptr() if centers.numel() else 0,
                                     charges.data_ptr() if charges.numel() else 0, out.data_ptr(), stream)
     return out
+
+
+# ------------------------------------------------------------------ learned screening (shgo_mlp.h)
+MLP_IN, MLP_HIDDEN = 16, 64
+MLP_NPARAM = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def _bind_mlp():
+    f32p = ctypes.POINTER(ctypes.c_float)
+    vp = ctypes.c_void_p
+    L = _lib
+    L.shgo_mlp_create.argtypes = [f32p, f32p, f32p, ctypes.POINTER(vp)]
+    L.shgo_mlp_create.restype = ctypes.c_int
+    L.shgo_mlp_free.argtypes = [vp]
+    L.shgo_mlp_free.restype = None
+    L.shgo_mlp_get_params.argtypes = [vp, f32p]
+    L.shgo_mlp_get_params.restype = ctypes.c_int
+    L.shgo_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    L.shgo_mlp_forward.restype = ctypes.c_int
+    L.shgo_mlp_gradients.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, f32p, f32p]
+    L.shgo_mlp_gradients.restype = ctypes.c_int
+    L.shgo_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float, f32p, vp]
+    L.shgo_mlp_train_step.restype = ctypes.c_int
+    L.shgo_screen_features.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp, vp]
+    L.shgo_screen_features.restype = ctypes.c_int
+    L.shgo_pair_shells.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.shgo_pair_shells.restype = ctypes.c_int
+    L.shgo_screen_build.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.shgo_screen_build.restype = ctypes.c_int
+    L.shgo_screen_mask.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
+    L.shgo_screen_mask.restype = ctypes.c_int
+    L.shgo_nuclear_attraction_screened.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    L.shgo_nuclear_attraction_screened.restype = ctypes.c_int
+
+
+_bind_mlp()
+
+
+class MLP:
+    """The screening network on the current device (FP32 master weights, BF16 forward)."""
+
+    def __init__(self, params, feature_mean, feature_sd):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        mu = np.ascontiguousarray(feature_mean, dtype=np.float32)
+        sd = np.ascontiguousarray(feature_sd, dtype=np.float32)
+        assert p.size == MLP_NPARAM and mu.size == MLP_IN and sd.size == MLP_IN
+        h = ctypes.c_void_p()
+        _check(_lib.shgo_mlp_create(_ptr(p, ctypes.c_float), _ptr(mu, ctypes.c_float), _ptr(sd, ctypes.c_float),
+                                    ctypes.byref(h)))
+        self.handle = h.value
+        self.mean = mu
+        self.sd = sd
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(_lib.shgo_mlp_get_params(ctypes.c_void_p(self.handle), _ptr(p, ctypes.c_float)))
+        return p
+
+    def forward(self, X, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(_lib.shgo_mlp_forward(ctypes.c_void_p(self.handle), ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                     ctypes.c_void_p(y.data_ptr()), _stream_handle(stream)))
+        return y
+
+    def gradients(self, X, T, under_weight=1.0):
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.shgo_mlp_gradients(ctypes.c_void_p(self.handle), ctypes.c_void_p(X.data_ptr()),
+                                       ctypes.c_void_p(T.data_ptr()), X.shape[0], float(under_weight),
+                                       _ptr(g, ctypes.c_float), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train_step(self, X, T, under_weight, lr, want_loss=False, stream=None):
+        loss = ctypes.c_float()
+        _check(_lib.shgo_mlp_train_step(ctypes.c_void_p(self.handle), ctypes.c_void_p(X.data_ptr()),
+                                        ctypes.c_void_p(T.data_ptr()), X.shape[0], float(under_weight), float(lr),
+                                        ctypes.byref(loss) if want_loss else None, _stream_handle(stream)))
+        return float(loss.value) if want_loss else None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.shgo_mlp_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pair_shells(handle, npairs):
+    a = np.zeros(npairs, dtype=np.int32)
+    b = np.zeros(npairs, dtype=np.int32)
+    _check(_lib.shgo_pair_shells(ctypes.c_void_p(handle), _ptr(a, ctypes.c_int32), _ptr(b, ctypes.c_int32)))
+    return a, b
+
+
+def screen_features(handle, centers, charges, triples, stream=None):
+    """Features [n, 16] (float32, device) of triples [n, 2] (int32 device: pair index, nucleus index)."""
+    import torch
+    n = triples.shape[0]
+    X = torch.empty((n, MLP_IN), dtype=torch.float32, device=triples.device)
+    _check(_lib.shgo_screen_features(ctypes.c_void_p(handle), ctypes.c_void_p(centers.data_ptr()),
+                                     ctypes.c_void_p(charges.data_ptr()), ctypes.c_void_p(triples.data_ptr()), n,
+                                     ctypes.c_void_p(X.data_ptr()), _stream_handle(stream)))
+    return X
+
+
+def screen_build(handle, mlp: MLP, centers, charges, n_centers, log10_threshold, log10_margin):
+    kept = ctypes.c_int64()
+    skipped = ctypes.c_int64()
+    _check(_lib.shgo_screen_build(ctypes.c_void_p(handle), ctypes.c_void_p(mlp.handle),
+                                  ctypes.c_void_p(centers.data_ptr() if centers.numel() else 0),
+                                  ctypes.c_void_p(charges.data_ptr() if charges.numel() else 0), int(n_centers),
+                                  float(log10_threshold), float(log10_margin), ctypes.byref(kept),
+                                  ctypes.byref(skipped)))
+    return int(kept.value), int(skipped.value)
+
+
+def screen_mask(handle, n_triples) -> np.ndarray:
+    m = np.zeros(max(n_triples, 1), dtype=np.uint8)
+    _check(_lib.shgo_screen_mask(ctypes.c_void_p(handle), _ptr(m, ctypes.c_uint8)))
+    return m[:n_triples]
+
+
+def nuclear_attraction_screened(handle, centers, charges, n_centers, out, stream=None):
+    _check(_lib.shgo_nuclear_attraction_screened(ctypes.c_void_p(handle),
+                                                 ctypes.c_void_p(centers.data_ptr() if centers.numel() else 0),
+                                                 ctypes.c_void_p(charges.data_ptr() if charges.numel() else 0),
+                                                 int(n_centers), ctypes.c_void_p(out.data_ptr()),
+                                                 _stream_handle(stream)))
+    return out
+
+
+def _batch_from_arrays(cls, mols: dict, mol_ncenters, precision: int = SHGO_PREC_FP64, device: int = -1):
+    """A batch from concatenated arrays: mols["nshells"][m] shells per molecule and the shell
+    arrays l, nprim, exps, coefs, xyz of all molecules back to back."""
+    self = cls.__new__(cls)
+    mol_nshells = np.ascontiguousarray(mols["nshells"], dtype=np.int32)
+    mol_ncent = np.ascontiguousarray(mol_ncenters, dtype=np.int64)
+    l = np.ascontiguousarray(mols["l"], dtype=np.int32)
+    nprim = np.ascontiguousarray(mols["nprim"], dtype=np.int32)
+    exps = np.ascontiguousarray(mols["exps"], dtype=np.float64)
+    coefs = np.ascontiguousarray(mols["coefs"], dtype=np.float64)
+    xyz = np.ascontiguousarray(mols["xyz"], dtype=np.float64).reshape(-1)
+    opt = shgo_options(int(precision), int(device))
+    handle = ctypes.c_void_p()
+    _check(_lib.shgo_batch_create(len(mol_nshells), _ptr(mol_nshells, ctypes.c_int32),
+                                  _ptr(mol_ncent, ctypes.c_int64), len(l), _ptr(l, ctypes.c_int32),
+                                  _ptr(nprim, ctypes.c_int32), _ptr(exps, ctypes.c_double),
+                                  _ptr(coefs, ctypes.c_double), _ptr(xyz, ctypes.c_double), ctypes.byref(opt),
+                                  ctypes.byref(handle)))
+    self.handle = handle.value
+    self.n_mol = len(mol_nshells)
+    self.mol_nbf = np.zeros(self.n_mol, dtype=np.int64)
+    self.mol_off = np.zeros(self.n_mol, dtype=np.int64)
+    _check(_lib.shgo_batch_layout(ctypes.c_void_p(self.handle), _ptr(self.mol_nbf, ctypes.c_int64),
+                                  _ptr(self.mol_off, ctypes.c_int64)))
+    self.out_size = int(_lib.shgo_batch_out_size(ctypes.c_void_p(self.handle)))
+    self.n_centers = int(mol_ncent.sum())
+    return self
+
+
+Batch.from_arrays = classmethod(_batch_from_arrays)

@@ -1,0 +1,151 @@
+"""Screening network and learned screening on the GPU.
+
+The network's forward pass and gradients (the library's own kernels) are checked against the numpy
+reference in oracle/mlp.py; screening is checked through its limits (keep everything = the plain
+method bit for bit, skip everything = zero), the features against an independent restatement, and
+a trained network against the plain method on a small cluster with an exact audit."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from paper_2404_16245_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def shgo():
+    from paper_2404_16245_gb300 import shgo as mod
+    return mod
+
+
+def test_mlp_gradients_match_reference(shgo):
+    rng = np.random.default_rng(1)
+    n = 333
+    X = rng.normal(size=(n, 16)).astype(np.float32)
+    T = rng.normal(size=n).astype(np.float32)
+    mean = (rng.normal(size=16) * 0.1).astype(np.float32)
+    sd = rng.uniform(0.5, 2.0, 16).astype(np.float32)
+    p = ref.init_params(7)
+    net = shgo.MLP(p, mean, sd)
+    g, loss = net.gradients(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), under_weight=4.0)
+    rloss, rg = ref.loss_and_grad(p, X, T, mean.astype(np.float64), sd.astype(np.float64), under_weight=4.0)
+    assert loss == pytest.approx(rloss, rel=1e-4)
+    scale = np.max(np.abs(rg))
+    assert np.max(np.abs(g - rg)) <= 2e-4 * scale, np.max(np.abs(g - rg)) / scale
+    y = net.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    ry, _ = ref.forward(p, X, mean.astype(np.float64), sd.astype(np.float64))
+    assert np.max(np.abs(y - ry)) <= 1e-4 * (1 + np.max(np.abs(ry)))
+    net.close()
+
+
+def test_mlp_training_reduces_loss(shgo):
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(8192, 16)).astype(np.float32)
+    w = rng.normal(size=16)
+    T = (X @ w + 0.5 * np.sin(X[:, 0])).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    net = shgo.MLP(ref.init_params(0), np.zeros(16), np.ones(16))
+    _, l0 = net.gradients(Xd, Td)
+    for _ in range(300):
+        net.train_step(Xd, Td, 1.0, 3e-3)
+    _, l1 = net.gradients(Xd, Td)
+    assert l1 < 0.05 * l0, (l0, l1)
+    net.close()
+
+
+def cluster(seed, n_atoms):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    box = (n_atoms / 0.1) ** (1 / 3)
+    return W.molecule(rng, n_atoms, box, 1, 9, lambda Z: [0] * 4 + [1] * 3 + [2] * 2 + [3],
+                      lambda r: r.integers(1, 7), 0.05, 5000.0)
+
+
+def const_net(shgo, bias):
+    p = np.zeros(ref.NPARAM, dtype=np.float32)
+    p[-1] = bias
+    return shgo.MLP(p, np.zeros(16), np.ones(16))
+
+
+def test_keep_all_equals_plain_and_skip_all_is_zero(shgo):
+    basis, C, Z = cluster(41, 8)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    plain = shgo.nuclear_attraction(B, Cd, Zd).cpu().numpy()
+    keep = const_net(shgo, 100.0)
+    kept, skipped = shgo.screen_build(B.handle, keep, Cd, Zd, len(Z), -12.0, 2.0)
+    assert skipped == 0 and kept == B.npairs * len(Z)
+    out = torch.empty_like(torch.tensor(plain, device="cuda"))
+    shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out)
+    assert np.array_equal(out.cpu().numpy(), plain)
+    drop = const_net(shgo, -100.0)
+    kept, skipped = shgo.screen_build(B.handle, drop, Cd, Zd, len(Z), -12.0, 2.0)
+    assert kept == 0
+    shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out)
+    assert np.array_equal(out.cpu().numpy(), np.zeros_like(plain))
+    B.close()
+
+
+def test_features_match_definitions(shgo):
+    basis, C, Z = cluster(43, 6)
+    B = shgo.Basis(basis)
+    a, b = shgo.pair_shells(B.handle, B.npairs)
+    rng = np.random.default_rng(0)
+    tr = np.stack([rng.integers(0, B.npairs, 50), rng.integers(0, len(Z), 50)], axis=1).astype(np.int32)
+    X = shgo.screen_features(B.handle, torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda"),
+                             torch.tensor(tr, device="cuda")).cpu().numpy()
+    poff = np.concatenate([[0], np.cumsum(basis["nprim"])])
+    for t, (q, c) in enumerate(tr):
+        sa, sb = a[q], b[q]
+        ea = basis["exps"][poff[sa]:poff[sa + 1]]
+        eb = basis["exps"][poff[sb]:poff[sb + 1]]
+        A, Bc, Cc = basis["xyz"][sa], basis["xyz"][sb], C[c]
+        amin, bmin = ea.min(), eb.min()
+        P = (amin * A + bmin * Bc) / (amin + bmin)
+        assert X[t, 0] == basis["l"][sa] and X[t, 1] == basis["l"][sb]
+        assert X[t, 2] == pytest.approx(math.log10(amin), abs=1e-5)
+        assert X[t, 5] == pytest.approx(math.log10(eb.max()), abs=1e-5)
+        assert X[t, 6] == pytest.approx(np.linalg.norm(Bc - A), abs=1e-4)
+        assert X[t, 7] == pytest.approx(-amin * bmin / (amin + bmin) * np.sum((Bc - A) ** 2) / math.log(10), rel=1e-5,
+                                        abs=1e-4)
+        assert X[t, 8] == pytest.approx(np.linalg.norm(P - Cc), abs=1e-4)
+        assert X[t, 10] == pytest.approx(math.log10(Z[c]), abs=1e-6)
+        assert X[t, 13] == pytest.approx(np.linalg.norm(A - Cc), abs=1e-4)
+    B.close()
+
+
+def test_trained_screening_error_and_audit(shgo):
+    from paper_2404_16245_gb300 import screening as S
+    train_basis, Ct, Zt = cluster(44, 14)
+    Bt = shgo.Basis(train_basis)
+    a, b = shgo.pair_shells(Bt.handle, Bt.npairs)
+    rng = np.random.default_rng(5)
+    dist = np.linalg.norm(train_basis["xyz"][a] - train_basis["xyz"][b], axis=1)
+    tr = S.sample_triples(rng, Bt.npairs, len(Zt), 60000, pair_dist=dist)
+    T = S.plain_labels(train_basis, a, b, Ct, Zt, tr)
+    X = shgo.screen_features(Bt.handle, torch.tensor(Ct, device="cuda"), torch.tensor(Zt, device="cuda"),
+                             torch.tensor(tr, device="cuda"))
+    net, losses = S.train(X, torch.tensor(T, dtype=torch.float32, device="cuda"), epochs=8, batch=2048)
+    assert losses[-1] < losses[0]
+    Bt.close()
+    basis, C, Z = cluster(45, 12)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    plain = shgo.nuclear_attraction(B, Cd, Zd).cpu().numpy()
+    kept, skipped = shgo.screen_build(B.handle, net, Cd, Zd, len(Z), -12.0, 2.0)
+    out = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device="cuda")
+    shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out)
+    err = np.max(np.abs(out.cpu().numpy() - plain))
+    a, b = shgo.pair_shells(B.handle, B.npairs)
+    mask = shgo.screen_mask(B.handle, kept + skipped)
+    rep = S.audit(basis, a, b, C, Z, mask, np.full(B.npairs, len(Z)), 0.05, np.random.default_rng(1), 1e-12)
+    print(f"\nscreening: kept {kept} skipped {skipped}; max |V - V_plain| {err:.2e}; audit {rep}")
+    assert skipped > 0
+    assert err < 1e-10
+    assert rep["false_skip_rate"] < 0.01
+    B.close()
+    net.close()
