@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -356,6 +357,97 @@ def run_batched(args) -> int:
     return 0
 
 
+def _cluster(seed: int, n_atoms: int):
+    """Screening workload: atoms uniform at 0.1 atoms/bohr^3, Z ~ U{1..9}, 4s3p2d1f on every atom
+    with 1..6 primitives, exponents log-uniform [0.05, 5000]."""
+    from paper_2404_16245_gb300 import workloads as W
+    rng = np.random.Generator(np.random.PCG64(seed))
+    box = (n_atoms / 0.1) ** (1 / 3)
+    return W.molecule(rng, n_atoms, box, 1, 9, lambda Z: [0] * 4 + [1] * 3 + [2] * 2 + [3],
+                      lambda r: r.integers(1, 7), 0.05, 5000.0)
+
+
+def run_screened(args) -> int:
+    """Learned screening against the plain method on one cluster: network trained on the plain
+    method's blocks of another cluster; plain and screened V timed with CUDA events; the screened V
+    compared with the plain one element by element; 1% of the skipped triples audited exactly."""
+    import torch
+
+    from paper_2404_16245_gb300 import screening as S
+    from paper_2404_16245_gb300 import shgo
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    # training set from the plain method on a different cluster
+    t0 = time.perf_counter()
+    tb, tC, tZ = _cluster(4001, args.train_atoms)
+    Bt = shgo.Basis(tb)
+    a, b = shgo.pair_shells(Bt.handle, Bt.npairs)
+    rng = np.random.default_rng(4001)
+    dist = np.linalg.norm(tb["xyz"][a] - tb["xyz"][b], axis=1)
+    tr = S.sample_triples(rng, Bt.npairs, len(tZ), args.train_triples, pair_dist=dist)
+    T = S.plain_labels(tb, a, b, tC, tZ, tr)
+    X = shgo.screen_features(Bt.handle, torch.tensor(tC, device=dev), torch.tensor(tZ, device=dev),
+                             torch.tensor(tr, device=dev))
+    label_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    net, losses = S.train(X, torch.tensor(T, dtype=torch.float32, device=dev), epochs=args.epochs, batch=4096, log=log)
+    train_s = time.perf_counter() - t1
+    Bt.close()
+    # evaluation cluster
+    basis, C, Z = _cluster(4000, args.atoms)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device=dev), torch.tensor(Z, device=dev)
+    out_plain = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device=dev)
+    out_scr = torch.empty_like(out_plain)
+    flops, trip = shgo.shgo_basis_flops(B.handle, len(Z))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    shgo.nuclear_attraction(B, Cd, Zd, out=out_plain, stream=stream)  # warm
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        shgo.nuclear_attraction(B, Cd, Zd, out=out_plain, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    kept, skipped = shgo.screen_build(B.handle, net, Cd, Zd, len(Z), math.log10(args.threshold), math.log10(args.margin))
+    ev[3].record(stream)
+    shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out_scr, stream=stream)  # warm
+    torch.cuda.synchronize()
+    ev[4].record(stream)
+    for _ in range(args.steps):
+        shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out_scr, stream=stream)
+    ev[5].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    build_ms = ev[2].elapsed_time(ev[3])
+    scr_ms = ev[4].elapsed_time(ev[5]) / args.steps
+    err = float((out_scr - out_plain).abs().max())
+    mask = shgo.screen_mask(B.handle, kept + skipped)
+    pa, pb = shgo.pair_shells(B.handle, B.npairs)
+    rep = S.audit(basis, pa, pb, C, Z, mask, np.full(B.npairs, len(Z)), args.audit, np.random.default_rng(7),
+                  args.threshold)
+    line = {"metric": METRIC, "value": float(trip[0]) / ((build_ms + scr_ms) / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "ms_per_step": build_ms + scr_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"learned screening: {args.atoms}-atom cluster at 0.1 atoms/bohr^3, 4s3p2d1f",
+                       "shell_triples": float(trip[0]), "primitive_triples": float(trip[1]),
+                       "threshold": args.threshold, "margin": args.margin},
+            "screening": {"kept": kept, "skipped": skipped, "skipped_fraction": skipped / max(1, kept + skipped),
+                          "plain_ms": plain_ms, "build_ms": build_ms, "screened_ms": scr_ms,
+                          "speedup_vs_plain": plain_ms / (build_ms + scr_ms),
+                          "speedup_vs_plain_reusing_mask": plain_ms / scr_ms,
+                          "max_abs_error_vs_plain": err, "audit": rep},
+            "training": {"triples": int(len(tr)), "train_atoms": args.train_atoms, "epochs": args.epochs,
+                         "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "label_s": label_s,
+                         "train_s": train_s}}
+    print(json.dumps(line), flush=True)
+    B.close()
+    net.close()
+    return 0
+
+
 def run_precision_sweep(n_triples: int, n_oracle: int) -> int:
     """Precision sweep over independent primitive triples (la, lb <= 8, exponents log-uniform
     [0.01, 1000], |AB|, |PC| <= 15): per (la, lb) class, the block-normwise error of FP32-bulk and
@@ -443,9 +535,16 @@ def main():
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
     ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
-    ap.add_argument("--workload", default="highl", choices=["highl", "batched"],
+    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
+    ap.add_argument("--atoms", type=int, default=200, help="atoms of the screening cluster")
+    ap.add_argument("--train-atoms", type=int, default=120, help="atoms of the training cluster")
+    ap.add_argument("--train-triples", type=int, default=1_000_000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--threshold", type=float, default=1e-12)
+    ap.add_argument("--margin", type=float, default=100.0)
+    ap.add_argument("--audit", type=float, default=0.01, help="fraction of skipped triples checked exactly")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
@@ -463,6 +562,8 @@ def main():
         return run_precision_sweep(args.precision_sweep, args.sweep_oracle)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "screened":
+        return run_screened(args)
     ws, rank, local = _dist()
     if ws > 1:
         import torch
