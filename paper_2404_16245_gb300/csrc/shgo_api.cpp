@@ -332,6 +332,20 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
       b->allocations.push_back(b->d.rbuf);
     }
   }
+  if (st == SHGO_OK) {
+    cudaError_t e = cudaMalloc((void**)&b->d.ppd, sizeof(PPData) * (size_t)(ppcount > 0 ? ppcount : 1));
+    if (e != cudaSuccess) {
+      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+      err = std::string("cudaMalloc primitive-pair data: ") + cudaGetErrorString(e);
+    } else {
+      b->allocations.push_back(b->d.ppd);
+    }
+  }
+  if (st == SHGO_OK) st = launch_pair_build(b->d, ppcount, 0, &err);
+  if (st == SHGO_OK && cudaDeviceSynchronize() != cudaSuccess) {
+    st = SHGO_ERR_CUDA;
+    err = "primitive-pair build failed";
+  }
   if (st == SHGO_OK) st = device_tables(device, &b->tabs, &err);
   if (st != SHGO_OK) {
     release(b);

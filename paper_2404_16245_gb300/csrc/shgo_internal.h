@@ -167,6 +167,13 @@ struct ClassWork {
   int64_t pp_base; // first primitive pair of the class in the primitive-pair arrays
 };
 
+// Per primitive pair, from the basis alone (Gaussian product, Eq. 5), built once per basis by
+// k_pair_build: p = alpha + beta, 1/p, sqrt(p), K_AB, prefactor c~_i c~_j K_AB, beta/p, alpha/p and
+// |P - A| (the offset of P along the pair axis).  kab == 0 marks a pair both kernels skip.
+struct PPData {
+  double p, rp, sp, kab, pref, ra, rb, shift;
+};
+
 struct DeviceBasis {
   // shells
   double* shell_xyz = nullptr;  // [n_shells][3]
@@ -185,6 +192,7 @@ struct DeviceBasis {
   int* pp_pair = nullptr;
   int* pp_ij = nullptr;          // i << 8 | j
   int64_t* pp_roff = nullptr;    // offset of the pair's coupling block in rbuf
+  PPData* ppd = nullptr;         // per primitive pair (class order)
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
   int precision = SHGO_PREC_FP64;  // a shgo_precision value
@@ -231,6 +239,9 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
                                       cudaStream_t stream, std::string* err, cudaEvent_t* events = nullptr,
                                       bool concurrent = true);
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
+
+// Fills db.ppd for the npp primitive pairs (asynchronous on `stream`).
+shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err);
 
 // Launch shape of one class: nucleus chunk of the coupling kernel (16 or 32) and threads per
 // block of the pair kernel (32, 64 or 128); 0 = the default rule.

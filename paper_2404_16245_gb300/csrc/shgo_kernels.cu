@@ -50,6 +50,31 @@ __device__ __forceinline__ double prim_kab(double ea, double eb, double ab2) {
   return exp(-__dmul_rn(__ddiv_rn(__dmul_rn(ea, eb), __dadd_rn(ea, eb)), ab2));
 }
 
+// Step S1, once per basis: the Gaussian-product data of every primitive pair.
+__global__ void k_pair_build(int64_t npp, const int* __restrict__ pp_pair, const int* __restrict__ pp_ij,
+                             const int* __restrict__ pair_a, const int* __restrict__ pair_b,
+                             const double* __restrict__ shell_xyz, const int* __restrict__ shell_poff,
+                             const double* __restrict__ prim_exp, const double* __restrict__ prim_coef,
+                             PPData* __restrict__ ppd) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npp; q += (int64_t)gridDim.x * blockDim.x) {
+    const int pr = pp_pair[q], ij = pp_ij[q];
+    const int a = pair_a[pr], b = pair_b[pr];
+    const int ia = shell_poff[a] + (ij >> 8), ib = shell_poff[b] + (ij & 255);
+    const double ea = prim_exp[ia], eb = prim_exp[ib];
+    const double ab2 = pair_ab2(shell_xyz, a, b);
+    PPData d;
+    d.p = ea + eb;
+    d.rp = 1.0 / d.p;
+    d.sp = sqrt(d.p);
+    d.kab = prim_kab(ea, eb, ab2);
+    d.pref = prim_coef[ia] * prim_coef[ib] * d.kab;
+    d.ra = eb * d.rp;
+    d.rb = ea * d.rp;
+    d.shift = d.ra * sqrt(ab2);
+    ppd[q] = d;
+  }
+}
+
 // Shared-memory bytes of one warp of k_coupling_block.
 __host__ __device__ inline size_t coupling_smem_per_warp(int lam, int nch) {
   const int rs = (n_harm(lam) + n_beta(lam)) | 1;
@@ -70,6 +95,7 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
                                                        const double* __restrict__ boys_tab,
                                                        const int* __restrict__ rmap,
                                                        const double* __restrict__ pair_rot,
+                                                       const PPData* __restrict__ ppd,
                                                        double* __restrict__ rbuf) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
@@ -81,20 +107,16 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
   for (int64_t w = blockIdx.x; w < npp; w += gridDim.x) {
     const int64_t q = pp_base + w;
     const int pr = pp_pair[q];
-    const int ij = pp_ij[q];
-    const int a = pair_a[pr], b = pair_b[pr];
-    const double ea = prim_exp[shell_poff[a] + (ij >> 8)];
-    const double eb = prim_exp[shell_poff[b] + (ij & 255)];
-    const double p = ea + eb;
-    const double rp = 1.0 / p;
+    const int a = pair_a[pr];
+    const PPData pd = ppd[q];
+    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
+    // skips such primitive pairs, so their coupling block is not needed
+    if (pd.kab == 0.0) continue;
+    const double p = pd.p, rp = pd.rp;
     // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
     const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double ab2 = pair_ab2(shell_xyz, a, b);
-    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
-    // skips such primitive pairs, so their coupling block is not needed
-    if (prim_kab(ea, eb, ab2) == 0.0) continue;
-    const double shift = eb * rp * sqrt(ab2);  // |P - A|, along z in the pair frame
+    const double shift = pd.shift;  // |P - A|, along z in the pair frame
     // frame of the pair: Q (b - a) is along z, so the translation of Eq. 7 is diagonal in m
     double Q[9];
 #pragma unroll
@@ -204,6 +226,7 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
                                                            const double* __restrict__ boys_tab,
                                                            const int* __restrict__ rmap,
                                                            const double* __restrict__ pair_rot,
+                                                           const PPData* __restrict__ ppd,
                                                            double* __restrict__ rbuf) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31;
@@ -217,21 +240,17 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
   for (int64_t w = blockIdx.x; w < npp; w += gridDim.x) {
     const int64_t q = pp_base + w;
     const int pr = pp_pair[q];
-    const int ij = pp_ij[q];
-    const int a = pair_a[pr], b = pair_b[pr];
-    const double ea = prim_exp[shell_poff[a] + (ij >> 8)];
-    const double eb = prim_exp[shell_poff[b] + (ij & 255)];
-    const double p = ea + eb;
-    const double rp = 1.0 / p;
+    const int a = pair_a[pr];
+    const PPData pd = ppd[q];
+    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
+    // skips such primitive pairs, so their coupling block is not needed
+    if (pd.kab == 0.0) continue;
+    const double p = pd.p, rp = pd.rp;
     // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
     const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double ab2 = pair_ab2(shell_xyz, a, b);
-    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
-    // skips such primitive pairs, so their coupling block is not needed
-    if (prim_kab(ea, eb, ab2) == 0.0) continue;
-    const double shift = eb * rp * sqrt(ab2);  // |P - A|, along z in the pair frame
-    const double sp = sqrt(p);
+    const double shift = pd.shift;  // |P - A|, along z in the pair frame
+    const double sp = pd.sp;
     double Q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q[k] = pair_rot[9 * pr + k];
@@ -341,7 +360,7 @@ __host__ __device__ inline size_t pair_smem(int la, int lb) {
   const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb;
   return sizeof(double) * ((size_t)nWa * nWb + rot_doff(lm + 1) + (la + 1) * na + (lb + 1) * nb + nWa * nb +
-                           2 * na * nb + (la + 1) * (lb + 1) + n_r(la + lb) + 16);
+                           2 * na * nb + (la + 1) * (lb + 1) + n_r(la + lb) + 32);
 }
 
 // Threads per block of k_pair_block for a class: enough to cover the W entries of large classes.
@@ -377,6 +396,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     const GTerm* __restrict__ g_terms,
                                                     const int* __restrict__ rot_ptr,
                                                     const GTerm* __restrict__ rot_terms,
+                                                    const PPData* __restrict__ ppd,
                                                     const double* __restrict__ rbuf, MolView mv,
                                                     double* __restrict__ out) {
   extern __shared__ double smem[];
@@ -396,25 +416,31 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   double* fab = Yb + na * nb;              // [l1][l2]
   double* Rs = fab + (la + 1) * (lb + 1);  // coupling block of one primitive pair
   double* Rq = Rs + nR;                    // R = Q^T, row-major
+  double* scal = Rq + 9;                   // per primitive pair: prefactor, beta/p, alpha/p
+  double* dpow = scal + 4;                 // |b - a|^k, k <= max(la, lb)
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
-    const double ABx = shell_xyz[3 * b] - shell_xyz[3 * a], ABy = shell_xyz[3 * b + 1] - shell_xyz[3 * a + 1],
-                 ABz = shell_xyz[3 * b + 2] - shell_xyz[3 * a + 2];
-    const double ab2 = ABx * ABx + ABy * ABy + ABz * ABz;
-    const double ab2_exact = pair_ab2(shell_xyz, a, b);
-    const double dist = sqrt(ab2);
     __syncthreads();
+    // per-pair scalars once per block (FP64 division, sqrt and exp are costly on this GPU)
+    if (tid == 0) {
+      const double dist = sqrt(pair_ab2(shell_xyz, a, b));
+      double v = 1.0;
+      for (int k = 0; k <= lm; ++k) {
+        dpow[k] = v;
+        v *= dist;
+      }
+    }
     if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
     for (int e = tid; e < nW; e += nth) W[e] = 0.0;
+    __syncthreads();
     // translation along z (Eq. 7 with Eq. 8 coefficients, real basis): only nu = 0 survives,
     // t_A(l1, ma) = E^{la}(ma; l1 ma; 0) |b-a|^{la-l1}, t_B(l2, mb) = E^{lb}(mb; l2 mb; 0) (-|b-a|)^{lb-l2}
     for (int e = tid; e < (la + 1) * na; e += nth) {
       const int l1 = e / na, ma = e % na - la, lr = la - l1;
       double v = 0.0;
       if (l1 >= (ma < 0 ? -ma : ma)) {
-        v = etab[eoff[la] + translation_offset_dev(la, ma, l1, ma) + lr];
-        for (int k = 0; k < lr; ++k) v *= dist;
+        v = etab[eoff[la] + translation_offset_dev(la, ma, l1, ma) + lr] * dpow[lr];
       }
       tA[e] = v;
     }
@@ -422,8 +448,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       const int l2 = e / nb, mb = e % nb - lb, lr = lb - l2;
       double v = 0.0;
       if (l2 >= (mb < 0 ? -mb : mb)) {
-        v = etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr];
-        for (int k = 0; k < lr; ++k) v *= -dist;
+        v = etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr] * ((lr & 1) ? -dpow[lr] : dpow[lr]);
       }
       tB[e] = v;
     }
@@ -471,19 +496,23 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
     const int npa = shell_nprim[a], npb = shell_nprim[b];
     const int64_t q0 = pair_ppoff[pr];
     for (int ij = 0; ij < npa * npb; ++ij) {
-      const int i = ij / npb, j = ij % npb;
-      const double ea = prim_exp[shell_poff[a] + i], eb = prim_exp[shell_poff[b] + j];
-      const double p = ea + eb, rp = 1.0 / p;
-      const double kab = prim_kab(ea, eb, ab2_exact);
-      if (kab == 0.0) continue;  // uniform over the block; the coupling kernel skipped this pair too
-      const double pref = prim_coef[shell_poff[a] + i] * prim_coef[shell_poff[b] + j] * kab;
-      __syncthreads();            // the previous primitive pair is done with Rs and fab
+      __syncthreads();  // the previous primitive pair is done with Rs, fab and scal
+      if (tid == 0) {
+        const PPData pd = ppd[q0 + ij];
+        scal[0] = pd.pref;
+        scal[1] = pd.ra;
+        scal[2] = pd.rb;
+        scal[3] = pd.kab;
+      }
+      __syncthreads();
+      if (scal[3] == 0.0) continue;  // uniform over the block; the coupling kernel skipped this pair too
+      const double pref = scal[0];
       const double* R = rbuf + rbase + (q0 + ij - pp_base) * (int64_t)nR;
       for (int e = tid; e < nR; e += nth) Rs[e] = R[e];
       if (tid < (la + 1) * (lb + 1)) {
         const int l1 = tid / (lb + 1), l2 = tid % (lb + 1);
         double v = pref;
-        const double ra = eb * rp, rb = ea * rp;
+        const double ra = scal[1], rb = scal[2];
         for (int k = 0; k < la - l1; ++k) v *= ra;
         for (int k = 0; k < lb - l2; ++k) v *= rb;
         fab[tid] = v;
@@ -717,7 +746,7 @@ struct Launcher {
       const int grid = grid_cap(w.npp, 16);
 #define SHGO_F32_ARGS                                                                                              \
   lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.prim_exp, \
-      mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf
+      mv, centers, charges, dt.boys, rmap, db.pair_rot, db.ppd, db.rbuf
       const bool comp = db.precision == SHGO_PREC_FP32_BULK;
       if (nch == 32 && comp)
         k_coupling_block_f32<32, true><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
@@ -734,11 +763,11 @@ struct Launcher {
     if (nch == 32)
       k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
+          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.ppd, db.rbuf);
     else
       k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.rbuf);
+          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.ppd, db.rbuf);
   }
   void pair(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
     if (w.npairs == 0) return;
@@ -748,7 +777,7 @@ struct Launcher {
         w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_rot,
         db.shell_xyz, db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
         dt.g_rowinfo + th.g_rowbase[cid], dt.g_rowptr + th.g_rowbase[cid], dt.g_terms + th.g_termbase[cid],
-        dt.rot_ptr, dt.rot_terms, db.rbuf, mv, out);
+        dt.rot_ptr, dt.rot_terms, db.ppd, db.rbuf, mv, out);
   }
 };
 
@@ -982,6 +1011,14 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return launch_error(err);
+}
+
+shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err) {
+  if (npp == 0) return SHGO_OK;
+  const int64_t blocks = std::min<int64_t>((npp + 255) / 256, 152 * 32);
+  k_pair_build<<<(int)blocks, 256, 0, stream>>>(npp, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz,
+                                                 db.shell_poff, db.prim_exp, db.prim_coef, db.ppd);
   return launch_error(err);
 }
 

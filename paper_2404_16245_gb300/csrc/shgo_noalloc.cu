@@ -203,6 +203,7 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   const size_t o_pppair = pk.add(sizeof(int) * (size_t)npp);
   const size_t o_ppij = pk.add(sizeof(int) * (size_t)npp);
   const size_t host_bytes = pk.used;
+  const size_t o_ppd = pk.add(sizeof(PPData) * (size_t)npp);
   const size_t o_rbuf = pk.add(sizeof(double) * (size_t)rlen);
   const size_t need = pk.used;
 
@@ -315,6 +316,9 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   db.pp_ij = reinterpret_cast<int*>(region + o_ppij);
   db.rbuf = reinterpret_cast<double*>(region + o_rbuf);
   db.rbuf_len = rlen;
+  db.ppd = reinterpret_cast<PPData*>(region + o_ppd);
+  st = launch_pair_build(db, npp, s, &err);
+  if (st != SHGO_OK) return noalloc_fail(st, err);
   st = launch_nuclear_attraction(db, nd->tabs, work, nbf, centers->n, centers->xyz, charges, out, s, &err, nullptr,
                                  /*concurrent=*/false);
   if (st != SHGO_OK) return noalloc_fail(st, err);
