@@ -176,6 +176,14 @@ int64_t shgo_batch_out_size(const shgo_basis* batch);
 shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* centers, const double* charges,
                                             double* out, void* stream);
 
+/* Overlap matrix S_ab = <a|b> of a basis or of every molecule of a batch (Eqs. 9-10): both
+ * Gaussians of a pair translated to the product centre P (Eq. 7), where the one-centre integral is
+ * diagonal in (l, m) by the orthogonality of Eq. 10, then rotated from the pair frame back to the
+ * molecular frame.  out: device array, row-major nbf x nbf for a basis (symmetric, fully
+ * overwritten), the batched layout of shgo_batch_layout for a batch.  Asynchronous on `stream`;
+ * no nuclei are involved.  Errors: SHGO_ERR_INVALID_ARG (NULL basis or out), SHGO_ERR_CUDA. */
+shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream);
+
 /* Release a basis and its device memory (synchronises its device).  NULL-safe. */
 void shgo_free(shgo_basis* basis);
 

@@ -240,6 +240,10 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
                                       bool concurrent = true);
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
 
+// Overlap blocks of every shell pair into out (one molecule or a batch, per mv).
+shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                           const MolView& mv, double* out, cudaStream_t stream, std::string* err);
+
 // Fills db.ppd for the npp primitive pairs (asynchronous on `stream`).
 shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err);
 

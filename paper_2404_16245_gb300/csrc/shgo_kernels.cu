@@ -379,6 +379,51 @@ __device__ __forceinline__ int translation_offset_dev(int la, int ma, int l1, in
   return (ma + la) * per_ma + below + (m1 + l1) * (2 * (la - l1) + 1);
 }
 
+// Real rotation matrices D^l(R), l <= lm, R = Q^T (row-major in Rq), for the block's threads:
+// D^0 = 1, D^1 from R, then D^{l+1} from D^l through the harmonic part of u_c S_{l,m'}(u) (the
+// Gaunt product rule with one factor of degree 1).  Ends without a barrier after the last level.
+__device__ void build_rotations(int lm, const double* Rq, double* Dm, const int* __restrict__ rot_ptr,
+                                const GTerm* __restrict__ rot_terms) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) Dm[0] = 1.0;
+  if (lm >= 1 && tid < 9) {
+    const int m = tid / 3 - 1, c = tid % 3;  // row m, Cartesian column c (x, y, z)
+    const int crow = m == -1 ? 1 : (m == 0 ? 2 : 0);
+    const int mp = c == 0 ? 1 : (c == 1 ? -1 : 0);
+    Dm[1 + (m + 1) * 3 + (mp + 1)] = Rq[crow * 3 + c];
+  }
+  for (int l = 1; l < lm; ++l) {
+    __syncthreads();
+    const double* Dl = Dm + rot_doff(l);
+    double* Dn = Dm + rot_doff(l + 1);
+    const int n1 = 2 * l + 3;
+    for (int e = tid; e < n1 * n1; e += nth) {
+      const int m = e / n1 - (l + 1), M = e % n1 - (l + 1);
+      const int q = rot_index(l, M);
+      double s = 0.0;
+      if (m >= -l && m <= l) {
+        for (int t = rot_ptr[q]; t < rot_ptr[q + 1]; ++t) {
+          const GTerm g = rot_terms[t];
+          s = fma(g.coef * Rq[6 + g.ridx], Dl[(m + l) * (2 * l + 1) + g.pad + l], s);
+        }
+        s *= c_harm.a[harm_index(l, m)];
+      } else {
+        const double* top = Dl + (2 * l) * (2 * l + 1);  // row m = l
+        const double* bot = Dl;                          // row m = -l
+        for (int t = rot_ptr[q]; t < rot_ptr[q + 1]; ++t) {
+          const GTerm g = rot_terms[t];
+          const double rx = Rq[g.ridx], ry = Rq[3 + g.ridx];
+          const double v = (m > 0) ? (rx * top[g.pad + l] - ry * bot[g.pad + l])
+                                   : (ry * top[g.pad + l] + rx * bot[g.pad + l]);
+          s = fma(g.coef, v, s);
+        }
+        s *= c_harm.c[l];
+      }
+      Dn[e] = s;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, int pair_base, int64_t pp_base,
                                                     int64_t rbase, const int* __restrict__ pair_a,
                                                     const int* __restrict__ pair_b,
@@ -453,45 +498,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       tB[e] = v;
     }
     __syncthreads();
-    // real rotation matrices D^l(R), R = Q^T: D^0 = 1, D^1 from R, then D^{l+1} from D^l through the
-    // harmonic part of u_c S_{l,m'}(u) (Gaunt product rule with one factor of degree 1)
-    if (tid == 0) Dm[0] = 1.0;
-    if (lm >= 1 && tid < 9) {
-      const int m = tid / 3 - 1, c = tid % 3;  // row m, Cartesian column c (x, y, z)
-      const int crow = m == -1 ? 1 : (m == 0 ? 2 : 0);
-      const int mp = c == 0 ? 1 : (c == 1 ? -1 : 0);
-      Dm[1 + (m + 1) * 3 + (mp + 1)] = Rq[crow * 3 + c];
-    }
-    for (int l = 1; l < lm; ++l) {
-      __syncthreads();
-      const double* Dl = Dm + rot_doff(l);
-      double* Dn = Dm + rot_doff(l + 1);
-      const int n1 = 2 * l + 3;
-      for (int e = tid; e < n1 * n1; e += nth) {
-        const int m = e / n1 - (l + 1), M = e % n1 - (l + 1);
-        const int q = rot_index(l, M);
-        double s = 0.0;
-        if (m >= -l && m <= l) {
-          for (int t = rot_ptr[q]; t < rot_ptr[q + 1]; ++t) {
-            const GTerm g = rot_terms[t];
-            s = fma(g.coef * Rq[6 + g.ridx], Dl[(m + l) * (2 * l + 1) + g.pad + l], s);
-          }
-          s *= c_harm.a[harm_index(l, m)];
-        } else {
-          const double* top = Dl + (2 * l) * (2 * l + 1);  // row m = l
-          const double* bot = Dl;                          // row m = -l
-          for (int t = rot_ptr[q]; t < rot_ptr[q + 1]; ++t) {
-            const GTerm g = rot_terms[t];
-            const double rx = Rq[g.ridx], ry = Rq[3 + g.ridx];
-            const double v = (m > 0) ? (rx * top[g.pad + l] - ry * bot[g.pad + l])
-                                     : (ry * top[g.pad + l] + rx * bot[g.pad + l]);
-            s = fma(g.coef, v, s);
-          }
-          s *= c_harm.c[l];
-        }
-        Dn[e] = s;
-      }
-    }
+    build_rotations(lm, Rq, Dm, rot_ptr, rot_terms);
     // coupling (Gaunt) and primitive contraction, in the pair frame
     const int npa = shell_nprim[a], npb = shell_nprim[b];
     const int64_t q0 = pair_ppoff[pr];
@@ -578,6 +585,117 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       const int ma = e / nb, mb = e % nb;
       // diagonal shell block: the upper triangle serves both halves (exact symmetry)
       const double v = (a == b && ma > mb) ? Vp[mb * nb + ma] : Vp[e];
+      o[(fa0 + ma) * ld + fb0 + mb] = v;
+      if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = v;
+    }
+  }
+}
+
+// Overlap block of one shell pair (Eqs. 9-10): both orbitals translated to P (Eq. 7) in the pair
+// frame, where the one-centre integrals are diagonal by orthogonality,
+//   int S_{l1 m1}(r_P) S_{l2 m2}(r_P) e^{-p r_P^2} = delta delta 4 pi (pi/2)^{1/2} (2 l1 - 1)!! / (2p)^{l1+3/2},
+// so S'[ma][mb] = delta_{ma mb} sum_{l1 >= |ma|} t_A(l1, ma) t_B(l1, ma) w(l1) with
+// w(l1) = sum_ij c~_i c~_j K_ij (beta/p)^{la-l1} (alpha/p)^{lb-l1} 4 pi (pi/2)^{1/2} (2 l1 - 1)!!/(2p)^{l1+3/2};
+// the block is rotated back with D^{la} S' (D^{lb})^T.
+__host__ __device__ inline size_t overlap_smem(int la, int lb) {
+  const int lm = la > lb ? la : lb;
+  return sizeof(double) * ((size_t)rot_doff(lm + 1) + (la + 1) * (2 * la + 1) + (lb + 1) * (2 * lb + 1) +
+                           (2 * la + 1) * (2 * lb + 1) + 2 * (lm + 1) + 32);
+}
+
+__global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs, int pair_base,
+                                                      const int* __restrict__ pair_a, const int* __restrict__ pair_b,
+                                                      const int64_t* __restrict__ pair_ppoff,
+                                                      const double* __restrict__ pair_rot,
+                                                      const double* __restrict__ shell_xyz,
+                                                      const int* __restrict__ shell_nprim,
+                                                      const int64_t* __restrict__ shell_foff,
+                                                      const double* __restrict__ etab, const int* __restrict__ eoff,
+                                                      const int* __restrict__ rot_ptr,
+                                                      const GTerm* __restrict__ rot_terms,
+                                                      const PPData* __restrict__ ppd, MolView mv,
+                                                      double* __restrict__ out) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int na = 2 * la + 1, nb = 2 * lb + 1;
+  const int lm = la > lb ? la : lb, ln = la < lb ? la : lb;
+  double* Dm = smem;
+  double* tA = Dm + rot_doff(lm + 1);
+  double* tB = tA + (la + 1) * na;
+  double* Vs = tB + (lb + 1) * nb;
+  double* wl = Vs + na * nb;   // w(l1)
+  double* dpow = wl + lm + 1;  // |b - a|^k
+  double* Rq = dpow + lm + 1;
+  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
+    const int pr = pair_base + w;
+    const int a = pair_a[pr], b = pair_b[pr];
+    __syncthreads();
+    if (tid == 0) {
+      const double dist = sqrt(pair_ab2(shell_xyz, a, b));
+      double v = 1.0;
+      for (int k = 0; k <= lm; ++k) {
+        dpow[k] = v;
+        v *= dist;
+      }
+    }
+    if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
+    // radial sums over primitive pairs, one l1 per thread
+    if (tid <= ln) {
+      const int l1 = tid;
+      double dfact = 1.0;
+      for (int k = 2 * l1 - 1; k > 1; k -= 2) dfact *= k;
+      // 4 pi (pi/2)^{1/2} / 2^{l1 + 3/2} (2 l1 - 1)!!
+      double c = 4.0 * 3.14159265358979323846 * 1.2533141373155002512 * dfact * 0.35355339059327376220;
+      for (int k = 0; k < l1; ++k) c *= 0.5;
+      const int64_t q0 = pair_ppoff[pr];
+      const int npp = shell_nprim[a] * shell_nprim[b];
+      double acc = 0.0;
+      for (int ij = 0; ij < npp; ++ij) {
+        const PPData pd = ppd[q0 + ij];
+        if (pd.kab == 0.0) continue;
+        double v = pd.pref * pd.rp / pd.sp;  // p^{-3/2}
+        for (int k = 0; k < l1; ++k) v *= pd.rp;
+        for (int k = 0; k < la - l1; ++k) v *= pd.ra;
+        for (int k = 0; k < lb - l1; ++k) v *= pd.rb;
+        acc += v;
+      }
+      wl[l1] = c * acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < (la + 1) * na; e += nth) {
+      const int l1 = e / na, ma = e % na - la, lr = la - l1;
+      tA[e] = l1 >= (ma < 0 ? -ma : ma) ? etab[eoff[la] + translation_offset_dev(la, ma, l1, ma) + lr] * dpow[lr] : 0.0;
+    }
+    for (int e = tid; e < (lb + 1) * nb; e += nth) {
+      const int l2 = e / nb, mb = e % nb - lb, lr = lb - l2;
+      tB[e] = l2 >= (mb < 0 ? -mb : mb)
+                  ? etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr] * ((lr & 1) ? -dpow[lr] : dpow[lr])
+                  : 0.0;
+    }
+    build_rotations(lm, Rq, Dm, rot_ptr, rot_terms);
+    __syncthreads();
+    // S = D^{la} S' (D^{lb})^T with S' diagonal in m (|m| <= min(la, lb))
+    const double* Da = Dm + rot_doff(la);
+    const double* Db = Dm + rot_doff(lb);
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      double s = 0.0;
+      for (int m = -ln; m <= ln; ++m) {
+        const int am = m < 0 ? -m : m;
+        double d = 0.0;
+        for (int l1 = am; l1 <= ln; ++l1) d = fma(tA[l1 * na + m + la] * tB[l1 * nb + m + lb], wl[l1], d);
+        s = fma(Da[ma * na + m + la] * Db[mb * nb + m + lb], d, s);
+      }
+      Vs[e] = s;
+    }
+    __syncthreads();
+    const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
+    int64_t obase, ld;
+    mol_output(mv, pr, obase, ld);
+    double* o = out + obase;
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      const double v = (a == b && ma > mb) ? Vs[mb * nb + ma] : Vs[e];
       o[(fa0 + ma) * ld + fb0 + mb] = v;
       if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = v;
     }
@@ -1019,6 +1137,22 @@ shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t s
   const int64_t blocks = std::min<int64_t>((npp + 255) / 256, 152 * 32);
   k_pair_build<<<(int)blocks, 256, 0, stream>>>(npp, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz,
                                                  db.shell_poff, db.prim_exp, db.prim_coef, db.ppd);
+  return launch_error(err);
+}
+
+shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                           const MolView& mv, double* out, cudaStream_t stream, std::string* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_overlap_block, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  for (const ClassWork& w : work) {
+    if (w.npairs == 0) continue;
+    k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), stream>>>(
+        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_rot, db.shell_xyz,
+        db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, dt.rot_ptr, dt.rot_terms, db.ppd, mv, out);
+  }
   return launch_error(err);
 }
 

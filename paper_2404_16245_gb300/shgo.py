@@ -72,6 +72,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_nuclear_attraction_batched.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_nuclear_attraction_batched.restype = ctypes.c_int
+    lib.shgo_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_overlap.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -228,6 +230,26 @@ def nuclear_attraction(basis: Basis, centers, charges, out=None, stream=None):
     n = centers.shape[0] if centers.numel() else 0
     shgo_nuclear_attraction(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
                             out.data_ptr(), stream)
+    return out
+
+
+def shgo_overlap(basis, out_ptr, stream=None):
+    _check(_lib.shgo_overlap(ctypes.c_void_p(basis), ctypes.c_void_p(int(out_ptr) or 0), _stream_handle(stream)))
+
+
+def overlap(basis, out=None, stream=None, device="cuda"):
+    """S (FP64 device tensor): [nbf, nbf] for a Basis, the concatenated per-molecule blocks for a
+    Batch (see Batch.block)."""
+    import torch
+    if isinstance(basis, Basis):
+        shape = (basis.nbf, basis.nbf)
+    else:
+        shape = (max(basis.out_size, 1),)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != shape:
+        raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
+    shgo_overlap(basis.handle, out.data_ptr(), stream)
     return out
 
 
