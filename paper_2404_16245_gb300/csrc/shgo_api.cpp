@@ -278,6 +278,7 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   b->h_pair_mol = pmol;
   std::vector<double> prot(9 * pa.size());
   for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
+  const int64_t rotlen = assign_rot_bases(b->work);
   int64_t rlen = 0, max_pair_r = 0;
   for (const auto& w : b->work) rlen += w.npp * n_r(w.la + w.lb);
   b->h_ppoff.assign(ppoff.begin(), ppoff.end());
@@ -341,12 +342,22 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
       b->allocations.push_back(b->d.ppd);
     }
   }
-  if (st == SHGO_OK) st = launch_pair_build(b->d, ppcount, 0, &err);
-  if (st == SHGO_OK && cudaDeviceSynchronize() != cudaSuccess) {
-    st = SHGO_ERR_CUDA;
-    err = "primitive-pair build failed";
+  if (st == SHGO_OK) {
+    cudaError_t e = cudaMalloc((void**)&b->d.rotd, sizeof(double) * (size_t)(rotlen > 0 ? rotlen : 1));
+    if (e != cudaSuccess) {
+      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+      err = std::string("cudaMalloc pair rotations: ") + cudaGetErrorString(e);
+    } else {
+      b->allocations.push_back(b->d.rotd);
+    }
   }
   if (st == SHGO_OK) st = device_tables(device, &b->tabs, &err);
+  if (st == SHGO_OK) st = launch_pair_build(b->d, ppcount, 0, &err);
+  if (st == SHGO_OK) st = launch_pair_rotations(b->d, *b->tabs, b->work, 0, &err);
+  if (st == SHGO_OK && cudaDeviceSynchronize() != cudaSuccess) {
+    st = SHGO_ERR_CUDA;
+    err = "primitive-pair and pair-frame build failed";
+  }
   if (st != SHGO_OK) {
     release(b);
     return fail(st, err);
@@ -541,31 +552,29 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
     const double pp_cent = basis->batch ? basis->class_pp_cent[wi] : (double)w.npp * (double)n_centers;
     const int la = w.la, lb = w.lb, lam = la + lb;
     const double nB = n_beta(lam), nR = n_r(lam);
-    // per primitive triple
-    double s_lm = lam >= 2 ? 5.0 : 0.0;
-    for (int l = 1; l < lam; ++l) s_lm += 8.0 * l + 8.0;
-    const double boys = 4.0 * kBoysK + 1 + 3.0 * lam;
-    const double per_triple = 9 + boys + (lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
-    f0 += per_triple * pp_cent + nR * (double)w.npp;
+    // per primitive triple (flops, an FMA counting two): geometry 9; |d|^2, T, 1/|d|, |d| and the
+    // unit vector 11; Boys: Horner over kBoysK Taylor terms (5 per term), exp 1, downward
+    // recursion 3 per order; Z |d|^n F_n 2 Lambda + 1; (p |d|)^j / j! 2 per j; the beta running
+    // sums 2 per entry beyond the first of each L; the unit-vector harmonic recursion 6 l + 5 for
+    // level l + 1; the nucleus sum 2 per R entry
+    double s_lm = 0.0;
+    for (int l = 1; l < lam; ++l) s_lm += 6.0 * l + 5.0;
+    const double boys = 5.0 * kBoysK + 1 + 3.0 * lam;
+    const double per_triple =
+        9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
+    f0 += per_triple * pp_cent + 2.0 * nR * (double)w.npp;
     // per primitive pair: coupling
     const int cid = class_id(la, lb);
     const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
-    const double terms = t.g_rowptr[t.g_rowbase[cid] + nW];
+    const double terms = t.g_nnz[cid];
     f1 += (2.0 * terms + 4.0 * nW) * (double)w.npp;
-    // per shell pair: real rotation matrices up to max(la, lb), the translation along the pair axis
-    // (diagonal in m) and the rotation of the block back to the molecular frame
-    const int lm = std::max(la, lb);
-    double rot = 0;
-    for (int l = 1; l < lm; ++l)
-      for (int M = -(l + 1); M <= l + 1; ++M) {
-        const int q = rot_index(l, M);
-        rot += 2.0 * (t.rot_ptr[q + 1] - t.rot_ptr[q]) * (2 * l + 3);
-      }
+    // per shell pair: the translation along the pair axis (diagonal in m) and the rotation of the
+    // block back to the molecular frame (the rotation matrices themselves are built once per basis)
     const double na = 2 * la + 1, nb = 2 * lb + 1;
     double zt = 0, vt = 0;
     for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
     for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
-    f1 += (rot + zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
+    f1 += (zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
     st += pair_cent;
     pt += pp_cent;
   }

@@ -47,6 +47,11 @@ struct HarmCoef {
   double a[(kHarmMax + 1) * (kHarmMax + 1)];
   double b[(kHarmMax + 1) * (kHarmMax + 1)];
   double c[kHarmMax + 1];
+  // Unnormalised harmonics U_lm = S_lm / N_lm of a unit vector, whose recursion needs one constant:
+  //   U_{l+1,m} = z U_lm + ng_lm U_{l-1,m} (|m| < l),  U_{l+1,+-l} = z U_{l,+-l},
+  //   U_{l+1,l+1} = x U_ll - y U_{l,-l},  U_{l+1,-l-1} = y U_ll + x U_{l,-l}.
+  double ng[(kHarmMax + 1) * (kHarmMax + 1)];  // -gamma_lm
+  double n[(kHarmMax + 1) * (kHarmMax + 1)];   // N_lm
 };
 const HarmCoef& harm_coef_host();
 
@@ -66,17 +71,22 @@ struct Tables {
   std::vector<double> etab;
   std::vector<int> eoff;  // [kLmax + 2]
   // Gaunt programs per class (la >= lb): one row per W entry (l1 m1, l2 m2), rows sorted by
-  // decreasing term count so that neighbouring threads run loops of equal length.  Row r has
-  // g_rowinfo[r] = W index (row-major, (lb+1)^2 columns) | l1 << 16 | l2 << 20 and terms
-  // g_rowptr[r] .. g_rowptr[r+1] (local to the class) of (coefficient, R' index for Lambda = la+lb).
-  std::vector<int> g_rowinfo;
-  std::vector<int> g_rowptr;   // concatenated, class c rows at g_rowbase[c] .. + nW + 1
+  // decreasing term count and cut into groups of 32 (one warp; the last group padded with empty
+  // rows).  Row r has g_rowinfo[r] = W index (row-major with w_stride(lb) columns) | l1 << 16 |
+  // l2 << 20, or -1 for padding.  Group g holds K_g = g_grp[2g + 1] terms per row, interleaved:
+  // term j of the row in lane i is g_terms[g_grp[2g] + 32 j + i] (coefficient, R' index for
+  // Lambda = la + lb), zero-coefficient terms filling rows shorter than K_g.
+  std::vector<int> g_rowinfo;   // class c rows at g_rowbase[c] .., a multiple of 32 per class
+  std::vector<int> g_grp;       // class c groups at 2 g_grpbase[c] ..; term offsets local to the class
   std::vector<GTerm> g_terms;
-  std::vector<int> g_rowbase;  // [n classes]
-  std::vector<int> g_termbase; // [n classes]
+  std::vector<int> g_rowbase;   // [n classes]
+  std::vector<int> g_grpbase;   // [n classes]
+  std::vector<int> g_termbase;  // [n classes]
+  std::vector<int> g_nnz;       // [n classes] nonzero coupling coefficients (without padding)
   // R layout per Lambda: packed (harm index | beta index << 12 | k << 24) for entry e.
   std::vector<int> rmap;
   std::vector<int> rmap_off;  // [kLamMax + 2]
+  std::vector<double> rnorm;  // N_LM of entry e (HarmCoef::n), aligned with rmap
   // Real rotation matrices D^{l+1} from D^l (S_lm(R y) = sum_m' D^l[m][m'] S_lm'(y)): the
   // harmonic part of u_c S_{l,m'}(u) for a Cartesian component c is sum_M G(1 m(c), l m'; l+1 M)
   // S_{l+1,M}.  For l = 0..kLmax-1 and M = -(l+1)..l+1 the list rot_terms[rot_ptr[q] .. rot_ptr[q+1]]
@@ -91,6 +101,10 @@ const Tables& tables_host();
 __host__ __device__ inline int rot_index(int l, int M) { return l * (l + 2) + M + l + 1; }
 
 inline int class_id(int la, int lb) { return la * (la + 1) / 2 + lb; }  // la >= lb
+
+// Row stride of the coupling block W[(l1 m1)][(l2 m2)] in shared memory: (lb + 1)^2 rounded up to an
+// odd count, so that a warp reading one column (consecutive rows) touches distinct banks.
+__host__ __device__ inline int w_stride(int lb) { return ((lb + 1) * (lb + 1)) | 1; }
 constexpr int kNumClasses = (kLmax + 1) * (kLmax + 2) / 2;
 
 // Offset inside the la block of etab for (ma, l1, m1); nu runs over 2(la - l1) + 1 values.
@@ -106,9 +120,10 @@ struct DeviceTables {
   double* etab = nullptr;
   int* eoff = nullptr;
   int* g_rowinfo = nullptr;
-  int* g_rowptr = nullptr;
+  int* g_grp = nullptr;
   GTerm* g_terms = nullptr;
   int* rmap = nullptr;
+  double* rnorm = nullptr;
   int* rot_ptr = nullptr;
   GTerm* rot_terms = nullptr;
 };
@@ -165,7 +180,14 @@ struct ClassWork {
   int pair_base;   // first pair of the class in the pair arrays
   int64_t npp;     // primitive pairs of the class
   int64_t pp_base; // first primitive pair of the class in the primitive-pair arrays
+  int64_t rot_base = 0;  // first double of the class's per-pair rotation blocks in DeviceBasis::rotd
 };
+
+// Per shell pair, from the basis alone, built once per basis by k_pair_rotations: |b - a| followed by
+// the real rotation matrices D^{la}(Q^T) and, when lb != la, D^{lb}(Q^T) (row-major, (2l+1)^2 each).
+__host__ __device__ inline int64_t rot_per_pair(int la, int lb) {
+  return 1 + (int64_t)(2 * la + 1) * (2 * la + 1) + (la != lb ? (int64_t)(2 * lb + 1) * (2 * lb + 1) : 0);
+}
 
 // Per primitive pair, from the basis alone (Gaussian product, Eq. 5), built once per basis by
 // k_pair_build: p = alpha + beta, 1/p, sqrt(p), K_AB, prefactor c~_i c~_j K_AB, beta/p, alpha/p and
@@ -193,6 +215,7 @@ struct DeviceBasis {
   int* pp_ij = nullptr;          // i << 8 | j
   int64_t* pp_roff = nullptr;    // offset of the pair's coupling block in rbuf
   PPData* ppd = nullptr;         // per primitive pair (class order)
+  double* rotd = nullptr;        // per shell pair: |b - a|, D^{la}, D^{lb} (see rot_per_pair)
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
   int precision = SHGO_PREC_FP64;  // a shgo_precision value
@@ -246,6 +269,20 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
 
 // Fills db.ppd for the npp primitive pairs (asynchronous on `stream`).
 shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err);
+
+// Fills db.rotd for every shell pair of `work` (asynchronous on `stream`).
+shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                                  cudaStream_t stream, std::string* err);
+
+// Sets w.rot_base for every class and returns the doubles of the rotation buffer.
+inline int64_t assign_rot_bases(std::vector<ClassWork>& work) {
+  int64_t n = 0;
+  for (ClassWork& w : work) {
+    w.rot_base = n;
+    n += (int64_t)w.npairs * rot_per_pair(w.la, w.lb);
+  }
+  return n;
+}
 
 // Launch shape of one class: nucleus chunk of the coupling kernel (16 or 32) and threads per
 // block of the pair kernel (32, 64 or 128); 0 = the default rule.

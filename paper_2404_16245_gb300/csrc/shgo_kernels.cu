@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
                                                        const double* __restrict__ charges,
                                                        const double* __restrict__ boys_tab,
                                                        const int* __restrict__ rmap,
+                                                       const double* __restrict__ rnorm,
                                                        const double* __restrict__ pair_rot,
                                                        const PPData* __restrict__ ppd,
                                                        double* __restrict__ rbuf) {
@@ -137,14 +138,31 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
           dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - shift;
           z = charges[c];
         }
-        const double T = p * (dx * dx + dy * dy + dz * dz);
+        const double s2 = dx * dx + dy * dy + dz * dz;
+        const double T = p * s2;
+        // unit vector and length of d: S_LM(d) = |d|^L N_LM U_LM(d/|d|), the |d|^L going with the
+        // radial factors (d = 0 leaves only L = 0, which any unit vector gives)
+        double ux = 0.0, uy = 0.0, uz = 1.0, dn = 0.0;
+        if (s2 > 0.0) {
+          const double ri = rsqrt(s2);
+          dn = s2 * ri;
+          ux = dx * ri;
+          uy = dy * ri;
+          uz = dz * ri;
+        }
         boys_eval(lam, T, row, 1, boys_tab, c_boys);
-        // Z F_n, and T^k / k! behind it
-        for (int n = 0; n <= lam; ++n) row[n] *= z;
+        // G_n = Z |d|^n F_n, and tau_j = (p |d|)^j / j! behind it, so that
+        // |d|^L Z sum_j T^j/j! F_{L+j} = sum_j tau_j G_{L+j}
+        double zp = z;
+        for (int n = 0; n <= lam; ++n) {
+          row[n] *= zp;
+          zp *= dn;
+        }
         double* tk = row + lam + 1;
         tk[0] = 1.0;
-        for (int k = 1; k <= (lam >> 1); ++k) tk[k] = tk[k - 1] * T * c_boys.inv_int[k];
-        // beta_{L,k} / k! = sum_j T^j/j! Z F_{L+j}  (running sum over k)
+        const double pdn = p * dn;
+        for (int k = 1; k <= (lam >> 1); ++k) tk[k] = tk[k - 1] * pdn * c_boys.inv_int[k];
+        // |d|^L beta_{L,k} / k! = sum_{j<=k} tau_j G_{L+j}  (running sum over k)
         double* brow = row + nS;
         int bo = 0;
         for (int L = 0; L <= lam; ++L) {
@@ -157,23 +175,21 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
           }
           bo += km + 1;
         }
-        solid_harmonics(lam, dx, dy, dz, row, 1, c_harm.a, c_harm.b, c_harm.c);
+        solid_harmonics_unit(lam, ux, uy, uz, row, 1, c_harm.ng);
       }
       __syncwarp();
       const int* rm = rmap;
       for (int e = lane; e < nR; e += 32) {
         const int code = __ldg(rm + e);
         const int si = code & 0xfff, bi = nS + ((code >> 12) & 0xfff);
-        // four independent partial sums over the nuclei of the chunk
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        // two partial sums over the nuclei of the chunk, the first continuing the running total
+        double a0 = racc[e], a1 = 0.0;
 #pragma unroll
-        for (int c = 0; c < NCH; c += 4) {
+        for (int c = 0; c < NCH; c += 2) {
           a0 = fma(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], a0);
           a1 = fma(rows[(size_t)(c + 1) * rs + si], rows[(size_t)(c + 1) * rs + bi], a1);
-          a2 = fma(rows[(size_t)(c + 2) * rs + si], rows[(size_t)(c + 2) * rs + bi], a2);
-          a3 = fma(rows[(size_t)(c + 3) * rs + si], rows[(size_t)(c + 3) * rs + bi], a3);
         }
-        racc[e] += (a0 + a1) + (a2 + a3);
+        racc[e] = a0 + a1;
       }
     }
     // scale 2 pi k! p^{-(k+1)}
@@ -184,7 +200,9 @@ __global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int
     }
     __syncwarp();
     double* out = rbuf + rbase + w * (int64_t)nR;
-    for (int e = lane; e < nR; e += 32) out[e] = racc[e] * scl[(__ldg(rmap + e) >> 24) & 0xff];
+    for (int e = lane; e < nR; e += 32) {
+      out[e] = racc[e] * (scl[(__ldg(rmap + e) >> 24) & 0xff] * __ldg(rnorm + e));
+    }
     __syncwarp();
   }
 }
@@ -356,10 +374,9 @@ __host__ __device__ inline int rot_doff(int l) { return l * (2 * l - 1) * (2 * l
 
 // Shared-memory bytes of one block of k_pair_block.
 __host__ __device__ inline size_t pair_smem(int la, int lb) {
-  const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1);
+  const int nWa = (la + 1) * (la + 1);
   const int na = 2 * la + 1, nb = 2 * lb + 1;
-  const int lm = la > lb ? la : lb;
-  return sizeof(double) * ((size_t)nWa * nWb + rot_doff(lm + 1) + (la + 1) * na + (lb + 1) * nb + nWa * nb +
+  return sizeof(double) * ((size_t)nWa * w_stride(lb) + na * na + nb * nb + (la + 1) * na + (lb + 1) * nb + nWa * nb +
                            2 * na * nb + (la + 1) * (lb + 1) + n_r(la + lb) + 32);
 }
 
@@ -424,12 +441,40 @@ __device__ void build_rotations(int lm, const double* Rq, double* Dm, const int*
   }
 }
 
+// Once per basis: |b - a| and the rotation matrices D^{la}, D^{lb} of the pair frame of every shell
+// pair of one class (one block per pair; they depend on the shell centres only).
+__global__ void __launch_bounds__(64) k_pair_rotations(int la, int lb, int npairs, int pair_base, int64_t rot_base,
+                                                       const int* __restrict__ pair_a, const int* __restrict__ pair_b,
+                                                       const double* __restrict__ pair_rot,
+                                                       const double* __restrict__ shell_xyz,
+                                                       const int* __restrict__ rot_ptr,
+                                                       const GTerm* __restrict__ rot_terms, double* __restrict__ rotd) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lm = la > lb ? la : lb, na = 2 * la + 1, nb = 2 * lb + 1;
+  const int64_t per = rot_per_pair(la, lb);
+  double* Dm = smem;
+  double* Rq = Dm + rot_doff(lm + 1);
+  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
+    const int pr = pair_base + w;
+    __syncthreads();
+    if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
+    __syncthreads();
+    build_rotations(lm, Rq, Dm, rot_ptr, rot_terms);
+    __syncthreads();
+    double* o = rotd + rot_base + (int64_t)w * per;
+    if (tid == 0) o[0] = sqrt(pair_ab2(shell_xyz, pair_a[pr], pair_b[pr]));
+    for (int e = tid; e < na * na; e += nth) o[1 + e] = Dm[rot_doff(la) + e];
+    if (la != lb)
+      for (int e = tid; e < nb * nb; e += nth) o[1 + na * na + e] = Dm[rot_doff(lb) + e];
+  }
+}
+
 __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, int pair_base, int64_t pp_base,
                                                     int64_t rbase, const int* __restrict__ pair_a,
                                                     const int* __restrict__ pair_b,
                                                     const int64_t* __restrict__ pair_ppoff,
-                                                    const double* __restrict__ pair_rot,
-                                                    const double* __restrict__ shell_xyz,
+                                                    int64_t rot_base, const double* __restrict__ rotd,
                                                     const int* __restrict__ shell_poff,
                                                     const int* __restrict__ shell_nprim,
                                                     const int64_t* __restrict__ shell_foff,
@@ -437,10 +482,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     const double* __restrict__ prim_coef,
                                                     const double* __restrict__ etab, const int* __restrict__ eoff,
                                                     const int* __restrict__ g_rowinfo,
-                                                    const int* __restrict__ g_rowptr,
+                                                    const int* __restrict__ g_grp,
                                                     const GTerm* __restrict__ g_terms,
-                                                    const int* __restrict__ rot_ptr,
-                                                    const GTerm* __restrict__ rot_terms,
                                                     const PPData* __restrict__ ppd,
                                                     const double* __restrict__ rbuf, MolView mv,
                                                     double* __restrict__ out) {
@@ -449,35 +492,37 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   const int lam = la + lb;
   const int nR = n_r(lam);
   const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
+  const int ws = w_stride(lb), nWs = nWa * ws, nrp = (nW + 31) & ~31;
   const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb;
-  double* W = smem;
-  double* Dm = W + nW;                     // D^l for l <= lm, D = D(Q^T)
-  double* tA = Dm + rot_doff(lm + 1);      // [l1][ma]
+  const int nDb = la != lb ? nb * nb : 0;
+  const int64_t per = rot_per_pair(la, lb);
+  double* W = smem;                        // [l1 m1][l2 m2], row stride ws
+  double* Dm = W + nWs;                    // D^{la}(Q^T), then D^{lb}(Q^T) when lb != la
+  double* tA = Dm + na * na + nb * nb;     // [l1][ma]
   double* tB = tA + (la + 1) * na;         // [l2][mb]
   double* Zb = tB + (lb + 1) * nb;         // [l1 m1][mb]
   double* Vp = Zb + nWa * nb;              // [ma][mb] in the pair frame, later the final block
   double* Yb = Vp + na * nb;               // [ma][mb]
   double* fab = Yb + na * nb;              // [l1][l2]
   double* Rs = fab + (la + 1) * (lb + 1);  // coupling block of one primitive pair
-  double* Rq = Rs + nR;                    // R = Q^T, row-major
-  double* scal = Rq + 9;                   // per primitive pair: prefactor, beta/p, alpha/p
+  double* scal = Rs + nR;                  // per primitive pair: prefactor, beta/p, alpha/p
   double* dpow = scal + 4;                 // |b - a|^k, k <= max(la, lb)
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
+    const double* rd = rotd + rot_base + (int64_t)w * per;
     __syncthreads();
-    // per-pair scalars once per block (FP64 division, sqrt and exp are costly on this GPU)
     if (tid == 0) {
-      const double dist = sqrt(pair_ab2(shell_xyz, a, b));
+      const double dist = rd[0];
       double v = 1.0;
       for (int k = 0; k <= lm; ++k) {
         dpow[k] = v;
         v *= dist;
       }
     }
-    if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
-    for (int e = tid; e < nW; e += nth) W[e] = 0.0;
+    for (int e = tid; e < na * na + nDb; e += nth) Dm[e] = rd[1 + e];
+    for (int e = tid; e < nWs; e += nth) W[e] = 0.0;
     __syncthreads();
     // translation along z (Eq. 7 with Eq. 8 coefficients, real basis): only nu = 0 survives,
     // t_A(l1, ma) = E^{la}(ma; l1 ma; 0) |b-a|^{la-l1}, t_B(l2, mb) = E^{lb}(mb; l2 mb; 0) (-|b-a|)^{lb-l2}
@@ -497,8 +542,6 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       }
       tB[e] = v;
     }
-    __syncthreads();
-    build_rotations(lm, Rq, Dm, rot_ptr, rot_terms);
     // coupling (Gaunt) and primitive contraction, in the pair frame
     const int npa = shell_nprim[a], npb = shell_nprim[b];
     const int64_t q0 = pair_ppoff[pr];
@@ -525,44 +568,50 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
         fab[tid] = v;
       }
       __syncthreads();
-      for (int r = tid; r < nW; r += nth) {
+      // rows r of one warp form one group: equal trip counts, one coalesced load per term
+      for (int r = tid; r < nrp; r += nth) {
         const int info = g_rowinfo[r];
-        const int t0 = g_rowptr[r], t1 = g_rowptr[r + 1];
+        const int gi = r >> 5, K = g_grp[2 * gi + 1];
+        const GTerm* tp = g_terms + g_grp[2 * gi] + (r & 31);
         double acc0 = 0.0, acc1 = 0.0;
-        int t = t0;
-        for (; t + 1 < t1; t += 2) {
-          const GTerm g0 = g_terms[t], g1 = g_terms[t + 1];
+        int j = 0;
+        for (; j + 1 < K; j += 2) {
+          const GTerm g0 = tp[32 * j], g1 = tp[32 * j + 32];
           acc0 = fma(g0.coef, Rs[g0.ridx], acc0);
           acc1 = fma(g1.coef, Rs[g1.ridx], acc1);
         }
-        if (t < t1) {
-          const GTerm g0 = g_terms[t];
+        if (j < K) {
+          const GTerm g0 = tp[32 * j];
           acc0 = fma(g0.coef, Rs[g0.ridx], acc0);
         }
-        const double acc = acc0 + acc1;
-        const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
-        W[e] = fma(fab[l1 * (lb + 1) + l2], acc, W[e]);
+        if (info >= 0) {
+          const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
+          W[e] = fma(fab[l1 * (lb + 1) + l2], acc0 + acc1, W[e]);
+        }
       }
     }
     __syncthreads();
-    // V' = t_A W t_B (diagonal in m), first over l2
+    // V' = t_A W t_B (diagonal in m), first over l2.  Threads are ordered by |m| (m = 0, 1, -1,
+    // 2, -2, ...) so that the lanes of a warp run loops of (nearly) equal length.
     for (int e = tid; e < nWa * nb; e += nth) {
-      const int i1 = e / nb, mb = e % nb - lb, amb = mb < 0 ? -mb : mb;
+      const int q = e / nWa, i1 = e - q * nWa;
+      const int amb = (q + 1) >> 1, mb = (q & 1) ? amb : -amb;
       double s = 0.0;
-      for (int l2 = amb; l2 <= lb; ++l2) s = fma(tB[l2 * nb + mb + lb], W[i1 * nWb + l2 * l2 + l2 + mb], s);
-      Zb[e] = s;
+      for (int l2 = amb; l2 <= lb; ++l2) s = fma(tB[l2 * nb + mb + lb], W[i1 * ws + l2 * l2 + l2 + mb], s);
+      Zb[i1 * nb + mb + lb] = s;
     }
     __syncthreads();
     for (int e = tid; e < na * nb; e += nth) {
-      const int ma = e / nb - la, mb = e % nb, ama = ma < 0 ? -ma : ma;
+      const int q = e / nb, mb = e - q * nb;
+      const int ama = (q + 1) >> 1, ma = (q & 1) ? ama : -ama;
       double s = 0.0;
       for (int l1 = ama; l1 <= la; ++l1) s = fma(tA[l1 * na + ma + la], Zb[(l1 * l1 + l1 + ma) * nb + mb], s);
-      Vp[e] = s;
+      Vp[(ma + la) * nb + mb] = s;
     }
     __syncthreads();
     // back to the molecular frame: V = D^{la} V' (D^{lb})^T
-    const double* Da = Dm + rot_doff(la);
-    const double* Db = Dm + rot_doff(lb);
+    const double* Da = Dm;
+    const double* Db = la != lb ? Dm + na * na : Dm;
     for (int e = tid; e < na * nb; e += nth) {
       const int ma = e / nb, mb = e % nb;
       double s = 0.0;
@@ -598,47 +647,45 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
 // w(l1) = sum_ij c~_i c~_j K_ij (beta/p)^{la-l1} (alpha/p)^{lb-l1} 4 pi (pi/2)^{1/2} (2 l1 - 1)!!/(2p)^{l1+3/2};
 // the block is rotated back with D^{la} S' (D^{lb})^T.
 __host__ __device__ inline size_t overlap_smem(int la, int lb) {
-  const int lm = la > lb ? la : lb;
-  return sizeof(double) * ((size_t)rot_doff(lm + 1) + (la + 1) * (2 * la + 1) + (lb + 1) * (2 * lb + 1) +
-                           (2 * la + 1) * (2 * lb + 1) + 2 * (lm + 1) + 32);
+  const int lm = la > lb ? la : lb, na = 2 * la + 1, nb = 2 * lb + 1;
+  return sizeof(double) * ((size_t)na * na + nb * nb + (la + 1) * na + (lb + 1) * nb + na * nb + 2 * (lm + 1) + 32);
 }
 
 __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs, int pair_base,
                                                       const int* __restrict__ pair_a, const int* __restrict__ pair_b,
                                                       const int64_t* __restrict__ pair_ppoff,
-                                                      const double* __restrict__ pair_rot,
-                                                      const double* __restrict__ shell_xyz,
+                                                      int64_t rot_base, const double* __restrict__ rotd,
                                                       const int* __restrict__ shell_nprim,
                                                       const int64_t* __restrict__ shell_foff,
                                                       const double* __restrict__ etab, const int* __restrict__ eoff,
-                                                      const int* __restrict__ rot_ptr,
-                                                      const GTerm* __restrict__ rot_terms,
                                                       const PPData* __restrict__ ppd, MolView mv,
                                                       double* __restrict__ out) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb, ln = la < lb ? la : lb;
-  double* Dm = smem;
-  double* tA = Dm + rot_doff(lm + 1);
+  const int nDb = la != lb ? nb * nb : 0;
+  const int64_t per = rot_per_pair(la, lb);
+  double* Dm = smem;  // D^{la}(Q^T), then D^{lb}(Q^T) when lb != la
+  double* tA = Dm + na * na + nb * nb;
   double* tB = tA + (la + 1) * na;
   double* Vs = tB + (lb + 1) * nb;
   double* wl = Vs + na * nb;   // w(l1)
   double* dpow = wl + lm + 1;  // |b - a|^k
-  double* Rq = dpow + lm + 1;
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
+    const double* rd = rotd + rot_base + (int64_t)w * per;
     __syncthreads();
     if (tid == 0) {
-      const double dist = sqrt(pair_ab2(shell_xyz, a, b));
+      const double dist = rd[0];
       double v = 1.0;
       for (int k = 0; k <= lm; ++k) {
         dpow[k] = v;
         v *= dist;
       }
     }
-    if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
+    for (int e = tid; e < na * na + nDb; e += nth) Dm[e] = rd[1 + e];
     // radial sums over primitive pairs, one l1 per thread
     if (tid <= ln) {
       const int l1 = tid;
@@ -672,11 +719,10 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
                   ? etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr] * ((lr & 1) ? -dpow[lr] : dpow[lr])
                   : 0.0;
     }
-    build_rotations(lm, Rq, Dm, rot_ptr, rot_terms);
     __syncthreads();
     // S = D^{la} S' (D^{lb})^T with S' diagonal in m (|m| <= min(la, lb))
-    const double* Da = Dm + rot_doff(la);
-    const double* Db = Dm + rot_doff(lb);
+    const double* Da = Dm;
+    const double* Db = la != lb ? Dm + na * na : Dm;
     for (int e = tid; e < na * nb; e += nth) {
       const int ma = e / nb, mb = e % nb;
       double s = 0.0;
@@ -738,9 +784,10 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.etab, t.etab);
   if (e == cudaSuccess) e = upload(&d.eoff, t.eoff);
   if (e == cudaSuccess) e = upload(&d.g_rowinfo, t.g_rowinfo);
-  if (e == cudaSuccess) e = upload(&d.g_rowptr, t.g_rowptr);
+  if (e == cudaSuccess) e = upload(&d.g_grp, t.g_grp);
   if (e == cudaSuccess) e = upload(&d.g_terms, t.g_terms);
   if (e == cudaSuccess) e = upload(&d.rmap, t.rmap);
+  if (e == cudaSuccess) e = upload(&d.rnorm, t.rnorm);
   if (e == cudaSuccess) e = upload(&d.rot_ptr, t.rot_ptr);
   if (e == cudaSuccess) e = upload(&d.rot_terms, t.rot_terms);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
@@ -881,21 +928,21 @@ struct Launcher {
     if (nch == 32)
       k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.ppd, db.rbuf);
+          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, dt.rnorm + th.rmap_off[lam], db.pair_rot, db.ppd, db.rbuf);
     else
       k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, s>>>(
           lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, db.pair_rot, db.ppd, db.rbuf);
+          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, dt.rnorm + th.rmap_off[lam], db.pair_rot, db.ppd, db.rbuf);
   }
   void pair(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
     if (w.npairs == 0) return;
     const int cid = class_id(w.la, w.lb);
     const size_t sm = pair_smem(w.la, w.lb);
     k_pair_block<<<grid_cap(w.npairs, 16), threads_of(c, w.la, w.lb), sm, s>>>(
-        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_rot,
-        db.shell_xyz, db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
-        dt.g_rowinfo + th.g_rowbase[cid], dt.g_rowptr + th.g_rowbase[cid], dt.g_terms + th.g_termbase[cid],
-        dt.rot_ptr, dt.rot_terms, db.ppd, db.rbuf, mv, out);
+        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, w.rot_base, db.rotd,
+        db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
+        dt.g_rowinfo + th.g_rowbase[cid], dt.g_grp + 2 * th.g_grpbase[cid], dt.g_terms + th.g_termbase[cid],
+        db.ppd, db.rbuf, mv, out);
   }
 };
 
@@ -906,7 +953,7 @@ std::vector<ClassWork> class_chunks(const ClassWork& w, const int64_t* ppoff, in
   int q = w.pair_base;
   const int qend = w.pair_base + w.npairs;
   while (q < qend) {
-    ClassWork ch{w.la, w.lb, 0, q, 0, ppoff[q]};
+    ClassWork ch{w.la, w.lb, 0, q, 0, ppoff[q], w.rot_base + (int64_t)(q - w.pair_base) * rot_per_pair(w.la, w.lb)};
     int64_t used = 0;
     while (q < qend && (ch.npairs == 0 || used + (ppoff[q + 1] - ppoff[q]) * nR <= region)) {
       used += (ppoff[q + 1] - ppoff[q]) * nR;
@@ -1132,6 +1179,19 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
   return launch_error(err);
 }
 
+shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                                  cudaStream_t stream, std::string* err) {
+  for (const ClassWork& w : work) {
+    if (w.npairs == 0) continue;
+    const int lm = std::max(w.la, w.lb);
+    const size_t sm = sizeof(double) * ((size_t)rot_doff(lm + 1) + 16);
+    k_pair_rotations<<<grid_cap(w.npairs, 16), 64, sm, stream>>>(w.la, w.lb, w.npairs, w.pair_base, w.rot_base,
+                                                                   db.pair_a, db.pair_b, db.pair_rot, db.shell_xyz,
+                                                                   dt.rot_ptr, dt.rot_terms, db.rotd);
+  }
+  return launch_error(err);
+}
+
 shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err) {
   if (npp == 0) return SHGO_OK;
   const int64_t blocks = std::min<int64_t>((npp + 255) / 256, 152 * 32);
@@ -1150,8 +1210,8 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
   for (const ClassWork& w : work) {
     if (w.npairs == 0) continue;
     k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), stream>>>(
-        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_rot, db.shell_xyz,
-        db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, dt.rot_ptr, dt.rot_terms, db.ppd, mv, out);
+        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, w.rot_base, db.rotd,
+        db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
   }
   return launch_error(err);
 }

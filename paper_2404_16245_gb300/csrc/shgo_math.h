@@ -34,6 +34,26 @@ __host__ __device__ inline void solid_harmonics(int lmax, T x, T y, T z, T* out,
   }
 }
 
+// Unnormalised solid harmonics U_lm(u) = S_lm(u) / N_lm of a unit vector u (|u| = 1), l <= lmax,
+// by the one-constant recursion documented with HarmCoef::ng.  Two FP64 operations per entry.
+__host__ __device__ inline void solid_harmonics_unit(int lmax, double x, double y, double z, double* out, int stride,
+                                                     const double* ng) {
+  out[0] = 1.0;
+  if (lmax < 1) return;
+  out[stride * 1] = y;
+  out[stride * 2] = z;
+  out[stride * 3] = x;
+  for (int l = 1; l < lmax; ++l) {
+    const int cur = l * l + l, prv = (l - 1) * (l - 1) + (l - 1), nxt = (l + 1) * (l + 1) + (l + 1);
+    const double sll = out[stride * (cur + l)], slml = out[stride * (cur - l)];
+    out[stride * (nxt + l + 1)] = fma(x, sll, -y * slml);
+    out[stride * (nxt - l - 1)] = fma(y, sll, x * slml);
+    out[stride * (nxt - l)] = z * slml;
+    out[stride * (nxt + l)] = z * sll;
+    for (int m = -l + 1; m < l; ++m) out[stride * (nxt + m)] = fma(ng[cur + m], out[stride * (prv + m)], z * out[stride * (cur + m)]);
+  }
+}
+
 // Constants of the Boys evaluation: 1/k! for the Taylor weights and 1/(2n+1).
 struct BoysConst {
   double inv_fact[kBoysK + 1];
@@ -58,13 +78,13 @@ __host__ __device__ inline double boys_eval(int nmax, double T, double* F, int s
 #endif
     const double dT = double(g) * (1.0 / kBoysInvH) - T;  // = -(T - T_g)
     const double* row = tab + (size_t)g * kBoysStride;
-    double w = 1.0, ftop = row[1 + nmax], ew = 1.0;
+    // Horner in dT with the weights dT/k: sum_k c_k dT^k / k! = c_0 + dT/1 (c_1 + dT/2 (c_2 + ...))
+    double ftop = row[1 + nmax + kBoysK], ew = 1.0;
 #pragma unroll
-    for (int k = 1; k <= kBoysK; ++k) {
-      w *= dT;
-      const double wk = w * bc.inv_fact[k];
-      ftop += row[1 + nmax + k] * wk;
-      ew += wk;
+    for (int k = kBoysK; k >= 1; --k) {
+      const double q = dT * bc.inv_int[k];
+      ftop = fma(ftop, q, row[nmax + k]);
+      ew = fma(ew, q, 1.0);
     }
     const double ex = row[0] * ew;
     F[nmax * stride] = ftop;

@@ -76,9 +76,10 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   const size_t o_etab = pk.add(t.etab.size() * sizeof(double));
   const size_t o_eoff = pk.add(t.eoff.size() * sizeof(int));
   const size_t o_rowinfo = pk.add(t.g_rowinfo.size() * sizeof(int));
-  const size_t o_rowptr = pk.add(t.g_rowptr.size() * sizeof(int));
+  const size_t o_grp = pk.add(t.g_grp.size() * sizeof(int));
   const size_t o_terms = pk.add(t.g_terms.size() * sizeof(GTerm));
   const size_t o_rmap = pk.add(t.rmap.size() * sizeof(int));
+  const size_t o_rnorm = pk.add(t.rnorm.size() * sizeof(double));
   const size_t o_rotptr = pk.add(t.rot_ptr.size() * sizeof(int));
   const size_t o_rotterms = pk.add(t.rot_terms.size() * sizeof(GTerm));
   if (pk.used > kNoallocScratchBytes) {
@@ -93,9 +94,10 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
                 {o_etab, t.etab.data(), t.etab.size() * sizeof(double)},
                 {o_eoff, t.eoff.data(), t.eoff.size() * sizeof(int)},
                 {o_rowinfo, t.g_rowinfo.data(), t.g_rowinfo.size() * sizeof(int)},
-                {o_rowptr, t.g_rowptr.data(), t.g_rowptr.size() * sizeof(int)},
+                {o_grp, t.g_grp.data(), t.g_grp.size() * sizeof(int)},
                 {o_terms, t.g_terms.data(), t.g_terms.size() * sizeof(GTerm)},
                 {o_rmap, t.rmap.data(), t.rmap.size() * sizeof(int)},
+                {o_rnorm, t.rnorm.data(), t.rnorm.size() * sizeof(double)},
                 {o_rotptr, t.rot_ptr.data(), t.rot_ptr.size() * sizeof(int)},
                 {o_rotterms, t.rot_terms.data(), t.rot_terms.size() * sizeof(GTerm)}};
   for (const Piece& p : pieces) {
@@ -111,9 +113,10 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
   d.tabs.etab = reinterpret_cast<double*>(d.base + o_etab);
   d.tabs.eoff = reinterpret_cast<int*>(d.base + o_eoff);
   d.tabs.g_rowinfo = reinterpret_cast<int*>(d.base + o_rowinfo);
-  d.tabs.g_rowptr = reinterpret_cast<int*>(d.base + o_rowptr);
+  d.tabs.g_grp = reinterpret_cast<int*>(d.base + o_grp);
   d.tabs.g_terms = reinterpret_cast<GTerm*>(d.base + o_terms);
   d.tabs.rmap = reinterpret_cast<int*>(d.base + o_rmap);
+  d.tabs.rnorm = reinterpret_cast<double*>(d.base + o_rnorm);
   d.tabs.rot_ptr = reinterpret_cast<int*>(d.base + o_rotptr);
   d.tabs.rot_terms = reinterpret_cast<GTerm*>(d.base + o_rotterms);
   d.tables_end = pk.used;
@@ -203,7 +206,14 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   const size_t o_pppair = pk.add(sizeof(int) * (size_t)npp);
   const size_t o_ppij = pk.add(sizeof(int) * (size_t)npp);
   const size_t host_bytes = pk.used;
+  int64_t rotlen = 0;
+  for (int la = 0; la <= kLmax; ++la)
+    for (int lb = 0; lb <= la; ++lb) {
+      const int64_t pairs = la == lb ? (int64_t)count_l[la] * (count_l[la] + 1) / 2 : (int64_t)count_l[la] * count_l[lb];
+      rotlen += pairs * rot_per_pair(la, lb);
+    }
   const size_t o_ppd = pk.add(sizeof(PPData) * (size_t)npp);
+  const size_t o_rotd = pk.add(sizeof(double) * (size_t)rotlen);
   const size_t o_rbuf = pk.add(sizeof(double) * (size_t)rlen);
   const size_t need = pk.used;
 
@@ -317,7 +327,10 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   db.rbuf = reinterpret_cast<double*>(region + o_rbuf);
   db.rbuf_len = rlen;
   db.ppd = reinterpret_cast<PPData*>(region + o_ppd);
+  db.rotd = reinterpret_cast<double*>(region + o_rotd);
+  if (assign_rot_bases(work) != rotlen) return noalloc_fail(SHGO_ERR_INVALID_ARG, "inconsistent pair count");
   st = launch_pair_build(db, npp, s, &err);
+  if (st == SHGO_OK) st = launch_pair_rotations(db, nd->tabs, work, s, &err);
   if (st != SHGO_OK) return noalloc_fail(st, err);
   st = launch_nuclear_attraction(db, nd->tabs, work, nbf, centers->n, centers->xyz, charges, out, s, &err, nullptr,
                                  /*concurrent=*/false);

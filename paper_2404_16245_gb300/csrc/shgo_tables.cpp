@@ -2,11 +2,12 @@
 // harmonics, the real translation tensors (addition theorem, Eqs. 7-8), the real coupling
 // (Gaunt) programs (Clebsch-Gordan product rule, Supp. Eq. 4), the packed layout of the
 // per-primitive-pair coupling block, and the Boys grid.  Built once per process in long double.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
-#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "shgo_internal.h"
 #include "shgo_math.h"
@@ -139,6 +140,23 @@ const HarmCoef& harm_coef_host() {
         hc.b[k] = (double)std::sqrt((ld)(l + m) * (ld)(l - m) / ((ld)(l + m + 1) * (ld)(l - m + 1)));
       }
     }
+    // N_lm follows the normalised recursion's constants: N_{l+1,m} = a_lm N_lm for |m| <= l,
+    // N_{l+1,+-(l+1)} = c_l N_{l,l}; then gamma_lm = b_lm N_{l-1,m} / (a_lm N_lm)
+    std::vector<ld> N((size_t)(kHarmMax + 1) * (kHarmMax + 1), 0.0L);
+    N[0] = 1.0L;
+    if (kHarmMax >= 1) N[1] = N[2] = N[3] = 1.0L;
+    for (int l = 1; l < kHarmMax; ++l) {
+      const ld cl = std::sqrt((ld)(2 * l + 1) / (ld)(2 * l + 2));
+      N[harm_index(l + 1, l + 1)] = cl * N[harm_index(l, l)];
+      N[harm_index(l + 1, -l - 1)] = cl * N[harm_index(l, -l)];
+      for (int m = -l; m <= l; ++m) {
+        const ld a = (ld)(2 * l + 1) / std::sqrt((ld)(l + m + 1) * (ld)(l - m + 1));
+        const ld b = std::sqrt((ld)(l + m) * (ld)(l - m) / ((ld)(l + m + 1) * (ld)(l - m + 1)));
+        N[harm_index(l + 1, m)] = a * N[harm_index(l, m)];
+        if (m > -l && m < l) hc.ng[harm_index(l, m)] = (double)(-b * N[harm_index(l - 1, m)] / (a * N[harm_index(l, m)]));
+      }
+    }
+    for (size_t k = 0; k < N.size(); ++k) hc.n[k] = (double)N[k];
   });
   return hc;
 }
@@ -209,6 +227,8 @@ void build_tables(Tables& t) {
       boff += km + 1;
     }
   }
+  t.rnorm.resize(t.rmap.size());
+  for (size_t e = 0; e < t.rmap.size(); ++e) t.rnorm[e] = harm_coef_host().n[t.rmap[e] & 0xfff];
   // Rotation recursion lists: Cartesian component c = 0, 1, 2 (x, y, z) is S_{1, m(c)} with
   // m(x) = 1, m(y) = -1, m(z) = 0.
   t.rot_ptr.clear();
@@ -242,14 +262,17 @@ void build_tables(Tables& t) {
             }
         }
   t.g_rowbase.assign(kNumClasses, 0);
+  t.g_grpbase.assign(kNumClasses, 0);
   t.g_termbase.assign(kNumClasses, 0);
+  t.g_nnz.assign(kNumClasses, 0);
   t.g_rowinfo.clear();
-  t.g_rowptr.clear();
+  t.g_grp.clear();
   t.g_terms.clear();
   for (int la = 0; la <= kLmax; ++la)
     for (int lb = 0; lb <= la; ++lb) {
       const int cid = class_id(la, lb), lam = la + lb;
-      t.g_rowbase[cid] = (int)t.g_rowptr.size();
+      t.g_rowbase[cid] = (int)t.g_rowinfo.size();
+      t.g_grpbase[cid] = (int)t.g_grp.size() / 2;
       t.g_termbase[cid] = (int)t.g_terms.size();
       // R index of (L, M, k) in the Lambda layout
       auto ridx = [&](int L, int M, int k) {
@@ -257,31 +280,50 @@ void build_tables(Tables& t) {
         for (int Lp = 0; Lp < L; ++Lp) off += (2 * Lp + 1) * (kmax_of(lam, Lp) + 1);
         return off + (M + L) * (kmax_of(lam, L) + 1) + k;
       };
-      const int nWb = (lb + 1) * (lb + 1);
+      const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb, ws = w_stride(lb);
       std::vector<int> order;
-      for (int i1 = 0; i1 < (la + 1) * (la + 1); ++i1)
+      for (int i1 = 0; i1 < nWa; ++i1)
         for (int i2 = 0; i2 < nWb; ++i2) order.push_back(i1 * nWb + i2);
-      auto count = [&](int e) { return (int)terms[(size_t)(e / nWb) * nh + (e % nWb)].size(); };
-      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count(x) > count(y); });
+      auto row_terms = [&](int e) -> const std::vector<std::pair<int, double>>& {
+        return terms[(size_t)(e / nWb) * nh + (e % nWb)];
+      };
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return row_terms(x).size() > row_terms(y).size(); });
+      const int nrp = (nW + 31) / 32 * 32;
       int local = 0;
-      for (int e : order) {
-        const int i1 = e / nWb, i2 = e % nWb;
-        int l1 = 0, l2 = 0;
-        while ((l1 + 1) * (l1 + 1) <= i1) ++l1;
-        while ((l2 + 1) * (l2 + 1) <= i2) ++l2;
-        t.g_rowinfo.push_back(e | (l1 << 16) | (l2 << 20));
-        t.g_rowptr.push_back(local);
-        for (const auto& tm : terms[(size_t)i1 * nh + i2]) {
-          const int hi = tm.first & 0xfff, k = tm.first >> 12;
-          int L = 0;
-          while ((L + 1) * (L + 1) <= hi) ++L;
-          const int M = hi - L * L - L;
-          t.g_terms.push_back(GTerm{tm.second, ridx(L, M, k), 0});
-          ++local;
+      for (int g0 = 0; g0 < nrp; g0 += 32) {
+        int K = 0;
+        for (int i = 0; i < 32 && g0 + i < nW; ++i) K = std::max(K, (int)row_terms(order[g0 + i]).size());
+        t.g_grp.push_back(local);
+        t.g_grp.push_back(K);
+        for (int j = 0; j < K; ++j)
+          for (int i = 0; i < 32; ++i) {
+            GTerm gt{0.0, 0, 0};
+            if (g0 + i < nW) {
+              const auto& v = row_terms(order[g0 + i]);
+              if (j < (int)v.size()) {
+                const int hi = v[j].first & 0xfff, k = v[j].first >> 12;
+                int L = 0;
+                while ((L + 1) * (L + 1) <= hi) ++L;
+                gt = GTerm{v[j].second, ridx(L, hi - L * L - L, k), 0};
+              }
+            }
+            t.g_terms.push_back(gt);
+          }
+        local += 32 * K;
+        for (int i = 0; i < 32; ++i) {
+          if (g0 + i >= nW) {
+            t.g_rowinfo.push_back(-1);
+            continue;
+          }
+          const int e = order[g0 + i], i1 = e / nWb, i2 = e % nWb;
+          int l1 = 0, l2 = 0;
+          while ((l1 + 1) * (l1 + 1) <= i1) ++l1;
+          while ((l2 + 1) * (l2 + 1) <= i2) ++l2;
+          t.g_rowinfo.push_back((i1 * ws + i2) | (l1 << 16) | (l2 << 20));
+          t.g_nnz[cid] += (int)row_terms(e).size();
         }
       }
-      t.g_rowptr.push_back(local);
-      t.g_rowinfo.push_back(0);  // keeps g_rowinfo aligned with g_rowptr (nW + 1 entries per class)
     }
 }
 
