@@ -1,0 +1,266 @@
+// FP64 coupling kernel (step S2), one instantiation per Lambda = la + lb and nucleus-chunk size.
+//
+// For one primitive pair (one warp) and its nuclei C, in the pair frame with d = C - P:
+//   R'[L,M,k] = 2 pi k! p^{-(k+1)} sum_C Z_C S_LM(d) beta_{L,k}(T) / k!,
+//   beta_{L,k} / k! = sum_{j<=k} T^j / j! F_{L+j}(T),  T = p |d|^2,
+// the radial part of the corrected one-centre integral (Eq. 12 with the same-centre coupling
+// restored) before the Clebsch-Gordan coupling of the pair kernel.  S_LM(d) = |d|^L N_LM U_LM(u)
+// with u = d/|d|; the |d|^L goes with the radial factors (sum_j tau_j G_{L+j}, tau_j = (p|d|)^j/j!,
+// G_n = Z |d|^n F_n) and N_LM with the final scale.
+//
+// A block of two warps works on one primitive pair.  Lane i of both warps owns nucleus i of a chunk
+// of NCH: warp 0 evaluates the Boys values, the radial sums and part of the unit-vector harmonic
+// columns, warp 1 the other columns, every loop unrolled (Lambda is a template parameter, so the
+// recursions run in registers with their constants as immediate operands); they write column i of
+// two shared tables S[h][c] and B[b][c].  Then thread t owns R' entries e = t, t + 64, ...: their
+// sums over the chunk's nuclei read both table rows with 16-byte loads at fixed offsets.  Row
+// stride NCH + 2 doubles keeps those loads free of bank conflicts.  Two warps per block double
+// the warps an SM holds for the same shared memory.
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "shgo_internal.h"
+#include "shgo_math.h"
+
+namespace shgo {
+
+namespace {
+
+__constant__ HarmCoef k_harm;
+__constant__ BoysConst k_boys;
+
+constexpr double kTwoPiC = 6.283185307179586476925286766559;
+
+__host__ __device__ constexpr int cn_harm(int lam) { return (lam + 1) * (lam + 1); }
+__host__ __device__ constexpr int cn_beta(int lam) {
+  int n = 0;
+  for (int L = 0; L <= lam; ++L) n += ((lam - L) >> 1) + 1;
+  return n;
+}
+__host__ __device__ constexpr int cn_r(int lam) { return (lam + 1) * (lam + 2) * (lam + 3) / 6; }
+
+template <int LAM, int NCH>
+struct CouplingShape {
+  static constexpr int nS = cn_harm(LAM), nB = cn_beta(LAM), nR = cn_r(LAM);
+  static constexpr int CS = NCH + 2;  // row stride of the nucleus tables (even: 16-byte rows)
+  static constexpr size_t smem = sizeof(double) * ((size_t)(nS + nB) * CS + nR + 16);
+};
+
+// Harmonic columns: for fixed m the recursion U_{l+1,m} = z U_lm + ng_lm U_{l-1,m} (|m| < l),
+// U_{|m|+1,m} = z U_{|m|,m}, runs on its own once the diagonal U_{|m|,+-|m|} is known, and the
+// diagonal chain U_{l+1,l+1} = x U_ll - y U_{l,-l}, U_{l+1,-l-1} = y U_ll + x U_{l,-l} is two
+// values per level.  Each entry is formed with the same operations as the level-by-level
+// recursion, so a split of the columns between warps changes no result.
+// Columns m in [M0, M1] of U_lm(u), l <= LAM, into col[h * CS] with h = l^2 + l + m.
+template <int LAM, int CS, int M0, int M1>
+__device__ __forceinline__ void harmonic_columns(double x, double y, double z, double* col) {
+  double dp[LAM + 1], dm[LAM + 1];  // U_{l,l}, U_{l,-l}
+  dp[0] = dm[0] = 1.0;
+  if constexpr (LAM >= 1) {
+    dp[1] = x;
+    dm[1] = y;
+#pragma unroll
+    for (int l = 1; l < LAM; ++l) {
+      dp[l + 1] = fma(x, dp[l], -y * dm[l]);
+      dm[l + 1] = fma(y, dp[l], x * dm[l]);
+    }
+  }
+#pragma unroll
+  for (int m = M0; m <= M1; ++m) {
+    const int am = m < 0 ? -m : m;
+    double prv = m < 0 ? dm[am] : dp[am];
+    col[(am * am + am + m) * CS] = prv;
+    if (am + 1 <= LAM) {
+      double cur = z * prv;
+      col[((am + 1) * (am + 1) + am + 1 + m) * CS] = cur;
+#pragma unroll
+      for (int l = am + 1; l < LAM; ++l) {
+        const double nxt = fma(k_harm.ng[l * l + l + m], prv, z * cur);
+        col[((l + 1) * (l + 1) + l + 1 + m) * CS] = nxt;
+        prv = cur;
+        cur = nxt;
+      }
+    }
+  }
+}
+
+// Split point of the harmonic columns between the two warps: warp 0 (which also evaluates the
+// Boys values and radial sums) takes m < split, warp 1 takes m >= split, balancing FP64 operations.
+__host__ __device__ constexpr int column_split(int lam) {
+  const int radial = 5 * 7 + 1 + 3 * lam + 2 * lam + 1 + lam + 2 * (cn_beta(lam) - lam - 1);
+  int best = -lam, best_gap = 1 << 30;
+  for (int ms = -lam; ms <= lam + 1; ++ms) {
+    int w0 = radial, w1 = 0;
+    for (int m = -lam; m <= lam; ++m) (m < ms ? w0 : w1) += 2 * (lam - (m < 0 ? -m : m) + 1);
+    const int gap = w0 > w1 ? w0 - w1 : w1 - w0;
+    if (gap < best_gap) {
+      best_gap = gap;
+      best = ms;
+    }
+  }
+  return best;
+}
+
+template <int NCH, int LAM>
+__global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
+  using Sh = CouplingShape<LAM, NCH>;
+  constexpr int nS = Sh::nS, nR = Sh::nR, CS = Sh::CS;
+  constexpr int MS = column_split(LAM);
+  extern __shared__ __align__(16) double smem[];
+  double* Stab = smem;             // [nS][CS]
+  double* Btab = Stab + nS * CS;   // [nB][CS]
+  double* racc = Btab + Sh::nB * CS;
+  double* scl = racc + nR;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int64_t w = blockIdx.x; w < A.npp; w += gridDim.x) {
+    const int64_t q = A.pp_base + w;
+    const int pr = A.pp_pair[q];
+    const int a = A.pair_a[pr];
+    const PPData pd = A.ppd[q];
+    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
+    // skips such primitive pairs, so their coupling block is not needed
+    if (pd.kab == 0.0) continue;
+    const double p = pd.p;
+    // C - P = (C - A) - (beta/p)(B - A), in the pair frame where B - A is along z
+    const double Ax = A.shell_xyz[3 * a], Ay = A.shell_xyz[3 * a + 1], Az = A.shell_xyz[3 * a + 2];
+    double Q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Q[k] = A.pair_rot[9 * pr + k];
+    __syncthreads();  // the previous primitive pair is done with racc and scl
+    for (int e = tid; e < nR; e += 64) racc[e] = 0.0;
+    int64_t cbeg, ncen;
+    mol_centers(A.mv, pr, cbeg, ncen);
+    for (int64_t c0 = 0; c0 < ncen; c0 += NCH) {
+      __syncthreads();  // the tables of the previous chunk are consumed
+      if (lane < NCH) {
+        double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
+        if (c0 + lane < ncen) {
+          const int64_t c = mol_center_index(A.mv, cbeg + c0 + lane);
+          const double ux = A.centers[3 * c] - Ax, uy = A.centers[3 * c + 1] - Ay, uz = A.centers[3 * c + 2] - Az;
+          dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
+          dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
+          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - pd.shift;
+          z = A.charges[c];
+        }
+        const double s2 = dx * dx + dy * dy + dz * dz;
+        // unit vector and length of d (d = 0 leaves only L = 0, which any unit vector gives)
+        double ex = 0.0, ey = 0.0, ez = 1.0, dn = 0.0;
+        if (s2 > 0.0) {
+          const double ri = rsqrt(s2);
+          dn = s2 * ri;
+          ex = dx * ri;
+          ey = dy * ri;
+          ez = dz * ri;
+        }
+        if (wid == 0) {
+          const double T = p * s2;
+          double F[LAM + 1];
+          boys_eval(LAM, T, F, 1, A.boys_tab, k_boys);
+          // G_n = Z |d|^n F_n and tau_j = (p |d|)^j / j!
+          double zp = z;
+#pragma unroll
+          for (int n = 0; n <= LAM; ++n) {
+            F[n] *= zp;
+            zp *= dn;
+          }
+          double tau[LAM / 2 + 1];
+          tau[0] = 1.0;
+          const double pdn = p * dn;
+#pragma unroll
+          for (int k = 1; k <= LAM / 2; ++k) tau[k] = tau[k - 1] * pdn * k_boys.inv_int[k];
+          // |d|^L beta_{L,k} / k! = sum_{j<=k} tau_j G_{L+j}, running sums over k
+          double* bcol = Btab + lane;
+          int bo = 0;
+#pragma unroll
+          for (int L = 0; L <= LAM; ++L) {
+            double acc = F[L];
+            bcol[bo * CS] = acc;
+#pragma unroll
+            for (int k = 1; k <= (LAM - L) / 2; ++k) {
+              acc = fma(tau[k], F[L + k], acc);
+              bcol[(bo + k) * CS] = acc;
+            }
+            bo += (LAM - L) / 2 + 1;
+          }
+          if constexpr (MS > -LAM) harmonic_columns<LAM, CS, -LAM, MS - 1>(ex, ey, ez, Stab + lane);
+        } else {
+          if constexpr (MS <= LAM) harmonic_columns<LAM, CS, MS, LAM>(ex, ey, ez, Stab + lane);
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < nR; e += 64) {
+        const int code = __ldg(A.rmap + e);
+        const double2* S = reinterpret_cast<const double2*>(Stab + (code & 0xfff) * CS);
+        const double2* B = reinterpret_cast<const double2*>(Btab + ((code >> 12) & 0xfff) * CS);
+        double a0 = racc[e], a1 = 0.0;
+#pragma unroll
+        for (int c = 0; c < NCH / 2; ++c) {
+          const double2 s = S[c], b = B[c];
+          a0 = fma(s.x, b.x, a0);
+          a1 = fma(s.y, b.y, a1);
+        }
+        racc[e] = a0 + a1;
+      }
+    }
+    // scale 2 pi k! p^{-(k+1)} N_LM (each thread scales the entries it accumulated)
+    if (tid <= LAM / 2) {
+      double s = kTwoPiC * pd.rp;
+      for (int k = 1; k <= tid; ++k) s *= double(k) * pd.rp;
+      scl[tid] = s;
+    }
+    __syncthreads();
+    double* out = A.rbuf + A.rbase + w * (int64_t)nR;
+    for (int e = tid; e < nR; e += 64) out[e] = racc[e] * (scl[(__ldg(A.rmap + e) >> 24) & 0xff] * __ldg(A.rnorm + e));
+  }
+}
+
+using CouplingKernel = void (*)(CouplingArgs);
+
+template <int NCH, int... L>
+constexpr CouplingKernel kernel_at(int lam, std::integer_sequence<int, L...>) {
+  CouplingKernel k = nullptr;
+  ((lam == L ? (k = &k_coupling_fp64<NCH, L>, 0) : 0), ...);
+  return k;
+}
+
+template <int NCH, int... L>
+constexpr size_t smem_at(int lam, std::integer_sequence<int, L...>) {
+  size_t s = 0;
+  ((lam == L ? (s = CouplingShape<L, NCH>::smem, 0) : 0), ...);
+  return s;
+}
+
+using Lams = std::make_integer_sequence<int, kLamMax + 1>;
+
+CouplingKernel coupling_kernel(int lam, int nch) {
+  if (lam < 0 || lam > kLamMax) return nullptr;
+  return nch == 16 ? kernel_at<16>(lam, Lams{}) : kernel_at<32>(lam, Lams{});
+}
+
+}  // namespace
+
+size_t coupling_fp64_smem(int lam, int nch) {
+  if (lam < 0 || lam > kLamMax) return 0;
+  return nch == 16 ? smem_at<16>(lam, Lams{}) : smem_at<32>(lam, Lams{});
+}
+
+cudaError_t coupling_fp64_setup() {
+  cudaError_t e = cudaMemcpyToSymbol(k_harm, &harm_coef_host(), sizeof(HarmCoef));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_boys, &boys_const_host(), sizeof(BoysConst));
+  for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam)
+    for (int nch : {16, 32}) {
+      e = cudaFuncSetAttribute(coupling_kernel(lam, nch), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (e != cudaSuccess) break;
+    }
+  return e;
+}
+
+cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream) {
+  const CouplingKernel k = coupling_kernel(lam, nch);
+  if (!k) return cudaErrorInvalidValue;
+  k<<<grid, 64, coupling_fp64_smem(lam, nch), stream>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace shgo

@@ -267,6 +267,28 @@ int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err);
 
+// Arguments of the FP64 coupling kernel for one class (shgo_coupling.cu).
+struct CouplingArgs {
+  int64_t npp = 0, pp_base = 0, rbase = 0;
+  const int* pp_pair = nullptr;
+  const int* pair_a = nullptr;
+  const double* shell_xyz = nullptr;
+  MolView mv;
+  const double* centers = nullptr;
+  const double* charges = nullptr;
+  const double* boys_tab = nullptr;
+  const int* rmap = nullptr;     // R layout of this Lambda
+  const double* rnorm = nullptr; // N_LM per R entry of this Lambda
+  const double* pair_rot = nullptr;
+  const PPData* ppd = nullptr;
+  double* rbuf = nullptr;
+};
+// Launches the Lambda = lam instantiation with nucleus chunks of nch (16 or 32) on `grid` warps.
+cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream);
+size_t coupling_fp64_smem(int lam, int nch);
+// Constants and launch attributes of the FP64 coupling kernels on the current device.
+cudaError_t coupling_fp64_setup();
+
 // Fills db.ppd for the npp primitive pairs (asynchronous on `stream`).
 shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err);
 

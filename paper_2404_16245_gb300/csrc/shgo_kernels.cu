@@ -75,140 +75,8 @@ __global__ void k_pair_build(int64_t npp, const int* __restrict__ pp_pair, const
   }
 }
 
-// Shared-memory bytes of one warp of k_coupling_block.
-__host__ __device__ inline size_t coupling_smem_per_warp(int lam, int nch) {
-  const int rs = (n_harm(lam) + n_beta(lam)) | 1;
-  return sizeof(double) * ((size_t)nch * rs + n_r(lam) + 16);
-}
-
-template <int NCH>
-__global__ void __launch_bounds__(32) k_coupling_block(int lam, int64_t npp, int64_t pp_base, int64_t rbase,
-                                                       const int* __restrict__ pp_pair,
-                                                       const int* __restrict__ pp_ij, const int* __restrict__ pair_a,
-                                                       const int* __restrict__ pair_b,
-                                                       const double* __restrict__ shell_xyz,
-                                                       const int* __restrict__ shell_poff,
-                                                       const int* __restrict__ shell_nprim,
-                                                       const double* __restrict__ prim_exp, MolView mv,
-                                                       const double* __restrict__ centers,
-                                                       const double* __restrict__ charges,
-                                                       const double* __restrict__ boys_tab,
-                                                       const int* __restrict__ rmap,
-                                                       const double* __restrict__ rnorm,
-                                                       const double* __restrict__ pair_rot,
-                                                       const PPData* __restrict__ ppd,
-                                                       double* __restrict__ rbuf) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int nS = n_harm(lam), nB = n_beta(lam), nR = n_r(lam);
-  const int rs = odd_pad(nS + nB);
-  double* rows = smem;
-  double* racc = smem + (size_t)NCH * rs;
-  double* scl = racc + nR;
-  for (int64_t w = blockIdx.x; w < npp; w += gridDim.x) {
-    const int64_t q = pp_base + w;
-    const int pr = pp_pair[q];
-    const int a = pair_a[pr];
-    const PPData pd = ppd[q];
-    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
-    // skips such primitive pairs, so their coupling block is not needed
-    if (pd.kab == 0.0) continue;
-    const double p = pd.p, rp = pd.rp;
-    // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
-    // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
-    const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double shift = pd.shift;  // |P - A|, along z in the pair frame
-    // frame of the pair: Q (b - a) is along z, so the translation of Eq. 7 is diagonal in m
-    double Q[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Q[k] = pair_rot[9 * pr + k];
-    for (int e = lane; e < nR; e += 32) racc[e] = 0.0;
-    int64_t cbeg, ncen;
-    mol_centers(mv, pr, cbeg, ncen);
-    for (int64_t c0 = 0; c0 < ncen; c0 += NCH) {
-      __syncwarp();
-      if (lane < NCH) {
-        double* row = rows + (size_t)lane * rs;
-        const int64_t c = mol_center_index(mv, cbeg + c0 + lane);
-        double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
-        if (c0 + lane < ncen) {
-          const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;
-          dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
-          dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
-          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - shift;
-          z = charges[c];
-        }
-        const double s2 = dx * dx + dy * dy + dz * dz;
-        const double T = p * s2;
-        // unit vector and length of d: S_LM(d) = |d|^L N_LM U_LM(d/|d|), the |d|^L going with the
-        // radial factors (d = 0 leaves only L = 0, which any unit vector gives)
-        double ux = 0.0, uy = 0.0, uz = 1.0, dn = 0.0;
-        if (s2 > 0.0) {
-          const double ri = rsqrt(s2);
-          dn = s2 * ri;
-          ux = dx * ri;
-          uy = dy * ri;
-          uz = dz * ri;
-        }
-        boys_eval(lam, T, row, 1, boys_tab, c_boys);
-        // G_n = Z |d|^n F_n, and tau_j = (p |d|)^j / j! behind it, so that
-        // |d|^L Z sum_j T^j/j! F_{L+j} = sum_j tau_j G_{L+j}
-        double zp = z;
-        for (int n = 0; n <= lam; ++n) {
-          row[n] *= zp;
-          zp *= dn;
-        }
-        double* tk = row + lam + 1;
-        tk[0] = 1.0;
-        const double pdn = p * dn;
-        for (int k = 1; k <= (lam >> 1); ++k) tk[k] = tk[k - 1] * pdn * c_boys.inv_int[k];
-        // |d|^L beta_{L,k} / k! = sum_{j<=k} tau_j G_{L+j}  (running sum over k)
-        double* brow = row + nS;
-        int bo = 0;
-        for (int L = 0; L <= lam; ++L) {
-          const int km = (lam - L) >> 1;
-          double acc = row[L];
-          brow[bo] = acc;
-          for (int k = 1; k <= km; ++k) {
-            acc = fma(tk[k], row[L + k], acc);
-            brow[bo + k] = acc;
-          }
-          bo += km + 1;
-        }
-        solid_harmonics_unit(lam, ux, uy, uz, row, 1, c_harm.ng);
-      }
-      __syncwarp();
-      const int* rm = rmap;
-      for (int e = lane; e < nR; e += 32) {
-        const int code = __ldg(rm + e);
-        const int si = code & 0xfff, bi = nS + ((code >> 12) & 0xfff);
-        // two partial sums over the nuclei of the chunk, the first continuing the running total
-        double a0 = racc[e], a1 = 0.0;
-#pragma unroll
-        for (int c = 0; c < NCH; c += 2) {
-          a0 = fma(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], a0);
-          a1 = fma(rows[(size_t)(c + 1) * rs + si], rows[(size_t)(c + 1) * rs + bi], a1);
-        }
-        racc[e] = a0 + a1;
-      }
-    }
-    // scale 2 pi k! p^{-(k+1)}
-    if (lane <= (lam >> 1)) {
-      double s = kTwoPi * rp;
-      for (int k = 1; k <= lane; ++k) s *= double(k) * rp;
-      scl[lane] = s;
-    }
-    __syncwarp();
-    double* out = rbuf + rbase + w * (int64_t)nR;
-    for (int e = lane; e < nR; e += 32) {
-      out[e] = racc[e] * (scl[(__ldg(rmap + e) >> 24) & 0xff] * __ldg(rnorm + e));
-    }
-    __syncwarp();
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
-// FP32-bulk variant of k_coupling_block.  FP64 stays on the geometry, T = p |d|^2 and the Boys
+// FP32-bulk variant of the FP64 coupling kernel (shgo_coupling.cu).  FP64 stays on the geometry, T = p |d|^2 and the Boys
 // function (tabulated Taylor + downward recursion, or asymptotic start + upward recursion); the
 // per-nucleus bulk (radial factors, solid-harmonic recursion) and the nucleus sums run in FP32.
 // FP32 works on dimensionless quantities so nothing of consequence leaves its exponent range:
@@ -792,6 +660,7 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.rot_terms, t.rot_terms);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
+  if (e == cudaSuccess) e = coupling_fp64_setup();
   if (e == cudaSuccess) {
     int lof[(kLmax + 1) * (kLmax + 1)];
     for (int l = 0; l <= kLmax; ++l)
@@ -813,6 +682,7 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
 shgo_status upload_constants(std::string* err) {
   cudaError_t e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
+  if (e == cudaSuccess) e = coupling_fp64_setup();
   if (e == cudaSuccess) {
     int lof[(kLmax + 1) * (kLmax + 1)];
     for (int l = 0; l <= kLmax; ++l)
@@ -872,8 +742,6 @@ void set_kernel_attributes() {
   std::lock_guard<std::mutex> lk(g_pool_mu);
   if (g_attr_ok[dev]) return;
   const int lim = 227 * 1024;
-  cudaFuncSetAttribute(k_coupling_block<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_coupling_block<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_pair_block, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_coupling_block_f32<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_coupling_block_f32<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -924,15 +792,23 @@ struct Launcher {
 #undef SHGO_F32_ARGS
       return;
     }
-    const size_t sm = coupling_smem_per_warp(lam, nch);
-    if (nch == 32)
-      k_coupling_block<32><<<grid_cap(w.npp, 8), 32, sm, s>>>(
-          lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, dt.rnorm + th.rmap_off[lam], db.pair_rot, db.ppd, db.rbuf);
-    else
-      k_coupling_block<16><<<grid_cap(w.npp, 8), 32, sm, s>>>(
-          lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
-          db.shell_nprim, db.prim_exp, mv, centers, charges, dt.boys, rmap, dt.rnorm + th.rmap_off[lam], db.pair_rot, db.ppd, db.rbuf);
+    CouplingArgs a;
+    a.npp = w.npp;
+    a.pp_base = w.pp_base;
+    a.rbase = rbase;
+    a.pp_pair = db.pp_pair;
+    a.pair_a = db.pair_a;
+    a.shell_xyz = db.shell_xyz;
+    a.mv = mv;
+    a.centers = centers;
+    a.charges = charges;
+    a.boys_tab = dt.boys;
+    a.rmap = rmap;
+    a.rnorm = dt.rnorm + th.rmap_off[lam];
+    a.pair_rot = db.pair_rot;
+    a.ppd = db.ppd;
+    a.rbuf = db.rbuf;
+    launch_coupling_fp64(lam, nch, a, grid_cap(w.npp, 8), s);
   }
   void pair(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
     if (w.npairs == 0) return;
