@@ -278,7 +278,11 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   b->h_pair_mol = pmol;
   std::vector<double> prot(9 * pa.size());
   for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
-  const int64_t rotlen = assign_rot_bases(b->work);
+  std::vector<int> pair_site, site_rep;
+  build_site_pairs(shell_xyz, pa, pb, pair_site, site_rep);
+  b->d.n_sites = (int)site_rep.size();
+  for (int s = 0; s < n_shells; ++s) b->d.rot_lmax = std::max(b->d.rot_lmax, (int)l[s]);
+  const int64_t rotlen = (int64_t)site_rep.size() * rot_block(b->d.rot_lmax);
   int64_t rlen = 0, max_pair_r = 0;
   for (const auto& w : b->work) rlen += w.npp * n_r(w.la + w.lb);
   b->h_ppoff.assign(ppoff.begin(), ppoff.end());
@@ -310,6 +314,8 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_b, pb, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_ppoff, ppoff, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_rot, prot, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_site, pair_site, &err);
+  if (st == SHGO_OK) st = dev_upload(b, &b->d.site_rep, site_rep, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_pair, pp_pair, &err);
   if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_ij, pp_ij, &err);
   if (batch) {
@@ -353,7 +359,7 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   }
   if (st == SHGO_OK) st = device_tables(device, &b->tabs, &err);
   if (st == SHGO_OK) st = launch_pair_build(b->d, ppcount, 0, &err);
-  if (st == SHGO_OK) st = launch_pair_rotations(b->d, *b->tabs, b->work, 0, &err);
+  if (st == SHGO_OK) st = launch_pair_rotations(b->d, *b->tabs, 0, &err);
   if (st == SHGO_OK && cudaDeviceSynchronize() != cudaSuccess) {
     st = SHGO_ERR_CUDA;
     err = "primitive-pair and pair-frame build failed";

@@ -180,14 +180,19 @@ struct ClassWork {
   int pair_base;   // first pair of the class in the pair arrays
   int64_t npp;     // primitive pairs of the class
   int64_t pp_base; // first primitive pair of the class in the primitive-pair arrays
-  int64_t rot_base = 0;  // first double of the class's per-pair rotation blocks in DeviceBasis::rotd
 };
 
-// Per shell pair, from the basis alone, built once per basis by k_pair_rotations: |b - a| followed by
-// the real rotation matrices D^{la}(Q^T) and, when lb != la, D^{lb}(Q^T) (row-major, (2l+1)^2 each).
-__host__ __device__ inline int64_t rot_per_pair(int la, int lb) {
-  return 1 + (int64_t)(2 * la + 1) * (2 * la + 1) + (la != lb ? (int64_t)(2 * lb + 1) * (2 * lb + 1) : 0);
-}
+// Rotations of the pair frames, from the basis alone, built once per basis by k_pair_rotations for
+// every ordered pair of centre positions (A, B) that some shell pair (a on A, b on B) uses:
+// |B - A| followed by the real rotation matrices D^l(Q^T), l = 0..lmax, row-major (2l+1)^2 each,
+// D^l at offset 1 + rot_doff(l).  Shell pairs on the same two centres share one block.
+__host__ __device__ inline int rot_doff(int l) { return l * (2 * l - 1) * (2 * l + 1) / 3; }
+__host__ __device__ inline int64_t rot_block(int lmax) { return 1 + (int64_t)rot_doff(lmax + 1); }
+
+// Ordered centre pairs of the shell pairs (pa[q], pb[q]): pair_site[q] = index of the pair of
+// positions (xyz[pa[q]], xyz[pb[q]]) (exact coordinates), site_rep[i] = one shell pair using pair i.
+void build_site_pairs(const double* shell_xyz, const std::vector<int>& pa, const std::vector<int>& pb,
+                      std::vector<int>& pair_site, std::vector<int>& site_rep);
 
 // Per primitive pair, from the basis alone (Gaussian product, Eq. 5), built once per basis by
 // k_pair_build: p = alpha + beta, 1/p, sqrt(p), K_AB, prefactor c~_i c~_j K_AB, beta/p, alpha/p and
@@ -215,7 +220,11 @@ struct DeviceBasis {
   int* pp_ij = nullptr;          // i << 8 | j
   int64_t* pp_roff = nullptr;    // offset of the pair's coupling block in rbuf
   PPData* ppd = nullptr;         // per primitive pair (class order)
-  double* rotd = nullptr;        // per shell pair: |b - a|, D^{la}, D^{lb} (see rot_per_pair)
+  int* pair_site = nullptr;      // per pair: its ordered centre pair (a block of rotd)
+  double* rotd = nullptr;        // per ordered centre pair: |B - A|, D^0 .. D^rot_lmax (rot_block doubles)
+  int* site_rep = nullptr;       // per ordered centre pair: one shell pair on it
+  int n_sites = 0;               // ordered centre pairs
+  int rot_lmax = 0;              // largest shell l of the basis
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
   int precision = SHGO_PREC_FP64;  // a shgo_precision value
@@ -292,19 +301,8 @@ cudaError_t coupling_fp64_setup();
 // Fills db.ppd for the npp primitive pairs (asynchronous on `stream`).
 shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err);
 
-// Fills db.rotd for every shell pair of `work` (asynchronous on `stream`).
-shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
-                                  cudaStream_t stream, std::string* err);
-
-// Sets w.rot_base for every class and returns the doubles of the rotation buffer.
-inline int64_t assign_rot_bases(std::vector<ClassWork>& work) {
-  int64_t n = 0;
-  for (ClassWork& w : work) {
-    w.rot_base = n;
-    n += (int64_t)w.npairs * rot_per_pair(w.la, w.lb);
-  }
-  return n;
-}
+// Fills db.rotd for every ordered centre pair (asynchronous on `stream`).
+shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt, cudaStream_t stream, std::string* err);
 
 // Launch shape of one class: nucleus chunk of the coupling kernel (16 or 32) and threads per
 // block of the pair kernel (32, 64 or 128); 0 = the default rule.

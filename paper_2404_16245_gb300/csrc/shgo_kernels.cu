@@ -237,8 +237,6 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
   }
 }
 
-// Doubles in D^0 .. D^{l-1} (real rotation matrices stored one after the other).
-__host__ __device__ inline int rot_doff(int l) { return l * (2 * l - 1) * (2 * l + 1) / 3; }
 
 // Shared-memory bytes of one block of k_pair_block.
 __host__ __device__ inline size_t pair_smem(int la, int lb) {
@@ -309,9 +307,9 @@ __device__ void build_rotations(int lm, const double* Rq, double* Dm, const int*
   }
 }
 
-// Once per basis: |b - a| and the rotation matrices D^{la}, D^{lb} of the pair frame of every shell
-// pair of one class (one block per pair; they depend on the shell centres only).
-__global__ void __launch_bounds__(64) k_pair_rotations(int la, int lb, int npairs, int pair_base, int64_t rot_base,
+// Once per basis: |B - A| and the rotation matrices D^0 .. D^lmax of the pair frame of every ordered
+// pair of centres (one block each; they depend on the two positions only).
+__global__ void __launch_bounds__(64) k_pair_rotations(int n_sites, int lmax, const int* __restrict__ site_rep,
                                                        const int* __restrict__ pair_a, const int* __restrict__ pair_b,
                                                        const double* __restrict__ pair_rot,
                                                        const double* __restrict__ shell_xyz,
@@ -319,22 +317,20 @@ __global__ void __launch_bounds__(64) k_pair_rotations(int la, int lb, int npair
                                                        const GTerm* __restrict__ rot_terms, double* __restrict__ rotd) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int lm = la > lb ? la : lb, na = 2 * la + 1, nb = 2 * lb + 1;
-  const int64_t per = rot_per_pair(la, lb);
+  const int64_t per = rot_block(lmax);
+  const int nD = rot_doff(lmax + 1);
   double* Dm = smem;
-  double* Rq = Dm + rot_doff(lm + 1);
-  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
-    const int pr = pair_base + w;
+  double* Rq = Dm + nD;
+  for (int i = blockIdx.x; i < n_sites; i += gridDim.x) {
+    const int pr = site_rep[i];
     __syncthreads();
     if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
     __syncthreads();
-    build_rotations(lm, Rq, Dm, rot_ptr, rot_terms);
+    build_rotations(lmax, Rq, Dm, rot_ptr, rot_terms);
     __syncthreads();
-    double* o = rotd + rot_base + (int64_t)w * per;
+    double* o = rotd + (int64_t)i * per;
     if (tid == 0) o[0] = sqrt(pair_ab2(shell_xyz, pair_a[pr], pair_b[pr]));
-    for (int e = tid; e < na * na; e += nth) o[1 + e] = Dm[rot_doff(la) + e];
-    if (la != lb)
-      for (int e = tid; e < nb * nb; e += nth) o[1 + na * na + e] = Dm[rot_doff(lb) + e];
+    for (int e = tid; e < nD; e += nth) o[1 + e] = Dm[e];
   }
 }
 
@@ -342,7 +338,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     int64_t rbase, const int* __restrict__ pair_a,
                                                     const int* __restrict__ pair_b,
                                                     const int64_t* __restrict__ pair_ppoff,
-                                                    int64_t rot_base, const double* __restrict__ rotd,
+                                                    const int* __restrict__ pair_site, int64_t rot_per,
+                                                    const double* __restrict__ rotd,
                                                     const int* __restrict__ shell_poff,
                                                     const int* __restrict__ shell_nprim,
                                                     const int64_t* __restrict__ shell_foff,
@@ -364,7 +361,6 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb;
   const int nDb = la != lb ? nb * nb : 0;
-  const int64_t per = rot_per_pair(la, lb);
   double* W = smem;                        // [l1 m1][l2 m2], row stride ws
   double* Dm = W + nWs;                    // D^{la}(Q^T), then D^{lb}(Q^T) when lb != la
   double* tA = Dm + na * na + nb * nb;     // [l1][ma]
@@ -379,7 +375,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
-    const double* rd = rotd + rot_base + (int64_t)w * per;
+    const double* rd = rotd + (int64_t)pair_site[pr] * rot_per;
     __syncthreads();
     if (tid == 0) {
       const double dist = rd[0];
@@ -389,7 +385,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
         v *= dist;
       }
     }
-    for (int e = tid; e < na * na + nDb; e += nth) Dm[e] = rd[1 + e];
+    for (int e = tid; e < na * na; e += nth) Dm[e] = rd[1 + rot_doff(la) + e];
+    for (int e = tid; e < nDb; e += nth) Dm[na * na + e] = rd[1 + rot_doff(lb) + e];
     for (int e = tid; e < nWs; e += nth) W[e] = 0.0;
     __syncthreads();
     // translation along z (Eq. 7 with Eq. 8 coefficients, real basis): only nu = 0 survives,
@@ -522,7 +519,8 @@ __host__ __device__ inline size_t overlap_smem(int la, int lb) {
 __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs, int pair_base,
                                                       const int* __restrict__ pair_a, const int* __restrict__ pair_b,
                                                       const int64_t* __restrict__ pair_ppoff,
-                                                      int64_t rot_base, const double* __restrict__ rotd,
+                                                      const int* __restrict__ pair_site, int64_t rot_per,
+                                                      const double* __restrict__ rotd,
                                                       const int* __restrict__ shell_nprim,
                                                       const int64_t* __restrict__ shell_foff,
                                                       const double* __restrict__ etab, const int* __restrict__ eoff,
@@ -533,7 +531,6 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
   const int na = 2 * la + 1, nb = 2 * lb + 1;
   const int lm = la > lb ? la : lb, ln = la < lb ? la : lb;
   const int nDb = la != lb ? nb * nb : 0;
-  const int64_t per = rot_per_pair(la, lb);
   double* Dm = smem;  // D^{la}(Q^T), then D^{lb}(Q^T) when lb != la
   double* tA = Dm + na * na + nb * nb;
   double* tB = tA + (la + 1) * na;
@@ -543,7 +540,7 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
   for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
-    const double* rd = rotd + rot_base + (int64_t)w * per;
+    const double* rd = rotd + (int64_t)pair_site[pr] * rot_per;
     __syncthreads();
     if (tid == 0) {
       const double dist = rd[0];
@@ -553,7 +550,8 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
         v *= dist;
       }
     }
-    for (int e = tid; e < na * na + nDb; e += nth) Dm[e] = rd[1 + e];
+    for (int e = tid; e < na * na; e += nth) Dm[e] = rd[1 + rot_doff(la) + e];
+    for (int e = tid; e < nDb; e += nth) Dm[na * na + e] = rd[1 + rot_doff(lb) + e];
     // radial sums over primitive pairs, one l1 per thread
     if (tid <= ln) {
       const int l1 = tid;
@@ -815,7 +813,8 @@ struct Launcher {
     const int cid = class_id(w.la, w.lb);
     const size_t sm = pair_smem(w.la, w.lb);
     k_pair_block<<<grid_cap(w.npairs, 16), threads_of(c, w.la, w.lb), sm, s>>>(
-        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, w.rot_base, db.rotd,
+        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, rbase, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site,
+        rot_block(db.rot_lmax), db.rotd,
         db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
         dt.g_rowinfo + th.g_rowbase[cid], dt.g_grp + 2 * th.g_grpbase[cid], dt.g_terms + th.g_termbase[cid],
         db.ppd, db.rbuf, mv, out);
@@ -829,7 +828,7 @@ std::vector<ClassWork> class_chunks(const ClassWork& w, const int64_t* ppoff, in
   int q = w.pair_base;
   const int qend = w.pair_base + w.npairs;
   while (q < qend) {
-    ClassWork ch{w.la, w.lb, 0, q, 0, ppoff[q], w.rot_base + (int64_t)(q - w.pair_base) * rot_per_pair(w.la, w.lb)};
+    ClassWork ch{w.la, w.lb, 0, q, 0, ppoff[q]};
     int64_t used = 0;
     while (q < qend && (ch.npairs == 0 || used + (ppoff[q + 1] - ppoff[q]) * nR <= region)) {
       used += (ppoff[q + 1] - ppoff[q]) * nR;
@@ -1055,16 +1054,12 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
   return launch_error(err);
 }
 
-shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
-                                  cudaStream_t stream, std::string* err) {
-  for (const ClassWork& w : work) {
-    if (w.npairs == 0) continue;
-    const int lm = std::max(w.la, w.lb);
-    const size_t sm = sizeof(double) * ((size_t)rot_doff(lm + 1) + 16);
-    k_pair_rotations<<<grid_cap(w.npairs, 16), 64, sm, stream>>>(w.la, w.lb, w.npairs, w.pair_base, w.rot_base,
-                                                                   db.pair_a, db.pair_b, db.pair_rot, db.shell_xyz,
-                                                                   dt.rot_ptr, dt.rot_terms, db.rotd);
-  }
+shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt, cudaStream_t stream, std::string* err) {
+  if (db.n_sites == 0) return SHGO_OK;
+  const size_t sm = sizeof(double) * ((size_t)rot_doff(db.rot_lmax + 1) + 16);
+  k_pair_rotations<<<grid_cap(db.n_sites, 16), 64, sm, stream>>>(db.n_sites, db.rot_lmax, db.site_rep, db.pair_a,
+                                                                   db.pair_b, db.pair_rot, db.shell_xyz, dt.rot_ptr,
+                                                                   dt.rot_terms, db.rotd);
   return launch_error(err);
 }
 
@@ -1086,7 +1081,8 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
   for (const ClassWork& w : work) {
     if (w.npairs == 0) continue;
     k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), stream>>>(
-        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, w.rot_base, db.rotd,
+        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site, rot_block(db.rot_lmax),
+        db.rotd,
         db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
   }
   return launch_error(err);

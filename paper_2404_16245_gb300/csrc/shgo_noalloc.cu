@@ -15,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "shgo_internal.h"
@@ -205,13 +206,19 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   const size_t o_prot = pk.add(sizeof(double) * 9 * (size_t)npairs);
   const size_t o_pppair = pk.add(sizeof(int) * (size_t)npp);
   const size_t o_ppij = pk.add(sizeof(int) * (size_t)npp);
+  const size_t o_psite = pk.add(sizeof(int) * (size_t)npairs);
+  const size_t o_srep = pk.add(sizeof(int) * (size_t)npairs);
   const size_t host_bytes = pk.used;
-  int64_t rotlen = 0;
-  for (int la = 0; la <= kLmax; ++la)
-    for (int lb = 0; lb <= la; ++lb) {
-      const int64_t pairs = la == lb ? (int64_t)count_l[la] * (count_l[la] + 1) / 2 : (int64_t)count_l[la] * count_l[lb];
-      rotlen += pairs * rot_per_pair(la, lb);
-    }
+  // rotation blocks: one per ordered pair of distinct centre positions
+  int lmax_b = 0;
+  for (int s = 0; s < n_shells; ++s) lmax_b = std::max(lmax_b, (int)l[s]);
+  int64_t npos = 0;
+  {
+    std::unordered_set<std::string> pos;
+    for (int s = 0; s < n_shells; ++s) pos.emplace(reinterpret_cast<const char*>(shell_xyz + 3 * s), 3 * sizeof(double));
+    npos = (int64_t)pos.size();
+  }
+  const int64_t rotlen = std::min(npairs, npos * npos) * rot_block(lmax_b);
   const size_t o_ppd = pk.add(sizeof(PPData) * (size_t)npp);
   const size_t o_rotd = pk.add(sizeof(double) * (size_t)rotlen);
   const size_t o_rbuf = pk.add(sizeof(double) * (size_t)rlen);
@@ -303,6 +310,10 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   }
   put(o_pppair, pp_pair.data(), sizeof(int) * pp_pair.size());
   put(o_ppij, pp_ij.data(), sizeof(int) * pp_ij.size());
+  std::vector<int> pair_site, site_rep;
+  build_site_pairs(shell_xyz, pa, pb, pair_site, site_rep);
+  put(o_psite, pair_site.data(), sizeof(int) * pair_site.size());
+  put(o_srep, site_rep.data(), sizeof(int) * site_rep.size());
 
   unsigned char* region = nd->base + nd->tables_end;
   cudaStream_t s = (cudaStream_t)stream;
@@ -328,9 +339,12 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   db.rbuf_len = rlen;
   db.ppd = reinterpret_cast<PPData*>(region + o_ppd);
   db.rotd = reinterpret_cast<double*>(region + o_rotd);
-  if (assign_rot_bases(work) != rotlen) return noalloc_fail(SHGO_ERR_INVALID_ARG, "inconsistent pair count");
+  db.pair_site = reinterpret_cast<int*>(region + o_psite);
+  db.site_rep = reinterpret_cast<int*>(region + o_srep);
+  db.n_sites = (int)site_rep.size();
+  db.rot_lmax = lmax_b;
   st = launch_pair_build(db, npp, s, &err);
-  if (st == SHGO_OK) st = launch_pair_rotations(db, nd->tabs, work, s, &err);
+  if (st == SHGO_OK) st = launch_pair_rotations(db, nd->tabs, s, &err);
   if (st != SHGO_OK) return noalloc_fail(st, err);
   st = launch_nuclear_attraction(db, nd->tabs, work, nbf, centers->n, centers->xyz, charges, out, s, &err, nullptr,
                                  /*concurrent=*/false);

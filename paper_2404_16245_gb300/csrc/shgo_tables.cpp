@@ -7,6 +7,8 @@
 #include <complex>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "shgo_internal.h"
@@ -328,6 +330,31 @@ void build_tables(Tables& t) {
 }
 
 }  // namespace
+
+void build_site_pairs(const double* shell_xyz, const std::vector<int>& pa, const std::vector<int>& pb,
+                      std::vector<int>& pair_site, std::vector<int>& site_rep) {
+  // shells -> positions (bitwise-equal coordinates), then ordered position pairs
+  int nsh = 0;
+  for (size_t q = 0; q < pa.size(); ++q) nsh = std::max(nsh, std::max(pa[q], pb[q]) + 1);
+  std::vector<int> shell_pos(nsh, -1);
+  std::unordered_map<std::string, int> pos;
+  auto pos_of = [&](int s) {
+    if (shell_pos[s] < 0) {
+      const std::string key(reinterpret_cast<const char*>(shell_xyz + 3 * s), 3 * sizeof(double));
+      shell_pos[s] = pos.emplace(key, (int)pos.size()).first->second;
+    }
+    return shell_pos[s];
+  };
+  std::unordered_map<int64_t, int> sp;
+  pair_site.resize(pa.size());
+  site_rep.clear();
+  for (size_t q = 0; q < pa.size(); ++q) {
+    const int64_t key = (int64_t)pos_of(pa[q]) << 32 | (uint32_t)pos_of(pb[q]);
+    const auto ins = sp.emplace(key, (int)site_rep.size());
+    if (ins.second) site_rep.push_back((int)q);
+    pair_site[q] = ins.first->second;
+  }
+}
 
 const Tables& tables_host() {
   static Tables t;
