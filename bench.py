@@ -52,6 +52,23 @@ def _dist():
     return ws, rank, local
 
 
+def replica_seeds(rank: int, replicas: int) -> list:
+    """Replica indices of one rank: ranks hold disjoint, seeded replicas of the workload (the
+    path shards into independent molecules, so ranks exchange nothing but the step time)."""
+    return [rank * replicas + r for r in range(replicas)]
+
+
+def max_over_ranks(total_ms: float, ws: int, device=None) -> float:
+    """Largest timed total over the ranks (the job's wall time for the same per-rank work)."""
+    if ws <= 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -172,7 +189,7 @@ def run_shgo(args, ws, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     R = args.replicas
-    reps = [W.config2(replica=rank * R + r) for r in range(R)]
+    reps = [W.config2(replica=k) for k in replica_seeds(rank, R)]
     prec = {"fp64": shgo.SHGO_PREC_FP64, "fp32": shgo.SHGO_PREC_FP32_BULK}[args.precision]
     bases = [shgo.Basis(b, precision=prec) for b, _, _ in reps]
     cents = [torch.tensor(C, device=dev) for _, C, _ in reps]
@@ -212,10 +229,7 @@ def run_shgo(args, ws, rank, local):
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
-    tot_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(tot_ms, op=dist.ReduceOp.MAX)
-    ms_per_step = float(tot_ms.item()) / args.steps
+    ms_per_step = max_over_ranks(sum(step_ms), ws, dev) / args.steps
     value = ws * triples_per_step / (ms_per_step / 1e3)
 
     # dominant kernel: live phase timings (CUDA events on the launching stream)

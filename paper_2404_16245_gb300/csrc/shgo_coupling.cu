@@ -189,16 +189,28 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
         }
       }
       __syncthreads();
+      // a partial last chunk sums only its occupied columns (rounded up to a pair; empty columns
+      // carry Z = 0 and so add exact zeros)
+      const int nv2 = ncen - c0 >= NCH ? NCH / 2 : (int)((ncen - c0 + 1) >> 1);
       for (int e = tid; e < nR; e += 64) {
         const int code = __ldg(A.rmap + e);
         const double2* S = reinterpret_cast<const double2*>(Stab + (code & 0xfff) * CS);
         const double2* B = reinterpret_cast<const double2*>(Btab + ((code >> 12) & 0xfff) * CS);
         double a0 = racc[e], a1 = 0.0;
+        if (nv2 == NCH / 2) {
 #pragma unroll
-        for (int c = 0; c < NCH / 2; ++c) {
-          const double2 s = S[c], b = B[c];
-          a0 = fma(s.x, b.x, a0);
-          a1 = fma(s.y, b.y, a1);
+          for (int c = 0; c < NCH / 2; ++c) {
+            const double2 s = S[c], b = B[c];
+            a0 = fma(s.x, b.x, a0);
+            a1 = fma(s.y, b.y, a1);
+          }
+        } else {
+#pragma unroll 4
+          for (int c = 0; c < nv2; ++c) {
+            const double2 s = S[c], b = B[c];
+            a0 = fma(s.x, b.x, a0);
+            a1 = fma(s.y, b.y, a1);
+          }
         }
         racc[e] = a0 + a1;
       }

@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
       if (lane < NCH) {
         float* row = rows + (size_t)lane * rs;
         double* F = fscr + (size_t)lane * (lam + 2);
-        const int64_t c = mol_center_index(mv, cbeg + c0 + lane);
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
         if (c0 + lane < ncen) {
+          const int64_t c = mol_center_index(mv, cbeg + c0 + lane);
           const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;
           dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
           dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
@@ -188,13 +188,16 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
                                c_harm.b, c_harm.c);
       }
       __syncwarp();
+      // a partial last chunk sums only its occupied rows (empty rows carry Z = 0)
+      const int nv = ncen - c0 >= NCH ? NCH : (int)(ncen - c0);
+      const int nv2 = (nv + 1) & ~1;
       for (int e = lane; e < nR; e += 32) {
         const int code = __ldg(rmap + e);
         const int si = code & 0xfff, bi = nS + ((code >> 12) & 0xfff);
         float2 acc = racc[e];
         if (COMP) {
 #pragma unroll 4
-          for (int c = 0; c < NCH; ++c) {
+          for (int c = 0; c < nv; ++c) {
             const float x = rows[(size_t)c * rs + si], y = rows[(size_t)c * rs + bi];
             const float prod = x * y;
             acc.y += fmaf(x, y, -prod);  // rounding error of the product
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
         } else {
           float a0 = 0.f, a1 = 0.f;
 #pragma unroll 4
-          for (int c = 0; c < NCH; c += 2) {
+          for (int c = 0; c < nv2; c += 2) {
             a0 = fmaf(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], a0);
             a1 = fmaf(rows[(size_t)(c + 1) * rs + si], rows[(size_t)(c + 1) * rs + bi], a1);
           }

@@ -130,3 +130,24 @@ def test_user_stream(shgo):
     with torch.cuda.stream(s):
         V = gpu_V(shgo, basis, C, Z, stream=s)
     parity.check(V, ref_V(basis, C, Z), what="stream")
+
+
+def test_arbitrary_point_charges(shgo):
+    # external point charges (fractional, negative, off the atoms, some inside the basis region):
+    # the operator is the same sum over charged points, so V must follow the oracle as for nuclei
+    basis = W.random_basis(31, 16, 6, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0)
+    rng = np.random.default_rng(32)
+    C = rng.uniform(-2.0, 5.0, (45, 3))
+    Z = rng.uniform(-1.5, 1.5, 45)
+    parity.check(gpu_V(shgo, basis, C, Z), ref_V(basis, C, Z), what="point charges")
+
+
+def test_linear_in_the_charges(shgo):
+    # V(q1 + 2 q2) = V(q1) + 2 V(q2) for the same positions (exact up to rounding)
+    basis = W.random_basis(33, 10, 5, max_prim=2)
+    rng = np.random.default_rng(34)
+    C = rng.uniform(0.0, 4.0, (37, 3))
+    q1, q2 = rng.uniform(-1, 1, 37), rng.uniform(-1, 1, 37)
+    v = gpu_V(shgo, basis, C, q1 + 2 * q2)
+    v1, v2 = gpu_V(shgo, basis, C, q1), gpu_V(shgo, basis, C, q2)
+    assert np.max(np.abs(v - (v1 + 2 * v2))) <= 1e-12 * np.max(np.abs(v))
