@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -72,23 +73,61 @@ struct shgo_basis {
 };
 
 namespace {
-template <typename T>
-shgo_status dev_upload(shgo_basis* b, T** dst, const std::vector<T>& src, std::string* err) {
-  const size_t bytes = sizeof(T) * (src.empty() ? 1 : src.size());
-  cudaError_t e = cudaMalloc((void**)dst, bytes);
-  if (e != cudaSuccess) {
-    *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+// Packed host image of per-basis arrays (each at a 256-byte aligned offset), followed by device-only
+// regions that kernels fill; the whole arena is one allocation and the image one copy.
+class HostImage {
+ public:
+  template <typename T>
+  size_t put(const T* src, size_t n) {
+    const size_t off = align(bytes_.size());
+    bytes_.resize(off + sizeof(T) * n);
+    if (n) std::memcpy(bytes_.data() + off, src, sizeof(T) * n);
+    return off;
   }
-  b->allocations.push_back(*dst);
-  if (!src.empty()) {
-    e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      *err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
-      return SHGO_ERR_CUDA;
+  template <typename T>
+  size_t put(const std::vector<T>& v) {
+    return put(v.data(), v.size());
+  }
+  // Device-only region after the image (call after every put).
+  size_t reserve(size_t n) {
+    const size_t off = align(std::max(total_, bytes_.size()));
+    total_ = off + std::max<size_t>(n, 1);
+    return off;
+  }
+  const unsigned char* data() const { return bytes_.data(); }
+  size_t size() const { return bytes_.size(); }
+  size_t total() const { return std::max<size_t>(std::max(total_, bytes_.size()), 256); }
+
+ private:
+  static size_t align(size_t x) { return (x + 255) & ~(size_t)255; }
+  std::vector<unsigned char> bytes_;
+  size_t total_ = 0;
+};
+
+// Per-device memory pool for basis arrays: stream-ordered allocations that keep their memory after a
+// basis is freed (release threshold = unlimited), so creating and freeing bases repeatedly does not go
+// back to the driver each time.  All pool operations are ordered on the legacy default stream and the
+// basis build synchronises before use on other streams.
+cudaError_t pool_alloc(int device, void** p, size_t bytes) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (!pools[device]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      cudaError_t e = cudaMemPoolCreate(&pools[device], &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pools[device], cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    pool = pools[device];
   }
-  return SHGO_OK;
+  return cudaMallocFromPoolAsync(p, bytes, pool, 0);
 }
 
 void release(shgo_basis* b) {
@@ -104,7 +143,8 @@ void release(shgo_basis* b) {
   cudaFree(b->scr_clist_off);
   cudaFree(b->scr_clist);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-  for (void* p : b->allocations) cudaFree(p);
+  for (void* p : b->allocations) cudaFreeAsync(p, 0);
+  cudaStreamSynchronize(0);
   cudaSetDevice(prev);
   delete b;
 }
@@ -276,10 +316,9 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   b->h_pair_a = pa;
   b->h_pair_b = pb;
   b->h_pair_mol = pmol;
-  std::vector<double> prot(9 * pa.size());
-  for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
   std::vector<int> pair_site, site_rep;
-  build_site_pairs(shell_xyz, pa, pb, pair_site, site_rep);
+  std::vector<double> site_rot;
+  build_site_pairs(shell_xyz, pa, pb, pair_site, site_rep, site_rot);
   b->d.n_sites = (int)site_rep.size();
   for (int s = 0; s < n_shells; ++s) b->d.rot_lmax = std::max(b->d.rot_lmax, (int)l[s]);
   const int64_t rotlen = (int64_t)site_rep.size() * rot_block(b->d.rot_lmax);
@@ -299,62 +338,89 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   }
   b->d.h_ppoff = b->h_ppoff.data();
 
-  std::vector<double> xyz(shell_xyz, shell_xyz + 3 * (size_t)n_shells);
-  std::vector<int> lv(l, l + n_shells), npv(n_prim, n_prim + n_shells);
+  // one host image of every per-basis array, one device arena (image + device-built data), one copy
   std::vector<int> poffv(poff.begin(), poff.end() - 1);
-  shgo_status st = SHGO_OK;
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_xyz, xyz, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_l, lv, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_nprim, npv, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_poff, poffv, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.shell_foff, foff, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.prim_exp, pexp, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.prim_coef, pcoef, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_a, pa, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_b, pb, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_ppoff, ppoff, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_rot, prot, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pair_site, pair_site, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.site_rep, site_rep, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_pair, pp_pair, &err);
-  if (st == SHGO_OK) st = dev_upload(b, &b->d.pp_ij, pp_ij, &err);
+  HostImage im;
+  const size_t o_xyz = im.put(shell_xyz, 3 * (size_t)n_shells);
+  const size_t o_l = im.put(l, (size_t)n_shells);
+  const size_t o_np = im.put(n_prim, (size_t)n_shells);
+  const size_t o_poff = im.put(poffv);
+  const size_t o_foff = im.put(foff);
+  const size_t o_exp = im.put(pexp);
+  const size_t o_coef = im.put(pcoef);
+  const size_t o_pa = im.put(pa);
+  const size_t o_pb = im.put(pb);
+  const size_t o_ppoff = im.put(ppoff);
+  const size_t o_srot = im.put(site_rot);
+  const size_t o_psite = im.put(pair_site);
+  const size_t o_srep = im.put(site_rep);
+  const size_t o_pppair = im.put(pp_pair);
+  const size_t o_ppij = im.put(pp_ij);
+  size_t o_pmol = 0, o_c0 = 0, o_nc = 0, o_out = 0, o_ld = 0;
   if (batch) {
-    if (st == SHGO_OK) st = dev_upload(b, &b->pair_mol, pmol, &err);
-    if (st == SHGO_OK) st = dev_upload(b, &b->mol_c0_d, b->mol_c0, &err);
-    if (st == SHGO_OK) st = dev_upload(b, &b->mol_nc_d, b->mol_nc, &err);
-    if (st == SHGO_OK) st = dev_upload(b, &b->mol_out_d, b->mol_out, &err);
-    if (st == SHGO_OK) st = dev_upload(b, &b->mol_ld_d, b->mol_nbf, &err);
-    if (st == SHGO_OK && cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
-      st = SHGO_ERR_CUDA;
-      err = "cannot create the capture stream";
+    o_pmol = im.put(pmol);
+    o_c0 = im.put(b->mol_c0);
+    o_nc = im.put(b->mol_nc);
+    o_out = im.put(b->mol_out);
+    o_ld = im.put(b->mol_nbf);
+  }
+  const size_t host_bytes = im.size();
+  const size_t o_ppd = im.reserve(sizeof(PPData) * (size_t)ppcount);
+  const size_t o_rotd = im.reserve(sizeof(double) * (size_t)rotlen);
+  shgo_status st = SHGO_OK;
+  unsigned char* base = nullptr;
+  {
+    cudaError_t e = pool_alloc(device, (void**)&base, im.total());
+    if (e != cudaSuccess) {
+      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+      err = std::string("allocating basis arrays: ") + cudaGetErrorString(e);
+    } else {
+      b->allocations.push_back(base);
+      e = cudaMemcpyAsync(base, im.data(), host_bytes, cudaMemcpyHostToDevice, 0);
+      if (e != cudaSuccess) {
+        st = SHGO_ERR_CUDA;
+        err = std::string("copying the basis arrays: ") + cudaGetErrorString(e);
+      }
     }
+  }
+  if (st == SHGO_OK) {
+    b->d.shell_xyz = reinterpret_cast<double*>(base + o_xyz);
+    b->d.shell_l = reinterpret_cast<int*>(base + o_l);
+    b->d.shell_nprim = reinterpret_cast<int*>(base + o_np);
+    b->d.shell_poff = reinterpret_cast<int*>(base + o_poff);
+    b->d.shell_foff = reinterpret_cast<int64_t*>(base + o_foff);
+    b->d.prim_exp = reinterpret_cast<double*>(base + o_exp);
+    b->d.prim_coef = reinterpret_cast<double*>(base + o_coef);
+    b->d.pair_a = reinterpret_cast<int*>(base + o_pa);
+    b->d.pair_b = reinterpret_cast<int*>(base + o_pb);
+    b->d.pair_ppoff = reinterpret_cast<int64_t*>(base + o_ppoff);
+    b->d.site_rot = reinterpret_cast<double*>(base + o_srot);
+    b->d.pair_site = reinterpret_cast<int*>(base + o_psite);
+    b->d.site_rep = reinterpret_cast<int*>(base + o_srep);
+    b->d.pp_pair = reinterpret_cast<int*>(base + o_pppair);
+    b->d.pp_ij = reinterpret_cast<int*>(base + o_ppij);
+    b->d.ppd = reinterpret_cast<PPData*>(base + o_ppd);
+    b->d.rotd = reinterpret_cast<double*>(base + o_rotd);
+    if (batch) {
+      b->pair_mol = reinterpret_cast<int*>(base + o_pmol);
+      b->mol_c0_d = reinterpret_cast<int64_t*>(base + o_c0);
+      b->mol_nc_d = reinterpret_cast<int64_t*>(base + o_nc);
+      b->mol_out_d = reinterpret_cast<int64_t*>(base + o_out);
+      b->mol_ld_d = reinterpret_cast<int64_t*>(base + o_ld);
+    }
+  }
+  if (batch && st == SHGO_OK && cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    st = SHGO_ERR_CUDA;
+    err = "cannot create the capture stream";
   }
   if (st == SHGO_OK) {
     b->d.rbuf_len = rlen;
-    cudaError_t e = cudaMalloc((void**)&b->d.rbuf, sizeof(double) * (size_t)(rlen > 0 ? rlen : 1));
+    cudaError_t e = pool_alloc(device, (void**)&b->d.rbuf, sizeof(double) * (size_t)(rlen > 0 ? rlen : 1));
     if (e != cudaSuccess) {
       st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
-      err = std::string("cudaMalloc coupling buffer: ") + cudaGetErrorString(e);
+      err = std::string("allocating the coupling buffer: ") + cudaGetErrorString(e);
     } else {
       b->allocations.push_back(b->d.rbuf);
-    }
-  }
-  if (st == SHGO_OK) {
-    cudaError_t e = cudaMalloc((void**)&b->d.ppd, sizeof(PPData) * (size_t)(ppcount > 0 ? ppcount : 1));
-    if (e != cudaSuccess) {
-      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
-      err = std::string("cudaMalloc primitive-pair data: ") + cudaGetErrorString(e);
-    } else {
-      b->allocations.push_back(b->d.ppd);
-    }
-  }
-  if (st == SHGO_OK) {
-    cudaError_t e = cudaMalloc((void**)&b->d.rotd, sizeof(double) * (size_t)(rotlen > 0 ? rotlen : 1));
-    if (e != cudaSuccess) {
-      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
-      err = std::string("cudaMalloc pair rotations: ") + cudaGetErrorString(e);
-    } else {
-      b->allocations.push_back(b->d.rotd);
     }
   }
   if (st == SHGO_OK) st = device_tables(device, &b->tabs, &err);

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
     const double Ax = A.shell_xyz[3 * a], Ay = A.shell_xyz[3 * a + 1], Az = A.shell_xyz[3 * a + 2];
     double Q[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Q[k] = A.pair_rot[9 * pr + k];
+    for (int k = 0; k < 9; ++k) Q[k] = A.site_rot[9 * A.pair_site[pr] + k];
     __syncthreads();  // the previous primitive pair is done with racc and scl
     for (int e = tid; e < nR; e += 64) racc[e] = 0.0;
     int64_t cbeg, ncen;

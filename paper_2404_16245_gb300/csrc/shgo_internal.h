@@ -190,9 +190,10 @@ __host__ __device__ inline int rot_doff(int l) { return l * (2 * l - 1) * (2 * l
 __host__ __device__ inline int64_t rot_block(int lmax) { return 1 + (int64_t)rot_doff(lmax + 1); }
 
 // Ordered centre pairs of the shell pairs (pa[q], pb[q]): pair_site[q] = index of the pair of
-// positions (xyz[pa[q]], xyz[pb[q]]) (exact coordinates), site_rep[i] = one shell pair using pair i.
+// positions (xyz[pa[q]], xyz[pb[q]]) (exact coordinates), site_rep[i] = one shell pair using pair i,
+// site_rot[9 i ..] = its frame Q (pair_frame).
 void build_site_pairs(const double* shell_xyz, const std::vector<int>& pa, const std::vector<int>& pb,
-                      std::vector<int>& pair_site, std::vector<int>& site_rep);
+                      std::vector<int>& pair_site, std::vector<int>& site_rep, std::vector<double>& site_rot);
 
 // Per primitive pair, from the basis alone (Gaussian product, Eq. 5), built once per basis by
 // k_pair_build: p = alpha + beta, 1/p, sqrt(p), K_AB, prefactor c~_i c~_j K_AB, beta/p, alpha/p and
@@ -214,7 +215,7 @@ struct DeviceBasis {
   int* pair_a = nullptr;
   int* pair_b = nullptr;
   int64_t* pair_ppoff = nullptr;  // first primitive pair of the pair
-  double* pair_rot = nullptr;     // per pair, 3x3 row-major Q with Q (b - a)/|b - a| = z (identity if a = b)
+  double* site_rot = nullptr;     // per ordered centre pair, 3x3 row-major Q with Q (B - A)/|B - A| = z (identity if A = B)
   // primitive pairs, class-sorted: owning pair, i (prim of a), j (prim of b)
   int* pp_pair = nullptr;
   int* pp_ij = nullptr;          // i << 8 | j
@@ -288,7 +289,8 @@ struct CouplingArgs {
   const double* boys_tab = nullptr;
   const int* rmap = nullptr;     // R layout of this Lambda
   const double* rnorm = nullptr; // N_LM per R entry of this Lambda
-  const double* pair_rot = nullptr;
+  const double* site_rot = nullptr;
+  const int* pair_site = nullptr;
   const PPData* ppd = nullptr;
   double* rbuf = nullptr;
 };

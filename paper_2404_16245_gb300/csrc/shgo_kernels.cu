@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
                                                            const double* __restrict__ charges,
                                                            const double* __restrict__ boys_tab,
                                                            const int* __restrict__ rmap,
-                                                           const double* __restrict__ pair_rot,
+                                                           const double* __restrict__ site_rot,
+                                                           const int* __restrict__ pair_site,
                                                            const PPData* __restrict__ ppd,
                                                            double* __restrict__ rbuf) {
   extern __shared__ double smem[];
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
     const double sp = pd.sp;
     double Q[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Q[k] = pair_rot[9 * pr + k];
+    for (int k = 0; k < 9; ++k) Q[k] = site_rot[9 * pair_site[pr] + k];
     for (int e = lane; e < nR; e += 32) racc[e] = make_float2(0.f, 0.f);
     int64_t cbeg, ncen;
     mol_centers(mv, pr, cbeg, ncen);
@@ -314,7 +315,7 @@ __device__ void build_rotations(int lm, const double* Rq, double* Dm, const int*
 // pair of centres (one block each; they depend on the two positions only).
 __global__ void __launch_bounds__(64) k_pair_rotations(int n_sites, int lmax, const int* __restrict__ site_rep,
                                                        const int* __restrict__ pair_a, const int* __restrict__ pair_b,
-                                                       const double* __restrict__ pair_rot,
+                                                       const double* __restrict__ site_rot,
                                                        const double* __restrict__ shell_xyz,
                                                        const int* __restrict__ rot_ptr,
                                                        const GTerm* __restrict__ rot_terms, double* __restrict__ rotd) {
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(64) k_pair_rotations(int n_sites, int lmax, co
   for (int i = blockIdx.x; i < n_sites; i += gridDim.x) {
     const int pr = site_rep[i];
     __syncthreads();
-    if (tid < 9) Rq[tid] = pair_rot[9 * pr + (tid % 3) * 3 + tid / 3];
+    if (tid < 9) Rq[tid] = site_rot[9 * i + (tid % 3) * 3 + tid / 3];
     __syncthreads();
     build_rotations(lmax, Rq, Dm, rot_ptr, rot_terms);
     __syncthreads();
@@ -780,7 +781,7 @@ struct Launcher {
       const int grid = grid_cap(w.npp, 16);
 #define SHGO_F32_ARGS                                                                                              \
   lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.prim_exp, \
-      mv, centers, charges, dt.boys, rmap, db.pair_rot, db.ppd, db.rbuf
+      mv, centers, charges, dt.boys, rmap, db.site_rot, db.pair_site, db.ppd, db.rbuf
       const bool comp = db.precision == SHGO_PREC_FP32_BULK;
       if (nch == 32 && comp)
         k_coupling_block_f32<32, true><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
@@ -806,7 +807,8 @@ struct Launcher {
     a.boys_tab = dt.boys;
     a.rmap = rmap;
     a.rnorm = dt.rnorm + th.rmap_off[lam];
-    a.pair_rot = db.pair_rot;
+    a.site_rot = db.site_rot;
+    a.pair_site = db.pair_site;
     a.ppd = db.ppd;
     a.rbuf = db.rbuf;
     launch_coupling_fp64(lam, nch, a, grid_cap(w.npp, 8), s);
@@ -1061,7 +1063,7 @@ shgo_status launch_pair_rotations(const DeviceBasis& db, const DeviceTables& dt,
   if (db.n_sites == 0) return SHGO_OK;
   const size_t sm = sizeof(double) * ((size_t)rot_doff(db.rot_lmax + 1) + 16);
   k_pair_rotations<<<grid_cap(db.n_sites, 16), 64, sm, stream>>>(db.n_sites, db.rot_lmax, db.site_rep, db.pair_a,
-                                                                   db.pair_b, db.pair_rot, db.shell_xyz, dt.rot_ptr,
+                                                                   db.pair_b, db.site_rot, db.shell_xyz, dt.rot_ptr,
                                                                    dt.rot_terms, db.rotd);
   return launch_error(err);
 }

@@ -203,7 +203,7 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   const size_t o_pa = pk.add(sizeof(int) * (size_t)npairs);
   const size_t o_pb = pk.add(sizeof(int) * (size_t)npairs);
   const size_t o_ppoff = pk.add(sizeof(int64_t) * (size_t)npairs);
-  const size_t o_prot = pk.add(sizeof(double) * 9 * (size_t)npairs);
+  const size_t o_srot = pk.add(sizeof(double) * 9 * (size_t)npairs);
   const size_t o_pppair = pk.add(sizeof(int) * (size_t)npp);
   const size_t o_ppij = pk.add(sizeof(int) * (size_t)npp);
   const size_t o_psite = pk.add(sizeof(int) * (size_t)npairs);
@@ -303,17 +303,14 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   put(o_pa, pa.data(), sizeof(int) * pa.size());
   put(o_pb, pb.data(), sizeof(int) * pb.size());
   put(o_ppoff, ppoff.data(), sizeof(int64_t) * ppoff.size());
-  {
-    std::vector<double> prot(9 * pa.size());
-    for (size_t q = 0; q < pa.size(); ++q) pair_frame(shell_xyz + 3 * pa[q], shell_xyz + 3 * pb[q], &prot[9 * q]);
-    put(o_prot, prot.data(), sizeof(double) * prot.size());
-  }
   put(o_pppair, pp_pair.data(), sizeof(int) * pp_pair.size());
   put(o_ppij, pp_ij.data(), sizeof(int) * pp_ij.size());
   std::vector<int> pair_site, site_rep;
-  build_site_pairs(shell_xyz, pa, pb, pair_site, site_rep);
+  std::vector<double> site_rot;
+  build_site_pairs(shell_xyz, pa, pb, pair_site, site_rep, site_rot);
   put(o_psite, pair_site.data(), sizeof(int) * pair_site.size());
   put(o_srep, site_rep.data(), sizeof(int) * site_rep.size());
+  put(o_srot, site_rot.data(), sizeof(double) * site_rot.size());
 
   unsigned char* region = nd->base + nd->tables_end;
   cudaStream_t s = (cudaStream_t)stream;
@@ -332,7 +329,7 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   db.pair_a = reinterpret_cast<int*>(region + o_pa);
   db.pair_b = reinterpret_cast<int*>(region + o_pb);
   db.pair_ppoff = reinterpret_cast<int64_t*>(region + o_ppoff);
-  db.pair_rot = reinterpret_cast<double*>(region + o_prot);
+  db.site_rot = reinterpret_cast<double*>(region + o_srot);
   db.pp_pair = reinterpret_cast<int*>(region + o_pppair);
   db.pp_ij = reinterpret_cast<int*>(region + o_ppij);
   db.rbuf = reinterpret_cast<double*>(region + o_rbuf);

@@ -332,28 +332,44 @@ void build_tables(Tables& t) {
 }  // namespace
 
 void build_site_pairs(const double* shell_xyz, const std::vector<int>& pa, const std::vector<int>& pb,
-                      std::vector<int>& pair_site, std::vector<int>& site_rep) {
+                      std::vector<int>& pair_site, std::vector<int>& site_rep, std::vector<double>& site_rot) {
   // shells -> positions (bitwise-equal coordinates), then ordered position pairs
   int nsh = 0;
   for (size_t q = 0; q < pa.size(); ++q) nsh = std::max(nsh, std::max(pa[q], pb[q]) + 1);
   std::vector<int> shell_pos(nsh, -1);
   std::unordered_map<std::string, int> pos;
-  auto pos_of = [&](int s) {
-    if (shell_pos[s] < 0) {
-      const std::string key(reinterpret_cast<const char*>(shell_xyz + 3 * s), 3 * sizeof(double));
-      shell_pos[s] = pos.emplace(key, (int)pos.size()).first->second;
-    }
-    return shell_pos[s];
-  };
-  std::unordered_map<int64_t, int> sp;
+  for (size_t q = 0; q < pa.size(); ++q)
+    for (const int s : {pa[q], pb[q]})
+      if (shell_pos[s] < 0) {
+        const std::string key(reinterpret_cast<const char*>(shell_xyz + 3 * s), 3 * sizeof(double));
+        shell_pos[s] = pos.emplace(key, (int)pos.size()).first->second;
+      }
+  const int64_t np = (int64_t)pos.size();
   pair_site.resize(pa.size());
   site_rep.clear();
-  for (size_t q = 0; q < pa.size(); ++q) {
-    const int64_t key = (int64_t)pos_of(pa[q]) << 32 | (uint32_t)pos_of(pb[q]);
-    const auto ins = sp.emplace(key, (int)site_rep.size());
-    if (ins.second) site_rep.push_back((int)q);
-    pair_site[q] = ins.first->second;
+  auto add = [&](size_t q) {
+    site_rep.push_back((int)q);
+    return (int)site_rep.size() - 1;
+  };
+  if (np * np <= ((int64_t)1 << 24)) {
+    std::vector<int> table((size_t)(np * np), -1);
+    for (size_t q = 0; q < pa.size(); ++q) {
+      int& t = table[(size_t)(shell_pos[pa[q]] * np + shell_pos[pb[q]])];
+      if (t < 0) t = add(q);
+      pair_site[q] = t;
+    }
+  } else {
+    std::unordered_map<int64_t, int> sp;
+    for (size_t q = 0; q < pa.size(); ++q) {
+      const int64_t key = (int64_t)shell_pos[pa[q]] * np + shell_pos[pb[q]];
+      auto it = sp.find(key);
+      if (it == sp.end()) it = sp.emplace(key, add(q)).first;
+      pair_site[q] = it->second;
+    }
   }
+  site_rot.resize(9 * site_rep.size());
+  for (size_t i = 0; i < site_rep.size(); ++i)
+    pair_frame(shell_xyz + 3 * pa[site_rep[i]], shell_xyz + 3 * pb[site_rep[i]], &site_rot[9 * i]);
 }
 
 const Tables& tables_host() {
