@@ -40,41 +40,130 @@ __device__ void stage_weights(const __nv_bfloat16* __restrict__ wq, const float*
   (void)bias_src;
 }
 
-// Network output for one standardised input row (weights staged in shared memory).
-__device__ __forceinline__ float mlp_eval(const float* __restrict__ sw, const float* x) {
-  float a1[kH];
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float z = sw[kOffB1 + j];
-#pragma unroll
-    for (int k = 0; k < kIn; ++k) z = fmaf(sw[kOffW1 + j * kIn + k], x[k], z);
-    a1[j] = silu(z);
-  }
-  float out = sw[kOffB3];
-  for (int j = 0; j < kH; ++j) {
-    float z = sw[kOffB2 + j];
-#pragma unroll
-    for (int k = 0; k < kH; ++k) z = fmaf(sw[kOffW2 + j * kH + k], a1[k], z);
-    out = fmaf(sw[kOffW3 + j], silu(z), out);
-  }
-  return out;
+// ---------------------------------------------------------------------------------------------
+// Tensor-core inference: one warp evaluates 32 samples with mma.sync m16n8k16 (BF16 inputs, FP32
+// accumulation).  The weights are BF16 already; each FP32 activation is split into a BF16 high part
+// and a BF16 low part (x = hi + lo to about 2^-16 relative) and both are multiplied, so the result
+// follows the FP32-activation forward pass to ~1e-5 instead of BF16 rounding of the activations.
+// Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A rows g and g + 8, columns 2t, 2t + 1
+// and 2t + 8, 2t + 9; B columns g, rows 2t, 2t + 1 and 2t + 8, 2t + 9; C/D rows g and g + 8,
+// columns 2t, 2t + 1.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Inference: one sample per thread.
+__device__ __forceinline__ uint32_t pack_bf16(float lo_col, float hi_col) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_col, hi_col);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// hi/lo BF16 split of two FP32 values (the lower column first).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const float h0 = __bfloat162float(__float2bfloat16_rn(x0)), h1 = __bfloat162float(__float2bfloat16_rn(x1));
+  hi = pack_bf16(h0, h1);
+  lo = pack_bf16(x0 - h0, x1 - h1);
+}
+
+__device__ __forceinline__ uint32_t ldw2(const __nv_bfloat16* w, int i) {  // i even
+  return *reinterpret_cast<const uint32_t*>(w + i);
+}
+
+// Outputs of 32 standardised samples xs[32][kIn] (shared, this warp's) into ys[32] (shared).
+// Every lane of the warp must call it.
+__device__ void mlp_eval_warp(const __nv_bfloat16* __restrict__ wq, const float* xs, float* ys) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float out[2][2];  // [m tile][row g, g + 8] partial sums over this thread's columns
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    // layer 1: A = x (16 samples x 16 features), one k step
+    const float* r0 = xs + (16 * mt + g) * kIn;
+    const float* r1 = xs + (16 * mt + g + 8) * kIn;
+    uint32_t ah[4], al[4];
+    split2(r0[2 * t], r0[2 * t + 1], ah[0], al[0]);
+    split2(r1[2 * t], r1[2 * t + 1], ah[1], al[1]);
+    split2(r0[2 * t + 8], r0[2 * t + 9], ah[2], al[2]);
+    split2(r1[2 * t + 8], r1[2 * t + 9], ah[3], al[3]);
+    // hidden layer 1 (64 = 8 n tiles), SiLU, then split into the A fragments of layer 2
+    uint32_t h2h[4][4], h2l[4][4];  // [k step][fragment register]
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int j = 8 * nt + g;  // output unit held as B column
+      const uint32_t b0 = ldw2(wq, kOffW1 + j * kIn + 2 * t), b1 = ldw2(wq, kOffW1 + j * kIn + 2 * t + 8);
+      const float bias0 = __bfloat162float(wq[kOffB1 + 8 * nt + 2 * t]);
+      const float bias1 = __bfloat162float(wq[kOffB1 + 8 * nt + 2 * t + 1]);
+      float d[4] = {bias0, bias1, bias0, bias1};
+      mma_bf16(d, ah, b0, b1);
+      mma_bf16(d, al, b0, b1);
+      // D tile nt covers hidden units 8 nt .. 8 nt + 7 = columns of k step nt / 2
+      const int kk = nt >> 1, half = nt & 1;
+      split2(silu(d[0]), silu(d[1]), h2h[kk][2 * half], h2l[kk][2 * half]);
+      split2(silu(d[2]), silu(d[3]), h2h[kk][2 * half + 1], h2l[kk][2 * half + 1]);
+    }
+    // hidden layer 2 and the output unit
+    float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int j = 8 * nt + g;
+      const float bias0 = __bfloat162float(wq[kOffB2 + 8 * nt + 2 * t]);
+      const float bias1 = __bfloat162float(wq[kOffB2 + 8 * nt + 2 * t + 1]);
+      float d[4] = {bias0, bias1, bias0, bias1};
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t b0 = ldw2(wq, kOffW2 + j * kH + 16 * kk + 2 * t);
+        const uint32_t b1 = ldw2(wq, kOffW2 + j * kH + 16 * kk + 2 * t + 8);
+        mma_bf16(d, h2h[kk], b0, b1);
+        mma_bf16(d, h2l[kk], b0, b1);
+      }
+      const float w30 = __bfloat162float(wq[kOffW3 + 8 * nt + 2 * t]);
+      const float w31 = __bfloat162float(wq[kOffW3 + 8 * nt + 2 * t + 1]);
+      o0 = fmaf(w31, silu(d[1]), fmaf(w30, silu(d[0]), o0));
+      o1 = fmaf(w31, silu(d[3]), fmaf(w30, silu(d[2]), o1));
+    }
+    out[mt][0] = o0;
+    out[mt][1] = o1;
+  }
+  // sum the four threads of each row
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v = out[mt][h];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      out[mt][h] = v;
+    }
+  if (t == 0) {
+    const float b3 = __bfloat162float(wq[kOffB3]);
+    ys[g] = out[0][0] + b3;
+    ys[g + 8] = out[0][1] + b3;
+    ys[16 + g] = out[1][0] + b3;
+    ys[24 + g] = out[1][1] + b3;
+  }
+  __syncwarp();
+}
+
+// Inference: one warp per 32 samples on the tensor cores.
 __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ X, int64_t n,
                                                      const __nv_bfloat16* __restrict__ wq,
                                                      const float* __restrict__ norm,  // mean[16], 1/sd[16]
                                                      float* __restrict__ y) {
-  __shared__ float sw[kNParam];
-  __shared__ float snorm[2 * kIn];
-  stage_weights(wq, nullptr, sw);
-  for (int i = threadIdx.x; i < 2 * kIn; i += blockDim.x) snorm[i] = norm[i];
-  __syncthreads();
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    float x[kIn];
+  __shared__ float sxs[4][32 * kIn];
+  __shared__ float sys[4][32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int64_t warp = blockIdx.x * 4ll + wi, nwarps = (int64_t)gridDim.x * 4;
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t s = base + lane;
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) x[k] = (X[s * kIn + k] - snorm[k]) * snorm[kIn + k];
-    y[s] = mlp_eval(sw, x);
+    for (int k = 0; k < kIn; ++k) sxs[wi][lane * kIn + k] = s < n ? (X[s * kIn + k] - norm[k]) * norm[kIn + k] : 0.f;
+    __syncwarp();
+    mlp_eval_warp(wq, sxs[wi], sys[wi]);
+    if (s < n) y[s] = sys[wi][lane];
+    __syncwarp();
   }
 }
 
@@ -211,7 +300,9 @@ struct PairFeat {
   double Pmin[3], pmin, A[3], B[3];
 };
 
-__device__ void pair_features(const ScreenBasis& sb, int pr, PairFeat& pf) {
+// lane / nlanes split the primitive-pair sum of the overlap scale over the lanes of a warp
+// (nlanes = 32: every lane of the warp must call, and all receive the full sum).
+__device__ void pair_features(const ScreenBasis& sb, int pr, PairFeat& pf, int lane = 0, int nlanes = 1) {
   const int a = sb.pair_a[pr], b = sb.pair_b[pr];
   const int la = sb.shell_l[a], lb = sb.shell_l[b];
   const int pa = sb.shell_poff[a], pb = sb.shell_poff[b], na = sb.shell_nprim[a], nb = sb.shell_nprim[b];
@@ -233,12 +324,14 @@ __device__ void pair_features(const ScreenBasis& sb, int pr, PairFeat& pf) {
     ab2 += (pf.B[c] - pf.A[c]) * (pf.B[c] - pf.A[c]);
   }
   double ovl = 0;
-  for (int i = 0; i < na; ++i)
-    for (int j = 0; j < nb; ++j) {
-      const double ea = sb.prim_exp[pa + i], eb = sb.prim_exp[pb + j], p = ea + eb;
-      const double sp = 3.14159265358979323846 / p;
-      ovl += fabs(sb.prim_coef[pa + i] * sb.prim_coef[pb + j]) * exp(-ea * eb / p * ab2) * sp * sqrt(sp);
-    }
+  for (int ij = lane; ij < na * nb; ij += nlanes) {
+    const int i = ij / nb, j = ij - (ij / nb) * nb;
+    const double ea = sb.prim_exp[pa + i], eb = sb.prim_exp[pb + j], p = ea + eb;
+    const double sp = 3.14159265358979323846 / p;
+    ovl += fabs(sb.prim_coef[pa + i] * sb.prim_coef[pb + j]) * exp(-ea * eb / p * ab2) * sp * sqrt(sp);
+  }
+  if (nlanes == 32)
+    for (int o = 16; o > 0; o >>= 1) ovl += __shfl_xor_sync(0xffffffffu, ovl, o);
   const double pmin = amin + bmin;
   pf.pmin = pmin;
   for (int c = 0; c < 3; ++c) pf.Pmin[c] = (amin * pf.A[c] + bmin * pf.B[c]) / pmin;
@@ -255,20 +348,23 @@ __device__ void pair_features(const ScreenBasis& sb, int pr, PairFeat& pf) {
   pf.f[15] = (float)log10(ovl + 1e-300);
 }
 
+// Nucleus-dependent features in FP32 (only the coordinate differences are formed in FP64): they
+// are network inputs, and FP64 square roots and logarithms are costly on this GPU.
 __device__ void nucleus_features(const PairFeat& pf, const double* C, double Z, float* x) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) x[k] = pf.f[k];
-  double pc2 = 0, ac2 = 0, bc2 = 0;
+  float pc2 = 0.f, ac2 = 0.f, bc2 = 0.f;
   for (int c = 0; c < 3; ++c) {
-    pc2 += (pf.Pmin[c] - C[c]) * (pf.Pmin[c] - C[c]);
-    ac2 += (pf.A[c] - C[c]) * (pf.A[c] - C[c]);
-    bc2 += (pf.B[c] - C[c]) * (pf.B[c] - C[c]);
+    const float dp = (float)(pf.Pmin[c] - C[c]), da = (float)(pf.A[c] - C[c]), db = (float)(pf.B[c] - C[c]);
+    pc2 = fmaf(dp, dp, pc2);
+    ac2 = fmaf(da, da, ac2);
+    bc2 = fmaf(db, db, bc2);
   }
-  x[8] = (float)sqrt(pc2);
-  x[9] = (float)log10(1.0 + pf.pmin * pc2);
-  x[10] = (float)log10(fmax(Z, 1e-300));
-  x[13] = (float)sqrt(ac2);
-  x[14] = (float)sqrt(bc2);
+  x[8] = sqrtf(pc2);
+  x[9] = log10f(fmaf((float)pf.pmin, pc2, 1.f));
+  x[10] = log10f(fmaxf((float)Z, 1e-30f));
+  x[13] = sqrtf(ac2);
+  x[14] = sqrtf(bc2);
 }
 
 __global__ void k_screen_features(ScreenBasis sb, const double* __restrict__ centers,
@@ -293,14 +389,14 @@ __global__ void __launch_bounds__(128) k_screen_pairs(ScreenBasis sb, int64_t np
                                                      const float* __restrict__ norm, float cut, int pass,
                                                      uint8_t* __restrict__ mask, int64_t* __restrict__ counts,
                                                      int* __restrict__ clist) {
-  __shared__ float sw[kNParam];
   __shared__ float snorm[2 * kIn];
+  __shared__ float sxs[4][32 * kIn];
+  __shared__ float sys[4][32];
   if (pass == 0) {
-    stage_weights(wq, nullptr, sw);
     for (int i = threadIdx.x; i < 2 * kIn; i += blockDim.x) snorm[i] = norm[i];
     __syncthreads();
   }
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int64_t warp = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t pr = warp; pr < npairs; pr += nwarps) {
@@ -316,20 +412,27 @@ __global__ void __launch_bounds__(128) k_screen_pairs(ScreenBasis sb, int64_t np
     const int64_t moff = sb.mask_off[pr];
     if (pass == 0) {
       PairFeat pf;
-      pair_features(sb, (int)pr, pf);
+      pair_features(sb, (int)pr, pf, lane, 32);
       int64_t kept = 0;
       for (int64_t k0 = 0; k0 < nc; k0 += 32) {
         const int64_t k = k0 + lane;
-        bool keep = false;
+        float x[16];
         if (k < nc) {
-          float x[16];
           nucleus_features(pf, centers + 3 * (c0 + k), charges[c0 + k], x);
 #pragma unroll
           for (int q = 0; q < kIn; ++q) x[q] = (x[q] - snorm[q]) * snorm[kIn + q];
-          keep = mlp_eval(sw, x) >= cut;
-          mask[moff + k] = keep ? 1 : 0;
+        } else {
+#pragma unroll
+          for (int q = 0; q < kIn; ++q) x[q] = 0.f;
         }
+#pragma unroll
+        for (int q = 0; q < kIn; ++q) sxs[wi][lane * kIn + q] = x[q];
+        __syncwarp();
+        mlp_eval_warp(wq, sxs[wi], sys[wi]);  // all lanes
+        const bool keep = k < nc && sys[wi][lane] >= cut;
+        if (k < nc) mask[moff + k] = keep ? 1 : 0;
         kept += __popc(__ballot_sync(0xffffffffu, keep));
+        __syncwarp();
       }
       if (lane == 0) counts[pr] = kept;
     } else {

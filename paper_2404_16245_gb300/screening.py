@@ -103,6 +103,19 @@ def train(X, T, *, epochs=20, batch=4096, lr=2e-3, under_weight=4.0, seed=0, log
     return net, losses
 
 
+def calibrate_margin(net, X, T, log10_cut: float, safety: float = 1.0) -> float:
+    """Margin (log10 units) for the rule "skip when prediction < log10_cut - margin" such that no
+    held-out triple whose label is at or above the cut would be skipped: the largest
+    under-prediction among those triples, plus `safety`.  X [n, 16] and T [n] are held-out
+    features and labels (torch CUDA tensors / numpy)."""
+    y = net.forward(X).cpu().numpy().astype(np.float64)
+    t = np.asarray(T, dtype=np.float64)
+    pos = t >= log10_cut
+    if not np.any(pos):
+        return safety
+    return float(max(0.0, np.max(log10_cut - y[pos])) + safety)
+
+
 def audit(basis: dict, shell_a, shell_b, centers, charges, mask, pair_nuc, fraction, rng, threshold):
     """Exact check of a random `fraction` of the skipped triples.  mask is the screening mask over
     all triples in pair order (pair q owns pair_nuc[q] consecutive entries, nuclei in order)."""
