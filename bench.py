@@ -254,6 +254,45 @@ def run_shgo(args, ws, rank, local):
                                                                            float(flops[1] / ph[1] / 1e9)],
                 "algorithmic_flops_per_step": [float(flops[0]), float(flops[1])]}
 
+    # per (la, lb) class: each class's two kernels alone (classes one after another), CUDA events
+    stats = shgo.shgo_basis_class_stats(bases[0].handle, cents[0].shape[0])
+    cms = np.zeros((len(stats), 2))
+    for i in range(nrep):
+        flush.zero_()
+        cms += shgo.shgo_nuclear_attraction_class_timed(bases[i % R].handle, cents[i % R].shape[0],
+                                                        cents[i % R].data_ptr(), chgs[i % R].data_ptr(),
+                                                        outs[i % R].data_ptr(), stream)
+    cms /= nrep
+    per_class = []
+    for (la, lb, trip_c, ints_c, f0, f1), (m0, m1) in sorted(zip(stats, cms), key=lambda x: (-x[0][0], -x[0][1])):
+        sec = (m0 + m1) / 1e3
+        per_class.append({"la": la, "lb": lb, "shell_triples_per_s": trip_c / sec, "integrals_per_s": ints_c / sec,
+                          "ms": m0 + m1, "tflops": (f0 + f1) / sec / 1e12,
+                          "frac": (f0 + f1) / sec / 1e12 / peak})
+
+    # the same per class on 64 replicas in one batch: one launch per kernel and class for all of them
+    per_class_64 = []
+    if rank == 0 and not args.no_per_class_batch:
+        rb = [W.config2(replica=100 + k) for k in range(64)]
+        batch = shgo.Batch([(b, len(Z)) for b, _, Z in rb])
+        Cb = torch.tensor(np.concatenate([C for _, C, _ in rb]), device=dev)
+        Zb = torch.tensor(np.concatenate([Z for _, _, Z in rb]), device=dev)
+        outb = torch.empty(batch.out_size, dtype=torch.float64, device=dev)
+        stats_b = shgo.shgo_basis_class_stats(batch.handle, 0)
+        msb = np.zeros((len(stats_b), 2))
+        for it in range(4):
+            m = shgo.shgo_nuclear_attraction_class_timed(batch.handle, Cb.shape[0], Cb.data_ptr(), Zb.data_ptr(),
+                                                         outb.data_ptr(), stream)
+            if it:
+                msb += m / 3
+        for (la, lb, trip_c, ints_c, f0, f1), (m0, m1) in sorted(zip(stats_b, msb), key=lambda x: (-x[0][0], -x[0][1])):
+            sec = (m0 + m1) / 1e3
+            per_class_64.append({"la": la, "lb": lb, "shell_triples_per_s": trip_c / sec,
+                                 "integrals_per_s": ints_c / sec, "ms": m0 + m1, "tflops": (f0 + f1) / sec / 1e12,
+                                 "frac": (f0 + f1) / sec / 1e12 / peak})
+        batch.close()
+        del outb
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -301,6 +340,9 @@ def run_shgo(args, ws, rank, local):
                        "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write, outside step events)",
                        "wall_s_timed_region": wall},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "per_class": {"note": "each class's coupling + pair kernels timed alone (classes one after another); "
+                                  "frac = algorithmic FP64 flops / time / peak", "classes": per_class,
+                          "classes_64_replicas_batched": per_class_64},
             "gpu_launches": launches_per_step * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -591,6 +633,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-class-batch", action="store_true", help="skip the 64-replica per-class timing")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case()

@@ -184,6 +184,22 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
  * no nuclei are involved.  Errors: SHGO_ERR_INVALID_ARG (NULL basis or out), SHGO_ERR_CUDA. */
 shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream);
 
+/* Per (la, lb) class (measurement): number of classes of a basis (-1 for NULL); for class c
+ * (0 <= c < nclasses, in the library's launch order) its la >= lb in la_lb[2] and, for n_centers
+ * nuclei, stats[4] = shell-triples, integrals (shell-triples x (2la+1)(2lb+1)), algorithmic flops of
+ * the coupling kernel and of the pair kernel (FMA = 2 flops).  Errors: SHGO_ERR_INVALID_ARG. */
+int32_t shgo_basis_nclasses(const shgo_basis* basis);
+shgo_status shgo_basis_class_stats(const shgo_basis* basis, int64_t n_centers, int32_t c, int32_t* la_lb,
+                                   double* stats);
+
+/* V as shgo_nuclear_attraction (or, for a batch, shgo_nuclear_attraction_batched with centers->n =
+ * all its nuclei) computes it, but with the classes run one after another on `stream` and the
+ * device time of each class's coupling and pair kernels written to ms[2 c], ms[2 c + 1] (host array
+ * of 2 x nclasses).  Blocks until done.  Bases whose coupling buffer is split into regions are
+ * rejected (SHGO_ERR_INVALID_ARG). */
+shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const shgo_centers* centers,
+                                                const double* charges, double* out, void* stream, double* ms);
+
 /* Release a basis and its device memory (synchronises its device).  NULL-safe. */
 void shgo_free(shgo_basis* basis);
 

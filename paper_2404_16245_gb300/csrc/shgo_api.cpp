@@ -440,6 +440,47 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
 
 }  // namespace
 
+namespace {
+// Per class wi of a basis: out[0] shell triples, out[1] unused, out[2] algorithmic flops of the
+// coupling kernel (S2), out[3] flops of the pair kernel (S3-S5), out[4] primitive triples, out[5]
+// integrals (shell triples x (2la+1)(2lb+1)).  Flops count an FMA as two.
+void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* out) {
+  const Tables& t = tables_host();
+  const ClassWork& w = basis->work[wi];
+  // nuclei seen by the class: per call for one molecule, per molecule for a batch
+  const double pair_cent = basis->batch ? basis->class_pair_cent[wi] : (double)w.npairs * (double)n_centers;
+  const double pp_cent = basis->batch ? basis->class_pp_cent[wi] : (double)w.npp * (double)n_centers;
+  const int la = w.la, lb = w.lb, lam = la + lb;
+  const double nB = n_beta(lam), nR = n_r(lam);
+  // per primitive triple: geometry 9; |d|^2, T, 1/|d|, |d| and the unit vector 11; Boys: Horner over
+  // kBoysK Taylor terms (5 per term), exp 1, downward recursion 3 per order; Z |d|^n F_n 2 Lambda + 1;
+  // (p |d|)^j / j! 2 per j; the beta running sums 2 per entry beyond the first of each L; the
+  // unit-vector harmonic recursion 6 l + 5 for level l + 1; the nucleus sum 2 per R entry
+  double s_lm = 0.0;
+  for (int l = 1; l < lam; ++l) s_lm += 6.0 * l + 5.0;
+  const double boys = 5.0 * kBoysK + 1 + 3.0 * lam;
+  const double per_triple =
+      9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
+  const double f0 = per_triple * pp_cent + 2.0 * nR * (double)w.npp;
+  // per primitive pair: coupling
+  const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
+  double f1 = (2.0 * t.g_nnz[class_id(la, lb)] + 4.0 * nW) * (double)w.npp;
+  // per shell pair: the translation along the pair axis (diagonal in m) and the rotation of the
+  // block back to the molecular frame (the rotation matrices themselves are built once per basis)
+  const double na = 2 * la + 1, nb = 2 * lb + 1;
+  double zt = 0, vt = 0;
+  for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
+  for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
+  f1 += (zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
+  out[0] = pair_cent;
+  out[1] = 0;
+  out[2] = f0;
+  out[3] = f1;
+  out[4] = pp_cent;
+  out[5] = pair_cent * na * nb;
+}
+}  // namespace
+
 extern "C" {
 
 shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
@@ -615,45 +656,63 @@ int64_t shgo_basis_launches(const shgo_basis* basis) { return basis ? launches_p
 
 shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples) {
   if (!basis || !flops || !triples || n_centers < 0) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
-  const Tables& t = tables_host();
-  double f0 = 0, f1 = 0, st = 0, pt = 0;
+  flops[0] = flops[1] = triples[0] = triples[1] = 0;
   for (size_t wi = 0; wi < basis->work.size(); ++wi) {
-    const ClassWork& w = basis->work[wi];
-    // nuclei seen by the class: per call for one molecule, per molecule for a batch
-    const double pair_cent = basis->batch ? basis->class_pair_cent[wi] : (double)w.npairs * (double)n_centers;
-    const double pp_cent = basis->batch ? basis->class_pp_cent[wi] : (double)w.npp * (double)n_centers;
-    const int la = w.la, lb = w.lb, lam = la + lb;
-    const double nB = n_beta(lam), nR = n_r(lam);
-    // per primitive triple (flops, an FMA counting two): geometry 9; |d|^2, T, 1/|d|, |d| and the
-    // unit vector 11; Boys: Horner over kBoysK Taylor terms (5 per term), exp 1, downward
-    // recursion 3 per order; Z |d|^n F_n 2 Lambda + 1; (p |d|)^j / j! 2 per j; the beta running
-    // sums 2 per entry beyond the first of each L; the unit-vector harmonic recursion 6 l + 5 for
-    // level l + 1; the nucleus sum 2 per R entry
-    double s_lm = 0.0;
-    for (int l = 1; l < lam; ++l) s_lm += 6.0 * l + 5.0;
-    const double boys = 5.0 * kBoysK + 1 + 3.0 * lam;
-    const double per_triple =
-        9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
-    f0 += per_triple * pp_cent + 2.0 * nR * (double)w.npp;
-    // per primitive pair: coupling
-    const int cid = class_id(la, lb);
-    const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
-    const double terms = t.g_nnz[cid];
-    f1 += (2.0 * terms + 4.0 * nW) * (double)w.npp;
-    // per shell pair: the translation along the pair axis (diagonal in m) and the rotation of the
-    // block back to the molecular frame (the rotation matrices themselves are built once per basis)
-    const double na = 2 * la + 1, nb = 2 * lb + 1;
-    double zt = 0, vt = 0;
-    for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
-    for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
-    f1 += (zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
-    st += pair_cent;
-    pt += pp_cent;
+    double c[6];
+    class_model(basis, wi, n_centers, c);
+    flops[0] += c[2];
+    flops[1] += c[3];
+    triples[0] += c[0];
+    triples[1] += c[4];
   }
-  flops[0] = f0;
-  flops[1] = f1;
-  triples[0] = st;
-  triples[1] = pt;
+  return SHGO_OK;
+}
+
+int32_t shgo_basis_nclasses(const shgo_basis* basis) { return basis ? (int32_t)basis->work.size() : -1; }
+
+shgo_status shgo_basis_class_stats(const shgo_basis* basis, int64_t n_centers, int32_t c, int32_t* la_lb,
+                                   double* stats) {
+  if (!basis || !la_lb || !stats || n_centers < 0 || c < 0 || c >= (int32_t)basis->work.size())
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  double m[6];
+  class_model(basis, (size_t)c, n_centers, m);
+  la_lb[0] = basis->work[c].la;
+  la_lb[1] = basis->work[c].lb;
+  stats[0] = m[0];
+  stats[1] = m[5];
+  stats[2] = m[2];
+  stats[3] = m[3];
+  return SHGO_OK;
+}
+
+shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const shgo_centers* centers,
+                                                const double* charges, double* out, void* stream, double* ms) {
+  g_last_error.clear();
+  if (!basis || !ms) return fail(SHGO_ERR_INVALID_ARG, "basis or ms is NULL");
+  if (!centers || centers->n < 0) return fail(SHGO_ERR_INVALID_ARG, "centers is NULL or negative count");
+  if (centers->n > 0 && (!centers->xyz || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
+  if ((basis->batch ? basis->out_size : basis->nbf) > 0 && !out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  if (basis->d.region > 0) return fail(SHGO_ERR_INVALID_ARG, "class timing needs the whole coupling buffer");
+  if (basis->batch && centers->n != basis->total_centers)
+    return fail(SHGO_ERR_INVALID_ARG, "a batch takes all its molecules' nuclei");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  MolView mv;
+  if (basis->batch) {
+    mv.pair_mol = basis->pair_mol;
+    mv.c0 = basis->mol_c0_d;
+    mv.nc = basis->mol_nc_d;
+    mv.out_off = basis->mol_out_d;
+    mv.ld = basis->mol_ld_d;
+  }
+  mv.ncenters = centers->n;
+  mv.nbf = basis->nbf;
+  std::string err;
+  const shgo_status st = launch_class_timed(basis->d, *basis->tabs, basis->work, mv, centers->xyz, charges, out,
+                                            (cudaStream_t)stream, ms, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;
 }
 

@@ -273,6 +273,12 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
                                       bool concurrent = true);
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
 
+// The same launches one class after another on `stream`, with the device time of each class's
+// coupling and pair kernels in ms[2 c], ms[2 c + 1] (blocks until done).
+shgo_status launch_class_timed(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                               const MolView& mv, const double* centers, const double* charges, double* out,
+                               cudaStream_t stream, double* ms, std::string* err);
+
 // Overlap blocks of every shell pair into out (one molecule or a batch, per mv).
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err);

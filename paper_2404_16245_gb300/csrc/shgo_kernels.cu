@@ -977,6 +977,43 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
   return launch_error(err);
 }
 
+shgo_status launch_class_timed(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                               const MolView& mv, const double* centers, const double* charges, double* out,
+                               cudaStream_t stream, double* ms, std::string* err) {
+  if (work.empty()) return SHGO_OK;
+  set_kernel_attributes();
+  const Tables& th = tables_host();
+  const std::vector<int64_t> rbases = class_rbases(work);
+  const Launcher L{db, dt, th, mv, centers, charges, out, nullptr};
+  std::vector<cudaEvent_t> ev(3 * work.size(), nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  for (size_t c = 0; c < work.size() && e == cudaSuccess; ++c) {
+    cudaEventRecord(ev[3 * c], stream);
+    L.coupling(work[c], c, rbases[c], stream);
+    cudaEventRecord(ev[3 * c + 1], stream);
+    L.pair(work[c], c, rbases[c], stream);
+    cudaEventRecord(ev[3 * c + 2], stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+  for (size_t c = 0; c < work.size() && e == cudaSuccess; ++c) {
+    float a = 0, b = 0;
+    e = cudaEventElapsedTime(&a, ev[3 * c], ev[3 * c + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * c + 1], ev[3 * c + 2]);
+    ms[2 * c] = a;
+    ms[2 * c + 1] = b;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e != cudaSuccess) {
+    *err = std::string("class timing: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return SHGO_OK;
+}
+
 shgo_status launch_batched(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double nuclei_per_pair, const double* centers, const double* charges,
                            double* out, const std::vector<ClassTune>* tune, cudaStream_t stream, std::string* err) {

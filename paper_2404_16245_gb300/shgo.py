@@ -72,6 +72,13 @@ def _load() -> ctypes.CDLL:
     lib.shgo_nuclear_attraction_batched.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_nuclear_attraction_batched.restype = ctypes.c_int
+    lib.shgo_basis_nclasses.argtypes = [ctypes.c_void_p]
+    lib.shgo_basis_nclasses.restype = ctypes.c_int32
+    lib.shgo_basis_class_stats.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, i32p, f64p]
+    lib.shgo_basis_class_stats.restype = ctypes.c_int
+    lib.shgo_nuclear_attraction_class_timed.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers),
+                                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, f64p]
+    lib.shgo_nuclear_attraction_class_timed.restype = ctypes.c_int
     lib.shgo_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_overlap.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
@@ -231,6 +238,30 @@ def nuclear_attraction(basis: Basis, centers, charges, out=None, stream=None):
     shgo_nuclear_attraction(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
                             out.data_ptr(), stream)
     return out
+
+
+def shgo_basis_class_stats(basis, n_centers):
+    """Per class: list of (la, lb, shell_triples, integrals, coupling_flops, pair_flops)."""
+    rows = []
+    for c in range(int(_lib.shgo_basis_nclasses(ctypes.c_void_p(basis)))):
+        ll = np.zeros(2, dtype=np.int32)
+        st = np.zeros(4)
+        _check(_lib.shgo_basis_class_stats(ctypes.c_void_p(basis), int(n_centers), c, _ptr(ll, ctypes.c_int32),
+                                           _ptr(st, ctypes.c_double)))
+        rows.append((int(ll[0]), int(ll[1]), *map(float, st)))
+    return rows
+
+
+def shgo_nuclear_attraction_class_timed(basis, n_centers, centers_ptr, charges_ptr, out_ptr, stream=None):
+    """Per class device times (ms) of the coupling and pair kernels, classes run one after another."""
+    n = int(_lib.shgo_basis_nclasses(ctypes.c_void_p(basis)))
+    ms = np.zeros(2 * max(n, 1))
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    _check(_lib.shgo_nuclear_attraction_class_timed(ctypes.c_void_p(basis), ctypes.byref(c),
+                                                    ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0),
+                                                    ctypes.c_void_p(int(out_ptr) if out_ptr else 0),
+                                                    _stream_handle(stream), _ptr(ms, ctypes.c_double)))
+    return ms[:2 * n].reshape(n, 2)
 
 
 def shgo_overlap(basis, out_ptr, stream=None):

@@ -151,3 +151,18 @@ def test_linear_in_the_charges(shgo):
     v = gpu_V(shgo, basis, C, q1 + 2 * q2)
     v1, v2 = gpu_V(shgo, basis, C, q1), gpu_V(shgo, basis, C, q2)
     assert np.max(np.abs(v - (v1 + 2 * v2))) <= 1e-12 * np.max(np.abs(v))
+
+
+def test_class_timed_call_gives_the_same_V(shgo):
+    basis, C, Z = W.config2(n_atoms=6)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    V = shgo.nuclear_attraction(B, Cd, Zd).cpu().numpy()
+    out = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device="cuda")
+    ms = shgo.shgo_nuclear_attraction_class_timed(B.handle, len(Z), Cd.data_ptr(), Zd.data_ptr(), out.data_ptr())
+    assert np.array_equal(out.cpu().numpy(), V)
+    stats = shgo.shgo_basis_class_stats(B.handle, len(Z))
+    assert ms.shape == (len(stats), 2) and np.all(ms >= 0)
+    n = len(basis["l"])
+    assert sum(s[2] for s in stats) == n * (n + 1) // 2 * len(Z)
+    B.close()
