@@ -54,6 +54,10 @@ struct shgo_basis {
   std::vector<int64_t> mol_nbf, mol_out, mol_c0, mol_nc;
   int64_t out_size = 0, total_centers = 0;
   std::vector<double> class_pair_cent, class_pp_cent;  // per class: sum over pairs / primitive pairs of nuclei
+  // per class, after the primitive-pair bound: live primitive pairs, shell pairs with one, and (batches)
+  // the sum of nuclei over live primitive pairs
+  std::vector<int64_t> live_pp, live_pairs;
+  std::vector<double> live_cent;
   int* pair_mol = nullptr;
   int64_t *mol_c0_d = nullptr, *mol_nc_d = nullptr, *mol_out_d = nullptr, *mol_ld_d = nullptr;
   std::vector<ClassTune> tune;
@@ -430,6 +434,9 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     st = SHGO_ERR_CUDA;
     err = "primitive-pair and pair-frame build failed";
   }
+  if (st == SHGO_OK)
+    st = live_counts(b->d, b->work, (int64_t)pa.size(), ppcount, batch ? b->pair_mol : nullptr,
+                     batch ? b->mol_nc_d : nullptr, b->live_pp, b->live_pairs, b->live_cent, &err);
   if (st != SHGO_OK) {
     release(b);
     return fail(st, err);
@@ -447,9 +454,12 @@ namespace {
 void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* out) {
   const Tables& t = tables_host();
   const ClassWork& w = basis->work[wi];
-  // nuclei seen by the class: per call for one molecule, per molecule for a batch
+  // nuclei seen by the class: per call for one molecule, per molecule for a batch.  Shell triples
+  // count every pair (the output is complete); the work counts only live primitive pairs (those not
+  // dropped by K_AB underflow or the per-basis bound) and shell pairs with at least one.
   const double pair_cent = basis->batch ? basis->class_pair_cent[wi] : (double)w.npairs * (double)n_centers;
-  const double pp_cent = basis->batch ? basis->class_pp_cent[wi] : (double)w.npp * (double)n_centers;
+  const double live_pp = (double)basis->live_pp[wi], live_pairs = (double)basis->live_pairs[wi];
+  const double pp_cent = basis->batch ? basis->live_cent[wi] : live_pp * (double)n_centers;
   const int la = w.la, lb = w.lb, lam = la + lb;
   const double nB = n_beta(lam), nR = n_r(lam);
   // per primitive triple: geometry 9; |d|^2, T, 1/|d|, |d| and the unit vector 11; Boys: Horner over
@@ -461,22 +471,22 @@ void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* 
   const double boys = 5.0 * kBoysK + 1 + 3.0 * lam;
   const double per_triple =
       9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
-  const double f0 = per_triple * pp_cent + 2.0 * nR * (double)w.npp;
+  const double f0 = per_triple * pp_cent + 2.0 * nR * live_pp;
   // per primitive pair: coupling
   const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
-  double f1 = (2.0 * t.g_nnz[class_id(la, lb)] + 4.0 * nW) * (double)w.npp;
+  double f1 = (2.0 * t.g_nnz[class_id(la, lb)] + 4.0 * nW) * live_pp;
   // per shell pair: the translation along the pair axis (diagonal in m) and the rotation of the
   // block back to the molecular frame (the rotation matrices themselves are built once per basis)
   const double na = 2 * la + 1, nb = 2 * lb + 1;
   double zt = 0, vt = 0;
   for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
   for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
-  f1 += (zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * (double)w.npairs;
+  f1 += (zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * live_pairs;
   out[0] = pair_cent;
   out[1] = 0;
   out[2] = f0;
   out[3] = f1;
-  out[4] = pp_cent;
+  out[4] = basis->batch ? basis->class_pp_cent[wi] : (double)w.npp * (double)n_centers;
   out[5] = pair_cent * na * nb;
 }
 }  // namespace

@@ -118,9 +118,9 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
     const int pr = A.pp_pair[q];
     const int a = A.pair_a[pr];
     const PPData pd = A.ppd[q];
-    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
-    // skips such primitive pairs, so their coupling block is not needed
-    if (pd.kab == 0.0) continue;
+    // primitive pairs with a zero prefactor (K_AB of Eq. 5 underflowed, or the pair is below the
+    // per-basis bound) are skipped by the pair kernel too, so their coupling block is not needed
+    if (pd.pref == 0.0) continue;
     const double p = pd.p;
     // C - P = (C - A) - (beta/p)(B - A), in the pair frame where B - A is along z
     const double Ax = A.shell_xyz[3 * a], Ay = A.shell_xyz[3 * a + 1], Az = A.shell_xyz[3 * a + 2];

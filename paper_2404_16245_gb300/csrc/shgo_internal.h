@@ -306,6 +306,16 @@ size_t coupling_fp64_smem(int lam, int nch);
 // Constants and launch attributes of the FP64 coupling kernels on the current device.
 cudaError_t coupling_fp64_setup();
 
+// Primitive pairs whose elementwise bound per unit of total nuclear charge is below this are skipped
+// (k_pair_build); an element of V changes by at most kPrimSkip x sum |Z| per skipped pair.
+constexpr double kPrimSkip = 1e-20;
+
+// Per class of `work`: live primitive pairs, shell pairs with a live primitive pair, and (batches)
+// the sum of the molecule's nucleus counts over live primitive pairs.  Blocking.
+shgo_status live_counts(const DeviceBasis& db, const std::vector<ClassWork>& work, int64_t npairs, int64_t npp,
+                        const int* pair_mol, const int64_t* mol_nc, std::vector<int64_t>& live_pp,
+                        std::vector<int64_t>& live_pairs, std::vector<double>& live_cent, std::string* err);
+
 // Fills db.ppd for the npp primitive pairs (asynchronous on `stream`).
 shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t stream, std::string* err);
 

@@ -50,12 +50,46 @@ __device__ __forceinline__ double prim_kab(double ea, double eb, double ab2) {
   return exp(-__dmul_rn(__ddiv_rn(__dmul_rn(ea, eb), __dadd_rn(ea, eb)), ab2));
 }
 
-// Step S1, once per basis: the Gaussian-product data of every primitive pair.
+// Bound on every element of one primitive pair's block, per unit of total nuclear charge:
+// |S_lm(r)| <= |r|^l (Racah normalisation) and |r_A| <= r_P + |PA|, and the potential of a non-negative
+// radial density at any point is at most its value at the centre, int f(r)/r d^3r; so
+//   |<a_i|1/|r-C||b_j>| <= |c_i c_j| K_AB 4 pi int_0^inf (r + |PA|)^la (r + |PB|)^lb e^{-p r^2} r dr.
+// The overlap integrand is bounded the same way with r^2 dr; the larger of the two is returned.
+// Moments: int_0^inf r^n e^{-p r^2} dr = M_n with M_0 = sqrt(pi/p)/2, M_1 = 1/(2p),
+// M_{n+2} = (n+1)/(2p) M_n.
+__device__ double prim_pair_bound(int la, int lb, double pa, double pb, double p, double pref) {
+  double M[2 * kLmax + 4];
+  M[0] = 0.5 * sqrt(3.14159265358979323846 / p);
+  M[1] = 0.5 / p;
+  for (int n = 0; n + 2 < 2 * kLmax + 4; ++n) M[n + 2] = (n + 1) * M[n] * (0.5 / p);
+  double i1 = 0.0, i2 = 0.0, ca = 1.0;  // ca = C(la, i) pa^(la-i)
+  double pa_pow[kLmax + 1], pb_pow[kLmax + 1];
+  pa_pow[0] = pb_pow[0] = 1.0;
+  for (int k = 1; k <= kLmax; ++k) {
+    pa_pow[k] = pa_pow[k - 1] * pa;
+    pb_pow[k] = pb_pow[k - 1] * pb;
+  }
+  for (int i = 0; i <= la; ++i) {
+    ca = (i == 0) ? 1.0 : ca * (la - i + 1) / i;
+    double cb = 1.0;
+    for (int j = 0; j <= lb; ++j) {
+      cb = (j == 0) ? 1.0 : cb * (lb - j + 1) / j;
+      const double w = ca * cb * pa_pow[la - i] * pb_pow[lb - j];
+      i1 += w * M[i + j + 1];
+      i2 += w * M[i + j + 2];
+    }
+  }
+  return fabs(pref) * 4.0 * 3.14159265358979323846 * fmax(i1, i2);
+}
+
+// Step S1, once per basis: the Gaussian-product data of every primitive pair.  A primitive pair whose
+// bound (prim_pair_bound) is below kPrimSkip gets pref = 0, which every kernel treats as "skip": it
+// changes any V element by at most kPrimSkip x sum |Z_C| (and any S element by at most kPrimSkip).
 __global__ void k_pair_build(int64_t npp, const int* __restrict__ pp_pair, const int* __restrict__ pp_ij,
                              const int* __restrict__ pair_a, const int* __restrict__ pair_b,
-                             const double* __restrict__ shell_xyz, const int* __restrict__ shell_poff,
-                             const double* __restrict__ prim_exp, const double* __restrict__ prim_coef,
-                             PPData* __restrict__ ppd) {
+                             const double* __restrict__ shell_xyz, const int* __restrict__ shell_l,
+                             const int* __restrict__ shell_poff, const double* __restrict__ prim_exp,
+                             const double* __restrict__ prim_coef, PPData* __restrict__ ppd) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npp; q += (int64_t)gridDim.x * blockDim.x) {
     const int pr = pp_pair[q], ij = pp_ij[q];
     const int a = pair_a[pr], b = pair_b[pr];
@@ -70,8 +104,33 @@ __global__ void k_pair_build(int64_t npp, const int* __restrict__ pp_pair, const
     d.pref = prim_coef[ia] * prim_coef[ib] * d.kab;
     d.ra = eb * d.rp;
     d.rb = ea * d.rp;
-    d.shift = d.ra * sqrt(ab2);
+    const double ab = sqrt(ab2);
+    d.shift = d.ra * ab;
+    if (d.pref != 0.0 && prim_pair_bound(shell_l[a], shell_l[b], d.shift, d.rb * ab, d.p, d.pref) < kPrimSkip)
+      d.pref = 0.0;
     ppd[q] = d;
+  }
+}
+
+// Per class (classes given by their first pair, pair_cls[c] .. pair_cls[c + 1]): live primitive pairs
+// (pref != 0), shell pairs with at least one, and the sum over live primitive pairs of their
+// molecule's nucleus count (batches; 0 otherwise).
+__global__ void k_live_counts(int npairs, int ncls, const int* __restrict__ pair_cls,
+                              const int64_t* __restrict__ pair_ppoff, int64_t npp_total,
+                              const PPData* __restrict__ ppd, const int* __restrict__ pair_mol,
+                              const int64_t* __restrict__ mol_nc, unsigned long long* __restrict__ live_pp,
+                              unsigned long long* __restrict__ live_pairs, double* __restrict__ live_cent) {
+  for (int pr = blockIdx.x * blockDim.x + threadIdx.x; pr < npairs; pr += gridDim.x * blockDim.x) {
+    int c = 0;
+    while (c + 1 < ncls && pair_cls[c + 1] <= pr) ++c;
+    const int64_t q1 = pr + 1 < npairs ? pair_ppoff[pr + 1] : npp_total;
+    unsigned long long n = 0;
+    for (int64_t q = pair_ppoff[pr]; q < q1; ++q) n += ppd[q].pref != 0.0;
+    if (n) {
+      atomicAdd(live_pp + c, n);
+      atomicAdd(live_pairs + c, 1ull);
+      if (pair_mol) atomicAdd(live_cent + c, (double)n * (double)mol_nc[pair_mol[pr]]);
+    }
   }
 }
 
@@ -131,7 +190,7 @@ __global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp,
     const PPData pd = ppd[q];
     // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
     // skips such primitive pairs, so their coupling block is not needed
-    if (pd.kab == 0.0) continue;
+    if (pd.pref == 0.0) continue;
     const double p = pd.p, rp = pd.rp;
     // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
     // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
@@ -414,6 +473,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
     // coupling (Gaunt) and primitive contraction, in the pair frame
     const int npa = shell_nprim[a], npb = shell_nprim[b];
     const int64_t q0 = pair_ppoff[pr];
+    bool live = false;  // uniform over the block
     for (int ij = 0; ij < npa * npb; ++ij) {
       __syncthreads();  // the previous primitive pair is done with Rs, fab and scal
       if (tid == 0) {
@@ -424,7 +484,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
         scal[3] = pd.kab;
       }
       __syncthreads();
-      if (scal[3] == 0.0) continue;  // uniform over the block; the coupling kernel skipped this pair too
+      if (scal[0] == 0.0) continue;  // uniform over the block; the coupling kernel skipped this pair too
+      live = true;
       const double pref = scal[0];
       const double* R = rbuf + rbase + (q0 + ij - pp_base) * (int64_t)nR;
       for (int e = tid; e < nR; e += nth) Rs[e] = R[e];
@@ -460,6 +521,19 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       }
     }
     __syncthreads();
+    if (!live) {
+      // every primitive pair skipped: the block is zero
+      const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
+      int64_t obase, ld;
+      mol_output(mv, pr, obase, ld);
+      double* o = out + obase;
+      for (int e = tid; e < na * nb; e += nth) {
+        const int ma = e / nb, mb = e % nb;
+        o[(fa0 + ma) * ld + fb0 + mb] = 0.0;
+        if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = 0.0;
+      }
+      continue;
+    }
     // V' = t_A W t_B (diagonal in m), first over l2.  Threads are ordered by |m| (m = 0, 1, -1,
     // 2, -2, ...) so that the lanes of a warp run loops of (nearly) equal length.
     for (int e = tid; e < nWa * nb; e += nth) {
@@ -569,7 +643,7 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
       double acc = 0.0;
       for (int ij = 0; ij < npp; ++ij) {
         const PPData pd = ppd[q0 + ij];
-        if (pd.kab == 0.0) continue;
+        if (pd.pref == 0.0) continue;
         double v = pd.pref * pd.rp / pd.sp;  // p^{-3/2}
         for (int k = 0; k < l1; ++k) v *= pd.rp;
         for (int k = 0; k < la - l1; ++k) v *= pd.ra;
@@ -1109,8 +1183,50 @@ shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t s
   if (npp == 0) return SHGO_OK;
   const int64_t blocks = std::min<int64_t>((npp + 255) / 256, 152 * 32);
   k_pair_build<<<(int)blocks, 256, 0, stream>>>(npp, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz,
-                                                 db.shell_poff, db.prim_exp, db.prim_coef, db.ppd);
+                                                 db.shell_l, db.shell_poff, db.prim_exp, db.prim_coef, db.ppd);
   return launch_error(err);
+}
+
+shgo_status live_counts(const DeviceBasis& db, const std::vector<ClassWork>& work, int64_t npairs, int64_t npp,
+                        const int* pair_mol, const int64_t* mol_nc, std::vector<int64_t>& live_pp,
+                        std::vector<int64_t>& live_pairs, std::vector<double>& live_cent, std::string* err) {
+  const int nc = (int)work.size();
+  live_pp.assign(nc, 0);
+  live_pairs.assign(nc, 0);
+  live_cent.assign(nc, 0.0);
+  if (nc == 0 || npairs == 0) return SHGO_OK;
+  std::vector<int> cls(nc);
+  for (int c = 0; c < nc; ++c) cls[c] = work[c].pair_base;
+  // one scratch block: class starts, then the three counters
+  const size_t b_cls = sizeof(int) * nc, b_cnt = sizeof(unsigned long long) * nc, b_cent = sizeof(double) * nc;
+  unsigned char* scratch = nullptr;
+  cudaError_t e = cudaMalloc((void**)&scratch, b_cls + 2 * b_cnt + b_cent + 64);
+  if (e == cudaSuccess) e = cudaMemset(scratch, 0, b_cls + 2 * b_cnt + b_cent + 64);
+  int* d_cls = reinterpret_cast<int*>(scratch);
+  unsigned long long* d_pp = reinterpret_cast<unsigned long long*>(scratch + ((b_cls + 15) & ~(size_t)15));
+  unsigned long long* d_pairs = d_pp + nc;
+  double* d_cent = reinterpret_cast<double*>(d_pairs + nc);
+  if (e == cudaSuccess) e = cudaMemcpy(d_cls, cls.data(), b_cls, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int64_t blocks = std::min<int64_t>((npairs + 255) / 256, 152 * 16);
+    k_live_counts<<<(int)blocks, 256>>>((int)npairs, nc, d_cls, db.pair_ppoff, npp, db.ppd, pair_mol, mol_nc, d_pp,
+                                        d_pairs, d_cent);
+    e = cudaGetLastError();
+  }
+  std::vector<unsigned long long> hp(nc), hq(nc);
+  if (e == cudaSuccess) e = cudaMemcpy(hp.data(), d_pp, b_cnt, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hq.data(), d_pairs, b_cnt, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(live_cent.data(), d_cent, b_cent, cudaMemcpyDeviceToHost);
+  cudaFree(scratch);
+  if (e != cudaSuccess) {
+    *err = std::string("counting live primitive pairs: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  for (int c = 0; c < nc; ++c) {
+    live_pp[c] = (int64_t)hp[c];
+    live_pairs[c] = (int64_t)hq[c];
+  }
+  return SHGO_OK;
 }
 
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
