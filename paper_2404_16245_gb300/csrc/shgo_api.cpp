@@ -25,12 +25,14 @@ shgo_status fail(shgo_status s, const std::string& msg) {
 }
 
 // N(l, alpha)^-2 = int S_lm^2 e^{-2 alpha r^2} d^3r = pi^{3/2} (2l-1)!! / (2^l (2 alpha)^{l+3/2})
+// Normalisation N(l, alpha) of a primitive, N^-2 = pi^{3/2} (2l-1)!! / (2^l (2 alpha)^{l+3/2}).
+// Double precision: the host's long double may be a software binary128 type, far slower, and the
+// factor needs no more than double accuracy.
 double prim_norm(int l, double alpha) {
-  long double df = 1;
+  double df = 1;
   for (int k = 2 * l - 1; k > 1; k -= 2) df *= k;
-  const long double n2 = std::pow(3.14159265358979323846264338327950288L, 1.5L) * df /
-                         (std::pow(2.0L, (long double)l) * std::pow(2.0L * alpha, (long double)l + 1.5L));
-  return (double)(1.0L / std::sqrt(n2));
+  const double n2 = 5.5683279968317078453 * df / (std::ldexp(1.0, l) * std::pow(2.0 * alpha, l + 1.5));
+  return 1.0 / std::sqrt(n2);
 }
 }  // namespace
 
@@ -237,18 +239,18 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     const int ls = l[s];
     for (int i = 0; i < n_prim[s]; ++i) pcoef[poff[s] + i] = coefs[poff[s] + i] * prim_norm(ls, exponents[poff[s] + i]);
     // <phi|phi> = sum_ij d_i d_j (2 sqrt(a_i a_j)/(a_i + a_j))^{l+3/2} / (N_i N_j) with d = c N
-    long double self = 0;
+    double self = 0;
     for (int i = 0; i < n_prim[s]; ++i)
       for (int j = 0; j < n_prim[s]; ++j) {
-        const long double ai = exponents[poff[s] + i], aj = exponents[poff[s] + j];
-        const long double ov = std::pow(2 * std::sqrt(ai * aj) / (ai + aj), (long double)ls + 1.5L);
-        self += (long double)coefs[poff[s] + i] * coefs[poff[s] + j] * ov;
+        const double ai = exponents[poff[s] + i], aj = exponents[poff[s] + j];
+        const double ov = std::pow(2 * std::sqrt(ai * aj) / (ai + aj), ls + 1.5);
+        self += coefs[poff[s] + i] * coefs[poff[s] + j] * ov;
       }
     if (!(self > 0)) {
       release(b);
       return fail(SHGO_ERR_NUMERIC, "contracted shell " + std::to_string(s) + " has zero norm");
     }
-    const double scale = (double)(1.0L / std::sqrt(self));
+    const double scale = 1.0 / std::sqrt(self);
     for (int i = 0; i < n_prim[s]; ++i) pcoef[poff[s] + i] *= scale;
   }
   // function offsets inside each molecule's V block

@@ -132,12 +132,12 @@ shgo_status noalloc_fail(shgo_status s, const std::string& msg) {
 }
 
 // N(l, alpha) of Eq. 1: N^-2 = pi^{3/2} (2l-1)!! / (2^l (2 alpha)^{l+3/2}).
+// The same expressions as the basis build, so both entry points normalise identically.
 double noalloc_prim_norm(int l, double alpha) {
-  long double df = 1;
+  double df = 1;
   for (int k = 2 * l - 1; k > 1; k -= 2) df *= k;
-  const long double n2 = std::pow(3.14159265358979323846264338327950288L, 1.5L) * df /
-                         (std::pow(2.0L, (long double)l) * std::pow(2.0L * alpha, (long double)l + 1.5L));
-  return (double)(1.0L / std::sqrt(n2));
+  const double n2 = 5.5683279968317078453 * df / (std::ldexp(1.0, l) * std::pow(2.0 * alpha, l + 1.5));
+  return 1.0 / std::sqrt(n2);
 }
 
 }  // namespace
@@ -248,15 +248,15 @@ extern "C" shgo_status shgo_nuclear_attraction_noalloc(int32_t n_shells, const i
   for (int s = 0; s < n_shells; ++s) foff[s + 1] = foff[s] + 2 * l[s] + 1;
   std::vector<double> pcoef(nprim_total);
   for (int s = 0; s < n_shells; ++s) {
-    long double self = 0;
+    double self = 0;
     for (int i = 0; i < n_prim[s]; ++i)
       for (int j = 0; j < n_prim[s]; ++j) {
-        const long double ai = exponents[poff[s] + i], aj = exponents[poff[s] + j];
-        self += (long double)coefs[poff[s] + i] * coefs[poff[s] + j] *
-                std::pow(2 * std::sqrt(ai * aj) / (ai + aj), (long double)l[s] + 1.5L);
+        const double ai = exponents[poff[s] + i], aj = exponents[poff[s] + j];
+        const double ov = std::pow(2 * std::sqrt(ai * aj) / (ai + aj), l[s] + 1.5);
+        self += coefs[poff[s] + i] * coefs[poff[s] + j] * ov;
       }
     if (!(self > 0)) return noalloc_fail(SHGO_ERR_NUMERIC, "a contracted shell has zero norm");
-    const double scale = (double)(1.0L / std::sqrt(self));
+    const double scale = 1.0 / std::sqrt(self);
     for (int i = 0; i < n_prim[s]; ++i)
       pcoef[poff[s] + i] = coefs[poff[s] + i] * noalloc_prim_norm(l[s], exponents[poff[s] + i]) * scale;
   }
