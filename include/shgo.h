@@ -176,6 +176,20 @@ int64_t shgo_batch_out_size(const shgo_basis* batch);
 shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* centers, const double* charges,
                                             double* out, void* stream);
 
+/* Electrostatic potential of a density at arbitrary points (positive sign convention, as V):
+ *   phi[k] = sum_{a,b} D_ab < phi_a | 1/|r - x_k| | phi_b >,
+ * i.e. the attraction matrix of a unit point charge at x_k contracted with D (the electronic potential
+ * of a one-particle density D is -phi).  Computed without forming any per-point matrix: the pair
+ * kernel's linear map (Gaunt coupling of the one-centre integral, Eq. 12 corrected; translation,
+ * Eqs. 7-8; rotation to the pair frame) is applied backwards to each density block once, and every
+ * point then needs only the Boys values and solid harmonics of x_k - P per primitive pair (Eq. 11).
+ * density: device, nbf x nbf row-major, symmetric (D_ab and D_ba both enter).  points: device
+ * [n][3] (bohr).  phi: device [n], overwritten.  Single bases only (a batch, or a basis whose
+ * coupling buffer is split into regions, gives SHGO_ERR_INVALID_ARG); uses the basis's coupling
+ * buffer, so calls on one basis must be ordered with its other calls.  Asynchronous on `stream`. */
+shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
+                     void* stream);
+
 /* Overlap matrix S_ab = <a|b> of a basis or of every molecule of a batch (Eqs. 9-10): both
  * Gaussians of a pair translated to the product centre P (Eq. 7), where the one-centre integral is
  * diagonal in (l, m) by the orthogonality of Eq. 10, then rotated from the pair frame back to the

@@ -587,6 +587,27 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
   return SHGO_OK;
 }
 
+shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
+                     void* stream) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "the potential takes a single basis, not a batch");
+  if (basis->d.region > 0) return fail(SHGO_ERR_INVALID_ARG, "the potential needs the whole coupling buffer");
+  if (!points || points->n < 0) return fail(SHGO_ERR_INVALID_ARG, "points is NULL or negative count");
+  if (points->n > 0 && (!points->xyz || !phi)) return fail(SHGO_ERR_INVALID_ARG, "NULL points or phi");
+  if (basis->nbf > 0 && !density) return fail(SHGO_ERR_INVALID_ARG, "density is NULL");
+  if (points->n == 0) return SHGO_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  std::string err;
+  const shgo_status st = launch_esp(basis->d, *basis->tabs, basis->work, basis->nbf, density, points->n, points->xyz,
+                                    phi, basis->d.rbuf, (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+
 shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream) {
   g_last_error.clear();
   if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");

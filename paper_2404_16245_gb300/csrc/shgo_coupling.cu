@@ -102,11 +102,72 @@ __host__ __device__ constexpr int column_split(int lam) {
   return best;
 }
 
+// Tables of one nucleus (or point) for the chunk column `lane`: warp 0 writes the radial sums
+// |d|^L beta_{L,k}/k! (times the charge z) into column lane of Btab and the harmonic columns m < MS of
+// U_LM(d/|d|) into Stab, warp 1 the columns m >= MS.  d is C - P in the pair frame.
+template <int LAM, int CS>
+__device__ __forceinline__ void point_tables(int wid, int lane, double p, double dx, double dy, double dz, double z,
+                                             const double* __restrict__ boys_tab, double* Stab, double* Btab) {
+  constexpr int MS = column_split(LAM);
+  const double s2 = dx * dx + dy * dy + dz * dz;
+  // unit vector and length of d (d = 0 leaves only L = 0, which any unit vector gives)
+  double ex = 0.0, ey = 0.0, ez = 1.0, dn = 0.0;
+  if (s2 > 0.0) {
+    const double ri = rsqrt(s2);
+    dn = s2 * ri;
+    ex = dx * ri;
+    ey = dy * ri;
+    ez = dz * ri;
+  }
+  if (wid == 0) {
+    const double T = p * s2;
+    double F[LAM + 1];
+    boys_eval(LAM, T, F, 1, boys_tab, k_boys);
+    // G_n = Z |d|^n F_n and tau_j = (p |d|)^j / j!
+    double zp = z;
+#pragma unroll
+    for (int n = 0; n <= LAM; ++n) {
+      F[n] *= zp;
+      zp *= dn;
+    }
+    double tau[LAM / 2 + 1];
+    tau[0] = 1.0;
+    const double pdn = p * dn;
+#pragma unroll
+    for (int k = 1; k <= LAM / 2; ++k) tau[k] = tau[k - 1] * pdn * k_boys.inv_int[k];
+    // |d|^L beta_{L,k} / k! = sum_{j<=k} tau_j G_{L+j}, running sums over k
+    double* bcol = Btab + lane;
+    int bo = 0;
+#pragma unroll
+    for (int L = 0; L <= LAM; ++L) {
+      double acc = F[L];
+      bcol[bo * CS] = acc;
+#pragma unroll
+      for (int k = 1; k <= (LAM - L) / 2; ++k) {
+        acc = fma(tau[k], F[L + k], acc);
+        bcol[(bo + k) * CS] = acc;
+      }
+      bo += (LAM - L) / 2 + 1;
+    }
+    if constexpr (MS > -LAM) harmonic_columns<LAM, CS, -LAM, MS - 1>(ex, ey, ez, Stab + lane);
+  } else {
+    if constexpr (MS <= LAM) harmonic_columns<LAM, CS, MS, LAM>(ex, ey, ez, Stab + lane);
+  }
+}
+
+// C - P in the pair frame for the nucleus at `c` (Q rows, A the a-shell centre, shift = |P - A|).
+__device__ __forceinline__ void pair_frame_offset(const double* Q, double Ax, double Ay, double Az, double shift,
+                                                  const double* c, double& dx, double& dy, double& dz) {
+  const double ux = c[0] - Ax, uy = c[1] - Ay, uz = c[2] - Az;
+  dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
+  dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
+  dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - shift;
+}
+
 template <int NCH, int LAM>
 __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
   using Sh = CouplingShape<LAM, NCH>;
   constexpr int nS = Sh::nS, nR = Sh::nR, CS = Sh::CS;
-  constexpr int MS = column_split(LAM);
   extern __shared__ __align__(16) double smem[];
   double* Stab = smem;             // [nS][CS]
   double* Btab = Stab + nS * CS;   // [nB][CS]
@@ -121,7 +182,6 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
     // primitive pairs with a zero prefactor (K_AB of Eq. 5 underflowed, or the pair is below the
     // per-basis bound) are skipped by the pair kernel too, so their coupling block is not needed
     if (pd.pref == 0.0) continue;
-    const double p = pd.p;
     // C - P = (C - A) - (beta/p)(B - A), in the pair frame where B - A is along z
     const double Ax = A.shell_xyz[3 * a], Ay = A.shell_xyz[3 * a + 1], Az = A.shell_xyz[3 * a + 2];
     double Q[9];
@@ -137,56 +197,10 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
         double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
         if (c0 + lane < ncen) {
           const int64_t c = mol_center_index(A.mv, cbeg + c0 + lane);
-          const double ux = A.centers[3 * c] - Ax, uy = A.centers[3 * c + 1] - Ay, uz = A.centers[3 * c + 2] - Az;
-          dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
-          dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
-          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - pd.shift;
+          pair_frame_offset(Q, Ax, Ay, Az, pd.shift, A.centers + 3 * c, dx, dy, dz);
           z = A.charges[c];
         }
-        const double s2 = dx * dx + dy * dy + dz * dz;
-        // unit vector and length of d (d = 0 leaves only L = 0, which any unit vector gives)
-        double ex = 0.0, ey = 0.0, ez = 1.0, dn = 0.0;
-        if (s2 > 0.0) {
-          const double ri = rsqrt(s2);
-          dn = s2 * ri;
-          ex = dx * ri;
-          ey = dy * ri;
-          ez = dz * ri;
-        }
-        if (wid == 0) {
-          const double T = p * s2;
-          double F[LAM + 1];
-          boys_eval(LAM, T, F, 1, A.boys_tab, k_boys);
-          // G_n = Z |d|^n F_n and tau_j = (p |d|)^j / j!
-          double zp = z;
-#pragma unroll
-          for (int n = 0; n <= LAM; ++n) {
-            F[n] *= zp;
-            zp *= dn;
-          }
-          double tau[LAM / 2 + 1];
-          tau[0] = 1.0;
-          const double pdn = p * dn;
-#pragma unroll
-          for (int k = 1; k <= LAM / 2; ++k) tau[k] = tau[k - 1] * pdn * k_boys.inv_int[k];
-          // |d|^L beta_{L,k} / k! = sum_{j<=k} tau_j G_{L+j}, running sums over k
-          double* bcol = Btab + lane;
-          int bo = 0;
-#pragma unroll
-          for (int L = 0; L <= LAM; ++L) {
-            double acc = F[L];
-            bcol[bo * CS] = acc;
-#pragma unroll
-            for (int k = 1; k <= (LAM - L) / 2; ++k) {
-              acc = fma(tau[k], F[L + k], acc);
-              bcol[(bo + k) * CS] = acc;
-            }
-            bo += (LAM - L) / 2 + 1;
-          }
-          if constexpr (MS > -LAM) harmonic_columns<LAM, CS, -LAM, MS - 1>(ex, ey, ez, Stab + lane);
-        } else {
-          if constexpr (MS <= LAM) harmonic_columns<LAM, CS, MS, LAM>(ex, ey, ez, Stab + lane);
-        }
+        point_tables<LAM, CS>(wid, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
       }
       __syncthreads();
       // a partial last chunk sums only its occupied columns (rounded up to a pair; empty columns
@@ -227,7 +241,80 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
   }
 }
 
+// Electrostatic potential (adjoint of the coupling): for a chunk of NCH points and a range of primitive
+// pairs of one class, phi(C) += sum_e G'[e] U_{L(e)M(e)}(d/|d|) |d|^L beta_{L,k}/k! (d = C - P, unit
+// charge), G' being the density-weighted adjoint block of the primitive pair (k_esp_adjoint).  Block
+// (chunk, split): the splits divide the class's primitive pairs; each block adds its partial sums to
+// phi once per point.
+template <int NCH, int LAM>
+__global__ void __launch_bounds__(64) k_esp_fp64(EspArgs A) {
+  using Sh = CouplingShape<LAM, NCH>;
+  constexpr int nS = Sh::nS, nR = Sh::nR, CS = Sh::CS;
+  extern __shared__ __align__(16) double smem[];
+  double* Stab = smem;
+  double* Btab = Stab + nS * CS;
+  double* gam = Btab + Sh::nB * CS;  // [nR]
+  double* part = gam + nR;           // [NCH] partial sums of warp 1
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int chunk = blockIdx.x % A.nchunks, split = blockIdx.x / A.nchunks;
+  const int64_t per = (A.npp + A.nsplit - 1) / A.nsplit;
+  const int64_t w0 = split * per, w1 = min(A.npp, w0 + per);
+  const int64_t c = (int64_t)chunk * NCH + lane;
+  const bool valid = lane < NCH && c < A.npoints;
+  double acc = 0.0;
+  // R' entries split between the warps for the point sums
+  const int e0 = wid == 0 ? 0 : nR / 2, e1 = wid == 0 ? nR / 2 : nR;
+  for (int64_t w = w0; w < w1; ++w) {
+    const int64_t q = A.pp_base + w;
+    const PPData pd = A.ppd[q];
+    if (pd.pref == 0.0) continue;
+    const int pr = A.pp_pair[q];
+    const int a = A.pair_a[pr];
+    const double Ax = A.shell_xyz[3 * a], Ay = A.shell_xyz[3 * a + 1], Az = A.shell_xyz[3 * a + 2];
+    double Q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Q[k] = A.site_rot[9 * A.pair_site[pr] + k];
+    __syncthreads();  // the previous primitive pair is done with the tables and gam
+    for (int e = tid; e < nR; e += 64) gam[e] = A.gam[w * (int64_t)nR + e];
+    if (lane < NCH) {
+      double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
+      if (valid) {
+        pair_frame_offset(Q, Ax, Ay, Az, pd.shift, A.points + 3 * c, dx, dy, dz);
+        z = 1.0;
+      }
+      point_tables<LAM, CS>(wid, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
+    }
+    __syncthreads();
+    if (lane < NCH) {
+      double s0 = 0.0, s1 = 0.0;
+      int e = e0;
+      for (; e + 1 < e1; e += 2) {
+        const int c0 = __ldg(A.rmap + e), c1 = __ldg(A.rmap + e + 1);
+        s0 = fma(gam[e] * Stab[(c0 & 0xfff) * CS + lane], Btab[((c0 >> 12) & 0xfff) * CS + lane], s0);
+        s1 = fma(gam[e + 1] * Stab[(c1 & 0xfff) * CS + lane], Btab[((c1 >> 12) & 0xfff) * CS + lane], s1);
+      }
+      if (e < e1) {
+        const int c0 = __ldg(A.rmap + e);
+        s0 = fma(gam[e] * Stab[(c0 & 0xfff) * CS + lane], Btab[((c0 >> 12) & 0xfff) * CS + lane], s0);
+      }
+      acc += s0 + s1;
+    }
+  }
+  __syncthreads();
+  if (wid == 1 && lane < NCH) part[lane] = acc;
+  __syncthreads();
+  if (wid == 0 && valid) atomicAdd(A.phi + c, acc + part[lane]);
+}
+
 using CouplingKernel = void (*)(CouplingArgs);
+using EspKernel = void (*)(EspArgs);
+
+template <int... L>
+constexpr EspKernel esp_kernel_at(int lam, std::integer_sequence<int, L...>) {
+  EspKernel k = nullptr;
+  ((lam == L ? (k = &k_esp_fp64<32, L>, 0) : 0), ...);
+  return k;
+}
 
 template <int NCH, int... L>
 constexpr CouplingKernel kernel_at(int lam, std::integer_sequence<int, L...>) {
@@ -257,6 +344,15 @@ size_t coupling_fp64_smem(int lam, int nch) {
   return nch == 16 ? smem_at<16>(lam, Lams{}) : smem_at<32>(lam, Lams{});
 }
 
+size_t esp_fp64_smem(int lam) { return coupling_fp64_smem(lam, 32) + sizeof(double) * 40; }
+
+cudaError_t launch_esp_fp64(int lam, const EspArgs& args, cudaStream_t stream) {
+  if (lam < 0 || lam > kLamMax) return cudaErrorInvalidValue;
+  const EspKernel k = esp_kernel_at(lam, Lams{});
+  k<<<args.nchunks * args.nsplit, 64, esp_fp64_smem(lam), stream>>>(args);
+  return cudaGetLastError();
+}
+
 cudaError_t coupling_fp64_setup() {
   cudaError_t e = cudaMemcpyToSymbol(k_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_boys, &boys_const_host(), sizeof(BoysConst));
@@ -265,6 +361,8 @@ cudaError_t coupling_fp64_setup() {
       e = cudaFuncSetAttribute(coupling_kernel(lam, nch), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       if (e != cudaSuccess) break;
     }
+  for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam)
+    e = cudaFuncSetAttribute(esp_kernel_at(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   return e;
 }
 

@@ -83,6 +83,13 @@ struct Tables {
   std::vector<int> g_grpbase;   // [n classes]
   std::vector<int> g_termbase;  // [n classes]
   std::vector<int> g_nnz;       // [n classes] nonzero coupling coefficients (without padding)
+  // The same coupling, transposed (for the adjoint used by the electrostatic potential): per class,
+  // for each R' entry e of Lambda = la + lb, terms gt_terms[gt_ptr[gt_base[c] + e] .. + 1] of
+  // (coefficient, W index (row-major, w_stride(lb) columns), l1 (lb + 1) + l2).
+  std::vector<int> gt_ptr;      // class c: gt_base[c] .. + n_r(Lambda) + 1 (term offsets local to the class)
+  std::vector<GTerm> gt_terms;
+  std::vector<int> gt_base;     // [n classes]
+  std::vector<int> gt_termbase; // [n classes]
   // R layout per Lambda: packed (harm index | beta index << 12 | k << 24) for entry e.
   std::vector<int> rmap;
   std::vector<int> rmap_off;  // [kLamMax + 2]
@@ -121,6 +128,8 @@ struct DeviceTables {
   int* eoff = nullptr;
   int* g_rowinfo = nullptr;
   int* g_grp = nullptr;
+  int* gt_ptr = nullptr;
+  GTerm* gt_terms = nullptr;
   GTerm* g_terms = nullptr;
   int* rmap = nullptr;
   double* rnorm = nullptr;
@@ -279,6 +288,12 @@ shgo_status launch_class_timed(const DeviceBasis& db, const DeviceTables& dt, co
                                const MolView& mv, const double* centers, const double* charges, double* out,
                                cudaStream_t stream, double* ms, std::string* err);
 
+// Electrostatic potential phi[k] = sum_ab D_ab <a|1/|r - points_k||b> of a single basis (D device,
+// nbf x nbf row-major, symmetric); gbuf holds n_r(Lambda) doubles per primitive pair of every class.
+shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                       int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
+                       cudaStream_t stream, std::string* err);
+
 // Overlap blocks of every shell pair into out (one molecule or a batch, per mv).
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err);
@@ -300,6 +315,25 @@ struct CouplingArgs {
   const PPData* ppd = nullptr;
   double* rbuf = nullptr;
 };
+// Arguments of the electrostatic-potential kernel for one class (shgo_coupling.cu).
+struct EspArgs {
+  int64_t npp = 0, pp_base = 0;  // the class's primitive pairs
+  const int* pp_pair = nullptr;
+  const int* pair_a = nullptr;
+  const double* shell_xyz = nullptr;
+  const double* site_rot = nullptr;
+  const int* pair_site = nullptr;
+  const PPData* ppd = nullptr;
+  const double* boys_tab = nullptr;
+  const int* rmap = nullptr;     // R layout of this Lambda
+  const double* gam = nullptr;   // adjoint blocks of the class, n_r(Lambda) per primitive pair
+  int64_t npoints = 0;
+  const double* points = nullptr;
+  double* phi = nullptr;
+  int nchunks = 0, nsplit = 0;   // blocks = nchunks x nsplit
+};
+cudaError_t launch_esp_fp64(int lam, const EspArgs& args, cudaStream_t stream);
+
 // Launches the Lambda = lam instantiation with nucleus chunks of nch (16 or 32) on `grid` warps.
 cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream);
 size_t coupling_fp64_smem(int lam, int nch);

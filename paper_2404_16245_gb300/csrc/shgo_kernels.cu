@@ -583,6 +583,150 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   }
 }
 
+// Adjoint of the pair kernel for the electrostatic potential: for one shell pair and a symmetric
+// density D, the weights G'[e] of every primitive pair such that
+//   sum_{mu in a, nu in b} D_{mu nu} V_{mu nu} (+ the transposed block when a != b) = sum_pp sum_e G'_pp[e] racc_pp[e],
+// racc being the unscaled nucleus sums of the coupling kernel.  Steps reversed: the density block is
+// rotated into the pair frame (D' = D^la^T D_blk D^lb), weighted by the translation factors
+// (Wbar[l1 m1][l2 m2] = t_A(l1, m1) t_B(l2, m2) D'[m1][m2]), pulled back through the Gaunt coupling
+// (transposed program, primitive factors) and scaled by 2 pi k! p^{-(k+1)} N_LM.
+__host__ __device__ inline size_t esp_adjoint_smem(int la, int lb) {
+  const int nWa = (la + 1) * (la + 1), na = 2 * la + 1, nb = 2 * lb + 1, lm = la > lb ? la : lb;
+  return sizeof(double) * ((size_t)nWa * w_stride(lb) + na * na + nb * nb + (la + 1) * na + (lb + 1) * nb +
+                           3 * na * nb + (la + 1) * (lb + 1) + (la + lb) / 2 + 1 + lm + 1 + 8 + 32);
+}
+
+__global__ void __launch_bounds__(128) k_esp_adjoint(int la, int lb, int npairs, int pair_base, int64_t pp_base,
+                                                     const int* __restrict__ pair_a, const int* __restrict__ pair_b,
+                                                     const int64_t* __restrict__ pair_ppoff,
+                                                     const int* __restrict__ pair_site, int64_t rot_per,
+                                                     const double* __restrict__ rotd,
+                                                     const int* __restrict__ shell_nprim,
+                                                     const int64_t* __restrict__ shell_foff,
+                                                     const double* __restrict__ etab, const int* __restrict__ eoff,
+                                                     const int* __restrict__ gt_ptr, const GTerm* __restrict__ gt_terms,
+                                                     const int* __restrict__ rmap, const double* __restrict__ rnorm,
+                                                     const PPData* __restrict__ ppd, const double* __restrict__ D,
+                                                     int64_t ld, double* __restrict__ gam) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lam = la + lb, nR = n_r(lam);
+  const int nWa = (la + 1) * (la + 1), ws = w_stride(lb), nWs = nWa * ws;
+  const int na = 2 * la + 1, nb = 2 * lb + 1;
+  const int lm = la > lb ? la : lb;
+  const int nDb = la != lb ? nb * nb : 0;
+  double* Wb = smem;                       // [l1 m1][l2 m2], row stride ws
+  double* Dm = Wb + nWs;                   // D^la, then D^lb when lb != la
+  double* tA = Dm + na * na + nb * nb;
+  double* tB = tA + (la + 1) * na;
+  double* Db = tB + (lb + 1) * nb;         // density block [ma][mb]
+  double* Y = Db + na * nb;
+  double* Dp = Y + na * nb;                // pair-frame density
+  double* fab = Dp + na * nb;
+  double* scl = fab + (la + 1) * (lb + 1);
+  double* dpow = scl + lam / 2 + 1;
+  double* scal = dpow + lm + 1;
+  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
+    const int pr = pair_base + w;
+    const int a = pair_a[pr], b = pair_b[pr];
+    const double* rd = rotd + (int64_t)pair_site[pr] * rot_per;
+    const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
+    __syncthreads();
+    if (tid == 0) {
+      double v = 1.0;
+      for (int k = 0; k <= lm; ++k) {
+        dpow[k] = v;
+        v *= rd[0];
+      }
+    }
+    for (int e = tid; e < na * na; e += nth) Dm[e] = rd[1 + rot_doff(la) + e];
+    for (int e = tid; e < nDb; e += nth) Dm[na * na + e] = rd[1 + rot_doff(lb) + e];
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      double v = D[(fa0 + ma) * ld + fb0 + mb];
+      if (a != b) v += D[(fb0 + mb) * ld + fa0 + ma];
+      Db[e] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < (la + 1) * na; e += nth) {
+      const int l1 = e / na, ma = e % na - la, lr = la - l1;
+      tA[e] = l1 >= (ma < 0 ? -ma : ma) ? etab[eoff[la] + translation_offset_dev(la, ma, l1, ma) + lr] * dpow[lr] : 0.0;
+    }
+    for (int e = tid; e < (lb + 1) * nb; e += nth) {
+      const int l2 = e / nb, mb = e % nb - lb, lr = lb - l2;
+      tB[e] = l2 >= (mb < 0 ? -mb : mb)
+                  ? etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr] * ((lr & 1) ? -dpow[lr] : dpow[lr])
+                  : 0.0;
+    }
+    const double* Da = Dm;
+    const double* Dbr = la != lb ? Dm + na * na : Dm;
+    // Y = D_blk D^lb, then D' = D^la^T Y
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, k = e % nb;
+      double sacc = 0.0;
+      for (int mb = 0; mb < nb; ++mb) sacc = fma(Db[ma * nb + mb], Dbr[mb * nb + k], sacc);
+      Y[e] = sacc;
+    }
+    __syncthreads();
+    for (int e = tid; e < na * nb; e += nth) {
+      const int k = e / nb, k2 = e % nb;
+      double sacc = 0.0;
+      for (int ma = 0; ma < na; ++ma) sacc = fma(Da[ma * na + k], Y[ma * nb + k2], sacc);
+      Dp[e] = sacc;
+    }
+    __syncthreads();
+    for (int e = tid; e < nWs; e += nth) {
+      const int i1 = e / ws, i2 = e % ws;
+      double v = 0.0;
+      if (i2 < (lb + 1) * (lb + 1)) {
+        int l1 = 0, l2 = 0;
+        while ((l1 + 1) * (l1 + 1) <= i1) ++l1;
+        while ((l2 + 1) * (l2 + 1) <= i2) ++l2;
+        const int m1 = i1 - l1 * l1 - l1, m2 = i2 - l2 * l2 - l2;
+        v = tA[l1 * na + m1 + la] * tB[l2 * nb + m2 + lb] * Dp[(m1 + la) * nb + m2 + lb];
+      }
+      Wb[e] = v;
+    }
+    const int npp = shell_nprim[a] * shell_nprim[b];
+    const int64_t q0 = pair_ppoff[pr];
+    for (int ij = 0; ij < npp; ++ij) {
+      __syncthreads();
+      if (tid == 0) {
+        const PPData pd = ppd[q0 + ij];
+        scal[0] = pd.pref;
+        scal[1] = pd.ra;
+        scal[2] = pd.rb;
+        scal[3] = pd.rp;
+      }
+      __syncthreads();
+      double* g = gam + (q0 + ij - pp_base) * (int64_t)nR;
+      if (scal[0] == 0.0) continue;  // skipped by the potential kernel as well
+      if (tid < (la + 1) * (lb + 1)) {
+        const int l1 = tid / (lb + 1), l2 = tid % (lb + 1);
+        double v = scal[0];
+        for (int k = 0; k < la - l1; ++k) v *= scal[1];
+        for (int k = 0; k < lb - l2; ++k) v *= scal[2];
+        fab[tid] = v;
+      }
+      if (tid <= lam / 2) {
+        double sv = 6.283185307179586476925286766559 * scal[3];
+        for (int k = 1; k <= tid; ++k) sv *= double(k) * scal[3];
+        scl[tid] = sv;
+      }
+      __syncthreads();
+      for (int e = tid; e < nR; e += nth) {
+        double acc = 0.0;
+        for (int t = gt_ptr[e]; t < gt_ptr[e + 1]; ++t) {
+          const GTerm gt = gt_terms[t];
+          acc = fma(gt.coef * fab[gt.pad], Wb[gt.ridx], acc);
+        }
+        const int code = __ldg(rmap + e);
+        g[e] = acc * (scl[(code >> 24) & 0xff] * __ldg(rnorm + e));
+      }
+    }
+  }
+}
+
 // Overlap block of one shell pair (Eqs. 9-10): both orbitals translated to P (Eq. 7) in the pair
 // frame, where the one-centre integrals are diagonal by orthogonality,
 //   int S_{l1 m1}(r_P) S_{l2 m2}(r_P) e^{-p r_P^2} = delta delta 4 pi (pi/2)^{1/2} (2 l1 - 1)!! / (2p)^{l1+3/2},
@@ -729,6 +873,8 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.eoff, t.eoff);
   if (e == cudaSuccess) e = upload(&d.g_rowinfo, t.g_rowinfo);
   if (e == cudaSuccess) e = upload(&d.g_grp, t.g_grp);
+  if (e == cudaSuccess) e = upload(&d.gt_ptr, t.gt_ptr);
+  if (e == cudaSuccess) e = upload(&d.gt_terms, t.gt_terms);
   if (e == cudaSuccess) e = upload(&d.g_terms, t.g_terms);
   if (e == cudaSuccess) e = upload(&d.rmap, t.rmap);
   if (e == cudaSuccess) e = upload(&d.rnorm, t.rnorm);
@@ -1225,6 +1371,58 @@ shgo_status live_counts(const DeviceBasis& db, const std::vector<ClassWork>& wor
   for (int c = 0; c < nc; ++c) {
     live_pp[c] = (int64_t)hp[c];
     live_pairs[c] = (int64_t)hq[c];
+  }
+  return SHGO_OK;
+}
+
+shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                       int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
+                       cudaStream_t stream, std::string* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_esp_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  const Tables& th = tables_host();
+  cudaError_t e = cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)std::max<int64_t>(npoints, 1), stream);
+  int64_t gb = 0;
+  for (const ClassWork& w : work) {
+    if (w.npairs == 0 || e != cudaSuccess) continue;
+    const int lam = w.la + w.lb, cid = class_id(w.la, w.lb);
+    double* g = gbuf + gb;
+    k_esp_adjoint<<<grid_cap(w.npairs, 16), pair_threads(w.la, w.lb), esp_adjoint_smem(w.la, w.lb), stream>>>(
+        w.la, w.lb, w.npairs, w.pair_base, w.pp_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site,
+        rot_block(db.rot_lmax), db.rotd, db.shell_nprim, db.shell_foff, dt.etab, dt.eoff,
+        dt.gt_ptr + th.gt_base[cid], dt.gt_terms + th.gt_termbase[cid], dt.rmap + th.rmap_off[lam],
+        dt.rnorm + th.rmap_off[lam], db.ppd, D, nbf, g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || npoints == 0) {
+      gb += w.npp * n_r(lam);
+      continue;
+    }
+    EspArgs A;
+    A.npp = w.npp;
+    A.pp_base = w.pp_base;
+    A.pp_pair = db.pp_pair;
+    A.pair_a = db.pair_a;
+    A.shell_xyz = db.shell_xyz;
+    A.site_rot = db.site_rot;
+    A.pair_site = db.pair_site;
+    A.ppd = db.ppd;
+    A.boys_tab = dt.boys;
+    A.rmap = dt.rmap + th.rmap_off[lam];
+    A.gam = g;
+    A.npoints = npoints;
+    A.points = points;
+    A.phi = phi;
+    A.nchunks = (int)((npoints + 31) / 32);
+    A.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(w.npp, (int64_t)152 * 8 / A.nchunks));
+    e = launch_esp_fp64(lam, A, stream);
+    gb += w.npp * n_r(lam);
+  }
+  if (e != cudaSuccess) {
+    *err = std::string("electrostatic potential: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
   }
   return SHGO_OK;
 }

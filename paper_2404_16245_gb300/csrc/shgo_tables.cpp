@@ -267,6 +267,10 @@ void build_tables(Tables& t) {
   t.g_grpbase.assign(kNumClasses, 0);
   t.g_termbase.assign(kNumClasses, 0);
   t.g_nnz.assign(kNumClasses, 0);
+  t.gt_base.assign(kNumClasses, 0);
+  t.gt_termbase.assign(kNumClasses, 0);
+  t.gt_ptr.clear();
+  t.gt_terms.clear();
   t.g_rowinfo.clear();
   t.g_grp.clear();
   t.g_terms.clear();
@@ -325,6 +329,32 @@ void build_tables(Tables& t) {
           t.g_rowinfo.push_back((i1 * ws + i2) | (l1 << 16) | (l2 << 20));
           t.g_nnz[cid] += (int)row_terms(e).size();
         }
+      }
+      // transposed program: for each R' entry, the (coefficient, W entry, l1 l2) pairs feeding it
+      {
+        const int nr = n_r(lam);
+        std::vector<std::vector<GTerm>> byr(nr);
+        for (int i1 = 0; i1 < nWa; ++i1)
+          for (int i2 = 0; i2 < nWb; ++i2) {
+            int l1 = 0, l2 = 0;
+            while ((l1 + 1) * (l1 + 1) <= i1) ++l1;
+            while ((l2 + 1) * (l2 + 1) <= i2) ++l2;
+            for (const auto& v : row_terms(i1 * nWb + i2)) {
+              const int hi = v.first & 0xfff, k = v.first >> 12;
+              int L = 0;
+              while ((L + 1) * (L + 1) <= hi) ++L;
+              byr[ridx(L, hi - L * L - L, k)].push_back(GTerm{v.second, i1 * ws + i2, l1 * (lb + 1) + l2});
+            }
+          }
+        t.gt_base[cid] = (int)t.gt_ptr.size();
+        t.gt_termbase[cid] = (int)t.gt_terms.size();
+        int loc = 0;
+        for (int e = 0; e < nr; ++e) {
+          t.gt_ptr.push_back(loc);
+          for (const GTerm& g : byr[e]) t.gt_terms.push_back(g);
+          loc += (int)byr[e].size();
+        }
+        t.gt_ptr.push_back(loc);
       }
     }
 }

@@ -79,6 +79,9 @@ def _load() -> ctypes.CDLL:
     lib.shgo_nuclear_attraction_class_timed.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers),
                                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, f64p]
     lib.shgo_nuclear_attraction_class_timed.restype = ctypes.c_int
+    lib.shgo_esp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
+                             ctypes.c_void_p]
+    lib.shgo_esp.restype = ctypes.c_int
     lib.shgo_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_overlap.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
@@ -262,6 +265,27 @@ def shgo_nuclear_attraction_class_timed(basis, n_centers, centers_ptr, charges_p
                                                     ctypes.c_void_p(int(out_ptr) if out_ptr else 0),
                                                     _stream_handle(stream), _ptr(ms, ctypes.c_double)))
     return ms[:2 * n].reshape(n, 2)
+
+
+def shgo_esp(basis, density_ptr, n_points, points_ptr, phi_ptr, stream=None):
+    c = shgo_centers(int(n_points), ctypes.c_void_p(int(points_ptr) if points_ptr else 0))
+    _check(_lib.shgo_esp(ctypes.c_void_p(basis), ctypes.c_void_p(int(density_ptr) or 0), ctypes.byref(c),
+                         ctypes.c_void_p(int(phi_ptr) if phi_ptr else 0), _stream_handle(stream)))
+
+
+def esp(basis, density, points, out=None, stream=None):
+    """phi[k] = sum_ab D_ab <a|1/|r - points[k]||b> (FP64 device tensor [n]); density [nbf, nbf] and
+    points [n, 3] are CUDA float64 tensors."""
+    import torch
+    density = density.contiguous()
+    points = points.contiguous()
+    if tuple(density.shape) != (basis.nbf, basis.nbf) or density.dtype != torch.float64:
+        raise ValueError("density must be a float64 [nbf, nbf] tensor")
+    n = points.shape[0] if points.numel() else 0
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float64, device=points.device)
+    shgo_esp(basis.handle, density.data_ptr(), n, points.data_ptr() if n else 0, out.data_ptr(), stream)
+    return out[:n]
 
 
 def shgo_overlap(basis, out_ptr, stream=None):
