@@ -422,6 +422,45 @@ def run_batched(args) -> int:
     return 0
 
 
+def run_esp(args) -> int:
+    """Electrostatic potential of a density on a grid of points around the benchmark molecule (32 atoms,
+    l <= 6): a seeded symmetric density, points uniform in the molecule's box padded by 4 bohr.
+    One step = phi at all points (the adjoint pass over the density and the per-point pass)."""
+    import torch
+
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    b, C, Z = W.config2()
+    B = shgo.Basis(b)
+    rng = np.random.default_rng(7000)
+    d = rng.normal(size=(B.nbf, B.nbf))
+    D = torch.tensor((d + d.T) / 2, device=dev)
+    X = torch.tensor(rng.uniform(-4.0, 24.0, (args.points, 3)), device=dev)
+    phi = torch.empty(args.points, dtype=torch.float64, device=dev)
+    for _ in range(max(3, args.warmup)):
+        shgo.esp(B, D, X, out=phi, stream=stream)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        shgo.esp(B, D, X, out=phi, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    npairs = B.npairs
+    line = {"metric": "electrostatic potential points/s", "value": args.points / (ms / 1e3), "unit": "points/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"potential of a density of the 32-atom l <= 6 basis at {args.points} points",
+                       "shell_pairs": npairs, "shell_pair_points_per_s": npairs * args.points / (ms / 1e3)}}
+    print(json.dumps(line), flush=True)
+    B.close()
+    return 0
+
+
 def _cluster(seed: int, n_atoms: int):
     """Screening workload: atoms uniform at 0.1 atoms/bohr^3, Z ~ U{1..9}, 4s3p2d1f on every atom
     with 1..6 primitives, exponents log-uniform [0.05, 5000]."""
@@ -609,9 +648,10 @@ def main():
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
     ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
-    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened"],
+    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
+    ap.add_argument("--points", type=int, default=100000, help="points of the potential workload")
     ap.add_argument("--atoms", type=int, default=200, help="atoms of the screening cluster")
     ap.add_argument("--train-atoms", type=int, default=120, help="atoms of the training cluster")
     ap.add_argument("--train-triples", type=int, default=1_000_000)
@@ -643,6 +683,8 @@ def main():
         return run_batched(args)
     if args.workload == "screened":
         return run_screened(args)
+    if args.workload == "esp":
+        return run_esp(args)
     ws, rank, local = _dist()
     if ws > 1:
         import torch
