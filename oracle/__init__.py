@@ -63,6 +63,10 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
         lib.oracle_nuclear_attraction.argtypes = [
             ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_long, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_nuclear_attraction.restype = ctypes.c_int
+        lib.oracle_nuclear_field.argtypes = [
+            ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_long, _f64p, _f64p, ctypes.c_int, _f64p,
+            ctypes.c_int]
+        lib.oracle_nuclear_field.restype = ctypes.c_int
         lib.oracle_overlap.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_overlap.restype = ctypes.c_int
         lib.oracle_prim_norm.argtypes = [ctypes.c_int, ctypes.c_double]
@@ -99,6 +103,25 @@ def nuclear_attraction(basis, centers, charges, threads: int = 1, precision: str
     if rc != 0:
         raise ValueError(f"oracle rejected the basis (code {rc})")
     return out[: n * n].reshape(n, n)
+
+
+def nuclear_field(basis, centers, charges, threads: int = 1, precision: str = "f64") -> np.ndarray:
+    """dV/dC: [3, nbf, nbf], component c = sum_C Z_C d/dC_c <phi_a|1/|r-C||phi_b> (McMurchie-Davidson:
+    d/dC_x R_tuv(P - C) = -R_{t+1,u,v})."""
+    l, nprim, exps, coefs, xyz = _basis_arrays(basis)
+    C = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    Z = np.ascontiguousarray(charges, dtype=np.float64).reshape(-1)
+    n = nbf(basis)
+    res = np.zeros((3, n, n))
+    for c in range(3):
+        out = np.zeros(max(n * n, 1), dtype=np.float64)
+        rc = _lib(precision).oracle_nuclear_field(len(l), l, nprim, exps, coefs, xyz, len(Z),
+                                                  C if C.size else np.zeros(3), Z if Z.size else np.zeros(1), c,
+                                                  out, threads)
+        if rc != 0:
+            raise ValueError(f"oracle rejected the basis (code {rc})")
+        res[c] = out[: n * n].reshape(n, n)
+    return res
 
 
 def overlap(basis, threads: int = 1, precision: str = "f64") -> np.ndarray:

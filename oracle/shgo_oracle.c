@@ -349,10 +349,14 @@ static int setup_shells(int n_shells, const int* l, const int* nprim, const doub
  *   sum_C Z_C <a, ma | 1/|r-C| | b, mb>.
  * Per primitive pair: R^0_tuv is summed over nuclei weighted by Z_C (the operator of Eq. 11 is
  * the sum of the nuclear potentials), then contracted with E^x_t E^y_u E^z_v and (2 pi / p). */
+/* dcomp < 0: the block of sum_C Z_C <a|1/|r-C||b>.  dcomp = 0, 1, 2: its derivative with respect to the
+ * x, y or z coordinate of the nuclei, sum_C Z_C d/dC_c <a|1/|r-C||b>: R_tuv depends on C through P - C,
+ * and d/dC_x R_tuv(P - C) = -R_{t+1,u,v}, so the same sum runs over the shifted R table. */
 static void nuclear_block(const shell_t* a, const shell_t* b, const real* ca, const real* cb, long nC,
-                          const double* C, const double* Z, real* out) {
+                          const double* C, const double* Z, real* out, int dcomp) {
   const int la = a->l, lb = b->l, L = la + lb, nca = ncart(la), ncb = ncart(lb);
-  const int tdim = L + 1, d = L + 1;
+  const int Lr = dcomp >= 0 ? L + 1 : L;  /* order of the R table */
+  const int tdim = L + 1, d = Lr + 1;
   real* Ex = (real*)malloc(sizeof(real) * 3 * (size_t)(la + 1) * (lb + 1) * tdim);
   real* Ey = Ex + (size_t)(la + 1) * (lb + 1) * tdim;
   real* Ez = Ey + (size_t)(la + 1) * (lb + 1) * tdim;
@@ -374,10 +378,10 @@ static void nuclear_block(const shell_t* a, const shell_t* b, const real* ca, co
       hermite_E(la, lb, p, P[2] - a->A[2], P[2] - b->A[2], E00[2], Ez);
       memset(Rs, 0, sizeof(real) * (size_t)d * d * d);
       for (long c = 0; c < nC; ++c) {
-        hermite_R(L, p, P[0] - (real)C[3 * c], P[1] - (real)C[3 * c + 1], P[2] - (real)C[3 * c + 2], work, Rc);
-        for (int t = 0; t <= L; ++t)
-          for (int u = 0; u + t <= L; ++u)
-            for (int v = 0; v + u + t <= L; ++v) Rs[(t * d + u) * d + v] += (real)Z[c] * Rc[(t * d + u) * d + v];
+        hermite_R(Lr, p, P[0] - (real)C[3 * c], P[1] - (real)C[3 * c + 1], P[2] - (real)C[3 * c + 2], work, Rc);
+        for (int t = 0; t <= Lr; ++t)
+          for (int u = 0; u + t <= Lr; ++u)
+            for (int v = 0; v + u + t <= Lr; ++v) Rs[(t * d + u) * d + v] += (real)Z[c] * Rc[(t * d + u) * d + v];
       }
       const real pre = a->coef[i] * b->coef[j] * 2 * RPI / p;
       for (int ix = la; ix >= 0; --ix)
@@ -389,11 +393,13 @@ static void nuclear_block(const shell_t* a, const shell_t* b, const real* ca, co
               const real* ex = Ex + (ix * (lb + 1) + jx) * tdim;
               const real* ey = Ey + (iy * (lb + 1) + jy) * tdim;
               const real* ez = Ez + (iz * (lb + 1) + jz) * tdim;
+              const int dt = dcomp == 0, du = dcomp == 1, dv = dcomp == 2;
               real s = 0;
               for (int t = 0; t <= ix + jx; ++t)
                 for (int u = 0; u <= iy + jy; ++u)
-                  for (int v = 0; v <= iz + jz; ++v) s += ex[t] * ey[u] * ez[v] * Rs[(t * d + u) * d + v];
-              Vc[ia * ncb + ib] += pre * s;
+                  for (int v = 0; v <= iz + jz; ++v)
+                    s += ex[t] * ey[u] * ez[v] * Rs[((t + dt) * d + u + du) * d + v + dv];
+              Vc[ia * ncb + ib] += (dcomp >= 0 ? -pre : pre) * s;
             }
         }
     }
@@ -418,7 +424,7 @@ typedef enum { OP_OVERLAP = 0, OP_NUCLEAR = 1 } op_t;
 
 static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, const double* exps,
                         const double* coefs, const double* xyz, long nC, const double* C, const double* Z,
-                        double* out, int n_threads) {
+                        double* out, int n_threads, int dcomp) {
   if (n_shells < 0) return -1;
   shell_t* sh = (shell_t*)calloc((size_t)(n_shells > 0 ? n_shells : 1), sizeof(shell_t));
   real* cart[ORACLE_LMAX + 1];
@@ -448,7 +454,7 @@ static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, c
       if (op == OP_OVERLAP)
         overlap_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], blk);
       else
-        nuclear_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], nC, C, Z, blk);
+        nuclear_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], nC, C, Z, blk, dcomp);
       for (int i = 0; i < na; ++i)
         for (int j = 0; j < nb; ++j) {
           out[(off[a] + i) * nbf + off[b] + j] = (double)blk[i * nb + j];
@@ -471,13 +477,24 @@ int oracle_nuclear_attraction(int n_shells, const int* l, const int* nprim, cons
                               const double* coefs, const double* xyz, long n_centers, const double* centers,
                               const double* charges, double* out, int n_threads) {
   return one_electron(OP_NUCLEAR, n_shells, l, nprim, exps, coefs, xyz, n_centers, centers, charges, out,
-                      n_threads);
+                      n_threads, -1);
+}
+
+/* Derivative of V with respect to coordinate `component` (0, 1, 2 = x, y, z) of the nuclei:
+ * sum_C Z_C d/dC_component <phi_a | 1/|r - C| | phi_b> (for one nucleus, the field integrals of the
+ * point C, up to sign).  Same layout and conventions as oracle_nuclear_attraction. */
+int oracle_nuclear_field(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
+                         const double* xyz, long n_centers, const double* centers, const double* charges,
+                         int component, double* out, int n_threads) {
+  if (component < 0 || component > 2) return -1;
+  return one_electron(OP_NUCLEAR, n_shells, l, nprim, exps, coefs, xyz, n_centers, centers, charges, out,
+                      n_threads, component);
 }
 
 /* S_ab = <phi_a | phi_b> (Eq. 4) over the same basis; same layout and conventions. */
 int oracle_overlap(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
                    const double* xyz, double* out, int n_threads) {
-  return one_electron(OP_OVERLAP, n_shells, l, nprim, exps, coefs, xyz, 0, NULL, NULL, out, n_threads);
+  return one_electron(OP_OVERLAP, n_shells, l, nprim, exps, coefs, xyz, 0, NULL, NULL, out, n_threads, -1);
 }
 
 /* Primitive normalisation N(l, alpha) of Eq. 1, as used above. */

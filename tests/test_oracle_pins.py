@@ -272,3 +272,37 @@ def test_double_oracle_certified_by_extended_precision(la, lb):
         worst = max(worst, float(np.max(err)))
     assert oracle.real_bits("ld") > 64
     assert worst <= 1.0
+
+
+def test_field_integrals_are_the_position_derivative_of_V():
+    # d V / d C from the shifted Hermite table against a fourth-order central difference of V itself
+    basis = W.random_basis(7, 6, 4, max_prim=2, box=2.0, exp_lo=0.2, exp_hi=5.0)
+    C, Z = np.array([[0.7, -0.3, 1.1], [1.9, 0.4, -0.6]]), np.array([1.0, -0.5])
+    F = oracle.nuclear_field(basis, C, Z, precision="ld")
+    h = 1e-3
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+
+        def f(s):
+            return oracle.nuclear_attraction(basis, C + s * e, Z, precision="ld")
+
+        fd = (8 * (f(1) - f(-1)) - (f(2) - f(-2))) / (12 * h)
+        assert np.max(np.abs(fd - F[c])) <= 1e-9 * np.max(np.abs(F[c]))
+
+
+def test_field_ss_closed_form():
+    # d/dC (2 pi / p) K_AB F_0(p |P - C|^2) N_a N_b = -(2 pi / p) K_AB N_a N_b F_1(T) 2 p (C - P)
+    a, b = 0.8, 1.7
+    A, B = np.array([0.0, 0.1, -0.2]), np.array([0.9, -0.4, 0.5])
+    C = np.array([[0.3, 0.8, 0.2]])
+    basis = W.make_basis([0, 0], [1, 1], [a, b], [1.0, 1.0], [A, B])
+    p = a + b
+    P = (a * A + b * B) / p
+    K = math.exp(-a * b / p * float(np.sum((A - B) ** 2)))
+    T = p * float(np.sum((P - C[0]) ** 2))
+    F1 = sp.gamma(1.5) * sp.gammainc(1.5, T) / (2 * T ** 1.5)  # F_1(T) by the incomplete gamma function
+    nn = oracle.prim_norm(0, a) * oracle.prim_norm(0, b)
+    ref = -(2 * math.pi / p) * K * nn * F1 * 2 * p * (C[0] - P)
+    F = oracle.nuclear_field(basis, C, np.ones(1))
+    assert np.allclose(F[:, 0, 1], ref, rtol=1e-13, atol=1e-16)
