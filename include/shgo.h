@@ -190,6 +190,16 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
 shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
                      void* stream);
 
+/* Gradient of that potential with respect to each point, grad[k][c] = d phi_k / d x_{k,c}
+ *   = sum_{a,b} D_ab d/dx_{k,c} < phi_a | 1/|r - x_k| | phi_b >
+ * (for a point charge q_k the force from the density's part of the energy sum_k q_k phi_k is -q_k grad[k];
+ * for a nucleus, its Hellmann-Feynman term).  Same pipeline as shgo_esp with derivative tables per
+ * point: gradients of the solid-harmonic polynomials (degree L -> L - 1, the raising/lowering of Eq. 3)
+ * and dB_{L,k}/dT = -T^k/k! F_{L+k+1} (one more Boys order).  grad: device [n][3], overwritten.  Same
+ * arguments, restrictions and errors as shgo_esp. */
+shgo_status shgo_esp_gradient(const shgo_basis* basis, const double* density, const shgo_centers* points,
+                              double* grad, void* stream);
+
 /* Overlap matrix S_ab = <a|b> of a basis or of every molecule of a batch (Eqs. 9-10): both
  * Gaussians of a pair translated to the product centre P (Eq. 7), where the one-centre integral is
  * diagonal in (l, m) by the orthogonality of Eq. 10, then rotated from the pair frame back to the

@@ -587,8 +587,9 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
   return SHGO_OK;
 }
 
-shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
-                     void* stream) {
+namespace {
+shgo_status esp_call(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
+                     void* stream, bool gradient) {
   g_last_error.clear();
   if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
   if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "the potential takes a single basis, not a batch");
@@ -602,10 +603,21 @@ shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_
   if (prev != basis->device) cudaSetDevice(basis->device);
   std::string err;
   const shgo_status st = launch_esp(basis->d, *basis->tabs, basis->work, basis->nbf, density, points->n, points->xyz,
-                                    phi, basis->d.rbuf, (cudaStream_t)stream, &err);
+                                    phi, basis->d.rbuf, gradient, (cudaStream_t)stream, &err);
   if (prev != basis->device) cudaSetDevice(prev);
   if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;
+}
+}  // namespace
+
+shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
+                     void* stream) {
+  return esp_call(basis, density, points, phi, stream, false);
+}
+
+shgo_status shgo_esp_gradient(const shgo_basis* basis, const double* density, const shgo_centers* points,
+                              double* grad, void* stream) {
+  return esp_call(basis, density, points, grad, stream, true);
 }
 
 shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream) {

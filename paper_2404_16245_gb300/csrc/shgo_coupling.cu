@@ -306,8 +306,196 @@ __global__ void __launch_bounds__(64) k_esp_fp64(EspArgs A) {
   if (wid == 0 && valid) atomicAdd(A.phi + c, acc + part[lane]);
 }
 
+// Solid-harmonic polynomials S~_lm(d) = |d|^l U_lm(d/|d|) (degree l, same constants as U) and their
+// gradients, columns m in [M0, M1], l <= LAM, into P, Gx, Gy, Gz at row h = l^2 + l + m (stride CS):
+// forward-mode derivatives of S~_{l+1,m} = z S~_lm + ng_lm r^2 S~_{l-1,m}, S~_{|m|+1,m} = z S~_{|m|,m}
+// and of the diagonal chain (which does not depend on z).
+template <int LAM, int CS, int M0, int M1>
+__device__ __forceinline__ void harmonic_columns_grad(double x, double y, double z, double* P, double* Gx,
+                                                      double* Gy, double* Gz) {
+  const double r2 = x * x + y * y + z * z;
+  double dp[LAM + 1], dm[LAM + 1], dpx[LAM + 1], dpy[LAM + 1], dmx[LAM + 1], dmy[LAM + 1];
+  dp[0] = dm[0] = 1.0;
+  dpx[0] = dpy[0] = dmx[0] = dmy[0] = 0.0;
+  if constexpr (LAM >= 1) {
+    dp[1] = x;
+    dm[1] = y;
+    dpx[1] = 1.0;
+    dpy[1] = 0.0;
+    dmx[1] = 0.0;
+    dmy[1] = 1.0;
+#pragma unroll
+    for (int l = 1; l < LAM; ++l) {
+      dp[l + 1] = fma(x, dp[l], -y * dm[l]);
+      dm[l + 1] = fma(y, dp[l], x * dm[l]);
+      dpx[l + 1] = dp[l] + fma(x, dpx[l], -y * dmx[l]);
+      dpy[l + 1] = fma(x, dpy[l], -y * dmy[l]) - dm[l];
+      dmx[l + 1] = fma(y, dpx[l], x * dmx[l]) + dm[l];
+      dmy[l + 1] = fma(y, dpy[l], x * dmy[l]) + dp[l];
+    }
+  }
+#pragma unroll
+  for (int m = M0; m <= M1; ++m) {
+    const int am = m < 0 ? -m : m;
+    double v0 = m < 0 ? dm[am] : dp[am];
+    double x0 = m < 0 ? dmx[am] : dpx[am], y0 = m < 0 ? dmy[am] : dpy[am], z0 = 0.0;
+    int h = am * am + am + m;
+    P[h * CS] = v0;
+    Gx[h * CS] = x0;
+    Gy[h * CS] = y0;
+    Gz[h * CS] = z0;
+    if (am + 1 <= LAM) {
+      double v1 = z * v0, x1 = z * x0, y1 = z * y0, z1 = v0;
+      h = (am + 1) * (am + 1) + am + 1 + m;
+      P[h * CS] = v1;
+      Gx[h * CS] = x1;
+      Gy[h * CS] = y1;
+      Gz[h * CS] = z1;
+#pragma unroll
+      for (int l = am + 1; l < LAM; ++l) {
+        const double g = k_harm.ng[l * l + l + m];
+        const double v2 = fma(g * r2, v0, z * v1);
+        const double x2 = fma(g, fma(2.0 * x, v0, r2 * x0), z * x1);
+        const double y2 = fma(g, fma(2.0 * y, v0, r2 * y0), z * y1);
+        const double z2 = fma(g, fma(2.0 * z, v0, r2 * z0), fma(z, z1, v1));
+        h = (l + 1) * (l + 1) + l + 1 + m;
+        P[h * CS] = v2;
+        Gx[h * CS] = x2;
+        Gy[h * CS] = y2;
+        Gz[h * CS] = z2;
+        v0 = v1; x0 = x1; y0 = y1; z0 = z1;
+        v1 = v2; x1 = x2; y1 = y2; z1 = z2;
+      }
+    }
+  }
+}
+
+template <int LAM>
+struct GradShape {
+  static constexpr int NCH = 16, CS = NCH + 2;
+  static constexpr int nS = cn_harm(LAM), nB = cn_beta(LAM), nR = cn_r(LAM);
+  static constexpr size_t smem = sizeof(double) * ((size_t)(4 * nS + 2 * nB) * CS + nR + 3 * NCH + 4 * 64 + 16);
+};
+
+// Gradient of the electrostatic potential at each point: for a chunk of 16 points and a range of
+// primitive pairs of one class, grad phi(C) += Q^T sum_e G'[e] d/dd [S~_{LM}(d) B_{L,k}(T)], d = C - P in the
+// pair frame, B_{L,k} = sum_{j<=k} T^j/j! F_{L+j} and dB_{L,k}/dT = -T^k/k! F_{L+k+1}, so
+// d/dd [S~ B] = B grad S~ - 2p T^k/k! F_{L+k+1} S~ d.  Threads: point c = t % 16; in the table phase
+// warp 0 (16 lanes) evaluates the Boys values and radial factors, warp 1 the harmonic columns; in the
+// sum phase the four groups of 16 threads take a quarter of the R' entries each.
+template <int LAM>
+__global__ void __launch_bounds__(64) k_esp_grad_fp64(EspArgs A) {
+  using Sh = GradShape<LAM>;
+  constexpr int NCH = Sh::NCH, CS = Sh::CS, nS = Sh::nS, nB = Sh::nB, nR = Sh::nR;
+  extern __shared__ __align__(16) double smem[];
+  double* Pt = smem;
+  double* Gxt = Pt + nS * CS;
+  double* Gyt = Gxt + nS * CS;
+  double* Gzt = Gyt + nS * CS;
+  double* Bt = Gzt + nS * CS;
+  double* Bq = Bt + nB * CS;
+  double* gam = Bq + nB * CS;
+  double* dv = gam + nR;      // [3][NCH]
+  double* red = dv + 3 * NCH; // [3][64]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, pc = tid & 15, quarter = tid >> 4;
+  const int chunk = blockIdx.x % A.nchunks, split = blockIdx.x / A.nchunks;
+  const int64_t per = (A.npp + A.nsplit - 1) / A.nsplit;
+  const int64_t w0 = split * per, w1 = min(A.npp, w0 + per);
+  const int64_t c = (int64_t)chunk * NCH + pc;
+  const bool valid = c < A.npoints;
+  const int e0 = quarter * nR / 4, e1 = (quarter + 1) * nR / 4;
+  double gm[3] = {0.0, 0.0, 0.0};
+  for (int64_t w = w0; w < w1; ++w) {
+    const int64_t q = A.pp_base + w;
+    const PPData pd = A.ppd[q];
+    if (pd.pref == 0.0) continue;
+    const int pr = A.pp_pair[q];
+    const int a = A.pair_a[pr];
+    double Q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Q[k] = A.site_rot[9 * A.pair_site[pr] + k];
+    double dx = 0.0, dy = 0.0, dz = 0.0;
+    if (valid)
+      pair_frame_offset(Q, A.shell_xyz[3 * a], A.shell_xyz[3 * a + 1], A.shell_xyz[3 * a + 2], pd.shift,
+                        A.points + 3 * c, dx, dy, dz);
+    __syncthreads();  // the previous primitive pair is done with the tables
+    for (int e = tid; e < nR; e += 64) gam[e] = A.gam[w * (int64_t)nR + e];
+    if (lane < NCH) {
+      if (wid == 0) {
+        dv[pc] = dx;
+        dv[NCH + pc] = dy;
+        dv[2 * NCH + pc] = dz;
+        const double T = pd.p * (dx * dx + dy * dy + dz * dz);
+        double F[LAM + 2];
+        boys_eval(LAM + 1, T, F, 1, A.boys_tab, k_boys);
+        double tk[LAM / 2 + 1];  // T^k / k!
+        tk[0] = 1.0;
+#pragma unroll
+        for (int k = 1; k <= LAM / 2; ++k) tk[k] = tk[k - 1] * T * k_boys.inv_int[k];
+        const double m2p = -2.0 * pd.p;
+        int bo = 0;
+#pragma unroll
+        for (int L = 0; L <= LAM; ++L) {
+          double acc = 0.0;
+#pragma unroll
+          for (int k = 0; k <= (LAM - L) / 2; ++k) {
+            acc = fma(tk[k], F[L + k], acc);
+            Bt[(bo + k) * CS + pc] = valid ? acc : 0.0;
+            Bq[(bo + k) * CS + pc] = valid ? m2p * tk[k] * F[L + k + 1] : 0.0;
+          }
+          bo += (LAM - L) / 2 + 1;
+        }
+      } else {
+        harmonic_columns_grad<LAM, CS, -LAM, LAM>(dx, dy, dz, Pt + pc, Gxt + pc, Gyt + pc, Gzt + pc);
+      }
+    }
+    __syncthreads();
+    double gx = 0.0, gy = 0.0, gz = 0.0, sb = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      const int code = __ldg(A.rmap + e);
+      const int si = (code & 0xfff) * CS + pc, bi = ((code >> 12) & 0xfff) * CS + pc;
+      const double g = gam[e];
+      const double ab = g * Bt[bi];
+      gx = fma(ab, Gxt[si], gx);
+      gy = fma(ab, Gyt[si], gy);
+      gz = fma(ab, Gzt[si], gz);
+      sb = fma(g * Pt[si], Bq[bi], sb);
+    }
+    gx = fma(sb, dv[pc], gx);
+    gy = fma(sb, dv[NCH + pc], gy);
+    gz = fma(sb, dv[2 * NCH + pc], gz);
+    // back to the molecular frame: grad_C = Q^T grad_d
+    gm[0] += Q[0] * gx + Q[3] * gy + Q[6] * gz;
+    gm[1] += Q[1] * gx + Q[4] * gy + Q[7] * gz;
+    gm[2] += Q[2] * gx + Q[5] * gy + Q[8] * gz;
+  }
+  __syncthreads();
+  red[tid] = gm[0];
+  red[64 + tid] = gm[1];
+  red[128 + tid] = gm[2];
+  __syncthreads();
+  if (tid < NCH && valid)
+    for (int k = 0; k < 3; ++k)
+      atomicAdd(A.phi + 3 * c + k, red[k * 64 + tid] + red[k * 64 + tid + 16] + red[k * 64 + tid + 32] +
+                                       red[k * 64 + tid + 48]);
+}
+
 using CouplingKernel = void (*)(CouplingArgs);
 using EspKernel = void (*)(EspArgs);
+
+template <int... L>
+constexpr EspKernel esp_grad_kernel_at(int lam, std::integer_sequence<int, L...>) {
+  EspKernel k = nullptr;
+  ((lam == L ? (k = &k_esp_grad_fp64<L>, 0) : 0), ...);
+  return k;
+}
+
+template <int... L>
+constexpr size_t esp_grad_smem_at(int lam, std::integer_sequence<int, L...>) {
+  size_t s = 0;
+  ((lam == L ? (s = GradShape<L>::smem, 0) : 0), ...);
+  return s;
+}
 
 template <int... L>
 constexpr EspKernel esp_kernel_at(int lam, std::integer_sequence<int, L...>) {
@@ -353,6 +541,13 @@ cudaError_t launch_esp_fp64(int lam, const EspArgs& args, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_esp_grad_fp64(int lam, const EspArgs& args, cudaStream_t stream) {
+  if (lam < 0 || lam > kLamMax) return cudaErrorInvalidValue;
+  const EspKernel k = esp_grad_kernel_at(lam, Lams{});
+  k<<<args.nchunks * args.nsplit, 64, esp_grad_smem_at(lam, Lams{}), stream>>>(args);
+  return cudaGetLastError();
+}
+
 cudaError_t coupling_fp64_setup() {
   cudaError_t e = cudaMemcpyToSymbol(k_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_boys, &boys_const_host(), sizeof(BoysConst));
@@ -361,8 +556,12 @@ cudaError_t coupling_fp64_setup() {
       e = cudaFuncSetAttribute(coupling_kernel(lam, nch), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       if (e != cudaSuccess) break;
     }
-  for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam)
+  for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam) {
     e = cudaFuncSetAttribute(esp_kernel_at(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(esp_grad_kernel_at(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               227 * 1024);
+  }
   return e;
 }
 

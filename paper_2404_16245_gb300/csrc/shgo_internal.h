@@ -290,9 +290,10 @@ shgo_status launch_class_timed(const DeviceBasis& db, const DeviceTables& dt, co
 
 // Electrostatic potential phi[k] = sum_ab D_ab <a|1/|r - points_k||b> of a single basis (D device,
 // nbf x nbf row-major, symmetric); gbuf holds n_r(Lambda) doubles per primitive pair of every class.
+// gradient = true: phi receives grad_x phi at each point, [npoints][3].
 shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                        int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
-                       cudaStream_t stream, std::string* err);
+                       bool gradient, cudaStream_t stream, std::string* err);
 
 // Overlap blocks of every shell pair into out (one molecule or a batch, per mv).
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
@@ -333,6 +334,8 @@ struct EspArgs {
   int nchunks = 0, nsplit = 0;   // blocks = nchunks x nsplit
 };
 cudaError_t launch_esp_fp64(int lam, const EspArgs& args, cudaStream_t stream);
+// Gradient of the potential: args.phi receives 3 values per point; chunks of 16 points.
+cudaError_t launch_esp_grad_fp64(int lam, const EspArgs& args, cudaStream_t stream);
 
 // Launches the Lambda = lam instantiation with nucleus chunks of nch (16 or 32) on `grid` warps.
 cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream);

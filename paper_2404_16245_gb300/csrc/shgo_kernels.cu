@@ -1377,14 +1377,15 @@ shgo_status live_counts(const DeviceBasis& db, const std::vector<ClassWork>& wor
 
 shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                        int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
-                       cudaStream_t stream, std::string* err) {
+                       bool gradient, cudaStream_t stream, std::string* err) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_esp_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
   const Tables& th = tables_host();
-  cudaError_t e = cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)std::max<int64_t>(npoints, 1), stream);
+  cudaError_t e =
+      cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)std::max<int64_t>(npoints, 1) * (gradient ? 3 : 1), stream);
   int64_t gb = 0;
   for (const ClassWork& w : work) {
     if (w.npairs == 0 || e != cudaSuccess) continue;
@@ -1415,9 +1416,10 @@ shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std:
     A.npoints = npoints;
     A.points = points;
     A.phi = phi;
-    A.nchunks = (int)((npoints + 31) / 32);
+    const int pts = gradient ? 16 : 32;
+    A.nchunks = (int)((npoints + pts - 1) / pts);
     A.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(w.npp, (int64_t)152 * 8 / A.nchunks));
-    e = launch_esp_fp64(lam, A, stream);
+    e = gradient ? launch_esp_grad_fp64(lam, A, stream) : launch_esp_fp64(lam, A, stream);
     gb += w.npp * n_r(lam);
   }
   if (e != cudaSuccess) {

@@ -82,6 +82,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_esp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
                              ctypes.c_void_p]
     lib.shgo_esp.restype = ctypes.c_int
+    lib.shgo_esp_gradient.argtypes = lib.shgo_esp.argtypes
+    lib.shgo_esp_gradient.restype = ctypes.c_int
     lib.shgo_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_overlap.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
@@ -285,6 +287,26 @@ def esp(basis, density, points, out=None, stream=None):
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.float64, device=points.device)
     shgo_esp(basis.handle, density.data_ptr(), n, points.data_ptr() if n else 0, out.data_ptr(), stream)
+    return out[:n]
+
+
+def shgo_esp_gradient(basis, density_ptr, n_points, points_ptr, grad_ptr, stream=None):
+    c = shgo_centers(int(n_points), ctypes.c_void_p(int(points_ptr) if points_ptr else 0))
+    _check(_lib.shgo_esp_gradient(ctypes.c_void_p(basis), ctypes.c_void_p(int(density_ptr) or 0), ctypes.byref(c),
+                                  ctypes.c_void_p(int(grad_ptr) if grad_ptr else 0), _stream_handle(stream)))
+
+
+def esp_gradient(basis, density, points, out=None, stream=None):
+    """grad[k] = d phi_k / d points[k] (FP64 device tensor [n, 3])."""
+    import torch
+    density = density.contiguous()
+    points = points.contiguous()
+    if tuple(density.shape) != (basis.nbf, basis.nbf) or density.dtype != torch.float64:
+        raise ValueError("density must be a float64 [nbf, nbf] tensor")
+    n = points.shape[0] if points.numel() else 0
+    if out is None:
+        out = torch.empty((max(n, 1), 3), dtype=torch.float64, device=points.device)
+    shgo_esp_gradient(basis.handle, density.data_ptr(), n, points.data_ptr() if n else 0, out.data_ptr(), stream)
     return out[:n]
 
 

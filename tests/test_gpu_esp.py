@@ -87,3 +87,40 @@ def test_no_points(shgo):
                    torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
     assert phi.numel() == 0
     B.close()
+
+
+def check_gradient(shgo, basis, D, X):
+    B = shgo.Basis(basis)
+    g = shgo.esp_gradient(B, torch.tensor(D, device="cuda"), torch.tensor(X, device="cuda")).cpu().numpy()
+    B.close()
+    for k, x in enumerate(X):
+        F = oracle.nuclear_field(basis, x[None, :], np.ones(1), threads=THREADS, precision="ld")
+        for c in range(3):
+            ref = float(np.sum(D * F[c]))
+            scale = float(np.sum(np.abs(D * F[c])))
+            assert abs(g[k, c] - ref) <= 1e-11 * scale + 1e-13, (k, c, g[k, c], ref, scale)
+
+
+def test_gradient_small_contracted_basis(shgo):
+    basis = W.random_basis(61, 10, 4, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0)
+    rng = np.random.default_rng(62)
+    X = np.vstack([rng.uniform(-1.0, 4.0, (18, 3)), basis["xyz"][:2]])
+    check_gradient(shgo, basis, density(W.nbf(basis), 63), X)
+
+
+def test_gradient_every_class_up_to_l8(shgo):
+    ls = list(range(9)) * 2
+    rng = np.random.default_rng(64)
+    sites = rng.uniform(0, 2.5, (3, 3))
+    exps = np.exp(rng.uniform(np.log(0.2), np.log(8.0), len(ls) * 2))
+    basis = W.make_basis(ls, [2] * len(ls), exps, rng.uniform(0.2, 1, len(ls) * 2),
+                         [sites[i % 3] for i in range(len(ls))])
+    X = rng.uniform(-1.0, 3.5, (5, 3))
+    check_gradient(shgo, basis, density(W.nbf(basis), 65), X)
+
+
+def test_gradient_ragged_chunks(shgo):
+    basis = W.random_basis(66, 8, 3, max_prim=2)
+    rng = np.random.default_rng(67)
+    X = np.vstack([rng.uniform(0, 4, (17, 3)), [[25.0, -3.0, 2.0]]])
+    check_gradient(shgo, basis, density(W.nbf(basis), 68), X)
