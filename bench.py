@@ -39,6 +39,9 @@ WORKLOAD = "high-l FP64: 32 atoms / 20 bohr cube, one uncontracted shell per l=0
 # thread-instructions per cycle over the 152 SMs), 2 flops each, at the SM clock.  A DFMA
 # microbenchmark measured 1.20 TFLOP/s; 1.25 TFLOP/s is the nominal figure.
 FP64_DFMA_PER_CLK = 304
+# DRAM traffic of the coupling phase of one V of this workload, from an ncu capture of the current
+# kernels (dram__bytes_read.sum + dram__bytes_write.sum over the 28 class launches of one call).
+COUPLING_DRAM_BYTES_PER_V = 8.149e6
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
@@ -242,12 +245,14 @@ def run_shgo(args, ws, rank, local):
                                                   outs[i % R].data_ptr(), stream)
         ph += (a, b)
     ph /= nrep
-    names = ["k_coupling_block", "k_pair_block"]
+    names = ["k_coupling_fp64", "k_pair_block"]
     dom = int(np.argmax(ph))
     achieved = flops[dom] / (ph[dom] / 1e3) / 1e12
     peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
     roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": COUPLING_DRAM_BYTES_PER_V if dom == 0 else None,
+                "traffic_note": "DRAM bytes read + written by the 28 coupling launches of one V (ncu capture, "
+                                "profiles/k_coupling_fp64_lam11_highl_fp64.md)",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock (nominal 1.25, "
                                "DFMA microbenchmark 1.20 TFLOP/s)",
                 "phase_ms": [float(ph[0]), float(ph[1])], "phase_tflops": [float(flops[0] / ph[0] / 1e9),
