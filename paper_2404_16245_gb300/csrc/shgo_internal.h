@@ -27,14 +27,14 @@ constexpr int kBoysNmax = kLamMax + 1 + kBoysK;  // 24: F_{Lambda+1} may be need
 constexpr int kBoysStride = kBoysNmax + 2;       // exp slot + orders 0..kBoysNmax
 
 // Sizes of the per-primitive-pair layouts for Lambda = la + lb.
-__host__ __device__ inline int n_harm(int lam) { return (lam + 1) * (lam + 1); }
-__host__ __device__ inline int kmax_of(int lam, int L) { return (lam - L) >> 1; }
-__host__ __device__ inline int n_beta(int lam) {
+__host__ __device__ constexpr inline int n_harm(int lam) { return (lam + 1) * (lam + 1); }
+__host__ __device__ constexpr inline int kmax_of(int lam, int L) { return (lam - L) >> 1; }
+__host__ __device__ constexpr inline int n_beta(int lam) {
   int n = 0;
   for (int L = 0; L <= lam; ++L) n += kmax_of(lam, L) + 1;
   return n;
 }
-__host__ __device__ inline int n_r(int lam) { return (lam + 1) * (lam + 2) * (lam + 3) / 6; }
+__host__ __device__ constexpr inline int n_r(int lam) { return (lam + 1) * (lam + 2) * (lam + 3) / 6; }
 __host__ __device__ inline int harm_index(int l, int m) { return l * l + l + m; }
 
 // Coefficients of the real solid-harmonic recursion (Racah normalisation):
@@ -135,6 +135,10 @@ struct DeviceTables {
   double* rnorm = nullptr;
   int* rot_ptr = nullptr;
   GTerm* rot_terms = nullptr;
+  float2* boys_ff = nullptr;  // boys as (hi, lo) FP32 pairs
+  float2* exp_ff = nullptr;   // exp(-g/16) as (hi, lo) FP32 pairs
+  float2* rnorm_ff = nullptr; // rnorm as (hi, lo) FP32 pairs
+  int* f32_items = nullptr;   // FP32-bulk work items, aligned with rmap (rmap_off)
 };
 shgo_status device_tables(int device, const DeviceTables** out, std::string* err);
 
@@ -315,6 +319,11 @@ struct CouplingArgs {
   const int* pair_site = nullptr;
   const PPData* ppd = nullptr;
   double* rbuf = nullptr;
+  // FP32-bulk kernel only: the Boys grid and exp(-g/16), g < 2048, as (hi, lo) FP32 pairs
+  const float2* boys_ff = nullptr;
+  const float2* exp_ff = nullptr;
+  const int* items = nullptr;         // work items of this Lambda (coupling_f32_items)
+  const float2* rnorm_ff = nullptr;   // rnorm of this Lambda as (hi, lo) pairs
 };
 // Arguments of the electrostatic-potential kernel for one class (shgo_coupling.cu).
 struct EspArgs {
@@ -342,6 +351,19 @@ cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int
 size_t coupling_fp64_smem(int lam, int nch);
 // Constants and launch attributes of the FP64 coupling kernels on the current device.
 cudaError_t coupling_fp64_setup();
+
+// FP32-bulk coupling (shgo_coupling_f32.cu): the Lambda = lam instantiation, compensated (pair
+// arithmetic) or plain, on `grid` blocks of 64 threads; args.boys_ff and args.exp_ff must be set.
+cudaError_t launch_coupling_f32(int lam, bool compensated, const CouplingArgs& args, int grid, cudaStream_t stream);
+size_t coupling_f32_smem(int lam, bool compensated);
+cudaError_t coupling_f32_setup();
+// The tables those kernels read, as (hi, lo) FP32 pairs: the Boys grid, and exp(-g/16) for g < 2048.
+std::vector<float2> boys_table_pairs(const std::vector<double>& boys);
+std::vector<float2> exp_table_pairs();
+std::vector<float2> pairs_of(const std::vector<double>& v);
+// Work items of the FP32-bulk nucleus sums for every Lambda, aligned with Tables::rmap: per Lambda
+// the first entry e of each pair (L, M, k), (L, M, k + 1), then each entry left over.
+std::vector<int> coupling_f32_items(const std::vector<int>& rmap_off);
 
 // Primitive pairs whose elementwise bound per unit of total nuclear charge is below this are skipped
 // (k_pair_build); an element of V changes by at most kPrimSkip x sum |Z| per skipped pair.

@@ -35,7 +35,6 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-__device__ __forceinline__ int odd_pad(int n) { return n | 1; }
 
 // |B - A|^2 and K_AB = exp(-alpha beta/(alpha + beta) |B - A|^2) of Eq. 5, with every operation
 // rounded explicitly so that the coupling and pair kernels agree bit for bit on which primitive
@@ -133,173 +132,6 @@ __global__ void k_live_counts(int npairs, int ncls, const int* __restrict__ pair
     }
   }
 }
-
-// ---------------------------------------------------------------------------------------------
-// FP32-bulk variant of the FP64 coupling kernel (shgo_coupling.cu).  FP64 stays on the geometry, T = p |d|^2 and the Boys
-// function (tabulated Taylor + downward recursion, or asymptotic start + upward recursion); the
-// per-nucleus bulk (radial factors, solid-harmonic recursion) and the nucleus sums run in FP32.
-// FP32 works on dimensionless quantities so nothing of consequence leaves its exponent range:
-//   S_LM(d) T^j F_{L+j}(T) = p^{-L/2} S_LM(e) t_j Phi_{L+j},  e = d/|d|,  t_j = T^{j/2},
-//   Phi_n = T^{n/2} F_n(T),
-// with p^{-L/2} applied in FP64 when the block is written.  COMP selects compensated
-// accumulation over nuclei (exact product error by FMA + two-sum into a (hi, lo) pair).
-// ---------------------------------------------------------------------------------------------
-__host__ __device__ inline size_t coupling_smem_f32(int lam, int nch) {
-  const int rs = (n_harm(lam) + n_beta(lam)) | 1;
-  return sizeof(float) * (size_t)nch * rs + sizeof(double) * ((size_t)nch * (lam + 2) + 2 * (lam + 2)) +
-         sizeof(float2) * (size_t)n_r(lam) + 64;
-}
-
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bb = s - hi;
-  lo += (hi - (s - bb)) + (v - bb);
-  hi = s;
-}
-
-template <int NCH, bool COMP>
-__global__ void __launch_bounds__(32) k_coupling_block_f32(int lam, int64_t npp, int64_t pp_base, int64_t rbase,
-                                                           const int* __restrict__ pp_pair,
-                                                           const int* __restrict__ pp_ij,
-                                                           const int* __restrict__ pair_a,
-                                                           const int* __restrict__ pair_b,
-                                                           const double* __restrict__ shell_xyz,
-                                                           const int* __restrict__ shell_poff,
-                                                           const double* __restrict__ prim_exp, MolView mv,
-                                                           const double* __restrict__ centers,
-                                                           const double* __restrict__ charges,
-                                                           const double* __restrict__ boys_tab,
-                                                           const int* __restrict__ rmap,
-                                                           const double* __restrict__ site_rot,
-                                                           const int* __restrict__ pair_site,
-                                                           const PPData* __restrict__ ppd,
-                                                           double* __restrict__ rbuf) {
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int nS = n_harm(lam), nB = n_beta(lam), nR = n_r(lam);
-  const int rs = odd_pad(nS + nB);
-  double* fscr = smem;                                 // [NCH][lam + 2] FP64 Boys values
-  double* sclk = fscr + (size_t)NCH * (lam + 2);       // 2 pi k! p^{-(k+1)}
-  double* sclL = sclk + (lam + 2);                     // p^{-L/2}
-  float2* racc = reinterpret_cast<float2*>(sclL + (lam + 2));
-  float* rows = reinterpret_cast<float*>(racc + nR);   // [NCH][rs] FP32 rows
-  for (int64_t w = blockIdx.x; w < npp; w += gridDim.x) {
-    const int64_t q = pp_base + w;
-    const int pr = pp_pair[q];
-    const int a = pair_a[pr];
-    const PPData pd = ppd[q];
-    // K_AB of Eq. 5 underflows to exactly 0 for tight primitives on distant centres; the pair kernel
-    // skips such primitive pairs, so their coupling block is not needed
-    if (pd.pref == 0.0) continue;
-    const double p = pd.p, rp = pd.rp;
-    // C - P = (C - A) - (beta/p)(B - A): exact when the nucleus sits on coincident shell centres
-    // (forming P = (alpha A + beta B)/p first would move it by an ulp, which tight Gaussians amplify)
-    const double Ax = shell_xyz[3 * a], Ay = shell_xyz[3 * a + 1], Az = shell_xyz[3 * a + 2];
-    const double shift = pd.shift;  // |P - A|, along z in the pair frame
-    const double sp = pd.sp;
-    double Q[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Q[k] = site_rot[9 * pair_site[pr] + k];
-    for (int e = lane; e < nR; e += 32) racc[e] = make_float2(0.f, 0.f);
-    int64_t cbeg, ncen;
-    mol_centers(mv, pr, cbeg, ncen);
-    for (int64_t c0 = 0; c0 < ncen; c0 += NCH) {
-      __syncwarp();
-      if (lane < NCH) {
-        float* row = rows + (size_t)lane * rs;
-        double* F = fscr + (size_t)lane * (lam + 2);
-        double dx = 0.0, dy = 0.0, dz = 0.0, z = 0.0;
-        if (c0 + lane < ncen) {
-          const int64_t c = mol_center_index(mv, cbeg + c0 + lane);
-          const double ux = centers[3 * c] - Ax, uy = centers[3 * c + 1] - Ay, uz = centers[3 * c + 2] - Az;
-          dx = Q[0] * ux + Q[1] * uy + Q[2] * uz;
-          dy = Q[3] * ux + Q[4] * uy + Q[5] * uz;
-          dz = Q[6] * ux + Q[7] * uy + Q[8] * uz - shift;
-          z = charges[c];
-        }
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double T = p * r2;
-        boys_eval(lam, T, F, 1, boys_tab, c_boys);
-        const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
-        const double st = sp * r2 * rinv;  // sqrt(T)
-        // Phi_n = Z T^{n/2} F_n (FP64, then FP32) and t_j = T^{j/2}/j! (FP32) behind it
-        double pw = z;
-        for (int n = 0; n <= lam; ++n) {
-          row[n] = (float)(pw * F[n]);
-          pw *= st;
-        }
-        float* tj = row + lam + 1;
-        const float stf = (float)st;
-        tj[0] = 1.f;
-        for (int j = 1; j <= (lam >> 1); ++j) tj[j] = tj[j - 1] * stf * (float)c_boys.inv_int[j];
-        float* brow = row + nS;
-        int bo = 0;
-        for (int L = 0; L <= lam; ++L) {
-          const int km = (lam - L) >> 1;
-          float acc = row[L];
-          brow[bo] = acc;
-          for (int k = 1; k <= km; ++k) {
-            acc = fmaf(tj[k], row[L + k], acc);
-            brow[bo + k] = acc;
-          }
-          bo += km + 1;
-        }
-        solid_harmonics<float>(lam, (float)(dx * rinv), (float)(dy * rinv), (float)(dz * rinv), row, 1, c_harm.a,
-                               c_harm.b, c_harm.c);
-      }
-      __syncwarp();
-      // a partial last chunk sums only its occupied rows (empty rows carry Z = 0)
-      const int nv = ncen - c0 >= NCH ? NCH : (int)(ncen - c0);
-      const int nv2 = (nv + 1) & ~1;
-      for (int e = lane; e < nR; e += 32) {
-        const int code = __ldg(rmap + e);
-        const int si = code & 0xfff, bi = nS + ((code >> 12) & 0xfff);
-        float2 acc = racc[e];
-        if (COMP) {
-#pragma unroll 4
-          for (int c = 0; c < nv; ++c) {
-            const float x = rows[(size_t)c * rs + si], y = rows[(size_t)c * rs + bi];
-            const float prod = x * y;
-            acc.y += fmaf(x, y, -prod);  // rounding error of the product
-            two_sum_acc(acc.x, acc.y, prod);
-          }
-        } else {
-          float a0 = 0.f, a1 = 0.f;
-#pragma unroll 4
-          for (int c = 0; c < nv2; c += 2) {
-            a0 = fmaf(rows[(size_t)c * rs + si], rows[(size_t)c * rs + bi], a0);
-            a1 = fmaf(rows[(size_t)(c + 1) * rs + si], rows[(size_t)(c + 1) * rs + bi], a1);
-          }
-          acc.x += a0 + a1;
-        }
-        racc[e] = acc;
-      }
-    }
-    // scales: 2 pi k! p^{-(k+1)} and p^{-L/2}
-    if (lane <= (lam >> 1)) {
-      double s = kTwoPi * rp;
-      for (int k = 1; k <= lane; ++k) s *= double(k) * rp;
-      sclk[lane] = s;
-    }
-    if (lane <= lam) {
-      const double ip = 1.0 / sp;
-      double s = 1.0;
-      for (int k = 0; k < lane; ++k) s *= ip;
-      sclL[lane] = s;
-    }
-    __syncwarp();
-    double* out = rbuf + rbase + w * (int64_t)nR;
-    for (int e = lane; e < nR; e += 32) {
-      const int code = __ldg(rmap + e);
-      const int hi = code & 0xfff;
-      const int L = (int)sqrtf((float)hi + 0.5f);
-      const float2 acc = racc[e];
-      out[e] = ((double)acc.x + (double)acc.y) * sclk[(code >> 24) & 0xff] * sclL[L];
-    }
-    __syncwarp();
-  }
-}
-
 
 // Shared-memory bytes of one block of k_pair_block.
 __host__ __device__ inline size_t pair_smem(int la, int lb) {
@@ -880,9 +712,14 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.rnorm, t.rnorm);
   if (e == cudaSuccess) e = upload(&d.rot_ptr, t.rot_ptr);
   if (e == cudaSuccess) e = upload(&d.rot_terms, t.rot_terms);
+  if (e == cudaSuccess) e = upload(&d.boys_ff, boys_table_pairs(t.boys));
+  if (e == cudaSuccess) e = upload(&d.exp_ff, exp_table_pairs());
+  if (e == cudaSuccess) e = upload(&d.rnorm_ff, pairs_of(t.rnorm));
+  if (e == cudaSuccess) e = upload(&d.f32_items, coupling_f32_items(t.rmap_off));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
   if (e == cudaSuccess) e = coupling_fp64_setup();
+  if (e == cudaSuccess) e = coupling_f32_setup();
   if (e == cudaSuccess) {
     int lof[(kLmax + 1) * (kLmax + 1)];
     for (int l = 0; l <= kLmax; ++l)
@@ -965,10 +802,6 @@ void set_kernel_attributes() {
   if (g_attr_ok[dev]) return;
   const int lim = 227 * 1024;
   cudaFuncSetAttribute(k_pair_block, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_coupling_block_f32<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_coupling_block_f32<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_coupling_block_f32<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_coupling_block_f32<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   g_attr_ok[dev] = true;
 }
 
@@ -996,24 +829,6 @@ struct Launcher {
     const int lam = w.la + w.lb;
     const int nch = nch_of(c, lam);
     const int* rmap = dt.rmap + th.rmap_off[lam];
-    if (db.precision != SHGO_PREC_FP64) {
-      const size_t sm32 = coupling_smem_f32(lam, nch);
-      const int grid = grid_cap(w.npp, 16);
-#define SHGO_F32_ARGS                                                                                              \
-  lam, w.npp, w.pp_base, rbase, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.prim_exp, \
-      mv, centers, charges, dt.boys, rmap, db.site_rot, db.pair_site, db.ppd, db.rbuf
-      const bool comp = db.precision == SHGO_PREC_FP32_BULK;
-      if (nch == 32 && comp)
-        k_coupling_block_f32<32, true><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
-      else if (nch == 32)
-        k_coupling_block_f32<32, false><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
-      else if (comp)
-        k_coupling_block_f32<16, true><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
-      else
-        k_coupling_block_f32<16, false><<<grid, 32, sm32, s>>>(SHGO_F32_ARGS);
-#undef SHGO_F32_ARGS
-      return;
-    }
     CouplingArgs a;
     a.npp = w.npp;
     a.pp_base = w.pp_base;
@@ -1031,6 +846,14 @@ struct Launcher {
     a.pair_site = db.pair_site;
     a.ppd = db.ppd;
     a.rbuf = db.rbuf;
+    if (db.precision != SHGO_PREC_FP64) {
+      a.boys_ff = dt.boys_ff;
+      a.exp_ff = dt.exp_ff;
+      a.items = dt.f32_items + th.rmap_off[lam];
+      a.rnorm_ff = dt.rnorm_ff + th.rmap_off[lam];
+      launch_coupling_f32(lam, db.precision == SHGO_PREC_FP32_BULK, a, grid_cap(w.npp, 8), s);
+      return;
+    }
     launch_coupling_fp64(lam, nch, a, grid_cap(w.npp, 8), s);
   }
   void pair(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
