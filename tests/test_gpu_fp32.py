@@ -59,7 +59,8 @@ def test_fp32_bulk_blockwise_error(shgo, name, factory, capsys):
     ep = block_errors(basis, plain, ref)
     with capsys.disabled():
         print(f"\n{name}: FP32-bulk block error max {eb.max():.2e} median {np.median(eb):.2e}; "
-              f"FP32-plain max {ep.max():.2e} median {np.median(ep):.2e}")
+              f"FP32-plain max {ep.max():.2e} median {np.median(ep):.2e}; "
+              f"max abs difference FP32-bulk {np.max(np.abs(bulk - ref)):.2e} (max |V| {np.max(np.abs(ref)):.2e})")
     assert np.all(np.isfinite(bulk)) and np.all(np.isfinite(plain))
     assert eb.max() < 1e-10
     assert ep.max() < 1e-4
