@@ -156,3 +156,67 @@ def test_trained_screening_error_and_audit(shgo):
     assert rep["false_skip_rate"] < 0.01
     B.close()
     net.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_repeated_screened_calls_keep_all(shgo, precision):
+    """Every call of the screened entry point (the tuning call, the graph capture and the replays) gives
+    the plain result when the network keeps every triple: bit for bit in FP64, and to the FP32-bulk
+    block accuracy otherwise."""
+    prec = shgo.SHGO_PREC_FP64 if precision == "fp64" else shgo.SHGO_PREC_FP32_BULK
+    basis, C, Z = cluster(46, 30)
+    B = shgo.Basis(basis, precision=prec)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    plain = shgo.nuclear_attraction(B, Cd, Zd).cpu().numpy()
+    keep = const_net(shgo, 100.0)
+    kept, skipped = shgo.screen_build(B.handle, keep, Cd, Zd, len(Z), -12.0, 2.0)
+    assert skipped == 0
+    out = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device="cuda")
+    for call in range(4):
+        out.fill_(float("nan"))
+        shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out)
+        got = out.cpu().numpy()
+        diff = float(np.max(np.abs(got - plain)))
+        if precision == "fp64":
+            assert np.array_equal(got, plain), (call, diff)
+        else:
+            assert diff <= 1e-10 * max(1.0, float(np.max(np.abs(plain)))), (call, diff)
+    B.close()
+    keep.close()
+
+
+def charge_net(shgo):
+    """A hand-set network whose prediction falls with the nucleus charge (feature 10 is log10 Z):
+    y = 10 - silu(silu(10 log10 Z + 5)), at or above 0 exactly for Z <= 3."""
+    H, IN = 64, 16
+    W1 = np.zeros((H, IN))
+    b1 = np.zeros(H)
+    W2 = np.zeros((H, H))
+    W3 = np.zeros(H)
+    W1[0, 10], b1[0], W2[0, 0], W3[0] = 10.0, 5.0, 1.0, -1.0
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), np.zeros(H), W3, [10.0]]).astype(np.float32)
+    assert p.size == ref.NPARAM
+    return shgo.MLP(p, np.zeros(16), np.ones(16))
+
+
+def test_ragged_nucleus_lists_equal_plain_over_the_kept_nuclei(shgo):
+    """A mask that keeps, for every pair, the nuclei with Z <= 3 gives each pair a nucleus list
+    shorter than the molecule's (a partial chunk): the screened V equals the plain V over those
+    nuclei bit for bit, on every call (tuning, capture, replays)."""
+    basis, C, Z = cluster(47, 30)
+    keep_z = Z <= 3
+    assert 0 < keep_z.sum() < len(Z)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    expect = shgo.nuclear_attraction(B, torch.tensor(C[keep_z], device="cuda"),
+                                     torch.tensor(Z[keep_z], device="cuda")).cpu().numpy()
+    net = charge_net(shgo)
+    kept, skipped = shgo.screen_build(B.handle, net, Cd, Zd, len(Z), 0.0, 0.0)
+    assert kept == B.npairs * int(keep_z.sum()) and skipped == B.npairs * int((~keep_z).sum())
+    out = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device="cuda")
+    for call in range(3):
+        out.fill_(float("nan"))
+        shgo.nuclear_attraction_screened(B.handle, Cd, Zd, len(Z), out)
+        assert np.array_equal(out.cpu().numpy(), expect), call
+    B.close()
+    net.close()
