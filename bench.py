@@ -48,6 +48,35 @@ def fp64_peak_tflops(sm_mhz: float) -> float:
     return 2.0 * FP64_DFMA_PER_CLK * sm_mhz * 1e6 / 1e12
 
 
+# FP32 lanes per SM (the FP32-bulk coupling kernel issues FP32 instructions of pair arithmetic).
+FP32_LANES_PER_SM = 128
+
+
+def fp32_lane_peak_t(sm_mhz: float) -> float:
+    """FP32 lane-instructions per second (units of 1e12): 152 SMs x 128 lanes x SM clock."""
+    return 152 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+
+
+def f32_coupling_instructions(basis_handle, n_centers: int) -> float:
+    """Useful FP32 lane-instructions of the FP32-bulk coupling kernel for one V: per live primitive pair
+    and nucleus, the pair-frame offset and T (~250), one Boys form (~650), t_j (7 Lambda), the radial sums
+    (16 per entry), the harmonic recursion (20 per entry) and the nucleus sums (12 per R' entry, the Dot2
+    step).  The live primitive-pair count of each class is recovered from the library's FP64 flop model
+    (per primitive pair and nucleus as documented with shgo_basis_class_stats)."""
+    from paper_2404_16245_gb300 import shgo
+    total = 0.0
+    for la, lb, _trip, _integrals, f0, _f1 in shgo.shgo_basis_class_stats(basis_handle, n_centers):
+        lam = la + lb
+        nb = sum((lam - L) // 2 + 1 for L in range(lam + 1))
+        nr = (lam + 1) * (lam + 2) * (lam + 3) // 6
+        ns = (lam + 1) ** 2
+        per_triple = (9 + 11 + 5 * 7 + 1 + 3 * lam + 2 * lam + 1 + 2 * (lam // 2) + 2 * (nb - lam - 1)
+                      + sum(6 * l + 5 for l in range(1, lam)) + 2 * nr)
+        live_pp = f0 / (per_triple * n_centers + 2 * nr) if n_centers > 0 else 0.0
+        total += live_pp * n_centers * (250 + 650 + 7 * lam + 16 * nb + 20 * ns + 12 * nr)
+    return total
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,19 +274,33 @@ def run_shgo(args, ws, rank, local):
                                                   outs[i % R].data_ptr(), stream)
         ph += (a, b)
     ph /= nrep
-    names = ["k_coupling_fp64", "k_pair_block"]
+    f32 = args.precision != "fp64"
+    names = ["k_coupling_f32" if f32 else "k_coupling_fp64", "k_pair_block"]
     dom = int(np.argmax(ph))
-    achieved = flops[dom] / (ph[dom] / 1e3) / 1e12
-    peak = fp64_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
-    roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": COUPLING_DRAM_BYTES_PER_V if dom == 0 else None,
-                "traffic_note": "DRAM bytes read + written by the 28 coupling launches of one V (ncu capture, "
-                                "profiles/k_coupling_fp64_lam11_highl_fp64.md)",
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock (nominal 1.25, "
-                               "DFMA microbenchmark 1.20 TFLOP/s)",
-                "phase_ms": [float(ph[0]), float(ph[1])], "phase_tflops": [float(flops[0] / ph[0] / 1e9),
-                                                                           float(flops[1] / ph[1] / 1e9)],
-                "algorithmic_flops_per_step": [float(flops[0]), float(flops[1])]}
+    clk = clocks.get("sm_max_mhz") or 2070.0
+    if f32 and dom == 0:
+        # FP32-bulk coupling: FP32 lane-instructions of its pair arithmetic (one operation each)
+        work = f32_coupling_instructions(bases[0].handle, cents[0].shape[0])
+        achieved = work / (ph[0] / 1e3) / 1e12
+        peak = fp32_lane_peak_t(clk)
+        roofline = {"bound": "alu", "kernel": names[0], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock; each FP32 instruction of "
+                                   "the pair arithmetic counted as one operation (model in bench.py)",
+                    "model_fp32_instructions_per_step": work}
+    else:
+        achieved = flops[dom] / (ph[dom] / 1e3) / 1e12
+        peak = fp64_peak_tflops(clk)
+        roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": COUPLING_DRAM_BYTES_PER_V if dom == 0 else None,
+                    "traffic_note": "DRAM bytes read + written by the 28 coupling launches of one V (ncu capture, "
+                                    "profiles/k_coupling_fp64_lam11_highl_fp64.md)",
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock (nominal 1.25, "
+                                   "DFMA microbenchmark 1.20 TFLOP/s)"}
+    roofline.update({"phase_ms": [float(ph[0]), float(ph[1])],
+                     "phase_tflops": [float(flops[0] / ph[0] / 1e9), float(flops[1] / ph[1] / 1e9)],
+                     "algorithmic_flops_per_step": [float(flops[0]), float(flops[1])]})
 
     # per (la, lb) class: each class's two kernels alone (classes one after another), CUDA events
     stats = shgo.shgo_basis_class_stats(bases[0].handle, cents[0].shape[0])

@@ -58,8 +58,12 @@ struct shgo_basis {
   std::vector<double> class_pair_cent, class_pp_cent;  // per class: sum over pairs / primitive pairs of nuclei
   // per class, after the primitive-pair bound: live primitive pairs, shell pairs with one, and (batches)
   // the sum of nuclei over live primitive pairs
+  // filled on first use by the statistics calls (class_model), not at creation
   std::vector<int64_t> live_pp, live_pairs;
   std::vector<double> live_cent;
+  bool live_ready = false;
+  std::mutex live_mu;
+  int64_t ppcount = 0;
   int* pair_mol = nullptr;
   int64_t *mol_c0_d = nullptr, *mol_nc_d = nullptr, *mol_out_d = nullptr, *mol_ld_d = nullptr;
   std::vector<ClassTune> tune;
@@ -284,31 +288,66 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   std::vector<int64_t> ppoff;
   std::vector<int> pp_pair, pp_ij;
   int64_t ppcount = 0;
+  {
+    // sizes first, then the lists filled by index
+    int64_t np_total = 0, npp_total = 0;
+    for (int m = 0; m < nm; ++m)
+      for (int la = 0; la <= kLmax; ++la)
+        for (int lb = 0; lb <= la; ++lb) {
+          const auto& A = by_l[m][la];
+          const auto& B = by_l[m][lb];
+          if (la == lb) {
+            int64_t run = 0;
+            for (const int x : A) {
+              run += n_prim[x];
+              npp_total += (int64_t)n_prim[x] * run;  // y <= x
+            }
+            np_total += (int64_t)A.size() * ((int64_t)A.size() + 1) / 2;
+          } else {
+            int64_t sa = 0, sb = 0;
+            for (const int x : A) sa += n_prim[x];
+            for (const int y : B) sb += n_prim[y];
+            np_total += (int64_t)A.size() * (int64_t)B.size();
+            npp_total += sa * sb;
+          }
+        }
+    pa.resize(np_total);
+    pb.resize(np_total);
+    pmol.resize(np_total);
+    ppoff.resize(np_total);
+    pp_pair.resize(npp_total);
+    pp_ij.resize(npp_total);
+  }
+  int64_t q = 0;
   for (int la = 0; la <= kLmax; ++la)
     for (int lb = 0; lb <= la; ++lb) {
-      ClassWork w{la, lb, 0, (int)pa.size(), 0, ppcount};
+      ClassWork w{la, lb, 0, (int)q, 0, ppcount};
       double pc = 0, ppc = 0;
       for (int m = 0; m < nm; ++m) {
         const auto& A = by_l[m][la];
         const auto& B = by_l[m][lb];
+        const double nc = (double)b->mol_nc[m];
         for (size_t x = 0; x < A.size(); ++x) {
           const size_t ylim = (la == lb) ? x + 1 : B.size();
-          for (size_t y = 0; y < ylim; ++y) {
-            const int sa = A[x], sb = B[y];
-            pa.push_back(sa);
-            pb.push_back(sb);
-            pmol.push_back(m);
-            ppoff.push_back(ppcount);
-            for (int i = 0; i < n_prim[sa]; ++i)
-              for (int j = 0; j < n_prim[sb]; ++j) {
-                pp_pair.push_back((int)pa.size() - 1);
-                pp_ij.push_back((i << 8) | j);
+          const int sa = A[x], npa = n_prim[sa];
+          for (size_t y = 0; y < ylim; ++y, ++q) {
+            const int sb = B[y], npb = n_prim[sb];
+            pa[q] = sa;
+            pb[q] = sb;
+            pmol[q] = m;
+            ppoff[q] = ppcount;
+            int* ppp = pp_pair.data() + ppcount;
+            int* ppi = pp_ij.data() + ppcount;
+            for (int i = 0; i < npa; ++i)
+              for (int j = 0; j < npb; ++j) {
+                *ppp++ = (int)q;
+                *ppi++ = (i << 8) | j;
               }
-            ppcount += (int64_t)n_prim[sa] * n_prim[sb];
-            ++w.npairs;
-            pc += (double)b->mol_nc[m];
-            ppc += (double)b->mol_nc[m] * n_prim[sa] * n_prim[sb];
+            ppcount += (int64_t)npa * npb;
+            ppc += nc * npa * npb;
           }
+          pc += nc * (double)ylim;
+          w.npairs += (int)ylim;
         }
       }
       w.npp = ppcount - w.pp_base;
@@ -436,9 +475,7 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     st = SHGO_ERR_CUDA;
     err = "primitive-pair and pair-frame build failed";
   }
-  if (st == SHGO_OK)
-    st = live_counts(b->d, b->work, (int64_t)pa.size(), ppcount, batch ? b->pair_mol : nullptr,
-                     batch ? b->mol_nc_d : nullptr, b->live_pp, b->live_pairs, b->live_cent, &err);
+  b->ppcount = ppcount;
   if (st != SHGO_OK) {
     release(b);
     return fail(st, err);
@@ -453,6 +490,21 @@ namespace {
 // Per class wi of a basis: out[0] shell triples, out[1] unused, out[2] algorithmic flops of the
 // coupling kernel (S2), out[3] flops of the pair kernel (S3-S5), out[4] primitive triples, out[5]
 // integrals (shell triples x (2la+1)(2lb+1)).  Flops count an FMA as two.
+// The per-class live counts behind the flop model, computed on first use (a kernel and a copy back).
+shgo_status ensure_live_counts(const shgo_basis* cb, std::string* err) {
+  shgo_basis* b = const_cast<shgo_basis*>(cb);
+  std::lock_guard<std::mutex> lk(b->live_mu);
+  if (b->live_ready) return SHGO_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != b->device) cudaSetDevice(b->device);
+  const shgo_status st = live_counts(b->d, b->work, b->npairs, b->ppcount, b->batch ? b->pair_mol : nullptr,
+                                     b->batch ? b->mol_nc_d : nullptr, b->live_pp, b->live_pairs, b->live_cent, err);
+  if (prev != b->device) cudaSetDevice(prev);
+  b->live_ready = st == SHGO_OK;
+  return st;
+}
+
 void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* out) {
   const Tables& t = tables_host();
   const ClassWork& w = basis->work[wi];
@@ -701,6 +753,11 @@ int64_t shgo_basis_launches(const shgo_basis* basis) { return basis ? launches_p
 
 shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples) {
   if (!basis || !flops || !triples || n_centers < 0) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  {
+    std::string err;
+    const shgo_status st = ensure_live_counts(basis, &err);
+    if (st != SHGO_OK) return fail(st, err);
+  }
   flops[0] = flops[1] = triples[0] = triples[1] = 0;
   for (size_t wi = 0; wi < basis->work.size(); ++wi) {
     double c[6];
@@ -719,6 +776,11 @@ shgo_status shgo_basis_class_stats(const shgo_basis* basis, int64_t n_centers, i
                                    double* stats) {
   if (!basis || !la_lb || !stats || n_centers < 0 || c < 0 || c >= (int32_t)basis->work.size())
     return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  {
+    std::string err;
+    const shgo_status st = ensure_live_counts(basis, &err);
+    if (st != SHGO_OK) return fail(st, err);
+  }
   double m[6];
   class_model(basis, (size_t)c, n_centers, m);
   la_lb[0] = basis->work[c].la;

@@ -366,14 +366,29 @@ void build_site_pairs(const double* shell_xyz, const std::vector<int>& pa, const
   // shells -> positions (bitwise-equal coordinates), then ordered position pairs
   int nsh = 0;
   for (size_t q = 0; q < pa.size(); ++q) nsh = std::max(nsh, std::max(pa[q], pb[q]) + 1);
+  // positions keyed by the bits of their three coordinates
+  struct Key {
+    uint64_t x, y, z;
+    bool operator==(const Key& o) const { return x == o.x && y == o.y && z == o.z; }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      uint64_t h = k.x * 0x9E3779B97F4A7C15ull;
+      h ^= (k.y + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2)) * 0xBF58476D1CE4E5B9ull;
+      h ^= (k.z + 0x94D049BB133111EBull + (h << 6) + (h >> 2)) * 0x9E3779B97F4A7C15ull;
+      return (size_t)(h ^ (h >> 31));
+    }
+  };
   std::vector<int> shell_pos(nsh, -1);
-  std::unordered_map<std::string, int> pos;
-  for (size_t q = 0; q < pa.size(); ++q)
-    for (const int s : {pa[q], pb[q]})
-      if (shell_pos[s] < 0) {
-        const std::string key(reinterpret_cast<const char*>(shell_xyz + 3 * s), 3 * sizeof(double));
-        shell_pos[s] = pos.emplace(key, (int)pos.size()).first->second;
-      }
+  std::unordered_map<Key, int, KeyHash> pos;
+  pos.reserve((size_t)nsh);
+  for (int s = 0; s < nsh; ++s) {
+    Key k{};
+    std::memcpy(&k.x, shell_xyz + 3 * s, sizeof(double));
+    std::memcpy(&k.y, shell_xyz + 3 * s + 1, sizeof(double));
+    std::memcpy(&k.z, shell_xyz + 3 * s + 2, sizeof(double));
+    shell_pos[s] = pos.emplace(k, (int)pos.size()).first->second;
+  }
   const int64_t np = (int64_t)pos.size();
   pair_site.resize(pa.size());
   site_rep.clear();
