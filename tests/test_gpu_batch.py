@@ -118,3 +118,35 @@ def test_bounded_coupling_buffer_chunks_match(monkeypatch):
         parity.check(batch.block(outs[-1], m), oracle.nuclear_attraction(b, Cm, Zm, precision="ld"), what=f"m{m}")
     assert np.array_equal(outs[1], outs[2])
     batch.close()
+
+
+@pytest.mark.parametrize("cap", [None, "20000"])
+def test_fp32_bulk_batched_matches_fp64(monkeypatch, cap):
+    """FP32-bulk through the batched entry point (tuned first call, graph capture, replays) and, with a
+    tiny cap, through per-stream regions of the coupling buffer: every molecule within 1e-10 of the FP64
+    batched result relative to its largest element, replays bit for bit, and the bounded buffer equal
+    to the unbounded one."""
+    from paper_2404_16245_gb300 import shgo
+    mols = small_molecules(33, 6)
+    entries = [(b, len(Z)) for b, _, Z in mols]
+    C = torch.tensor(np.concatenate([c for _, c, _ in mols]), device="cuda")
+    Zt = torch.tensor(np.concatenate([z for _, _, z in mols]), device="cuda")
+    b64 = shgo.Batch(entries)
+    ref = shgo.nuclear_attraction_batched(b64, C, Zt).cpu().numpy()
+    b64.close()
+    unbounded = None
+    if cap:
+        b0 = shgo.Batch(entries, precision=shgo.SHGO_PREC_FP32_BULK)
+        unbounded = [shgo.nuclear_attraction_batched(b0, C, Zt).cpu().numpy() for _ in range(2)][-1]
+        b0.close()
+        monkeypatch.setenv("SHGO_RBUF_CAP_DOUBLES", cap)
+    b32 = shgo.Batch(entries, precision=shgo.SHGO_PREC_FP32_BULK)
+    runs = [shgo.nuclear_attraction_batched(b32, C, Zt).cpu().numpy() for _ in range(4)]
+    assert np.array_equal(runs[1], runs[2]) and np.array_equal(runs[2], runs[3])
+    for m in range(len(mols)):
+        r = b32.block(ref, m)
+        for g in runs:
+            assert np.max(np.abs(b32.block(g, m) - r)) <= 1e-10 * max(1.0, float(np.max(np.abs(r)))), m
+    if unbounded is not None:
+        assert np.array_equal(runs[-1], unbounded)
+    b32.close()
