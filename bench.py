@@ -728,13 +728,17 @@ def run_precision_sweep(n_triples: int, n_oracle: int) -> int:
     return 0
 
 
-def run_profile_case(precision: str = "fp64") -> int:
-    """Small fixed case for ncu captures: one warm and one measured V of the benchmark workload."""
+def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
+    """Small fixed case for ncu captures: one warm and one measured V of the benchmark workload
+    (highl) or of the first molecule of the batched workload (batched)."""
     import torch
 
     from paper_2404_16245_gb300 import shgo
     from paper_2404_16245_gb300 import workloads as W
-    b, C, Z = W.config2()
+    if case == "batched":
+        b, C, Z = W.config3_molecule(np.random.Generator(np.random.PCG64(3000)))
+    else:
+        b, C, Z = W.config2()
     B = shgo.Basis(b, precision={"fp64": shgo.SHGO_PREC_FP64, "fp32": shgo.SHGO_PREC_FP32_BULK}[precision])
     Cd = torch.tensor(C, device="cuda")
     Zd = torch.tensor(Z, device="cuda")
@@ -748,7 +752,8 @@ def run_profile_case(precision: str = "fp64") -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", action="store_true", help="one warm + one measured call, for ncu")
+    ap.add_argument("--profile-case", nargs="?", const="highl", choices=["highl", "batched"],
+                    help="one warm + one measured call, for ncu (the benchmark molecule or one batched molecule)")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
     ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
@@ -782,7 +787,7 @@ def main():
     ap.add_argument("--no-per-class-batch", action="store_true", help="skip the 64-replica per-class timing")
     args = ap.parse_args()
     if args.profile_case:
-        return run_profile_case(args.precision)
+        return run_profile_case(args.precision, args.profile_case)
     if args.precision_sweep:
         return run_precision_sweep(args.precision_sweep, args.sweep_oracle)
     if args.workload == "batched":
