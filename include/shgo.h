@@ -43,10 +43,14 @@ typedef enum {
 
 typedef enum {
   SHGO_PREC_FP64 = 0,      /* every step in FP64 */
-  SHGO_PREC_FP32_BULK = 1, /* nucleus loop in FP32 (solid harmonics, radial factors, nucleus sums with
-                              compensated two-sum accumulation); geometry, T and the Boys function in
-                              FP64; Gaunt coupling, contraction and translation in FP64 */
-  SHGO_PREC_FP32_PLAIN = 2 /* as SHGO_PREC_FP32_BULK without the compensation (for error studies) */
+  SHGO_PREC_FP32_BULK = 1, /* nucleus loop (Eq. 11's per-nucleus factors and sums) in FP32 instructions:
+                              every factor (pair-frame offset, T, the Boys Taylor step and recursions
+                              from the FP64 grid, radial sums, unit-vector solid harmonics) an
+                              unevaluated pair of FP32 numbers built with error-free transformations,
+                              nucleus sums compensated (two-sum); block error ~1e-13 of the block's
+                              largest element against FP64.  Gaunt coupling, primitive contraction,
+                              translation and rotation in FP64 */
+  SHGO_PREC_FP32_PLAIN = 2 /* the same kernel on single FP32 numbers (for error studies; ~1e-6) */
 } shgo_precision;
 
 typedef struct {
