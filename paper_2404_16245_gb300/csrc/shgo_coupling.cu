@@ -307,65 +307,70 @@ __global__ void __launch_bounds__(64) k_esp_fp64(EspArgs A) {
 }
 
 // Solid-harmonic polynomials S~_lm(d) = |d|^l U_lm(d/|d|) (degree l, same constants as U) and their
-// gradients, columns m in [M0, M1], l <= LAM, into P, Gx, Gy, Gz at row h = l^2 + l + m (stride CS):
-// forward-mode derivatives of S~_{l+1,m} = z S~_lm + ng_lm r^2 S~_{l-1,m}, S~_{|m|+1,m} = z S~_{|m|,m}
-// and of the diagonal chain (which does not depend on z).
-template <int LAM, int CS, int M0, int M1>
-__device__ __forceinline__ void harmonic_columns_grad(double x, double y, double z, double* P, double* Gx,
-                                                      double* Gy, double* Gz) {
+// gradients, l <= LAM, into P, Gx, Gy, Gz at row h = l^2 + l + m (stride CS): forward-mode derivatives of
+// S~_{l+1,m} = z S~_lm + ng_lm r^2 S~_{l-1,m}, S~_{|m|+1,m} = z S~_{|m|,m} and of the diagonal chain
+// S~_{l+1,l+1} = x S~_ll - y S~_{l,-l}, S~_{l+1,-l-1} = y S~_ll + x S~_{l,-l} (which does not depend on z).
+// The columns are split by the sign of m between the two half-warps: lanes of half `neg` take
+// m = -|m| for |m| >= 1, the others m = +|m| for |m| >= 0.  The diagonal chain and the column
+// recursions run as loops over |m| and l, so that both halves, whose columns of one |m| have equal
+// lengths, advance in step.
+template <int LAM, int CS>
+__device__ __forceinline__ void harmonic_columns_grad_half(bool neg, double x, double y, double z, double* P,
+                                                           double* Gx, double* Gy, double* Gz) {
   const double r2 = x * x + y * y + z * z;
-  double dp[LAM + 1], dm[LAM + 1], dpx[LAM + 1], dpy[LAM + 1], dmx[LAM + 1], dmy[LAM + 1];
-  dp[0] = dm[0] = 1.0;
-  dpx[0] = dpy[0] = dmx[0] = dmy[0] = 0.0;
-  if constexpr (LAM >= 1) {
-    dp[1] = x;
-    dm[1] = y;
-    dpx[1] = 1.0;
-    dpy[1] = 0.0;
-    dmx[1] = 0.0;
-    dmy[1] = 1.0;
-#pragma unroll
-    for (int l = 1; l < LAM; ++l) {
-      dp[l + 1] = fma(x, dp[l], -y * dm[l]);
-      dm[l + 1] = fma(y, dp[l], x * dm[l]);
-      dpx[l + 1] = dp[l] + fma(x, dpx[l], -y * dmx[l]);
-      dpy[l + 1] = fma(x, dpy[l], -y * dmy[l]) - dm[l];
-      dmx[l + 1] = fma(y, dpx[l], x * dmx[l]) + dm[l];
-      dmy[l + 1] = fma(y, dpy[l], x * dmy[l]) + dp[l];
-    }
-  }
-#pragma unroll
-  for (int m = M0; m <= M1; ++m) {
-    const int am = m < 0 ? -m : m;
-    double v0 = m < 0 ? dm[am] : dp[am];
-    double x0 = m < 0 ? dmx[am] : dpx[am], y0 = m < 0 ? dmy[am] : dpy[am], z0 = 0.0;
-    int h = am * am + am + m;
-    P[h * CS] = v0;
-    Gx[h * CS] = x0;
-    Gy[h * CS] = y0;
-    Gz[h * CS] = z0;
-    if (am + 1 <= LAM) {
-      double v1 = z * v0, x1 = z * x0, y1 = z * y0, z1 = v0;
-      h = (am + 1) * (am + 1) + am + 1 + m;
-      P[h * CS] = v1;
-      Gx[h * CS] = x1;
-      Gy[h * CS] = y1;
-      Gz[h * CS] = z1;
-#pragma unroll
-      for (int l = am + 1; l < LAM; ++l) {
-        const double g = k_harm.ng[l * l + l + m];
-        const double v2 = fma(g * r2, v0, z * v1);
-        const double x2 = fma(g, fma(2.0 * x, v0, r2 * x0), z * x1);
-        const double y2 = fma(g, fma(2.0 * y, v0, r2 * y0), z * y1);
-        const double z2 = fma(g, fma(2.0 * z, v0, r2 * z0), fma(z, z1, v1));
-        h = (l + 1) * (l + 1) + l + 1 + m;
-        P[h * CS] = v2;
-        Gx[h * CS] = x2;
-        Gy[h * CS] = y2;
-        Gz[h * CS] = z2;
-        v0 = v1; x0 = x1; y0 = y1; z0 = z1;
-        v1 = v2; x1 = x2; y1 = y2; z1 = z2;
+  double dp = 1.0, dm = 1.0, dpx = 0.0, dpy = 0.0, dmx = 0.0, dmy = 0.0;  // U_{am,+-am} and gradients
+#pragma unroll 1
+  for (int am = 0; am <= LAM; ++am) {
+    if (!(neg && am == 0)) {
+      const int m = neg ? -am : am;
+      double v0 = neg ? dm : dp, x0 = neg ? dmx : dpx, y0 = neg ? dmy : dpy, z0 = 0.0;
+      int h = am * am + am + m;
+      P[h * CS] = v0;
+      Gx[h * CS] = x0;
+      Gy[h * CS] = y0;
+      Gz[h * CS] = z0;
+      if (am + 1 <= LAM) {
+        double v1 = z * v0, x1 = z * x0, y1 = z * y0, z1 = v0;
+        h = (am + 1) * (am + 1) + am + 1 + m;
+        P[h * CS] = v1;
+        Gx[h * CS] = x1;
+        Gy[h * CS] = y1;
+        Gz[h * CS] = z1;
+#pragma unroll 2
+        for (int l = am + 1; l < LAM; ++l) {
+          const double g = k_harm.ng[l * l + l + m];
+          const double v2 = fma(g * r2, v0, z * v1);
+          const double x2 = fma(g, fma(2.0 * x, v0, r2 * x0), z * x1);
+          const double y2 = fma(g, fma(2.0 * y, v0, r2 * y0), z * y1);
+          const double z2 = fma(g, fma(2.0 * z, v0, r2 * z0), fma(z, z1, v1));
+          h = (l + 1) * (l + 1) + l + 1 + m;
+          P[h * CS] = v2;
+          Gx[h * CS] = x2;
+          Gy[h * CS] = y2;
+          Gz[h * CS] = z2;
+          v0 = v1; x0 = x1; y0 = y1; z0 = z1;
+          v1 = v2; x1 = x2; y1 = y2; z1 = z2;
+        }
       }
+    }
+    // the diagonal chain one level up
+    if (am == 0) {
+      dp = x;
+      dm = y;
+      dpx = 1.0;
+      dpy = 0.0;
+      dmx = 0.0;
+      dmy = 1.0;
+    } else {
+      const double np = fma(x, dp, -y * dm), nm = fma(y, dp, x * dm);
+      const double npx = dp + fma(x, dpx, -y * dmx), npy = fma(x, dpy, -y * dmy) - dm;
+      const double nmx = fma(y, dpx, x * dmx) + dm, nmy = fma(y, dpy, x * dmy) + dp;
+      dp = np;
+      dm = nm;
+      dpx = npx;
+      dpy = npy;
+      dmx = nmx;
+      dmy = nmy;
     }
   }
 }
@@ -381,8 +386,9 @@ struct GradShape {
 // primitive pairs of one class, grad phi(C) += Q^T sum_e G'[e] d/dd [S~_{LM}(d) B_{L,k}(T)], d = C - P in the
 // pair frame, B_{L,k} = sum_{j<=k} T^j/j! F_{L+j} and dB_{L,k}/dT = -T^k/k! F_{L+k+1}, so
 // d/dd [S~ B] = B grad S~ - 2p T^k/k! F_{L+k+1} S~ d.  Threads: point c = t % 16; in the table phase
-// warp 0 (16 lanes) evaluates the Boys values and radial factors, warp 1 the harmonic columns; in the
-// sum phase the four groups of 16 threads take a quarter of the R' entries each.
+// warp 0 (16 lanes) evaluates the Boys values and radial factors, warp 1 the harmonic columns (its two
+// halves the columns of m >= 0 and m < 0); in the sum phase the four groups of 16 threads take a quarter
+// of the R' entries each.
 template <int LAM>
 __global__ void __launch_bounds__(64) k_esp_grad_fp64(EspArgs A) {
   using Sh = GradShape<LAM>;
@@ -445,9 +451,11 @@ __global__ void __launch_bounds__(64) k_esp_grad_fp64(EspArgs A) {
           }
           bo += (LAM - L) / 2 + 1;
         }
-      } else {
-        harmonic_columns_grad<LAM, CS, -LAM, LAM>(dx, dy, dz, Pt + pc, Gxt + pc, Gyt + pc, Gzt + pc);
       }
+    }
+    if (wid == 1) {
+      // both half-warps: the columns of m >= 0 (lanes 0-15) and m < 0 (lanes 16-31) of the same points
+      harmonic_columns_grad_half<LAM, CS>(lane >= NCH, dx, dy, dz, Pt + pc, Gxt + pc, Gyt + pc, Gzt + pc);
     }
     __syncthreads();
     double gx = 0.0, gy = 0.0, gz = 0.0, sb = 0.0;
