@@ -6,7 +6,7 @@
  * leaves what is computed unchanged up to a stated threshold: a small network predicts
  * log10 max_{ma,mb} |Z_C <a ma|1/|r-C||b mb>| for one shell pair (a, b) and one nucleus C, and
  * triples predicted below a threshold (with a safety margin) are left out of the nucleus sum of
- * Eq. 11.  The exact method stays the judge: callers audit a sample of the skipped triples with it.
+ * Eq. 11.  The exact method remains the reference: callers audit a sample of the skipped triples with it.
  *
  * Network: 16 inputs (shgo_screen_features) -> 64 -> 64 -> 1, SiLU activations.  The forward pass
  * uses BF16 weights (rounded from FP32 master weights after every update) with FP32 accumulation;

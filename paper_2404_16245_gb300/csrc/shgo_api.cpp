@@ -116,7 +116,7 @@ class HostImage {
 
 // Per-device memory pool for basis arrays: stream-ordered allocations that keep their memory after a
 // basis is freed (release threshold = unlimited), so creating and freeing bases repeatedly does not go
-// back to the driver each time.  All pool operations are ordered on the legacy default stream and the
+// back to the CUDA driver each time.  All pool operations are ordered on the legacy default stream and the
 // basis build synchronises before use on other streams.
 cudaError_t pool_alloc(int device, void** p, size_t bytes) {
   static std::mutex mu;

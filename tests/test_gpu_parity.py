@@ -38,7 +38,7 @@ THREADS = os.cpu_count() or 1
 
 
 def ref_V(basis, C, Z):
-    # The judge is the oracle built in extended precision (long double: 80-bit on x86-64, binary128
+    # The reference is the oracle built in extended precision (long double: 80-bit on x86-64, binary128
     # on aarch64).  The double build loses up to ~4e-12 absolute to Cartesian-route cancellation at
     # l >= 5 with large exponents, which exceeds the 1e-11 relative bar on small elements.
     return oracle.nuclear_attraction(basis, C, Z, threads=THREADS, precision="ld")
