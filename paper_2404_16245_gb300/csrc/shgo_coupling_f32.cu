@@ -8,7 +8,7 @@
 // with p^{-L/2}, N_LM and 2 pi k! p^{-(k+1)} applied in FP64 when the block is written.  The pair-frame
 // geometry and the Boys grid stay FP64; everything per nucleus after them (the Boys Taylor step and
 // recursions, Phi_n, t_j, the radial sums, the unit-vector harmonics U) and the nucleus sums run as
-// FP32 instructions, 64 of which issue for each FP64 one on this GPU.
+// FP32 instructions, 64 of which issue for each FP64 one on GB300 (sm_103a).
 //
 // FF = false (plain): each factor is one FP32 number and the nucleus sums are FMA chains.
 // FF = true (compensated): each factor is an unevaluated pair hi + lo of FP32 numbers (48 significant

@@ -349,7 +349,7 @@ __device__ void pair_features(const ScreenBasis& sb, int pr, PairFeat& pf, int l
 }
 
 // Nucleus-dependent features in FP32 (only the coordinate differences are formed in FP64): they
-// are network inputs, and FP64 square roots and logarithms are costly on this GPU.
+// are network inputs, and FP64 square roots and logarithms are costly on GB300 (sm_103a).
 __device__ void nucleus_features(const PairFeat& pf, const double* C, double Z, float* x) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) x[k] = pf.f[k];
