@@ -68,6 +68,7 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             ctypes.c_int]
         lib.oracle_nuclear_field.restype = ctypes.c_int
         lib.oracle_overlap.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
+        lib.oracle_coulomb_2c.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_overlap.restype = ctypes.c_int
         lib.oracle_prim_norm.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.oracle_prim_norm.restype = ctypes.c_double
@@ -130,6 +131,17 @@ def overlap(basis, threads: int = 1, precision: str = "f64") -> np.ndarray:
     n = nbf(basis)
     out = np.zeros(max(n * n, 1), dtype=np.float64)
     rc = _lib(precision).oracle_overlap(len(l), l, nprim, exps, coefs, xyz, out, threads)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the basis (code {rc})")
+    return out[: n * n].reshape(n, n)
+
+
+def coulomb_2c(basis, threads: int = 1, precision: str = "f64") -> np.ndarray:
+    """(a|b) = int int phi_a(r1) phi_b(r2) / |r1 - r2| (two-centre electron repulsion), nbf x nbf."""
+    l, nprim, exps, coefs, xyz = _basis_arrays(basis)
+    n = nbf(basis)
+    out = np.zeros(max(n * n, 1), dtype=np.float64)
+    rc = _lib(precision).oracle_coulomb_2c(len(l), l, nprim, exps, coefs, xyz, out, threads)
     if rc != 0:
         raise ValueError(f"oracle rejected the basis (code {rc})")
     return out[: n * n].reshape(n, n)

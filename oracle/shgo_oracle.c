@@ -417,10 +417,78 @@ static void nuclear_block(const shell_t* a, const shell_t* b, const real* ca, co
   free(Ex);
 }
 
+/* Two-centre Coulomb block of one shell pair: out[ma * (2lb+1) + mb] =
+ *   (a, ma | b, mb) = int int phi_a(r1) phi_b(r2) / |r1 - r2| d3r1 d3r2.
+ * McMurchie-Davidson with each orbital its own one-Gaussian "pair": per primitive pair,
+ *   2 pi^{5/2} / (alpha beta sqrt(alpha + beta)) sum_{tuv} E^a_{tuv} sum_{t'u'v'} E^b_{t'u'v'} (-1)^{t'+u'+v'}
+ *       R^0_{t+t', u+u', v+v'}(rho, A - B),   rho = alpha beta / (alpha + beta),
+ * where the Hermite coefficients of x_A^i exp(-alpha x_A^2) follow from hermite_E with jmax = 0,
+ * X_PA = 0 and E^{00}_0 = 1. */
+static void coulomb2c_block(const shell_t* a, const shell_t* b, const real* ca, const real* cb, real* out) {
+  const int la = a->l, lb = b->l, L = la + lb, nca = ncart(la), ncb = ncart(lb), d = L + 1;
+  real* Ea = (real*)malloc(sizeof(real) * 3 * (size_t)(la + 1) * (la + 1));
+  real* Eb = (real*)malloc(sizeof(real) * 3 * (size_t)(lb + 1) * (lb + 1));
+  real* work = (real*)malloc(sizeof(real) * (size_t)d * d * d * d);
+  real* R = (real*)malloc(sizeof(real) * (size_t)d * d * d);
+  real* Vc = (real*)calloc((size_t)nca * ncb, sizeof(real));
+  for (int i = 0; i < a->nprim; ++i)
+    for (int j = 0; j < b->nprim; ++j) {
+      const real al = a->alpha[i], be = b->alpha[j], rho = al * be / (al + be);
+      for (int c = 0; c < 3; ++c) {
+        hermite_E(la, 0, al, 0, 0, 1, Ea + (size_t)c * (la + 1) * (la + 1));
+        hermite_E(lb, 0, be, 0, 0, 1, Eb + (size_t)c * (lb + 1) * (lb + 1));
+      }
+      hermite_R(L, rho, a->A[0] - b->A[0], a->A[1] - b->A[1], a->A[2] - b->A[2], work, R);
+      const real pre = a->coef[i] * b->coef[j] * 2 * RX(pow)(RPI, (real)2.5) / (al * be * RX(sqrt)(al + be));
+      for (int ix = la; ix >= 0; --ix)
+        for (int iy = la - ix; iy >= 0; --iy) {
+          const int iz = la - ix - iy, ia = cart_index(la, ix, iy);
+          const real* ex = Ea + ix * (la + 1);
+          const real* ey = Ea + (size_t)(la + 1) * (la + 1) + iy * (la + 1);
+          const real* ez = Ea + (size_t)2 * (la + 1) * (la + 1) + iz * (la + 1);
+          for (int jx = lb; jx >= 0; --jx)
+            for (int jy = lb - jx; jy >= 0; --jy) {
+              const int jz = lb - jx - jy, ib = cart_index(lb, jx, jy);
+              const real* fx = Eb + jx * (lb + 1);
+              const real* fy = Eb + (size_t)(lb + 1) * (lb + 1) + jy * (lb + 1);
+              const real* fz = Eb + (size_t)2 * (lb + 1) * (lb + 1) + jz * (lb + 1);
+              real sum = 0;
+              for (int t = 0; t <= ix; ++t)
+                for (int u = 0; u <= iy; ++u)
+                  for (int v = 0; v <= iz; ++v) {
+                    const real e = ex[t] * ey[u] * ez[v];
+                    if (e == 0) continue;
+                    for (int t2 = 0; t2 <= jx; ++t2)
+                      for (int u2 = 0; u2 <= jy; ++u2)
+                        for (int v2 = 0; v2 <= jz; ++v2) {
+                          const real f = fx[t2] * fy[u2] * fz[v2];
+                          if (f == 0) continue;
+                          const real sg = ((t2 + u2 + v2) & 1) ? -1 : 1;
+                          sum += e * f * sg * R[((t + t2) * d + u + u2) * d + v + v2];
+                        }
+                  }
+              Vc[ia * ncb + ib] += pre * sum;
+            }
+        }
+    }
+  for (int ma = 0; ma < 2 * la + 1; ++ma)
+    for (int mb = 0; mb < 2 * lb + 1; ++mb) {
+      real s2 = 0;
+      for (int ia = 0; ia < nca; ++ia)
+        for (int ib = 0; ib < ncb; ++ib) s2 += ca[ma * nca + ia] * cb[mb * ncb + ib] * Vc[ia * ncb + ib];
+      out[ma * (2 * lb + 1) + mb] = s2;
+    }
+  free(Vc);
+  free(R);
+  free(work);
+  free(Eb);
+  free(Ea);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Public entry points.                                                                       */
 /* ------------------------------------------------------------------------------------------ */
-typedef enum { OP_OVERLAP = 0, OP_NUCLEAR = 1 } op_t;
+typedef enum { OP_OVERLAP = 0, OP_NUCLEAR = 1, OP_COULOMB2C = 2 } op_t;
 
 static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, const double* exps,
                         const double* coefs, const double* xyz, long nC, const double* C, const double* Z,
@@ -453,6 +521,8 @@ static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, c
       real* blk = (real*)malloc(sizeof(real) * (size_t)na * nb);
       if (op == OP_OVERLAP)
         overlap_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], blk);
+      else if (op == OP_COULOMB2C)
+        coulomb2c_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], blk);
       else
         nuclear_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], nC, C, Z, blk, dcomp);
       for (int i = 0; i < na; ++i)
@@ -495,6 +565,14 @@ int oracle_nuclear_field(int n_shells, const int* l, const int* nprim, const dou
 int oracle_overlap(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
                    const double* xyz, double* out, int n_threads) {
   return one_electron(OP_OVERLAP, n_shells, l, nprim, exps, coefs, xyz, 0, NULL, NULL, out, n_threads, -1);
+}
+
+/* Two-centre Coulomb integrals (a|b) = int int phi_a(r1) phi_b(r2) / |r1 - r2| over the same basis (the
+ * metric of density fitting; the two-centre case of the electron-repulsion integrals of Eqs. 13-15);
+ * same layout and conventions. */
+int oracle_coulomb_2c(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
+                      const double* xyz, double* out, int n_threads) {
+  return one_electron(OP_COULOMB2C, n_shells, l, nprim, exps, coefs, xyz, 0, NULL, NULL, out, n_threads, -1);
 }
 
 /* Primitive normalisation N(l, alpha) of Eq. 1, as used above. */

@@ -306,3 +306,62 @@ def test_field_ss_closed_form():
     ref = -(2 * math.pi / p) * K * nn * F1 * 2 * p * (C[0] - P)
     F = oracle.nuclear_field(basis, C, np.ones(1))
     assert np.allclose(F[:, 0, 1], ref, rtol=1e-13, atol=1e-16)
+
+
+# ---- two-centre Coulomb integrals (a|b) (the two-centre case of Eqs. 13-15) ----
+
+def _norm_s(a):
+    return (2 * a / math.pi) ** 0.75
+
+
+@pytest.mark.parametrize("R", [0.0, 1.3, 7.5])
+def test_coulomb2c_ss_closed_form(R):
+    """(s|s) of normalised primitives: N_a N_b 2 pi^{5/2} / (a b sqrt(a + b)) F_0(rho R^2), rho = ab/(a+b),
+    with F_0 from erf (the R = 0 limit 1 taken exactly)."""
+    a, b = 0.7, 1.9
+    basis = W.make_basis([0, 0], [1, 1], [a, b], [1.0, 1.0], [np.zeros(3), np.array([0.0, 0.0, R])])
+    J = oracle.coulomb_2c(basis, precision="ld")
+    T = a * b / (a + b) * R * R
+    F0 = 1.0 if T == 0 else 0.5 * math.sqrt(math.pi / T) * sp.erf(math.sqrt(T))
+    ref = _norm_s(a) * _norm_s(b) * 2 * math.pi ** 2.5 / (a * b * math.sqrt(a + b)) * F0
+    assert J[0, 1] == pytest.approx(ref, rel=1e-14)
+    self_ref = _norm_s(a) ** 2 * 2 * math.pi ** 2.5 / (a * a * math.sqrt(2 * a))
+    assert J[0, 0] == pytest.approx(self_ref, rel=1e-14)
+
+
+def test_coulomb2c_dipole_far_field():
+    """Two p shells 400 bohr apart along z interact as point dipoles mu = int z phi_z: (z|z) -> -2 mu_a mu_b / R^3,
+    (x|x) = (y|y) -> mu_a mu_b / R^3, mixed components -> 0 (relative corrections ~ (extent / R)^2)."""
+    a, b, R = 0.9, 1.4, 400.0
+    basis = W.make_basis([1, 1], [1, 1], [a, b], [1.0, 1.0], [np.zeros(3), np.array([0.0, 0.0, R])])
+    J = oracle.coulomb_2c(basis, precision="ld")
+
+    def mu(al):  # normalised primitive z exp(-al r^2): N^2 = 2 (2 al)^{5/2} / pi^{3/2}
+        return math.sqrt(2 * (2 * al) ** 2.5 / math.pi ** 1.5) * (math.pi / al) ** 1.5 / (2 * al)
+
+    d = mu(a) * mu(b) / R ** 3
+    assert J[1, 4] == pytest.approx(-2 * d, rel=1e-8)   # m = 0 (z)
+    assert J[0, 3] == pytest.approx(d, rel=1e-8)        # m = -1 (y)
+    assert J[2, 5] == pytest.approx(d, rel=1e-8)        # m = +1 (x)
+    assert abs(J[0, 4]) < 1e-12 * d and abs(J[1, 5]) < 1e-12 * d
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_coulomb2c_rotation_covariance_and_metric(seed):
+    """(a|b) of a rotated basis is D^la (a|b) D^lb^T with fitted real Wigner blocks; the matrix is
+    symmetric and positive definite (a Coulomb metric)."""
+    basis = W.random_basis(40 + seed, 8, 4, max_prim=2)
+    R = RM.rotation_matrix(seed)
+    J = oracle.coulomb_2c(basis, precision="ld")
+    b2 = dict(basis)
+    b2["xyz"] = basis["xyz"] @ R.T
+    J2 = oracle.coulomb_2c(b2, precision="ld")
+    off = np.concatenate([[0], np.cumsum(2 * basis["l"] + 1)])
+    D = [RM.wigner_real(int(l), R) for l in basis["l"]]
+    for a in range(len(basis["l"])):
+        for b in range(len(basis["l"])):
+            blk = J[off[a]:off[a + 1], off[b]:off[b + 1]]
+            blk2 = J2[off[a]:off[a + 1], off[b]:off[b + 1]]
+            assert np.allclose(D[a] @ blk @ D[b].T, blk2, rtol=0, atol=1e-11 * np.max(np.abs(J)))
+    assert np.array_equal(J, J.T)
+    assert np.min(np.linalg.eigvalsh(J)) > 0
