@@ -212,6 +212,16 @@ shgo_status shgo_esp_gradient(const shgo_basis* basis, const double* density, co
  * no nuclei are involved.  Errors: SHGO_ERR_INVALID_ARG (NULL basis or out), SHGO_ERR_CUDA. */
 shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream);
 
+/* Two-centre Coulomb integrals (a|b) = int int phi_a(r1) phi_b(r2) / |r1 - r2| (the two-centre case of the
+ * electron-repulsion integrals, Eqs. 13-15; the Coulomb metric of density fitting) of a basis or of every
+ * molecule of a batch.  With Eq. 3 each orbital is a solid-harmonic derivative of an s Gaussian with
+ * respect to its centre, so (a|b) is S_la(grad_R) S_lb(grad_R) applied to the s-s integral, a function of
+ * |A - B|^2 through F_0; the product rule of solid harmonics (the Gaunt coupling) and Hobson's theorem
+ * turn it into sum_{L,M} G 2^L S_LM(A - B) times Boys values F_{L+k+j}.  Computed in FP64 whatever the
+ * basis's precision option.  out: as for shgo_overlap (symmetric, fully overwritten).  Asynchronous on
+ * `stream`.  Errors: SHGO_ERR_INVALID_ARG (NULL basis or out), SHGO_ERR_CUDA. */
+shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream);
+
 /* Per (la, lb) class (measurement): number of classes of a basis (-1 for NULL); for class c
  * (0 <= c < nclasses, in the library's launch order) its la >= lb in la_lb[2] and, for n_centers
  * nuclei, stats[4] = shell-triples, integrals (shell-triples x (2la+1)(2lb+1)), algorithmic flops of

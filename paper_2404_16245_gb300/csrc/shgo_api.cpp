@@ -695,6 +695,30 @@ shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream) {
   return SHGO_OK;
 }
 
+shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (!out && (basis->batch ? basis->out_size : basis->nbf) > 0) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  MolView mv;
+  if (basis->batch) {
+    mv.pair_mol = basis->pair_mol;
+    mv.c0 = basis->mol_c0_d;
+    mv.nc = basis->mol_nc_d;
+    mv.out_off = basis->mol_out_d;
+    mv.ld = basis->mol_ld_d;
+  }
+  mv.nbf = basis->nbf;
+  std::string err;
+  const shgo_status st = launch_coulomb2c(basis->d, *basis->tabs, tables_host(), basis->work, mv, out,
+                                          (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+
 int64_t shgo_basis_nbf(const shgo_basis* basis) { return basis ? basis->nbf : -1; }
 int64_t shgo_basis_npairs(const shgo_basis* basis) { return basis ? basis->npairs : -1; }
 

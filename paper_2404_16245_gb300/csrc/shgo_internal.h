@@ -100,7 +100,17 @@ struct Tables {
   // (q = l^2 + 2l + M + l + 1 ... see rot_index()) holds (G, Cartesian component c, m').
   std::vector<int> rot_ptr;
   std::vector<GTerm> rot_terms;
+  // Two-centre Coulomb integrals: per class (la >= lb) and block entry e = (ma + la)(2lb + 1) + mb + lb,
+  // the product-rule terms S_la,ma S_lb,mb = sum_{L,M} G |v|^{2k} S_LM as c2_terms[c2_ptr[c2_base[c] + e] ..
+  // c2_ptr[c2_base[c] + e + 1]) = (G, L^2 + L + M, L); and the coefficients of
+  // (Delta_L)^k f^{(L)} = sum_j a_{k,j}(L) u^j f^{(L+k+j)}, Delta_L f = 4u f'' + (4L + 6) f', at
+  // c2_a[(L (kC2K + 1) + k)(kC2K + 1) + j].
+  std::vector<int> c2_ptr;
+  std::vector<GTerm> c2_terms;
+  std::vector<int> c2_base;  // [n classes]
+  std::vector<double> c2_a;
 };
+constexpr int kC2K = kLamMax / 2;  // largest k of the two-centre radial factors
 const Tables& tables_host();
 
 // Index of the (l -> l+1, M) list of the rotation recursion: lists for l = 0.. are stored one after
@@ -135,6 +145,9 @@ struct DeviceTables {
   double* rnorm = nullptr;
   int* rot_ptr = nullptr;
   GTerm* rot_terms = nullptr;
+  int* c2_ptr = nullptr;
+  GTerm* c2_terms = nullptr;
+  double* c2_a = nullptr;
   float2* boys_ff = nullptr;  // boys as (hi, lo) FP32 pairs
   float2* exp_ff = nullptr;   // exp(-g/16) as (hi, lo) FP32 pairs
   float2* rnorm_ff = nullptr; // rnorm as (hi, lo) FP32 pairs
@@ -351,6 +364,11 @@ cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int
 size_t coupling_fp64_smem(int lam, int nch);
 // Constants and launch attributes of the FP64 coupling kernels on the current device.
 cudaError_t coupling_fp64_setup();
+
+// Two-centre Coulomb integrals (a|b) of every class of `work` into out (layout of V, both triangles).
+shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
+                             const std::vector<ClassWork>& work, const MolView& mv, double* out, cudaStream_t stream,
+                             std::string* err);
 
 // FP32-bulk coupling (shgo_coupling_f32.cu): the Lambda = lam instantiation, compensated (pair
 // arithmetic) or plain, on `grid` blocks of 64 threads; args.boys_ff and args.exp_ff must be set.

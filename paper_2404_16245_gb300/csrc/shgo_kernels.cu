@@ -712,6 +712,9 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.rnorm, t.rnorm);
   if (e == cudaSuccess) e = upload(&d.rot_ptr, t.rot_ptr);
   if (e == cudaSuccess) e = upload(&d.rot_terms, t.rot_terms);
+  if (e == cudaSuccess) e = upload(&d.c2_ptr, t.c2_ptr);
+  if (e == cudaSuccess) e = upload(&d.c2_terms, t.c2_terms);
+  if (e == cudaSuccess) e = upload(&d.c2_a, t.c2_a);
   if (e == cudaSuccess) e = upload(&d.boys_ff, boys_table_pairs(t.boys));
   if (e == cudaSuccess) e = upload(&d.exp_ff, exp_table_pairs());
   if (e == cudaSuccess) e = upload(&d.rnorm_ff, pairs_of(t.rnorm));
@@ -1250,6 +1253,126 @@ shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std:
     return SHGO_ERR_CUDA;
   }
   return SHGO_OK;
+}
+
+// Two-centre Coulomb integrals (a|b) of one class, one block per shell pair.  With Eq. 3 each primitive is
+// N (2 alpha)^{-l} S_l(grad_A) exp(-alpha |r - A|^2), so for R = A - B (grad_B = -grad_R on functions of R)
+//   (a|b) = c_a c_b (2 alpha)^{-la} (2 beta)^{-lb} (-1)^lb S_la(grad_R) S_lb(grad_R) g(|R|^2),
+//   g(u) = 2 pi^{5/2} / (alpha beta sqrt(alpha + beta)) F_0(rho u),  rho = alpha beta / (alpha + beta),
+// the Coulomb integral of two s Gaussians.  The product rule of solid harmonics (the Gaunt coupling of the
+// pair kernel) gives S_la S_lb = sum_{L,M} G |v|^{2k} S_LM with k = (la + lb - L)/2, Hobson's theorem
+// S_LM(grad) f(u) = 2^L S_LM(R) f^{(L)}(u), and the Laplacian of S_LM(R) f(u) is S_LM(R) (4u f'' + (4L + 6) f'),
+// so every term is 2^L S_LM(R) sum_j a_{k,j}(L) u^j g^{(L+k+j)}(u), with
+// g^{(n)}(u) = 2 pi^{5/2} / (alpha beta sqrt(alpha + beta)) (-rho)^n F_n(rho u).
+// Threads: one primitive pair each for the Boys values, one L each for the radial sums over primitive pairs,
+// one block entry each for the coupling; the block and its transpose are written as in the overlap.
+__global__ void __launch_bounds__(64) k_coulomb2c(int la, int lb, int npairs, int pair_base,
+                                                  const int* __restrict__ pair_a, const int* __restrict__ pair_b,
+                                                  const double* __restrict__ shell_xyz,
+                                                  const int* __restrict__ shell_poff, const int* __restrict__ shell_nprim,
+                                                  const int64_t* __restrict__ shell_foff,
+                                                  const double* __restrict__ prim_exp,
+                                                  const double* __restrict__ prim_coef,
+                                                  const double* __restrict__ boys_tab, const int* __restrict__ c2_ptr,
+                                                  const GTerm* __restrict__ c2_terms, const double* __restrict__ c2_a,
+                                                  MolView mv, double* __restrict__ out) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lam = la + lb, na = 2 * la + 1, nb = 2 * lb + 1, nf = lam + 1;
+  double* S = smem;                      // [(lam + 1)^2] S_LM(R)
+  double* X = S + nf * nf;               // [lam + 1] radial sums over primitive pairs, by L
+  double* F = X + nf;                    // [64][lam + 1] Boys values of a batch of primitive pairs
+  double* pf = F + 64 * nf;              // [64] prefactors
+  double* mr = pf + 64;                  // [64] -rho
+  double* ru = mr + 64;                  // [1] |R|^2
+  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
+    const int pr = pair_base + w;
+    const int a = pair_a[pr], b = pair_b[pr];
+    const double Rx = shell_xyz[3 * a] - shell_xyz[3 * b], Ry = shell_xyz[3 * a + 1] - shell_xyz[3 * b + 1],
+                 Rz = shell_xyz[3 * a + 2] - shell_xyz[3 * b + 2];
+    const double u = Rx * Rx + Ry * Ry + Rz * Rz;
+    __syncthreads();  // the previous pair is done with S and X
+    if (tid == 0) {
+      solid_harmonics<double>(lam, Rx, Ry, Rz, S, 1, c_harm.a, c_harm.b, c_harm.c);
+      *ru = u;
+    }
+    if (tid < nf) X[tid] = 0.0;
+    const int npa = shell_nprim[a], npb = shell_nprim[b], npp = npa * npb;
+    for (int q0 = 0; q0 < npp; q0 += 64) {
+      __syncthreads();  // the previous batch is consumed
+      const int q = q0 + tid;
+      if (tid < 64 && q < npp) {
+        const int i = q / npb, j = q - i * npb;
+        const double al = prim_exp[shell_poff[a] + i], be = prim_exp[shell_poff[b] + j];
+        const double rho = al * be / (al + be);
+        double v = prim_coef[shell_poff[a] + i] * prim_coef[shell_poff[b] + j] * 6.2831853071795864769 *
+                   5.5683279968317078453 / (al * be * sqrt(al + be));  // 2 pi^{5/2} = 2 pi x pi^{3/2}
+        const double ia = 0.5 / al, ib = 0.5 / be;
+        for (int k = 0; k < la; ++k) v *= ia;
+        for (int k = 0; k < lb; ++k) v *= ib;
+        pf[tid] = (lb & 1) ? -v : v;
+        mr[tid] = -rho;
+        boys_eval(lam, rho * u, F + tid * nf, 1, boys_tab, c_boys);
+      }
+      __syncthreads();
+      const int nq = min(64, npp - q0);
+      // radial sums: one L per thread (L = la - lb, la - lb + 2, ..., la + lb)
+      const int L = la - lb + 2 * tid;
+      if (L <= lam) {
+        const int k = (lam - L) / 2;
+        const double* ak = c2_a + ((size_t)L * (kC2K + 1) + k) * (kC2K + 1);
+        double acc = X[L];
+        for (int t = 0; t < nq; ++t) {
+          const double* Ft = F + t * nf;
+          double mrp = 1.0;  // (-rho)^{L+k}
+          for (int n = 0; n < L + k; ++n) mrp *= mr[t];
+          double s = 0.0, uj = 1.0;
+          for (int j = 0; j <= k; ++j) {
+            s = fma(ak[j] * uj, mrp * Ft[L + k + j], s);
+            uj *= u;
+            mrp *= mr[t];
+          }
+          acc = fma(pf[t], s, acc);
+        }
+        X[L] = acc;
+      }
+    }
+    __syncthreads();
+    // coupling: sum over (L, M) of G 2^L S_LM(R) X_L, one block entry per thread
+    const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
+    int64_t obase, ld;
+    mol_output(mv, pr, obase, ld);
+    double* o = out + obase;
+    const int* ptr = c2_ptr;
+    for (int e = tid; e < na * nb; e += nth) {
+      double v = 0.0;
+      for (int t = ptr[e]; t < ptr[e + 1]; ++t) {
+        const GTerm g = c2_terms[t];
+        v = fma(g.coef * S[g.ridx], ldexp(X[g.pad], g.pad), v);
+      }
+      const int ma = e / nb, mb = e - ma * nb;
+      o[(fa0 + ma) * ld + fb0 + mb] = v;
+      if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = v;
+    }
+  }
+}
+
+size_t coulomb2c_smem(int la, int lb) {
+  const int nf = la + lb + 1;
+  return sizeof(double) * ((size_t)nf * nf + nf + 64 * (size_t)nf + 64 + 64 + 1 + 8);
+}
+
+shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
+                             const std::vector<ClassWork>& work, const MolView& mv, double* out, cudaStream_t stream,
+                             std::string* err) {
+  for (const ClassWork& w : work) {
+    if (w.npairs == 0) continue;
+    k_coulomb2c<<<grid_cap(w.npairs, 16), 64, coulomb2c_smem(w.la, w.lb), stream>>>(
+        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.shell_nprim,
+        db.shell_foff, db.prim_exp, db.prim_coef, dt.boys, dt.c2_ptr + th.c2_base[class_id(w.la, w.lb)],
+        dt.c2_terms, dt.c2_a, mv, out);
+  }
+  return launch_error(err);
 }
 
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,

@@ -248,6 +248,40 @@ void build_tables(Tables& t) {
       }
     t.rot_ptr.push_back((int)t.rot_terms.size());
   }
+  // two-centre Coulomb: product-rule terms per class and block entry, and the radial coefficients
+  t.c2_ptr.clear();
+  t.c2_terms.clear();
+  t.c2_base.assign(kNumClasses, 0);
+  for (int la = 0; la <= kLmax; ++la)
+    for (int lb = 0; lb <= la; ++lb) {
+      t.c2_base[class_id(la, lb)] = (int)t.c2_ptr.size();
+      for (int ma = -la; ma <= la; ++ma)
+        for (int mb = -lb; mb <= lb; ++mb) {
+          t.c2_ptr.push_back((int)t.c2_terms.size());
+          for (int L = la - lb; L <= la + lb; L += 2)
+            for (int M = -L; M <= L; ++M) {
+              const double g = gaunt_real(la, ma, lb, mb, L, M);
+              if (std::fabs(g) > 1e-15) t.c2_terms.push_back(GTerm{g, L * L + L + M, L});
+            }
+        }
+      t.c2_ptr.push_back((int)t.c2_terms.size());
+    }
+  t.c2_a.assign((size_t)(kLamMax + 1) * (kC2K + 1) * (kC2K + 1), 0.0);
+  for (int L = 0; L <= kLamMax; ++L) {
+    // a_{0,0} = 1; Delta_L (u^j f^{(n)}) = (4j^2 + (4L + 2) j) u^{j-1} f^{(n)} + (8j + 4L + 6) u^j f^{(n+1)}
+    //                                     + 4 u^{j+1} f^{(n+2)}, with n = L + k + j
+    std::vector<ld> cur(1, 1.0L);
+    for (int k = 0; k <= kC2K; ++k) {
+      for (int j = 0; j <= k; ++j) t.c2_a[((size_t)L * (kC2K + 1) + k) * (kC2K + 1) + j] = (double)cur[j];
+      std::vector<ld> nxt(k + 2, 0.0L);
+      for (int j = 0; j <= k; ++j) {
+        if (j >= 1) nxt[j - 1] += cur[j] * (ld)(4 * j * j + (4 * L + 2) * j);
+        nxt[j] += cur[j] * (ld)(8 * j + 4 * L + 6);
+        nxt[j + 1] += cur[j] * 4.0L;
+      }
+      cur.swap(nxt);
+    }
+  }
   // Gaunt programs per class
   std::vector<std::vector<std::pair<int, double>>> terms;  // per (i1, i2) over all l <= kLmax
   const int nh = (kLmax + 1) * (kLmax + 1);

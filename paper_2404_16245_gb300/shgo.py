@@ -86,6 +86,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_esp_gradient.restype = ctypes.c_int
     lib.shgo_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_overlap.restype = ctypes.c_int
+    lib.shgo_coulomb_2c.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_coulomb_2c.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -327,6 +329,25 @@ def overlap(basis, out=None, stream=None, device="cuda"):
     if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != shape:
         raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
     shgo_overlap(basis.handle, out.data_ptr(), stream)
+    return out
+
+
+def shgo_coulomb_2c(basis, out_ptr, stream=None):
+    _check(_lib.shgo_coulomb_2c(ctypes.c_void_p(basis), ctypes.c_void_p(int(out_ptr) or 0), _stream_handle(stream)))
+
+
+def coulomb_2c(basis, out=None, stream=None, device="cuda"):
+    """Two-centre Coulomb integrals (a|b) (FP64 device tensor), laid out as overlap()."""
+    import torch
+    if isinstance(basis, Basis):
+        shape = (basis.nbf, basis.nbf)
+    else:
+        shape = (max(basis.out_size, 1),)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != shape:
+        raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
+    shgo_coulomb_2c(basis.handle, out.data_ptr(), stream)
     return out
 
 
