@@ -1266,6 +1266,38 @@ shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std:
 // g^{(n)}(u) = 2 pi^{5/2} / (alpha beta sqrt(alpha + beta)) (-rho)^n F_n(rho u).
 // Threads: one primitive pair each for the Boys values, one L each for the radial sums over primitive pairs,
 // one block entry each for the coupling; the block and its transpose are written as in the overlap.
+// Real solid harmonics S_lm(x, y, z), l <= lmax, by columns: thread t of nth takes the columns
+// m = t - lmax, t + nth - lmax, ...; each walks the diagonal chain S_{l+1,+-(l+1)} = c_l (x S_ll -+ y S_{l,-l})
+// (S_11 = x, S_1-1 = y) up to |m| and then S_{l+1,m} = a_lm z S_lm - b_lm r^2 S_{l-1,m} (the recursion of
+// solid_harmonics, whose entries it reproduces operation for operation) into S[l^2 + l + m].
+__device__ void solid_harmonics_columns(int lmax, double x, double y, double z, double* S, int tid, int nth) {
+  const double r2 = x * x + y * y + z * z;
+  for (int col = tid; col < 2 * lmax + 1; col += nth) {
+    const int m = col - lmax, am = m < 0 ? -m : m;
+    double sp = 1.0, sm = 0.0;  // S_{l,l}, S_{l,-l}
+    if (am >= 1) {
+      sp = x;
+      sm = y;
+      for (int l = 1; l < am; ++l) {
+        const double c = c_harm.c[l];
+        const double np = c * (x * sp - y * sm), nm = c * (y * sp + x * sm);
+        sp = np;
+        sm = nm;
+      }
+    }
+    double prv = 0.0, cur = m < 0 ? sm : sp;
+    S[am * am + am + m] = cur;
+    for (int l = am; l < lmax; ++l) {
+      const int k = l * l + l + m;
+      double v = c_harm.a[k] * (z * cur);
+      if (m > -l && m < l) v -= c_harm.b[k] * (r2 * prv);
+      S[(l + 1) * (l + 1) + l + 1 + m] = v;
+      prv = cur;
+      cur = v;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(64) k_coulomb2c(int la, int lb, int npairs, int pair_base,
                                                   const int* __restrict__ pair_a, const int* __restrict__ pair_b,
                                                   const double* __restrict__ shell_xyz,
@@ -1292,10 +1324,8 @@ __global__ void __launch_bounds__(64) k_coulomb2c(int la, int lb, int npairs, in
                  Rz = shell_xyz[3 * a + 2] - shell_xyz[3 * b + 2];
     const double u = Rx * Rx + Ry * Ry + Rz * Rz;
     __syncthreads();  // the previous pair is done with S and X
-    if (tid == 0) {
-      solid_harmonics<double>(lam, Rx, Ry, Rz, S, 1, c_harm.a, c_harm.b, c_harm.c);
-      *ru = u;
-    }
+    solid_harmonics_columns(lam, Rx, Ry, Rz, S, tid, nth);
+    if (tid == 0) *ru = u;
     if (tid < nf) X[tid] = 0.0;
     const int npa = shell_nprim[a], npb = shell_nprim[b], npp = npa * npb;
     for (int q0 = 0; q0 < npp; q0 += 64) {
@@ -1338,6 +1368,8 @@ __global__ void __launch_bounds__(64) k_coulomb2c(int la, int lb, int npairs, in
       }
     }
     __syncthreads();
+    if (tid <= lam) X[tid] = ldexp(X[tid], tid);  // 2^L X_L
+    __syncthreads();
     // coupling: sum over (L, M) of G 2^L S_LM(R) X_L, one block entry per thread
     const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
     int64_t obase, ld;
@@ -1348,7 +1380,7 @@ __global__ void __launch_bounds__(64) k_coulomb2c(int la, int lb, int npairs, in
       double v = 0.0;
       for (int t = ptr[e]; t < ptr[e + 1]; ++t) {
         const GTerm g = c2_terms[t];
-        v = fma(g.coef * S[g.ridx], ldexp(X[g.pad], g.pad), v);
+        v = fma(g.coef * S[g.ridx], X[g.pad], v);
       }
       const int ma = e / nb, mb = e - ma * nb;
       o[(fa0 + ma) * ld + fb0 + mb] = v;
