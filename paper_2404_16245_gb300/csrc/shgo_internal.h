@@ -264,7 +264,7 @@ struct DeviceBasis {
 
 // Coupling-buffer cap (doubles) above which a basis switches to per-stream regions (2 GiB).
 constexpr int64_t kRbufCapDoubles = (int64_t)1 << 28;
-constexpr int kPoolStreamsPublic = 8;
+constexpr int kPoolStreamsPublic = 16;
 
 // Frame of a shell pair: rows (e1, e2, n) of a rotation Q with Q n = z for n = (B - A)/|B - A|,
 // e1 perpendicular to n along the axis least aligned with it, e2 = n x e1 (det Q = +1).

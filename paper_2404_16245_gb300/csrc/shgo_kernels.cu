@@ -774,7 +774,7 @@ static int grid_cap(int64_t n, int per_sm) {
 }
 
 namespace {
-constexpr int kPoolStreams = 8;
+constexpr int kPoolStreams = 16;
 std::mutex g_pool_mu;
 cudaStream_t g_pool[64][kPoolStreams];
 bool g_pool_ok[64] = {};
