@@ -70,6 +70,8 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
         lib.oracle_overlap.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_coulomb_2c.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_overlap.restype = ctypes.c_int
+        lib.oracle_eri.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
+        lib.oracle_eri.restype = ctypes.c_int
         lib.oracle_prim_norm.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.oracle_prim_norm.restype = ctypes.c_double
         lib.oracle_real_bits.argtypes = []
@@ -145,6 +147,18 @@ def coulomb_2c(basis, threads: int = 1, precision: str = "f64") -> np.ndarray:
     if rc != 0:
         raise ValueError(f"oracle rejected the basis (code {rc})")
     return out[: n * n].reshape(n, n)
+
+
+def eri(basis, threads: int = 1, precision: str = "f64") -> np.ndarray:
+    """(ij|kl) = int int phi_i(r1) phi_j(r1) phi_k(r2) phi_l(r2) / |r1 - r2| (four-centre electron
+    repulsion, Eqs. 13-15), nbf x nbf x nbf x nbf."""
+    l, nprim, exps, coefs, xyz = _basis_arrays(basis)
+    n = nbf(basis)
+    out = np.zeros(max(n ** 4, 1), dtype=np.float64)
+    rc = _lib(precision).oracle_eri(len(l), l, nprim, exps, coefs, xyz, out, threads)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the basis (code {rc})")
+    return out[: n ** 4].reshape(n, n, n, n)
 
 
 def boys(nmax: int, T: float, precision: str = "f64") -> np.ndarray:

@@ -20,6 +20,8 @@
  *  - N(l, alpha) of Eq. 1 normalises each primitive; the contracted function is then
  *    renormalised to <phi|phi> = 1, using this file's own Cartesian overlap integrals.
  *  - V carries no minus sign.  Functions are ordered shell by shell, m = -l..l.
+ *  - The same file holds the overlap (Eq. 10), the field integrals, and the two- and four-centre
+ *    electron-repulsion integrals (Eqs. 13-15), each by the same Cartesian route.
  *
  * The scalar type is `real`: double by default, long double when compiled with
  * -DORACLE_LONG_DOUBLE (80-bit on x86-64, IEEE binary128 on aarch64).  All public entry
@@ -485,6 +487,129 @@ static void coulomb2c_block(const shell_t* a, const shell_t* b, const real* ca, 
   free(Ea);
 }
 
+/* Four-centre electron-repulsion block: out[((ma nb + mb) nc + mc) nd + md] =
+ *   (a, ma b, mb | c, mc d, md) = int int phi_a(r1) phi_b(r1) phi_c(r2) phi_d(r2) / |r1 - r2| d3r1 d3r2,
+ * the two-electron Coulomb integral whose SHGO form Eqs. 13-15 derive.  McMurchie-Davidson: per primitive
+ * quartet, with p = alpha + beta, q = gamma + delta and the Hermite coefficients E^{ab} about P and E^{cd}
+ * about Q,
+ *   2 pi^{5/2} / (p q sqrt(p + q)) sum_{tuv} E^{ab}_{tuv} sum_{t'u'v'} (-1)^{t'+u'+v'} E^{cd}_{t'u'v'}
+ *       R^0_{t+t', u+u', v+v'}(pq / (p + q), P - Q),
+ * done as two passes: the ket sum for every bra Hermite index first, then the bra sum. */
+static void eri_block(const shell_t* a, const shell_t* b, const shell_t* c, const shell_t* dd, const real* ca,
+                      const real* cb, const real* cc, const real* cd, real* out) {
+  const int la = a->l, lb = b->l, lc = c->l, ld = dd->l;
+  const int L1 = la + lb, L2 = lc + ld, L = L1 + L2, d = L + 1;
+  const int nca = ncart(la), ncb = ncart(lb), ncc = ncart(lc), ncd = ncart(ld);
+  const int t1 = L1 + 1, t2 = L2 + 1;
+  const size_t eab = (size_t)(la + 1) * (lb + 1) * t1, ecd = (size_t)(lc + 1) * (ld + 1) * t2;
+  real* Eab = (real*)malloc(sizeof(real) * 3 * eab);
+  real* Ecd = (real*)malloc(sizeof(real) * 3 * ecd);
+  real* work = (real*)malloc(sizeof(real) * (size_t)d * d * d * d);
+  real* R = (real*)malloc(sizeof(real) * (size_t)d * d * d);
+  real* Wk = (real*)malloc(sizeof(real) * (size_t)t1 * t1 * t1);
+  const size_t nabcd = (size_t)nca * ncb * ncc * ncd;
+  real* G = (real*)calloc(nabcd, sizeof(real));
+  for (int i = 0; i < a->nprim; ++i)
+    for (int j = 0; j < b->nprim; ++j) {
+      const real al = a->alpha[i], be = b->alpha[j], p = al + be, mu = al * be / p;
+      real P[3];
+      for (int x = 0; x < 3; ++x) {
+        P[x] = (al * a->A[x] + be * b->A[x]) / p;
+        const real X = a->A[x] - b->A[x];
+        hermite_E(la, lb, p, P[x] - a->A[x], P[x] - b->A[x], RX(exp)(-mu * X * X), Eab + x * eab);
+      }
+      for (int k = 0; k < c->nprim; ++k)
+        for (int l = 0; l < dd->nprim; ++l) {
+          const real ga = c->alpha[k], de = dd->alpha[l], q = ga + de, nu = ga * de / q;
+          real Q[3];
+          for (int x = 0; x < 3; ++x) {
+            Q[x] = (ga * c->A[x] + de * dd->A[x]) / q;
+            const real X = c->A[x] - dd->A[x];
+            hermite_E(lc, ld, q, Q[x] - c->A[x], Q[x] - dd->A[x], RX(exp)(-nu * X * X), Ecd + x * ecd);
+          }
+          hermite_R(L, p * q / (p + q), P[0] - Q[0], P[1] - Q[1], P[2] - Q[2], work, R);
+          const real pre = a->coef[i] * b->coef[j] * c->coef[k] * dd->coef[l] * 2 * RX(pow)(RPI, (real)2.5) /
+                           (p * q * RX(sqrt)(p + q));
+          for (int kx = lc; kx >= 0; --kx)
+            for (int ky = lc - kx; ky >= 0; --ky) {
+              const int kz = lc - kx - ky, ic = cart_index(lc, kx, ky);
+              for (int lx = ld; lx >= 0; --lx)
+                for (int ly = ld - lx; ly >= 0; --ly) {
+                  const int lz = ld - lx - ly, id = cart_index(ld, lx, ly);
+                  const real* fx = Ecd + (kx * (ld + 1) + lx) * t2;
+                  const real* fy = Ecd + ecd + (ky * (ld + 1) + ly) * t2;
+                  const real* fz = Ecd + 2 * ecd + (kz * (ld + 1) + lz) * t2;
+                  /* ket pass: W[t][u][v] for every bra Hermite index with t + u + v <= L1 */
+                  for (int t = 0; t <= L1; ++t)
+                    for (int u = 0; u + t <= L1; ++u)
+                      for (int v = 0; v + u + t <= L1; ++v) {
+                        real w = 0;
+                        for (int tt = 0; tt <= kx + lx; ++tt)
+                          for (int uu = 0; uu <= ky + ly; ++uu)
+                            for (int vv = 0; vv <= kz + lz; ++vv) {
+                              const real f = fx[tt] * fy[uu] * fz[vv];
+                              const real sg = ((tt + uu + vv) & 1) ? -1 : 1;
+                              w += sg * f * R[((t + tt) * d + u + uu) * d + v + vv];
+                            }
+                        Wk[(t * t1 + u) * t1 + v] = w;
+                      }
+                  /* bra pass */
+                  for (int ix = la; ix >= 0; --ix)
+                    for (int iy = la - ix; iy >= 0; --iy) {
+                      const int iz = la - ix - iy, ia = cart_index(la, ix, iy);
+                      for (int jx = lb; jx >= 0; --jx)
+                        for (int jy = lb - jx; jy >= 0; --jy) {
+                          const int jz = lb - jx - jy, ib = cart_index(lb, jx, jy);
+                          const real* ex = Eab + (ix * (lb + 1) + jx) * t1;
+                          const real* ey = Eab + eab + (iy * (lb + 1) + jy) * t1;
+                          const real* ez = Eab + 2 * eab + (iz * (lb + 1) + jz) * t1;
+                          real s = 0;
+                          for (int t = 0; t <= ix + jx; ++t)
+                            for (int u = 0; u <= iy + jy; ++u)
+                              for (int v = 0; v <= iz + jz; ++v) s += ex[t] * ey[u] * ez[v] * Wk[(t * t1 + u) * t1 + v];
+                          G[(((size_t)ia * ncb + ib) * ncc + ic) * ncd + id] += pre * s;
+                        }
+                    }
+                }
+            }
+        }
+    }
+  /* Cartesian -> real solid harmonics, one index at a time */
+  const int na = 2 * la + 1, nb = 2 * lb + 1, nc = 2 * lc + 1, nd = 2 * ld + 1;
+  real* T1 = (real*)calloc((size_t)na * ncb * ncc * ncd, sizeof(real));
+  real* T2 = (real*)calloc((size_t)na * nb * ncc * ncd, sizeof(real));
+  real* T3 = (real*)calloc((size_t)na * nb * nc * ncd, sizeof(real));
+  for (int ma = 0; ma < na; ++ma)
+    for (int ia = 0; ia < nca; ++ia)
+      for (size_t r = 0; r < (size_t)ncb * ncc * ncd; ++r)
+        T1[(size_t)ma * ncb * ncc * ncd + r] += ca[ma * nca + ia] * G[(size_t)ia * ncb * ncc * ncd + r];
+  for (int ma = 0; ma < na; ++ma)
+    for (int mb = 0; mb < nb; ++mb)
+      for (int ib = 0; ib < ncb; ++ib)
+        for (size_t r = 0; r < (size_t)ncc * ncd; ++r)
+          T2[((size_t)ma * nb + mb) * ncc * ncd + r] += cb[mb * ncb + ib] * T1[((size_t)ma * ncb + ib) * ncc * ncd + r];
+  for (size_t ab = 0; ab < (size_t)na * nb; ++ab)
+    for (int mc = 0; mc < nc; ++mc)
+      for (int ic = 0; ic < ncc; ++ic)
+        for (int id = 0; id < ncd; ++id)
+          T3[(ab * nc + mc) * ncd + id] += cc[mc * ncc + ic] * T2[(ab * ncc + ic) * ncd + id];
+  for (size_t abc = 0; abc < (size_t)na * nb * nc; ++abc)
+    for (int md = 0; md < nd; ++md) {
+      real s = 0;
+      for (int id = 0; id < ncd; ++id) s += cd[md * ncd + id] * T3[abc * ncd + id];
+      out[abc * nd + md] = s;
+    }
+  free(T3);
+  free(T2);
+  free(T1);
+  free(G);
+  free(Wk);
+  free(R);
+  free(work);
+  free(Ecd);
+  free(Eab);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Public entry points.                                                                       */
 /* ------------------------------------------------------------------------------------------ */
@@ -573,6 +698,69 @@ int oracle_overlap(int n_shells, const int* l, const int* nprim, const double* e
 int oracle_coulomb_2c(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
                       const double* xyz, double* out, int n_threads) {
   return one_electron(OP_COULOMB2C, n_shells, l, nprim, exps, coefs, xyz, 0, NULL, NULL, out, n_threads, -1);
+}
+
+/* Four-centre electron-repulsion integrals (ab|cd) over the same basis (Eqs. 13-15), written to out
+ * (nbf^4 doubles, row-major: out[((i nbf + j) nbf + k) nbf + l] = (ij|kl)).  Each shell quartet with
+ * pair index (a, b) >= (c, d), a >= b and c >= d is computed once and written to its eight
+ * permutations (the integrals of real orbitals share one value).  Returns 0, or -1 on bad input. */
+int oracle_eri(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
+               const double* xyz, double* out, int n_threads) {
+  if (n_shells < 0) return -1;
+  shell_t* sh = (shell_t*)calloc((size_t)(n_shells > 0 ? n_shells : 1), sizeof(shell_t));
+  real* cart[ORACLE_LMAX + 1];
+  for (int ll = 0; ll <= ORACLE_LMAX; ++ll) {
+    cart[ll] = (real*)malloc(sizeof(real) * (size_t)(2 * ll + 1) * ncart(ll));
+    solid_harmonic_cart(ll, cart[ll]);
+  }
+  const int rc = setup_shells(n_shells, l, nprim, exps, coefs, xyz, sh, cart);
+  long* off = (long*)malloc(sizeof(long) * (size_t)(n_shells + 1));
+  off[0] = 0;
+  for (int s = 0; s < n_shells; ++s) off[s + 1] = off[s] + (rc == 0 ? 2 * sh[s].l + 1 : 0);
+  const long n = off[n_shells];
+  if (rc == 0) {
+    const long npairs = (long)n_shells * (n_shells + 1) / 2;
+    long* pa = (long*)malloc(sizeof(long) * (size_t)(npairs > 0 ? npairs : 1));
+    long* pb = (long*)malloc(sizeof(long) * (size_t)(npairs > 0 ? npairs : 1));
+    for (long a = 0, q = 0; a < n_shells; ++a)
+      for (long b = 0; b <= a; ++b, ++q) {
+        pa[q] = a;
+        pb[q] = b;
+      }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (long q1 = 0; q1 < npairs; ++q1)
+      for (long q2 = 0; q2 <= q1; ++q2) {
+        const long A = pa[q1], B = pb[q1], C = pa[q2], D = pb[q2];
+        const int na = 2 * sh[A].l + 1, nb = 2 * sh[B].l + 1, nc = 2 * sh[C].l + 1, nd = 2 * sh[D].l + 1;
+        real* blk = (real*)malloc(sizeof(real) * (size_t)na * nb * nc * nd);
+        eri_block(&sh[A], &sh[B], &sh[C], &sh[D], cart[sh[A].l], cart[sh[B].l], cart[sh[C].l], cart[sh[D].l], blk);
+        for (int i = 0; i < na; ++i)
+          for (int j = 0; j < nb; ++j)
+            for (int k = 0; k < nc; ++k)
+              for (int m = 0; m < nd; ++m) {
+                const double v = (double)blk[((i * nb + j) * nc + k) * nd + m];
+                const long I = off[A] + i, J = off[B] + j, K = off[C] + k, M = off[D] + m;
+                out[((I * n + J) * n + K) * n + M] = v;
+                out[((J * n + I) * n + K) * n + M] = v;
+                out[((I * n + J) * n + M) * n + K] = v;
+                out[((J * n + I) * n + M) * n + K] = v;
+                out[((K * n + M) * n + I) * n + J] = v;
+                out[((M * n + K) * n + I) * n + J] = v;
+                out[((K * n + M) * n + J) * n + I] = v;
+                out[((M * n + K) * n + J) * n + I] = v;
+              }
+        free(blk);
+      }
+    free(pb);
+    free(pa);
+  }
+  free(off);
+  for (int ll = 0; ll <= ORACLE_LMAX; ++ll) free(cart[ll]);
+  free(sh);
+  return rc;
 }
 
 /* Primitive normalisation N(l, alpha) of Eq. 1, as used above. */
