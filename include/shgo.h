@@ -222,6 +222,21 @@ shgo_status shgo_overlap(const shgo_basis* basis, double* out, void* stream);
  * `stream`.  Errors: SHGO_ERR_INVALID_ARG (NULL basis or out), SHGO_ERR_CUDA. */
 shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream);
 
+/* Four-centre electron-repulsion integrals (ab|cd) = int int phi_a(r1) phi_b(r1) phi_c(r2) phi_d(r2) /
+ * |r1 - r2| (Eqs. 13-15) of a single basis (not a batch) whose shells all have l <= 4.  Each pair is
+ * translated to its product centre (Eq. 7) and its harmonics coupled there (Gaunt coefficients); the
+ * r^{2k} factors of the coupled terms become powers of the Laplacian, so with Eq. 3 both pairs are
+ * harmonic differential operators applied to the s-s integral of the two product Gaussians, which the
+ * product rule and Hobson's theorem evaluate as sum_{L,M} G 2^L S_LM(P - Q) times Boys values F_N(rho
+ * |P - Q|^2), rho = pq/(p + q).  FP64 whatever the basis's precision option.  out: device array of
+ * nbf^4 doubles, row-major, out[((i nbf + j) nbf + k) nbf + l] = (ij|kl), fully overwritten (every
+ * unique quartet once, written to its eight permutations).  A per-call device buffer of
+ * sum over primitive pairs of (2la+1)(2lb+1) C(la+lb+3, 3) doubles is taken from the device's default
+ * stream-ordered pool and returned on `stream`.  Asynchronous on `stream`.  Errors: SHGO_ERR_INVALID_ARG
+ * (NULL basis or out, a batch, nbf > 40000), SHGO_ERR_UNSUPPORTED_L (a shell with l > 4), SHGO_ERR_OOM,
+ * SHGO_ERR_CUDA. */
+shgo_status shgo_eri(const shgo_basis* basis, double* out, void* stream);
+
 /* Per (la, lb) class (measurement): number of classes of a basis (-1 for NULL); for class c
  * (0 <= c < nclasses, in the library's launch order) its la >= lb in la_lb[2] and, for n_centers
  * nuclei, stats[4] = shell-triples, integrals (shell-triples x (2la+1)(2lb+1)), algorithmic flops of

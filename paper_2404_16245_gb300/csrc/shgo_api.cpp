@@ -719,6 +719,25 @@ shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream) 
   return SHGO_OK;
 }
 
+shgo_status shgo_eri(const shgo_basis* basis, double* out, void* stream) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "electron-repulsion integrals take a single basis, not a batch");
+  if (basis->nbf > 40000) return fail(SHGO_ERR_INVALID_ARG, "nbf^4 output too large");
+  for (const ClassWork& w : basis->work)
+    if (w.la > kEriLmax) return fail(SHGO_ERR_UNSUPPORTED_L, "electron-repulsion integrals support l <= 4");
+  if (!out && basis->nbf > 0) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  std::string err;
+  const shgo_status st =
+      launch_eri(basis->d, *basis->tabs, tables_host(), basis->work, basis->nbf, out, (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+
 int64_t shgo_basis_nbf(const shgo_basis* basis) { return basis ? basis->nbf : -1; }
 int64_t shgo_basis_npairs(const shgo_basis* basis) { return basis ? basis->npairs : -1; }
 

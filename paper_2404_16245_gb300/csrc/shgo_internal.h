@@ -109,6 +109,9 @@ struct Tables {
   std::vector<GTerm> c2_terms;
   std::vector<int> c2_base;  // [n classes]
   std::vector<double> c2_a;
+  // Four-centre electron repulsion: r^{2k} S_LM(r) e^{-p r^2} = sum_{n<=k} eps_{k,n}(L) p^{-(k+n)}
+  // Laplacian^n [S_LM(r) e^{-p r^2}], with eps_{k,n}(L) at eri_eps[(L (kC2K + 1) + k)(kC2K + 1) + n].
+  std::vector<double> eri_eps;
 };
 constexpr int kC2K = kLamMax / 2;  // largest k of the two-centre radial factors
 const Tables& tables_host();
@@ -148,6 +151,8 @@ struct DeviceTables {
   int* c2_ptr = nullptr;
   GTerm* c2_terms = nullptr;
   double* c2_a = nullptr;
+  double* eri_eps = nullptr;  // Tables::eri_eps
+  int* c2_cbase = nullptr;    // Tables::c2_base (first c2_ptr entry of each class)
   float2* boys_ff = nullptr;  // boys as (hi, lo) FP32 pairs
   float2* exp_ff = nullptr;   // exp(-g/16) as (hi, lo) FP32 pairs
   float2* rnorm_ff = nullptr; // rnorm as (hi, lo) FP32 pairs
@@ -369,6 +374,15 @@ cudaError_t coupling_fp64_setup();
 shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
                              const std::vector<ClassWork>& work, const MolView& mv, double* out, cudaStream_t stream,
                              std::string* err);
+
+// Largest shell l of the four-centre electron-repulsion integrals (la + lb + lc + ld <= 16).
+constexpr int kEriLmax = 4;
+
+// Four-centre electron-repulsion integrals (ab|cd) of every quartet of pairs of `work` into out
+// (nbf^4, row-major, all eight permutations written).  Classes must have la <= kEriLmax.
+shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
+                       const std::vector<ClassWork>& work, int64_t nbf, double* out, cudaStream_t stream,
+                       std::string* err);
 
 // FP32-bulk coupling (shgo_coupling_f32.cu): the Lambda = lam instantiation, compensated (pair
 // arithmetic) or plain, on `grid` blocks of 64 threads; args.boys_ff and args.exp_ff must be set.

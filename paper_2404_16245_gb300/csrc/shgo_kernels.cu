@@ -715,6 +715,8 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.c2_ptr, t.c2_ptr);
   if (e == cudaSuccess) e = upload(&d.c2_terms, t.c2_terms);
   if (e == cudaSuccess) e = upload(&d.c2_a, t.c2_a);
+  if (e == cudaSuccess) e = upload(&d.eri_eps, t.eri_eps);
+  if (e == cudaSuccess) e = upload(&d.c2_cbase, t.c2_base);
   if (e == cudaSuccess) e = upload(&d.boys_ff, boys_table_pairs(t.boys));
   if (e == cudaSuccess) e = upload(&d.exp_ff, exp_table_pairs());
   if (e == cudaSuccess) e = upload(&d.rnorm_ff, pairs_of(t.rnorm));
@@ -1405,6 +1407,341 @@ shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, cons
         dt.c2_terms, dt.c2_a, mv, out);
   }
   return launch_error(err);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Four-centre electron-repulsion integrals (ab|cd) (Eqs. 13-15), in the SHGO form re-derived from
+// Eqs. 3 and 7-8 (the printed Eq. 15 carries the same-centre coupling defect of Eq. 12):
+//  1. Each pair is translated to its product centre (Eq. 7, real addition theorem) and its two
+//     harmonics at P coupled by the Gaunt coefficients:
+//       phi_a phi_b = c c' K_AB sum_{L,M,k} Y[L,M,k] r_P^{2k} S_LM(r_P) e^{-p r_P^2}.
+//  2. r^{2k} S_LM e^{-pr^2} = sum_n eps_{k,n}(L) p^{-(k+n)} Laplacian^n [S_LM e^{-pr^2}], and by Eq. 3
+//     S_LM(r_P) e^{-p r_P^2} = (2p)^{-L} S_LM(grad_P) e^{-p r_P^2}, so the pair is
+//       sum_{L,M,n} D[L,M,n] Laplacian_P^n S_LM(grad_P) e^{-p r_P^2}
+//     (k_eri_dist writes D per primitive pair and block entry (ma, mb)).
+//  3. For two such terms at P and Q, with R = P - Q and u = |R|^2, every operator acts on the s-s integral
+//     g(u) = 2 pi^{5/2} / (p q sqrt(p + q)) F_0(rho u), rho = pq/(p + q), as grad_P = grad_R, grad_Q = -grad_R:
+//       (-1)^{L2} Laplacian^{n1+n2} S_L1M1(grad) S_L2M2(grad) g
+//         = (-1)^{L2} sum_{L,M} G(L1M1, L2M2; LM) 2^L S_LM(R) sum_j a_{K,j}(L) u^j g^{(L+K+j)}(u),
+//     K = (L1 + L2 - L)/2 + n1 + n2 (product rule, Hobson's theorem and Laplacian_L of the two-centre
+//     kernel), g^{(N)}(u) = 2 pi^{5/2} / (p q sqrt(p + q)) (-rho)^N F_N(rho u).
+//  4. (ab|cd) = sum over primitive quartets of D_ab I D_cd^T (k_eri_quartet).
+// The entries (L, M, n) of a pair use the (L, M, k) layout of the coupling buffer for Lambda = la + lb.
+// ---------------------------------------------------------------------------------------------
+constexpr int kEriTile = 16;  // ket entries per tile of the interaction matrix
+
+__device__ __forceinline__ int lmk_first(int lam, int L) {
+  int off = 0;
+  for (int Lp = 0; Lp < L; ++Lp) off += (2 * Lp + 1) * (kmax_of(lam, Lp) + 1);
+  return off;
+}
+
+__device__ __forceinline__ int l_of_index(int h) {
+  int L = (int)sqrtf((float)h);
+  while (L * L > h) --L;
+  while ((L + 1) * (L + 1) <= h) ++L;
+  return L;
+}
+
+// One primitive pair per block iteration: D[(ma mb) nr + e], e over the (L, M, n) entries of
+// Lambda = la + lb, for the class's primitive pairs pp_base .. pp_base + npp (dist: the class block).
+__global__ void __launch_bounds__(128) k_eri_dist(int la, int lb, int64_t npp, int64_t pp_base,
+                                                  const int* __restrict__ pp_pair, const int* __restrict__ pp_ij,
+                                                  const int* __restrict__ pair_a, const int* __restrict__ pair_b,
+                                                  const double* __restrict__ shell_xyz,
+                                                  const int* __restrict__ shell_poff,
+                                                  const double* __restrict__ prim_exp,
+                                                  const double* __restrict__ prim_coef, const double* __restrict__ etab,
+                                                  const int* __restrict__ eoff, const int* __restrict__ gt_ptr,
+                                                  const GTerm* __restrict__ gt_terms, const double* __restrict__ eps,
+                                                  double* __restrict__ dist) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lam = la + lb, na = 2 * la + 1, nb = 2 * lb + 1, nr = n_r(lam), nh = n_harm(lam);
+  const int nha = n_harm(la), nhb = n_harm(lb), ws = w_stride(lb);
+  double* S = smem;             // [nha] S_lm(B - A)
+  double* EA = S + nha;         // [na][nha] translation of a to P
+  double* EB = EA + na * nha;   // [nb][nhb] translation of b to P
+  for (int64_t w = blockIdx.x; w < npp; w += gridDim.x) {
+    const int64_t pp = pp_base + w;
+    const int pr = pp_pair[pp], ij = pp_ij[pp];
+    const int a = pair_a[pr], b = pair_b[pr];
+    const int ia = shell_poff[a] + (ij >> 8), ib = shell_poff[b] + (ij & 255);
+    const double al = prim_exp[ia], be = prim_exp[ib], p = al + be, ip = 1.0 / p;
+    const double dx = shell_xyz[3 * b] - shell_xyz[3 * a], dy = shell_xyz[3 * b + 1] - shell_xyz[3 * a + 1],
+                 dz = shell_xyz[3 * b + 2] - shell_xyz[3 * a + 2];
+    __syncthreads();  // the previous primitive pair is done with S, EA, EB
+    solid_harmonics_columns(la, dx, dy, dz, S, tid, nth);
+    __syncthreads();
+    // S_la,ma(r - A) = sum_{l1 m1} EA[ma][l1 m1] S_l1m1(r - P): P - A = (beta/p)(B - A)
+    for (int e = tid; e < na * nha; e += nth) {
+      const int ma = e / nha - la, i1 = e - (ma + la) * nha, l1 = c_lof[i1], m1 = i1 - l1 * l1 - l1, lr = la - l1;
+      const double* t = etab + eoff[la] + translation_offset_dev(la, ma, l1, m1);
+      double v = 0.0, f = 1.0;
+      for (int nu = -lr; nu <= lr; ++nu) v = fma(t[nu + lr], S[lr * lr + lr + nu], v);
+      for (int k = 0; k < lr; ++k) f *= be * ip;
+      EA[e] = v * f;
+    }
+    // P - B = (alpha/p)(A - B) and S_l(A - B) = (-1)^l S_l(B - A)
+    for (int e = tid; e < nb * nhb; e += nth) {
+      const int mb = e / nhb - lb, i2 = e - (mb + lb) * nhb, l2 = c_lof[i2], m2 = i2 - l2 * l2 - l2, lr = lb - l2;
+      const double* t = etab + eoff[lb] + translation_offset_dev(lb, mb, l2, m2);
+      double v = 0.0, f = 1.0;
+      for (int nu = -lr; nu <= lr; ++nu) v = fma(t[nu + lr], S[lr * lr + lr + nu], v);
+      for (int k = 0; k < lr; ++k) f *= -al * ip;
+      EB[e] = v * f;
+    }
+    __syncthreads();
+    const double ab2 = dx * dx + dy * dy + dz * dz;
+    const double pref = prim_coef[ia] * prim_coef[ib] * exp(-al * be * ip * ab2);
+    double* out = dist + w * (int64_t)(na * nb) * nr;
+    // one (ma mb, L, M) per thread: Y[L,M,k] for every k by the Gaunt coupling, then the Laplacian form
+    for (int g = tid; g < na * nb * nh; g += nth) {
+      const int mamb = g / nh, h = g - mamb * nh, L = c_lof[h], M = h - L * L - L, km = kmax_of(lam, L);
+      const int ma = mamb / nb, mb = mamb - ma * nb;
+      const int e0 = lmk_first(lam, L) + (M + L) * (km + 1);
+      double Y[kC2K + 1];
+#pragma unroll
+      for (int k = 0; k <= kC2K; ++k) {
+        double y = 0.0;
+        if (k <= km)
+          for (int t = gt_ptr[e0 + k]; t < gt_ptr[e0 + k + 1]; ++t) {
+            const GTerm gtm = gt_terms[t];
+            const int i1 = gtm.ridx / ws, i2 = gtm.ridx - i1 * ws;
+            y = fma(gtm.coef * EA[ma * nha + i1], EB[mb * nhb + i2], y);
+          }
+        Y[k] = y;
+      }
+      double scale = pref;
+      for (int k = 0; k < L; ++k) scale *= 0.5 * ip;
+#pragma unroll
+      for (int n = 0; n <= kC2K; ++n) {
+        if (n > km) break;
+        const double* en = eps + (size_t)L * (kC2K + 1) * (kC2K + 1) + n;
+        double v = 0.0, pw = 1.0;
+        for (int k = 0; k < 2 * n; ++k) pw *= ip;  // p^{-(k+n)} at k = n
+#pragma unroll
+        for (int k = 0; k <= kC2K; ++k) {
+          if (k < n || k > km) continue;
+          v = fma(en[k * (kC2K + 1)] * pw, Y[k], v);
+          pw *= ip;
+        }
+        out[mamb * nr + e0 + n] = scale * v;
+      }
+    }
+  }
+}
+
+size_t eri_dist_smem(int la, int lb) {
+  return sizeof(double) * ((size_t)n_harm(la) + (2 * la + 1) * n_harm(la) + (2 * lb + 1) * n_harm(lb) + 8);
+}
+
+// One unique shell quartet (pair P1 of the bra class, P2 of the ket class; P1 >= P2 when the classes
+// are the same) per block iteration: (ab|cd) = sum over primitive quartets of D_ab I D_cd^T, with the
+// interaction matrix I built in tiles of kEriTile ket entries and contracted into X = sum_{ket} I D_cd^T
+// before the bra contraction; each element of the block is written to its eight permutations, so the
+// output has the permutational symmetry exactly.
+__global__ void __launch_bounds__(256) k_eri_quartet(
+    int la, int lb, int lc, int ld, int n1, int base1, int n2, int base2, int same, const int* __restrict__ pair_a,
+    const int* __restrict__ pair_b, const int64_t* __restrict__ pair_ppoff, int64_t pp_base1, int64_t pp_base2,
+    const double* __restrict__ shell_xyz, const int* __restrict__ shell_poff, const int* __restrict__ shell_nprim,
+    const int64_t* __restrict__ shell_foff, const double* __restrict__ prim_exp, const double* __restrict__ dist1,
+    const double* __restrict__ dist2, const double* __restrict__ boys_tab, const int* __restrict__ rmap1,
+    const int* __restrict__ rmap2, const int* __restrict__ rmapt, const int* __restrict__ c2_ptr,
+    const int* __restrict__ c2_cbase, const GTerm* __restrict__ c2_terms, const double* __restrict__ c2_a,
+    int64_t nbf, double* __restrict__ out) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2;
+  const int nr1 = n_r(lam1), nr2 = n_r(lam2), nrt = n_r(lt);
+  const int na = 2 * la + 1, nb = 2 * lb + 1, nc = 2 * lc + 1, nd = 2 * ld + 1, nab = na * nb, ncd = nc * nd;
+  double* S = smem;                       // [(lt + 1)^2] S_LM(P - Q)
+  double* F = S + n_harm(lt);             // [lt + 1] Boys values
+  double* Z = F + lt + 1;                 // [nrt] 2^L S_LM(R) sum_j a_{K,j}(L) u^j g^{(L+K+j)}(u)
+  double* It = Z + nrt;                   // [nr1][kEriTile] interaction tile
+  double* X = It + nr1 * kEriTile;        // [nr1][ncd] interaction contracted with the ket distributions
+  double* Acc = X + (size_t)nr1 * ncd;    // [nab][ncd] block
+  int* kap1 = (int*)(Acc + (size_t)nab * ncd);  // bra entries: h | n << 12 | L << 20
+  int* kap2 = kap1 + nr1;                        // ket entries
+  int* zoff = kap2 + nr2;                        // [lt + 1] first Z entry of each L
+  for (int e = tid; e < nr1; e += nth) {
+    const int r = rmap1[e], h = r & 0xfff;
+    kap1[e] = h | ((r >> 24) << 12) | (l_of_index(h) << 20);
+  }
+  for (int e = tid; e < nr2; e += nth) {
+    const int r = rmap2[e], h = r & 0xfff;
+    kap2[e] = h | ((r >> 24) << 12) | (l_of_index(h) << 20);
+  }
+  if (tid <= lt) zoff[tid] = lmk_first(lt, tid);
+  const int64_t nq = same ? (int64_t)n1 * (n1 + 1) / 2 : (int64_t)n1 * n2;
+  for (int64_t w = blockIdx.x; w < nq; w += gridDim.x) {
+    int q1, q2;
+    if (same) {
+      int64_t r = (int64_t)((sqrt(8.0 * (double)w + 1.0) - 1.0) * 0.5);
+      while (r * (r + 1) / 2 > w) --r;
+      while ((r + 1) * (r + 2) / 2 <= w) ++r;
+      q1 = (int)r;
+      q2 = (int)(w - r * (r + 1) / 2);
+    } else {
+      q1 = (int)(w / n2);
+      q2 = (int)(w - (int64_t)q1 * n2);
+    }
+    const int pr1 = base1 + q1, pr2 = base2 + q2;
+    const int a = pair_a[pr1], b = pair_b[pr1], c = pair_a[pr2], d = pair_b[pr2];
+    const int npa = shell_nprim[a], npb = shell_nprim[b], npc = shell_nprim[c], npd = shell_nprim[d];
+    __syncthreads();  // the previous quartet's block has been written
+    for (int x = tid; x < nab * ncd; x += nth) Acc[x] = 0.0;
+    for (int i1 = 0; i1 < npa * npb; ++i1) {
+      const int ia = shell_poff[a] + i1 / npb, ib = shell_poff[b] + i1 % npb;
+      const double al = prim_exp[ia], be = prim_exp[ib], p = al + be;
+      double P[3];
+      for (int x = 0; x < 3; ++x) P[x] = (al * shell_xyz[3 * a + x] + be * shell_xyz[3 * b + x]) / p;
+      const double* d1 = dist1 + (pair_ppoff[pr1] - pp_base1 + i1) * (int64_t)nab * nr1;
+      __syncthreads();  // X has been consumed by the previous bra primitive pair
+      for (int x = tid; x < nr1 * ncd; x += nth) X[x] = 0.0;
+      for (int i2 = 0; i2 < npc * npd; ++i2) {
+        const int ic = shell_poff[c] + i2 / npd, id = shell_poff[d] + i2 % npd;
+        const double ga = prim_exp[ic], de = prim_exp[id], q = ga + de;
+        double R[3];
+        for (int x = 0; x < 3; ++x) R[x] = P[x] - (ga * shell_xyz[3 * c + x] + de * shell_xyz[3 * d + x]) / q;
+        const double u = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+        const double rho = p * q / (p + q), mrho = -rho;
+        const double cpq = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 / (p * q * sqrt(p + q));
+        const double* d2 = dist2 + (pair_ppoff[pr2] - pp_base2 + i2) * (int64_t)ncd * nr2;
+        __syncthreads();  // S, F, Z and It are free
+        if (tid < 32)
+          solid_harmonics_columns(lt, R[0], R[1], R[2], S, tid, 32);
+        else if (tid == 32)
+          boys_eval(lt, rho * u, F, 1, boys_tab, c_boys);
+        __syncthreads();
+        for (int e = tid; e < nrt; e += nth) {
+          const int r = rmapt[e], h = r & 0xfff, K = r >> 24, L = l_of_index(h);
+          const double* aK = c2_a + ((size_t)L * (kC2K + 1) + K) * (kC2K + 1);
+          double mr = cpq, uj = 1.0, rad = 0.0;
+          for (int n = 0; n < L + K; ++n) mr *= mrho;
+          for (int j = 0; j <= K; ++j) {
+            rad = fma(aK[j] * uj, mr * F[L + K + j], rad);
+            uj *= u;
+            mr *= mrho;
+          }
+          Z[e] = ldexp(S[h] * rad, L);
+        }
+        __syncthreads();
+        for (int t0 = 0; t0 < nr2; t0 += kEriTile) {
+          const int tw = min(kEriTile, nr2 - t0);
+          for (int x = tid; x < nr1 * tw; x += nth) {
+            const int e1 = x / tw, jj = x - e1 * tw;
+            const int k1 = kap1[e1], k2 = kap2[t0 + jj];
+            const int h1 = k1 & 0xfff, n1e = (k1 >> 12) & 0xff, L1 = k1 >> 20;
+            const int h2 = k2 & 0xfff, n2e = (k2 >> 12) & 0xff, L2 = k2 >> 20;
+            const int M1 = h1 - L1 * L1 - L1, M2 = h2 - L2 * L2 - L2;
+            const int* lst = L1 >= L2 ? c2_ptr + c2_cbase[L1 * (L1 + 1) / 2 + L2] + (M1 + L1) * (2 * L2 + 1) + M2 + L2
+                                      : c2_ptr + c2_cbase[L2 * (L2 + 1) / 2 + L1] + (M2 + L2) * (2 * L1 + 1) + M1 + L1;
+            double v = 0.0;
+            for (int t = lst[0]; t < lst[1]; ++t) {
+              const GTerm g = c2_terms[t];
+              const int L = g.pad, K = (L1 + L2 - L) / 2 + n1e + n2e;
+              v = fma(g.coef, Z[zoff[L] + (g.ridx - L * L) * (kmax_of(lt, L) + 1) + K], v);
+            }
+            It[e1 * kEriTile + jj] = (L2 & 1) ? -v : v;
+          }
+          __syncthreads();
+          for (int x = tid; x < nr1 * ncd; x += nth) {
+            const int e1 = x / ncd, cd = x - e1 * ncd;
+            const double* dr = d2 + (int64_t)cd * nr2 + t0;
+            const double* ir = It + e1 * kEriTile;
+            double s = 0.0;
+            for (int jj = 0; jj < tw; ++jj) s = fma(ir[jj], dr[jj], s);
+            X[x] += s;
+          }
+          __syncthreads();
+        }
+      }
+      for (int x = tid; x < nab * ncd; x += nth) {
+        const int ab = x / ncd, cd = x - ab * ncd;
+        const double* dr = d1 + (int64_t)ab * nr1;
+        double s = 0.0;
+        for (int e1 = 0; e1 < nr1; ++e1) s = fma(dr[e1], X[e1 * ncd + cd], s);
+        Acc[x] += s;
+      }
+    }
+    __syncthreads();
+    const int64_t fa = shell_foff[a], fb = shell_foff[b], fc = shell_foff[c], fd = shell_foff[d];
+    for (int x = tid; x < nab * ncd; x += nth) {
+      const int ab = x / ncd, cd = x - ab * ncd, ma = ab / nb, mb = ab - ma * nb, mc = cd / nd, md = cd - mc * nd;
+      // one writer per permutation orbit: where a = b, c = d or the two pairs coincide the block holds
+      // several members of an orbit (computed with different rounding); the canonical one is written
+      if ((a == b && ma < mb) || (c == d && mc < md) || (pr1 == pr2 && ab < cd)) continue;
+      const int64_t I = fa + ma, J = fb + mb, K = fc + mc, M = fd + md;
+      const double v = Acc[x];
+      out[((I * nbf + J) * nbf + K) * nbf + M] = v;
+      out[((J * nbf + I) * nbf + K) * nbf + M] = v;
+      out[((I * nbf + J) * nbf + M) * nbf + K] = v;
+      out[((J * nbf + I) * nbf + M) * nbf + K] = v;
+      out[((K * nbf + M) * nbf + I) * nbf + J] = v;
+      out[((M * nbf + K) * nbf + I) * nbf + J] = v;
+      out[((K * nbf + M) * nbf + J) * nbf + I] = v;
+      out[((M * nbf + K) * nbf + J) * nbf + I] = v;
+    }
+  }
+}
+
+size_t eri_quartet_smem(int la, int lb, int lc, int ld) {
+  const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2, nr1 = n_r(lam1), nr2 = n_r(lam2);
+  const size_t nab = (size_t)(2 * la + 1) * (2 * lb + 1), ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
+  const size_t dbl = n_harm(lt) + lt + 1 + n_r(lt) + (size_t)nr1 * kEriTile + nr1 * ncd + nab * ncd;
+  const size_t ints = nr1 + nr2 + lt + 1;
+  return sizeof(double) * dbl + sizeof(int) * ints;
+}
+
+shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
+                       const std::vector<ClassWork>& work, int64_t nbf, double* out, cudaStream_t stream,
+                       std::string* err) {
+  const size_t nw = work.size();
+  std::vector<int64_t> doff(nw + 1, 0);
+  for (size_t c = 0; c < nw; ++c) {
+    const ClassWork& w = work[c];
+    doff[c + 1] = doff[c] + w.npp * (int64_t)(2 * w.la + 1) * (2 * w.lb + 1) * n_r(w.la + w.lb);
+  }
+  if (doff[nw] == 0) return SHGO_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static bool attr[64] = {};
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaFuncSetAttribute(k_eri_quartet, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr[dev] = true;
+  }
+  double* dist = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&dist, sizeof(double) * (size_t)doff[nw], stream);
+  if (e != cudaSuccess) {
+    *err = std::string("distribution buffer: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+  }
+  for (size_t c = 0; c < nw; ++c) {
+    const ClassWork& w = work[c];
+    if (w.npp == 0) continue;
+    const int cid = class_id(w.la, w.lb);
+    k_eri_dist<<<grid_cap(w.npp, 8), 128, eri_dist_smem(w.la, w.lb), stream>>>(
+        w.la, w.lb, w.npp, w.pp_base, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff,
+        db.prim_exp, db.prim_coef, dt.etab, dt.eoff, dt.gt_ptr + th.gt_base[cid], dt.gt_terms + th.gt_termbase[cid],
+        dt.eri_eps, dist + doff[c]);
+  }
+  for (size_t c1 = 0; c1 < nw; ++c1)
+    for (size_t c2 = 0; c2 <= c1; ++c2) {
+      const ClassWork &w1 = work[c1], &w2 = work[c2];
+      if (w1.npairs == 0 || w2.npairs == 0) continue;
+      const int64_t nq = c1 == c2 ? (int64_t)w1.npairs * (w1.npairs + 1) / 2 : (int64_t)w1.npairs * w2.npairs;
+      k_eri_quartet<<<grid_cap(nq, 4), 256, eri_quartet_smem(w1.la, w1.lb, w2.la, w2.lb), stream>>>(
+          w1.la, w1.lb, w2.la, w2.lb, w1.npairs, w1.pair_base, w2.npairs, w2.pair_base, c1 == c2 ? 1 : 0, db.pair_a,
+          db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base, db.shell_xyz, db.shell_poff, db.shell_nprim,
+          db.shell_foff, db.prim_exp, dist + doff[c1], dist + doff[c2], dt.boys,
+          dt.rmap + th.rmap_off[w1.la + w1.lb], dt.rmap + th.rmap_off[w2.la + w2.lb],
+          dt.rmap + th.rmap_off[w1.la + w1.lb + w2.la + w2.lb], dt.c2_ptr, dt.c2_cbase, dt.c2_terms, dt.c2_a, nbf,
+          out);
+    }
+  const shgo_status st = launch_error(err);
+  cudaFreeAsync(dist, stream);
+  return st;
 }
 
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,

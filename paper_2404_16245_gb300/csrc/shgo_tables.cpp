@@ -282,6 +282,23 @@ void build_tables(Tables& t) {
       cur.swap(nxt);
     }
   }
+  // eps_{k,n}(L): x^{k+1} S_L e^{-px} = [Delta + (8k + 4L + 6) p] (x^k S_L e^{-px}) / (4p^2)
+  //               - (4k^2 + (4L + 2) k) x^{k-1} S_L e^{-px} / (4p^2), x = r^2, from
+  // Delta (S_L f(x)) = S_L (4x f'' + (4L + 6) f'); the powers of p factor out as p^{-(k+n)}.
+  t.eri_eps.assign((size_t)(kLamMax + 1) * (kC2K + 1) * (kC2K + 1), 0.0);
+  for (int L = 0; L <= kLamMax; ++L) {
+    std::vector<std::vector<ld>> e(kC2K + 1, std::vector<ld>(kC2K + 1, 0.0L));
+    e[0][0] = 1.0L;
+    for (int k = 0; k < kC2K; ++k)
+      for (int n = 0; n <= k + 1; ++n) {
+        ld v = (ld)(8 * k + 4 * L + 6) * (n <= k ? e[k][n] : 0.0L);
+        if (n >= 1) v += e[k][n - 1];
+        if (k >= 1 && n <= k - 1) v -= (ld)(4 * k * k + (4 * L + 2) * k) * e[k - 1][n];
+        e[k + 1][n] = v / 4;
+      }
+    for (int k = 0; k <= kC2K; ++k)
+      for (int n = 0; n <= k; ++n) t.eri_eps[((size_t)L * (kC2K + 1) + k) * (kC2K + 1) + n] = (double)e[k][n];
+  }
   // Gaunt programs per class
   std::vector<std::vector<std::pair<int, double>>> terms;  // per (i1, i2) over all l <= kLmax
   const int nh = (kLmax + 1) * (kLmax + 1);

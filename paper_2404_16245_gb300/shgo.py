@@ -88,6 +88,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_overlap.restype = ctypes.c_int
     lib.shgo_coulomb_2c.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_coulomb_2c.restype = ctypes.c_int
+    lib.shgo_eri.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_eri.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -348,6 +350,24 @@ def coulomb_2c(basis, out=None, stream=None, device="cuda"):
     if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != shape:
         raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
     shgo_coulomb_2c(basis.handle, out.data_ptr(), stream)
+    return out
+
+
+def shgo_eri(basis, out_ptr, stream=None):
+    _check(_lib.shgo_eri(ctypes.c_void_p(basis), ctypes.c_void_p(int(out_ptr) or 0), _stream_handle(stream)))
+
+
+def eri(basis, out=None, stream=None, device="cuda"):
+    """Four-centre electron-repulsion integrals (ij|kl) of a basis (FP64 device tensor nbf^4)."""
+    import torch
+    if not isinstance(basis, Basis):
+        raise ValueError("eri takes a Basis, not a Batch")
+    shape = (basis.nbf,) * 4
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != shape:
+        raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
+    shgo_eri(basis.handle, out.data_ptr(), stream)
     return out
 
 
