@@ -777,6 +777,163 @@ def run_coulomb2c(args) -> int:
     return 0
 
 
+def _eri_pairs(basis):
+    """Shell pairs as the library forms them: (l, nprim) of the pair with la >= lb, one per unordered pair."""
+    ls, nps = [int(x) for x in basis["l"]], [int(x) for x in basis["nprim"]]
+    out = []
+    for la in range(9):
+        A = [s for s in range(len(ls)) if ls[s] == la]
+        for lb in range(la + 1):
+            B = [s for s in range(len(ls)) if ls[s] == lb]
+            for x, sa in enumerate(A):
+                for sb in (B[:x + 1] if la == lb else B):
+                    out.append((la, lb, nps[sa] * nps[sb]))
+    return out
+
+
+def eri_flops(basis) -> tuple[float, int]:
+    """Algorithmic FP64 flops (FMA = 2) of the quartet kernels of one shgo_eri call, and the unique shell
+    quartets.  Per primitive quartet: the radial factors Z (one FMA per Boys term of each (L, M, K) entry of
+    Lambda_t = la + lb + lc + ld), the interaction matrix I (one FMA per Gaunt term of every bra x ket entry)
+    and X += I D_cd^T (nr1 nr2 ncd FMAs); per bra primitive pair and ket pair D_ab X (nab ncd nr1 FMAs); the
+    reduction over bra primitive pairs (nab ncd adds each).  The distributions (once per primitive pair) are
+    not counted."""
+    from paper_2404_16245_gb300 import shgo
+
+    def n_r(lam):
+        return (lam + 1) * (lam + 2) * (lam + 3) // 6
+
+    gaunt_terms = {}
+
+    def nterms(L1, M1, L2, M2):
+        key = (L1, M1, L2, M2)
+        if key not in gaunt_terms:
+            n = 0
+            for L in range(abs(L1 - L2), L1 + L2 + 1, 2):
+                for M in {abs(M1) + abs(M2), -(abs(M1) + abs(M2)), abs(abs(M1) - abs(M2)), -abs(abs(M1) - abs(M2))}:
+                    if abs(M) <= L and abs(shgo.host_gaunt(L1, M1, L2, M2, L, M)) > 1e-15:
+                        n += 1
+            gaunt_terms[key] = n
+        return gaunt_terms[key]
+
+    iterms = {}
+
+    def i_terms(l1, l2):
+        if (l1, l2) not in iterms:
+            t = 0
+            for L1 in range(l1 + 1):
+                for L2 in range(l2 + 1):
+                    w = ((l1 - L1) // 2 + 1) * ((l2 - L2) // 2 + 1)
+                    t += w * sum(nterms(L1, M1, L2, M2) for M1 in range(-L1, L1 + 1) for M2 in range(-L2, L2 + 1))
+            iterms[(l1, l2)] = t
+        return iterms[(l1, l2)]
+
+    def z_terms(lt):
+        return sum((2 * L + 1) * sum(K + 1 for K in range((lt - L) // 2 + 1)) for L in range(lt + 1))
+
+    pairs = _eri_pairs(basis)
+    order = sorted(range(len(pairs)), key=lambda i: (pairs[i][0] * (pairs[i][0] + 1) // 2 + pairs[i][1]))
+    pairs = [pairs[i] for i in order]
+    flops, nq = 0.0, 0
+    for i, (la, lb, np1) in enumerate(pairs):
+        for (lc, ld, np2) in pairs[:i + 1]:
+            l1, l2 = la + lb, lc + ld
+            nab, ncd = (2 * la + 1) * (2 * lb + 1), (2 * lc + 1) * (2 * ld + 1)
+            per_pq = 2 * (z_terms(l1 + l2) + i_terms(l1, l2) + n_r(l1) * n_r(l2) * ncd)
+            flops += np1 * np2 * per_pq + np1 * 2 * nab * ncd * n_r(l1) + np1 * nab * ncd
+            nq += 1
+    return flops, nq
+
+
+def run_eri(args) -> int:
+    """Four-centre electron-repulsion integrals (ab|cd) of the plain FP64 basis (4 atoms in a 6 bohr cube,
+    l = 0, 1, 2 shells of 3 primitives on every atom: 12 shells, 36 functions, 78 shell pairs, 3081 unique
+    shell quartets): one step = the whole nbf^4 tensor.  Steps cycle over seeded replicas of that
+    distribution, all resident on the device; L2 is flushed between steps (outside the step events)."""
+    import torch
+
+    import oracle
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    R = 4
+    dicts = [W.config1(replica=r)[0] for r in range(R)]
+    bases = [shgo.Basis(b) for b in dicts]
+    n = bases[0].nbf
+    outs = [torch.empty((n, n, n, n), dtype=torch.float64, device="cuda") for _ in range(R)]
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")  # 256 MiB, larger than L2
+    for k in range(max(3, args.warmup)):
+        shgo.eri(bases[k % R], out=outs[k % R], stream=stream)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 200))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    for k, (e0, e1) in enumerate(evs):
+        flush.zero_()
+        e0.record(stream)
+        shgo.eri(bases[k % R], out=outs[k % R], stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+    flops, nq = eri_flops(dicts[0])
+    integrals = sum((2 * la + 1) * (2 * lb + 1) for la, lb, _ in _eri_pairs(dicts[0]))
+    clk = clocks.get("sm_max_mhz") or 2070.0
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = fp64_peak_tflops(clk)
+    # end to end through the public API: basis from host arrays, the tensor back to pinned host memory
+    host = torch.empty((n, n, n, n), dtype=torch.float64, pin_memory=True)
+    h2d = sum(np.asarray(dicts[0][k]).nbytes for k in ("l", "nprim", "exps", "coefs", "xyz"))
+    e2e_steps = 10
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        B = shgo.Basis(dicts[k % R])
+        shgo.eri(B, out=outs[k % R], stream=stream)
+        host.copy_(outs[k % R], non_blocking=True)
+        torch.cuda.synchronize()
+        B.close()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    # CPU oracle on the host cores, whole tensors of the same workload
+    cpu = None
+    if not args.no_cpu_baseline:
+        oracle.build()
+        cores = os.cpu_count() or 1
+        done, t0 = 0, time.perf_counter()
+        while True:
+            oracle.eri(dicts[done % R], threads=cores)
+            done += 1
+            if time.perf_counter() - t0 >= min(args.cpu_seconds, 10.0):
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": done * nq / el, "unit": "shell-quartets/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} whole tensors of the workload in {el:.1f} s"}
+    # launches: distributions once per class, then part + reduce per class pair (one rectangle each here)
+    ncls = len({(la, lb) for la, lb, _ in _eri_pairs(dicts[0])})
+    launches = (ncls + 2 * ncls * (ncls + 1) // 2) * steps
+    line = {"metric": "four-centre ERI unique shell quartets/s", "value": nq / (ms / 1e3), "unit": "shell-quartets/s",
+            "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"(ab|cd) of the plain FP64 basis: 4 atoms, l = 0..2 x 3 primitives, {n} functions",
+                       "unique_shell_quartets": nq, "unique_integrals_per_s": integrals * (integrals + 1) / 2 / (ms / 1e3),
+                       "l2": "flushed between steps (256 MiB write, outside step events)"},
+            "roofline": {"bound": "alu", "kernel": "k_eri_part", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "algorithmic flops of k_eri_part + k_eri_reduce (model in bench.py) over the whole call",
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": nq / e2e_s, "unit": "shell-quartets/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(n ** 4 * 8), "steps": e2e_steps,
+                    "note": "basis upload + eri + D2H of the nbf^4 tensor, wall clock"},
+            "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    for B in bases:
+        B.close()
+    return 0
+
+
 def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
     """Small fixed case for ncu captures: one warm and one measured V of the benchmark workload
     (highl) or of the first molecule of the batched workload (batched)."""
@@ -806,7 +963,7 @@ def main():
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
     ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
-    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c"],
+    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
     ap.add_argument("--points", type=int, default=100000, help="points of the potential workload")
@@ -847,6 +1004,8 @@ def main():
         return run_esp(args)
     if args.workload == "coulomb2c":
         return run_coulomb2c(args)
+    if args.workload == "eri":
+        return run_eri(args)
     ws, rank, local = _dist()
     if ws > 1:
         import torch

@@ -1425,11 +1425,9 @@ shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, cons
 //         = (-1)^{L2} sum_{L,M} G(L1M1, L2M2; LM) 2^L S_LM(R) sum_j a_{K,j}(L) u^j g^{(L+K+j)}(u),
 //     K = (L1 + L2 - L)/2 + n1 + n2 (product rule, Hobson's theorem and Laplacian_L of the two-centre
 //     kernel), g^{(N)}(u) = 2 pi^{5/2} / (p q sqrt(p + q)) (-rho)^N F_N(rho u).
-//  4. (ab|cd) = sum over primitive quartets of D_ab I D_cd^T (k_eri_quartet).
+//  4. (ab|cd) = sum over primitive quartets of D_ab I D_cd^T (k_eri_part, summed by k_eri_reduce).
 // The entries (L, M, n) of a pair use the (L, M, k) layout of the coupling buffer for Lambda = la + lb.
 // ---------------------------------------------------------------------------------------------
-constexpr int kEriTile = 16;  // ket entries per tile of the interaction matrix
-
 __device__ __forceinline__ int lmk_first(int lam, int L) {
   int off = 0;
   for (int Lp = 0; Lp < L; ++Lp) off += (2 * Lp + 1) * (kmax_of(lam, Lp) + 1);
@@ -1536,34 +1534,41 @@ size_t eri_dist_smem(int la, int lb) {
   return sizeof(double) * ((size_t)n_harm(la) + (2 * la + 1) * n_harm(la) + (2 * lb + 1) * n_harm(lb) + 8);
 }
 
-// One unique shell quartet (pair P1 of the bra class, P2 of the ket class; P1 >= P2 when the classes
-// are the same) per block iteration: (ab|cd) = sum over primitive quartets of D_ab I D_cd^T, with the
-// interaction matrix I built in tiles of kEriTile ket entries and contracted into X = sum_{ket} I D_cd^T
-// before the bra contraction; each element of the block is written to its eight permutations, so the
-// output has the permutational symmetry exactly.
-__global__ void __launch_bounds__(256) k_eri_quartet(
-    int la, int lb, int lc, int ld, int n1, int base1, int n2, int base2, int same, const int* __restrict__ pair_a,
+// Work item of k_eri_part: one bra primitive pair pp1 (of the bra class, in [pp_lo, pp_hi)) and one ket
+// shell pair q2 (of the ket class, in [q2_lo, q2_hi)); for the same class only q2 <= q1 is needed.  The item
+// computes X = sum over the ket primitive pairs of I D_cd^T (I: the interaction matrix of step 3, built in
+// tiles of kEriPartTile columns over (ket primitive pair, ket entry)) and writes its share of the block,
+// D_ab X, to part[((pp1 - pp_lo) n2w + q2 - q2_lo) nab ncd].  Ket primitive pairs are taken `chunk` at a time:
+// one warp per primitive pair for the solid harmonics S_LM(P - Q) and the Boys values, then the radial
+// factors Z of all of them, then the tiles.
+constexpr int kEriPartTile = 32;
+
+__global__ void __launch_bounds__(256) k_eri_part(
+    int la, int lb, int lc, int ld, int64_t pp_lo, int64_t pp_hi, int base1, int q2_lo, int q2_hi, int same,
+    int chunk, const int* __restrict__ pp_pair, const int* __restrict__ pp_ij, const int* __restrict__ pair_a,
     const int* __restrict__ pair_b, const int64_t* __restrict__ pair_ppoff, int64_t pp_base1, int64_t pp_base2,
-    const double* __restrict__ shell_xyz, const int* __restrict__ shell_poff, const int* __restrict__ shell_nprim,
-    const int64_t* __restrict__ shell_foff, const double* __restrict__ prim_exp, const double* __restrict__ dist1,
+    int base2, const double* __restrict__ shell_xyz, const int* __restrict__ shell_poff,
+    const int* __restrict__ shell_nprim, const double* __restrict__ prim_exp, const double* __restrict__ dist1,
     const double* __restrict__ dist2, const double* __restrict__ boys_tab, const int* __restrict__ rmap1,
     const int* __restrict__ rmap2, const int* __restrict__ rmapt, const int* __restrict__ c2_ptr,
     const int* __restrict__ c2_cbase, const GTerm* __restrict__ c2_terms, const double* __restrict__ c2_a,
-    int64_t nbf, double* __restrict__ out) {
+    double* __restrict__ part) {
   extern __shared__ double smem[];
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2;
-  const int nr1 = n_r(lam1), nr2 = n_r(lam2), nrt = n_r(lt);
-  const int na = 2 * la + 1, nb = 2 * lb + 1, nc = 2 * lc + 1, nd = 2 * ld + 1, nab = na * nb, ncd = nc * nd;
-  double* S = smem;                       // [(lt + 1)^2] S_LM(P - Q)
-  double* F = S + n_harm(lt);             // [lt + 1] Boys values
-  double* Z = F + lt + 1;                 // [nrt] 2^L S_LM(R) sum_j a_{K,j}(L) u^j g^{(L+K+j)}(u)
-  double* It = Z + nrt;                   // [nr1][kEriTile] interaction tile
-  double* X = It + nr1 * kEriTile;        // [nr1][ncd] interaction contracted with the ket distributions
-  double* Acc = X + (size_t)nr1 * ncd;    // [nab][ncd] block
-  int* kap1 = (int*)(Acc + (size_t)nab * ncd);  // bra entries: h | n << 12 | L << 20
-  int* kap2 = kap1 + nr1;                        // ket entries
-  int* zoff = kap2 + nr2;                        // [lt + 1] first Z entry of each L
+  const int nr1 = n_r(lam1), nr2 = n_r(lam2), nrt = n_r(lt), nht = n_harm(lt);
+  const int nab = (2 * la + 1) * (2 * lb + 1), ncd = (2 * lc + 1) * (2 * ld + 1);
+  const int n2w = q2_hi - q2_lo;
+  double* X = smem;                            // [nr1][ncd]
+  double* It = X + (size_t)nr1 * ncd;          // [nr1][kEriPartTile]
+  double* Dt = It + nr1 * kEriPartTile;        // [ncd][kEriPartTile] ket distributions of the tile
+  double* S = Dt + ncd * kEriPartTile;         // [chunk][nht]
+  double* F = S + (size_t)chunk * nht;         // [chunk][lt + 1]
+  double* Z = F + (size_t)chunk * (lt + 1);    // [chunk][nrt]
+  double* G = Z + (size_t)chunk * nrt;         // [chunk][4]: u, -rho, 2 pi^{5/2} / (p q sqrt(p + q))
+  int* kap1 = (int*)(G + 4 * chunk);           // bra entries: h | n << 12 | L << 20
+  int* kap2 = kap1 + nr1;                      // ket entries
+  int* zoff = kap2 + nr2;                      // [lt + 1]
   for (int e = tid; e < nr1; e += nth) {
     const int r = rmap1[e], h = r & 0xfff;
     kap1[e] = h | ((r >> 24) << 12) | (l_of_index(h) << 20);
@@ -1573,107 +1578,158 @@ __global__ void __launch_bounds__(256) k_eri_quartet(
     kap2[e] = h | ((r >> 24) << 12) | (l_of_index(h) << 20);
   }
   if (tid <= lt) zoff[tid] = lmk_first(lt, tid);
-  const int64_t nq = same ? (int64_t)n1 * (n1 + 1) / 2 : (int64_t)n1 * n2;
-  for (int64_t w = blockIdx.x; w < nq; w += gridDim.x) {
-    int q1, q2;
-    if (same) {
-      int64_t r = (int64_t)((sqrt(8.0 * (double)w + 1.0) - 1.0) * 0.5);
-      while (r * (r + 1) / 2 > w) --r;
-      while ((r + 1) * (r + 2) / 2 <= w) ++r;
-      q1 = (int)r;
-      q2 = (int)(w - r * (r + 1) / 2);
-    } else {
-      q1 = (int)(w / n2);
-      q2 = (int)(w - (int64_t)q1 * n2);
-    }
-    const int pr1 = base1 + q1, pr2 = base2 + q2;
-    const int a = pair_a[pr1], b = pair_b[pr1], c = pair_a[pr2], d = pair_b[pr2];
-    const int npa = shell_nprim[a], npb = shell_nprim[b], npc = shell_nprim[c], npd = shell_nprim[d];
-    __syncthreads();  // the previous quartet's block has been written
-    for (int x = tid; x < nab * ncd; x += nth) Acc[x] = 0.0;
-    for (int i1 = 0; i1 < npa * npb; ++i1) {
-      const int ia = shell_poff[a] + i1 / npb, ib = shell_poff[b] + i1 % npb;
-      const double al = prim_exp[ia], be = prim_exp[ib], p = al + be;
-      double P[3];
-      for (int x = 0; x < 3; ++x) P[x] = (al * shell_xyz[3 * a + x] + be * shell_xyz[3 * b + x]) / p;
-      const double* d1 = dist1 + (pair_ppoff[pr1] - pp_base1 + i1) * (int64_t)nab * nr1;
-      __syncthreads();  // X has been consumed by the previous bra primitive pair
-      for (int x = tid; x < nr1 * ncd; x += nth) X[x] = 0.0;
-      for (int i2 = 0; i2 < npc * npd; ++i2) {
-        const int ic = shell_poff[c] + i2 / npd, id = shell_poff[d] + i2 % npd;
+  const int64_t nitems = (pp_hi - pp_lo) * n2w;
+  const int nxr = (nr1 + 1) >> 1, nxc = (ncd + 1) >> 1;  // 2 x 2 register tiles of X
+  for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int64_t pp1 = pp_lo + it / n2w;
+    const int q2 = q2_lo + (int)(it - (it / n2w) * n2w);
+    const int pr1 = pp_pair[pp1];
+    if (same && q2 > pr1 - base1) continue;  // uniform over the block
+    const int ij = pp_ij[pp1], a = pair_a[pr1], b = pair_b[pr1];
+    const double al = prim_exp[shell_poff[a] + (ij >> 8)], be = prim_exp[shell_poff[b] + (ij & 255)], p = al + be;
+    double P[3];
+    for (int x = 0; x < 3; ++x) P[x] = (al * shell_xyz[3 * a + x] + be * shell_xyz[3 * b + x]) / p;
+    const int pr2 = base2 + q2, c = pair_a[pr2], d = pair_b[pr2], npd = shell_nprim[d];
+    const int npp2 = shell_nprim[c] * npd;
+    const double* d2p = dist2 + (pair_ppoff[pr2] - pp_base2) * (int64_t)ncd * nr2;
+    __syncthreads();  // the previous item is done with X and the tables
+    for (int x = tid; x < nr1 * ncd; x += nth) X[x] = 0.0;
+    for (int k0 = 0; k0 < npp2; k0 += chunk) {
+      const int nck = min(chunk, npp2 - k0);
+      __syncthreads();  // S, F, Z, G of the previous chunk are consumed
+      for (int w = warp; w < nck; w += nwarp) {
+        const int i2 = k0 + w, ic = shell_poff[c] + i2 / npd, id = shell_poff[d] + i2 % npd;
         const double ga = prim_exp[ic], de = prim_exp[id], q = ga + de;
         double R[3];
         for (int x = 0; x < 3; ++x) R[x] = P[x] - (ga * shell_xyz[3 * c + x] + de * shell_xyz[3 * d + x]) / q;
-        const double u = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
-        const double rho = p * q / (p + q), mrho = -rho;
-        const double cpq = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 / (p * q * sqrt(p + q));
-        const double* d2 = dist2 + (pair_ppoff[pr2] - pp_base2 + i2) * (int64_t)ncd * nr2;
-        __syncthreads();  // S, F, Z and It are free
-        if (tid < 32)
-          solid_harmonics_columns(lt, R[0], R[1], R[2], S, tid, 32);
-        else if (tid == 32)
-          boys_eval(lt, rho * u, F, 1, boys_tab, c_boys);
-        __syncthreads();
-        for (int e = tid; e < nrt; e += nth) {
-          const int r = rmapt[e], h = r & 0xfff, K = r >> 24, L = l_of_index(h);
-          const double* aK = c2_a + ((size_t)L * (kC2K + 1) + K) * (kC2K + 1);
-          double mr = cpq, uj = 1.0, rad = 0.0;
-          for (int n = 0; n < L + K; ++n) mr *= mrho;
-          for (int j = 0; j <= K; ++j) {
-            rad = fma(aK[j] * uj, mr * F[L + K + j], rad);
-            uj *= u;
-            mr *= mrho;
-          }
-          Z[e] = ldexp(S[h] * rad, L);
-        }
-        __syncthreads();
-        for (int t0 = 0; t0 < nr2; t0 += kEriTile) {
-          const int tw = min(kEriTile, nr2 - t0);
-          for (int x = tid; x < nr1 * tw; x += nth) {
-            const int e1 = x / tw, jj = x - e1 * tw;
-            const int k1 = kap1[e1], k2 = kap2[t0 + jj];
-            const int h1 = k1 & 0xfff, n1e = (k1 >> 12) & 0xff, L1 = k1 >> 20;
-            const int h2 = k2 & 0xfff, n2e = (k2 >> 12) & 0xff, L2 = k2 >> 20;
-            const int M1 = h1 - L1 * L1 - L1, M2 = h2 - L2 * L2 - L2;
-            const int* lst = L1 >= L2 ? c2_ptr + c2_cbase[L1 * (L1 + 1) / 2 + L2] + (M1 + L1) * (2 * L2 + 1) + M2 + L2
-                                      : c2_ptr + c2_cbase[L2 * (L2 + 1) / 2 + L1] + (M2 + L2) * (2 * L1 + 1) + M1 + L1;
-            double v = 0.0;
-            for (int t = lst[0]; t < lst[1]; ++t) {
-              const GTerm g = c2_terms[t];
-              const int L = g.pad, K = (L1 + L2 - L) / 2 + n1e + n2e;
-              v = fma(g.coef, Z[zoff[L] + (g.ridx - L * L) * (kmax_of(lt, L) + 1) + K], v);
-            }
-            It[e1 * kEriTile + jj] = (L2 & 1) ? -v : v;
-          }
-          __syncthreads();
-          for (int x = tid; x < nr1 * ncd; x += nth) {
-            const int e1 = x / ncd, cd = x - e1 * ncd;
-            const double* dr = d2 + (int64_t)cd * nr2 + t0;
-            const double* ir = It + e1 * kEriTile;
-            double s = 0.0;
-            for (int jj = 0; jj < tw; ++jj) s = fma(ir[jj], dr[jj], s);
-            X[x] += s;
-          }
-          __syncthreads();
+        const double u = R[0] * R[0] + R[1] * R[1] + R[2] * R[2], rho = p * q / (p + q);
+        solid_harmonics_columns(lt, R[0], R[1], R[2], S + (size_t)w * nht, lane, 32);
+        if (lane == 0) {
+          boys_eval(lt, rho * u, F + (size_t)w * (lt + 1), 1, boys_tab, c_boys);
+          G[4 * w] = u;
+          G[4 * w + 1] = -rho;
+          G[4 * w + 2] = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 / (p * q * sqrt(p + q));
         }
       }
-      for (int x = tid; x < nab * ncd; x += nth) {
-        const int ab = x / ncd, cd = x - ab * ncd;
-        const double* dr = d1 + (int64_t)ab * nr1;
-        double s = 0.0;
-        for (int e1 = 0; e1 < nr1; ++e1) s = fma(dr[e1], X[e1 * ncd + cd], s);
-        Acc[x] += s;
+      __syncthreads();
+      for (int x = tid; x < nck * nrt; x += nth) {
+        const int w = x / nrt, e = x - w * nrt;
+        const int r = rmapt[e], h = r & 0xfff, K = r >> 24, L = l_of_index(h);
+        const double u = G[4 * w], mrho = G[4 * w + 1];
+        const double* Fw = F + (size_t)w * (lt + 1);
+        const double* aK = c2_a + ((size_t)L * (kC2K + 1) + K) * (kC2K + 1);
+        double mr = G[4 * w + 2], uj = 1.0, rad = 0.0;
+        for (int n = 0; n < L + K; ++n) mr *= mrho;
+        for (int j = 0; j <= K; ++j) {
+          rad = fma(aK[j] * uj, mr * Fw[L + K + j], rad);
+          uj *= u;
+          mr *= mrho;
+        }
+        Z[x] = ldexp(S[(size_t)w * nht + h] * rad, L);
+      }
+      __syncthreads();
+      const int ncol = nck * nr2;  // columns (ket primitive pair, ket entry) of this chunk
+      for (int t0 = 0; t0 < ncol; t0 += kEriPartTile) {
+        const int tw = min(kEriPartTile, ncol - t0);
+        for (int x = tid; x < nr1 * tw; x += nth) {
+          const int e1 = x / tw, jj = x - e1 * tw, col = t0 + jj, w = col / nr2, e2 = col - w * nr2;
+          const int k1 = kap1[e1], k2 = kap2[e2];
+          const int h1 = k1 & 0xfff, n1e = (k1 >> 12) & 0xff, L1 = k1 >> 20;
+          const int h2 = k2 & 0xfff, n2e = (k2 >> 12) & 0xff, L2 = k2 >> 20;
+          const int M1 = h1 - L1 * L1 - L1, M2 = h2 - L2 * L2 - L2;
+          const int* lst = L1 >= L2 ? c2_ptr + c2_cbase[L1 * (L1 + 1) / 2 + L2] + (M1 + L1) * (2 * L2 + 1) + M2 + L2
+                                    : c2_ptr + c2_cbase[L2 * (L2 + 1) / 2 + L1] + (M2 + L2) * (2 * L1 + 1) + M1 + L1;
+          const double* Zw = Z + (size_t)w * nrt;
+          double v = 0.0;
+          for (int t = lst[0]; t < lst[1]; ++t) {
+            const GTerm g = c2_terms[t];
+            const int L = g.pad, K = (L1 + L2 - L) / 2 + n1e + n2e;
+            v = fma(g.coef, Zw[zoff[L] + (g.ridx - L * L) * (kmax_of(lt, L) + 1) + K], v);
+          }
+          It[e1 * kEriPartTile + jj] = (L2 & 1) ? -v : v;
+        }
+        for (int x = tid; x < ncd * tw; x += nth) {
+          const int cd = x / tw, jj = x - cd * tw, col = t0 + jj, w = col / nr2, e2 = col - w * nr2;
+          Dt[cd * kEriPartTile + jj] = d2p[((int64_t)(k0 + w) * ncd + cd) * nr2 + e2];
+        }
+        __syncthreads();
+        for (int x = tid; x < nxr * nxc; x += nth) {
+          const int r0 = 2 * (x / nxc), c0 = 2 * (x - (x / nxc) * nxc);
+          const bool r1ok = r0 + 1 < nr1, c1ok = c0 + 1 < ncd;
+          const double* i0 = It + r0 * kEriPartTile;
+          const double* i1 = It + (r1ok ? r0 + 1 : r0) * kEriPartTile;
+          const double* j0 = Dt + c0 * kEriPartTile;
+          const double* j1 = Dt + (c1ok ? c0 + 1 : c0) * kEriPartTile;
+          double s00 = 0.0, s01 = 0.0, s10 = 0.0, s11 = 0.0;
+          for (int jj = 0; jj < tw; ++jj) {
+            const double x0 = i0[jj], x1 = i1[jj], y0 = j0[jj], y1 = j1[jj];
+            s00 = fma(x0, y0, s00);
+            s01 = fma(x0, y1, s01);
+            s10 = fma(x1, y0, s10);
+            s11 = fma(x1, y1, s11);
+          }
+          X[r0 * ncd + c0] += s00;
+          if (c1ok) X[r0 * ncd + c0 + 1] += s01;
+          if (r1ok) {
+            X[(r0 + 1) * ncd + c0] += s10;
+            if (c1ok) X[(r0 + 1) * ncd + c0 + 1] += s11;
+          }
+        }
+        __syncthreads();
       }
     }
-    __syncthreads();
-    const int64_t fa = shell_foff[a], fb = shell_foff[b], fc = shell_foff[c], fd = shell_foff[d];
+    // this bra primitive pair's share of the block: D_ab X
+    const double* d1 = dist1 + (pp1 - pp_base1) * (int64_t)nab * nr1;
+    double* o = part + ((pp1 - pp_lo) * n2w + (q2 - q2_lo)) * (int64_t)nab * ncd;
     for (int x = tid; x < nab * ncd; x += nth) {
+      const int ab = x / ncd, cd = x - ab * ncd;
+      const double* dr = d1 + (int64_t)ab * nr1;
+      double s0 = 0.0;
+      for (int e1 = 0; e1 < nr1; ++e1) s0 = fma(dr[e1], X[e1 * ncd + cd], s0);
+      o[x] = s0;
+    }
+  }
+}
+
+size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk) {
+  const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2, nr1 = n_r(lam1), nr2 = n_r(lam2);
+  const size_t ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
+  const size_t dbl = (size_t)nr1 * ncd + (size_t)nr1 * kEriPartTile + ncd * kEriPartTile +
+                     (size_t)chunk * (n_harm(lt) + lt + 1 + n_r(lt) + 4);
+  return sizeof(double) * dbl + sizeof(int) * (nr1 + nr2 + lt + 1);
+}
+
+// Sum of the bra primitive pairs' shares of each unique quartet (q1 in [q1_lo, q1_hi), q2 in [q2_lo, q2_hi),
+// q2 <= q1 for the same class) in a fixed order, written to the eight permutations of every element.  Where
+// a = b, c = d or the two pairs coincide the block holds several members of one permutation orbit; only the
+// canonical member is written, so the output has the permutational symmetry exactly.
+__global__ void __launch_bounds__(128) k_eri_reduce(int la, int lb, int lc, int ld, int q1_lo, int q1_hi,
+                                                    int base1, int q2_lo, int q2_hi, int base2, int same,
+                                                    int64_t pp_lo, const int* __restrict__ pair_a,
+                                                    const int* __restrict__ pair_b,
+                                                    const int64_t* __restrict__ pair_ppoff,
+                                                    const int* __restrict__ shell_nprim,
+                                                    const int64_t* __restrict__ shell_foff,
+                                                    const double* __restrict__ part, int64_t nbf,
+                                                    double* __restrict__ out) {
+  const int nb = 2 * lb + 1, nd = 2 * ld + 1, nab = (2 * la + 1) * nb, ncd = (2 * lc + 1) * nd;
+  const int n2w = q2_hi - q2_lo;
+  const int64_t nitems = (int64_t)(q1_hi - q1_lo) * n2w;
+  for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int q1 = q1_lo + (int)(it / n2w), q2 = q2_lo + (int)(it - (it / n2w) * n2w);
+    if (same && q2 > q1) continue;
+    const int pr1 = base1 + q1, pr2 = base2 + q2;
+    const int a = pair_a[pr1], b = pair_b[pr1], c = pair_a[pr2], d = pair_b[pr2];
+    const int npp1 = shell_nprim[a] * shell_nprim[b];
+    const double* src = part + ((pair_ppoff[pr1] - pp_lo) * n2w + (q2 - q2_lo)) * (int64_t)nab * ncd;
+    const int64_t stride = (int64_t)n2w * nab * ncd;
+    const int64_t fa = shell_foff[a], fb = shell_foff[b], fc = shell_foff[c], fd = shell_foff[d];
+    for (int x = threadIdx.x; x < nab * ncd; x += blockDim.x) {
       const int ab = x / ncd, cd = x - ab * ncd, ma = ab / nb, mb = ab - ma * nb, mc = cd / nd, md = cd - mc * nd;
-      // one writer per permutation orbit: where a = b, c = d or the two pairs coincide the block holds
-      // several members of an orbit (computed with different rounding); the canonical one is written
       if ((a == b && ma < mb) || (c == d && mc < md) || (pr1 == pr2 && ab < cd)) continue;
+      double v = 0.0;
+      for (int i = 0; i < npp1; ++i) v += src[i * stride + x];
       const int64_t I = fa + ma, J = fb + mb, K = fc + mc, M = fd + md;
-      const double v = Acc[x];
       out[((I * nbf + J) * nbf + K) * nbf + M] = v;
       out[((J * nbf + I) * nbf + K) * nbf + M] = v;
       out[((I * nbf + J) * nbf + M) * nbf + K] = v;
@@ -1686,13 +1742,36 @@ __global__ void __launch_bounds__(256) k_eri_quartet(
   }
 }
 
-size_t eri_quartet_smem(int la, int lb, int lc, int ld) {
-  const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2, nr1 = n_r(lam1), nr2 = n_r(lam2);
-  const size_t nab = (size_t)(2 * la + 1) * (2 * lb + 1), ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
-  const size_t dbl = n_harm(lt) + lt + 1 + n_r(lt) + (size_t)nr1 * kEriTile + nr1 * ncd + nab * ncd;
-  const size_t ints = nr1 + nr2 + lt + 1;
-  return sizeof(double) * dbl + sizeof(int) * ints;
+namespace {
+// A rectangle of quartets (bra pairs [q1_lo, q1_hi) x ket pairs [q2_lo, q2_hi) of one class pair) whose
+// shares fit one stream's scratch region.
+struct EriRect {
+  int q1_lo, q1_hi, q2_lo, q2_hi;
+  int64_t pp_lo, pp_hi;
+};
+
+std::vector<EriRect> eri_rects(const ClassWork& w1, const ClassWork& w2, bool same, const int64_t* h_ppoff,
+                               int64_t region) {
+  const int64_t blk = (int64_t)(2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1);
+  const int64_t* pp = h_ppoff + w1.pair_base;  // bra pair q has primitive pairs pp[q] .. pp[q + 1]
+  std::vector<EriRect> out;
+  int q1 = 0;
+  while (q1 < w1.npairs) {
+    int q1e = q1 + 1;  // extend the run of bra pairs while the rectangle still fits
+    while (q1e < w1.npairs && (pp[q1e + 1] - pp[q1]) * (same ? q1e + 1 : w2.npairs) * blk <= region) ++q1e;
+    const int n2 = same ? q1e : w2.npairs;
+    if ((pp[q1e] - pp[q1]) * n2 * blk <= region) {
+      out.push_back(EriRect{q1, q1e, 0, n2, pp[q1], pp[q1e]});
+    } else {  // a single bra pair against too many ket pairs: split the ket range
+      const int step = (int)std::max<int64_t>(1, region / ((pp[q1 + 1] - pp[q1]) * blk));
+      for (int q2 = 0; q2 < n2; q2 += step)
+        out.push_back(EriRect{q1, q1 + 1, q2, std::min(n2, q2 + step), pp[q1], pp[q1 + 1]});
+    }
+    q1 = q1e;
+  }
+  return out;
 }
+}  // namespace
 
 shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
                        const std::vector<ClassWork>& work, int64_t nbf, double* out, cudaStream_t stream,
@@ -1708,15 +1787,54 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
   cudaGetDevice(&dev);
   static bool attr[64] = {};
   if (dev >= 0 && dev < 64 && !attr[dev]) {
-    cudaFuncSetAttribute(k_eri_quartet, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_eri_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr[dev] = true;
   }
-  double* dist = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&dist, sizeof(double) * (size_t)doff[nw], stream);
+  // class pairs, largest first, and each one's chunk of ket primitive pairs
+  struct CP {
+    size_t c1, c2;
+    double cost;
+    int chunk;
+  };
+  std::vector<CP> cps;
+  int64_t need_max = 0, one_max = 1;
+  for (size_t c1 = 0; c1 < nw; ++c1)
+    for (size_t c2 = 0; c2 <= c1; ++c2) {
+      const ClassWork &w1 = work[c1], &w2 = work[c2];
+      if (w1.npairs == 0 || w2.npairs == 0) continue;
+      const double nq = c1 == c2 ? 0.5 * w1.npp * (w1.npairs + 1) : (double)w1.npp * w2.npairs;
+      const double ppq = nq * ((double)w2.npp / w2.npairs);
+      const double cost = ppq * n_r(w1.la + w1.lb) * n_r(w2.la + w2.lb) * (2 * w2.la + 1) * (2 * w2.lb + 1);
+      int maxnp = 1;
+      for (int q = 0; q < w2.npairs; ++q)
+        maxnp = (int)std::max<int64_t>(maxnp, db.h_ppoff[w2.pair_base + q + 1] - db.h_ppoff[w2.pair_base + q]);
+      int chunk = std::min(16, maxnp);
+      while (chunk > 1 && eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, chunk) > 96 * 1024) --chunk;
+      cps.push_back(CP{c1, c2, cost, chunk});
+      const int64_t full = (c1 == c2 ? w1.npp * (int64_t)w1.npairs : w1.npp * (int64_t)w2.npairs) *
+                           (2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1);
+      need_max = std::max(need_max, full);
+      int64_t np1 = 1;  // one bra pair against one ket pair must fit a region
+      for (int q = 0; q < w1.npairs; ++q)
+        np1 = std::max<int64_t>(np1, db.h_ppoff[w1.pair_base + q + 1] - db.h_ppoff[w1.pair_base + q]);
+      one_max = std::max(one_max, np1 * (2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1));
+    }
+  std::stable_sort(cps.begin(), cps.end(), [](const CP& x, const CP& y) { return x.cost > y.cost; });
+  cudaStream_t* pool = nullptr;
+  cudaError_t e = stream_pool(&pool);
   if (e != cudaSuccess) {
-    *err = std::string("distribution buffer: ") + cudaGetErrorString(e);
+    *err = std::string("stream pool: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  const int ns = (int)std::min<size_t>(cps.size(), (size_t)kPoolStreams);
+  const int64_t region = std::max<int64_t>(std::min<int64_t>(need_max, (int64_t)1 << 23), one_max);
+  double* dist = nullptr;
+  e = cudaMallocAsync((void**)&dist, sizeof(double) * (size_t)(doff[nw] + (int64_t)ns * region), stream);
+  if (e != cudaSuccess) {
+    *err = std::string("distribution and scratch buffers: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
   }
+  double* scratch = dist + doff[nw];
   for (size_t c = 0; c < nw; ++c) {
     const ClassWork& w = work[c];
     if (w.npp == 0) continue;
@@ -1726,19 +1844,40 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
         db.prim_exp, db.prim_coef, dt.etab, dt.eoff, dt.gt_ptr + th.gt_base[cid], dt.gt_terms + th.gt_termbase[cid],
         dt.eri_eps, dist + doff[c]);
   }
-  for (size_t c1 = 0; c1 < nw; ++c1)
-    for (size_t c2 = 0; c2 <= c1; ++c2) {
-      const ClassWork &w1 = work[c1], &w2 = work[c2];
-      if (w1.npairs == 0 || w2.npairs == 0) continue;
-      const int64_t nq = c1 == c2 ? (int64_t)w1.npairs * (w1.npairs + 1) / 2 : (int64_t)w1.npairs * w2.npairs;
-      k_eri_quartet<<<grid_cap(nq, 4), 256, eri_quartet_smem(w1.la, w1.lb, w2.la, w2.lb), stream>>>(
-          w1.la, w1.lb, w2.la, w2.lb, w1.npairs, w1.pair_base, w2.npairs, w2.pair_base, c1 == c2 ? 1 : 0, db.pair_a,
-          db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base, db.shell_xyz, db.shell_poff, db.shell_nprim,
-          db.shell_foff, db.prim_exp, dist + doff[c1], dist + doff[c2], dt.boys,
-          dt.rmap + th.rmap_off[w1.la + w1.lb], dt.rmap + th.rmap_off[w2.la + w2.lb],
-          dt.rmap + th.rmap_off[w1.la + w1.lb + w2.la + w2.lb], dt.c2_ptr, dt.c2_cbase, dt.c2_terms, dt.c2_a, nbf,
-          out);
+  cudaEvent_t fork;
+  e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    cudaEventRecord(fork, stream);
+    for (int i = 0; i < ns; ++i) cudaStreamWaitEvent(pool[i], fork, 0);
+    for (size_t k = 0; k < cps.size(); ++k) {
+      const ClassWork &w1 = work[cps[k].c1], &w2 = work[cps[k].c2];
+      const bool same = cps[k].c1 == cps[k].c2;
+      cudaStream_t s = pool[k % ns];
+      double* reg = scratch + (int64_t)(k % ns) * region;
+      const int lam1 = w1.la + w1.lb, lam2 = w2.la + w2.lb;
+      for (const EriRect& r : eri_rects(w1, w2, same, db.h_ppoff, region)) {
+        const int64_t items = (r.pp_hi - r.pp_lo) * (int64_t)(r.q2_hi - r.q2_lo);
+        k_eri_part<<<grid_cap(items, 4), 256, eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, cps[k].chunk), s>>>(
+            w1.la, w1.lb, w2.la, w2.lb, r.pp_lo, r.pp_hi, w1.pair_base, r.q2_lo, r.q2_hi, same ? 1 : 0,
+            cps[k].chunk, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base,
+            w2.pair_base, db.shell_xyz, db.shell_poff, db.shell_nprim, db.prim_exp, dist + doff[cps[k].c1],
+            dist + doff[cps[k].c2], dt.boys, dt.rmap + th.rmap_off[lam1], dt.rmap + th.rmap_off[lam2],
+            dt.rmap + th.rmap_off[lam1 + lam2], dt.c2_ptr, dt.c2_cbase, dt.c2_terms, dt.c2_a, reg);
+        const int64_t quartets = (int64_t)(r.q1_hi - r.q1_lo) * (r.q2_hi - r.q2_lo);
+        k_eri_reduce<<<grid_cap(quartets, 16), 128, 0, s>>>(
+            w1.la, w1.lb, w2.la, w2.lb, r.q1_lo, r.q1_hi, w1.pair_base, r.q2_lo, r.q2_hi, w2.pair_base,
+            same ? 1 : 0, r.pp_lo, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_nprim, db.shell_foff, reg, nbf, out);
+      }
     }
+    for (int i = 0; i < ns; ++i) {
+      cudaEvent_t join;
+      if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) break;
+      cudaEventRecord(join, pool[i]);
+      cudaStreamWaitEvent(stream, join, 0);
+      cudaEventDestroy(join);
+    }
+    cudaEventDestroy(fork);
+  }
   const shgo_status st = launch_error(err);
   cudaFreeAsync(dist, stream);
   return st;
