@@ -1565,8 +1565,9 @@ __global__ void __launch_bounds__(256) k_eri_part(
   double* S = Dt + ncd * kEriPartTile;         // [chunk][nht]
   double* F = S + (size_t)chunk * nht;         // [chunk][lt + 1]
   double* Z = F + (size_t)chunk * (lt + 1);    // [chunk][nrt]
-  double* G = Z + (size_t)chunk * nrt;         // [chunk][4]: u, -rho, 2 pi^{5/2} / (p q sqrt(p + q))
-  int* kap1 = (int*)(G + 4 * chunk);           // bra entries: h | n << 12 | L << 20
+  double* G = Z + (size_t)chunk * nrt;         // [chunk][lt + 1]: g^{(N)}(u) = cpq (-rho)^N F_N(rho u)
+  double* U = G + (size_t)chunk * (lt + 1);    // [chunk][lt / 2 + 1]: u^j
+  int* kap1 = (int*)(U + (size_t)chunk * (lt / 2 + 1));  // bra entries: h | n << 12 | L << 20
   int* kap2 = kap1 + nr1;                      // ket entries
   int* zoff = kap2 + nr2;                      // [lt + 1]
   for (int e = tid; e < nr1; e += nth) {
@@ -1587,8 +1588,9 @@ __global__ void __launch_bounds__(256) k_eri_part(
     if (same && q2 > pr1 - base1) continue;  // uniform over the block
     const int ij = pp_ij[pp1], a = pair_a[pr1], b = pair_b[pr1];
     const double al = prim_exp[shell_poff[a] + (ij >> 8)], be = prim_exp[shell_poff[b] + (ij & 255)], p = al + be;
+    const double ip = 1.0 / p;
     double P[3];
-    for (int x = 0; x < 3; ++x) P[x] = (al * shell_xyz[3 * a + x] + be * shell_xyz[3 * b + x]) / p;
+    for (int x = 0; x < 3; ++x) P[x] = (al * shell_xyz[3 * a + x] + be * shell_xyz[3 * b + x]) * ip;
     const int pr2 = base2 + q2, c = pair_a[pr2], d = pair_b[pr2], npd = shell_nprim[d];
     const int npp2 = shell_nprim[c] * npd;
     const double* d2p = dist2 + (pair_ppoff[pr2] - pp_base2) * (int64_t)ncd * nr2;
@@ -1599,33 +1601,40 @@ __global__ void __launch_bounds__(256) k_eri_part(
       __syncthreads();  // S, F, Z, G of the previous chunk are consumed
       for (int w = warp; w < nck; w += nwarp) {
         const int i2 = k0 + w, ic = shell_poff[c] + i2 / npd, id = shell_poff[d] + i2 % npd;
-        const double ga = prim_exp[ic], de = prim_exp[id], q = ga + de;
+        const double ga = prim_exp[ic], de = prim_exp[id], q = ga + de, iq = 1.0 / q;
         double R[3];
-        for (int x = 0; x < 3; ++x) R[x] = P[x] - (ga * shell_xyz[3 * c + x] + de * shell_xyz[3 * d + x]) / q;
-        const double u = R[0] * R[0] + R[1] * R[1] + R[2] * R[2], rho = p * q / (p + q);
+        for (int x = 0; x < 3; ++x) R[x] = P[x] - (ga * shell_xyz[3 * c + x] + de * shell_xyz[3 * d + x]) * iq;
+        const double u = R[0] * R[0] + R[1] * R[1] + R[2] * R[2], rpq = 1.0 / (p + q), rho = p * q * rpq;
         solid_harmonics_columns(lt, R[0], R[1], R[2], S + (size_t)w * nht, lane, 32);
         if (lane == 0) {
-          boys_eval(lt, rho * u, F + (size_t)w * (lt + 1), 1, boys_tab, c_boys);
-          G[4 * w] = u;
-          G[4 * w + 1] = -rho;
-          G[4 * w + 2] = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 / (p * q * sqrt(p + q));
+          double* Fw = F + (size_t)w * (lt + 1);
+          boys_eval(lt, rho * u, Fw, 1, boys_tab, c_boys);
+          // g^{(N)}(u) = 2 pi^{5/2} / (p q sqrt(p + q)) (-rho)^N F_N(rho u), and u^j
+          double gN = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 * ip * iq * sqrt(rpq);
+          double* Gw = G + (size_t)w * (lt + 1);
+          for (int n = 0; n <= lt; ++n) {
+            Gw[n] = gN * Fw[n];
+            gN *= -rho;
+          }
+          double* Uw = U + (size_t)w * (lt / 2 + 1);
+          double uj = 1.0;
+          for (int j = 0; j <= lt / 2; ++j) {
+            Uw[j] = uj;
+            uj *= u;
+          }
         }
       }
       __syncthreads();
       for (int x = tid; x < nck * nrt; x += nth) {
         const int w = x / nrt, e = x - w * nrt;
         const int r = rmapt[e], h = r & 0xfff, K = r >> 24, L = l_of_index(h);
-        const double u = G[4 * w], mrho = G[4 * w + 1];
-        const double* Fw = F + (size_t)w * (lt + 1);
+        const double* Gw = G + (size_t)w * (lt + 1) + L + K;
+        const double* Uw = U + (size_t)w * (lt / 2 + 1);
         const double* aK = c2_a + ((size_t)L * (kC2K + 1) + K) * (kC2K + 1);
-        double mr = G[4 * w + 2], uj = 1.0, rad = 0.0;
-        for (int n = 0; n < L + K; ++n) mr *= mrho;
-        for (int j = 0; j <= K; ++j) {
-          rad = fma(aK[j] * uj, mr * Fw[L + K + j], rad);
-          uj *= u;
-          mr *= mrho;
-        }
-        Z[x] = ldexp(S[(size_t)w * nht + h] * rad, L);
+        double rad = 0.0;
+        for (int j = 0; j <= K; ++j) rad = fma(aK[j] * Uw[j], Gw[j], rad);
+        // 2^L S_LM(R) rad, the power of two exact
+        Z[x] = (S[(size_t)w * nht + h] * rad) * __longlong_as_double((long long)(1023 + L) << 52);
       }
       __syncthreads();
       const int ncol = nck * nr2;  // columns (ket primitive pair, ket entry) of this chunk
@@ -1695,7 +1704,7 @@ size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk) {
   const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2, nr1 = n_r(lam1), nr2 = n_r(lam2);
   const size_t ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
   const size_t dbl = (size_t)nr1 * ncd + (size_t)nr1 * kEriPartTile + ncd * kEriPartTile +
-                     (size_t)chunk * (n_harm(lt) + lt + 1 + n_r(lt) + 4);
+                     (size_t)chunk * (n_harm(lt) + 2 * (lt + 1) + n_r(lt) + lt / 2 + 1);
   return sizeof(double) * dbl + sizeof(int) * (nr1 + nr2 + lt + 1);
 }
 
@@ -1857,7 +1866,9 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
       const int lam1 = w1.la + w1.lb, lam2 = w2.la + w2.lb;
       for (const EriRect& r : eri_rects(w1, w2, same, db.h_ppoff, region)) {
         const int64_t items = (r.pp_hi - r.pp_lo) * (int64_t)(r.q2_hi - r.q2_lo);
-        k_eri_part<<<grid_cap(items, 4), 256, eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, cps[k].chunk), s>>>(
+        // one block per item, so that blocks of the class pairs running on other streams share the SMs
+        k_eri_part<<<(unsigned)std::min<int64_t>(items, 0x7fffffff), 256,
+                     eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, cps[k].chunk), s>>>(
             w1.la, w1.lb, w2.la, w2.lb, r.pp_lo, r.pp_hi, w1.pair_base, r.q2_lo, r.q2_hi, same ? 1 : 0,
             cps[k].chunk, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base,
             w2.pair_base, db.shell_xyz, db.shell_poff, db.shell_nprim, db.prim_exp, dist + doff[cps[k].c1],
