@@ -231,7 +231,9 @@ shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream);
  * |P - Q|^2), rho = pq/(p + q).  FP64 whatever the basis's precision option.  out: device array of
  * nbf^4 doubles, row-major, out[((i nbf + j) nbf + k) nbf + l] = (ij|kl), fully overwritten (every
  * unique quartet once, written to its eight permutations).  A per-call device buffer of
- * sum over primitive pairs of (2la+1)(2lb+1) C(la+lb+3, 3) doubles is taken from the device's default
+ * sum over primitive pairs of (2la+1)(2lb+1) C(la+lb+3, 3) doubles, plus a scratch region of partial
+ * blocks per pool stream (at most 8M doubles each, or the count in the environment variable
+ * SHGO_ERI_SCRATCH_DOUBLES; larger work is cut into pieces that fit), is taken from the device's default
  * stream-ordered pool and returned on `stream`.  Asynchronous on `stream`.  Errors: SHGO_ERR_INVALID_ARG
  * (NULL basis or out, a batch, nbf > 40000), SHGO_ERR_UNSUPPORTED_L (a shell with l > 4), SHGO_ERR_OOM,
  * SHGO_ERR_CUDA. */

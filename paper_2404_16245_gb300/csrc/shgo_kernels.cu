@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -1534,18 +1535,20 @@ size_t eri_dist_smem(int la, int lb) {
   return sizeof(double) * ((size_t)n_harm(la) + (2 * la + 1) * n_harm(la) + (2 * lb + 1) * n_harm(lb) + 8);
 }
 
-// Work item of k_eri_part: one bra primitive pair pp1 (of the bra class, in [pp_lo, pp_hi)) and one ket
-// shell pair q2 (of the ket class, in [q2_lo, q2_hi)); for the same class only q2 <= q1 is needed.  The item
-// computes X = sum over the ket primitive pairs of I D_cd^T (I: the interaction matrix of step 3, built in
-// tiles of kEriPartTile columns over (ket primitive pair, ket entry)) and writes its share of the block,
-// D_ab X, to part[((pp1 - pp_lo) n2w + q2 - q2_lo) nab ncd].  Ket primitive pairs are taken `chunk` at a time:
+// Work item of k_eri_part: one bra primitive pair pp1 (of the bra class, in [pp_lo, pp_hi)), one slice of
+// its bra entries (nslice slices of equal height) and one ket shell pair q2 (of the ket class, in
+// [q2_lo, q2_hi)); for the same class only q2 <= q1 is needed.  The item computes the slice's rows of
+// X = sum over the ket primitive pairs of I D_cd^T (I: the interaction matrix of step 3, built in tiles of
+// kEriPartTile columns over (ket primitive pair, ket entry)) and writes its share of the block,
+// D_ab[:, slice] X[slice, :], to part[(((pp1 - pp_lo) nslice + slice) n2w + q2 - q2_lo) nab ncd].  Ket primitive pairs are taken `chunk` at a time:
 // one warp per primitive pair for the solid harmonics S_LM(P - Q) and the Boys values, then the radial
 // factors Z of all of them, then the tiles.
 constexpr int kEriPartTile = 32;
+constexpr size_t kEriSmemTarget = 56 * 1024;  // shared memory of a k_eri_part block (four per SM)
 
 __global__ void __launch_bounds__(256) k_eri_part(
     int la, int lb, int lc, int ld, int64_t pp_lo, int64_t pp_hi, int base1, int q2_lo, int q2_hi, int same,
-    int chunk, const int* __restrict__ pp_pair, const int* __restrict__ pp_ij, const int* __restrict__ pair_a,
+    int chunk, int nslice, const int* __restrict__ pp_pair, const int* __restrict__ pp_ij, const int* __restrict__ pair_a,
     const int* __restrict__ pair_b, const int64_t* __restrict__ pair_ppoff, int64_t pp_base1, int64_t pp_base2,
     int base2, const double* __restrict__ shell_xyz, const int* __restrict__ shell_poff,
     const int* __restrict__ shell_nprim, const double* __restrict__ prim_exp, const double* __restrict__ dist1,
@@ -1556,21 +1559,21 @@ __global__ void __launch_bounds__(256) k_eri_part(
   extern __shared__ double smem[];
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2;
-  const int nr1 = n_r(lam1), nr2 = n_r(lam2), nrt = n_r(lt), nht = n_harm(lt);
+  const int nr1f = n_r(lam1), nr2 = n_r(lam2), nrt = n_r(lt), nht = n_harm(lt);
   const int nab = (2 * la + 1) * (2 * lb + 1), ncd = (2 * lc + 1) * (2 * ld + 1);
-  const int n2w = q2_hi - q2_lo;
-  double* X = smem;                            // [nr1][ncd]
-  double* It = X + (size_t)nr1 * ncd;          // [nr1][kEriPartTile]
-  double* Dt = It + nr1 * kEriPartTile;        // [ncd][kEriPartTile] ket distributions of the tile
+  const int n2w = q2_hi - q2_lo, rows = (nr1f + nslice - 1) / nslice;
+  double* X = smem;                            // [rows][ncd]
+  double* It = X + (size_t)rows * ncd;         // [rows][kEriPartTile]
+  double* Dt = It + rows * kEriPartTile;       // [ncd][kEriPartTile] ket distributions of the tile
   double* S = Dt + ncd * kEriPartTile;         // [chunk][nht]
   double* F = S + (size_t)chunk * nht;         // [chunk][lt + 1]
   double* Z = F + (size_t)chunk * (lt + 1);    // [chunk][nrt]
   double* G = Z + (size_t)chunk * nrt;         // [chunk][lt + 1]: g^{(N)}(u) = cpq (-rho)^N F_N(rho u)
   double* U = G + (size_t)chunk * (lt + 1);    // [chunk][lt / 2 + 1]: u^j
   int* kap1 = (int*)(U + (size_t)chunk * (lt / 2 + 1));  // bra entries: h | n << 12 | L << 20
-  int* kap2 = kap1 + nr1;                      // ket entries
+  int* kap2 = kap1 + nr1f;                     // ket entries
   int* zoff = kap2 + nr2;                      // [lt + 1]
-  for (int e = tid; e < nr1; e += nth) {
+  for (int e = tid; e < nr1f; e += nth) {
     const int r = rmap1[e], h = r & 0xfff;
     kap1[e] = h | ((r >> 24) << 12) | (l_of_index(h) << 20);
   }
@@ -1579,11 +1582,12 @@ __global__ void __launch_bounds__(256) k_eri_part(
     kap2[e] = h | ((r >> 24) << 12) | (l_of_index(h) << 20);
   }
   if (tid <= lt) zoff[tid] = lmk_first(lt, tid);
-  const int64_t nitems = (pp_hi - pp_lo) * n2w;
-  const int nxr = (nr1 + 1) >> 1, nxc = (ncd + 1) >> 1;  // 2 x 2 register tiles of X
+  const int64_t nitems = (pp_hi - pp_lo) * nslice * n2w;
   for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int64_t pp1 = pp_lo + it / n2w;
-    const int q2 = q2_lo + (int)(it - (it / n2w) * n2w);
+    const int64_t row = it / n2w, pp1 = pp_lo + row / nslice;
+    const int slice = (int)(row - (row / nslice) * nslice), q2 = q2_lo + (int)(it - row * n2w);
+    const int r_lo = slice * rows, nr1 = min(rows, nr1f - r_lo);  // bra entries r_lo .. r_lo + nr1
+    const int nxr = (nr1 + 1) >> 1, nxc = (ncd + 1) >> 1;        // 2 x 2 register tiles of X
     const int pr1 = pp_pair[pp1];
     if (same && q2 > pr1 - base1) continue;  // uniform over the block
     const int ij = pp_ij[pp1], a = pair_a[pr1], b = pair_b[pr1];
@@ -1642,7 +1646,7 @@ __global__ void __launch_bounds__(256) k_eri_part(
         const int tw = min(kEriPartTile, ncol - t0);
         for (int x = tid; x < nr1 * tw; x += nth) {
           const int e1 = x / tw, jj = x - e1 * tw, col = t0 + jj, w = col / nr2, e2 = col - w * nr2;
-          const int k1 = kap1[e1], k2 = kap2[e2];
+          const int k1 = kap1[r_lo + e1], k2 = kap2[e2];
           const int h1 = k1 & 0xfff, n1e = (k1 >> 12) & 0xff, L1 = k1 >> 20;
           const int h2 = k2 & 0xfff, n2e = (k2 >> 12) & 0xff, L2 = k2 >> 20;
           const int M1 = h1 - L1 * L1 - L1, M2 = h2 - L2 * L2 - L2;
@@ -1687,12 +1691,12 @@ __global__ void __launch_bounds__(256) k_eri_part(
         __syncthreads();
       }
     }
-    // this bra primitive pair's share of the block: D_ab X
-    const double* d1 = dist1 + (pp1 - pp_base1) * (int64_t)nab * nr1;
-    double* o = part + ((pp1 - pp_lo) * n2w + (q2 - q2_lo)) * (int64_t)nab * ncd;
+    // this bra primitive pair's and slice's share of the block: D_ab[:, slice] X
+    const double* d1 = dist1 + (pp1 - pp_base1) * (int64_t)nab * nr1f + r_lo;
+    double* o = part + (row * n2w + (q2 - q2_lo)) * (int64_t)nab * ncd;
     for (int x = tid; x < nab * ncd; x += nth) {
       const int ab = x / ncd, cd = x - ab * ncd;
-      const double* dr = d1 + (int64_t)ab * nr1;
+      const double* dr = d1 + (int64_t)ab * nr1f;
       double s0 = 0.0;
       for (int e1 = 0; e1 < nr1; ++e1) s0 = fma(dr[e1], X[e1 * ncd + cd], s0);
       o[x] = s0;
@@ -1700,21 +1704,22 @@ __global__ void __launch_bounds__(256) k_eri_part(
   }
 }
 
-size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk) {
+size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk, int nslice) {
   const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2, nr1 = n_r(lam1), nr2 = n_r(lam2);
+  const int rows = (nr1 + nslice - 1) / nslice;
   const size_t ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
-  const size_t dbl = (size_t)nr1 * ncd + (size_t)nr1 * kEriPartTile + ncd * kEriPartTile +
+  const size_t dbl = (size_t)rows * ncd + (size_t)rows * kEriPartTile + ncd * kEriPartTile +
                      (size_t)chunk * (n_harm(lt) + 2 * (lt + 1) + n_r(lt) + lt / 2 + 1);
   return sizeof(double) * dbl + sizeof(int) * (nr1 + nr2 + lt + 1);
 }
 
-// Sum of the bra primitive pairs' shares of each unique quartet (q1 in [q1_lo, q1_hi), q2 in [q2_lo, q2_hi),
+// Sum of the shares (bra primitive pairs x slices) of each unique quartet (q1 in [q1_lo, q1_hi), q2 in [q2_lo, q2_hi),
 // q2 <= q1 for the same class) in a fixed order, written to the eight permutations of every element.  Where
 // a = b, c = d or the two pairs coincide the block holds several members of one permutation orbit; only the
 // canonical member is written, so the output has the permutational symmetry exactly.
 __global__ void __launch_bounds__(128) k_eri_reduce(int la, int lb, int lc, int ld, int q1_lo, int q1_hi,
                                                     int base1, int q2_lo, int q2_hi, int base2, int same,
-                                                    int64_t pp_lo, const int* __restrict__ pair_a,
+                                                    int nslice, int64_t pp_lo, const int* __restrict__ pair_a,
                                                     const int* __restrict__ pair_b,
                                                     const int64_t* __restrict__ pair_ppoff,
                                                     const int* __restrict__ shell_nprim,
@@ -1729,8 +1734,8 @@ __global__ void __launch_bounds__(128) k_eri_reduce(int la, int lb, int lc, int 
     if (same && q2 > q1) continue;
     const int pr1 = base1 + q1, pr2 = base2 + q2;
     const int a = pair_a[pr1], b = pair_b[pr1], c = pair_a[pr2], d = pair_b[pr2];
-    const int npp1 = shell_nprim[a] * shell_nprim[b];
-    const double* src = part + ((pair_ppoff[pr1] - pp_lo) * n2w + (q2 - q2_lo)) * (int64_t)nab * ncd;
+    const int npp1 = shell_nprim[a] * shell_nprim[b] * nslice;  // shares: bra primitive pairs x slices
+    const double* src = part + ((pair_ppoff[pr1] - pp_lo) * nslice * n2w + (q2 - q2_lo)) * (int64_t)nab * ncd;
     const int64_t stride = (int64_t)n2w * nab * ncd;
     const int64_t fa = shell_foff[a], fb = shell_foff[b], fc = shell_foff[c], fd = shell_foff[d];
     for (int x = threadIdx.x; x < nab * ncd; x += blockDim.x) {
@@ -1760,8 +1765,8 @@ struct EriRect {
 };
 
 std::vector<EriRect> eri_rects(const ClassWork& w1, const ClassWork& w2, bool same, const int64_t* h_ppoff,
-                               int64_t region) {
-  const int64_t blk = (int64_t)(2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1);
+                               int64_t region, int nslice) {
+  const int64_t blk = (int64_t)nslice * (2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1);
   const int64_t* pp = h_ppoff + w1.pair_base;  // bra pair q has primitive pairs pp[q] .. pp[q + 1]
   std::vector<EriRect> out;
   int q1 = 0;
@@ -1803,7 +1808,7 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
   struct CP {
     size_t c1, c2;
     double cost;
-    int chunk;
+    int chunk, nslice;
   };
   std::vector<CP> cps;
   int64_t need_max = 0, one_max = 1;
@@ -1817,16 +1822,20 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
       int maxnp = 1;
       for (int q = 0; q < w2.npairs; ++q)
         maxnp = (int)std::max<int64_t>(maxnp, db.h_ppoff[w2.pair_base + q + 1] - db.h_ppoff[w2.pair_base + q]);
-      int chunk = std::min(16, maxnp);
-      while (chunk > 1 && eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, chunk) > 96 * 1024) --chunk;
-      cps.push_back(CP{c1, c2, cost, chunk});
-      const int64_t full = (c1 == c2 ? w1.npp * (int64_t)w1.npairs : w1.npp * (int64_t)w2.npairs) *
+      // shared memory within kEriSmemTarget (four blocks of 256 threads per SM): fewer ket primitive pairs per
+      // chunk first, then the bra entries cut into slices
+      int chunk = std::min(16, maxnp), nslice = 1;
+      while (chunk > 1 && eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, chunk, 1) > kEriSmemTarget) --chunk;
+      while (nslice < n_r(w1.la + w1.lb) && eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, chunk, nslice) > kEriSmemTarget)
+        ++nslice;
+      cps.push_back(CP{c1, c2, cost, chunk, nslice});
+      const int64_t full = (c1 == c2 ? w1.npp * (int64_t)w1.npairs : w1.npp * (int64_t)w2.npairs) * nslice *
                            (2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1);
       need_max = std::max(need_max, full);
       int64_t np1 = 1;  // one bra pair against one ket pair must fit a region
       for (int q = 0; q < w1.npairs; ++q)
         np1 = std::max<int64_t>(np1, db.h_ppoff[w1.pair_base + q + 1] - db.h_ppoff[w1.pair_base + q]);
-      one_max = std::max(one_max, np1 * (2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1));
+      one_max = std::max(one_max, np1 * nslice * (2 * w1.la + 1) * (2 * w1.lb + 1) * (2 * w2.la + 1) * (2 * w2.lb + 1));
     }
   std::stable_sort(cps.begin(), cps.end(), [](const CP& x, const CP& y) { return x.cost > y.cost; });
   cudaStream_t* pool = nullptr;
@@ -1836,7 +1845,14 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
     return SHGO_ERR_CUDA;
   }
   const int ns = (int)std::min<size_t>(cps.size(), (size_t)kPoolStreams);
-  const int64_t region = std::max<int64_t>(std::min<int64_t>(need_max, (int64_t)1 << 23), one_max);
+  // scratch region per stream: what the largest class pair needs, at most 8M doubles (64 MiB) unless
+  // SHGO_ERI_SCRATCH_DOUBLES sets another cap; never less than one bra pair against one ket pair
+  int64_t cap = (int64_t)1 << 23;
+  if (const char* env = std::getenv("SHGO_ERI_SCRATCH_DOUBLES")) {
+    const long long v = std::atoll(env);
+    if (v > 0) cap = v;
+  }
+  const int64_t region = std::max<int64_t>(std::min<int64_t>(need_max, cap), one_max);
   double* dist = nullptr;
   e = cudaMallocAsync((void**)&dist, sizeof(double) * (size_t)(doff[nw] + (int64_t)ns * region), stream);
   if (e != cudaSuccess) {
@@ -1864,20 +1880,21 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
       cudaStream_t s = pool[k % ns];
       double* reg = scratch + (int64_t)(k % ns) * region;
       const int lam1 = w1.la + w1.lb, lam2 = w2.la + w2.lb;
-      for (const EriRect& r : eri_rects(w1, w2, same, db.h_ppoff, region)) {
-        const int64_t items = (r.pp_hi - r.pp_lo) * (int64_t)(r.q2_hi - r.q2_lo);
+      const int nsl = cps[k].nslice;
+      for (const EriRect& r : eri_rects(w1, w2, same, db.h_ppoff, region, nsl)) {
+        const int64_t items = (r.pp_hi - r.pp_lo) * nsl * (int64_t)(r.q2_hi - r.q2_lo);
         // one block per item, so that blocks of the class pairs running on other streams share the SMs
         k_eri_part<<<(unsigned)std::min<int64_t>(items, 0x7fffffff), 256,
-                     eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, cps[k].chunk), s>>>(
+                     eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, cps[k].chunk, nsl), s>>>(
             w1.la, w1.lb, w2.la, w2.lb, r.pp_lo, r.pp_hi, w1.pair_base, r.q2_lo, r.q2_hi, same ? 1 : 0,
-            cps[k].chunk, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base,
+            cps[k].chunk, nsl, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base,
             w2.pair_base, db.shell_xyz, db.shell_poff, db.shell_nprim, db.prim_exp, dist + doff[cps[k].c1],
             dist + doff[cps[k].c2], dt.boys, dt.rmap + th.rmap_off[lam1], dt.rmap + th.rmap_off[lam2],
             dt.rmap + th.rmap_off[lam1 + lam2], dt.c2_ptr, dt.c2_cbase, dt.c2_terms, dt.c2_a, reg);
         const int64_t quartets = (int64_t)(r.q1_hi - r.q1_lo) * (r.q2_hi - r.q2_lo);
         k_eri_reduce<<<grid_cap(quartets, 16), 128, 0, s>>>(
             w1.la, w1.lb, w2.la, w2.lb, r.q1_lo, r.q1_hi, w1.pair_base, r.q2_lo, r.q2_hi, w2.pair_base,
-            same ? 1 : 0, r.pp_lo, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_nprim, db.shell_foff, reg, nbf, out);
+            same ? 1 : 0, nsl, r.pp_lo, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_nprim, db.shell_foff, reg, nbf, out);
       }
     }
     for (int i = 0; i < ns; ++i) {

@@ -104,3 +104,14 @@ def test_metric_positive_semidefinite_and_eightfold(shgo):
     n = E.shape[0]
     ev = np.linalg.eigvalsh(E.reshape(n * n, n * n))
     assert ev.min() > -1e-11 * ev.max()
+
+
+@pytest.mark.parametrize("cap", ["700", "20000"])
+def test_scratch_split_into_rectangles(shgo, monkeypatch, cap):
+    """A small per-stream scratch region (SHGO_ERI_SCRATCH_DOUBLES) cuts every class pair into several
+    rectangles of quartets, down to single bra pairs against part of the ket range; the result is the same."""
+    monkeypatch.setenv("SHGO_ERI_SCRATCH_DOUBLES", cap)
+    basis = W.random_basis(12, 9, 3, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0, n_sites=9)
+    E = gpu_E(shgo, basis)
+    parity.check(E, ref_E(basis), what=f"eri scratch cap {cap}")
+    assert_eightfold(E)
