@@ -1557,7 +1557,7 @@ __global__ void __launch_bounds__(256) k_eri_part(
     const int* __restrict__ c2_cbase, const GTerm* __restrict__ c2_terms, const double* __restrict__ c2_a,
     double* __restrict__ part) {
   extern __shared__ double smem[];
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int tid = threadIdx.x, nth = blockDim.x;
   const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2;
   const int nr1f = n_r(lam1), nr2 = n_r(lam2), nrt = n_r(lt), nht = n_harm(lt);
   const int nab = (2 * la + 1) * (2 * lb + 1), ncd = (2 * lc + 1) * (2 * ld + 1);
@@ -1570,7 +1570,8 @@ __global__ void __launch_bounds__(256) k_eri_part(
   double* Z = F + (size_t)chunk * (lt + 1);    // [chunk][nrt]
   double* G = Z + (size_t)chunk * nrt;         // [chunk][lt + 1]: g^{(N)}(u) = cpq (-rho)^N F_N(rho u)
   double* U = G + (size_t)chunk * (lt + 1);    // [chunk][lt / 2 + 1]: u^j
-  int* kap1 = (int*)(U + (size_t)chunk * (lt / 2 + 1));  // bra entries: h | n << 12 | L << 20
+  double* Rv = U + (size_t)chunk * (lt / 2 + 1);  // [chunk][3]: P - Q
+  int* kap1 = (int*)(Rv + 3 * (size_t)chunk);    // bra entries: h | n << 12 | L << 20
   int* kap2 = kap1 + nr1f;                     // ket entries
   int* zoff = kap2 + nr2;                      // [lt + 1]
   for (int e = tid; e < nr1f; e += nth) {
@@ -1603,30 +1604,35 @@ __global__ void __launch_bounds__(256) k_eri_part(
     for (int k0 = 0; k0 < npp2; k0 += chunk) {
       const int nck = min(chunk, npp2 - k0);
       __syncthreads();  // S, F, Z, G of the previous chunk are consumed
-      for (int w = warp; w < nck; w += nwarp) {
+      // one thread per ket primitive pair: P - Q, the Boys values, g^{(N)}(u) and u^j
+      for (int w = tid; w < nck; w += nth) {
         const int i2 = k0 + w, ic = shell_poff[c] + i2 / npd, id = shell_poff[d] + i2 % npd;
         const double ga = prim_exp[ic], de = prim_exp[id], q = ga + de, iq = 1.0 / q;
         double R[3];
         for (int x = 0; x < 3; ++x) R[x] = P[x] - (ga * shell_xyz[3 * c + x] + de * shell_xyz[3 * d + x]) * iq;
         const double u = R[0] * R[0] + R[1] * R[1] + R[2] * R[2], rpq = 1.0 / (p + q), rho = p * q * rpq;
-        solid_harmonics_columns(lt, R[0], R[1], R[2], S + (size_t)w * nht, lane, 32);
-        if (lane == 0) {
-          double* Fw = F + (size_t)w * (lt + 1);
-          boys_eval(lt, rho * u, Fw, 1, boys_tab, c_boys);
-          // g^{(N)}(u) = 2 pi^{5/2} / (p q sqrt(p + q)) (-rho)^N F_N(rho u), and u^j
-          double gN = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 * ip * iq * sqrt(rpq);
-          double* Gw = G + (size_t)w * (lt + 1);
-          for (int n = 0; n <= lt; ++n) {
-            Gw[n] = gN * Fw[n];
-            gN *= -rho;
-          }
-          double* Uw = U + (size_t)w * (lt / 2 + 1);
-          double uj = 1.0;
-          for (int j = 0; j <= lt / 2; ++j) {
-            Uw[j] = uj;
-            uj *= u;
-          }
+        for (int x = 0; x < 3; ++x) Rv[3 * w + x] = R[x];
+        double* Fw = F + (size_t)w * (lt + 1);
+        boys_eval(lt, rho * u, Fw, 1, boys_tab, c_boys);
+        // g^{(N)}(u) = 2 pi^{5/2} / (p q sqrt(p + q)) (-rho)^N F_N(rho u), and u^j
+        double gN = 2.0 * 5.5683279968317078453 * 3.1415926535897932385 * ip * iq * sqrt(rpq);
+        double* Gw = G + (size_t)w * (lt + 1);
+        for (int n = 0; n <= lt; ++n) {
+          Gw[n] = gN * Fw[n];
+          gN *= -rho;
         }
+        double* Uw = U + (size_t)w * (lt / 2 + 1);
+        double uj = 1.0;
+        for (int j = 0; j <= lt / 2; ++j) {
+          Uw[j] = uj;
+          uj *= u;
+        }
+      }
+      __syncthreads();
+      // one thread per (ket primitive pair, harmonic column m) for S_LM(P - Q)
+      for (int x = tid; x < nck * (2 * lt + 1); x += nth) {
+        const int w = x / (2 * lt + 1), col = x - w * (2 * lt + 1);
+        solid_harmonics_columns(lt, Rv[3 * w], Rv[3 * w + 1], Rv[3 * w + 2], S + (size_t)w * nht, col, 2 * lt + 1);
       }
       __syncthreads();
       for (int x = tid; x < nck * nrt; x += nth) {
@@ -1709,7 +1715,7 @@ size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk, int nslice) {
   const int rows = (nr1 + nslice - 1) / nslice;
   const size_t ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
   const size_t dbl = (size_t)rows * ncd + (size_t)rows * kEriPartTile + ncd * kEriPartTile +
-                     (size_t)chunk * (n_harm(lt) + 2 * (lt + 1) + n_r(lt) + lt / 2 + 1);
+                     (size_t)chunk * (n_harm(lt) + 2 * (lt + 1) + n_r(lt) + lt / 2 + 1 + 3);
   return sizeof(double) * dbl + sizeof(int) * (nr1 + nr2 + lt + 1);
 }
 
@@ -1881,10 +1887,13 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
       double* reg = scratch + (int64_t)(k % ns) * region;
       const int lam1 = w1.la + w1.lb, lam2 = w2.la + w2.lb;
       const int nsl = cps[k].nslice;
+      // threads per block: fewer for the small class pairs, so that more items are resident per SM
+      const int xw = ((n_r(lam1) + nsl - 1) / nsl) * (2 * w2.la + 1) * (2 * w2.lb + 1);
+      const int threads = xw >= 1024 ? 256 : (xw >= 256 ? 128 : 64);
       for (const EriRect& r : eri_rects(w1, w2, same, db.h_ppoff, region, nsl)) {
         const int64_t items = (r.pp_hi - r.pp_lo) * nsl * (int64_t)(r.q2_hi - r.q2_lo);
         // one block per item, so that blocks of the class pairs running on other streams share the SMs
-        k_eri_part<<<(unsigned)std::min<int64_t>(items, 0x7fffffff), 256,
+        k_eri_part<<<(unsigned)std::min<int64_t>(items, 0x7fffffff), threads,
                      eri_part_smem(w1.la, w1.lb, w2.la, w2.lb, cps[k].chunk, nsl), s>>>(
             w1.la, w1.lb, w2.la, w2.lb, r.pp_lo, r.pp_hi, w1.pair_base, r.q2_lo, r.q2_hi, same ? 1 : 0,
             cps[k].chunk, nsl, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.pair_ppoff, w1.pp_base, w2.pp_base,
