@@ -239,6 +239,17 @@ shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream);
  * SHGO_ERR_CUDA. */
 shgo_status shgo_eri(const shgo_basis* basis, double* out, void* stream);
 
+/* Coulomb and exchange matrices of a density from the same integrals, without storing them:
+ * J[p][q] = sum_rs (pq|rs) D[r][s] and K[p][r] = sum_qs (pq|rs) D[q][s], all indices over the basis
+ * functions (Eqs. 13-15 as in shgo_eri; basis with l <= 4, not a batch).  density: device nbf x nbf
+ * row-major (any matrix; symmetric for the usual closed-shell use).  J, K: device nbf x nbf row-major,
+ * fully overwritten; either may be NULL, not both.  Each unique integral is formed once and added to
+ * the entries of its distinct permutations with atomic additions, so the last bits of J and K may vary
+ * from call to call.  Scratch as for shgo_eri; no nbf^4 storage.  Asynchronous on `stream`.
+ * Errors: SHGO_ERR_INVALID_ARG (NULL basis, density or both outputs, a batch), SHGO_ERR_UNSUPPORTED_L,
+ * SHGO_ERR_OOM, SHGO_ERR_CUDA. */
+shgo_status shgo_eri_jk(const shgo_basis* basis, const double* density, double* J, double* K, void* stream);
+
 /* Per (la, lb) class (measurement): number of classes of a basis (-1 for NULL); for class c
  * (0 <= c < nclasses, in the library's launch order) its la >= lb in la_lb[2] and, for n_centers
  * nuclei, stats[4] = shell-triples, integrals (shell-triples x (2la+1)(2lb+1)), algorithmic flops of

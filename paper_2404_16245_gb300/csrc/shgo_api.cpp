@@ -731,8 +731,36 @@ shgo_status shgo_eri(const shgo_basis* basis, double* out, void* stream) {
   cudaGetDevice(&prev);
   if (prev != basis->device) cudaSetDevice(basis->device);
   std::string err;
-  const shgo_status st =
-      launch_eri(basis->d, *basis->tabs, tables_host(), basis->work, basis->nbf, out, (cudaStream_t)stream, &err);
+  const shgo_status st = launch_eri(basis->d, *basis->tabs, tables_host(), basis->work, basis->nbf, out, nullptr,
+                                    nullptr, nullptr, (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+
+shgo_status shgo_eri_jk(const shgo_basis* basis, const double* density, double* J, double* K, void* stream) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "electron-repulsion integrals take a single basis, not a batch");
+  for (const ClassWork& w : basis->work)
+    if (w.la > kEriLmax) return fail(SHGO_ERR_UNSUPPORTED_L, "electron-repulsion integrals support l <= 4");
+  if (basis->nbf > 0 && (!density || (!J && !K))) return fail(SHGO_ERR_INVALID_ARG, "NULL density or no output");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  std::string err;
+  shgo_status st = SHGO_OK;
+  const size_t bytes = sizeof(double) * (size_t)basis->nbf * (size_t)basis->nbf;
+  cudaError_t e = cudaSuccess;
+  if (J && bytes) e = cudaMemsetAsync(J, 0, bytes, (cudaStream_t)stream);
+  if (e == cudaSuccess && K && bytes) e = cudaMemsetAsync(K, 0, bytes, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    st = SHGO_ERR_CUDA;
+    err = std::string("clearing J, K: ") + cudaGetErrorString(e);
+  } else {
+    st = launch_eri(basis->d, *basis->tabs, tables_host(), basis->work, basis->nbf, nullptr, density, J, K,
+                    (cudaStream_t)stream, &err);
+  }
   if (prev != basis->device) cudaSetDevice(prev);
   if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;

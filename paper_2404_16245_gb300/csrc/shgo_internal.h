@@ -379,10 +379,12 @@ shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, cons
 constexpr int kEriLmax = 4;
 
 // Four-centre electron-repulsion integrals (ab|cd) of every quartet of pairs of `work` into out
-// (nbf^4, row-major, all eight permutations written).  Classes must have la <= kEriLmax.
+// (nbf^4, row-major, all eight permutations written; out may be nullptr) and, with a density dens
+// (nbf x nbf), accumulated into Jm[p][q] += (pq|rs) D_rs and Km[p][r] += (pq|rs) D_qs (zeroed by the caller;
+// either may be nullptr).  Classes must have la <= kEriLmax.
 shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
-                       const std::vector<ClassWork>& work, int64_t nbf, double* out, cudaStream_t stream,
-                       std::string* err);
+                       const std::vector<ClassWork>& work, int64_t nbf, double* out, const double* dens,
+                       double* Jm, double* Km, cudaStream_t stream, std::string* err);
 
 // FP32-bulk coupling (shgo_coupling_f32.cu): the Lambda = lam instantiation, compensated (pair
 // arithmetic) or plain, on `grid` blocks of 64 threads; args.boys_ff and args.exp_ff must be set.

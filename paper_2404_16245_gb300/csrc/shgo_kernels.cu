@@ -1722,7 +1722,9 @@ size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk, int nslice) {
 // Sum of the shares (bra primitive pairs x slices) of each unique quartet (q1 in [q1_lo, q1_hi), q2 in [q2_lo, q2_hi),
 // q2 <= q1 for the same class) in a fixed order, written to the eight permutations of every element.  Where
 // a = b, c = d or the two pairs coincide the block holds several members of one permutation orbit; only the
-// canonical member is written, so the output has the permutational symmetry exactly.
+// canonical member is written, so the output has the permutational symmetry exactly.  With a density
+// (dens != nullptr) every distinct member (pq|rs) of the orbit adds (pq|rs) D_rs to Jm[p][q] and
+// (pq|rs) D_qs to Km[p][r] (either may be nullptr); out may then be nullptr.
 __global__ void __launch_bounds__(128) k_eri_reduce(int la, int lb, int lc, int ld, int q1_lo, int q1_hi,
                                                     int base1, int q2_lo, int q2_hi, int base2, int same,
                                                     int nslice, int64_t pp_lo, const int* __restrict__ pair_a,
@@ -1731,7 +1733,8 @@ __global__ void __launch_bounds__(128) k_eri_reduce(int la, int lb, int lc, int 
                                                     const int* __restrict__ shell_nprim,
                                                     const int64_t* __restrict__ shell_foff,
                                                     const double* __restrict__ part, int64_t nbf,
-                                                    double* __restrict__ out) {
+                                                    double* __restrict__ out, const double* __restrict__ dens,
+                                                    double* __restrict__ Jm, double* __restrict__ Km) {
   const int nb = 2 * lb + 1, nd = 2 * ld + 1, nab = (2 * la + 1) * nb, ncd = (2 * lc + 1) * nd;
   const int n2w = q2_hi - q2_lo;
   const int64_t nitems = (int64_t)(q1_hi - q1_lo) * n2w;
@@ -1750,14 +1753,28 @@ __global__ void __launch_bounds__(128) k_eri_reduce(int la, int lb, int lc, int 
       double v = 0.0;
       for (int i = 0; i < npp1; ++i) v += src[i * stride + x];
       const int64_t I = fa + ma, J = fb + mb, K = fc + mc, M = fd + md;
-      out[((I * nbf + J) * nbf + K) * nbf + M] = v;
-      out[((J * nbf + I) * nbf + K) * nbf + M] = v;
-      out[((I * nbf + J) * nbf + M) * nbf + K] = v;
-      out[((J * nbf + I) * nbf + M) * nbf + K] = v;
-      out[((K * nbf + M) * nbf + I) * nbf + J] = v;
-      out[((M * nbf + K) * nbf + I) * nbf + J] = v;
-      out[((K * nbf + M) * nbf + J) * nbf + I] = v;
-      out[((M * nbf + K) * nbf + J) * nbf + I] = v;
+      if (out) {
+        out[((I * nbf + J) * nbf + K) * nbf + M] = v;
+        out[((J * nbf + I) * nbf + K) * nbf + M] = v;
+        out[((I * nbf + J) * nbf + M) * nbf + K] = v;
+        out[((J * nbf + I) * nbf + M) * nbf + K] = v;
+        out[((K * nbf + M) * nbf + I) * nbf + J] = v;
+        out[((M * nbf + K) * nbf + I) * nbf + J] = v;
+        out[((K * nbf + M) * nbf + J) * nbf + I] = v;
+        out[((M * nbf + K) * nbf + J) * nbf + I] = v;
+      }
+      if (dens) {
+        const int64_t t[8][4] = {{I, J, K, M}, {J, I, K, M}, {I, J, M, K}, {J, I, M, K},
+                                 {K, M, I, J}, {M, K, I, J}, {K, M, J, I}, {M, K, J, I}};
+        for (int u = 0; u < 8; ++u) {
+          bool dup = false;
+          for (int w = 0; w < u; ++w)
+            dup = dup || (t[w][0] == t[u][0] && t[w][1] == t[u][1] && t[w][2] == t[u][2] && t[w][3] == t[u][3]);
+          if (dup) continue;
+          if (Jm) atomicAdd(Jm + t[u][0] * nbf + t[u][1], v * dens[t[u][2] * nbf + t[u][3]]);
+          if (Km) atomicAdd(Km + t[u][0] * nbf + t[u][2], v * dens[t[u][1] * nbf + t[u][3]]);
+        }
+      }
     }
   }
 }
@@ -1794,8 +1811,8 @@ std::vector<EriRect> eri_rects(const ClassWork& w1, const ClassWork& w2, bool sa
 }  // namespace
 
 shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
-                       const std::vector<ClassWork>& work, int64_t nbf, double* out, cudaStream_t stream,
-                       std::string* err) {
+                       const std::vector<ClassWork>& work, int64_t nbf, double* out, const double* dens,
+                       double* Jm, double* Km, cudaStream_t stream, std::string* err) {
   const size_t nw = work.size();
   std::vector<int64_t> doff(nw + 1, 0);
   for (size_t c = 0; c < nw; ++c) {
@@ -1903,7 +1920,8 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
         const int64_t quartets = (int64_t)(r.q1_hi - r.q1_lo) * (r.q2_hi - r.q2_lo);
         k_eri_reduce<<<grid_cap(quartets, 16), 128, 0, s>>>(
             w1.la, w1.lb, w2.la, w2.lb, r.q1_lo, r.q1_hi, w1.pair_base, r.q2_lo, r.q2_hi, w2.pair_base,
-            same ? 1 : 0, nsl, r.pp_lo, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_nprim, db.shell_foff, reg, nbf, out);
+            same ? 1 : 0, nsl, r.pp_lo, db.pair_a, db.pair_b, db.pair_ppoff, db.shell_nprim, db.shell_foff, reg, nbf, out,
+            dens, Jm, Km);
       }
     }
     for (int i = 0; i < ns; ++i) {

@@ -90,6 +90,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_coulomb_2c.restype = ctypes.c_int
     lib.shgo_eri.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_eri.restype = ctypes.c_int
+    lib.shgo_eri_jk.argtypes = [ctypes.c_void_p] * 5
+    lib.shgo_eri_jk.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -369,6 +371,27 @@ def eri(basis, out=None, stream=None, device="cuda"):
         raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
     shgo_eri(basis.handle, out.data_ptr(), stream)
     return out
+
+
+def shgo_eri_jk(basis, dens_ptr, j_ptr, k_ptr, stream=None):
+    _check(_lib.shgo_eri_jk(ctypes.c_void_p(basis), ctypes.c_void_p(int(dens_ptr) or 0),
+                            ctypes.c_void_p(int(j_ptr) or 0), ctypes.c_void_p(int(k_ptr) or 0), _stream_handle(stream)))
+
+
+def eri_jk(basis, density, coulomb=True, exchange=True, stream=None):
+    """Coulomb J[p,q] = sum_rs (pq|rs) D[r,s] and exchange K[p,r] = sum_qs (pq|rs) D[q,s] of a device density
+    (FP64 nbf x nbf); returns (J, K), None for the one not asked for."""
+    import torch
+    if not isinstance(basis, Basis):
+        raise ValueError("eri_jk takes a Basis, not a Batch")
+    n = basis.nbf
+    if not density.is_contiguous() or density.dtype != torch.float64 or tuple(density.shape) != (n, n):
+        raise ValueError(f"density must be a contiguous float64 [{n}, {n}] tensor")
+    J = torch.empty((n, n), dtype=torch.float64, device=density.device) if coulomb else None
+    K = torch.empty((n, n), dtype=torch.float64, device=density.device) if exchange else None
+    shgo_eri_jk(basis.handle, density.data_ptr(), J.data_ptr() if J is not None else 0,
+                K.data_ptr() if K is not None else 0, stream)
+    return J, K
 
 
 def host_solid_harmonics(l: int, xyz) -> np.ndarray:

@@ -115,3 +115,34 @@ def test_scratch_split_into_rectangles(shgo, monkeypatch, cap):
     E = gpu_E(shgo, basis)
     parity.check(E, ref_E(basis), what=f"eri scratch cap {cap}")
     assert_eightfold(E)
+
+
+@pytest.mark.parametrize("which", ["config1", "mixed"])
+def test_coulomb_and_exchange_matrices(shgo, which):
+    """J[p,q] = sum_rs (pq|rs) D[r,s] and K[p,r] = sum_qs (pq|rs) D[q,s] without the tensor, against the oracle's
+    tensor contracted with D (a symmetric density for config 1, a general matrix for the mixed basis).  Bar: the
+    elementwise bar carried through the contraction, 1e-11 sum |(pq|rs)| |D| + 1e-13 sum |D|."""
+    if which == "config1":
+        basis = W.config1()[0]
+    else:
+        basis = W.random_basis(12, 9, 3, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0, n_sites=9)
+    E = ref_E(basis)
+    n = E.shape[0]
+    d = np.random.default_rng(5).normal(size=(n, n))
+    D = (d + d.T) / 2 if which == "config1" else d
+    B = shgo.Basis(basis)
+    Dt = torch.tensor(D, device="cuda")
+    J, K = shgo.eri_jk(B, Dt)
+    J1, none1 = shgo.eri_jk(B, Dt, exchange=False)
+    none2, K1 = shgo.eri_jk(B, Dt, coulomb=False)
+    torch.cuda.synchronize()
+    B.close()
+    assert none1 is None and none2 is None
+    aE, aD = np.abs(E), np.abs(D)
+    refs = [(J, np.einsum("pqrs,rs->pq", E, D), np.einsum("pqrs,rs->pq", aE, aD)),
+            (J1, np.einsum("pqrs,rs->pq", E, D), np.einsum("pqrs,rs->pq", aE, aD)),
+            (K, np.einsum("pqrs,qs->pr", E, D), np.einsum("pqrs,qs->pr", aE, aD)),
+            (K1, np.einsum("pqrs,qs->pr", E, D), np.einsum("pqrs,qs->pr", aE, aD))]
+    for got, ref, scale in refs:
+        got = got.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-11 * scale + 1e-13 * aD.sum())
