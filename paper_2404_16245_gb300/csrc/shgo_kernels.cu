@@ -1544,6 +1544,7 @@ size_t eri_dist_smem(int la, int lb) {
 // one warp per primitive pair for the solid harmonics S_LM(P - Q) and the Boys values, then the radial
 // factors Z of all of them, then the tiles.
 constexpr int kEriPartTile = 32;
+constexpr int kEriTileStride = kEriPartTile + 1;  // odd row stride: rows read together fall in distinct banks
 constexpr size_t kEriSmemTarget = 56 * 1024;  // shared memory of a k_eri_part block (four per SM)
 
 __global__ void __launch_bounds__(256) k_eri_part(
@@ -1563,9 +1564,9 @@ __global__ void __launch_bounds__(256) k_eri_part(
   const int nab = (2 * la + 1) * (2 * lb + 1), ncd = (2 * lc + 1) * (2 * ld + 1);
   const int n2w = q2_hi - q2_lo, rows = (nr1f + nslice - 1) / nslice;
   double* X = smem;                            // [rows][ncd]
-  double* It = X + (size_t)rows * ncd;         // [rows][kEriPartTile]
-  double* Dt = It + rows * kEriPartTile;       // [ncd][kEriPartTile] ket distributions of the tile
-  double* S = Dt + ncd * kEriPartTile;         // [chunk][nht]
+  double* It = X + (size_t)rows * ncd;         // [rows][kEriTileStride]
+  double* Dt = It + rows * kEriTileStride;     // [ncd][kEriTileStride] ket distributions of the tile
+  double* S = Dt + ncd * kEriTileStride;       // [chunk][nht]
   double* F = S + (size_t)chunk * nht;         // [chunk][lt + 1]
   double* Z = F + (size_t)chunk * (lt + 1);    // [chunk][nrt]
   double* G = Z + (size_t)chunk * nrt;         // [chunk][lt + 1]: g^{(N)}(u) = cpq (-rho)^N F_N(rho u)
@@ -1588,7 +1589,8 @@ __global__ void __launch_bounds__(256) k_eri_part(
     const int64_t row = it / n2w, pp1 = pp_lo + row / nslice;
     const int slice = (int)(row - (row / nslice) * nslice), q2 = q2_lo + (int)(it - row * n2w);
     const int r_lo = slice * rows, nr1 = min(rows, nr1f - r_lo);  // bra entries r_lo .. r_lo + nr1
-    const int nxr = (nr1 + 1) >> 1, nxc = (ncd + 1) >> 1;        // 2 x 2 register tiles of X
+    // 2 x 2 register tiles of X: rows (r, r + nxr), columns (c, c + nxc), consecutive threads on consecutive c
+    const int nxr = (nr1 + 1) >> 1, nxc = (ncd + 1) >> 1;
     const int pr1 = pp_pair[pp1];
     if (same && q2 > pr1 - base1) continue;  // uniform over the block
     const int ij = pp_ij[pp1], a = pair_a[pr1], b = pair_b[pr1];
@@ -1665,20 +1667,20 @@ __global__ void __launch_bounds__(256) k_eri_part(
             const int L = g.pad, K = (L1 + L2 - L) / 2 + n1e + n2e;
             v = fma(g.coef, Zw[zoff[L] + (g.ridx - L * L) * (kmax_of(lt, L) + 1) + K], v);
           }
-          It[e1 * kEriPartTile + jj] = (L2 & 1) ? -v : v;
+          It[e1 * kEriTileStride + jj] = (L2 & 1) ? -v : v;
         }
         for (int x = tid; x < ncd * tw; x += nth) {
           const int cd = x / tw, jj = x - cd * tw, col = t0 + jj, w = col / nr2, e2 = col - w * nr2;
-          Dt[cd * kEriPartTile + jj] = d2p[((int64_t)(k0 + w) * ncd + cd) * nr2 + e2];
+          Dt[cd * kEriTileStride + jj] = d2p[((int64_t)(k0 + w) * ncd + cd) * nr2 + e2];
         }
         __syncthreads();
         for (int x = tid; x < nxr * nxc; x += nth) {
-          const int r0 = 2 * (x / nxc), c0 = 2 * (x - (x / nxc) * nxc);
-          const bool r1ok = r0 + 1 < nr1, c1ok = c0 + 1 < ncd;
-          const double* i0 = It + r0 * kEriPartTile;
-          const double* i1 = It + (r1ok ? r0 + 1 : r0) * kEriPartTile;
-          const double* j0 = Dt + c0 * kEriPartTile;
-          const double* j1 = Dt + (c1ok ? c0 + 1 : c0) * kEriPartTile;
+          const int r0 = x / nxc, c0 = x - r0 * nxc, r1 = r0 + nxr, c1 = c0 + nxc;
+          const bool r1ok = r1 < nr1, c1ok = c1 < ncd;
+          const double* i0 = It + r0 * kEriTileStride;
+          const double* i1 = It + (r1ok ? r1 : r0) * kEriTileStride;
+          const double* j0 = Dt + c0 * kEriTileStride;
+          const double* j1 = Dt + (c1ok ? c1 : c0) * kEriTileStride;
           double s00 = 0.0, s01 = 0.0, s10 = 0.0, s11 = 0.0;
           for (int jj = 0; jj < tw; ++jj) {
             const double x0 = i0[jj], x1 = i1[jj], y0 = j0[jj], y1 = j1[jj];
@@ -1688,10 +1690,10 @@ __global__ void __launch_bounds__(256) k_eri_part(
             s11 = fma(x1, y1, s11);
           }
           X[r0 * ncd + c0] += s00;
-          if (c1ok) X[r0 * ncd + c0 + 1] += s01;
+          if (c1ok) X[r0 * ncd + c1] += s01;
           if (r1ok) {
-            X[(r0 + 1) * ncd + c0] += s10;
-            if (c1ok) X[(r0 + 1) * ncd + c0 + 1] += s11;
+            X[r1 * ncd + c0] += s10;
+            if (c1ok) X[r1 * ncd + c1] += s11;
           }
         }
         __syncthreads();
@@ -1714,7 +1716,7 @@ size_t eri_part_smem(int la, int lb, int lc, int ld, int chunk, int nslice) {
   const int lam1 = la + lb, lam2 = lc + ld, lt = lam1 + lam2, nr1 = n_r(lam1), nr2 = n_r(lam2);
   const int rows = (nr1 + nslice - 1) / nslice;
   const size_t ncd = (size_t)(2 * lc + 1) * (2 * ld + 1);
-  const size_t dbl = (size_t)rows * ncd + (size_t)rows * kEriPartTile + ncd * kEriPartTile +
+  const size_t dbl = (size_t)rows * ncd + (size_t)rows * kEriTileStride + ncd * kEriTileStride +
                      (size_t)chunk * (n_harm(lt) + 2 * (lt + 1) + n_r(lt) + lt / 2 + 1 + 3);
   return sizeof(double) * dbl + sizeof(int) * (nr1 + nr2 + lt + 1);
 }
