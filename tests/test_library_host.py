@@ -44,6 +44,72 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
         shgo.shgo_basis_create(1, [1], [0], [], [], [0.0, 0.0, 0.0])
 
 
+def test_non_finite_and_out_of_range_inputs_are_rejected_on_the_host():
+    """Basis creation validates on the host before any device work: NaN or infinite exponents,
+    coefficients or centres, zero or negative exponents and primitive counts outside 1..64."""
+    bad = [
+        ([1], [1], [float("nan")], [1.0], [0.0, 0.0, 0.0]),
+        ([1], [1], [float("inf")], [1.0], [0.0, 0.0, 0.0]),
+        ([1], [1], [0.0], [1.0], [0.0, 0.0, 0.0]),
+        ([1], [1], [1.0], [float("nan")], [0.0, 0.0, 0.0]),
+        ([1], [1], [1.0], [float("-inf")], [0.0, 0.0, 0.0]),
+        ([1], [1], [1.0], [1.0], [0.0, float("nan"), 0.0]),
+        ([0], [65], [1.0] * 65, [1.0] * 65, [0.0, 0.0, 0.0]),
+    ]
+    for l, npr, ex, co, xyz in bad:
+        with pytest.raises(shgo.ShgoError) as e:
+            shgo.shgo_basis_create(1, l, npr, ex, co, xyz)
+        assert e.value.status == 1
+
+
+def test_every_entry_point_rejects_null_handles_without_gpu_work():
+    """Failure detection on the host: every call on a basis, batch or network handle returns
+    SHGO_ERR_INVALID_ARG for a NULL handle before any device work; size queries answer -1 and the
+    free calls accept NULL."""
+    import ctypes
+    lib = ctypes.CDLL(shgo._build.LIB)
+    vp, i64, i32, f32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
+    N = None
+    calls = {
+        "shgo_nuclear_attraction": ([vp] * 5, [N] * 5),
+        "shgo_nuclear_attraction_timed": ([vp] * 6, [N] * 6),
+        "shgo_nuclear_attraction_class_timed": ([vp] * 6, [N] * 6),
+        "shgo_nuclear_attraction_batched": ([vp] * 5, [N] * 5),
+        "shgo_esp": ([vp] * 5, [N] * 5),
+        "shgo_esp_gradient": ([vp] * 5, [N] * 5),
+        "shgo_overlap": ([vp] * 3, [N] * 3),
+        "shgo_coulomb_2c": ([vp] * 3, [N] * 3),
+        "shgo_eri": ([vp] * 3, [N] * 3),
+        "shgo_eri_jk": ([vp] * 5, [N] * 5),
+        "shgo_batch_layout": ([vp] * 3, [N] * 3),
+        "shgo_pair_shells": ([vp] * 3, [N] * 3),
+        "shgo_screen_mask": ([vp] * 2, [N] * 2),
+        "shgo_basis_flops": ([vp, i64, vp, vp], [N, 4, N, N]),
+        "shgo_basis_class_stats": ([vp, i64, i32, vp, vp], [N, 4, 0, N, N]),
+        "shgo_screen_features": ([vp, vp, vp, vp, i64, vp, vp], [N, N, N, N, 0, N, N]),
+        "shgo_screen_build": ([vp, vp, vp, vp, i64, f64, f64, vp, vp], [N, N, N, N, 0, -12.0, 0.0, N, N]),
+        "shgo_nuclear_attraction_screened": ([vp, vp, vp, i64, vp, vp], [N, N, N, 0, N, N]),
+        "shgo_mlp_get_params": ([vp] * 2, [N] * 2),
+        "shgo_mlp_forward": ([vp, vp, i64, vp, vp], [N, N, 1, N, N]),
+        "shgo_mlp_gradients": ([vp, vp, vp, i64, f32, vp, vp], [N, N, N, 1, 4.0, N, N]),
+        "shgo_mlp_train_step": ([vp, vp, vp, i64, f32, f32, vp, vp], [N, N, N, 1, 4.0, 1e-3, N, N]),
+    }
+    for name, (types, args) in calls.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = types, ctypes.c_int
+        assert f(*args) == 1, name
+    for name in ("shgo_basis_nbf", "shgo_basis_npairs", "shgo_basis_launches", "shgo_batch_out_size"):
+        f = getattr(lib, name)
+        f.argtypes, f.restype = [vp], i64
+        assert f(N) == -1, name
+    lib.shgo_basis_nclasses.argtypes, lib.shgo_basis_nclasses.restype = [vp], i32
+    assert lib.shgo_basis_nclasses(N) == -1
+    lib.shgo_free.argtypes, lib.shgo_free.restype = [vp], None
+    lib.shgo_free(N)
+    lib.shgo_mlp_free.argtypes, lib.shgo_mlp_free.restype = [vp], None
+    lib.shgo_mlp_free(N)
+
+
 @pytest.mark.parametrize("l", range(0, 17))
 def test_host_harmonic_recursion_matches_scipy(l):
     rng = np.random.default_rng(l)
