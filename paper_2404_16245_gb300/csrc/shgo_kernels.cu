@@ -1896,7 +1896,13 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
   }
   cudaEvent_t fork;
   e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) {
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dist, stream);
+    *err = std::string("fork event: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  bool joined = true;
+  {
     cudaEventRecord(fork, stream);
     for (int i = 0; i < ns; ++i) cudaStreamWaitEvent(pool[i], fork, 0);
     for (size_t k = 0; k < cps.size(); ++k) {
@@ -1926,16 +1932,27 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
             dens, Jm, Km);
       }
     }
-    for (int i = 0; i < ns; ++i) {
+    for (int i = 0; i < ns && joined; ++i) {
       cudaEvent_t join;
-      if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) break;
+      if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        joined = false;
+        break;
+      }
       cudaEventRecord(join, pool[i]);
       cudaStreamWaitEvent(stream, join, 0);
       cudaEventDestroy(join);
     }
     cudaEventDestroy(fork);
   }
-  const shgo_status st = launch_error(err);
+  shgo_status st = launch_error(err);
+  if (!joined) {
+    // `stream` does not wait for every pool stream: finish their work before the buffers are returned
+    for (int i = 0; i < ns; ++i) cudaStreamSynchronize(pool[i]);
+    if (st == SHGO_OK) {
+      st = SHGO_ERR_CUDA;
+      *err = "join event could not be created";
+    }
+  }
   cudaFreeAsync(dist, stream);
   return st;
 }
