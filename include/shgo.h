@@ -294,6 +294,15 @@ double shgo_host_translation(int32_t la, int32_t ma, int32_t l1, int32_t m1, int
  * expansion and downward recursion below T = 40, asymptotic start and upward recursion above). */
 shgo_status shgo_host_boys(int32_t nmax, double T, double* F);
 
+/* Coefficient a_{k,j}(L) of the k-fold Laplacian of a solid harmonic times a radial function:
+ * Laplacian^k [S_LM(R) f(u)] = S_LM(R) sum_j a_{k,j}(L) u^j f^{(k+j)}(u), u = |R|^2, as the two- and
+ * four-centre Coulomb kernels use it (L <= 2 SHGO_LMAX, j <= k <= SHGO_LMAX; 0 outside). */
+double shgo_host_laplacian_coef(int32_t L, int32_t k, int32_t j);
+
+/* Coefficient eps_{k,n}(L) of r^{2k} S_LM(r) e^{-p r^2} = sum_n eps_{k,n}(L) p^{-(k+n)} Laplacian^n
+ * [S_LM(r) e^{-p r^2}] (the four-centre kernels; L <= 2 SHGO_LMAX, n <= k <= SHGO_LMAX; 0 outside). */
+double shgo_host_eri_eps(int32_t L, int32_t k, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

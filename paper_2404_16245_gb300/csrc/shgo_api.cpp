@@ -918,6 +918,16 @@ double shgo_host_translation(int32_t la, int32_t ma, int32_t l1, int32_t m1, int
   return translation_real(la, ma, l1, m1, nu);
 }
 
+double shgo_host_laplacian_coef(int32_t L, int32_t k, int32_t j) {
+  if (L < 0 || L > kLamMax || k < 0 || k > kC2K || j < 0 || j > k) return 0.0;
+  return tables_host().c2_a[((size_t)L * (kC2K + 1) + k) * (kC2K + 1) + j];
+}
+
+double shgo_host_eri_eps(int32_t L, int32_t k, int32_t n) {
+  if (L < 0 || L > kLamMax || k < 0 || k > kC2K || n < 0 || n > k) return 0.0;
+  return tables_host().eri_eps[((size_t)L * (kC2K + 1) + k) * (kC2K + 1) + n];
+}
+
 shgo_status shgo_host_boys(int32_t nmax, double T, double* F) {
   if (nmax < 0 || nmax > kLamMax + 1 || !F || !(T >= 0) || !std::isfinite(T))
     return fail(SHGO_ERR_INVALID_ARG, "bad arguments");

@@ -108,6 +108,10 @@ def _load() -> ctypes.CDLL:
     lib.shgo_host_translation.restype = ctypes.c_double
     lib.shgo_host_boys.argtypes = [ctypes.c_int32, ctypes.c_double, f64p]
     lib.shgo_host_boys.restype = ctypes.c_int
+    lib.shgo_host_laplacian_coef.argtypes = [ctypes.c_int32] * 3
+    lib.shgo_host_laplacian_coef.restype = ctypes.c_double
+    lib.shgo_host_eri_eps.argtypes = [ctypes.c_int32] * 3
+    lib.shgo_host_eri_eps.restype = ctypes.c_double
     return lib
 
 
@@ -407,6 +411,14 @@ def host_gaunt(l1, m1, l2, m2, L, M) -> float:
 
 def host_translation(la, ma, l1, m1, nu) -> float:
     return float(_lib.shgo_host_translation(la, ma, l1, m1, nu))
+
+
+def host_laplacian_coef(L: int, k: int, j: int) -> float:
+    return float(_lib.shgo_host_laplacian_coef(L, k, j))
+
+
+def host_eri_eps(L: int, k: int, n: int) -> float:
+    return float(_lib.shgo_host_eri_eps(L, k, n))
 
 
 def host_boys(nmax: int, T: float) -> np.ndarray:
