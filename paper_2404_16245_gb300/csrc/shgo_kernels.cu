@@ -1824,10 +1824,14 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
   if (doff[nw] == 0) return SHGO_OK;
   int dev = 0;
   cudaGetDevice(&dev);
-  static bool attr[64] = {};
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    cudaFuncSetAttribute(k_eri_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr[dev] = true;
+  {
+    static std::mutex mu;
+    static bool attr[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+      cudaFuncSetAttribute(k_eri_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr[dev] = true;
+    }
   }
   // class pairs, largest first, and each one's chunk of ket primitive pairs
   struct CP {
