@@ -1540,9 +1540,11 @@ size_t eri_dist_smem(int la, int lb) {
 // [q2_lo, q2_hi)); for the same class only q2 <= q1 is needed.  The item computes the slice's rows of
 // X = sum over the ket primitive pairs of I D_cd^T (I: the interaction matrix of step 3, built in tiles of
 // kEriPartTile columns over (ket primitive pair, ket entry)) and writes its share of the block,
-// D_ab[:, slice] X[slice, :], to part[(((pp1 - pp_lo) nslice + slice) n2w + q2 - q2_lo) nab ncd].  Ket primitive pairs are taken `chunk` at a time:
-// one warp per primitive pair for the solid harmonics S_LM(P - Q) and the Boys values, then the radial
-// factors Z of all of them, then the tiles.
+// D_ab[:, slice] X[slice, :], to part[(((pp1 - pp_lo) nslice + slice) n2w + q2 - q2_lo) nab ncd].
+// Ket primitive pairs are taken `chunk` at a time: one thread per primitive pair for P - Q, its Boys values
+// and the tables g^{(N)}(u), u^j; one thread per (primitive pair, column m) for the solid harmonics
+// S_LM(P - Q); then the radial factors Z of all of them; then the tiles, contracted into X with 2 x 2
+// register tiles (rows r, r + nxr and columns c, c + nxc).
 constexpr int kEriPartTile = 32;
 constexpr int kEriTileStride = kEriPartTile + 1;  // odd row stride: rows read together fall in distinct banks
 constexpr size_t kEriSmemTarget = 56 * 1024;  // shared memory of a k_eri_part block (four per SM)
