@@ -392,3 +392,21 @@ def test_eri_method_model_matches_oracle(ls):
     ref = E[off[0]:off[1], off[1]:off[2], off[2]:off[3], off[3]:off[4]]
     got = _eri_model(ls, exps, cen)
     assert np.max(np.abs(got - ref)) <= 1e-14 + 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("ls,exps,shared", [
+    ((2, 2, 2, 2), (0.05, 0.1, 5000.0, 3000.0), "ket"),
+    ((3, 1, 2, 2), (5000.0, 3000.0, 0.05, 0.1), "bra"),
+    ((2, 1, 2, 1), (0.05, 4000.0, 0.08, 2500.0), "both"),
+])
+def test_eri_method_model_wide_exponent_ratios(ls, exps, shared):
+    """The Laplacian-power form sums terms of alternating sign; with exponents 1e5 apart (tight pairs on one
+    centre, so the Gaussian product factor stays 1) it still meets the parity bar against the oracle."""
+    A, B, C = np.zeros(3), np.array([0.9, -0.4, 0.6]), np.array([1.7, 0.8, -0.5])
+    cen = {"ket": (A, B, C, C), "bra": (A, A, B, C), "both": (A, A, C, C)}[shared]
+    basis = W.make_basis(list(ls), [1] * 4, np.array(exps), [1.0] * 4, list(cen))
+    E = oracle.eri(basis, precision="ld")
+    off = np.concatenate([[0], np.cumsum(2 * np.array(ls) + 1)])
+    ref = E[off[0]:off[1], off[1]:off[2], off[2]:off[3], off[3]:off[4]]
+    got = _eri_model(ls, np.array(exps), cen)
+    assert np.all(np.abs(got - ref) <= 1e-13 + 1e-11 * np.abs(ref))
