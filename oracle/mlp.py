@@ -6,7 +6,9 @@ are standardised by (x - mean)/sd.  Loss: sum_s w_s (y_s - t_s)^2 / n, w_s = und
 y_s < t_s.  The gradient is taken with respect to the weights as used (BF16-rounded values),
 which is the gradient the library applies to its FP32 master weights.
 
-Parameter layout: W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3[1].
+Parameter layout: W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3[1].  Initial weights are a
+seeded input drawn by the shared input generators (paper_2404_16245_gb300.workloads), not part of
+this reference.
 """
 from __future__ import annotations
 
@@ -78,13 +80,3 @@ def loss_and_grad(params, X, T, mean, sd, under_weight=1.0, quantize=True):
     gb1 = dz1.sum(axis=0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, [gb3]])
     return loss, g
-
-
-def init_params(seed: int) -> np.ndarray:
-    """He-style random initialisation (float32)."""
-    rng = np.random.default_rng(seed)
-    W1 = rng.normal(0, np.sqrt(2.0 / IN), (H, IN))
-    W2 = rng.normal(0, np.sqrt(2.0 / H), (H, H))
-    W3 = rng.normal(0, np.sqrt(1.0 / H), H)
-    p = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3, [0.0]])
-    return p.astype(np.float32)

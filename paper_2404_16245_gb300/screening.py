@@ -13,7 +13,7 @@ import time
 
 import numpy as np
 
-from . import shgo
+from . import shgo, workloads
 
 
 def _prim_index(nprim, poff, shells):
@@ -76,11 +76,10 @@ def train(X, T, *, epochs=20, batch=4096, lr=2e-3, under_weight=4.0, seed=0, log
     """Network fitted on features X [n, 16] and labels T [n] (torch CUDA tensors) with the library's
     training kernels; returns (MLP, per-epoch losses)."""
     import torch
-    from oracle import mlp as ref  # initial weights only (a seeded random draw)
     Xh = X.cpu().numpy()
     mean = Xh.mean(axis=0)
     sd = np.maximum(Xh.std(axis=0), 1e-3)
-    net = shgo.MLP(ref.init_params(seed), mean, sd)
+    net = shgo.MLP(workloads.mlp_init_params(seed), mean, sd)
     n = X.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
     losses = []

@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+"""Seeded synthetic inputs shared by the tests and the benchmark.
 
 This module only draws random numbers and lays them out; it holds none of the integral
 arithmetic.  A basis is a dict of numpy arrays:
@@ -182,3 +182,19 @@ def random_basis(seed: int, n_shells: int, lmax: int, max_prim: int = 4, box: fl
 def random_nuclei(seed: int, n: int, box: float = 4.0, z_lo: int = 1, z_hi: int = 10):
     rng = _rng(seed)
     return rng.uniform(0.0, box, (n, 3)), rng.integers(z_lo, z_hi + 1, n).astype(np.float64)
+
+
+MLP_IN, MLP_H = 16, 64
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Seeded initial weights of the 16-64-64-1 screening network (float32, the layout of
+    include/shgo_mlp.h: W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3): He-style normal draws
+    with standard deviation sqrt(2 / fan_in) for the two SiLU layers, sqrt(1 / fan_in) for the
+    linear output, zero biases."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, np.sqrt(2.0 / MLP_IN), (MLP_H, MLP_IN))
+    W2 = rng.normal(0, np.sqrt(2.0 / MLP_H), (MLP_H, MLP_H))
+    W3 = rng.normal(0, np.sqrt(1.0 / MLP_H), MLP_H)
+    p = np.concatenate([W1.ravel(), np.zeros(MLP_H), W2.ravel(), np.zeros(MLP_H), W3, [0.0]])
+    return p.astype(np.float32)

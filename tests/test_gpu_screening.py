@@ -30,7 +30,7 @@ def test_mlp_gradients_match_reference(shgo):
     T = rng.normal(size=n).astype(np.float32)
     mean = (rng.normal(size=16) * 0.1).astype(np.float32)
     sd = rng.uniform(0.5, 2.0, 16).astype(np.float32)
-    p = ref.init_params(7)
+    p = W.mlp_init_params(7)
     net = shgo.MLP(p, mean, sd)
     g, loss = net.gradients(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), under_weight=4.0)
     rloss, rg = ref.loss_and_grad(p, X, T, mean.astype(np.float64), sd.astype(np.float64), under_weight=4.0)
@@ -49,7 +49,7 @@ def test_mlp_training_reduces_loss(shgo):
     w = rng.normal(size=16)
     T = (X @ w + 0.5 * np.sin(X[:, 0])).astype(np.float32)
     Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
-    net = shgo.MLP(ref.init_params(0), np.zeros(16), np.ones(16))
+    net = shgo.MLP(W.mlp_init_params(0), np.zeros(16), np.ones(16))
     _, l0 = net.gradients(Xd, Td)
     for _ in range(300):
         net.train_step(Xd, Td, 1.0, 3e-3)
