@@ -57,6 +57,21 @@ def fp32_lane_peak_t(sm_mhz: float) -> float:
     return 152 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
 
 
+# Iterations of the FMA microbenchmark (2048 threads per SM x 8 chains x 4 x iters FMAs): about 25 ms on
+# each pipe of a GB300 at full clock.
+PEAK_ITERS = {"fp64": 1536, "fp32": 98304}
+
+
+def measure_fma_peak(precision: str, stream, repeats: int = 3) -> dict:
+    """The FP64 or FP32 multiply-add rate of this GPU measured now (shgo_measure_fma_rate: independent
+    FMA chains on every SM, CUDA events on `stream`); the best of `repeats` launches, in TFLOP/s."""
+    from paper_2404_16245_gb300 import shgo
+    prec = shgo.SHGO_PREC_FP64 if precision == "fp64" else shgo.SHGO_PREC_FP32_BULK
+    runs = [shgo.shgo_measure_fma_rate(prec, PEAK_ITERS[precision], stream) for _ in range(repeats)]
+    best = max(r[0] for r in runs)
+    return {"tflops": best / 1e12, "runs_tflops": [r[0] / 1e12 for r in runs], "ms": [r[1] for r in runs]}
+
+
 def f32_coupling_instructions(basis_handle, n_centers: int) -> float:
     """Useful FP32 lane-instructions of the FP32-bulk coupling kernel for one V: per live primitive pair
     and nucleus, the pair-frame offset and T (~250), one Boys form (~650), t_j (7 Lambda), the radial sums
@@ -210,6 +225,71 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def speedup_at_1e10(n_mol: int, steps: int, stream) -> dict:
+    """The metric's second half on a subset of the batched workload (its first n_mol molecules, seed
+    PCG64(3000)): the plain path, one molecule at a time in FP64 through shgo_nuclear_attraction, against
+    the batched path (one call for all molecules, CUDA-graph replays) in FP64 and in FP32-bulk.  Each
+    variant's V is compared element by element with the plain FP64 one; a variant counts toward the
+    speed-up at 1e-10 when its largest absolute difference is at most 1e-10.  CUDA events on `stream`,
+    `steps` timed passes after one warm pass (and the batched calls' tuning and capture calls)."""
+    import torch
+
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.Generator(np.random.PCG64(3000))
+    mols = [W.config3_molecule(rng) for _ in range(n_mol)]
+    cs = [torch.tensor(c, device=dev) for _, c, _ in mols]
+    zs = [torch.tensor(z, device=dev) for _, _, z in mols]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    bases = [shgo.Basis(b) for b, _, _ in mols]
+    plain = [torch.empty((B.nbf, B.nbf), dtype=torch.float64, device=dev) for B in bases]
+
+    def run_plain():
+        for i, B in enumerate(bases):
+            shgo.nuclear_attraction(B, cs[i], zs[i], out=plain[i], stream=stream)
+
+    ms_plain = timed(run_plain)
+    Cb = torch.cat(cs)
+    Zb = torch.cat(zs)
+    res = {"subset": f"first {n_mol} molecules of the batched workload (seed PCG64(3000), "
+                     f"{int(sum(len(z) for _, _, z in mols))} atoms)",
+           "plain_fp64_one_at_a_time_ms": ms_plain, "variants": {}}
+    vmax = max(float(v.abs().max()) for v in plain)
+    for name, prec in (("batched_fp64", shgo.SHGO_PREC_FP64), ("batched_fp32bulk", shgo.SHGO_PREC_FP32_BULK)):
+        batch = shgo.Batch([(b, len(z)) for b, _, z in mols], precision=prec)
+        out = torch.empty(batch.out_size, dtype=torch.float64, device=dev)
+        shgo.nuclear_attraction_batched(batch, Cb, Zb, out=out, stream=stream)  # tuning call
+        shgo.nuclear_attraction_batched(batch, Cb, Zb, out=out, stream=stream)  # capture call
+        ms = timed(lambda: shgo.nuclear_attraction_batched(batch, Cb, Zb, out=out, stream=stream))
+        diff = max(float((torch.as_tensor(batch.block(out, i)) - plain[i]).abs().max()) for i in range(n_mol))
+        res["variants"][name] = {"ms": ms, "speedup_vs_plain_fp64": ms_plain / ms, "max_abs_diff": diff,
+                                 "within_1e-10": diff <= 1e-10}
+        batch.close()
+        del out
+    for B in bases:
+        B.close()
+    ok = {k: v for k, v in res["variants"].items() if v["within_1e-10"]}
+    best = max(ok, key=lambda k: ok[k]["speedup_vs_plain_fp64"]) if ok else None
+    res.update({"max_abs_v": vmax, "best_within_1e-10": best,
+                "speedup_at_1e-10": ok[best]["speedup_vs_plain_fp64"] if best else None,
+                "screening": "not in this figure: at 1e-10 the learned mask skips little the primitive-pair "
+                             "bound has not already removed (bench.py --workload screened measures it)"})
+    return res
+
+
 def run_shgo(args, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -278,26 +358,33 @@ def run_shgo(args, ws, rank, local):
     names = ["k_coupling_f32" if f32 else "k_coupling_fp64", "k_pair_block"]
     dom = int(np.argmax(ph))
     clk = clocks.get("sm_max_mhz") or 2070.0
+    # the pipe's rate measured in this run, right after the timed region (the roofline's denominator)
+    pk64 = measure_fma_peak("fp64", stream)
+    pk32 = measure_fma_peak("fp32", stream) if args.precision != "fp64" else None
     if f32 and dom == 0:
         # FP32-bulk coupling: FP32 lane-instructions of its pair arithmetic (one operation each)
         work = f32_coupling_instructions(bases[0].handle, cents[0].shape[0])
         achieved = work / (ph[0] / 1e3) / 1e12
-        peak = fp32_lane_peak_t(clk)
+        # FP32 lane-instructions per second: the measured FFMA rate counts 2 flops per FFMA instruction
+        peak = pk32["tflops"] / 2.0
         roofline = {"bound": "alu", "kernel": names[0], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock; each FP32 instruction of "
+                    "peak_source": "measured in this run: shgo_measure_fma_rate FP32 (FFMA instructions per "
+                                   "second, 2048 threads per SM x 8 independent chains); each FP32 instruction of "
                                    "the pair arithmetic counted as one operation (model in bench.py)",
+                    "peak_derived_nominal": fp32_lane_peak_t(clk), "peak_measurements": pk32,
                     "model_fp32_instructions_per_step": work}
     else:
         achieved = flops[dom] / (ph[dom] / 1e3) / 1e12
-        peak = fp64_peak_tflops(clk)
+        peak = pk64["tflops"]
         roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
                     "traffic": COUPLING_DRAM_BYTES_PER_V if dom == 0 else None,
                     "traffic_note": "DRAM bytes read + written by the 28 coupling launches of one V (ncu capture, "
                                     "profiles/k_coupling_fp64_lam11_highl_fp64.md)",
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock (nominal 1.25, "
-                                   "DFMA microbenchmark 1.20 TFLOP/s)"}
+                    "peak_source": "measured in this run: shgo_measure_fma_rate FP64 (DFMA, 2048 threads per SM x "
+                                   "8 independent chains, CUDA events), best of 3",
+                    "peak_derived_nominal": fp64_peak_tflops(clk), "peak_measurements": pk64}
     roofline.update({"phase_ms": [float(ph[0]), float(ph[1])],
                      "phase_tflops": [float(flops[0] / ph[0] / 1e9), float(flops[1] / ph[1] / 1e9)],
                      "algorithmic_flops_per_step": [float(flops[0]), float(flops[1])]})
@@ -371,6 +458,10 @@ def run_shgo(args, ws, rank, local):
                "d2h_bytes_per_step": d2h // ksteps, "steps": ksteps,
                "note": "basis upload + pinned H2D of nuclei + kernels + D2H of V, wall clock"}
 
+    speedup = None
+    if rank == 0 and ws == 1 and args.speedup_molecules > 0:
+        speedup = speedup_at_1e10(args.speedup_molecules, 2, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -388,6 +479,7 @@ def run_shgo(args, ws, rank, local):
                        "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write, outside step events)",
                        "wall_s_timed_region": wall},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "speedup_vs_plain_at_1e-10": speedup,
             "per_class": {"note": "each class's coupling + pair kernels timed alone (classes one after another); "
                                   "frac = algorithmic FP64 flops / time / peak", "classes": per_class,
                           "classes_64_replicas_batched": per_class_64},
@@ -882,7 +974,8 @@ def run_eri(args) -> int:
     integrals = sum((2 * la + 1) * (2 * lb + 1) for la, lb, _ in _eri_pairs(dicts[0]))
     clk = clocks.get("sm_max_mhz") or 2070.0
     achieved = flops / (ms / 1e3) / 1e12
-    peak = fp64_peak_tflops(clk)
+    pk64 = measure_fma_peak("fp64", stream)
+    peak = pk64["tflops"]
     # end to end through the public API: basis from host arrays, the tensor back to pinned host memory
     host = torch.empty((n, n, n, n), dtype=torch.float64, pin_memory=True)
     h2d = sum(np.asarray(dicts[0][k]).nbytes for k in ("l", "nprim", "exps", "coefs", "xyz"))
@@ -922,7 +1015,8 @@ def run_eri(args) -> int:
             "roofline": {"bound": "alu", "kernel": "k_eri_part", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "note": "algorithmic flops of k_eri_part + k_eri_reduce (model in bench.py) over the whole call",
-                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"},
+                         "peak_source": "measured in this run: shgo_measure_fma_rate FP64, best of 3",
+                         "peak_derived_nominal": fp64_peak_tflops(clk)},
             "cpu_baseline": cpu,
             "e2e": {"value": nq / e2e_s, "unit": "shell-quartets/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(n ** 4 * 8), "steps": e2e_steps,
@@ -931,6 +1025,30 @@ def run_eri(args) -> int:
     print(json.dumps(line), flush=True)
     for B in bases:
         B.close()
+    return 0
+
+
+def run_peaks(args) -> int:
+    """The roofline denominators of this GPU: FP64 (DFMA) and FP32 (FFMA) multiply-add rates from
+    shgo_measure_fma_rate (2048 threads per SM, eight independent chains each, CUDA events), five
+    launches each with the SM clock sampled during them, as one JSON line."""
+    import torch
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    r64 = measure_fma_peak("fp64", stream, repeats=5)
+    r32 = measure_fma_peak("fp32", stream, repeats=5)
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    clk = clocks.get("sm_max_mhz") or 2070.0
+    line = {"workload": "peaks", "fp64_tflops": r64["tflops"], "fp32_tflops": r32["tflops"],
+            "fp64_runs": r64, "fp32_runs": r32, "clocks": clocks,
+            "fp64_nominal_at_max_clock": fp64_peak_tflops(clk), "fp32_nominal_at_max_clock": 2 * fp32_lane_peak_t(clk),
+            "how": "shgo_measure_fma_rate: grid of 2048 threads per SM, each 8 independent FMA chains x 4 x iters; "
+                   "best of 5 timed launches (CUDA events), one warm-up launch before each"}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -963,7 +1081,7 @@ def main():
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
     ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
-    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri"],
+    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri", "peaks"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
     ap.add_argument("--points", type=int, default=100000, help="points of the potential workload")
@@ -991,6 +1109,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-class-batch", action="store_true", help="skip the 64-replica per-class timing")
+    ap.add_argument("--speedup-molecules", type=int, default=16,
+                    help="molecules of the batched workload for the speed-up at 1e-10 in the default line (0 = skip)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args.precision, args.profile_case)
@@ -1006,6 +1126,8 @@ def main():
         return run_coulomb2c(args)
     if args.workload == "eri":
         return run_eri(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     ws, rank, local = _dist()
     if ws > 1:
         import torch

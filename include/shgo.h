@@ -132,8 +132,11 @@ int64_t shgo_basis_launches(const shgo_basis* basis);
  * basis arrays, device nuclei/charges and device output, on the current device.  It never calls
  * cudaMalloc, cudaFree or any allocating CUDA routine: the constant tables, this call's shells and
  * pair lists and its coupling buffer all live in one static device array of
- * SHGO_NOALLOC_SCRATCH_BYTES that the library holds on every GPU that loads it, until the process
- * exits.  A problem whose shells, pairs and coupling buffer do not fit the part of that array left
+ * SHGO_NOALLOC_SCRATCH_BYTES that the library holds on every GPU where it has been called, until the
+ * process exits.  The CUDA driver loads the library's device code lazily (the default since CUDA
+ * 12.2), so the array's memory is committed on a device when the first call runs there: make that
+ * first call before an external pool manager takes the device's free memory.  If the device has no
+ * room for the array at that point the call returns SHGO_ERR_OOM.  A problem whose shells, pairs and coupling buffer do not fit the part of that array left
  * after the tables (about 60 MiB; the 32-atom l <= 6 workload needs 24 MiB) is rejected with
  * SHGO_ERR_INVALID_ARG before any device work, and shgo_last_error() gives the sizes.
  *
@@ -265,6 +268,16 @@ shgo_status shgo_basis_class_stats(const shgo_basis* basis, int64_t n_centers, i
  * rejected (SHGO_ERR_INVALID_ARG). */
 shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const shgo_centers* centers,
                                                 const double* charges, double* out, void* stream, double* ms);
+
+/* Measurement: the fused multiply-add rate of the current GPU's FP64 pipe (precision = SHGO_PREC_FP64) or
+ * FP32 pipe (SHGO_PREC_FP32_BULK or SHGO_PREC_FP32_PLAIN), the denominator of the library's roofline
+ * fractions (the paper states no hardware rate).  A grid of 2048 threads per SM, each running eight
+ * independent multiply-add chains of 4 x iters steps, is launched once to warm up (iters / 16 + 1) and once
+ * timed with CUDA events on `stream`; blocks until done.  flops_per_s receives 2 x FMAs per second of the
+ * timed launch and ms its duration.  Takes a small scratch array from the device's default stream-ordered
+ * pool.  Errors: SHGO_ERR_INVALID_ARG (NULL output, iters outside 1..2^32, unknown precision),
+ * SHGO_ERR_OOM, SHGO_ERR_CUDA. */
+shgo_status shgo_measure_fma_rate(int32_t precision, int64_t iters, void* stream, double* flops_per_s, double* ms);
 
 /* Release a basis and its device memory (synchronises its device).  NULL-safe. */
 void shgo_free(shgo_basis* basis);

@@ -297,6 +297,10 @@ inline void pair_frame(const double* A, const double* B, double* Q) {
   }
 }
 
+// Raises `func`'s dynamic shared-memory limit to `bytes` on the current device, once per (kernel, device)
+// and under a lock: the attribute belongs to one device, so a process on several devices sets it on each.
+cudaError_t ensure_max_dynamic_smem(const void* func, int bytes);
+
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
                                       const double* centers, const double* charges, double* out,

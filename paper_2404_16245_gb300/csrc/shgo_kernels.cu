@@ -1207,11 +1207,7 @@ shgo_status live_counts(const DeviceBasis& db, const std::vector<ClassWork>& wor
 shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                        int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
                        bool gradient, cudaStream_t stream, std::string* err) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_esp_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr = true;
-  }
+  ensure_max_dynamic_smem((const void*)k_esp_adjoint, 227 * 1024);
   const Tables& th = tables_host();
   cudaError_t e =
       cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)std::max<int64_t>(npoints, 1) * (gradient ? 3 : 1), stream);
@@ -1824,17 +1820,7 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
     doff[c + 1] = doff[c] + w.npp * (int64_t)(2 * w.la + 1) * (2 * w.lb + 1) * n_r(w.la + w.lb);
   }
   if (doff[nw] == 0) return SHGO_OK;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  {
-    static std::mutex mu;
-    static bool attr[64] = {};
-    std::lock_guard<std::mutex> lk(mu);
-    if (dev >= 0 && dev < 64 && !attr[dev]) {
-      cudaFuncSetAttribute(k_eri_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      attr[dev] = true;
-    }
-  }
+  ensure_max_dynamic_smem((const void*)k_eri_part, 227 * 1024);
   // class pairs, largest first, and each one's chunk of ket primitive pairs
   struct CP {
     size_t c1, c2;
@@ -1965,11 +1951,7 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
 
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_overlap_block, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr = true;
-  }
+  ensure_max_dynamic_smem((const void*)k_overlap_block, 227 * 1024);
   for (const ClassWork& w : work) {
     if (w.npairs == 0) continue;
     k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), stream>>>(
@@ -1978,6 +1960,20 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
         db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
   }
   return launch_error(err);
+}
+
+cudaError_t ensure_max_dynamic_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;  // (kernel, device) pairs already set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto& d : done)
+    if (d.first == func && d.second == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.emplace_back(func, dev);
+  return e;
 }
 
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf) {

@@ -549,12 +549,8 @@ shgo_status shgo_mlp_forward(const shgo_mlp* mlp, const float* X, int64_t n, flo
 
 static shgo_status run_train(shgo_mlp* mlp, const float* X, const float* T, int64_t n, float under_weight,
                              cudaStream_t s) {
-  static bool attr = false;
   const size_t sm = train_smem();
-  if (!attr) {
-    cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  ensure_max_dynamic_smem((const void*)k_mlp_train, (int)sm);
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, mlp->device);
   const int64_t blocks = std::min<int64_t>((n + kTB - 1) / kTB, (int64_t)nsm * 2);

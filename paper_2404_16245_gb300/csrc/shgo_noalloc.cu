@@ -65,9 +65,15 @@ shgo_status noalloc_setup(int device, NoallocDevice** out, std::string* err) {
     return SHGO_OK;
   }
   void* ptr = nullptr;
+  // The CUDA driver loads this file's module, and with it commits the array's device memory, when the
+  // module is first used on the device, which is here; no room for it then is an out-of-memory error.
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
   if (e != cudaSuccess) {
     *err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();  // not a sticky error: clear it so the caller's next CUDA call does not report it
+      return SHGO_ERR_OOM;
+    }
     return SHGO_ERR_CUDA;
   }
   d.base = static_cast<unsigned char*>(ptr);

@@ -94,6 +94,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_eri_jk.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
+    lib.shgo_measure_fma_rate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, f64p, f64p]
+    lib.shgo_measure_fma_rate.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
     lib.shgo_basis_launches.restype = ctypes.c_int64
     lib.shgo_free.argtypes = [ctypes.c_void_p]
@@ -177,6 +179,15 @@ def shgo_basis_flops(basis, n_centers: int):
     _check(_lib.shgo_basis_flops(ctypes.c_void_p(basis), int(n_centers), _ptr(f, ctypes.c_double),
                                  _ptr(t, ctypes.c_double)))
     return f, t
+
+
+def shgo_measure_fma_rate(precision: int, iters: int, stream=None):
+    """(flops per second, ms) of the FP64 or FP32 multiply-add microbenchmark (one timed launch)."""
+    rate = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(_lib.shgo_measure_fma_rate(int(precision), int(iters), _stream_handle(stream), ctypes.byref(rate),
+                                      ctypes.byref(ms)))
+    return float(rate.value), float(ms.value)
 
 
 def shgo_basis_launches(basis) -> int:
