@@ -130,6 +130,17 @@ constexpr int kNumClasses = (kLmax + 1) * (kLmax + 2) / 2;
 // Offset inside the la block of etab for (ma, l1, m1); nu runs over 2(la - l1) + 1 values.
 int translation_offset(int la, int ma, int l1, int m1);
 
+// The same offset on the device (the translation kernels' inner index).
+__device__ __forceinline__ int translation_offset_dev(int la, int ma, int l1, int m1) {
+  int per_ma = 0, below = 0;
+  for (int k = 0; k <= la; ++k) {
+    const int t = (2 * k + 1) * (2 * (la - k) + 1);
+    per_ma += t;
+    if (k < l1) below += t;
+  }
+  return (ma + la) * per_ma + below + (m1 + l1) * (2 * (la - l1) + 1);
+}
+
 double gaunt_real(int l1, int m1, int l2, int m2, int L, int M);
 double translation_real(int la, int ma, int l1, int m1, int nu);
 void boys_host(int nmax, double T, double* F);
@@ -367,6 +378,84 @@ struct EspArgs {
 cudaError_t launch_esp_fp64(int lam, const EspArgs& args, cudaStream_t stream);
 // Gradient of the potential: args.phi receives 3 values per point; chunks of 16 points.
 cudaError_t launch_esp_grad_fp64(int lam, const EspArgs& args, cudaStream_t stream);
+
+// Arguments of one launch of the fused shell-pair kernel (shgo_fused.cu): steps S2-S5 for the shell
+// pairs items[0 .. nitems) of one Lambda, taken from a work queue.
+struct FusedArgs {
+  const int* items = nullptr;          // shell pairs, by decreasing estimated cost
+  int nitems = 0;
+  unsigned int* qctr = nullptr;        // queue position (zero before the launch)
+  unsigned long long* t0 = nullptr;    // start time of the launch's first block (zero before the launch)
+  int* err = nullptr;                  // set to SHGO_ERR_TIMEOUT when the time limit stops the launch
+  unsigned long long limit_ns = ~0ull; // time limit of the launch (ns; ~0 = none)
+  const int* pair_a = nullptr;
+  const int* pair_b = nullptr;
+  const int64_t* pair_ppoff = nullptr;
+  const int* pair_site = nullptr;
+  const double* site_rot = nullptr;
+  int64_t rot_per = 0;
+  const double* rotd = nullptr;
+  const double* shell_xyz = nullptr;
+  const int* shell_l = nullptr;
+  const int* shell_nprim = nullptr;
+  const int64_t* shell_foff = nullptr;
+  const PPData* ppd = nullptr;
+  MolView mv;
+  const double* centers = nullptr;
+  const double* charges = nullptr;
+  double* out = nullptr;
+  const double* boys_tab = nullptr;
+  const int* rmap = nullptr;           // R layout of this Lambda
+  const double* rnorm = nullptr;       // N_LM per R entry of this Lambda
+  const double* etab = nullptr;
+  const int* eoff = nullptr;
+  const int* g_rowinfo = nullptr;      // Gaunt programs of all classes (class offsets in constant memory)
+  const int* g_grp = nullptr;
+  const GTerm* g_terms = nullptr;
+  int64_t u_doubles = 0;               // union region: nucleus tables / (W and) epilogue matrices
+  int64_t w_doubles = 0;               // separate W region (0: W lives in the union region)
+};
+cudaError_t launch_fused(int lam, const FusedArgs& args, size_t smem, cudaStream_t stream);
+size_t fused_smem(int lam, int64_t u_doubles, int64_t w_doubles);
+void fused_regions(int lam, int la_lo, int la_hi, bool w_alias, int64_t* u_doubles, int64_t* w_doubles);
+// Constants and launch attributes of the fused kernels on the current device.
+cudaError_t fused_setup();
+
+// One launch of the fused kernel in a basis's plan: the items of one Lambda (or, for per-class timing,
+// of one class) at items + off, with its control slot and shared-memory regions.
+struct FusedLaunch {
+  int lam = 0, la_lo = 0, la_hi = 0;
+  int64_t off = 0, n = 0;
+  int slot = 0;
+  int64_t u_doubles = 0, w_doubles = 0;
+  double cost = 0;
+};
+// Control block of a basis's fused launches (device, zeroed before every call): the shared error word,
+// then per slot a queue counter and a start time.
+constexpr size_t kFusedCtrlHead = 16;
+constexpr size_t kFusedSlotBytes = 16;
+struct FusedPlan {
+  std::vector<FusedLaunch> groups;     // one per Lambda present, by decreasing cost
+  std::vector<FusedLaunch> per_class;  // aligned with the basis's class list
+  const int* items = nullptr;          // device
+  unsigned char* ctrl = nullptr;       // device
+  size_t ctrl_bytes = 0;
+};
+// Items and launches of a basis: pairs pa/pb (class order, as the ClassWork list), shell l and primitive
+// counts, nuclei per pair (nc_of_pair, or nullptr when every pair sees the same nuclei).  Returns the item
+// array (groups' items, then the classes') to upload; plan.items and plan.ctrl are set by the caller.
+std::vector<int> build_fused_plan(const std::vector<ClassWork>& work, const std::vector<int>& pa,
+                                  const std::vector<int>& pb, const int32_t* shell_nprim,
+                                  const std::vector<double>* nc_of_pair, FusedPlan& plan);
+// All of V, or with only_class >= 0 that class's shell pairs on `stream`.  Lambda <= fused_lam_max runs the
+// fused work-queue kernel (one launch per Lambda), larger Lambda the two-kernel form per class (coupling
+// blocks in the basis's coupling buffer, then the shell-pair kernel); all of it concurrently on the
+// stream pool, largest first, forked from and joined to `stream`.  The control block is cleared on
+// `stream` first.
+shgo_status launch_fused_call(const DeviceBasis& db, const DeviceTables& dt, const FusedPlan& plan,
+                              const std::vector<ClassWork>& work, int fused_lam_max, const MolView& mv,
+                              const double* centers, const double* charges, double* out,
+                              unsigned long long limit_ns, int only_class, cudaStream_t stream, std::string* err);
 
 // Launches the Lambda = lam instantiation with nucleus chunks of nch (16 or 32) on `grid` warps.
 cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream);

@@ -148,15 +148,6 @@ __host__ __device__ inline int pair_threads(int la, int lb) {
   return nW >= 1024 ? 128 : (nW >= 256 ? 64 : 32);
 }
 
-__device__ __forceinline__ int translation_offset_dev(int la, int ma, int l1, int m1) {
-  int per_ma = 0, below = 0;
-  for (int k = 0; k <= la; ++k) {
-    const int t = (2 * k + 1) * (2 * (la - k) + 1);
-    per_ma += t;
-    if (k < l1) below += t;
-  }
-  return (ma + la) * per_ma + below + (m1 + l1) * (2 * (la - l1) + 1);
-}
 
 // Real rotation matrices D^l(R), l <= lm, R = Q^T (row-major in Rq), for the block's threads:
 // D^0 = 1, D^1 from R, then D^{l+1} from D^l through the harmonic part of u_c S_{l,m'}(u) (the
@@ -726,6 +717,7 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
   if (e == cudaSuccess) e = coupling_fp64_setup();
   if (e == cudaSuccess) e = coupling_f32_setup();
+  if (e == cudaSuccess) e = fused_setup();
   if (e == cudaSuccess) {
     int lof[(kLmax + 1) * (kLmax + 1)];
     for (int l = 0; l <= kLmax; ++l)
@@ -1960,6 +1952,205 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
         db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
   }
   return launch_error(err);
+}
+
+std::vector<int> build_fused_plan(const std::vector<ClassWork>& work, const std::vector<int>& pa,
+                                  const std::vector<int>& pb, const int32_t* shell_nprim,
+                                  const std::vector<double>* nc_of_pair, FusedPlan& plan) {
+  // estimated cost of a shell pair: its primitive pairs x nuclei x R' entries (the nucleus sums dominate)
+  // plus its Gaunt coupling and epilogue
+  auto pair_cost = [&](const ClassWork& w, int q) {
+    const int lam = w.la + w.lb;
+    const double nW = (double)(w.la + 1) * (w.la + 1) * (w.lb + 1) * (w.lb + 1);
+    const double npp = (double)shell_nprim[pa[q]] * shell_nprim[pb[q]];
+    const double nc = nc_of_pair ? (*nc_of_pair)[q] : 32.0;
+    return npp * (nc * (2.0 * n_r(lam) + 4.0 * n_harm(lam)) + 8.0 * nW) + 30.0 * nW;
+  };
+  std::vector<int> items;
+  plan.groups.clear();
+  plan.per_class.assign(work.size(), FusedLaunch{});
+  std::vector<std::vector<size_t>> by_lam(kLamMax + 1);
+  for (size_t c = 0; c < work.size(); ++c) by_lam[work[c].la + work[c].lb].push_back(c);
+  auto add_launch = [&](int lam, const std::vector<size_t>& cls) {
+    FusedLaunch L;
+    L.lam = lam;
+    L.la_lo = kLmax + 1;
+    L.la_hi = -1;
+    L.off = (int64_t)items.size();
+    std::vector<std::pair<double, int>> its;
+    bool single = true;
+    for (size_t c : cls) {
+      const ClassWork& w = work[c];
+      L.la_lo = std::min(L.la_lo, w.la);
+      L.la_hi = std::max(L.la_hi, w.la);
+      for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q) {
+        const double cost = pair_cost(w, q);
+        its.emplace_back(-cost, q);
+        L.cost += cost;
+        if (shell_nprim[pa[q]] * shell_nprim[pb[q]] != 1) single = false;
+      }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (const auto& it : its) items.push_back(it.second);
+    L.n = (int64_t)its.size();
+    fused_regions(lam, L.la_lo, L.la_hi, single, &L.u_doubles, &L.w_doubles);
+    return L;
+  };
+  int slot = 0;
+  for (int lam = 0; lam <= kLamMax; ++lam) {
+    if (by_lam[lam].empty()) continue;
+    FusedLaunch L = add_launch(lam, by_lam[lam]);
+    L.slot = slot++;
+    plan.groups.push_back(L);
+  }
+  for (size_t c = 0; c < work.size(); ++c) {
+    FusedLaunch L = add_launch(work[c].la + work[c].lb, {c});
+    L.slot = slot++;
+    plan.per_class[c] = L;
+  }
+  std::stable_sort(plan.groups.begin(), plan.groups.end(),
+                   [](const FusedLaunch& x, const FusedLaunch& y) { return x.cost > y.cost; });
+  plan.ctrl_bytes = kFusedCtrlHead + kFusedSlotBytes * (size_t)slot;
+  return items;
+}
+
+namespace {
+FusedArgs fused_args(const DeviceBasis& db, const DeviceTables& dt, const FusedPlan& plan, const FusedLaunch& L,
+                     const MolView& mv, const double* centers, const double* charges, double* out,
+                     unsigned long long limit_ns) {
+  const Tables& th = tables_host();
+  FusedArgs a;
+  a.items = plan.items + L.off;
+  a.nitems = (int)L.n;
+  unsigned char* slot = plan.ctrl + kFusedCtrlHead + kFusedSlotBytes * (size_t)L.slot;
+  a.qctr = reinterpret_cast<unsigned int*>(slot);
+  a.t0 = reinterpret_cast<unsigned long long*>(slot + 8);
+  a.err = reinterpret_cast<int*>(plan.ctrl);
+  a.limit_ns = limit_ns;
+  a.pair_a = db.pair_a;
+  a.pair_b = db.pair_b;
+  a.pair_ppoff = db.pair_ppoff;
+  a.pair_site = db.pair_site;
+  a.site_rot = db.site_rot;
+  a.rot_per = rot_block(db.rot_lmax);
+  a.rotd = db.rotd;
+  a.shell_xyz = db.shell_xyz;
+  a.shell_l = db.shell_l;
+  a.shell_nprim = db.shell_nprim;
+  a.shell_foff = db.shell_foff;
+  a.ppd = db.ppd;
+  a.mv = mv;
+  a.centers = centers;
+  a.charges = charges;
+  a.out = out;
+  a.boys_tab = dt.boys;
+  a.rmap = dt.rmap + th.rmap_off[L.lam];
+  a.rnorm = dt.rnorm + th.rmap_off[L.lam];
+  a.etab = dt.etab;
+  a.eoff = dt.eoff;
+  a.g_rowinfo = dt.g_rowinfo;
+  a.g_grp = dt.g_grp;
+  a.g_terms = dt.g_terms;
+  a.u_doubles = L.u_doubles;
+  a.w_doubles = L.w_doubles;
+  return a;
+}
+}  // namespace
+
+shgo_status launch_fused_call(const DeviceBasis& db, const DeviceTables& dt, const FusedPlan& plan,
+                              const std::vector<ClassWork>& work, int fused_lam_max, const MolView& mv,
+                              const double* centers, const double* charges, double* out,
+                              unsigned long long limit_ns, int only_class, cudaStream_t stream, std::string* err) {
+  const Tables& th = tables_host();
+  const std::vector<int64_t> rbases = class_rbases(work);
+  const Launcher L2{db, dt, th, mv, centers, charges, out, nullptr};
+  cudaError_t e = cudaMemsetAsync(plan.ctrl, 0, plan.ctrl_bytes, stream);
+  auto fused_one = [&](const FusedLaunch& L, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    const FusedArgs a = fused_args(db, dt, plan, L, mv, centers, charges, out, limit_ns);
+    return launch_fused(L.lam, a, fused_smem(L.lam, L.u_doubles, L.w_doubles), s);
+  };
+  // the two-kernel form of class c on stream s (region: the stream's share of a bounded coupling buffer)
+  auto two_kernel = [&](size_t c, cudaStream_t s, int region) {
+    if (db.region > 0) {
+      const int64_t rb = (int64_t)region * db.region;
+      for (const ClassWork& ch : class_chunks(work[c], db.h_ppoff, db.region)) {
+        L2.coupling(ch, c, rb, s);
+        L2.pair(ch, c, rb, s);
+      }
+    } else {
+      L2.coupling(work[c], c, rbases[c], s);
+      L2.pair(work[c], c, rbases[c], s);
+    }
+    return cudaGetLastError();
+  };
+  if (e == cudaSuccess && only_class >= 0) {
+    const size_t c = (size_t)only_class;
+    if (work[c].la + work[c].lb <= fused_lam_max) {
+      e = fused_one(plan.per_class[c], stream);
+    } else {
+      set_kernel_attributes();
+      e = two_kernel(c, stream, 0);
+    }
+  } else if (e == cudaSuccess) {
+    // tasks: a fused launch per Lambda <= fused_lam_max, the two kernels of each class above it;
+    // largest first, dealt round-robin over the pool streams
+    struct Task {
+      double cost;
+      int group;  // index into plan.groups, or -1
+      int cls;    // class index for the two-kernel form
+    };
+    std::vector<Task> tasks;
+    for (size_t g = 0; g < plan.groups.size(); ++g) {
+      const FusedLaunch& G = plan.groups[g];
+      if (G.lam <= fused_lam_max) {
+        tasks.push_back({G.cost, (int)g, -1});
+      } else {
+        for (size_t c = 0; c < work.size(); ++c)
+          if (work[c].la + work[c].lb == G.lam) tasks.push_back({plan.per_class[c].cost, -1, (int)c});
+      }
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) { return x.cost > y.cost; });
+    bool any_two = false;
+    for (const Task& t : tasks) any_two = any_two || t.group < 0;
+    if (any_two) set_kernel_attributes();
+    cudaStream_t* pool = nullptr;
+    e = stream_pool(&pool);
+    const int ns = (int)std::min<size_t>(tasks.size(), (size_t)kPoolStreams);
+    auto run_task = [&](const Task& t, cudaStream_t s, int region) {
+      return t.group >= 0 ? fused_one(plan.groups[(size_t)t.group], s) : two_kernel((size_t)t.cls, s, region);
+    };
+    if (e == cudaSuccess && ns == 1) {
+      for (const Task& t : tasks)
+        if (e == cudaSuccess) e = run_task(t, stream, 0);
+    } else if (e == cudaSuccess && ns > 1) {
+      cudaEvent_t fork = nullptr;
+      e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(fork, stream);
+      for (int i = 0; i < ns && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pool[i], fork, 0);
+      for (size_t k = 0; k < tasks.size() && e == cudaSuccess; ++k)
+        e = run_task(tasks[k], pool[k % ns], (int)(k % ns));
+      // join every pool stream that received work, even after a failed launch
+      for (int i = 0; i < ns; ++i) {
+        cudaEvent_t join = nullptr;
+        cudaError_t ej = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (ej == cudaSuccess) ej = cudaEventRecord(join, pool[i]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(stream, join, 0);
+        if (join) cudaEventDestroy(join);
+        if (ej != cudaSuccess) {
+          for (int k = 0; k < ns; ++k) cudaStreamSynchronize(pool[k]);
+          if (e == cudaSuccess) e = ej;
+          break;
+        }
+      }
+      if (fork) cudaEventDestroy(fork);
+    }
+  }
+  if (e != cudaSuccess) {
+    *err = std::string("launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return SHGO_OK;
 }
 
 cudaError_t ensure_max_dynamic_smem(const void* func, int bytes) {

@@ -94,6 +94,10 @@ def _load() -> ctypes.CDLL:
     lib.shgo_eri_jk.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
+    lib.shgo_basis_set_time_limit.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.shgo_basis_set_time_limit.restype = ctypes.c_int
+    lib.shgo_basis_sync.argtypes = [ctypes.c_void_p]
+    lib.shgo_basis_sync.restype = ctypes.c_int
     lib.shgo_measure_fma_rate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, f64p, f64p]
     lib.shgo_measure_fma_rate.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
@@ -179,6 +183,15 @@ def shgo_basis_flops(basis, n_centers: int):
     _check(_lib.shgo_basis_flops(ctypes.c_void_p(basis), int(n_centers), _ptr(f, ctypes.c_double),
                                  _ptr(t, ctypes.c_double)))
     return f, t
+
+
+def shgo_basis_set_time_limit(basis, seconds: float) -> None:
+    _check(_lib.shgo_basis_set_time_limit(ctypes.c_void_p(basis), float(seconds)))
+
+
+def shgo_basis_sync(basis) -> None:
+    """Waits for the basis's last call; raises ShgoError (SHGO_ERR_TIMEOUT) if it hit the time limit."""
+    _check(_lib.shgo_basis_sync(ctypes.c_void_p(basis)))
 
 
 def shgo_measure_fma_rate(precision: int, iters: int, stream=None):
