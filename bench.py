@@ -39,11 +39,11 @@ WORKLOAD = "high-l FP64: 32 atoms / 20 bohr cube, one uncontracted shell per l=0
 # thread-instructions per cycle over the 152 SMs), 2 flops each, at the SM clock.  A DFMA
 # microbenchmark measured 1.20 TFLOP/s; 1.25 TFLOP/s is the nominal figure.
 FP64_DFMA_PER_CLK = 304
-# DRAM traffic of one V of this workload through the fused kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum over the launches of one call, from an ncu capture of the current kernel), or
-# None while no capture of the current kernel exists.
-FUSED_DRAM_BYTES_PER_V = None
-FUSED_DRAM_NOTE = "no ncu capture of the current fused kernel yet"
+# DRAM traffic of the coupling phase of one V of this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum over the 28 coupling launches of one call, from an ncu capture of the current
+# kernel), or None while no capture of the current kernel exists.
+COUPLING_DRAM_BYTES_PER_V = None
+COUPLING_DRAM_NOTE = "no ncu capture of the current coupling kernel yet"
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
@@ -357,8 +357,7 @@ def run_shgo(args, ws, rank, local):
         ph += (a, b)
     ph /= nrep
     f32 = args.precision != "fp64"
-    # FP64: one fused phase (k_shell_pair_fp64 launches, one per Lambda, concurrent), ph[1] = 0
-    names = ["k_coupling_f32", "k_pair_block"] if f32 else ["k_shell_pair_fp64", "-"]
+    names = ["k_coupling_f32" if f32 else "k_coupling_fp64", "k_pair_block"]
     dom = int(np.argmax(ph))
     clk = clocks.get("sm_max_mhz") or 2070.0
     # the pipe's rate measured in this run, right after the timed region (the roofline's denominator)
@@ -378,13 +377,12 @@ def run_shgo(args, ws, rank, local):
                     "peak_derived_nominal": fp32_lane_peak_t(clk), "peak_measurements": pk32,
                     "model_fp32_instructions_per_step": work}
     else:
-        work = float(flops.sum()) if not f32 else flops[dom]
-        achieved = work / (ph[dom] / 1e3) / 1e12
+        achieved = flops[dom] / (ph[dom] / 1e3) / 1e12
         peak = pk64["tflops"]
         roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": FUSED_DRAM_BYTES_PER_V if not f32 else None,
-                    "traffic_note": FUSED_DRAM_NOTE,
+                    "traffic": COUPLING_DRAM_BYTES_PER_V if dom == 0 else None,
+                    "traffic_note": COUPLING_DRAM_NOTE,
                     "peak_source": "measured in this run: shgo_measure_fma_rate FP64 (DFMA, 2048 threads per SM x "
                                    "8 independent chains, CUDA events), best of 3",
                     "peak_derived_nominal": fp64_peak_tflops(clk), "peak_measurements": pk64}

@@ -102,12 +102,10 @@ shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers*
                                     double* out, void* stream);
 
 /* Same computation as shgo_nuclear_attraction, with CUDA events recorded on `stream` around
- * its kernel phases; blocks until they complete and writes their device durations (ms).  FP64 bases
- * run one fused phase: phase_ms[0] = the whole call (every step for every shell pair), phase_ms[1] = 0.
- * FP32-bulk and FP32-plain bases run two: phase_ms[0] = primitive-pair coupling blocks (Gaussian
- * product, Boys, S_LM(C - P), nucleus sums), phase_ms[1] = shell-pair blocks (Gaunt coupling,
- * primitive contraction, translation, write).  For measurement; the arithmetic and launches are those
- * of the plain call. */
+ * the two kernel phases; blocks until they complete and writes their device durations (ms):
+ * phase_ms[0] = primitive-pair coupling blocks (Gaussian product, Boys, S_LM(C - P), nucleus
+ * sums), phase_ms[1] = shell-pair blocks (Gaunt coupling, primitive contraction, translation,
+ * write).  For measurement; the arithmetic and launches are those of the plain call. */
 shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_centers* centers,
                                           const double* charges, double* out, void* stream, double* phase_ms);
 
@@ -121,30 +119,29 @@ shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_ce
  * triples (primitive pairs x nuclei). */
 shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples);
 
-/* Number of kernel launches one shgo_nuclear_attraction call on this basis (or one
- * shgo_nuclear_attraction_batched call on this batch) makes (n > 0). */
+/* Number of kernel launches one shgo_nuclear_attraction call on this basis makes (n > 0). */
 int64_t shgo_basis_launches(const shgo_basis* basis);
 
-/* How an FP64 call runs (shgo_nuclear_attraction, _batched, _screened): one launch per Lambda = la + lb
- * present in the basis (or batch), the launches concurrent, each a persistent grid whose blocks take
- * shell pairs from a device work queue ordered by decreasing estimated cost; a block computes every
- * step for its shell pair (Gaussian product data, Boys values, S_LM(C - P) and nucleus sums for each
- * primitive pair, Gaunt coupling and primitive contraction, translation, rotation, write), so no block
- * waits on another.  FP32-bulk and FP32-plain bases run the two-kernel form (coupling blocks per
- * primitive pair into the basis's coupling buffer, then the shell-pair blocks).
+/* Work queues and the time limit.  A call launches, per (la, lb) class, the coupling kernel (one block
+ * per primitive pair at a time: Boys values, S_LM(C - P) and the nucleus sums) and then the pair kernel
+ * (one block per shell pair at a time: Gaunt coupling, primitive contraction, translation, rotation,
+ * write), the classes concurrently on a pool of streams.  Each launch is a grid of at most a few blocks
+ * per SM whose blocks take their next primitive pair (shell pair) from a device work queue with one atomic
+ * increment; in a batch the queue lists the work of molecules with more nuclei first.  No block waits on
+ * another.
  *
- * Time limit of each launch of the work queue (FP64 bases and batches), default none: before taking a
- * shell pair a block compares the time since its launch's first block started with the limit; once it
- * has passed, the block takes no more work and the call's device status becomes SHGO_ERR_TIMEOUT (the
- * output is then incomplete).  seconds = 0 stops every launch before any work (useful to test a
- * caller's error path); INFINITY removes the limit.  Applies to later calls.  Errors:
- * SHGO_ERR_INVALID_ARG (NULL basis, negative or NaN seconds). */
+ * Time limit of each launch, default none: before taking work a block compares the time since its
+ * launch's first block started with the limit; once it has passed, the block takes no more work and the
+ * call's device status becomes SHGO_ERR_TIMEOUT (the output is then incomplete).  seconds = 0 stops every
+ * launch before any work (useful to exercise a caller's error path without a fault); INFINITY removes the
+ * limit.  Applies to later shgo_nuclear_attraction, _batched and _screened calls on this basis or batch.
+ * Errors: SHGO_ERR_INVALID_ARG (NULL basis, negative or NaN seconds). */
 shgo_status shgo_basis_set_time_limit(shgo_basis* basis, double seconds);
 
-/* Waits for the basis's last call and returns its device-side status: SHGO_OK, or SHGO_ERR_TIMEOUT when
- * a launch of that call reached the time limit (shgo_basis_set_time_limit).  Reading the status clears
- * it.  For FP32-bulk and FP32-plain bases, which have no device-side status, it synchronises the device
- * and returns SHGO_OK.  Errors: SHGO_ERR_INVALID_ARG (NULL basis), SHGO_ERR_CUDA. */
+/* Waits for the basis's last call that launched kernels and returns the device-side status of the calls
+ * since the previous shgo_basis_sync: SHGO_OK, or SHGO_ERR_TIMEOUT when a launch of one of them reached the
+ * time limit (shgo_basis_set_time_limit).  Reading the status clears it.  Errors: SHGO_ERR_INVALID_ARG
+ * (NULL basis), SHGO_ERR_CUDA. */
 shgo_status shgo_basis_sync(const shgo_basis* basis);
 
 /* ---------------------------------------------------------------------------------------------
@@ -199,14 +196,13 @@ int64_t shgo_batch_out_size(const shgo_basis* batch);
 /* V_m for every molecule (Eq. 11 per molecule with its own nuclei).  centers [sum n_c][3] and
  * charges [sum n_c] are device arrays in molecule order; out is a device array of
  * shgo_batch_out_size doubles, fully overwritten.
- * FP64 batches run the fused work-queue launches (see shgo_basis_set_time_limit): the first call
- * launches them directly, the next captures the whole call into a CUDA graph on an internal stream, and
- * later calls with the same centers/charges/out pointers and time limit replay it with one
- * cudaGraphLaunch on `stream` (new pointers or a new limit re-capture).  FP32-bulk batches: the first
- * call tunes, per (la, lb) class, the nucleus-chunk size of the coupling kernel and the threads per
- * block of the pair kernel by timing them on this work (it synchronises `stream`; its output is exact),
- * then capture and replay as above.  Calls on one batch must be ordered, and batched calls on one
- * device should come from one host thread at a time. */
+ * The first call on a batch tunes, per (la, lb) class, the nucleus-chunk size of the coupling
+ * kernel and the threads per block of the pair kernel by timing them on this work (it
+ * synchronises `stream`; its output is exact).  The next call captures the whole launch sequence
+ * into a CUDA graph on an internal stream; later calls with the same centers/charges/out pointers and
+ * time limit replay it with one cudaGraphLaunch on `stream` (new pointers or a new limit re-capture).
+ * Calls on one batch must be ordered, and batched calls on one device should come from one host thread
+ * at a time. */
 shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* centers, const double* charges,
                                             double* out, void* stream);
 
@@ -290,10 +286,9 @@ shgo_status shgo_basis_class_stats(const shgo_basis* basis, int64_t n_centers, i
 
 /* V as shgo_nuclear_attraction (or, for a batch, shgo_nuclear_attraction_batched with centers->n =
  * all its nuclei) computes it, but with the classes run one after another on `stream` and the
- * device time of each class written to ms[2 c], ms[2 c + 1] (host array of 2 x nclasses): for FP64
- * bases the fused kernel over the class's shell pairs in ms[2 c] and 0 in ms[2 c + 1]; otherwise the
- * class's coupling and pair kernels.  Blocks until done.  FP32 bases whose coupling buffer is split
- * into regions are rejected (SHGO_ERR_INVALID_ARG). */
+ * device time of each class's coupling and pair kernels written to ms[2 c], ms[2 c + 1] (host array
+ * of 2 x nclasses).  Blocks until done.  Bases whose coupling buffer is split into regions are
+ * rejected (SHGO_ERR_INVALID_ARG). */
 shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const shgo_centers* centers,
                                                 const double* charges, double* out, void* stream, double* ms);
 

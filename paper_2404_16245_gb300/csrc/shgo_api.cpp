@@ -80,14 +80,10 @@ struct shgo_basis {
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
-  // fused work-queue path (FP64): launch plan, time limit per launch, device error word read back into
-  // pinned host memory after every call, and the event that marks that copy
-  FusedPlan fplan;
-  unsigned long long limit_ns = ~0ull;
-  int fused_lam_max = kLamMax;  // Lambda above this runs the two-kernel form
+  // device status of the last call: the control block's error word, copied after every call into
+  // pinned host memory, and the event that marks that copy (shgo_basis_sync)
   int* h_err = nullptr;
   cudaEvent_t done_ev = nullptr;
-  bool uses_fused() const { return d.precision == SHGO_PREC_FP64; }
 };
 
 namespace {
@@ -148,6 +144,31 @@ cudaError_t pool_alloc(int device, void** p, size_t bytes) {
   return cudaMallocFromPoolAsync(p, bytes, pool, 0);
 }
 
+// Pinned host words for the bases' device status, carved from page-locked slabs that live until the
+// process exits (pinning memory per basis would cost more than building the basis).
+std::mutex g_pin_mu;
+std::vector<int*> g_pin_free;
+
+cudaError_t pinned_status_word(int** p) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    constexpr int kSlab = 1024;
+    int* slab = nullptr;
+    const cudaError_t e = cudaMallocHost((void**)&slab, sizeof(int) * kSlab);
+    if (e != cudaSuccess) return e;
+    for (int i = kSlab - 1; i >= 0; --i) g_pin_free.push_back(slab + i);
+  }
+  *p = g_pin_free.back();
+  g_pin_free.pop_back();
+  **p = 0;
+  return cudaSuccess;
+}
+
+void release_status_word(int* p) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
 void release(shgo_basis* b) {
   if (!b) return;
   int prev = 0;
@@ -162,7 +183,7 @@ void release(shgo_basis* b) {
   cudaFree(b->scr_clist);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   if (b->done_ev) cudaEventDestroy(b->done_ev);
-  if (b->h_err) cudaFreeHost(b->h_err);
+  if (b->h_err) release_status_word(b->h_err);
   for (void* p : b->allocations) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
   cudaSetDevice(prev);
@@ -392,14 +413,37 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     rlen = b->d.region * kPoolStreamsPublic;
   }
   b->d.h_ppoff = b->h_ppoff.data();
-  std::vector<int> fitems;
-  {
-    std::vector<double> nc_pair;
-    if (batch) {
-      nc_pair.resize(pa.size());
-      for (size_t q = 0; q < pa.size(); ++q) nc_pair[q] = (double)b->mol_nc[pmol[q]];
+  // Work-queue orders of a batch: inside each class, the primitive pairs and shell pairs of molecules with
+  // more nuclei first (their cost per primitive pair grows with the nucleus count); a single molecule's
+  // work is uniform per class and keeps index order.
+  std::vector<int> cp_items, pr_items;
+  if (batch) {
+    std::vector<int> mol_order(nm);
+    for (int m = 0; m < nm; ++m) mol_order[m] = m;
+    std::stable_sort(mol_order.begin(), mol_order.end(),
+                     [&](int x, int y) { return b->mol_nc[x] > b->mol_nc[y]; });
+    std::vector<int> rank(nm);
+    for (int k = 0; k < nm; ++k) rank[mol_order[k]] = k;
+    cp_items.resize(ppcount);
+    pr_items.resize(pa.size());
+    for (const ClassWork& w : b->work) {
+      // counting sort of the class's pairs by molecule rank (pairs of one molecule are contiguous)
+      std::vector<int64_t> pair_start(nm + 1, 0), pp_start(nm + 1, 0);
+      for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q) {
+        pair_start[rank[pmol[q]] + 1] += 1;
+        pp_start[rank[pmol[q]] + 1] += b->h_ppoff[q + 1] - b->h_ppoff[q];
+      }
+      for (int k = 0; k < nm; ++k) {
+        pair_start[k + 1] += pair_start[k];
+        pp_start[k + 1] += pp_start[k];
+      }
+      for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q) {
+        const int r = rank[pmol[q]];
+        pr_items[w.pair_base + pair_start[r]++] = q - w.pair_base;
+        const int64_t p0 = b->h_ppoff[q], p1 = b->h_ppoff[q + 1];
+        for (int64_t x = p0; x < p1; ++x) cp_items[w.pp_base + pp_start[r]++] = (int)(x - w.pp_base);
+      }
     }
-    fitems = build_fused_plan(b->work, pa, pb, n_prim, batch ? &nc_pair : nullptr, b->fplan);
   }
 
   // one host image of every per-basis array, one device arena (image + device-built data), one copy
@@ -428,10 +472,11 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     o_out = im.put(b->mol_out);
     o_ld = im.put(b->mol_nbf);
   }
-  const size_t o_fitems = im.put(fitems);
+  const size_t o_cpit = batch ? im.put(cp_items) : 0;
+  const size_t o_prit = batch ? im.put(pr_items) : 0;
   const size_t host_bytes = im.size();
   const size_t o_ppd = im.reserve(sizeof(PPData) * (size_t)ppcount);
-  const size_t o_fctrl = im.reserve(b->fplan.ctrl_bytes);
+  const size_t o_ctrl = im.reserve(ctrl_bytes(b->work.size()));
   const size_t o_rotd = im.reserve(sizeof(double) * (size_t)rotlen);
   shgo_status st = SHGO_OK;
   unsigned char* base = nullptr;
@@ -467,8 +512,11 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     b->d.pp_ij = reinterpret_cast<int*>(base + o_ppij);
     b->d.ppd = reinterpret_cast<PPData*>(base + o_ppd);
     b->d.rotd = reinterpret_cast<double*>(base + o_rotd);
-    b->fplan.items = reinterpret_cast<const int*>(base + o_fitems);
-    b->fplan.ctrl = base + o_fctrl;
+    b->d.ctrl = base + o_ctrl;
+    if (batch) {
+      b->d.cp_items = reinterpret_cast<const int*>(base + o_cpit);
+      b->d.pr_items = reinterpret_cast<const int*>(base + o_prit);
+    }
     if (batch) {
       b->pair_mol = reinterpret_cast<int*>(base + o_pmol);
       b->mol_c0_d = reinterpret_cast<int64_t*>(base + o_c0);
@@ -477,12 +525,11 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
       b->mol_ld_d = reinterpret_cast<int64_t*>(base + o_ld);
     }
   }
-  if (st == SHGO_OK && (cudaMallocHost((void**)&b->h_err, sizeof(int)) != cudaSuccess ||
+  if (st == SHGO_OK && (pinned_status_word(&b->h_err) != cudaSuccess ||
                         cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming) != cudaSuccess)) {
     st = SHGO_ERR_CUDA;
     err = "cannot create the status word or its event";
   }
-  if (st == SHGO_OK) *b->h_err = 0;
   if (batch && st == SHGO_OK && cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     st = SHGO_ERR_CUDA;
     err = "cannot create the capture stream";
@@ -575,24 +622,16 @@ void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* 
 }  // namespace
 
 namespace {
-// Kernel view of a basis's molecules (one molecule: nuclei of the call; a batch: per-molecule tables).
-MolView basis_view(const shgo_basis* b, int64_t ncenters) {
-  MolView mv;
-  if (b->batch) {
-    mv.pair_mol = b->pair_mol;
-    mv.c0 = b->mol_c0_d;
-    mv.nc = b->mol_nc_d;
-    mv.out_off = b->mol_out_d;
-    mv.ld = b->mol_ld_d;
-  }
-  mv.ncenters = ncenters;
-  mv.nbf = b->nbf;
-  return mv;
+// After a call that launched kernels: the device error word into the basis's pinned status word, and the
+// event that marks the copy (read by shgo_basis_sync).
+cudaError_t status_readback(const shgo_basis* b, cudaStream_t s) {
+  return cudaMemcpyAsync(b->h_err, b->d.ctrl, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
-
-// After a call on the fused path: the device error word into pinned host memory (read by shgo_basis_sync).
-cudaError_t fused_readback(const shgo_basis* b, cudaStream_t s) {
-  return cudaMemcpyAsync(b->h_err, b->fplan.ctrl, sizeof(int), cudaMemcpyDeviceToHost, s);
+// A call without a time limit cannot change the error word, so only limited calls copy it.
+cudaError_t finish_call(const shgo_basis* b, cudaStream_t s) {
+  cudaError_t e = b->d.limit_ns != ~0ull ? status_readback(b, s) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaEventRecord(b->done_ev, s);
+  return e;
 }
 }  // namespace
 
@@ -646,60 +685,16 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
   std::string err;
   shgo_status st = SHGO_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (batch->uses_fused()) {
-    // fused work-queue path: the first call launches directly, the next captures the call (clearing the
-    // control block, every launch, the status read-back) into a CUDA graph that later calls replay
-    const void* key[4] = {centers, charges, out, reinterpret_cast<const void*>((uintptr_t)batch->limit_ns)};
-    if (!batch->tuned) {
-      st = launch_fused_call(batch->d, *batch->tabs, batch->fplan, batch->work, batch->fused_lam_max, mv, centers, charges, out, batch->limit_ns, -1, s,
-                             &err);
-      if (st == SHGO_OK && fused_readback(batch, s) != cudaSuccess) {
-        st = SHGO_ERR_CUDA;
-        err = "status read-back failed";
-      }
-      if (st == SHGO_OK) batch->tuned = true;
-    } else {
-      if (!batch->graph || std::memcmp(key, batch->graph_key, sizeof(key)) != 0) {
-        if (batch->graph) {
-          cudaGraphExecDestroy(batch->graph);
-          batch->graph = nullptr;
-        }
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(batch->capture_stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-          st = launch_fused_call(batch->d, *batch->tabs, batch->fplan, batch->work, batch->fused_lam_max, mv, centers, charges, out, batch->limit_ns, -1,
-                                 batch->capture_stream, &err);
-          if (st == SHGO_OK) e = fused_readback(batch, batch->capture_stream);
-          const cudaError_t e2 = cudaStreamEndCapture(batch->capture_stream, &g);
-          if (e == cudaSuccess) e = e2;
-        }
-        if (e == cudaSuccess && st == SHGO_OK) e = cudaGraphInstantiate(&batch->graph, g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess || st != SHGO_OK) {
-          if (st == SHGO_OK) {
-            st = SHGO_ERR_CUDA;
-            err = std::string("graph capture: ") + cudaGetErrorString(e);
-          }
-          batch->graph = nullptr;
-        } else {
-          std::memcpy(batch->graph_key, key, sizeof(key));
-        }
-      }
-      if (st == SHGO_OK) {
-        const cudaError_t e = cudaGraphLaunch(batch->graph, s);
-        if (e != cudaSuccess) {
-          st = SHGO_ERR_CUDA;
-          err = std::string("graph launch: ") + cudaGetErrorString(e);
-        }
-      }
-    }
-    if (st == SHGO_OK) cudaEventRecord(batch->done_ev, s);
-  } else if (!batch->tuned) {
+  if (!batch->tuned) {
     // first call: tune the launch shape of every class on the real work (its output is exact)
     st = autotune_batched(batch->d, *batch->tabs, batch->work, mv, centers, charges, out, &batch->tune, s, &err);
+    if (st == SHGO_OK && batch->d.limit_ns != ~0ull && status_readback(batch, s) != cudaSuccess) {
+      st = SHGO_ERR_CUDA;
+      err = "status read-back failed";
+    }
     if (st == SHGO_OK) batch->tuned = true;
   } else {
-    const void* key[4] = {centers, charges, out, nullptr};
+    const void* key[4] = {centers, charges, out, reinterpret_cast<const void*>((uintptr_t)batch->d.limit_ns)};
     if (!batch->graph || std::memcmp(key, batch->graph_key, sizeof(key)) != 0) {
       // capture the whole batch (all classes, both kernels, fork/join over the stream pool) once
       if (batch->graph) {
@@ -711,7 +706,9 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
       if (e == cudaSuccess) {
         st = launch_batched(batch->d, *batch->tabs, batch->work, mv, npp_cent, centers, charges, out, &batch->tune,
                             batch->capture_stream, &err);
-        e = cudaStreamEndCapture(batch->capture_stream, &g);
+        if (st == SHGO_OK && batch->d.limit_ns != ~0ull) e = status_readback(batch, batch->capture_stream);
+        const cudaError_t e2 = cudaStreamEndCapture(batch->capture_stream, &g);
+        if (e == cudaSuccess) e = e2;
       }
       if (e == cudaSuccess && st == SHGO_OK) e = cudaGraphInstantiate(&batch->graph, g, 0);
       if (g) cudaGraphDestroy(g);
@@ -733,6 +730,7 @@ shgo_status shgo_nuclear_attraction_batched(shgo_basis* batch, const double* cen
       }
     }
   }
+  if (st == SHGO_OK) cudaEventRecord(batch->done_ev, s);
   if (prev != batch->device) cudaSetDevice(prev);
   if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;
@@ -879,20 +877,11 @@ shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers*
   cudaGetDevice(&prev);
   if (prev != basis->device) cudaSetDevice(basis->device);
   std::string err;
-  shgo_status st = SHGO_OK;
-  const cudaStream_t s = (cudaStream_t)stream;
-  if (basis->uses_fused() && basis->nbf > 0 && centers->n > 0) {
-    st = launch_fused_call(basis->d, *basis->tabs, basis->fplan, basis->work, basis->fused_lam_max, basis_view(basis, centers->n), centers->xyz, charges,
-                           out, basis->limit_ns, -1, s, &err);
-    cudaError_t e = st == SHGO_OK ? fused_readback(basis, s) : cudaSuccess;
-    if (e == cudaSuccess && st == SHGO_OK) e = cudaEventRecord(basis->done_ev, s);
-    if (e != cudaSuccess && st == SHGO_OK) {
-      st = SHGO_ERR_CUDA;
-      err = std::string("status read-back: ") + cudaGetErrorString(e);
-    }
-  } else {
-    st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n, centers->xyz, charges,
-                                   out, s, &err);
+  shgo_status st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
+                                             centers->xyz, charges, out, (cudaStream_t)stream, &err);
+  if (st == SHGO_OK && basis->nbf > 0 && centers->n > 0 && finish_call(basis, (cudaStream_t)stream) != cudaSuccess) {
+    st = SHGO_ERR_CUDA;
+    err = "status read-back failed";
   }
   if (prev != basis->device) cudaSetDevice(prev);
   if (st != SHGO_OK) return fail(st, err);
@@ -903,7 +892,7 @@ shgo_status shgo_basis_set_time_limit(shgo_basis* basis, double seconds) {
   g_last_error.clear();
   if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
   if (!(seconds >= 0)) return fail(SHGO_ERR_INVALID_ARG, "time limit must be >= 0 (infinity = none)");
-  basis->limit_ns = std::isinf(seconds) || seconds >= 1.8e10 ? ~0ull : (unsigned long long)(seconds * 1e9);
+  basis->d.limit_ns = std::isinf(seconds) || seconds >= 1.8e10 ? ~0ull : (unsigned long long)(seconds * 1e9);
   return SHGO_OK;
 }
 
@@ -913,15 +902,20 @@ shgo_status shgo_basis_sync(const shgo_basis* basis) {
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != basis->device) cudaSetDevice(basis->device);
-  const cudaError_t e = basis->uses_fused() ? cudaEventSynchronize(basis->done_ev) : cudaDeviceSynchronize();
+  const cudaError_t e = cudaEventSynchronize(basis->done_ev);
   if (prev != basis->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return fail(SHGO_ERR_CUDA, std::string("waiting for the basis: ") + cudaGetErrorString(e));
-  if (basis->uses_fused() && *basis->h_err != 0) {
-    const int v = *basis->h_err;
+  const int v = *basis->h_err;
+  if (v != 0) {
+    // clear the word on both sides; the basis's last call has completed, and calls on one basis are ordered
     *basis->h_err = 0;
+    if (prev != basis->device) cudaSetDevice(basis->device);
+    const cudaError_t ec = cudaMemset(basis->d.ctrl, 0, sizeof(int));
+    if (prev != basis->device) cudaSetDevice(prev);
+    if (ec != cudaSuccess) return fail(SHGO_ERR_CUDA, std::string("clearing the status: ") + cudaGetErrorString(ec));
     if (v == SHGO_ERR_TIMEOUT)
       return fail(SHGO_ERR_TIMEOUT, "a launch of the last call reached the basis's time limit; its output is incomplete");
-    return fail(SHGO_ERR_CUDA, "device error word " + std::to_string(v));
+    return fail(SHGO_ERR_CUDA, "device status word " + std::to_string(v));
   }
   return SHGO_OK;
 }
@@ -939,20 +933,9 @@ shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_ce
   cudaEvent_t ev[3];
   for (auto& e : ev) cudaEventCreate(&e);
   std::string err;
-  shgo_status st = SHGO_OK;
-  if (basis->uses_fused() && basis->nbf > 0 && centers->n > 0) {
-    // one fused phase: phase_ms[0] is the whole call, phase_ms[1] = 0
-    cudaEventRecord(ev[0], (cudaStream_t)stream);
-    st = launch_fused_call(basis->d, *basis->tabs, basis->fplan, basis->work, basis->fused_lam_max, basis_view(basis, centers->n), centers->xyz, charges,
-                           out, basis->limit_ns, -1, (cudaStream_t)stream, &err);
-    cudaEventRecord(ev[1], (cudaStream_t)stream);
-    cudaEventRecord(ev[2], (cudaStream_t)stream);
-    if (st == SHGO_OK && fused_readback(basis, (cudaStream_t)stream) == cudaSuccess)
-      cudaEventRecord(basis->done_ev, (cudaStream_t)stream);
-  } else {
-    st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n, centers->xyz, charges,
-                                   out, (cudaStream_t)stream, &err, ev);
-  }
+  shgo_status st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
+                                             centers->xyz, charges, out, (cudaStream_t)stream, &err, ev);
+  if (st == SHGO_OK && basis->nbf > 0 && centers->n > 0) finish_call(basis, (cudaStream_t)stream);
   if (st == SHGO_OK) {
     cudaError_t e = cudaEventSynchronize(ev[2]);
     float t0 = 0, t1 = 0;
@@ -971,17 +954,7 @@ shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_ce
   return SHGO_OK;
 }
 
-int64_t shgo_basis_launches(const shgo_basis* basis) {
-  if (!basis) return -1;
-  if (basis->uses_fused()) {
-    int64_t n = 0;
-    for (const FusedLaunch& L : basis->fplan.groups) n += L.n > 0 && L.lam <= basis->fused_lam_max ? 1 : 0;
-    for (const ClassWork& w : basis->work)
-      if (w.la + w.lb > basis->fused_lam_max) n += (w.npp > 0 ? 1 : 0) + (w.npairs > 0 ? 1 : 0);
-    return basis->nbf > 0 || basis->batch ? n : 0;
-  }
-  return launches_per_call(basis->work, basis->nbf);
-}
+int64_t shgo_basis_launches(const shgo_basis* basis) { return basis ? launches_per_call(basis->work, basis->nbf) : -1; }
 
 shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples) {
   if (!basis || !flops || !triples || n_centers < 0) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
@@ -1031,8 +1004,7 @@ shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const s
   if (!centers || centers->n < 0) return fail(SHGO_ERR_INVALID_ARG, "centers is NULL or negative count");
   if (centers->n > 0 && (!centers->xyz || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
   if ((basis->batch ? basis->out_size : basis->nbf) > 0 && !out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
-  if (!basis->uses_fused() && basis->d.region > 0)
-    return fail(SHGO_ERR_INVALID_ARG, "class timing needs the whole coupling buffer");
+  if (basis->d.region > 0) return fail(SHGO_ERR_INVALID_ARG, "class timing needs the whole coupling buffer");
   if (basis->batch && centers->n != basis->total_centers)
     return fail(SHGO_ERR_INVALID_ARG, "a batch takes all its molecules' nuclei");
   int prev = 0;
@@ -1049,38 +1021,8 @@ shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const s
   mv.ncenters = centers->n;
   mv.nbf = basis->nbf;
   std::string err;
-  shgo_status st = SHGO_OK;
-  if (basis->uses_fused()) {
-    // each class alone through the fused kernel: ms[2 c] its time, ms[2 c + 1] = 0
-    const cudaStream_t s = (cudaStream_t)stream;
-    const size_t nc = basis->work.size();
-    std::vector<cudaEvent_t> ev(nc + 1, nullptr);
-    cudaError_t e = cudaSuccess;
-    for (auto& x : ev)
-      if (e == cudaSuccess) e = cudaEventCreate(&x);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
-    for (size_t c = 0; c < nc && e == cudaSuccess && st == SHGO_OK; ++c) {
-      st = launch_fused_call(basis->d, *basis->tabs, basis->fplan, basis->work, basis->fused_lam_max, mv, centers->xyz, charges, out, basis->limit_ns,
-                             (int)c, s, &err);
-      if (st == SHGO_OK) e = cudaEventRecord(ev[c + 1], s);
-    }
-    if (e == cudaSuccess && st == SHGO_OK) e = cudaEventSynchronize(ev[nc]);
-    for (size_t c = 0; c < nc && e == cudaSuccess && st == SHGO_OK; ++c) {
-      float t = 0.f;
-      e = cudaEventElapsedTime(&t, ev[c], ev[c + 1]);
-      ms[2 * c] = t;
-      ms[2 * c + 1] = 0.0;
-    }
-    for (auto& x : ev)
-      if (x) cudaEventDestroy(x);
-    if (e != cudaSuccess && st == SHGO_OK) {
-      st = SHGO_ERR_CUDA;
-      err = std::string("class timing: ") + cudaGetErrorString(e);
-    }
-  } else {
-    st = launch_class_timed(basis->d, *basis->tabs, basis->work, mv, centers->xyz, charges, out, (cudaStream_t)stream,
-                            ms, &err);
-  }
+  const shgo_status st = launch_class_timed(basis->d, *basis->tabs, basis->work, mv, centers->xyz, charges, out,
+                                            (cudaStream_t)stream, ms, &err);
   if (prev != basis->device) cudaSetDevice(prev);
   if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;
@@ -1250,16 +1192,9 @@ shgo_status shgo_nuclear_attraction_screened(shgo_basis* basis, const double* ce
   mv.clist_off = basis->scr_clist_off;
   const double per_pair = basis->npairs > 0 ? (double)basis->scr_ntrip / (double)basis->npairs : 0.0;
   std::string err;
-  shgo_status st = SHGO_OK;
-  if (basis->uses_fused() && (basis->batch ? basis->out_size : basis->nbf) > 0) {
-    st = launch_fused_call(basis->d, *basis->tabs, basis->fplan, basis->work, basis->fused_lam_max, mv, centers, charges, out, basis->limit_ns, -1,
-                           (cudaStream_t)stream, &err);
-    if (st == SHGO_OK && fused_readback(basis, (cudaStream_t)stream) == cudaSuccess)
-      cudaEventRecord(basis->done_ev, (cudaStream_t)stream);
-  } else {
-    st = launch_batched(basis->d, *basis->tabs, basis->work, mv, per_pair, centers, charges, out,
-                        basis->tuned && !basis->tune.empty() ? &basis->tune : nullptr, (cudaStream_t)stream, &err);
-  }
+  shgo_status st = launch_batched(basis->d, *basis->tabs, basis->work, mv, per_pair, centers, charges, out,
+                                  basis->tuned ? &basis->tune : nullptr, (cudaStream_t)stream, &err);
+  if (st == SHGO_OK) finish_call(basis, (cudaStream_t)stream);
   if (prev != basis->device) cudaSetDevice(prev);
   if (st != SHGO_OK) return fail(st, err);
   return SHGO_OK;

@@ -38,14 +38,16 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
   double* racc = Btab + Sh::nB * CS;
   double* scl = racc + nR;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int64_t w = blockIdx.x; w < A.npp; w += gridDim.x) {
+  __shared__ long long s_next[2];
+  __shared__ unsigned long long s_t0;
+  wq_for_each(A.q, A.npp, s_next, &s_t0, [&](long long w) {
     const int64_t q = A.pp_base + w;
     const int pr = A.pp_pair[q];
     const int a = A.pair_a[pr];
     const PPData pd = A.ppd[q];
     // primitive pairs with a zero prefactor (K_AB of Eq. 5 underflowed, or the pair is below the
     // per-basis bound) are skipped by the pair kernel too, so their coupling block is not needed
-    if (pd.pref == 0.0) continue;
+    if (pd.pref == 0.0) return;
     // C - P = (C - A) - (beta/p)(B - A), in the pair frame where B - A is along z
     const double Ax = A.shell_xyz[3 * a], Ay = A.shell_xyz[3 * a + 1], Az = A.shell_xyz[3 * a + 2];
     double Q[9];
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
     __syncthreads();
     double* out = A.rbuf + A.rbase + w * (int64_t)nR;
     for (int e = tid; e < nR; e += 64) out[e] = racc[e] * (scl[(__ldg(A.rmap + e) >> 24) & 0xff] * __ldg(A.rnorm + e));
-  }
+    });
 }
 
 // Electrostatic potential (adjoint of the coupling): for a chunk of NCH points and a range of primitive
@@ -425,14 +427,13 @@ cudaError_t coupling_fp64_setup() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_boys, &boys_const_host(), sizeof(BoysConst));
   for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam)
     for (int nch : {16, 32}) {
-      e = cudaFuncSetAttribute(coupling_kernel(lam, nch), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      e = set_max_dynamic_smem((const void*)coupling_kernel(lam, nch));
       if (e != cudaSuccess) break;
     }
   for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam) {
-    e = cudaFuncSetAttribute(esp_kernel_at(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = set_max_dynamic_smem((const void*)esp_kernel_at(lam, Lams{}));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(esp_grad_kernel_at(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               227 * 1024);
+      e = set_max_dynamic_smem((const void*)esp_grad_kernel_at(lam, Lams{}));
   }
   return e;
 }

@@ -522,12 +522,14 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
   const int a1 = wid == 0 ? cb1 : (wid == 1 ? cb2 : (wid == 2 ? cb3 : LAM + 1));
   const int L0 = wid == 0 ? 0 : (wid == 1 ? rb1 : (wid == 2 ? rb2 : rb3));
   const int L1 = wid == 0 ? rb1 : (wid == 1 ? rb2 : (wid == 2 ? rb3 : LAM + 1));
-  for (int64_t w = blockIdx.x; w < A.npp; w += gridDim.x) {
+  __shared__ long long s_next[2];
+  __shared__ unsigned long long s_t0;
+  wq_for_each(A.q, A.npp, s_next, &s_t0, [&](long long w) {
     const int64_t q = A.pp_base + w;
     const int pr = A.pp_pair[q];
     const PPData pd = A.ppd[q];
     // primitive pairs with a zero prefactor are skipped by the pair kernel too
-    if (pd.pref == 0.0) continue;
+    if (pd.pref == 0.0) return;
     __syncthreads();  // the previous primitive pair is done with racc, the scales and geo
     if (tid < 3) {
       geo[tid] = to_pair<FF>(A.shell_xyz[3 * A.pair_a[pr] + tid]);
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
       }
       out[e] = v * sclb[(code >> 12) & 0xfff];
     }
-  }
+    });
 }
 
 using Kernel = void (*)(CouplingArgs);
@@ -710,10 +712,8 @@ cudaError_t coupling_f32_setup() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(f_inv_int, ii, sizeof(ii));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(f_half_sqrt_pi, &hsp, sizeof(hsp));
   for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam) {
-    e = cudaFuncSetAttribute(kernel_at<true>(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kernel_at<false>(lam, Lams{}), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               227 * 1024);
+    e = set_max_dynamic_smem((const void*)kernel_at<true>(lam, Lams{}));
+    if (e == cudaSuccess) e = set_max_dynamic_smem((const void*)kernel_at<false>(lam, Lams{}));
   }
   return e;
 }

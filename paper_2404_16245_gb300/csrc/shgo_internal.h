@@ -215,6 +215,88 @@ __device__ __forceinline__ void mol_output(const MolView& mv, int pr, int64_t& b
   }
 }
 
+// Work queue of one launch of the coupling or pair kernel.  A block takes its next primitive pair (or
+// shell pair) with one atomic increment of qctr; items, when set, lists the launch's work in decreasing
+// estimated cost (local indices), otherwise the work is taken in index order.  With qctr == nullptr the
+// blocks stride over the work instead (uniform work, where a queue would only add the atomic's latency).  Time limit: t0 receives the start time of the launch's first
+// block; before taking work a block that finds limit_ns passed since then (or a limit of 0) takes no
+// more and sets *err = SHGO_ERR_TIMEOUT.  t0 == nullptr disables the limit.  No block waits on another.
+struct WorkQueue {
+  unsigned long long* qctr = nullptr;
+  unsigned long long* t0 = nullptr;
+  int* err = nullptr;
+  const int* items = nullptr;
+  unsigned long long limit_ns = ~0ull;
+};
+
+__device__ __forceinline__ unsigned long long wq_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0 of a block: records (or reads) the launch's start time into *t0_block.
+__device__ __forceinline__ void wq_begin(const WorkQueue& q, unsigned long long* t0_block) {
+  if (threadIdx.x == 0 && q.t0) {
+    const unsigned long long now = wq_clock();
+    const unsigned long long old = atomicCAS(q.t0, 0ull, now);
+    *t0_block = old == 0ull ? now : old;
+  }
+}
+
+// Thread 0 of a block: index of its next piece of work among n, or -1 when the queue is empty or the
+// time limit has passed.  `it` counts the block's iterations (used by the strided order).
+__device__ __forceinline__ long long wq_take(const WorkQueue& q, long long n, long long it, unsigned long long t0) {
+  if (q.t0 && q.limit_ns != ~0ull) {
+    const unsigned long long now = wq_clock();
+    if (q.limit_ns == 0ull || (now > t0 && now - t0 >= q.limit_ns)) {
+      atomicExch(q.err, (int)SHGO_ERR_TIMEOUT);
+      return -1;
+    }
+  }
+  const long long k = q.qctr ? (long long)atomicAdd(q.qctr, 1ull) : (long long)blockIdx.x + it * (long long)gridDim.x;
+  if (k >= n) return -1;
+  return q.items ? (long long)q.items[k] : k;
+}
+
+// Runs body(w) for this block's share of the n work items of a launch.  Without a queue or a time limit
+// the blocks stride over the work (body must start with a block-wide barrier before it reuses shared
+// memory, and may return early only uniformly over the block).  Otherwise thread 0 takes the next item
+// from the queue while the block runs the current one, a barrier closing each iteration.  body appears
+// once, so both orders run the same compiled arithmetic.
+template <typename Body>
+__device__ __forceinline__ void wq_for_each(const WorkQueue& q, long long n, long long* s_next,
+                                            unsigned long long* s_t0, Body&& body) {
+  const bool queued = q.qctr != nullptr || q.t0 != nullptr;  // uniform over the grid
+  long long w;
+  if (queued) {
+    wq_begin(q, s_t0);
+    if (threadIdx.x == 0) s_next[0] = wq_take(q, n, 0, *s_t0);
+    __syncthreads();
+    w = s_next[0];
+  } else {
+    w = (long long)blockIdx.x < n ? (long long)blockIdx.x : -1;
+  }
+  for (long long it = 0; w >= 0; ++it) {
+    if (queued && threadIdx.x == 0) s_next[(it + 1) & 1] = wq_take(q, n, it + 1, *s_t0);
+    body(w);
+    if (queued) {
+      __syncthreads();  // every thread has read slot it & 1 before thread 0 refills it
+      w = s_next[(it + 1) & 1];
+    } else {
+      w += gridDim.x;
+      if (w >= n) w = -1;
+    }
+  }
+}
+
+// Control block of a basis (device): the error word (zero until a launch times out; cleared when the host
+// reads it), then per class a queue slot for its coupling launch and one for its pair launch (counter,
+// start time), cleared at the start of every call.
+constexpr size_t kCtrlHead = 16;
+constexpr size_t kCtrlSlot = 16;
+inline size_t ctrl_bytes(size_t nclasses) { return kCtrlHead + 2 * kCtrlSlot * nclasses; }
+
 // Kernel launchers (shgo_kernels.cu).
 struct ClassWork {
   int la, lb;
@@ -276,6 +358,13 @@ struct DeviceBasis {
   // h_ppoff (host, npairs + 1) gives the primitive-pair offsets used to cut the chunks.
   int64_t region = 0;
   const int64_t* h_ppoff = nullptr;
+  // work queues (nullptr ctrl: strided blocks, no time limit): control block, items per class in
+  // decreasing cost (local indices at the class's primitive-pair / pair offset; nullptr = index order),
+  // and the time limit of each launch
+  unsigned char* ctrl = nullptr;
+  const int* cp_items = nullptr;
+  const int* pr_items = nullptr;
+  unsigned long long limit_ns = ~0ull;
 };
 
 // Coupling-buffer cap (doubles) above which a basis switches to per-stream regions (2 GiB).
@@ -308,9 +397,23 @@ inline void pair_frame(const double* A, const double* B, double* Q) {
   }
 }
 
-// Raises `func`'s dynamic shared-memory limit to `bytes` on the current device, once per (kernel, device)
-// and under a lock: the attribute belongs to one device, so a process on several devices sets it on each.
-cudaError_t ensure_max_dynamic_smem(const void* func, int bytes);
+// Raises `func`'s dynamic shared-memory limit on the current device to the most a block may take: the
+// device's opt-in per-block limit less the kernel's static shared memory.
+inline cudaError_t set_max_dynamic_smem(const void* func) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+// Raises `func`'s dynamic shared-memory limit to `bytes` (0: the most a block may take) on the current
+// device, once per (kernel, device) and under a lock: the attribute belongs to one device, so a process
+// on several devices sets it on each.
+cudaError_t ensure_max_dynamic_smem(const void* func, int bytes = 0);
 
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
@@ -339,6 +442,7 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
 // Arguments of the FP64 coupling kernel for one class (shgo_coupling.cu).
 struct CouplingArgs {
   int64_t npp = 0, pp_base = 0, rbase = 0;
+  WorkQueue q;
   const int* pp_pair = nullptr;
   const int* pair_a = nullptr;
   const double* shell_xyz = nullptr;
@@ -378,84 +482,6 @@ struct EspArgs {
 cudaError_t launch_esp_fp64(int lam, const EspArgs& args, cudaStream_t stream);
 // Gradient of the potential: args.phi receives 3 values per point; chunks of 16 points.
 cudaError_t launch_esp_grad_fp64(int lam, const EspArgs& args, cudaStream_t stream);
-
-// Arguments of one launch of the fused shell-pair kernel (shgo_fused.cu): steps S2-S5 for the shell
-// pairs items[0 .. nitems) of one Lambda, taken from a work queue.
-struct FusedArgs {
-  const int* items = nullptr;          // shell pairs, by decreasing estimated cost
-  int nitems = 0;
-  unsigned int* qctr = nullptr;        // queue position (zero before the launch)
-  unsigned long long* t0 = nullptr;    // start time of the launch's first block (zero before the launch)
-  int* err = nullptr;                  // set to SHGO_ERR_TIMEOUT when the time limit stops the launch
-  unsigned long long limit_ns = ~0ull; // time limit of the launch (ns; ~0 = none)
-  const int* pair_a = nullptr;
-  const int* pair_b = nullptr;
-  const int64_t* pair_ppoff = nullptr;
-  const int* pair_site = nullptr;
-  const double* site_rot = nullptr;
-  int64_t rot_per = 0;
-  const double* rotd = nullptr;
-  const double* shell_xyz = nullptr;
-  const int* shell_l = nullptr;
-  const int* shell_nprim = nullptr;
-  const int64_t* shell_foff = nullptr;
-  const PPData* ppd = nullptr;
-  MolView mv;
-  const double* centers = nullptr;
-  const double* charges = nullptr;
-  double* out = nullptr;
-  const double* boys_tab = nullptr;
-  const int* rmap = nullptr;           // R layout of this Lambda
-  const double* rnorm = nullptr;       // N_LM per R entry of this Lambda
-  const double* etab = nullptr;
-  const int* eoff = nullptr;
-  const int* g_rowinfo = nullptr;      // Gaunt programs of all classes (class offsets in constant memory)
-  const int* g_grp = nullptr;
-  const GTerm* g_terms = nullptr;
-  int64_t u_doubles = 0;               // union region: nucleus tables / (W and) epilogue matrices
-  int64_t w_doubles = 0;               // separate W region (0: W lives in the union region)
-};
-cudaError_t launch_fused(int lam, const FusedArgs& args, size_t smem, cudaStream_t stream);
-size_t fused_smem(int lam, int64_t u_doubles, int64_t w_doubles);
-void fused_regions(int lam, int la_lo, int la_hi, bool w_alias, int64_t* u_doubles, int64_t* w_doubles);
-// Constants and launch attributes of the fused kernels on the current device.
-cudaError_t fused_setup();
-
-// One launch of the fused kernel in a basis's plan: the items of one Lambda (or, for per-class timing,
-// of one class) at items + off, with its control slot and shared-memory regions.
-struct FusedLaunch {
-  int lam = 0, la_lo = 0, la_hi = 0;
-  int64_t off = 0, n = 0;
-  int slot = 0;
-  int64_t u_doubles = 0, w_doubles = 0;
-  double cost = 0;
-};
-// Control block of a basis's fused launches (device, zeroed before every call): the shared error word,
-// then per slot a queue counter and a start time.
-constexpr size_t kFusedCtrlHead = 16;
-constexpr size_t kFusedSlotBytes = 16;
-struct FusedPlan {
-  std::vector<FusedLaunch> groups;     // one per Lambda present, by decreasing cost
-  std::vector<FusedLaunch> per_class;  // aligned with the basis's class list
-  const int* items = nullptr;          // device
-  unsigned char* ctrl = nullptr;       // device
-  size_t ctrl_bytes = 0;
-};
-// Items and launches of a basis: pairs pa/pb (class order, as the ClassWork list), shell l and primitive
-// counts, nuclei per pair (nc_of_pair, or nullptr when every pair sees the same nuclei).  Returns the item
-// array (groups' items, then the classes') to upload; plan.items and plan.ctrl are set by the caller.
-std::vector<int> build_fused_plan(const std::vector<ClassWork>& work, const std::vector<int>& pa,
-                                  const std::vector<int>& pb, const int32_t* shell_nprim,
-                                  const std::vector<double>* nc_of_pair, FusedPlan& plan);
-// All of V, or with only_class >= 0 that class's shell pairs on `stream`.  Lambda <= fused_lam_max runs the
-// fused work-queue kernel (one launch per Lambda), larger Lambda the two-kernel form per class (coupling
-// blocks in the basis's coupling buffer, then the shell-pair kernel); all of it concurrently on the
-// stream pool, largest first, forked from and joined to `stream`.  The control block is cleared on
-// `stream` first.
-shgo_status launch_fused_call(const DeviceBasis& db, const DeviceTables& dt, const FusedPlan& plan,
-                              const std::vector<ClassWork>& work, int fused_lam_max, const MolView& mv,
-                              const double* centers, const double* charges, double* out,
-                              unsigned long long limit_ns, int only_class, cudaStream_t stream, std::string* err);
 
 // Launches the Lambda = lam instantiation with nucleus chunks of nch (16 or 32) on `grid` warps.
 cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream);

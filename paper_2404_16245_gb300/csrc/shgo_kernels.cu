@@ -238,8 +238,10 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
                                                     const GTerm* __restrict__ g_terms,
                                                     const PPData* __restrict__ ppd,
                                                     const double* __restrict__ rbuf, MolView mv,
-                                                    double* __restrict__ out) {
+                                                    double* __restrict__ out, WorkQueue wq) {
   extern __shared__ double smem[];
+  __shared__ long long s_next[2];
+  __shared__ unsigned long long s_t0;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lam = la + lb;
   const int nR = n_r(lam);
@@ -259,7 +261,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
   double* Rs = fab + (la + 1) * (lb + 1);  // coupling block of one primitive pair
   double* scal = Rs + nR;                  // per primitive pair: prefactor, beta/p, alpha/p
   double* dpow = scal + 4;                 // |b - a|^k, k <= max(la, lb)
-  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
+  wq_for_each(wq, npairs, s_next, &s_t0, [&](long long wn) {
+    const int w = (int)wn;
     const int pr = pair_base + w;
     const int a = pair_a[pr], b = pair_b[pr];
     const double* rd = rotd + (int64_t)pair_site[pr] * rot_per;
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
         o[(fa0 + ma) * ld + fb0 + mb] = 0.0;
         if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = 0.0;
       }
-      continue;
+      return;
     }
     // V' = t_A W t_B (diagonal in m), first over l2.  Threads are ordered by |m| (m = 0, 1, -1,
     // 2, -2, ...) so that the lanes of a warp run loops of (nearly) equal length.
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       o[(fa0 + ma) * ld + fb0 + mb] = v;
       if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = v;
     }
-  }
+    });
 }
 
 // Adjoint of the pair kernel for the electrostatic potential: for one shell pair and a symmetric
@@ -717,7 +720,6 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
   if (e == cudaSuccess) e = coupling_fp64_setup();
   if (e == cudaSuccess) e = coupling_f32_setup();
-  if (e == cudaSuccess) e = fused_setup();
   if (e == cudaSuccess) {
     int lof[(kLmax + 1) * (kLmax + 1)];
     for (int l = 0; l <= kLmax; ++l)
@@ -798,8 +800,7 @@ void set_kernel_attributes() {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_pool_mu);
   if (g_attr_ok[dev]) return;
-  const int lim = 227 * 1024;
-  cudaFuncSetAttribute(k_pair_block, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  set_max_dynamic_smem((const void*)k_pair_block);
   g_attr_ok[dev] = true;
 }
 
@@ -822,12 +823,41 @@ struct Launcher {
     return pair_threads(la, lb);
   }
 
+  // Work queue of class c's coupling (which = 0) or pair (which = 1) launch.  A launch over the whole
+  // class of a batch takes its work from the queue in the batch's cost order; the uniform work of one
+  // molecule, and the pieces of a class whose coupling buffer is split into regions, stride instead.
+  // All keep the time limit.
+  // Without a limit and without a queue the launch is the plain strided one (no atomics, no clock).
+  WorkQueue queue(const ClassWork& w, size_t c, int which) const {
+    WorkQueue q;
+    const int* items = which == 0 ? db.cp_items : db.pr_items;
+    const bool timed = db.limit_ns != ~0ull, queued = db.region == 0 && items;
+    if (!db.ctrl || (!timed && !queued)) return q;
+    unsigned char* slot = db.ctrl + kCtrlHead + kCtrlSlot * (2 * c + (size_t)which);
+    if (timed) {
+      q.t0 = reinterpret_cast<unsigned long long*>(slot + 8);
+      q.err = reinterpret_cast<int*>(db.ctrl);
+      q.limit_ns = db.limit_ns;
+    }
+    if (queued) {
+      q.qctr = reinterpret_cast<unsigned long long*>(slot);
+      q.items = items + (which == 0 ? w.pp_base : (int64_t)w.pair_base);
+    }
+    return q;
+  }
+  // Clears class c's two queue slots on `s` (before launching the class again within one call).
+  cudaError_t reset(size_t c, cudaStream_t s) const {
+    if (!db.ctrl || (db.limit_ns == ~0ull && !db.cp_items && !db.pr_items)) return cudaSuccess;
+    return cudaMemsetAsync(db.ctrl + kCtrlHead + kCtrlSlot * 2 * c, 0, 2 * kCtrlSlot, s);
+  }
+
   void coupling(const ClassWork& w, size_t c, int64_t rbase, cudaStream_t s) const {
     if (w.npp == 0) return;
     const int lam = w.la + w.lb;
     const int nch = nch_of(c, lam);
     const int* rmap = dt.rmap + th.rmap_off[lam];
     CouplingArgs a;
+    a.q = queue(w, c, 0);
     a.npp = w.npp;
     a.pp_base = w.pp_base;
     a.rbase = rbase;
@@ -863,9 +893,16 @@ struct Launcher {
         rot_block(db.rot_lmax), db.rotd,
         db.shell_poff, db.shell_nprim, db.shell_foff, db.prim_exp, db.prim_coef, dt.etab, dt.eoff,
         dt.g_rowinfo + th.g_rowbase[cid], dt.g_grp + 2 * th.g_grpbase[cid], dt.g_terms + th.g_termbase[cid],
-        db.ppd, db.rbuf, mv, out);
+        db.ppd, db.rbuf, mv, out, queue(w, c, 1));
   }
 };
+
+// Clears the queue slots of a basis's control block (counters, start times) on `stream`; the error word
+// stays set until the host reads it.
+cudaError_t clear_ctrl(const DeviceBasis& db, size_t nclasses, cudaStream_t stream) {
+  if (!db.ctrl || (db.limit_ns == ~0ull && !db.cp_items && !db.pr_items)) return cudaSuccess;
+  return cudaMemsetAsync(db.ctrl + kCtrlHead, 0, ctrl_bytes(nclasses) - kCtrlHead, stream);
+}
 
 // Pieces of a class whose coupling blocks fit `region` doubles, cut between shell pairs.
 std::vector<ClassWork> class_chunks(const ClassWork& w, const int64_t* ppoff, int64_t region) {
@@ -991,12 +1028,13 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
   mv.ncenters = ncenters;
   mv.nbf = nbf;
   const Launcher L{db, dt, th, mv, centers, charges, out, nullptr};
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = clear_ctrl(db, work.size(), stream);
   if (events && db.region > 0) {
     *err = "phase timing needs the whole coupling buffer; this basis uses bounded regions";
     return SHGO_ERR_INVALID_ARG;
   }
-  if (!concurrent) {
+  if (e != cudaSuccess) {
+  } else if (!concurrent) {
     for (size_t c = 0; c < work.size(); ++c) L.coupling(work[c], c, rbases[c], stream);
     if (events) cudaEventRecord(events[1], stream);
     for (size_t c = 0; c < work.size(); ++c) L.pair(work[c], c, rbases[c], stream);
@@ -1027,7 +1065,7 @@ shgo_status launch_class_timed(const DeviceBasis& db, const DeviceTables& dt, co
   const std::vector<int64_t> rbases = class_rbases(work);
   const Launcher L{db, dt, th, mv, centers, charges, out, nullptr};
   std::vector<cudaEvent_t> ev(3 * work.size(), nullptr);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = clear_ctrl(db, work.size(), stream);
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
   for (size_t c = 0; c < work.size() && e == cudaSuccess; ++c) {
@@ -1063,7 +1101,8 @@ shgo_status launch_batched(const DeviceBasis& db, const DeviceTables& dt, const 
   const Tables& th = tables_host();
   const std::vector<int64_t> rbases = class_rbases(work);
   const Launcher L{db, dt, th, mv, centers, charges, out, tune};
-  const cudaError_t e = run_concurrent(L, work, rbases, class_order(work, nuclei_per_pair), 2, stream);
+  cudaError_t e = clear_ctrl(db, work.size(), stream);
+  if (e == cudaSuccess) e = run_concurrent(L, work, rbases, class_order(work, nuclei_per_pair), 2, stream);
   if (e != cudaSuccess) {
     *err = std::string("kernel launch: ") + cudaGetErrorString(e);
     return SHGO_ERR_CUDA;
@@ -1080,6 +1119,7 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
   const Tables& th = tables_host();
   const std::vector<int64_t> rbases = class_rbases(work);
   tune->assign(work.size(), ClassTune{});
+  clear_ctrl(db, work.size(), stream);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1104,7 +1144,9 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
     int best_nch = 32;
     for (int nch : {16, 32}) {
       trial[c].nch = nch;
+      L.reset(c, stream);
       L.coupling(first, c, rb, stream);  // warm
+      L.reset(c, stream);
       const float ms = time_it([&] { L.coupling(first, c, rb, stream); });
       if (ms < best) {
         best = ms;
@@ -1112,13 +1154,16 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
       }
     }
     trial[c].nch = best_nch;
+    L.reset(c, stream);
     L.coupling(first, c, rb, stream);  // the kept shape leaves its coupling block in place
     (*tune)[c].nch = best_nch;
     best = 1e30f;
     int best_thr = pair_threads(w.la, w.lb);
     for (int thr : {32, 64, 128}) {
       trial[c].threads = thr;
+      L.reset(c, stream);
       L.pair(first, c, rb, stream);  // warm
+      L.reset(c, stream);
       const float ms = time_it([&] { L.pair(first, c, rb, stream); });
       if (ms < best) {
         best = ms;
@@ -1128,6 +1173,7 @@ shgo_status autotune_batched(const DeviceBasis& db, const DeviceTables& dt, cons
     (*tune)[c].threads = best_thr;
     trial[c].threads = best_thr;
     for (size_t k = 0; k < chunks.size(); ++k) {  // the whole class with the kept shapes
+      L.reset(c, stream);
       if (k > 0) L.coupling(chunks[k], c, rb, stream);
       L.pair(chunks[k], c, rb, stream);
     }
@@ -1199,7 +1245,7 @@ shgo_status live_counts(const DeviceBasis& db, const std::vector<ClassWork>& wor
 shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                        int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
                        bool gradient, cudaStream_t stream, std::string* err) {
-  ensure_max_dynamic_smem((const void*)k_esp_adjoint, 227 * 1024);
+  ensure_max_dynamic_smem((const void*)k_esp_adjoint);
   const Tables& th = tables_host();
   cudaError_t e =
       cudaMemsetAsync(phi, 0, sizeof(double) * (size_t)std::max<int64_t>(npoints, 1) * (gradient ? 3 : 1), stream);
@@ -1812,7 +1858,7 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
     doff[c + 1] = doff[c] + w.npp * (int64_t)(2 * w.la + 1) * (2 * w.lb + 1) * n_r(w.la + w.lb);
   }
   if (doff[nw] == 0) return SHGO_OK;
-  ensure_max_dynamic_smem((const void*)k_eri_part, 227 * 1024);
+  ensure_max_dynamic_smem((const void*)k_eri_part);
   // class pairs, largest first, and each one's chunk of ket primitive pairs
   struct CP {
     size_t c1, c2;
@@ -1943,7 +1989,7 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
 
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err) {
-  ensure_max_dynamic_smem((const void*)k_overlap_block, 227 * 1024);
+  ensure_max_dynamic_smem((const void*)k_overlap_block);
   for (const ClassWork& w : work) {
     if (w.npairs == 0) continue;
     k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), stream>>>(
@@ -1952,205 +1998,6 @@ shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const 
         db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
   }
   return launch_error(err);
-}
-
-std::vector<int> build_fused_plan(const std::vector<ClassWork>& work, const std::vector<int>& pa,
-                                  const std::vector<int>& pb, const int32_t* shell_nprim,
-                                  const std::vector<double>* nc_of_pair, FusedPlan& plan) {
-  // estimated cost of a shell pair: its primitive pairs x nuclei x R' entries (the nucleus sums dominate)
-  // plus its Gaunt coupling and epilogue
-  auto pair_cost = [&](const ClassWork& w, int q) {
-    const int lam = w.la + w.lb;
-    const double nW = (double)(w.la + 1) * (w.la + 1) * (w.lb + 1) * (w.lb + 1);
-    const double npp = (double)shell_nprim[pa[q]] * shell_nprim[pb[q]];
-    const double nc = nc_of_pair ? (*nc_of_pair)[q] : 32.0;
-    return npp * (nc * (2.0 * n_r(lam) + 4.0 * n_harm(lam)) + 8.0 * nW) + 30.0 * nW;
-  };
-  std::vector<int> items;
-  plan.groups.clear();
-  plan.per_class.assign(work.size(), FusedLaunch{});
-  std::vector<std::vector<size_t>> by_lam(kLamMax + 1);
-  for (size_t c = 0; c < work.size(); ++c) by_lam[work[c].la + work[c].lb].push_back(c);
-  auto add_launch = [&](int lam, const std::vector<size_t>& cls) {
-    FusedLaunch L;
-    L.lam = lam;
-    L.la_lo = kLmax + 1;
-    L.la_hi = -1;
-    L.off = (int64_t)items.size();
-    std::vector<std::pair<double, int>> its;
-    bool single = true;
-    for (size_t c : cls) {
-      const ClassWork& w = work[c];
-      L.la_lo = std::min(L.la_lo, w.la);
-      L.la_hi = std::max(L.la_hi, w.la);
-      for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q) {
-        const double cost = pair_cost(w, q);
-        its.emplace_back(-cost, q);
-        L.cost += cost;
-        if (shell_nprim[pa[q]] * shell_nprim[pb[q]] != 1) single = false;
-      }
-    }
-    std::stable_sort(its.begin(), its.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-    for (const auto& it : its) items.push_back(it.second);
-    L.n = (int64_t)its.size();
-    fused_regions(lam, L.la_lo, L.la_hi, single, &L.u_doubles, &L.w_doubles);
-    return L;
-  };
-  int slot = 0;
-  for (int lam = 0; lam <= kLamMax; ++lam) {
-    if (by_lam[lam].empty()) continue;
-    FusedLaunch L = add_launch(lam, by_lam[lam]);
-    L.slot = slot++;
-    plan.groups.push_back(L);
-  }
-  for (size_t c = 0; c < work.size(); ++c) {
-    FusedLaunch L = add_launch(work[c].la + work[c].lb, {c});
-    L.slot = slot++;
-    plan.per_class[c] = L;
-  }
-  std::stable_sort(plan.groups.begin(), plan.groups.end(),
-                   [](const FusedLaunch& x, const FusedLaunch& y) { return x.cost > y.cost; });
-  plan.ctrl_bytes = kFusedCtrlHead + kFusedSlotBytes * (size_t)slot;
-  return items;
-}
-
-namespace {
-FusedArgs fused_args(const DeviceBasis& db, const DeviceTables& dt, const FusedPlan& plan, const FusedLaunch& L,
-                     const MolView& mv, const double* centers, const double* charges, double* out,
-                     unsigned long long limit_ns) {
-  const Tables& th = tables_host();
-  FusedArgs a;
-  a.items = plan.items + L.off;
-  a.nitems = (int)L.n;
-  unsigned char* slot = plan.ctrl + kFusedCtrlHead + kFusedSlotBytes * (size_t)L.slot;
-  a.qctr = reinterpret_cast<unsigned int*>(slot);
-  a.t0 = reinterpret_cast<unsigned long long*>(slot + 8);
-  a.err = reinterpret_cast<int*>(plan.ctrl);
-  a.limit_ns = limit_ns;
-  a.pair_a = db.pair_a;
-  a.pair_b = db.pair_b;
-  a.pair_ppoff = db.pair_ppoff;
-  a.pair_site = db.pair_site;
-  a.site_rot = db.site_rot;
-  a.rot_per = rot_block(db.rot_lmax);
-  a.rotd = db.rotd;
-  a.shell_xyz = db.shell_xyz;
-  a.shell_l = db.shell_l;
-  a.shell_nprim = db.shell_nprim;
-  a.shell_foff = db.shell_foff;
-  a.ppd = db.ppd;
-  a.mv = mv;
-  a.centers = centers;
-  a.charges = charges;
-  a.out = out;
-  a.boys_tab = dt.boys;
-  a.rmap = dt.rmap + th.rmap_off[L.lam];
-  a.rnorm = dt.rnorm + th.rmap_off[L.lam];
-  a.etab = dt.etab;
-  a.eoff = dt.eoff;
-  a.g_rowinfo = dt.g_rowinfo;
-  a.g_grp = dt.g_grp;
-  a.g_terms = dt.g_terms;
-  a.u_doubles = L.u_doubles;
-  a.w_doubles = L.w_doubles;
-  return a;
-}
-}  // namespace
-
-shgo_status launch_fused_call(const DeviceBasis& db, const DeviceTables& dt, const FusedPlan& plan,
-                              const std::vector<ClassWork>& work, int fused_lam_max, const MolView& mv,
-                              const double* centers, const double* charges, double* out,
-                              unsigned long long limit_ns, int only_class, cudaStream_t stream, std::string* err) {
-  const Tables& th = tables_host();
-  const std::vector<int64_t> rbases = class_rbases(work);
-  const Launcher L2{db, dt, th, mv, centers, charges, out, nullptr};
-  cudaError_t e = cudaMemsetAsync(plan.ctrl, 0, plan.ctrl_bytes, stream);
-  auto fused_one = [&](const FusedLaunch& L, cudaStream_t s) {
-    if (L.n == 0) return cudaSuccess;
-    const FusedArgs a = fused_args(db, dt, plan, L, mv, centers, charges, out, limit_ns);
-    return launch_fused(L.lam, a, fused_smem(L.lam, L.u_doubles, L.w_doubles), s);
-  };
-  // the two-kernel form of class c on stream s (region: the stream's share of a bounded coupling buffer)
-  auto two_kernel = [&](size_t c, cudaStream_t s, int region) {
-    if (db.region > 0) {
-      const int64_t rb = (int64_t)region * db.region;
-      for (const ClassWork& ch : class_chunks(work[c], db.h_ppoff, db.region)) {
-        L2.coupling(ch, c, rb, s);
-        L2.pair(ch, c, rb, s);
-      }
-    } else {
-      L2.coupling(work[c], c, rbases[c], s);
-      L2.pair(work[c], c, rbases[c], s);
-    }
-    return cudaGetLastError();
-  };
-  if (e == cudaSuccess && only_class >= 0) {
-    const size_t c = (size_t)only_class;
-    if (work[c].la + work[c].lb <= fused_lam_max) {
-      e = fused_one(plan.per_class[c], stream);
-    } else {
-      set_kernel_attributes();
-      e = two_kernel(c, stream, 0);
-    }
-  } else if (e == cudaSuccess) {
-    // tasks: a fused launch per Lambda <= fused_lam_max, the two kernels of each class above it;
-    // largest first, dealt round-robin over the pool streams
-    struct Task {
-      double cost;
-      int group;  // index into plan.groups, or -1
-      int cls;    // class index for the two-kernel form
-    };
-    std::vector<Task> tasks;
-    for (size_t g = 0; g < plan.groups.size(); ++g) {
-      const FusedLaunch& G = plan.groups[g];
-      if (G.lam <= fused_lam_max) {
-        tasks.push_back({G.cost, (int)g, -1});
-      } else {
-        for (size_t c = 0; c < work.size(); ++c)
-          if (work[c].la + work[c].lb == G.lam) tasks.push_back({plan.per_class[c].cost, -1, (int)c});
-      }
-    }
-    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) { return x.cost > y.cost; });
-    bool any_two = false;
-    for (const Task& t : tasks) any_two = any_two || t.group < 0;
-    if (any_two) set_kernel_attributes();
-    cudaStream_t* pool = nullptr;
-    e = stream_pool(&pool);
-    const int ns = (int)std::min<size_t>(tasks.size(), (size_t)kPoolStreams);
-    auto run_task = [&](const Task& t, cudaStream_t s, int region) {
-      return t.group >= 0 ? fused_one(plan.groups[(size_t)t.group], s) : two_kernel((size_t)t.cls, s, region);
-    };
-    if (e == cudaSuccess && ns == 1) {
-      for (const Task& t : tasks)
-        if (e == cudaSuccess) e = run_task(t, stream, 0);
-    } else if (e == cudaSuccess && ns > 1) {
-      cudaEvent_t fork = nullptr;
-      e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventRecord(fork, stream);
-      for (int i = 0; i < ns && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pool[i], fork, 0);
-      for (size_t k = 0; k < tasks.size() && e == cudaSuccess; ++k)
-        e = run_task(tasks[k], pool[k % ns], (int)(k % ns));
-      // join every pool stream that received work, even after a failed launch
-      for (int i = 0; i < ns; ++i) {
-        cudaEvent_t join = nullptr;
-        cudaError_t ej = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-        if (ej == cudaSuccess) ej = cudaEventRecord(join, pool[i]);
-        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(stream, join, 0);
-        if (join) cudaEventDestroy(join);
-        if (ej != cudaSuccess) {
-          for (int k = 0; k < ns; ++k) cudaStreamSynchronize(pool[k]);
-          if (e == cudaSuccess) e = ej;
-          break;
-        }
-      }
-      if (fork) cudaEventDestroy(fork);
-    }
-  }
-  if (e != cudaSuccess) {
-    *err = std::string("launch: ") + cudaGetErrorString(e);
-    return SHGO_ERR_CUDA;
-  }
-  return SHGO_OK;
 }
 
 cudaError_t ensure_max_dynamic_smem(const void* func, int bytes) {
@@ -2162,7 +2009,8 @@ cudaError_t ensure_max_dynamic_smem(const void* func, int bytes) {
   std::lock_guard<std::mutex> lk(mu);
   for (const auto& d : done)
     if (d.first == func && d.second == dev) return cudaSuccess;
-  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = bytes > 0 ? cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                : set_max_dynamic_smem(func);
   if (e == cudaSuccess) done.emplace_back(func, dev);
   return e;
 }
