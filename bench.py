@@ -647,9 +647,14 @@ def _cluster(seed: int, n_atoms: int):
 
 
 def run_screened(args) -> int:
-    """Learned screening against the plain method on one cluster: network trained on the plain
-    method's blocks of another cluster; plain and screened V timed with CUDA events; the screened V
-    compared with the plain one element by element; 1% of the skipped triples audited exactly."""
+    """Learned screening on one cluster of the screening recipe, three variants side by side, all with
+    the block-sparse output (only shell pairs with a primitive pair above the elementwise bound store a
+    block): (a) no screening at all (SHGO_FLAG_NO_PRIM_BOUND: every primitive pair whose K_AB does not
+    underflow), (b) the primitive-pair bound alone (the default plain method), (c) the bound plus the
+    learned per-(shell pair, nucleus) mask, whose build is timed and charged to it.  The network is trained
+    on the plain method's blocks of another cluster of the same size; its margin is calibrated on held-out
+    triples; each variant's V is compared with (a) over the blocks (b) stores, and 1% of the skipped triples
+    are audited with the plain method."""
     import torch
 
     from paper_2404_16245_gb300 import screening as S
@@ -670,87 +675,103 @@ def run_screened(args) -> int:
     X = shgo.screen_features(Bt.handle, torch.tensor(tC, device=dev), torch.tensor(tZ, device=dev),
                              torch.tensor(tr, device=dev))
     label_s = time.perf_counter() - t0
-    # 90 % of the labelled triples train the network, 10 % calibrate the skip margin
     nval = max(1, len(tr) // 10)
     Tt = torch.tensor(T, dtype=torch.float32, device=dev)
     t1 = time.perf_counter()
     net, losses = S.train(X[nval:].contiguous(), Tt[nval:].contiguous(), epochs=args.epochs, batch=4096, log=log)
     train_s = time.perf_counter() - t1
     Bt.close()
+    Xv = X[:nval].contiguous().clone()
+    del X, Tt
     # evaluation cluster
     basis, C, Z = _cluster(4000, args.atoms)
-    # per-triple threshold: the error budget shared by every nucleus of a pair's sum
     threshold = args.threshold if args.threshold > 0 else args.target_error / len(Z)
-    margin = S.calibrate_margin(net, X[:nval].contiguous(), T[:nval], math.log10(threshold), safety=2.0) \
+    margin = S.calibrate_margin(net, Xv, T[:nval], math.log10(threshold), safety=2.0) \
         if args.margin <= 0 else math.log10(args.margin)
-    B = shgo.Basis(basis)
-    # the screened path in the requested precision; the plain reference is always FP64
-    Bs = B if args.precision == "fp64" else shgo.Basis(basis, precision=shgo.SHGO_PREC_FP32_BULK)
+    del Xv
     Cd, Zd = torch.tensor(C, device=dev), torch.tensor(Z, device=dev)
-    out_plain = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device=dev)
-    out_scr = torch.empty_like(out_plain)
-    flops, trip = shgo.shgo_basis_flops(B.handle, len(Z))
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    shgo.nuclear_attraction(B, Cd, Zd, out=out_plain, stream=stream)  # warm
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for _ in range(args.steps):
-        shgo.nuclear_attraction(B, Cd, Zd, out=out_plain, stream=stream)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    ev[2].record(stream)
-    kept, skipped = shgo.screen_build(Bs.handle, net, Cd, Zd, len(Z), math.log10(threshold), margin)
-    ev[3].record(stream)
-    shgo.nuclear_attraction_screened(Bs.handle, Cd, Zd, len(Z), out_scr, stream=stream)  # warm
-    torch.cuda.synchronize()
-    ev[4].record(stream)
-    for _ in range(args.steps):
-        shgo.nuclear_attraction_screened(Bs.handle, Cd, Zd, len(Z), out_scr, stream=stream)
-    ev[5].record(stream)
-    torch.cuda.synchronize()
-    plain32 = None
-    if Bs is not B:
-        # the same precision without screening, for the share of each pattern
-        out32 = torch.empty_like(out_plain)
-        shgo.nuclear_attraction(Bs, Cd, Zd, out=out32, stream=stream)
+    prec = shgo.SHGO_PREC_FP64 if args.precision == "fp64" else shgo.SHGO_PREC_FP32_BULK
+    Bn = shgo.Basis(basis, precision=prec, flags=shgo.SHGO_FLAG_BLOCK_SPARSE | shgo.SHGO_FLAG_NO_PRIM_BOUND)
+    Bb = shgo.Basis(basis, precision=prec, flags=shgo.SHGO_FLAG_BLOCK_SPARSE)
+
+    def timed(fn, steps):
+        fn()
         torch.cuda.synchronize()
-        e32 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        e32[0].record(stream)
-        for _ in range(args.steps):
-            shgo.nuclear_attraction(Bs, Cd, Zd, out=out32, stream=stream)
-        e32[1].record(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
         torch.cuda.synchronize()
-        plain32 = {"ms": e32[0].elapsed_time(e32[1]) / args.steps,
-                   "max_abs_diff_vs_fp64": float((out32 - out_plain).abs().max())}
-    plain_ms = ev[0].elapsed_time(ev[1]) / args.steps
-    build_ms = ev[2].elapsed_time(ev[3])
-    scr_ms = ev[4].elapsed_time(ev[5]) / args.steps
-    err = float((out_scr - out_plain).abs().max())
-    mask = shgo.screen_mask(Bs.handle, kept + skipped)
-    pa, pb = shgo.pair_shells(B.handle, B.npairs)
-    rep = S.audit(basis, pa, pb, C, Z, mask, np.full(B.npairs, len(Z)), args.audit, np.random.default_rng(7),
+        return e0.elapsed_time(e1) / steps
+
+    out_n = torch.empty(Bn.out_shape(), dtype=torch.float64, device=dev)
+    out_b = torch.empty(Bb.out_shape(), dtype=torch.float64, device=dev)
+    out_s = torch.empty(Bb.out_shape(), dtype=torch.float64, device=dev)
+    ms_n = timed(lambda: shgo.nuclear_attraction(Bn, Cd, Zd, out=out_n, stream=stream), args.steps)
+    ms_b = timed(lambda: shgo.nuclear_attraction(Bb, Cd, Zd, out=out_b, stream=stream), args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    kept, skipped = shgo.screen_build(Bb.handle, net, Cd, Zd, len(Z), math.log10(threshold), margin)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    ms_s = timed(lambda: shgo.nuclear_attraction_screened(Bb.handle, Cd, Zd, len(Z), out_s, stream=stream),
+                 args.steps)
+    # errors against (a) over the blocks (b) stores
+    _, _, off_n = shgo.shgo_sparse_layout(Bn.handle)
+    _, _, off_b = shgo.shgo_sparse_layout(Bb.handle)
+    pa, pb = shgo.pair_shells(Bb.handle, Bb.npairs)
+    lv = np.asarray(basis["l"])
+    sizes = (2 * lv[pa] + 1) * (2 * lv[pb] + 1)
+    idx_b = np.concatenate([np.arange(o, o + n) for o, n in zip(off_b[off_b >= 0], sizes[off_b >= 0])])
+    idx_n = np.concatenate([np.arange(o, o + n) for o, n in zip(off_n[off_b >= 0], sizes[off_b >= 0])])
+    vn = out_n.cpu().numpy()
+    ref = vn[idx_n]
+    err_b = float(np.max(np.abs(out_b.cpu().numpy()[idx_b] - ref)))
+    err_s = float(np.max(np.abs(out_s.cpu().numpy()[idx_b] - ref)))
+    only_n = (off_n >= 0) & (off_b < 0)
+    omitted = float(max((np.max(np.abs(vn[o:o + n])) for o, n in zip(off_n[only_n], sizes[only_n])), default=0.0))
+    mask = shgo.screen_mask(Bb.handle, kept + skipped)
+    rep = S.audit(basis, pa, pb, C, Z, mask, np.full(Bb.npairs, len(Z)), args.audit, np.random.default_rng(7),
                   threshold)
-    line = {"metric": METRIC, "value": float(trip[0]) / ((build_ms + scr_ms) / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": 1, "ms_per_step": build_ms + scr_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if Bs is B else "f32+f64", "data": "synthetic",
-            "config": {"workload": f"learned screening: {args.atoms}-atom cluster at 0.1 atoms/bohr^3, 4s3p2d1f",
-                       "precision": args.precision,
-                       "shell_triples": float(trip[0]), "primitive_triples": float(trip[1]),
+    fl_n, trip = shgo.shgo_basis_flops(Bn.handle, len(Z))
+    fl_b, _ = shgo.shgo_basis_flops(Bb.handle, len(Z))
+    value = float(trip[0]) / ((build_ms + ms_s) / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "ms_per_step": build_ms + ms_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == shgo.SHGO_PREC_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"learned screening: {args.atoms}-atom cluster at 0.1 atoms/bohr^3, 4s3p2d1f, "
+                                   f"1-6 primitives, exponents log-uniform [0.05, 5000], Z ~ U{{1..9}}",
+                       "precision": args.precision, "shell_triples": float(trip[0]),
+                       "shell_pairs": Bb.npairs, "nbf": Bb.nbf,
                        "target_max_error": args.target_error, "per_triple_threshold": threshold,
                        "margin_log10": margin,
-                       "margin_source": "calibrated on held-out triples" if args.margin <= 0 else "given"},
-            "screening": {"kept": kept, "skipped": skipped, "skipped_fraction": skipped / max(1, kept + skipped),
-                          "plain_ms": plain_ms, "build_ms": build_ms, "screened_ms": scr_ms,
-                          "speedup_vs_plain": plain_ms / (build_ms + scr_ms),
-                          "speedup_vs_plain_reusing_mask": plain_ms / scr_ms,
-                          "max_abs_error_vs_plain": err, "audit": rep, "unscreened_same_precision": plain32},
+                       "output": "block-sparse (shgo_sparse_layout)"},
+            "variants": {
+                "no_screening": {"ms": ms_n, "shell_triples_per_s": float(trip[0]) / (ms_n / 1e3),
+                                 "blocks_stored": int((off_n >= 0).sum()), "coupling_flops": float(fl_n[0]),
+                                 "largest_element_of_blocks_the_bound_omits": omitted},
+                "primitive_pair_bound": {"ms": ms_b, "shell_triples_per_s": float(trip[0]) / (ms_b / 1e3),
+                                         "speedup_vs_no_screening": ms_n / ms_b,
+                                         "blocks_stored": int((off_b >= 0).sum()), "coupling_flops": float(fl_b[0]),
+                                         "max_abs_error_vs_no_screening": err_b},
+                "bound_plus_learned_mask": {"ms_including_build": build_ms + ms_s, "build_ms": build_ms,
+                                            "screened_ms": ms_s, "kept_triples": kept, "skipped_triples": skipped,
+                                            "skipped_fraction": skipped / max(1, kept + skipped),
+                                            "speedup_vs_no_screening": ms_n / (build_ms + ms_s),
+                                            "speedup_vs_bound_alone": ms_b / (build_ms + ms_s),
+                                            "speedup_vs_bound_alone_reusing_mask": ms_b / ms_s,
+                                            "max_abs_error_vs_no_screening": err_s, "audit": rep}},
+            "memory": {"dense_V_bytes": 8 * Bb.nbf ** 2, "block_sparse_V_bytes": 8 * Bb.ndoubles,
+                       "blocks_stored": Bb.nblocks},
             "training": {"triples": int(len(tr)), "train_atoms": args.train_atoms, "epochs": args.epochs,
                          "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "label_s": label_s,
                          "train_s": train_s}}
     print(json.dumps(line), flush=True)
-    if Bs is not B:
-        Bs.close()
-    B.close()
+    Bn.close()
+    Bb.close()
     net.close()
     return 0
 

@@ -53,9 +53,16 @@ typedef enum {
   SHGO_PREC_FP32_PLAIN = 2 /* the same kernel on single FP32 numbers (for error studies; ~1e-6) */
 } shgo_precision;
 
+/* Option flags (shgo_options.flags). */
+#define SHGO_FLAG_BLOCK_SPARSE 1   /* V as the blocks of the shell pairs that have a primitive pair above the
+                                      elementwise bound, packed (shgo_sparse_layout); single bases only */
+#define SHGO_FLAG_NO_PRIM_BOUND 2  /* keep every primitive pair whose K_AB does not underflow: no
+                                      elementwise bound (the method with no screening at all) */
+
 typedef struct {
   int32_t precision; /* a shgo_precision value */
   int32_t device;    /* CUDA device ordinal, -1 = the current device */
+  int32_t flags;     /* SHGO_FLAG_* bits, 0 = dense V with the primitive-pair bound */
 } shgo_options;
 
 /* Opaque basis: host copies of the shells, their normalised contraction coefficients, the
@@ -83,6 +90,23 @@ typedef struct {
 shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
                               const double* coefs, const double* shell_xyz, const shgo_options* opt,
                               shgo_basis** out);
+
+/* Primitive-pair bound.  With |S_lm(r)| <= |r|^l and the potential of a non-negative radial density peaking
+ * at its centre, every element of one primitive pair's block is at most
+ *   |c_i c_j| K_AB 4 pi int_0^inf (r + |PA|)^la (r + |PB|)^lb e^{-p r^2} r dr    per unit of total charge.
+ * Primitive pairs whose bound is below 1e-20 are skipped by every kernel unless SHGO_FLAG_NO_PRIM_BOUND is
+ * set, so an element of V moves by at most 1e-20 sum_C |Z_C| per skipped pair.
+ *
+ * Block-sparse output (SHGO_FLAG_BLOCK_SPARSE).  For bases whose dense nbf x nbf matrix is too large
+ * (thousands of atoms): only the shell pairs with at least one primitive pair kept by the bound store a
+ * block; every element of an omitted block is zero up to that bound.  Block q of the library's pair order
+ * (shgo_pair_shells; a's l >= b's l, and a >= b within equal l) is (2 l_a + 1) x (2 l_b + 1) row-major at
+ * out[offset[q]] with rows m_a = -l_a..l_a of shell a and columns m_b of shell b; offset[q] = -1 for an
+ * omitted pair.  shgo_nuclear_attraction and shgo_nuclear_attraction_screened then write `out` in this
+ * layout (ndoubles values, fully overwritten); the other integrals of such a basis stay dense.
+ *   nblocks, ndoubles: host, may be NULL; offset: host array of shgo_basis_npairs values, may be NULL.
+ * Errors: SHGO_ERR_INVALID_ARG (NULL basis, a basis without the flag). */
+shgo_status shgo_sparse_layout(const shgo_basis* basis, int64_t* nblocks, int64_t* ndoubles, int64_t* offset);
 
 /* Number of basis functions sum(2 l + 1) and of unique shell pairs n(n+1)/2. */
 int64_t shgo_basis_nbf(const shgo_basis* basis);

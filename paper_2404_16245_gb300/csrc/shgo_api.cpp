@@ -84,6 +84,11 @@ struct shgo_basis {
   // pinned host memory, and the event that marks that copy (shgo_basis_sync)
   int* h_err = nullptr;
   cudaEvent_t done_ev = nullptr;
+  // block-sparse output (SHGO_FLAG_BLOCK_SPARSE): per pair the offset of its block, or -1
+  bool sparse = false;
+  int64_t sparse_nblocks = 0, sparse_ndoubles = 0;
+  std::vector<int64_t> h_blk_off;
+  int64_t* d_blk_off = nullptr;
 };
 
 namespace {
@@ -213,6 +218,10 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   if (opt && opt->precision != SHGO_PREC_FP64 && opt->precision != SHGO_PREC_FP32_BULK &&
       opt->precision != SHGO_PREC_FP32_PLAIN)
     return fail(SHGO_ERR_INVALID_ARG, "unknown precision mode");
+  const int32_t flags = opt ? opt->flags : 0;
+  if (flags & ~(SHGO_FLAG_BLOCK_SPARSE | SHGO_FLAG_NO_PRIM_BOUND)) return fail(SHGO_ERR_INVALID_ARG, "unknown option flag");
+  if ((flags & SHGO_FLAG_BLOCK_SPARSE) && n_mol > 0)
+    return fail(SHGO_ERR_INVALID_ARG, "block-sparse output is for single bases, not batches");
   const bool batch = n_mol > 0;
   if (n_mol < 0) return fail(SHGO_ERR_INVALID_ARG, "n_mol < 0");
   if (batch) {
@@ -251,6 +260,8 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   b->device = device;
   b->n_shells = n_shells;
   b->d.precision = opt ? opt->precision : SHGO_PREC_FP64;
+  b->d.prim_bound = (flags & SHGO_FLAG_NO_PRIM_BOUND) ? 0 : 1;
+  b->sparse = (flags & SHGO_FLAG_BLOCK_SPARSE) != 0;
   b->batch = batch;
   const int nm = batch ? n_mol : 1;
   b->n_mol = nm;
@@ -552,6 +563,37 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
     err = "primitive-pair and pair-frame build failed";
   }
   b->ppcount = ppcount;
+  if (st == SHGO_OK && b->sparse) {
+    // block-sparse layout: pairs with a kept primitive pair, in pair order
+    const int64_t np = (int64_t)pa.size();
+    uint8_t* live = nullptr;
+    cudaError_t e = pool_alloc(device, (void**)&live, (size_t)std::max<int64_t>(np, 1));
+    if (e == cudaSuccess) {
+      b->allocations.push_back(live);
+      st = launch_pair_live(b->d, np, ppcount, live, 0, &err);
+      std::vector<uint8_t> h(np);
+      if (st == SHGO_OK && np) e = cudaMemcpy(h.data(), live, (size_t)np, cudaMemcpyDeviceToHost);
+      b->h_blk_off.assign(np, -1);
+      int64_t off = 0, nblk = 0;
+      for (int64_t q = 0; q < np && e == cudaSuccess; ++q)
+        if (h[q]) {
+          b->h_blk_off[q] = off;
+          off += (int64_t)(2 * l[pa[q]] + 1) * (2 * l[pb[q]] + 1);
+          ++nblk;
+        }
+      b->sparse_nblocks = nblk;
+      b->sparse_ndoubles = off;
+      if (e == cudaSuccess) e = pool_alloc(device, (void**)&b->d_blk_off, sizeof(int64_t) * (size_t)std::max<int64_t>(np, 1));
+      if (e == cudaSuccess) {
+        b->allocations.push_back(b->d_blk_off);
+        if (np) e = cudaMemcpy(b->d_blk_off, b->h_blk_off.data(), sizeof(int64_t) * (size_t)np, cudaMemcpyHostToDevice);
+      }
+    }
+    if (e != cudaSuccess && st == SHGO_OK) {
+      st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+      err = std::string("block-sparse layout: ") + cudaGetErrorString(e);
+    }
+  }
   if (st != SHGO_OK) {
     release(b);
     return fail(st, err);
@@ -866,6 +908,16 @@ shgo_status shgo_eri_jk(const shgo_basis* basis, const double* density, double* 
 int64_t shgo_basis_nbf(const shgo_basis* basis) { return basis ? basis->nbf : -1; }
 int64_t shgo_basis_npairs(const shgo_basis* basis) { return basis ? basis->npairs : -1; }
 
+shgo_status shgo_sparse_layout(const shgo_basis* basis, int64_t* nblocks, int64_t* ndoubles, int64_t* offset) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (!basis->sparse) return fail(SHGO_ERR_INVALID_ARG, "the basis was not created with SHGO_FLAG_BLOCK_SPARSE");
+  if (nblocks) *nblocks = basis->sparse_nblocks;
+  if (ndoubles) *ndoubles = basis->sparse_ndoubles;
+  if (offset) std::copy(basis->h_blk_off.begin(), basis->h_blk_off.end(), offset);
+  return SHGO_OK;
+}
+
 shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers* centers, const double* charges,
                                     double* out, void* stream) {
   g_last_error.clear();
@@ -878,7 +930,8 @@ shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers*
   if (prev != basis->device) cudaSetDevice(basis->device);
   std::string err;
   shgo_status st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
-                                             centers->xyz, charges, out, (cudaStream_t)stream, &err);
+                                             centers->xyz, charges, out, (cudaStream_t)stream, &err, nullptr, true,
+                                             basis->sparse ? basis->d_blk_off : nullptr, basis->sparse_ndoubles);
   if (st == SHGO_OK && basis->nbf > 0 && centers->n > 0 && finish_call(basis, (cudaStream_t)stream) != cudaSuccess) {
     st = SHGO_ERR_CUDA;
     err = "status read-back failed";
@@ -934,7 +987,8 @@ shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_ce
   for (auto& e : ev) cudaEventCreate(&e);
   std::string err;
   shgo_status st = launch_nuclear_attraction(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
-                                             centers->xyz, charges, out, (cudaStream_t)stream, &err, ev);
+                                             centers->xyz, charges, out, (cudaStream_t)stream, &err, ev, true,
+                                             basis->sparse ? basis->d_blk_off : nullptr, basis->sparse_ndoubles);
   if (st == SHGO_OK && basis->nbf > 0 && centers->n > 0) finish_call(basis, (cudaStream_t)stream);
   if (st == SHGO_OK) {
     cudaError_t e = cudaEventSynchronize(ev[2]);
@@ -1020,6 +1074,7 @@ shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const s
   }
   mv.ncenters = centers->n;
   mv.nbf = basis->nbf;
+  mv.blk_off = basis->sparse ? basis->d_blk_off : nullptr;
   std::string err;
   const shgo_status st = launch_class_timed(basis->d, *basis->tabs, basis->work, mv, centers->xyz, charges, out,
                                             (cudaStream_t)stream, ms, &err);
@@ -1190,6 +1245,7 @@ shgo_status shgo_nuclear_attraction_screened(shgo_basis* basis, const double* ce
   mv.nbf = basis->nbf;
   mv.clist = basis->scr_clist;
   mv.clist_off = basis->scr_clist_off;
+  mv.blk_off = basis->sparse ? basis->d_blk_off : nullptr;
   const double per_pair = basis->npairs > 0 ? (double)basis->scr_ntrip / (double)basis->npairs : 0.0;
   std::string err;
   shgo_status st = launch_batched(basis->d, *basis->tabs, basis->work, mv, per_pair, centers, charges, out,

@@ -185,6 +185,8 @@ struct MolView {
   // Screening: when set, the nuclei of pair pr are centers[clist[clist_off[pr] .. clist_off[pr + 1])]
   const int* clist = nullptr;
   const int64_t* clist_off = nullptr;
+  // Block-sparse output: when set, pair pr's block goes row-major to out + blk_off[pr] (nothing for -1)
+  const int64_t* blk_off = nullptr;
 };
 
 __device__ __forceinline__ void mol_centers(const MolView& mv, int pr, int64_t& c_begin, int64_t& n) {
@@ -353,6 +355,7 @@ struct DeviceBasis {
   double* rbuf = nullptr;        // coupling buffer R'[L,M,k] per primitive pair
   int64_t rbuf_len = 0;
   int precision = SHGO_PREC_FP64;  // a shgo_precision value
+  int prim_bound = 1;              // 1: primitive pairs below the elementwise bound are skipped
   // Bounded coupling buffer: region > 0 means rbuf holds one region of `region` doubles per pool
   // stream and each class runs in chunks of whole shell pairs that fit its stream's region;
   // h_ppoff (host, npairs + 1) gives the primitive-pair offsets used to cut the chunks.
@@ -415,11 +418,16 @@ inline cudaError_t set_max_dynamic_smem(const void* func) {
 // on several devices sets it on each.
 cudaError_t ensure_max_dynamic_smem(const void* func, int bytes = 0);
 
+// blk_off (device, per pair) selects the block-sparse output of out_doubles values (see MolView::blk_off).
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
                                       const double* centers, const double* charges, double* out,
                                       cudaStream_t stream, std::string* err, cudaEvent_t* events = nullptr,
-                                      bool concurrent = true);
+                                      bool concurrent = true, const int64_t* blk_off = nullptr,
+                                      int64_t out_doubles = 0);
+// Per shell pair: 1 when at least one of its primitive pairs is kept (pref != 0), else 0 (device, async).
+shgo_status launch_pair_live(const DeviceBasis& db, int64_t npairs, int64_t npp, uint8_t* live, cudaStream_t stream,
+                             std::string* err);
 int64_t launches_per_call(const std::vector<ClassWork>& work, int64_t nbf);
 
 // The same launches one class after another on `stream`, with the device time of each class's

@@ -89,7 +89,7 @@ __global__ void k_pair_build(int64_t npp, const int* __restrict__ pp_pair, const
                              const int* __restrict__ pair_a, const int* __restrict__ pair_b,
                              const double* __restrict__ shell_xyz, const int* __restrict__ shell_l,
                              const int* __restrict__ shell_poff, const double* __restrict__ prim_exp,
-                             const double* __restrict__ prim_coef, PPData* __restrict__ ppd) {
+                             const double* __restrict__ prim_coef, int use_bound, PPData* __restrict__ ppd) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npp; q += (int64_t)gridDim.x * blockDim.x) {
     const int pr = pp_pair[q], ij = pp_ij[q];
     const int a = pair_a[pr], b = pair_b[pr];
@@ -106,9 +106,23 @@ __global__ void k_pair_build(int64_t npp, const int* __restrict__ pp_pair, const
     d.rb = ea * d.rp;
     const double ab = sqrt(ab2);
     d.shift = d.ra * ab;
-    if (d.pref != 0.0 && prim_pair_bound(shell_l[a], shell_l[b], d.shift, d.rb * ab, d.p, d.pref) < kPrimSkip)
+    if (use_bound && d.pref != 0.0 &&
+        prim_pair_bound(shell_l[a], shell_l[b], d.shift, d.rb * ab, d.p, d.pref) < kPrimSkip)
       d.pref = 0.0;
     ppd[q] = d;
+  }
+}
+
+// Per shell pair: whether any of its primitive pairs is kept (the block-sparse layout's criterion, the same
+// test the pair kernel applies before writing a block).
+__global__ void k_pair_live(int64_t npairs, const int64_t* __restrict__ pair_ppoff, int64_t npp_total,
+                            const PPData* __restrict__ ppd, uint8_t* __restrict__ live) {
+  for (int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pr < npairs;
+       pr += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q1 = pr + 1 < npairs ? pair_ppoff[pr + 1] : npp_total;
+    uint8_t any = 0;
+    for (int64_t q = pair_ppoff[pr]; q < q1 && !any; ++q) any = ppd[q].pref != 0.0;
+    live[pr] = any;
   }
 }
 
@@ -349,7 +363,8 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
     }
     __syncthreads();
     if (!live) {
-      // every primitive pair skipped: the block is zero
+      // every primitive pair skipped: the block is zero (and omitted from a block-sparse output)
+      if (mv.blk_off) return;
       const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
       int64_t obase, ld;
       mol_output(mv, pr, obase, ld);
@@ -396,6 +411,17 @@ __global__ void __launch_bounds__(128) k_pair_block(int la, int lb, int npairs, 
       Vp[e] = s;
     }
     __syncthreads();
+    if (mv.blk_off) {
+      // block-sparse output: the block alone, row-major
+      const int64_t off = mv.blk_off[pr];
+      if (off < 0) return;
+      double* o = out + off;
+      for (int e = tid; e < na * nb; e += nth) {
+        const int ma = e / nb, mb = e % nb;
+        o[e] = (a == b && ma > mb) ? Vp[mb * nb + ma] : Vp[e];
+      }
+      return;
+    }
     const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
     int64_t obase, ld;
     mol_output(mv, pr, obase, ld);
@@ -1003,7 +1029,8 @@ shgo_status launch_error(std::string* err) {
 shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables& dt,
                                       const std::vector<ClassWork>& work, int64_t nbf, int64_t ncenters,
                                       const double* centers, const double* charges, double* out,
-                                      cudaStream_t stream, std::string* err, cudaEvent_t* events, bool concurrent) {
+                                      cudaStream_t stream, std::string* err, cudaEvent_t* events, bool concurrent,
+                                      const int64_t* blk_off, int64_t out_doubles) {
   if (events) cudaEventRecord(events[0], stream);
   if (nbf == 0 || ncenters == 0) {
     if (events) cudaEventRecord(events[1], stream);
@@ -1013,7 +1040,8 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
     return SHGO_OK;
   }
   if (ncenters == 0) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nbf * (size_t)nbf, stream);
+    const size_t n = blk_off ? (size_t)out_doubles : (size_t)nbf * (size_t)nbf;
+    cudaError_t e = n ? cudaMemsetAsync(out, 0, sizeof(double) * n, stream) : cudaSuccess;
     if (events) cudaEventRecord(events[2], stream);
     if (e != cudaSuccess) {
       *err = cudaGetErrorString(e);
@@ -1027,6 +1055,7 @@ shgo_status launch_nuclear_attraction(const DeviceBasis& db, const DeviceTables&
   MolView mv;
   mv.ncenters = ncenters;
   mv.nbf = nbf;
+  mv.blk_off = blk_off;
   const Launcher L{db, dt, th, mv, centers, charges, out, nullptr};
   cudaError_t e = clear_ctrl(db, work.size(), stream);
   if (events && db.region > 0) {
@@ -1196,7 +1225,16 @@ shgo_status launch_pair_build(const DeviceBasis& db, int64_t npp, cudaStream_t s
   if (npp == 0) return SHGO_OK;
   const int64_t blocks = std::min<int64_t>((npp + 255) / 256, 152 * 32);
   k_pair_build<<<(int)blocks, 256, 0, stream>>>(npp, db.pp_pair, db.pp_ij, db.pair_a, db.pair_b, db.shell_xyz,
-                                                 db.shell_l, db.shell_poff, db.prim_exp, db.prim_coef, db.ppd);
+                                                 db.shell_l, db.shell_poff, db.prim_exp, db.prim_coef, db.prim_bound,
+                                                 db.ppd);
+  return launch_error(err);
+}
+
+shgo_status launch_pair_live(const DeviceBasis& db, int64_t npairs, int64_t npp, uint8_t* live, cudaStream_t stream,
+                             std::string* err) {
+  if (npairs == 0) return SHGO_OK;
+  const int64_t blocks = std::min<int64_t>((npairs + 255) / 256, 152 * 32);
+  k_pair_live<<<(int)blocks, 256, 0, stream>>>(npairs, db.pair_ppoff, npp, db.ppd, live);
   return launch_error(err);
 }
 

@@ -115,14 +115,27 @@ def calibrate_margin(net, X, T, log10_cut: float, safety: float = 1.0) -> float:
     return float(max(0.0, np.max(log10_cut - y[pos])) + safety)
 
 
-def audit(basis: dict, shell_a, shell_b, centers, charges, mask, pair_nuc, fraction, rng, threshold):
-    """Exact check of a random `fraction` of the skipped triples.  mask is the screening mask over
-    all triples in pair order (pair q owns pair_nuc[q] consecutive entries, nuclei in order)."""
-    skipped = np.nonzero(mask == 0)[0]
-    if len(skipped) == 0:
+def audit(basis: dict, shell_a, shell_b, centers, charges, mask, pair_nuc, fraction, rng, threshold,
+          max_audit: int = 200_000):
+    """Exact check of a random `fraction` of the skipped triples (at most max_audit of them).  mask is the
+    screening mask over all triples in pair order (pair q owns pair_nuc[q] consecutive entries, nuclei in
+    order).  Skipped triples are drawn by rejection from uniform triple indices, so no list of all skipped
+    triples is formed."""
+    n_skip = int(mask.size - np.count_nonzero(mask))
+    if n_skip == 0:
         return {"audited": 0, "false_skips": 0, "false_skip_rate": 0.0, "max_skipped_block": 0.0}
-    k = max(1, int(round(fraction * len(skipped))))
-    pick = np.sort(rng.choice(skipped, size=min(k, len(skipped)), replace=False))
+    k = min(max(1, int(round(fraction * n_skip))), max_audit, n_skip)
+    if k == n_skip:
+        pick = np.nonzero(mask == 0)[0]
+    else:
+        chosen = set()
+        while len(chosen) < k:
+            cand = rng.integers(0, mask.size, size=4 * (k - len(chosen)) * max(1, mask.size // n_skip))
+            for t in cand[mask[cand] == 0]:
+                chosen.add(int(t))
+                if len(chosen) == k:
+                    break
+        pick = np.sort(np.fromiter(chosen, dtype=np.int64))
     starts = np.concatenate([[0], np.cumsum(pair_nuc)[:-1]])
     q = np.searchsorted(starts, pick, side="right") - 1
     c = pick - starts[q]

@@ -31,7 +31,11 @@ class ShgoError(RuntimeError):
 
 
 class shgo_options(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+    _fields_ = [("precision", ctypes.c_int32), ("device", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+SHGO_FLAG_BLOCK_SPARSE = 1
+SHGO_FLAG_NO_PRIM_BOUND = 2
 
 
 class shgo_centers(ctypes.Structure):
@@ -94,6 +98,9 @@ def _load() -> ctypes.CDLL:
     lib.shgo_eri_jk.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
+    lib.shgo_sparse_layout.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]
+    lib.shgo_sparse_layout.restype = ctypes.c_int
     lib.shgo_basis_set_time_limit.argtypes = [ctypes.c_void_p, ctypes.c_double]
     lib.shgo_basis_set_time_limit.restype = ctypes.c_int
     lib.shgo_basis_sync.argtypes = [ctypes.c_void_p]
@@ -142,14 +149,15 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 
 # ------------------------------------------------------------------ C-ABI names
-def shgo_basis_create(n_shells, l, n_prim, exponents, coefs, shell_xyz, precision=SHGO_PREC_FP64, device=-1):
+def shgo_basis_create(n_shells, l, n_prim, exponents, coefs, shell_xyz, precision=SHGO_PREC_FP64, device=-1,
+                      flags=0):
     """Returns an opaque handle (int).  Host arrays are copied by the library."""
     l = np.ascontiguousarray(l, dtype=np.int32)
     n_prim = np.ascontiguousarray(n_prim, dtype=np.int32)
     exponents = np.ascontiguousarray(exponents, dtype=np.float64)
     coefs = np.ascontiguousarray(coefs, dtype=np.float64)
     shell_xyz = np.ascontiguousarray(shell_xyz, dtype=np.float64).reshape(-1)
-    opt = shgo_options(int(precision), int(device))
+    opt = shgo_options(int(precision), int(device), int(flags))
     handle = ctypes.c_void_p()
     _check(_lib.shgo_basis_create(int(n_shells), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32),
                                   _ptr(exponents, ctypes.c_double), _ptr(coefs, ctypes.c_double),
@@ -239,14 +247,31 @@ def shgo_basis_npairs(basis) -> int:
 
 
 # ------------------------------------------------------------------ convenience wrappers
+def shgo_sparse_layout(basis):
+    """(nblocks, ndoubles, offset[npairs]) of a block-sparse basis (offset -1 for an omitted pair)."""
+    nb = ctypes.c_int64()
+    nd = ctypes.c_int64()
+    off = np.zeros(max(shgo_basis_npairs(basis), 0), dtype=np.int64)
+    _check(_lib.shgo_sparse_layout(ctypes.c_void_p(basis), ctypes.byref(nb), ctypes.byref(nd),
+                                   _ptr(off, ctypes.c_int64)))
+    return int(nb.value), int(nd.value), off
+
+
 class Basis:
     """Owns a shgo_basis handle built from a basis dict (see workloads.py)."""
 
-    def __init__(self, basis: dict, precision: int = SHGO_PREC_FP64, device: int = -1):
+    def __init__(self, basis: dict, precision: int = SHGO_PREC_FP64, device: int = -1, flags: int = 0):
         self.handle = shgo_basis_create(len(basis["l"]), basis["l"], basis["nprim"], basis["exps"], basis["coefs"],
-                                        basis["xyz"], precision, device)
+                                        basis["xyz"], precision, device, flags)
         self.nbf = shgo_basis_nbf(self.handle)
         self.npairs = shgo_basis_npairs(self.handle)
+        self.sparse = bool(flags & SHGO_FLAG_BLOCK_SPARSE)
+        if self.sparse:
+            self.nblocks, self.ndoubles, self.offset = shgo_sparse_layout(self.handle)
+
+    def out_shape(self):
+        """Shape of V's output array: (nbf, nbf), or (ndoubles,) for a block-sparse basis."""
+        return (max(self.ndoubles, 1),) if self.sparse else (self.nbf, self.nbf)
 
     def close(self) -> None:
         if getattr(self, "handle", None):
@@ -270,9 +295,9 @@ def nuclear_attraction(basis: Basis, centers, charges, out=None, stream=None):
     centers = centers.contiguous()
     charges = charges.contiguous()
     if out is None:
-        out = torch.empty((basis.nbf, basis.nbf), dtype=torch.float64, device=centers.device)
-    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != (basis.nbf, basis.nbf):
-        raise ValueError("out must be a contiguous float64 [nbf, nbf] tensor")
+        out = torch.empty(basis.out_shape(), dtype=torch.float64, device=centers.device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != basis.out_shape():
+        raise ValueError(f"out must be a contiguous float64 {list(basis.out_shape())} tensor")
     n = centers.shape[0] if centers.numel() else 0
     shgo_nuclear_attraction(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
                             out.data_ptr(), stream)
@@ -463,7 +488,7 @@ class Batch:
         exps = np.ascontiguousarray(np.concatenate([b["exps"] for b, _ in molecules]), dtype=np.float64)
         coefs = np.ascontiguousarray(np.concatenate([b["coefs"] for b, _ in molecules]), dtype=np.float64)
         xyz = np.ascontiguousarray(np.concatenate([b["xyz"] for b, _ in molecules]), dtype=np.float64).reshape(-1)
-        opt = shgo_options(int(precision), int(device))
+        opt = shgo_options(int(precision), int(device), 0)
         handle = ctypes.c_void_p()
         _check(_lib.shgo_batch_create(len(molecules), _ptr(mol_nshells, ctypes.c_int32), _ptr(mol_ncent, ctypes.c_int64),
                                       len(l), _ptr(l, ctypes.c_int32), _ptr(nprim, ctypes.c_int32),

@@ -410,3 +410,28 @@ def test_eri_method_model_wide_exponent_ratios(ls, exps, shared):
     ref = E[off[0]:off[1], off[1]:off[2], off[2]:off[3], off[3]:off[4]]
     got = _eri_model(ls, np.array(exps), cen)
     assert np.all(np.abs(got - ref) <= 1e-13 + 1e-11 * np.abs(ref))
+
+
+def test_option_flags_are_validated_on_the_host():
+    """Unknown option bits and a block-sparse batch are rejected before any device work."""
+    import ctypes
+    opt = shgo.shgo_options(0, -1, 64)
+    h = ctypes.c_void_p()
+    l = np.array([0], dtype=np.int32)
+    npr = np.array([1], dtype=np.int32)
+    one = np.array([1.0])
+    xyz = np.zeros(3)
+    st = shgo._lib.shgo_basis_create(1, shgo._ptr(l, ctypes.c_int32), shgo._ptr(npr, ctypes.c_int32),
+                                     shgo._ptr(one, ctypes.c_double), shgo._ptr(one, ctypes.c_double),
+                                     shgo._ptr(xyz, ctypes.c_double), ctypes.byref(opt), ctypes.byref(h))
+    assert st == 1 and "flag" in shgo._lib.shgo_last_error().decode()
+    opt = shgo.shgo_options(0, -1, shgo.SHGO_FLAG_BLOCK_SPARSE)
+    nsh = np.array([1], dtype=np.int32)
+    nc = np.array([1], dtype=np.int64)
+    st = shgo._lib.shgo_batch_create(1, shgo._ptr(nsh, ctypes.c_int32), shgo._ptr(nc, ctypes.c_int64), 1,
+                                     shgo._ptr(l, ctypes.c_int32), shgo._ptr(npr, ctypes.c_int32),
+                                     shgo._ptr(one, ctypes.c_double), shgo._ptr(one, ctypes.c_double),
+                                     shgo._ptr(xyz, ctypes.c_double), ctypes.byref(opt), ctypes.byref(h))
+    assert st == 1 and "batch" in shgo._lib.shgo_last_error().decode()
+    with pytest.raises(shgo.ShgoError):
+        shgo.shgo_sparse_layout(0)
