@@ -776,69 +776,153 @@ def run_screened(args) -> int:
     return 0
 
 
-def run_precision_sweep(n_triples: int, n_oracle: int) -> int:
-    """Precision sweep over independent primitive triples (la, lb <= 8, exponents log-uniform
-    [0.01, 1000], |AB|, |PC| <= 15): per (la, lb) class, the block-normwise error of FP32-bulk and
-    FP32-plain against the FP64 GPU path, and of the FP64 GPU path against the oracle (double and
-    extended) on the first n_oracle triples.  Prints one JSON line."""
-    import torch
+def _sweep_oracle_blocks(job):
+    """Oracle blocks <a|Z/|r - C||b> of precision-sweep triples (runs in a spawned worker process):
+    job = (rows [k, 11] of la, lb, alpha, beta, B, C, Z; "f64" or "ld")."""
+    import oracle
+    from paper_2404_16245_gb300 import workloads as W
+    rows, precision = job
+    out = []
+    for r in rows:
+        la, lb = int(r[0]), int(r[1])
+        basis = W.make_basis([la, lb], [1, 1], [r[2], r[3]], [1.0, 1.0], [np.zeros(3), r[4:7]])
+        V = oracle.nuclear_attraction(basis, r[7:10].reshape(1, 3), r[10:11], precision=precision)
+        out.append(V[:2 * la + 1, 2 * la + 1:].copy())
+    return out
+
+
+def run_precision_sweep(n_triples: int, n_oracle: int, n_ext: int = 100, chunk: int = 250_000) -> int:
+    """Precision sweep over n_triples independent primitive triples (la, lb <= 8, exponents log-uniform
+    [0.01, 1000], |AB|, |PC| <= 15, Z <= 20).  Every triple runs through the batched entry point in FP64,
+    FP32-bulk and FP32-plain (one molecule per triple, `chunk` molecules per batch); per (la, lb) class the
+    block-normwise error max|x - y| / max|y| of the FP32 forms against FP64, and of FP64 against the oracle
+    in double on the first n_oracle triples of each class and in extended precision (binary128 on the
+    aarch64 host, 80-bit on x86-64) on the first n_ext.  The oracle runs in a pool of spawned processes, one
+    per host core, started before any GPU work.  Prints one JSON line."""
+    import multiprocessing as mp
 
     import oracle
-    from paper_2404_16245_gb300 import shgo
     from paper_2404_16245_gb300 import workloads as W
 
-    def gpu(basis, Cd, Zd, prec):
-        B = shgo.Basis(basis, precision=prec)
-        V = shgo.nuclear_attraction(B, Cd, Zd)
-        out = V.cpu().numpy()
-        B.close()
-        return out
+    t_start = time.perf_counter()
+    la, lb, alpha, beta, B, C, Z = W.config5_arrays(n_triples)
+    rows = np.column_stack([la, lb, alpha, beta, B, C, Z]).astype(np.float64)
+    cls = la * 9 + lb
+    sub_f64, sub_ext = {}, {}
+    for k in range(81):
+        idx = np.nonzero(cls == k)[0]
+        sub_f64[k] = idx[:n_oracle]
+        sub_ext[k] = idx[:n_ext]
+    oracle.build()
+    ncpu = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(ncpu)
 
-    def err(g, r, floor=1e-290):
-        # blocks below the normal double range (|y| < 1e-290: K_AB underflow) carry no relative accuracy;
-        # against the oracle, blocks below the primitive-pair bound (1e-20 per unit of total charge) are
-        # ones the GPU path may skip by design and are left out too
-        s = np.max(np.abs(r))
-        return float(np.max(np.abs(g - r)) / s) if s > floor else None
+    def submit(sub, precision):
+        order = np.concatenate([sub[k] for k in range(81)])
+        parts = np.array_split(order, max(1, 8 * ncpu))
+        return order, pool.map_async(_sweep_oracle_blocks, [(rows[p], precision) for p in parts])
 
-    stats: dict = {}
-    for t, (basis, C, Z) in enumerate(W.config5(n_triples, replica=0)):
-        la, lb = int(basis["l"][0]), int(basis["l"][1])
-        key = f"{max(la, lb)},{min(la, lb)}"
-        na = 2 * la + 1
-        Cd = torch.tensor(C, device="cuda")
-        Zd = torch.tensor(Z, device="cuda")
-        v64 = gpu(basis, Cd, Zd, shgo.SHGO_PREC_FP64)[:na, na:]
-        vb = gpu(basis, Cd, Zd, shgo.SHGO_PREC_FP32_BULK)[:na, na:]
-        vp = gpu(basis, Cd, Zd, shgo.SHGO_PREC_FP32_PLAIN)[:na, na:]
-        st = stats.setdefault(key, {"n": 0, "bulk": [], "plain": [], "fp64_vs_oracle": [], "oracle_f64_vs_ld": []})
-        st["n"] += 1
-        for name, val in (("bulk", err(vb, v64)), ("plain", err(vp, v64))):
-            if val is not None:
-                st[name].append(val)
-        if t < n_oracle:
-            ld = oracle.nuclear_attraction(basis, C, Z, precision="ld")[:na, na:]
-            d = oracle.nuclear_attraction(basis, C, Z)[:na, na:]
-            skip = 1.01e-20 * float(np.sum(np.abs(Z)))
-            for name, val in (("fp64_vs_oracle", err(v64, ld, skip)), ("oracle_f64_vs_ld", err(d, ld))):
-                if val is not None:
-                    st[name].append(val)
-    out = {}
-    for key, st in sorted(stats.items()):
-        row = {"n": st["n"]}
-        for name in ("bulk", "plain", "fp64_vs_oracle", "oracle_f64_vs_ld"):
-            if st[name]:
-                row[name] = {"max": max(st[name]), "median": float(np.median(st[name]))}
-        out[key] = row
-    allb = [e for st in stats.values() for e in st["bulk"]]
-    allp = [e for st in stats.values() for e in st["plain"]]
-    allo = [e for st in stats.values() for e in st["fp64_vs_oracle"]]
-    print(json.dumps({"precision_sweep": {"triples": n_triples, "oracle_triples": n_oracle,
-                                          "measure": "per block max|x-y| / max|y|",
-                                          "bulk_max": max(allb), "bulk_median": float(np.median(allb)),
-                                          "plain_max": max(allp), "plain_median": float(np.median(allp)),
-                                          "fp64_vs_extended_oracle_max": max(allo) if allo else None,
-                                          "per_class": out}}), flush=True)
+    ord_f64, job_f64 = submit(sub_f64, "f64")
+    ord_ext, job_ext = submit(sub_ext, "ld")
+
+    import torch
+
+    from paper_2404_16245_gb300 import shgo
+    dev = torch.device("cuda", 0)
+    keep = set(np.concatenate([ord_f64, ord_ext]).tolist())
+    fp64_blocks = {}
+    errs = {k: {"bulk": [], "plain": []} for k in range(81)}
+
+    def rel(g, r, floor):
+        s = np.max(np.abs(r), axis=(1, 2))
+        d = np.max(np.abs(g - r), axis=(1, 2))
+        ok = s > floor
+        return d[ok] / s[ok]
+
+    t_gpu = 0.0
+    for c0 in range(0, n_triples, chunk):
+        c1 = min(n_triples, c0 + chunk)
+        m = c1 - c0
+        l2 = np.column_stack([la[c0:c1], lb[c0:c1]]).reshape(-1)
+        xyz = np.zeros((m, 2, 3))
+        xyz[:, 1] = B[c0:c1]
+        mols = {"nshells": np.full(m, 2), "l": l2, "nprim": np.ones(2 * m, dtype=np.int32),
+                "exps": np.column_stack([alpha[c0:c1], beta[c0:c1]]).reshape(-1), "coefs": np.ones(2 * m),
+                "xyz": xyz.reshape(-1, 3)}
+        Cd = torch.tensor(C[c0:c1], device=dev)
+        Zd = torch.tensor(Z[c0:c1], device=dev)
+        blocks = {}
+        for name, prec in (("fp64", shgo.SHGO_PREC_FP64), ("bulk", shgo.SHGO_PREC_FP32_BULK),
+                           ("plain", shgo.SHGO_PREC_FP32_PLAIN)):
+            t0 = time.perf_counter()
+            batch = shgo.Batch.from_arrays(mols, np.ones(m, dtype=np.int64), precision=prec)
+            out = shgo.nuclear_attraction_batched(batch, Cd, Zd)
+            torch.cuda.synchronize()
+            t_gpu += time.perf_counter() - t0
+            oh = out.cpu().numpy()
+            per = {}
+            for k in np.unique(cls[c0:c1]):
+                i, j = int(k) // 9, int(k) % 9
+                na, nb = 2 * i + 1, 2 * j + 1
+                ms = np.nonzero(cls[c0:c1] == k)[0]
+                idx = (batch.mol_off[ms][:, None, None] + np.arange(na)[None, :, None] * (na + nb) + na
+                       + np.arange(nb)[None, None, :])
+                per[int(k)] = (ms, oh[idx])
+            blocks[name] = per
+            batch.close()
+            del out
+        for k, (ms, v64) in blocks["fp64"].items():
+            errs[k]["bulk"].append(rel(blocks["bulk"][k][1], v64, 1e-290))
+            errs[k]["plain"].append(rel(blocks["plain"][k][1], v64, 1e-290))
+            for t_local, blk in zip(ms, v64):
+                t = c0 + int(t_local)
+                if t in keep:
+                    fp64_blocks[t] = blk
+    res_f64 = [blk for part in job_f64.get() for blk in part]
+    res_ext = [blk for part in job_ext.get() for blk in part]
+    pool.close()
+    pool.join()
+    ref_f64 = dict(zip(ord_f64.tolist(), res_f64))
+    ref_ext = dict(zip(ord_ext.tolist(), res_ext))
+
+    def stat(v):
+        v = np.concatenate(v) if isinstance(v, list) and v and isinstance(v[0], np.ndarray) else np.asarray(v)
+        return {"max": float(v.max()), "median": float(np.median(v)), "n": int(v.size)} if v.size else None
+
+    per_class, all_b, all_p, all_o, all_x = {}, [], [], [], []
+    for k in range(81):
+        i, j = k // 9, k % 9
+        row = {"n": int(np.sum(cls == k)), "bulk_vs_fp64": stat(errs[k]["bulk"]),
+               "plain_vs_fp64": stat(errs[k]["plain"])}
+        skip = 1.01e-20 * 20.0  # below the primitive-pair bound the GPU path may skip by design
+        eo, ex, od = [], [], []
+        for t in sub_f64[k]:
+            r, g = ref_f64[int(t)], fp64_blocks[int(t)]
+            if np.max(np.abs(r)) > skip:
+                eo.append(np.max(np.abs(g - r)) / np.max(np.abs(r)))
+        for t in sub_ext[k]:
+            r, g = ref_ext[int(t)], fp64_blocks[int(t)]
+            if np.max(np.abs(r)) > skip:
+                ex.append(np.max(np.abs(g - r)) / np.max(np.abs(r)))
+                if int(t) in ref_f64:
+                    od.append(np.max(np.abs(ref_f64[int(t)] - r)) / np.max(np.abs(r)))
+        row["fp64_vs_oracle_double"] = stat(eo)
+        row["fp64_vs_oracle_extended"] = stat(ex)
+        row["oracle_double_vs_extended"] = stat(od)
+        per_class[f"{i},{j}"] = row
+        all_b += errs[k]["bulk"]
+        all_p += errs[k]["plain"]
+        all_o += eo
+        all_x += ex
+    line = {"precision_sweep": {
+        "triples": n_triples, "oracle_double_per_class": n_oracle, "oracle_extended_per_class": n_ext,
+        "oracle_extended_bits": oracle.real_bits("ld"), "host_cores": ncpu,
+        "measure": "per (shell pair, nucleus) block: max|x - y| / max|y|; blocks with max|y| below 1e-290 "
+                   "(K_AB underflow) or, against the oracle, below the primitive-pair bound left out",
+        "fp32_bulk_vs_fp64": stat(all_b), "fp32_plain_vs_fp64": stat(all_p),
+        "fp64_vs_oracle_double": stat(all_o), "fp64_vs_oracle_extended": stat(all_x),
+        "gpu_s": t_gpu, "wall_s": time.perf_counter() - t_start, "per_class": per_class}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -1062,11 +1146,23 @@ def run_peaks(args) -> int:
     time.sleep(0.3)
     r64 = measure_fma_peak("fp64", stream, repeats=5)
     r32 = measure_fma_peak("fp32", stream, repeats=5)
+    # launch-shape sweep: the rate should not depend on chains or threads once the pipe is full
+    from paper_2404_16245_gb300 import shgo
+    sweep = {}
+    for name, prec, iters in (("fp64", shgo.SHGO_PREC_FP64, PEAK_ITERS["fp64"]),
+                              ("fp32", shgo.SHGO_PREC_FP32_BULK, PEAK_ITERS["fp32"])):
+        rows = []
+        for chains in (4, 8, 16):
+            for tps in (512, 1024, 2048):
+                it = max(1, iters * 8 * 2048 // (chains * tps))
+                rate, ms = shgo.shgo_measure_fma_rate_shape(prec, it, chains, tps, stream)
+                rows.append({"chains": chains, "threads_per_sm": tps, "tflops": rate / 1e12, "ms": ms})
+        sweep[name] = rows
     time.sleep(0.3)
     clocks = sampler.stop()
     clk = clocks.get("sm_max_mhz") or 2070.0
     line = {"workload": "peaks", "fp64_tflops": r64["tflops"], "fp32_tflops": r32["tflops"],
-            "fp64_runs": r64, "fp32_runs": r32, "clocks": clocks,
+            "fp64_runs": r64, "fp32_runs": r32, "shape_sweep": sweep, "clocks": clocks,
             "fp64_nominal_at_max_clock": fp64_peak_tflops(clk), "fp32_nominal_at_max_clock": 2 * fp32_lane_peak_t(clk),
             "how": "shgo_measure_fma_rate: grid of 2048 threads per SM, each 8 independent FMA chains x 4 x iters; "
                    "best of 5 timed launches (CUDA events), one warm-up launch before each"}
@@ -1102,7 +1198,10 @@ def main():
                     help="one warm + one measured call, for ncu (the benchmark molecule or one batched molecule)")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
-    ap.add_argument("--sweep-oracle", type=int, default=200, help="triples also checked against the oracle")
+    ap.add_argument("--sweep-oracle", type=int, default=200,
+                    help="triples per (la, lb) class also checked against the double oracle")
+    ap.add_argument("--sweep-ext", type=int, default=20,
+                    help="triples per (la, lb) class also checked against the extended-precision oracle")
     ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri", "peaks"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
@@ -1137,7 +1236,7 @@ def main():
     if args.profile_case:
         return run_profile_case(args.precision, args.profile_case)
     if args.precision_sweep:
-        return run_precision_sweep(args.precision_sweep, args.sweep_oracle)
+        return run_precision_sweep(args.precision_sweep, args.sweep_oracle, args.sweep_ext)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "screened":

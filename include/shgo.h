@@ -326,6 +326,13 @@ shgo_status shgo_nuclear_attraction_class_timed(const shgo_basis* basis, const s
  * SHGO_ERR_OOM, SHGO_ERR_CUDA. */
 shgo_status shgo_measure_fma_rate(int32_t precision, int64_t iters, void* stream, double* flops_per_s, double* ms);
 
+/* The same measurement with a chosen launch shape: `chains` independent chains per thread (4, 8 or 16) and
+ * threads_per_sm threads on every SM (a multiple of 256, at most 2048); shgo_measure_fma_rate is chains = 8,
+ * threads_per_sm = 2048.  A sweep over shapes shows whether the rate is the pipe's or the launch's.
+ * Errors as shgo_measure_fma_rate, plus SHGO_ERR_INVALID_ARG for a shape outside those values. */
+shgo_status shgo_measure_fma_rate_shape(int32_t precision, int64_t iters, int32_t chains, int32_t threads_per_sm,
+                                        void* stream, double* flops_per_s, double* ms);
+
 /* Release a basis and its device memory (synchronises its device).  NULL-safe. */
 void shgo_free(shgo_basis* basis);
 

@@ -107,6 +107,9 @@ def _load() -> ctypes.CDLL:
     lib.shgo_basis_sync.restype = ctypes.c_int
     lib.shgo_measure_fma_rate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, f64p, f64p]
     lib.shgo_measure_fma_rate.restype = ctypes.c_int
+    lib.shgo_measure_fma_rate_shape.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_void_p, f64p, f64p]
+    lib.shgo_measure_fma_rate_shape.restype = ctypes.c_int
     lib.shgo_basis_launches.argtypes = [ctypes.c_void_p]
     lib.shgo_basis_launches.restype = ctypes.c_int64
     lib.shgo_free.argtypes = [ctypes.c_void_p]
@@ -208,6 +211,15 @@ def shgo_measure_fma_rate(precision: int, iters: int, stream=None):
     ms = ctypes.c_double()
     _check(_lib.shgo_measure_fma_rate(int(precision), int(iters), _stream_handle(stream), ctypes.byref(rate),
                                       ctypes.byref(ms)))
+    return float(rate.value), float(ms.value)
+
+
+def shgo_measure_fma_rate_shape(precision: int, iters: int, chains: int, threads_per_sm: int, stream=None):
+    """(flops per second, ms) of the multiply-add microbenchmark with a chosen launch shape."""
+    rate = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(_lib.shgo_measure_fma_rate_shape(int(precision), int(iters), int(chains), int(threads_per_sm),
+                                            _stream_handle(stream), ctypes.byref(rate), ctypes.byref(ms)))
     return float(rate.value), float(ms.value)
 
 

@@ -138,27 +138,35 @@ def config4(replica: int = 0, n_atoms: int = 5000):
     return molecule(rng, n_atoms, box, 1, 9, lambda Z: shells, lambda r: r.integers(1, 7), 0.05, 5000.0)
 
 
-def config5(n_triples: int, replica: int = 0, lmax: int = 8):
-    """Precision sweep: independent primitive triples.  la, lb ~ U{0..lmax}; exponents
+def config5_arrays(n_triples: int, replica: int = 0, lmax: int = 8):
+    """Precision sweep as arrays: independent primitive triples.  la, lb ~ U{0..lmax}; exponents
     log-uniform [0.01, 1000]; A = 0, B = |AB| u, |AB| ~ U[0, 15]; the nucleus sits at distance
-    |PC| ~ U[0, 15] in a uniform direction from the exponent-weighted centre of A and B;
-    Z ~ U{1..20}.  Returns a list of (basis with two one-primitive shells, centers, charges)."""
+    |PC| ~ U[0, 15] in a uniform direction v from the exponent-weighted centre of A and B;
+    Z ~ U{1..20}.  Returns (la, lb, alpha, beta, B [n, 3], C [n, 3], Z)."""
     rng = _rng(1000 * 5 + replica)
-    out = []
-    for _ in range(n_triples):
-        la, lb = (int(x) for x in rng.integers(0, lmax + 1, 2))
-        a, b = _log_uniform(rng, 0.01, 1000.0, 2)
-        u = rng.standard_normal(3)
-        u /= np.linalg.norm(u)
-        v = rng.standard_normal(3)
-        v /= np.linalg.norm(v)
-        B = rng.uniform(0.0, 15.0) * u
-        centre = (b * B) / (a + b)
-        C = centre + rng.uniform(0.0, 15.0) * v
-        Z = float(rng.integers(1, 21))
-        basis = make_basis([la, lb], [1, 1], [a, b], [1.0, 1.0], [np.zeros(3), B])
-        out.append((basis, C.reshape(1, 3), np.array([Z])))
-    return out
+    n = int(n_triples)
+    la = rng.integers(0, lmax + 1, n)
+    lb = rng.integers(0, lmax + 1, n)
+    lo, hi = np.log(0.01), np.log(1000.0)
+    alpha = np.exp(rng.uniform(lo, hi, n))
+    beta = np.exp(rng.uniform(lo, hi, n))
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    B = rng.uniform(0.0, 15.0, n)[:, None] * u
+    centre = (beta / (alpha + beta))[:, None] * B
+    C = centre + rng.uniform(0.0, 15.0, n)[:, None] * v
+    Z = rng.integers(1, 21, n).astype(np.float64)
+    return la, lb, alpha, beta, B, C, Z
+
+
+def config5(n_triples: int, replica: int = 0, lmax: int = 8):
+    """The precision-sweep triples of config5_arrays as a list of (basis with two one-primitive shells,
+    centers [1, 3], charges [1])."""
+    la, lb, alpha, beta, B, C, Z = config5_arrays(n_triples, replica, lmax)
+    return [(make_basis([int(la[t]), int(lb[t])], [1, 1], [alpha[t], beta[t]], [1.0, 1.0], [np.zeros(3), B[t]]),
+             C[t].reshape(1, 3), np.array([Z[t]])) for t in range(len(la))]
 
 
 def random_basis(seed: int, n_shells: int, lmax: int, max_prim: int = 4, box: float = 4.0,
