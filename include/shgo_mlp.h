@@ -40,6 +40,15 @@ void shgo_mlp_free(shgo_mlp* mlp);
 /* FP32 master parameters to a host array of SHGO_MLP_NPARAM. */
 shgo_status shgo_mlp_get_params(const shgo_mlp* mlp, float* params);
 
+/* Checkpoint of the training state (host arrays of SHGO_MLP_NPARAM): FP32 master parameters, Adam's first
+ * and second moments and the step count behind its bias corrections.  Waits for the device.  Restoring
+ * it into a network with the same feature normalisation and continuing with the same samples gives the
+ * same parameters, bit for bit, as training without the interruption: every training pass sums in a
+ * fixed order (see shgo_mlp_train_step). */
+shgo_status shgo_mlp_get_state(const shgo_mlp* mlp, float* params, float* adam_m, float* adam_v, int64_t* step);
+shgo_status shgo_mlp_set_state(shgo_mlp* mlp, const float* params, const float* adam_m, const float* adam_v,
+                               int64_t step);
+
 /* y[s] = network(X[s, :]) for n samples; X [n][16] and y [n] are device arrays.  Asynchronous. */
 shgo_status shgo_mlp_forward(const shgo_mlp* mlp, const float* X, int64_t n, float* y, void* stream);
 
@@ -50,7 +59,11 @@ shgo_status shgo_mlp_gradients(shgo_mlp* mlp, const float* X, const float* T, in
                                float* grad, float* loss);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss over the n samples; the loss of the
- * pass before the update goes to *loss when loss != NULL (then the call blocks on `stream`). */
+ * pass before the update goes to *loss when loss != NULL (then the call blocks on `stream`).
+ * The pass runs on the tensor cores (mma.sync BF16 with FP32 accumulation; FP32 activations and gradient
+ * operands split into BF16 high and low parts) in a fixed summation order: per block of 32-sample tiles,
+ * then over blocks in block order, the number of blocks depending only on n and the device.  Two runs over
+ * the same samples from the same state give the same bits. */
 shgo_status shgo_mlp_train_step(shgo_mlp* mlp, const float* X, const float* T, int64_t n, float under_weight,
                                 float lr, float* loss, void* stream);
 

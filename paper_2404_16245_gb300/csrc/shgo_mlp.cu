@@ -169,97 +169,278 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ X
 
 // One training pass over n samples: loss = sum_s w_s (y_s - t_s)^2 / n with w_s = under_weight when
 // the prediction is below the target (under-prediction is what causes false skips), 1 otherwise.
-// Gradients are accumulated into grad (FP32, zeroed by the caller); the loss sum into loss[0].
-constexpr int kTB = 64;  // samples (threads) per block
-__global__ void __launch_bounds__(kTB) k_mlp_train(const float* __restrict__ X, const float* __restrict__ T,
-                                                   int64_t n, const __nv_bfloat16* __restrict__ wq,
-                                                   const float* __restrict__ norm, float under_weight,
-                                                   float* __restrict__ grad, float* __restrict__ loss) {
-  extern __shared__ float sm[];
-  float* sw = sm;                       // kNParam
-  float* snorm = sw + kNParam;          // 2 kIn
-  float* sx = snorm + 2 * kIn;          // [kTB][kIn] normalised inputs
-  float* sa1 = sx + kTB * kIn;          // [kTB][kH] layer-1 activations
-  float* sd1 = sa1 + kTB * kH;          // [kTB][kH] d loss / d z1
-  float* sa2 = sd1 + kTB * kH;          // [kTB][kH] layer-2 activations
-  float* sd2 = sa2 + kTB * kH;          // [kTB][kH] d loss / d z2
-  float* sdy = sd2 + kTB * kH;          // [kTB]
-  stage_weights(wq, nullptr, sw);
-  for (int i = threadIdx.x; i < 2 * kIn; i += blockDim.x) snorm[i] = norm[i];
-  __syncthreads();
+//
+// Tensor cores in a fixed order.  A block is one warp; it takes tiles of 32 samples (tiles b, b + grid, ...)
+// and runs every product on mma.sync m16n8k16 (BF16 inputs, FP32 accumulation): the forward layers as in
+// inference (activations split into BF16 high and low parts, weights BF16 as used), the backward product
+// D2 W2 the same way, and the weight gradients D2^T A1 and D1^T X with both operands split (high x high +
+// high x low + low x high: FP32-level accuracy).  The block's gradient and loss accumulate in shared memory
+// in tile order and go to the block's slot of `part`; k_mlp_reduce adds the slots in block order.  Every
+// sum has a fixed order, so two passes over the same samples give the same bits.
+constexpr int kTS = 32;  // samples per tile (one warp)
+constexpr int kTrainFloats = kTS * kIn + 4 * kTS * kH + 2 * kTS + kNParam + 2 * kIn + 4;
+
+size_t train_smem() { return sizeof(float) * (size_t)kTrainFloats + sizeof(__nv_bfloat16) * kH * kH; }
+
+// A fragment of rows r0.. and columns c0.. of a row-major FP32 matrix M (row stride ld), split.
+__device__ __forceinline__ void load_a_split(const float* M, int ld, int r0, int c0, int g, int t, uint32_t* hi,
+                                             uint32_t* lo) {
+  const float* p0 = M + (r0 + g) * ld + c0;
+  const float* p1 = M + (r0 + g + 8) * ld + c0;
+  split2(p0[2 * t], p0[2 * t + 1], hi[0], lo[0]);
+  split2(p1[2 * t], p1[2 * t + 1], hi[1], lo[1]);
+  split2(p0[2 * t + 8], p0[2 * t + 9], hi[2], lo[2]);
+  split2(p1[2 * t + 8], p1[2 * t + 9], hi[3], lo[3]);
+}
+
+// A fragment of a transpose, A[m][k] = M[k0 + k][m0 + m] (M row-major, row stride ld), split.
+__device__ __forceinline__ void load_at_split(const float* M, int ld, int m0, int k0, int g, int t, uint32_t* hi,
+                                              uint32_t* lo) {
+  const float* c0 = M + k0 * ld + m0;
+  split2(c0[(2 * t) * ld + g], c0[(2 * t + 1) * ld + g], hi[0], lo[0]);
+  split2(c0[(2 * t) * ld + g + 8], c0[(2 * t + 1) * ld + g + 8], hi[1], lo[1]);
+  split2(c0[(2 * t + 8) * ld + g], c0[(2 * t + 9) * ld + g], hi[2], lo[2]);
+  split2(c0[(2 * t + 8) * ld + g + 8], c0[(2 * t + 9) * ld + g + 8], hi[3], lo[3]);
+}
+
+// B fragment, B[k][n] = M[k0 + k][n0 + n] (M row-major, row stride ld), split.
+__device__ __forceinline__ void load_b_split(const float* M, int ld, int k0, int n0, int g, int t, uint32_t* hi,
+                                             uint32_t* lo) {
+  const float* c0 = M + k0 * ld + n0 + g;
+  split2(c0[(2 * t) * ld], c0[(2 * t + 1) * ld], hi[0], lo[0]);
+  split2(c0[(2 * t + 8) * ld], c0[(2 * t + 9) * ld], hi[1], lo[1]);
+}
+
+// d += A B with both split: high x high + high x low + low x high.
+__device__ __forceinline__ void mma3(float* d, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
+                                     const uint32_t* bl) {
+  mma_bf16(d, ah, bh[0], bh[1]);
+  mma_bf16(d, ah, bl[0], bl[1]);
+  mma_bf16(d, al, bh[0], bh[1]);
+}
+
+__global__ void __launch_bounds__(32) k_mlp_train(const float* __restrict__ X, const float* __restrict__ T,
+                                                  int64_t n, const __nv_bfloat16* __restrict__ wq,
+                                                  const float* __restrict__ norm, float under_weight,
+                                                  float* __restrict__ part) {
+  extern __shared__ __align__(16) float sm[];
+  float* xs = sm;                       // [32][16] standardised inputs
+  float* A1 = xs + kTS * kIn;           // [32][64] layer-1 activations
+  float* S1 = A1 + kTS * kH;            // [32][64] silu'(z1), then D1 = d loss / d z1
+  float* A2 = S1 + kTS * kH;            // [32][64] layer-2 activations
+  float* S2 = A2 + kTS * kH;            // [32][64] silu'(z2), then D2 = d loss / d z2
+  float* dyv = S2 + kTS * kH;           // [32] d loss / d y
+  float* lterm = dyv + kTS;             // [32] loss term w (y - t)^2 of each sample
+  float* acc = lterm + kTS;             // [kNParam] this block's gradient
+  float* snorm = acc + kNParam;         // mean[16], 1/sd[16]
+  float* sloss = snorm + 2 * kIn;       // [1] this block's loss sum
+  __nv_bfloat16* w2t = reinterpret_cast<__nv_bfloat16*>(sm + kTrainFloats);  // w2t[k][j] = W2[j][k]
+  const int lane = threadIdx.x, g = lane >> 2, t = lane & 3;
+  for (int i = lane; i < kNParam; i += 32) acc[i] = 0.f;
+  for (int i = lane; i < 2 * kIn; i += 32) snorm[i] = norm[i];
+  for (int i = lane; i < kH * kH; i += 32) w2t[(i % kH) * kH + i / kH] = wq[kOffW2 + i];
+  if (lane == 0) sloss[0] = 0.f;
+  __syncwarp();
   const float inv_n = 1.f / (float)n;
-  float block_loss = 0.f;
-  for (int64_t base = blockIdx.x * (int64_t)kTB; base < n; base += (int64_t)gridDim.x * kTB) {
-    const int t = threadIdx.x;
-    const int64_t s = base + t;
-    const bool live = s < n;
-    // forward with saved activations
-    float z1[kH];
-    for (int k = 0; k < kIn; ++k) sx[t * kIn + k] = live ? (X[s * kIn + k] - snorm[k]) * snorm[kIn + k] : 0.f;
-    for (int j = 0; j < kH; ++j) {
-      float z = sw[kOffB1 + j];
-      for (int k = 0; k < kIn; ++k) z = fmaf(sw[kOffW1 + j * kIn + k], sx[t * kIn + k], z);
-      z1[j] = z;
-      sa1[t * kH + j] = silu(z);
+  const int64_t ntiles = (n + kTS - 1) / kTS;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t s0 = tile * kTS;
+    {
+      const int64_t s = s0 + lane;
+#pragma unroll
+      for (int k = 0; k < kIn; ++k) xs[lane * kIn + k] = s < n ? (X[s * kIn + k] - snorm[k]) * snorm[kIn + k] : 0.f;
     }
-    float out = sw[kOffB3];
-    for (int j = 0; j < kH; ++j) {
-      float z = sw[kOffB2 + j];
-      for (int k = 0; k < kH; ++k) z = fmaf(sw[kOffW2 + j * kH + k], sa1[t * kH + k], z);
-      sa2[t * kH + j] = silu(z);
-      sd2[t * kH + j] = z;  // z2 for now
-      out = fmaf(sw[kOffW3 + j], sa2[t * kH + j], out);
-    }
-    float dy = 0.f;
-    if (live) {
-      const float r = out - T[s];
-      const float w = r < 0.f ? under_weight : 1.f;
-      block_loss += w * r * r;
-      dy = 2.f * w * r * inv_n;
-    }
-    sdy[t] = dy;
-    // backward through the per-sample activations
-    for (int j = 0; j < kH; ++j) sd2[t * kH + j] = dy * sw[kOffW3 + j] * silu_grad(sd2[t * kH + j]);
-    for (int k = 0; k < kH; ++k) {
-      float acc = 0.f;
-      for (int j = 0; j < kH; ++j) acc = fmaf(sw[kOffW2 + j * kH + k], sd2[t * kH + j], acc);
-      sd1[t * kH + k] = acc * silu_grad(z1[k]);
-    }
-    __syncthreads();
-    // weight gradients: sums over this block's samples, one parameter slice per thread
-    for (int p = threadIdx.x; p < kNParam; p += blockDim.x) {
-      float g = 0.f;
-      if (p < kOffB1) {
-        const int j = p / kIn, k = p % kIn;
-        for (int u = 0; u < kTB; ++u) g = fmaf(sd1[u * kH + j], sx[u * kIn + k], g);
-      } else if (p < kOffW2) {
-        const int j = p - kOffB1;
-        for (int u = 0; u < kTB; ++u) g += sd1[u * kH + j];
-      } else if (p < kOffB2) {
-        const int q = p - kOffW2, j = q / kH, k = q % kH;
-        for (int u = 0; u < kTB; ++u) g = fmaf(sd2[u * kH + j], sa1[u * kH + k], g);
-      } else if (p < kOffW3) {
-        const int j = p - kOffB2;
-        for (int u = 0; u < kTB; ++u) g += sd2[u * kH + j];
-      } else if (p < kOffB3) {
-        const int j = p - kOffW3;
-        for (int u = 0; u < kTB; ++u) g = fmaf(sdy[u], sa2[u * kH + j], g);
-      } else {
-        for (int u = 0; u < kTB; ++u) g += sdy[u];
+    __syncwarp();
+    // forward, two m tiles of 16 samples; z1, z2 kept as activations and SiLU derivatives
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt;
+      uint32_t ah[4], al[4];
+      load_a_split(xs, kIn, r0, 0, g, t, ah, al);
+      uint32_t h2h[4][4], h2l[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int j = 8 * nt + g;
+        const uint32_t b0 = ldw2(wq, kOffW1 + j * kIn + 2 * t), b1 = ldw2(wq, kOffW1 + j * kIn + 2 * t + 8);
+        const float bias0 = __bfloat162float(wq[kOffB1 + 8 * nt + 2 * t]);
+        const float bias1 = __bfloat162float(wq[kOffB1 + 8 * nt + 2 * t + 1]);
+        float d[4] = {bias0, bias1, bias0, bias1};
+        mma_bf16(d, ah, b0, b1);
+        mma_bf16(d, al, b0, b1);
+        float a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + g + (q >> 1) * 8, c = 8 * nt + 2 * t + (q & 1);
+          a[q] = silu(d[q]);
+          A1[r * kH + c] = a[q];
+          S1[r * kH + c] = silu_grad(d[q]);
+        }
+        const int kk = nt >> 1, half = nt & 1;
+        split2(a[0], a[1], h2h[kk][2 * half], h2l[kk][2 * half]);
+        split2(a[2], a[3], h2h[kk][2 * half + 1], h2l[kk][2 * half + 1]);
       }
-      if (g != 0.f) atomicAdd(grad + p, g);
+      float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int j = 8 * nt + g;
+        const float bias0 = __bfloat162float(wq[kOffB2 + 8 * nt + 2 * t]);
+        const float bias1 = __bfloat162float(wq[kOffB2 + 8 * nt + 2 * t + 1]);
+        float d[4] = {bias0, bias1, bias0, bias1};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t b0 = ldw2(wq, kOffW2 + j * kH + 16 * kk + 2 * t);
+          const uint32_t b1 = ldw2(wq, kOffW2 + j * kH + 16 * kk + 2 * t + 8);
+          mma_bf16(d, h2h[kk], b0, b1);
+          mma_bf16(d, h2l[kk], b0, b1);
+        }
+        float a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + g + (q >> 1) * 8, c = 8 * nt + 2 * t + (q & 1);
+          a[q] = silu(d[q]);
+          A2[r * kH + c] = a[q];
+          S2[r * kH + c] = silu_grad(d[q]);
+        }
+        const int c = 8 * nt + 2 * t;
+        const float w30 = __bfloat162float(wq[kOffW3 + c]), w31 = __bfloat162float(wq[kOffW3 + c + 1]);
+        o0 = fmaf(w31, a[1], fmaf(w30, a[0], o0));
+        o1 = fmaf(w31, a[3], fmaf(w30, a[2], o1));
+      }
+      o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+      o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+      if (t == 0) {
+        const float b3 = __bfloat162float(wq[kOffB3]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = r0 + g + 8 * h;
+          const int64_t s = s0 + r;
+          float dy = 0.f, lt = 0.f;
+          if (s < n) {
+            const float res = (h ? o1 : o0) + b3 - T[s];
+            const float w = res < 0.f ? under_weight : 1.f;
+            lt = w * res * res;
+            dy = 2.f * w * res * inv_n;
+          }
+          dyv[r] = dy;
+          lterm[r] = lt;
+        }
+      }
     }
-    __syncthreads();
+    __syncwarp();
+    // D2 = (dy W3) * silu'(z2), in place of S2
+    for (int e = lane; e < kTS * kH; e += 32) {
+      const int r = e / kH, j = e % kH;
+      S2[e] = dyv[r] * __bfloat162float(wq[kOffW3 + j]) * S2[e];
+    }
+    __syncwarp();
+    // D1 = (D2 W2) * silu'(z1), in place of S1 (each thread rewrites the entries it reads)
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt;
+      uint32_t dh[4][4], dl[4][4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) load_a_split(S2, kH, r0, 16 * kk, g, t, dh[kk], dl[kk]);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        const int k = 8 * nt + g;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t b0 = ldw2(w2t, k * kH + 16 * kk + 2 * t), b1 = ldw2(w2t, k * kH + 16 * kk + 2 * t + 8);
+          mma_bf16(d, dh[kk], b0, b1);
+          mma_bf16(d, dl[kk], b0, b1);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + g + (q >> 1) * 8, c = 8 * nt + 2 * t + (q & 1);
+          S1[r * kH + c] = d[q] * S1[r * kH + c];
+        }
+      }
+    }
+    __syncwarp();
+    // gW2[j][k] += sum_r D2[r][j] A1[r][k]  and  gW1[j][k] += sum_r D1[r][j] x[r][k]
+#pragma unroll 1
+    for (int jm = 0; jm < 4; ++jm) {
+      uint32_t ah[2][4], al[2][4], eh[2][4], el[2][4];
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        load_at_split(S2, kH, 16 * jm, 16 * ks, g, t, ah[ks], al[ks]);
+        load_at_split(S1, kH, 16 * jm, 16 * ks, g, t, eh[ks], el[ks]);
+      }
+#pragma unroll 1
+      for (int nt = 0; nt < 8; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          uint32_t bh[2], bl[2];
+          load_b_split(A1, kH, 16 * ks, 8 * nt, g, t, bh, bl);
+          mma3(d, ah[ks], al[ks], bh, bl);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 16 * jm + g + (q >> 1) * 8, k = 8 * nt + 2 * t + (q & 1);
+          acc[kOffW2 + j * kH + k] += d[q];
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          uint32_t bh[2], bl[2];
+          load_b_split(xs, kIn, 16 * ks, 8 * nt, g, t, bh, bl);
+          mma3(d, eh[ks], el[ks], bh, bl);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 16 * jm + g + (q >> 1) * 8, k = 8 * nt + 2 * t + (q & 1);
+          acc[kOffW1 + j * kIn + k] += d[q];
+        }
+      }
+    }
+    // bias and output gradients, summed over the tile's samples in order
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      float gb1 = 0.f, gb2 = 0.f, gw3 = 0.f;
+      for (int r = 0; r < kTS; ++r) {
+        gb1 += S1[r * kH + j];
+        gb2 += S2[r * kH + j];
+        gw3 = fmaf(dyv[r], A2[r * kH + j], gw3);
+      }
+      acc[kOffB1 + j] += gb1;
+      acc[kOffB2 + j] += gb2;
+      acc[kOffW3 + j] += gw3;
+    }
+    if (lane == 0) {
+      float gb3 = 0.f, ls = 0.f;
+      for (int r = 0; r < kTS; ++r) {
+        gb3 += dyv[r];
+        ls += lterm[r];
+      }
+      acc[kOffB3] += gb3;
+      sloss[0] += ls;
+    }
+    __syncwarp();  // the tile's arrays are free for the next tile
   }
-  // block loss
-  __shared__ float red[kTB];
-  red[threadIdx.x] = block_loss;
-  __syncthreads();
-  for (int o = kTB / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  float* slot = part + (int64_t)blockIdx.x * (kNParam + 1);
+  for (int i = lane; i < kNParam; i += 32) slot[i] = acc[i];
+  if (lane == 0) slot[kNParam] = sloss[0];
+}
+
+// grad[p] = sum over blocks b = 0, 1, ... of part[b][p] (fixed order); loss = sum of the blocks' loss sums / n.
+__global__ void k_mlp_reduce(const float* __restrict__ part, int nblocks, float inv_n, float* __restrict__ grad,
+                             float* __restrict__ loss) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p <= kNParam; p += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * (kNParam + 1) + p];
+    if (p < kNParam)
+      grad[p] = s;
+    else
+      *loss = s * inv_n;
   }
-  if (threadIdx.x == 0) atomicAdd(loss, red[0] * inv_n);
 }
 
 // Adam on the FP32 master weights, then the BF16 copy; clears the gradient.
@@ -284,7 +465,6 @@ __global__ void k_quantize(const float* __restrict__ w, __nv_bfloat16* __restric
     wq[i] = __float2bfloat16_rn(w[i]);
 }
 
-size_t train_smem() { return sizeof(float) * (kNParam + 2 * kIn + kTB * kIn + 4 * kTB * kH + kTB); }
 
 shgo_status fail_mlp(shgo_status s, const std::string& m) {
   set_last_error(m);
@@ -474,6 +654,8 @@ struct shgo_mlp {
   float* norm = nullptr;  // mean[16], 1/sd[16]
   float* loss = nullptr;
   __nv_bfloat16* wq = nullptr;
+  float* part = nullptr;  // per training block: gradient partial sums and loss sum
+  int max_blocks = 0;
   int64_t step = 0;
 };
 
@@ -492,6 +674,10 @@ shgo_status shgo_mlp_create(const float* params, const float* feature_mean, cons
   if (e == cudaSuccess) e = cudaMalloc((void**)&M->norm, sizeof(float) * 2 * kIn);
   if (e == cudaSuccess) e = cudaMalloc((void**)&M->loss, sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&M->wq, sizeof(__nv_bfloat16) * kNParam);
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
+  M->max_blocks = 4 * nsm;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&M->part, sizeof(float) * (size_t)M->max_blocks * (kNParam + 1));
   std::vector<float> nrm(2 * kIn);
   for (int k = 0; k < kIn; ++k) {
     if (!(feature_sd[k] > 0.f)) e = e == cudaSuccess ? cudaErrorInvalidValue : e;
@@ -526,6 +712,7 @@ void shgo_mlp_free(shgo_mlp* mlp) {
   cudaFree(mlp->norm);
   cudaFree(mlp->loss);
   cudaFree(mlp->wq);
+  cudaFree(mlp->part);
   delete mlp;
 }
 
@@ -533,6 +720,34 @@ shgo_status shgo_mlp_get_params(const shgo_mlp* mlp, float* params) {
   if (!mlp || !params) return fail_mlp(SHGO_ERR_INVALID_ARG, "NULL argument");
   if (cudaMemcpy(params, mlp->w, sizeof(float) * kNParam, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail_mlp(SHGO_ERR_CUDA, "copy of the parameters failed");
+  return SHGO_OK;
+}
+
+shgo_status shgo_mlp_get_state(const shgo_mlp* mlp, float* params, float* adam_m, float* adam_v, int64_t* step) {
+  if (!mlp || !params || !adam_m || !adam_v || !step) return fail_mlp(SHGO_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(params, mlp->w, sizeof(float) * kNParam, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(adam_m, mlp->m, sizeof(float) * kNParam, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(adam_v, mlp->v, sizeof(float) * kNParam, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail_mlp(SHGO_ERR_CUDA, std::string("saving the state: ") + cudaGetErrorString(e));
+  *step = mlp->step;
+  return SHGO_OK;
+}
+
+shgo_status shgo_mlp_set_state(shgo_mlp* mlp, const float* params, const float* adam_m, const float* adam_v,
+                               int64_t step) {
+  if (!mlp || !params || !adam_m || !adam_v || step < 0) return fail_mlp(SHGO_ERR_INVALID_ARG, "bad arguments");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(mlp->w, params, sizeof(float) * kNParam, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(mlp->m, adam_m, sizeof(float) * kNParam, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(mlp->v, adam_v, sizeof(float) * kNParam, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(mlp->g, 0, sizeof(float) * kNParam);
+  if (e == cudaSuccess) {
+    k_quantize<<<(kNParam + 255) / 256, 256>>>(mlp->w, mlp->wq, kNParam);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) return fail_mlp(SHGO_ERR_CUDA, std::string("restoring the state: ") + cudaGetErrorString(e));
+  mlp->step = step;
   return SHGO_OK;
 }
 
@@ -547,15 +762,15 @@ shgo_status shgo_mlp_forward(const shgo_mlp* mlp, const float* X, int64_t n, flo
   return e == cudaSuccess ? SHGO_OK : fail_mlp(SHGO_ERR_CUDA, cudaGetErrorString(e));
 }
 
+// Gradient (mlp->g) and loss (mlp->loss) of the loss over n samples, in a fixed order: the block count
+// depends only on n and the device.
 static shgo_status run_train(shgo_mlp* mlp, const float* X, const float* T, int64_t n, float under_weight,
                              cudaStream_t s) {
   const size_t sm = train_smem();
   ensure_max_dynamic_smem((const void*)k_mlp_train, (int)sm);
-  int nsm = 152;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, mlp->device);
-  const int64_t blocks = std::min<int64_t>((n + kTB - 1) / kTB, (int64_t)nsm * 2);
-  cudaMemsetAsync(mlp->loss, 0, sizeof(float), s);
-  k_mlp_train<<<(int)blocks, kTB, sm, s>>>(X, T, n, mlp->wq, mlp->norm, under_weight, mlp->g, mlp->loss);
+  const int blocks = (int)std::min<int64_t>((n + kTS - 1) / kTS, (int64_t)mlp->max_blocks);
+  k_mlp_train<<<blocks, 32, sm, s>>>(X, T, n, mlp->wq, mlp->norm, under_weight, mlp->part);
+  k_mlp_reduce<<<(kNParam + 256) / 256, 256, 0, s>>>(mlp->part, blocks, 1.f / (float)n, mlp->g, mlp->loss);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SHGO_OK : fail_mlp(SHGO_ERR_CUDA, cudaGetErrorString(e));
 }

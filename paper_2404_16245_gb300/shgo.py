@@ -567,6 +567,10 @@ def _bind_mlp():
     L.shgo_mlp_free.restype = None
     L.shgo_mlp_get_params.argtypes = [vp, f32p]
     L.shgo_mlp_get_params.restype = ctypes.c_int
+    L.shgo_mlp_get_state.argtypes = [vp, f32p, f32p, f32p, ctypes.POINTER(ctypes.c_int64)]
+    L.shgo_mlp_get_state.restype = ctypes.c_int
+    L.shgo_mlp_set_state.argtypes = [vp, f32p, f32p, f32p, ctypes.c_int64]
+    L.shgo_mlp_set_state.restype = ctypes.c_int
     L.shgo_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     L.shgo_mlp_forward.restype = ctypes.c_int
     L.shgo_mlp_gradients.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, f32p, f32p]
@@ -603,6 +607,23 @@ class MLP:
         self.handle = h.value
         self.mean = mu
         self.sd = sd
+
+    def state(self) -> dict:
+        """Checkpoint: FP32 parameters, Adam moments and step count (host copies)."""
+        p = np.zeros(MLP_NPARAM, dtype=np.float32)
+        m = np.zeros(MLP_NPARAM, dtype=np.float32)
+        v = np.zeros(MLP_NPARAM, dtype=np.float32)
+        step = ctypes.c_int64()
+        _check(_lib.shgo_mlp_get_state(ctypes.c_void_p(self.handle), _ptr(p, ctypes.c_float), _ptr(m, ctypes.c_float),
+                                       _ptr(v, ctypes.c_float), ctypes.byref(step)))
+        return {"params": p, "adam_m": m, "adam_v": v, "step": int(step.value)}
+
+    def load_state(self, st: dict) -> None:
+        p = np.ascontiguousarray(st["params"], dtype=np.float32)
+        m = np.ascontiguousarray(st["adam_m"], dtype=np.float32)
+        v = np.ascontiguousarray(st["adam_v"], dtype=np.float32)
+        _check(_lib.shgo_mlp_set_state(ctypes.c_void_p(self.handle), _ptr(p, ctypes.c_float), _ptr(m, ctypes.c_float),
+                                       _ptr(v, ctypes.c_float), int(st["step"])))
 
     def params(self) -> np.ndarray:
         p = np.zeros(MLP_NPARAM, dtype=np.float32)

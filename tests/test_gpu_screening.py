@@ -220,3 +220,40 @@ def test_ragged_nucleus_lists_equal_plain_over_the_kept_nuclei(shgo):
         assert np.array_equal(out.cpu().numpy(), expect), call
     B.close()
     net.close()
+
+
+def test_training_repeats_and_resumes_bit_for_bit(shgo):
+    """Training sums in a fixed order: two runs from one initial state over the same batches give the
+    same parameters bit for bit, and stopping after 7 steps, saving the state (parameters, Adam moments,
+    step count), loading it into a fresh network and running the remaining steps gives them too.  The
+    sample count is not a multiple of the 32-sample tile."""
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(5000, 16)).astype(np.float32)
+    T = (X @ rng.normal(size=16) + np.sin(X[:, 1])).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    batches = [(int(s), int(s) + 1500) for s in rng.integers(0, 5000 - 1500, 18)]
+    mean, sd = X.mean(axis=0), X.std(axis=0)
+
+    def run(steps, state=None):
+        net = shgo.MLP(W.mlp_init_params(3), mean, sd)
+        if state is not None:
+            net.load_state(state)
+        done = state["step"] if state is not None else 0
+        for k in range(done, steps):
+            a, b = batches[k]
+            net.train_step(Xd[a:b].contiguous(), Td[a:b].contiguous(), 4.0, 2e-3)
+        torch.cuda.synchronize()
+        st = net.state()
+        net.close()
+        return st
+
+    full1 = run(18)
+    full2 = run(18)
+    assert np.array_equal(full1["params"], full2["params"])
+    assert np.array_equal(full1["adam_v"], full2["adam_v"]) and full1["step"] == 18
+    part = run(7)
+    resumed = run(18, part)
+    assert np.array_equal(resumed["params"], full1["params"])
+    assert np.array_equal(resumed["adam_m"], full1["adam_m"])
+    # training moved the parameters
+    assert not np.array_equal(full1["params"], W.mlp_init_params(3))
