@@ -120,7 +120,10 @@ int64_t shgo_basis_npairs(const shgo_basis* basis);
  *   out       device [nbf][nbf] row-major FP64, fully overwritten (both triangles)
  *   stream    cudaStream_t the kernels are queued on
  * Asynchronous.  Not reentrant for one basis: calls on the same basis must be ordered (they
- * share the basis's coupling buffer).
+ * share the basis's coupling buffer).  A call with the same centers->xyz, charges and out pointers,
+ * nucleus count and time limit as the basis's previous call replays that call's launches from a CUDA
+ * graph (captured on an internal stream at the first repetition), which reads the arrays' current
+ * contents; any other call launches directly and drops the graph.
  */
 shgo_status shgo_nuclear_attraction(const shgo_basis* basis, const shgo_centers* centers, const double* charges,
                                     double* out, void* stream);

@@ -78,3 +78,35 @@ def test_batch_time_limit_cost_order_and_graph_replays(shgo):
             parity.check(np.asarray(batch.block(outs[-1], m)), ref, what=f"molecule {m}")
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
     batch.close()
+
+
+def test_repeated_single_basis_calls_replay_a_graph_that_reads_current_contents(shgo):
+    """The second call with the same pointers captures the launches into a graph, later calls replay it;
+    each replay reads what the arrays hold at that time (nuclei moved in place between calls), and a call
+    with other pointers launches directly again.  Results equal a fresh basis's direct call bit for bit."""
+    basis = W.random_basis(81, 16, 5, max_prim=3)
+    C1, Z1 = W.random_nuclei(82, 21)
+    C2, Z2 = W.random_nuclei(83, 21)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C1, device="cuda"), torch.tensor(Z1, device="cuda")
+    out = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device="cuda")
+
+    def fresh(C, Z):
+        F = shgo.Basis(basis)
+        v = shgo.nuclear_attraction(F, torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")).cpu().numpy()
+        F.close()
+        return v
+
+    want1, want2 = fresh(C1, Z1), fresh(C2, Z2)
+    for k in range(3):  # direct, capture + replay, replay
+        out.fill_(float("nan"))
+        shgo.nuclear_attraction(B, Cd, Zd, out=out)
+        assert np.array_equal(out.cpu().numpy(), want1), k
+    Cd.copy_(torch.tensor(C2))
+    Zd.copy_(torch.tensor(Z2))
+    shgo.nuclear_attraction(B, Cd, Zd, out=out)  # replay on the new contents
+    assert np.array_equal(out.cpu().numpy(), want2)
+    other = torch.empty_like(out)
+    shgo.nuclear_attraction(B, Cd, Zd, out=other)  # new pointer: direct launch
+    assert np.array_equal(other.cpu().numpy(), want2)
+    B.close()
