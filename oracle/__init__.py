@@ -67,6 +67,10 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_long, _f64p, _f64p, ctypes.c_int, _f64p,
             ctypes.c_int]
         lib.oracle_nuclear_field.restype = ctypes.c_int
+        lib.oracle_nuclear_deriv.argtypes = [
+            ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_long, _f64p, _f64p, ctypes.c_int, _f64p,
+            ctypes.c_int]
+        lib.oracle_nuclear_deriv.restype = ctypes.c_int
         lib.oracle_overlap.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_coulomb_2c.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int]
         lib.oracle_overlap.restype = ctypes.c_int
@@ -119,6 +123,26 @@ def nuclear_field(basis, centers, charges, threads: int = 1, precision: str = "f
     for c in range(3):
         out = np.zeros(max(n * n, 1), dtype=np.float64)
         rc = _lib(precision).oracle_nuclear_field(len(l), l, nprim, exps, coefs, xyz, len(Z),
+                                                  C if C.size else np.zeros(3), Z if Z.size else np.zeros(1), c,
+                                                  out, threads)
+        if rc != 0:
+            raise ValueError(f"oracle rejected the basis (code {rc})")
+        res[c] = out[: n * n].reshape(n, n)
+    return res
+
+
+def nuclear_deriv(basis, centers, charges, threads: int = 1, precision: str = "f64") -> np.ndarray:
+    """d V / d (bra centre): [3, nbf, nbf], out[c][a][b] = d/dA_c sum_C Z_C <phi_a|1/|r-C||phi_b>, A the centre
+    of a's shell (b's held fixed); the derivative with respect to b's centre is out[c][b][a].  Cartesian
+    route: d/dA_x of x_A^i exp(-alpha r_A^2) = 2 alpha x_A^{i+1} exp(...) - i x_A^{i-1} exp(...)."""
+    l, nprim, exps, coefs, xyz = _basis_arrays(basis)
+    C = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    Z = np.ascontiguousarray(charges, dtype=np.float64).reshape(-1)
+    n = nbf(basis)
+    res = np.zeros((3, n, n))
+    for c in range(3):
+        out = np.zeros(max(n * n, 1), dtype=np.float64)
+        rc = _lib(precision).oracle_nuclear_deriv(len(l), l, nprim, exps, coefs, xyz, len(Z),
                                                   C if C.size else np.zeros(3), Z if Z.size else np.zeros(1), c,
                                                   out, threads)
         if rc != 0:

@@ -419,6 +419,89 @@ static void nuclear_block(const shell_t* a, const shell_t* b, const real* ca, co
   free(Ex);
 }
 
+/* One primitive Cartesian nuclear-attraction integral (without the 2 pi / p prefactor) from the Hermite
+ * expansion tables: sum_{t,u,v} E^x_{ix,jx;t} E^y_{iy,jy;u} E^z_{iz,jz;v} R_{tuv}, the E tables laid out
+ * as hermite_E writes them (ket extent lb + 1, t extent tdim) and R as hermite_R writes it (extent d). */
+static real hermite_cart(const real* Ex, const real* Ey, const real* Ez, int lb, int tdim, const real* R, int d,
+                         int ix, int iy, int iz, int jx, int jy, int jz) {
+  const real* ex = Ex + (ix * (lb + 1) + jx) * tdim;
+  const real* ey = Ey + (iy * (lb + 1) + jy) * tdim;
+  const real* ez = Ez + (iz * (lb + 1) + jz) * tdim;
+  real s = 0;
+  for (int t = 0; t <= ix + jx; ++t)
+    for (int u = 0; u <= iy + jy; ++u)
+      for (int v = 0; v <= iz + jz; ++v) s += ex[t] * ey[u] * ez[v] * R[(t * d + u) * d + v];
+  return s;
+}
+
+/* Derivative of the nuclear-attraction block with respect to coordinate `comp` of the bra shell's centre
+ * A (the ket's centre and the nuclei fixed): out[ma * (2lb+1) + mb] = d/dA_comp sum_C Z_C <a, ma|1/|r-C||b, mb>.
+ * A Cartesian primitive x_A^i y_A^j z_A^k exp(-alpha r_A^2) has d/dA_x = 2 alpha x_A^{i+1} ... - i x_A^{i-1} ...,
+ * so each Cartesian element is 2 alpha times the integral with the exponent of the differentiated
+ * coordinate raised by one, minus that exponent times the integral with it lowered by one; the Hermite
+ * tables run to la + 1 on the bra side and to order la + lb + 1 in R. */
+static void nuclear_dA_block(const shell_t* a, const shell_t* b, const real* ca, const real* cb, long nC,
+                             const double* C, const double* Z, real* out, int comp) {
+  const int la = a->l, lb = b->l, nca = ncart(la), ncb = ncart(lb);
+  const int ia1 = la + 1, L1 = la + lb + 1, tdim = ia1 + lb + 1, d = L1 + 1;
+  real* Ex = (real*)malloc(sizeof(real) * 3 * (size_t)(ia1 + 1) * (lb + 1) * tdim);
+  real* Ey = Ex + (size_t)(ia1 + 1) * (lb + 1) * tdim;
+  real* Ez = Ey + (size_t)(ia1 + 1) * (lb + 1) * tdim;
+  real* work = (real*)malloc(sizeof(real) * (size_t)d * d * d * d);
+  real* Rc = (real*)malloc(sizeof(real) * (size_t)d * d * d);
+  real* Rs = (real*)malloc(sizeof(real) * (size_t)d * d * d);
+  real* Vc = (real*)calloc((size_t)nca * ncb, sizeof(real));
+  for (int i = 0; i < a->nprim; ++i)
+    for (int j = 0; j < b->nprim; ++j) {
+      const real al = a->alpha[i], be = b->alpha[j], p = al + be, mu = al * be / p;
+      real P[3], E00[3];
+      for (int c = 0; c < 3; ++c) {
+        P[c] = (al * a->A[c] + be * b->A[c]) / p;
+        const real X = a->A[c] - b->A[c];
+        E00[c] = RX(exp)(-mu * X * X);
+      }
+      hermite_E(ia1, lb, p, P[0] - a->A[0], P[0] - b->A[0], E00[0], Ex);
+      hermite_E(ia1, lb, p, P[1] - a->A[1], P[1] - b->A[1], E00[1], Ey);
+      hermite_E(ia1, lb, p, P[2] - a->A[2], P[2] - b->A[2], E00[2], Ez);
+      memset(Rs, 0, sizeof(real) * (size_t)d * d * d);
+      for (long c = 0; c < nC; ++c) {
+        hermite_R(L1, p, P[0] - (real)C[3 * c], P[1] - (real)C[3 * c + 1], P[2] - (real)C[3 * c + 2], work, Rc);
+        for (int t = 0; t <= L1; ++t)
+          for (int u = 0; u + t <= L1; ++u)
+            for (int v = 0; v + u + t <= L1; ++v) Rs[(t * d + u) * d + v] += (real)Z[c] * Rc[(t * d + u) * d + v];
+      }
+      const real pre = a->coef[i] * b->coef[j] * 2 * RPI / p;
+      for (int ix = la; ix >= 0; --ix)
+        for (int iy = la - ix; iy >= 0; --iy) {
+          const int iz = la - ix - iy, ia = cart_index(la, ix, iy);
+          const int e[3] = {ix, iy, iz};
+          for (int jx = lb; jx >= 0; --jx)
+            for (int jy = lb - jx; jy >= 0; --jy) {
+              const int jz = lb - jx - jy, ib = cart_index(lb, jx, jy);
+              const int up[3] = {ix + (comp == 0), iy + (comp == 1), iz + (comp == 2)};
+              real v = 2 * al * hermite_cart(Ex, Ey, Ez, lb, tdim, Rs, d, up[0], up[1], up[2], jx, jy, jz);
+              if (e[comp] > 0) {
+                const int dn[3] = {ix - (comp == 0), iy - (comp == 1), iz - (comp == 2)};
+                v -= (real)e[comp] * hermite_cart(Ex, Ey, Ez, lb, tdim, Rs, d, dn[0], dn[1], dn[2], jx, jy, jz);
+              }
+              Vc[ia * ncb + ib] += pre * v;
+            }
+        }
+    }
+  for (int ma = 0; ma < 2 * la + 1; ++ma)
+    for (int mb = 0; mb < 2 * lb + 1; ++mb) {
+      real s = 0;
+      for (int ia = 0; ia < nca; ++ia)
+        for (int ib = 0; ib < ncb; ++ib) s += ca[ma * nca + ia] * cb[mb * ncb + ib] * Vc[ia * ncb + ib];
+      out[ma * (2 * lb + 1) + mb] = s;
+    }
+  free(Vc);
+  free(Rs);
+  free(Rc);
+  free(work);
+  free(Ex);
+}
+
 /* Two-centre Coulomb block of one shell pair: out[ma * (2lb+1) + mb] =
  *   (a, ma | b, mb) = int int phi_a(r1) phi_b(r2) / |r1 - r2| d3r1 d3r2.
  * McMurchie-Davidson with each orbital its own one-Gaussian "pair": per primitive pair,
@@ -613,7 +696,7 @@ static void eri_block(const shell_t* a, const shell_t* b, const shell_t* c, cons
 /* ------------------------------------------------------------------------------------------ */
 /* Public entry points.                                                                       */
 /* ------------------------------------------------------------------------------------------ */
-typedef enum { OP_OVERLAP = 0, OP_NUCLEAR = 1, OP_COULOMB2C = 2 } op_t;
+typedef enum { OP_OVERLAP = 0, OP_NUCLEAR = 1, OP_COULOMB2C = 2, OP_NUCLEAR_DA = 3 } op_t;
 
 static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, const double* exps,
                         const double* coefs, const double* xyz, long nC, const double* C, const double* Z,
@@ -644,6 +727,22 @@ static int one_electron(op_t op, int n_shells, const int* l, const int* nprim, c
       const long b = q - a * (a + 1) / 2;
       const int na = 2 * sh[a].l + 1, nb = 2 * sh[b].l + 1;
       real* blk = (real*)malloc(sizeof(real) * (size_t)na * nb);
+      if (op == OP_NUCLEAR_DA) {
+        /* rows of shell a: the derivative with respect to a's centre; rows of shell b (a != b): with
+         * respect to b's centre, the block with b as the bra */
+        nuclear_dA_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], nC, C, Z, blk, dcomp);
+        for (int i = 0; i < na; ++i)
+          for (int j = 0; j < nb; ++j) out[(off[a] + i) * nbf + off[b] + j] = (double)blk[i * nb + j];
+        if (a != b) {
+          real* blk2 = (real*)malloc(sizeof(real) * (size_t)na * nb);
+          nuclear_dA_block(&sh[b], &sh[a], cart[sh[b].l], cart[sh[a].l], nC, C, Z, blk2, dcomp);
+          for (int j = 0; j < nb; ++j)
+            for (int i = 0; i < na; ++i) out[(off[b] + j) * nbf + off[a] + i] = (double)blk2[j * na + i];
+          free(blk2);
+        }
+        free(blk);
+        continue;
+      }
       if (op == OP_OVERLAP)
         overlap_block(&sh[a], &sh[b], cart[sh[a].l], cart[sh[b].l], blk);
       else if (op == OP_COULOMB2C)
@@ -683,6 +782,18 @@ int oracle_nuclear_field(int n_shells, const int* l, const int* nprim, const dou
                          int component, double* out, int n_threads) {
   if (component < 0 || component > 2) return -1;
   return one_electron(OP_NUCLEAR, n_shells, l, nprim, exps, coefs, xyz, n_centers, centers, charges, out,
+                      n_threads, component);
+}
+
+/* Derivative of V with respect to coordinate `component` of the bra function's centre:
+ * out[a][b] = d/dA_component sum_C Z_C <phi_a | 1/|r - C| | phi_b>, A the centre of a's shell, with the
+ * centre of b's shell held fixed even where it coincides with A (so out is not symmetric; the derivative
+ * with respect to b's centre is out[b][a]).  nbf x nbf row-major; returns 0, or -1 on bad input. */
+int oracle_nuclear_deriv(int n_shells, const int* l, const int* nprim, const double* exps, const double* coefs,
+                         const double* xyz, long n_centers, const double* centers, const double* charges,
+                         int component, double* out, int n_threads) {
+  if (component < 0 || component > 2) return -1;
+  return one_electron(OP_NUCLEAR_DA, n_shells, l, nprim, exps, coefs, xyz, n_centers, centers, charges, out,
                       n_threads, component);
 }
 

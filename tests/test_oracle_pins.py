@@ -365,3 +365,85 @@ def test_coulomb2c_rotation_covariance_and_metric(seed):
             assert np.allclose(D[a] @ blk @ D[b].T, blk2, rtol=0, atol=1e-11 * np.max(np.abs(J)))
     assert np.array_equal(J, J.T)
     assert np.min(np.linalg.eigvalsh(J)) > 0
+
+
+# ---- derivatives with respect to the basis-function centres ----
+
+def _shift_shell(basis, s, delta):
+    b = dict(basis)
+    xyz = np.array(basis["xyz"], dtype=np.float64).reshape(-1, 3).copy()
+    xyz[s] += delta
+    b["xyz"] = xyz
+    return b
+
+
+def _shell_first(basis):
+    l = np.asarray(basis["l"])
+    return np.concatenate([[0], np.cumsum(2 * l + 1)]), l
+
+
+@pytest.mark.parametrize("seed,lmax", [(11, 4), (12, 7)])
+def test_centre_derivative_is_the_derivative_of_V(seed, lmax):
+    # moving shell s moves the rows and the columns of its functions: dV/dX_s = D[s rows] + D[s rows]^T
+    basis = W.random_basis(seed, 5, lmax, max_prim=2, box=2.5, exp_lo=0.2, exp_hi=4.0)
+    C, Z = np.array([[0.4, -0.8, 0.3], [-1.0, 0.5, 0.9], [0.2, 0.2, -1.2]]), np.array([1.0, 2.5, -0.7])
+    D = oracle.nuclear_deriv(basis, C, Z, precision="ld")
+    first, l = _shell_first(basis)
+    h = 1e-3
+    for s in range(len(l)):
+        rows = slice(first[s], first[s + 1])
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = h
+
+            def f(k):
+                return oracle.nuclear_attraction(_shift_shell(basis, s, k * e), C, Z, precision="ld")
+
+            fd = (8 * (f(1) - f(-1)) - (f(2) - f(-2))) / (12 * h)
+            an = np.zeros_like(fd)
+            an[rows, :] += D[c][rows, :]
+            an[:, rows] += D[c][rows, :].T
+            assert np.max(np.abs(fd - an)) <= 2e-9 * max(np.max(np.abs(an)), 1.0), (s, c)
+
+
+def test_centre_derivatives_and_field_sum_to_zero():
+    # translating the basis and the nuclei together leaves V unchanged: D + D^T + sum_C Z_C dV/dC = 0.
+    # The two sides come from different recurrences (raised bra exponents against raised Hermite R).
+    basis = W.random_basis(13, 9, 6, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0, n_sites=4)
+    xyz = np.asarray(basis["xyz"]).reshape(-1, 3)
+    C = np.vstack([xyz[0], np.array([[0.3, -0.2, 1.4], [-1.1, 0.6, 0.2]])])  # one nucleus on a basis centre
+    Z = np.array([3.0, 1.0, -2.0])
+    D = oracle.nuclear_deriv(basis, C, Z)
+    F = oracle.nuclear_field(basis, C, Z)
+    for c in range(3):
+        scale = np.max(np.abs(F[c]))
+        assert np.max(np.abs(D[c] + D[c].T + F[c])) <= 1e-12 * scale
+
+
+def test_centre_derivative_ss_closed_form():
+    # V = N_a N_b (2 pi / p) K F_0(T), K = exp(-mu |A - B|^2), T = p |P - C|^2, dP/dA = alpha / p:
+    # dV/dA = N_a N_b (2 pi / p) K [-2 mu (A - B) F_0(T) - 2 alpha (P - C) F_1(T)]
+    a, b = 0.9, 1.4
+    A, B = np.array([0.2, -0.3, 0.4]), np.array([-0.7, 0.5, 1.1])
+    C = np.array([[0.6, 0.9, -0.2]])
+    basis = W.make_basis([0, 0], [1, 1], [a, b], [1.0, 1.0], [A, B])
+    p, mu = a + b, a * b / (a + b)
+    P = (a * A + b * B) / p
+    K = math.exp(-mu * float(np.sum((A - B) ** 2)))
+    T = p * float(np.sum((P - C[0]) ** 2))
+    F0 = 0.5 * math.sqrt(math.pi / T) * sp.erf(math.sqrt(T))
+    F1 = sp.gamma(1.5) * sp.gammainc(1.5, T) / (2 * T ** 1.5)
+    nn = oracle.prim_norm(0, a) * oracle.prim_norm(0, b)
+    ref = nn * (2 * math.pi / p) * K * (-2 * mu * (A - B) * F0 - 2 * a * (P - C[0]) * F1)
+    D = oracle.nuclear_deriv(basis, C, np.ones(1))
+    assert np.allclose(D[:, 0, 1], ref, rtol=1e-13, atol=1e-16)
+    # the bra derivative of the (b, a) element moves B instead: swap the roles
+    refB = nn * (2 * math.pi / p) * K * (-2 * mu * (B - A) * F0 - 2 * b * (P - C[0]) * F1)
+    assert np.allclose(D[:, 1, 0], refB, rtol=1e-13, atol=1e-16)
+
+
+def test_centre_derivative_one_centre_s_shell_vanishes_without_nuclei_offset():
+    # a single s shell pair on one centre with the nucleus on that centre: V is stationary in A by symmetry
+    basis = W.make_basis([0, 0], [1, 1], [0.8, 2.0], [1.0, 1.0], [np.zeros(3), np.zeros(3)])
+    D = oracle.nuclear_deriv(basis, np.zeros((1, 3)), np.ones(1))
+    assert np.max(np.abs(D)) <= 1e-14
