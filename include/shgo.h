@@ -257,6 +257,37 @@ shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_
 shgo_status shgo_esp_gradient(const shgo_basis* basis, const double* density, const shgo_centers* points,
                               double* grad, void* stream);
 
+/* Derivatives of V with respect to the basis-function centres:
+ *   out[X][a][b] = d/dA_X sum_C Z_C < phi_a | 1/|r - C| | phi_b >,  X = x, y, z,
+ * A the centre of phi_a's shell, the centre of phi_b's shell held fixed even where it coincides with A
+ * (so out[X] is not symmetric; the derivative by the centre of phi_b is out[X][b][a]).  With the
+ * nuclei's derivatives (shgo_nuclear_field) they sum to zero: out[X] + out[X]^T + field[X] = 0.
+ * For phi_a = N S_la(r - A) exp(-alpha |r - A|^2) the derivative of the Gaussian product (Eq. 5) by A_X
+ * has three parts: the lowered harmonic d_X S_la (a combination of S_{la-1,M}, Eq. 3's lowering), the
+ * factor -2 mu (A - B)_X (mu = alpha beta / p) of K_AB, and 2 alpha (r - P)_X times the product, which
+ * raises the one-centre integral of Eq. 12 to order la + lb + 1 (Eq. 3's product of S_1 with S_L).  Each
+ * part runs through the steps of V (coupling at la + lb + 1, Gaunt coupling, translation, rotation) in
+ * FP64, whatever the basis's precision.
+ * centers, charges: device, as for shgo_nuclear_attraction.  out: device, 3 x nbf x nbf doubles
+ * (component-major, each nbf x nbf row-major), fully overwritten.  Single bases only (a batch gives
+ * SHGO_ERR_INVALID_ARG).  Allocates its work arrays stream-ordered on `stream` (about
+ * n_r(la + lb + 1) doubles per primitive pair and 9 blocks per shell pair; SHGO_ERR_OOM when they do not
+ * fit).  The time limit of shgo_basis_set_time_limit does not apply.  Asynchronous on `stream`; calls on
+ * one basis must be ordered with its other calls.  Errors: SHGO_ERR_INVALID_ARG, SHGO_ERR_OOM,
+ * SHGO_ERR_CUDA. */
+shgo_status shgo_nuclear_attraction_deriv(const shgo_basis* basis, const shgo_centers* centers,
+                                          const double* charges, double* out, void* stream);
+
+/* Field integrals of the nuclei (derivative of V by the nucleus positions, summed):
+ *   out[X][a][b] = sum_C Z_C d/dC_X < phi_a | 1/|r - C| | phi_b >   (symmetric in a, b).
+ * The matrix of one nucleus C (the Hellmann-Feynman force integrals) is the call with that nucleus alone
+ * and Z_C = 1.  The one-centre integral of Eq. 12 depends on C - P only, and its derivative is the
+ * integral of the differentiated integrand d_X [r^{2k} S_LM(r) e^{-p r^2}], which the l +- 1 steps of Eq. 3
+ * write as one-centre integrals of order la + lb + 1; the rest is the pipeline of V.  Same arguments,
+ * layout, restrictions and errors as shgo_nuclear_attraction_deriv (3 blocks per shell pair). */
+shgo_status shgo_nuclear_field(const shgo_basis* basis, const shgo_centers* centers, const double* charges,
+                               double* out, void* stream);
+
 /* Overlap matrix S_ab = <a|b> of a basis or of every molecule of a batch (Eqs. 9-10): both
  * Gaussians of a pair translated to the product centre P (Eq. 7), where the one-centre integral is
  * diagonal in (l, m) by the orthogonality of Eq. 10, then rotated from the pair frame back to the
@@ -348,7 +379,7 @@ const char* shgo_last_error(void);
  * ------------------------------------------------------------------------------------------- */
 
 /* Real solid harmonics S_lm(r), m = -l..l, of Eq. 2 by the library's recursion:
- * out[p * (2l+1) + m + l] for the npts points xyz[3p..3p+2].  l <= 2 * SHGO_LMAX. */
+ * out[p * (2l+1) + m + l] for the npts points xyz[3p..3p+2].  l <= 2 * SHGO_LMAX + 1. */
 shgo_status shgo_host_solid_harmonics(int32_t l, int64_t npts, const double* xyz, double* out);
 
 /* Real coupling coefficient G with S_{l1 m1}(r) S_{l2 m2}(r) = sum_{L,M} G r^{l1+l2-L} S_{LM}(r)
@@ -363,6 +394,19 @@ double shgo_host_translation(int32_t la, int32_t ma, int32_t l1, int32_t m1, int
 /* F_n(T), n = 0..nmax (nmax <= 2 * SHGO_LMAX + 1), by the device algorithm (tabulated Taylor
  * expansion and downward recursion below T = 40, asymptotic start and upward recursion above). */
 shgo_status shgo_host_boys(int32_t nmax, double T, double* F);
+
+/* The derivative integrals' steps on one coupling block, from the device tables.  r1 holds one-centre
+ * integrals R'[L, M, k] of order lam + 1 (n_r(lam + 1) = (lam+2)(lam+3)(lam+4)/6 entries, ordered by L, then
+ * M = -L..L, then k = 0..(lam + 1 - L)/2); raised and field receive n_r(lam) entries of order lam:
+ *   raised[L, M, k] = the integral with r^{2k} S_LM(r) replaced by x_c r^{2k} S_LM(r),
+ *   field[L, M, k]  = the integral with r^{2k} S_LM(r) e^{-p r^2} replaced by its derivative d/dx_c,
+ * c = comp (0, 1, 2 = x, y, z).  lam <= 2 * SHGO_LMAX. */
+shgo_status shgo_host_deriv_transform(int32_t lam, int32_t comp, double p, const double* r1, double* raised,
+                                      double* field);
+
+/* Lowering coefficients: d/dx_c S_lm(r) = sum_M' w[M' + l - 1] S_{l-1,M'}(r), 1 <= l <= SHGO_LMAX;
+ * w receives 2l - 1 values. */
+shgo_status shgo_host_deriv_lowering(int32_t l, int32_t comp, int32_t m, double* w);
 
 /* Coefficient a_{k,j}(L) of the k-fold Laplacian of a solid harmonic times a radial function:
  * Laplacian^k [S_LM(R) f(u)] = S_LM(R) sum_j a_{k,j}(L) u^j f^{(k+j)}(u), u = |R|^2, as the two- and

@@ -804,6 +804,37 @@ shgo_status esp_call(const shgo_basis* basis, const double* density, const shgo_
 }
 }  // namespace
 
+namespace {
+shgo_status deriv_call(const shgo_basis* basis, const shgo_centers* centers, const double* charges, double* out,
+                       void* stream, bool field) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "derivative integrals take a single basis, not a batch");
+  if (!centers || centers->n < 0) return fail(SHGO_ERR_INVALID_ARG, "centers is NULL or negative count");
+  if (centers->n > 0 && (!centers->xyz || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
+  if (basis->nbf > 0 && !out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  std::string err;
+  const shgo_status st = launch_nuclear_deriv(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n,
+                                              centers->xyz, charges, out, field, (cudaStream_t)stream, &err);
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
+}
+}  // namespace
+
+shgo_status shgo_nuclear_attraction_deriv(const shgo_basis* basis, const shgo_centers* centers,
+                                          const double* charges, double* out, void* stream) {
+  return deriv_call(basis, centers, charges, out, stream, false);
+}
+
+shgo_status shgo_nuclear_field(const shgo_basis* basis, const shgo_centers* centers, const double* charges,
+                               double* out, void* stream) {
+  return deriv_call(basis, centers, charges, out, stream, true);
+}
+
 shgo_status shgo_esp(const shgo_basis* basis, const double* density, const shgo_centers* points, double* phi,
                      void* stream) {
   return esp_call(basis, density, points, phi, stream, false);
@@ -1167,6 +1198,33 @@ double shgo_host_laplacian_coef(int32_t L, int32_t k, int32_t j) {
 double shgo_host_eri_eps(int32_t L, int32_t k, int32_t n) {
   if (L < 0 || L > kLamMax || k < 0 || k > kC2K || n < 0 || n > k) return 0.0;
   return tables_host().eri_eps[((size_t)L * (kC2K + 1) + k) * (kC2K + 1) + n];
+}
+
+shgo_status shgo_host_deriv_transform(int32_t lam, int32_t comp, double p, const double* r1, double* raised,
+                                      double* field) {
+  if (lam < 0 || lam > kLamMax || comp < 0 || comp > 2 || !r1 || !raised || !field)
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  const Tables& t = tables_host();
+  for (int e = 0; e < n_r(lam); ++e) {
+    const GTerm* tr = &t.d_raise[((size_t)(t.d_xoff[lam] + e) * 3 + comp) * kDerivSlots];
+    const GTerm* tf = &t.d_field[((size_t)(t.d_xoff[lam] + e) * 3 + comp) * kDerivSlots];
+    double s = 0.0, f = 0.0;
+    for (int k = 0; k < kDerivSlots; ++k) {
+      s += tr[k].coef * r1[tr[k].ridx];
+      f += tf[k].coef * r1[tf[k].ridx];
+    }
+    raised[e] = s;
+    field[e] = f - 2.0 * p * s;
+  }
+  return SHGO_OK;
+}
+
+shgo_status shgo_host_deriv_lowering(int32_t l, int32_t comp, int32_t m, double* w) {
+  if (l < 1 || l > kLmax || comp < 0 || comp > 2 || m < -l || m > l || !w)
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  const Tables& t = tables_host();
+  for (int k = 0; k < 2 * l - 1; ++k) w[k] = t.d_low[t.d_low_off[l] + ((size_t)comp * (2 * l + 1) + m + l) * (2 * l - 1) + k];
+  return SHGO_OK;
 }
 
 shgo_status shgo_host_boys(int32_t nmax, double T, double* F) {

@@ -393,17 +393,19 @@ constexpr size_t smem_at(int lam, std::integer_sequence<int, L...>) {
 }
 
 using Lams = std::make_integer_sequence<int, kLamMax + 1>;
+// the coupling kernel also runs at Lambda = la + lb + 1 (derivative integrals)
+using LamsDer = std::make_integer_sequence<int, kLamDer + 1>;
 
 CouplingKernel coupling_kernel(int lam, int nch) {
-  if (lam < 0 || lam > kLamMax) return nullptr;
-  return nch == 16 ? kernel_at<16>(lam, Lams{}) : kernel_at<32>(lam, Lams{});
+  if (lam < 0 || lam > kLamDer) return nullptr;
+  return nch == 16 ? kernel_at<16>(lam, LamsDer{}) : kernel_at<32>(lam, LamsDer{});
 }
 
 }  // namespace
 
 size_t coupling_fp64_smem(int lam, int nch) {
-  if (lam < 0 || lam > kLamMax) return 0;
-  return nch == 16 ? smem_at<16>(lam, Lams{}) : smem_at<32>(lam, Lams{});
+  if (lam < 0 || lam > kLamDer) return 0;
+  return nch == 16 ? smem_at<16>(lam, LamsDer{}) : smem_at<32>(lam, LamsDer{});
 }
 
 size_t esp_fp64_smem(int lam) { return coupling_fp64_smem(lam, 32) + sizeof(double) * 40; }
@@ -425,7 +427,7 @@ cudaError_t launch_esp_grad_fp64(int lam, const EspArgs& args, cudaStream_t stre
 cudaError_t coupling_fp64_setup() {
   cudaError_t e = cudaMemcpyToSymbol(k_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_boys, &boys_const_host(), sizeof(BoysConst));
-  for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam)
+  for (int lam = 0; lam <= kLamDer && e == cudaSuccess; ++lam)
     for (int nch : {16, 32}) {
       e = set_max_dynamic_smem((const void*)coupling_kernel(lam, nch));
       if (e != cudaSuccess) break;

@@ -1,0 +1,552 @@
+// Derivative integrals of the nuclear attraction: dV_ab/dA and dV_ab/dB (A, B the centres of the two basis
+// functions) and the field integrals sum_C Z_C dV_ab/dC, through the steps of V itself (nucleus sums S2,
+// Gaunt coupling and primitive contraction S3, translation and rotation S4) with one extra order of the
+// one-centre integral and the l +- 1 steps of Eq. 3.
+//
+// For a = N S_la(r - A) exp(-alpha |r - A|^2), b the same on B with beta, p = alpha + beta, P the product
+// centre (Eq. 5) and mu = alpha beta / p, the derivative of exp(-alpha |r - A|^2) by A_X is
+// 2 alpha (r - A)_X exp(...), and r - A = (r - P) + (beta / p)(B - A), so
+//   d/dA_X [a b] = -(d_X S_la)(r - A) [...]  -  2 mu (A - B)_X a b  +  2 alpha (r - P)_X a b.
+// Term 1 is a V block of the lowered class (la - 1, lb), combined with
+// d_X S_la,ma = (2 la + 1) sum_M G(1 m(X), la ma; la - 1 M) S_{la-1,M}.  Term 2 is V with every primitive pair
+// weighted by mu.  Term 3 multiplies the one-centre integrand of Eq. 12 by a Cartesian component of r - P,
+// which couples S_LM to L + 1 and (with r^2) to L - 1 as the product S_1 S_L of Eq. 3:
+//   r^{2k} x_c S_LM = sum G(1 m(c), L M; L+1 M') r^{2k} S_{L+1,M'} + sum G(1 m(c), L M; L-1 M') r^{2k+2} S_{L-1,M'},
+// so it reads the one-centre integrals R'[L, M, k] up to Lambda + 1 = la + lb + 1.  B is the same with beta,
+// the opposite sign of term 2 and the lowered class (la, lb - 1).  The field integrals move the nucleus: the
+// integral of f(r - P) / |r - C| has d/dC_X equal to the integral of (d_X f)(r - P) / |r - C|, and
+// d_c [r^{2k} S_LM e^{-p r^2}] is again a sum of R' terms of order Lambda + 1.
+//
+// The raised and differentiated terms live in the pair frame (component c of Q (r - A)); the molecular
+// component X is sum_c Q[c][X] (component c), Q the frame rotation, applied to the rotated blocks.
+//
+// Launches per class, on the pool streams: the FP64 coupling kernel at Lambda + 1 (one block per primitive
+// pair), k_deriv_block (one block per shell pair and variant, blockIdx.y: the mu-weighted block, the blocks
+// raised along c weighted by 2 alpha or 2 beta, the lowered classes, or the field blocks, each rotated to the
+// molecular frame into a scratch array) and k_deriv_combine, which adds a shell pair's variants in a fixed
+// order into the output (no atomics: the result does not depend on the schedule).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "shgo_internal.h"
+
+namespace shgo {
+
+namespace {
+
+// Variants of k_deriv_block.
+constexpr int kKindMu = 0;      // V with primitive-pair weight mu
+constexpr int kKindRaiseA = 1;  // .. 3: (r - P)_c raised, weight 2 alpha
+constexpr int kKindRaiseB = 4;  // .. 6: (r - P)_c raised, weight 2 beta
+constexpr int kKindLowA = 7;    // class (la - 1, lb)
+constexpr int kKindLowB = 8;    // class (la, lb - 1)
+constexpr int kKindField = 9;   // .. 11: d_c of the one-centre integrand
+constexpr int kKinds = 12;
+
+__host__ __device__ inline void deriv_shape(int la, int lb, int kind, int& lbra, int& lket) {
+  lbra = kind == kKindLowA ? la - 1 : la;
+  lket = kind == kKindLowB ? lb - 1 : lb;
+}
+
+// Shared memory of one k_deriv_block variant (doubles, see the carve-up in the kernel).
+__host__ __device__ inline size_t deriv_block_doubles(int la, int lb, int kind) {
+  int lbra, lket;
+  deriv_shape(la, lb, kind, lbra, lket);
+  const int lhi = lbra > lket ? lbra : lket, llo = lbra > lket ? lket : lbra;
+  const int na = 2 * lbra + 1, nb = 2 * lket + 1;
+  return (size_t)(lhi + 1) * (lhi + 1) * w_stride(llo) + na * na + nb * nb + (lbra + 1) * na + (lket + 1) * nb +
+         (size_t)(lbra + 1) * (lbra + 1) * nb + 2 * na * nb + (lhi + 1) * (llo + 1) + n_r(la + lb + 1) +
+         n_r(lbra + lket) + 8 + 16;
+}
+
+struct DerivArgs {
+  int la = 0, lb = 0, npairs = 0, pair_base = 0;
+  int64_t pp_base = 0, rbase = 0;  // the class's first primitive pair; its coupling blocks at r1buf + rbase
+  int nkind = 0;
+  int kinds[9] = {};
+  int64_t voff[kKinds] = {};  // offset of each variant's block in a shell pair's scratch (doubles)
+  int64_t per_pair = 0;       // scratch doubles per shell pair
+  double* scratch = nullptr;  // the class's scratch
+  const int* pair_a = nullptr;
+  const int* pair_b = nullptr;
+  const int64_t* pair_ppoff = nullptr;
+  const int* pair_site = nullptr;
+  int64_t rot_per = 0;
+  const double* rotd = nullptr;
+  const int* shell_poff = nullptr;
+  const int* shell_nprim = nullptr;
+  const double* prim_exp = nullptr;
+  const int* pp_ij = nullptr;
+  const double* etab = nullptr;
+  const int* eoff = nullptr;
+  const int* rowinfo[3] = {};  // Gaunt programs: the class, the class lowered on a, lowered on b
+  const int* grp[3] = {};
+  const GTerm* gterms[3] = {};
+  const int* map0 = nullptr;       // Lambda layout -> Lambda + 1 layout
+  const int* mapm = nullptr;       // Lambda - 1 layout -> Lambda + 1 layout
+  const GTerm* raise = nullptr;    // Tables::d_raise of this Lambda
+  const GTerm* fconst = nullptr;   // Tables::d_field of this Lambda
+  const PPData* ppd = nullptr;
+  const double* r1buf = nullptr;
+};
+
+__global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int kind = A.kinds[blockIdx.y];
+  int lbra, lket;
+  deriv_shape(A.la, A.lb, kind, lbra, lket);
+  // the lowered class (la - 1, la) has its Gaunt program stored as (la, la - 1): rows on the ket
+  const bool swap = lbra < lket;
+  const int lhi = swap ? lket : lbra, llo = swap ? lbra : lket;
+  const int prog = kind == kKindLowA ? 1 : (kind == kKindLowB ? 2 : 0);
+  const int* __restrict__ rowinfo = A.rowinfo[prog];
+  const int* __restrict__ grp = A.grp[prog];
+  const GTerm* __restrict__ gterms = A.gterms[prog];
+  const bool raised = kind >= kKindRaiseA && kind < kKindLowA;
+  const bool field = kind >= kKindField;
+  const int comp = field ? kind - kKindField : (kind >= kKindRaiseB ? kind - kKindRaiseB : kind - kKindRaiseA);
+  const int* __restrict__ rmap = (kind == kKindLowA || kind == kKindLowB) ? A.mapm : A.map0;
+  const int nR1 = n_r(A.la + A.lb + 1), nRv = n_r(lbra + lket);
+  const int nWh = (lhi + 1) * (lhi + 1), nWl = (llo + 1) * (llo + 1), nW = nWh * nWl;
+  const int ws = w_stride(llo), nWs = nWh * ws, nrp = (nW + 31) & ~31;
+  const int nWa = (lbra + 1) * (lbra + 1);
+  const int na = 2 * lbra + 1, nb = 2 * lket + 1;
+  const int lm = lbra > lket ? lbra : lket;
+  const int nDb = lbra != lket ? nb * nb : 0;
+  double* W = smem;                          // program layout [hi (l1 m1)][lo (l2 m2)], row stride ws
+  double* Dm = W + nWs;                      // D^{lbra}(Q^T), then D^{lket}(Q^T) when they differ
+  double* tA = Dm + na * na + nb * nb;       // [l1][ma]
+  double* tB = tA + (lbra + 1) * na;         // [l2][mb]
+  double* Zb = tB + (lket + 1) * nb;         // [bra (l1 m1)][mb]
+  double* Vp = Zb + nWa * nb;                // [ma][mb]
+  double* Yb = Vp + na * nb;                 // [ma][mb]
+  double* fab = Yb + na * nb;                // [hi l][lo l]
+  double* R1 = fab + (lhi + 1) * (llo + 1);  // coupling block of Lambda + 1 of one primitive pair
+  double* Rv = R1 + nR1;                     // the variant's block in the layout its program reads
+  double* scal = Rv + nRv;                   // prefactor, beta/p, alpha/p, weight, p
+  double* dpow = scal + 8;                   // |b - a|^k
+  for (int w = blockIdx.x; w < A.npairs; w += gridDim.x) {
+    const int pr = A.pair_base + w;
+    const int a = A.pair_a[pr], b = A.pair_b[pr];
+    const double* rd = A.rotd + (int64_t)A.pair_site[pr] * A.rot_per;
+    __syncthreads();
+    if (tid == 0) {
+      const double dist = rd[0];
+      double v = 1.0;
+      for (int k = 0; k <= lm; ++k) {
+        dpow[k] = v;
+        v *= dist;
+      }
+    }
+    for (int e = tid; e < na * na; e += nth) Dm[e] = rd[1 + rot_doff(lbra) + e];
+    for (int e = tid; e < nDb; e += nth) Dm[na * na + e] = rd[1 + rot_doff(lket) + e];
+    for (int e = tid; e < nWs; e += nth) W[e] = 0.0;
+    __syncthreads();
+    // translation along the pair axis (Eqs. 7-8, only nu = 0 survives), as in the V pair kernel
+    for (int e = tid; e < (lbra + 1) * na; e += nth) {
+      const int l1 = e / na, ma = e % na - lbra, lr = lbra - l1;
+      double v = 0.0;
+      if (l1 >= (ma < 0 ? -ma : ma)) v = A.etab[A.eoff[lbra] + translation_offset_dev(lbra, ma, l1, ma) + lr] * dpow[lr];
+      tA[e] = v;
+    }
+    for (int e = tid; e < (lket + 1) * nb; e += nth) {
+      const int l2 = e / nb, mb = e % nb - lket, lr = lket - l2;
+      double v = 0.0;
+      if (l2 >= (mb < 0 ? -mb : mb))
+        v = A.etab[A.eoff[lket] + translation_offset_dev(lket, mb, l2, mb) + lr] * ((lr & 1) ? -dpow[lr] : dpow[lr]);
+      tB[e] = v;
+    }
+    const int npa = A.shell_nprim[a], npb = A.shell_nprim[b];
+    const int64_t q0 = A.pair_ppoff[pr];
+    bool live = false;  // uniform over the block
+    for (int ij = 0; ij < npa * npb; ++ij) {
+      __syncthreads();  // the previous primitive pair is done with R1, Rv, fab and scal
+      if (tid == 0) {
+        const PPData pd = A.ppd[q0 + ij];
+        const int pij = A.pp_ij[q0 + ij];
+        const double al = A.prim_exp[A.shell_poff[a] + (pij >> 8)], be = A.prim_exp[A.shell_poff[b] + (pij & 0xff)];
+        scal[0] = pd.pref;
+        scal[1] = pd.ra;
+        scal[2] = pd.rb;
+        scal[3] = kind == kKindMu ? al * be * pd.rp
+                                  : (kind >= kKindRaiseA && kind < kKindRaiseB ? 2.0 * al
+                                                                               : (kind >= kKindRaiseB && kind < kKindLowA ? 2.0 * be : 1.0));
+        scal[4] = pd.p;
+      }
+      __syncthreads();
+      if (scal[0] == 0.0) continue;  // skipped by the coupling kernel too (uniform over the block)
+      live = true;
+      const double* R = A.r1buf + A.rbase + (q0 + ij - A.pp_base) * (int64_t)nR1;
+      for (int e = tid; e < nR1; e += nth) R1[e] = R[e];
+      if (tid < (lhi + 1) * (llo + 1)) {
+        const int l1 = tid / (llo + 1), l2 = tid % (llo + 1);
+        const int lb_i = swap ? l2 : l1, lk_i = swap ? l1 : l2;  // the bra's and the ket's l of the row
+        double v = scal[0] * scal[3];
+        const double ra = scal[1], rb = scal[2];
+        for (int k = 0; k < lbra - lb_i; ++k) v *= ra;
+        for (int k = 0; k < lket - lk_i; ++k) v *= rb;
+        fab[tid] = v;
+      }
+      __syncthreads();
+      if (raised || field) {
+        const double m2p = -2.0 * scal[4];
+        for (int e = tid; e < nRv; e += nth) {
+          const GTerm* tr = A.raise + ((size_t)e * 3 + comp) * kDerivSlots;
+          double s = 0.0;
+#pragma unroll
+          for (int t = 0; t < kDerivSlots; ++t) s = fma(tr[t].coef, R1[tr[t].ridx], s);
+          if (field) {
+            const GTerm* tf = A.fconst + ((size_t)e * 3 + comp) * kDerivSlots;
+            double f = 0.0;
+#pragma unroll
+            for (int t = 0; t < kDerivSlots; ++t) f = fma(tf[t].coef, R1[tf[t].ridx], f);
+            s = fma(m2p, s, f);
+          }
+          Rv[e] = s;
+        }
+      } else {
+        for (int e = tid; e < nRv; e += nth) Rv[e] = R1[rmap[e]];
+      }
+      __syncthreads();
+      // Gaunt coupling: rows of one warp form one group (equal trip counts, coalesced term loads)
+      for (int r = tid; r < nrp; r += nth) {
+        const int info = rowinfo[r];
+        const int gi = r >> 5, K = grp[2 * gi + 1];
+        const GTerm* tp = gterms + grp[2 * gi] + (r & 31);
+        double acc0 = 0.0, acc1 = 0.0;
+        int j = 0;
+        for (; j + 1 < K; j += 2) {
+          const GTerm g0 = tp[32 * j], g1 = tp[32 * j + 32];
+          acc0 = fma(g0.coef, Rv[g0.ridx], acc0);
+          acc1 = fma(g1.coef, Rv[g1.ridx], acc1);
+        }
+        if (j < K) {
+          const GTerm g0 = tp[32 * j];
+          acc0 = fma(g0.coef, Rv[g0.ridx], acc0);
+        }
+        if (info >= 0) {
+          const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
+          W[e] = fma(fab[l1 * (llo + 1) + l2], acc0 + acc1, W[e]);
+        }
+      }
+    }
+    __syncthreads();
+    double* o = A.scratch + (int64_t)w * A.per_pair + A.voff[kind];
+    if (!live) {
+      for (int e = tid; e < na * nb; e += nth) o[e] = 0.0;
+      continue;
+    }
+    // V' = t_A W t_B in the pair frame (diagonal in m), first over the ket's l
+    for (int e = tid; e < nWa * nb; e += nth) {
+      const int q = e / nWa, i1 = e - q * nWa;
+      const int amb = (q + 1) >> 1, mb = (q & 1) ? amb : -amb;
+      double s = 0.0;
+      for (int l2 = amb; l2 <= lket; ++l2) {
+        const int i2 = l2 * l2 + l2 + mb;
+        s = fma(tB[l2 * nb + mb + lket], swap ? W[i2 * ws + i1] : W[i1 * ws + i2], s);
+      }
+      Zb[i1 * nb + mb + lket] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < na * nb; e += nth) {
+      const int q = e / nb, mb = e - q * nb;
+      const int ama = (q + 1) >> 1, ma = (q & 1) ? ama : -ama;
+      double s = 0.0;
+      for (int l1 = ama; l1 <= lbra; ++l1) s = fma(tA[l1 * na + ma + lbra], Zb[(l1 * l1 + l1 + ma) * nb + mb], s);
+      Vp[(ma + lbra) * nb + mb] = s;
+    }
+    __syncthreads();
+    // to the molecular frame: D^{lbra} V' (D^{lket})^T
+    const double* Da = Dm;
+    const double* Db = lbra != lket ? Dm + na * na : Dm;
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      double s = 0.0;
+      for (int k = 0; k < nb; ++k) s = fma(Vp[ma * nb + k], Db[mb * nb + k], s);
+      Yb[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+      double s = 0.0;
+      for (int k = 0; k < na; ++k) s = fma(Da[ma * na + k], Yb[k * nb + mb], s);
+      o[e] = s;
+    }
+  }
+}
+
+struct CombineArgs {
+  int la = 0, lb = 0, npairs = 0, pair_base = 0;
+  bool field = false;
+  int64_t nbf = 0;
+  int64_t voff[kKinds] = {};
+  int64_t per_pair = 0;
+  const double* scratch = nullptr;
+  const int* pair_a = nullptr;
+  const int* pair_b = nullptr;
+  const int* pair_site = nullptr;
+  const double* site_rot = nullptr;
+  const double* shell_xyz = nullptr;
+  const int64_t* shell_foff = nullptr;
+  const double* low_a = nullptr;  // Tables::d_low of la (nullptr for la = 0)
+  const double* low_b = nullptr;  // of lb
+  double* out = nullptr;          // [3][nbf][nbf]
+};
+
+// One block per shell pair: the derivative (or field) blocks of the pair from its variants, both
+// orientations written.  Derivative: out[X][a][b] = -sum_M' low(la)[X][ma][M'] V_low_a[M'][mb]
+// - 2 (A - B)_X V_mu + sum_c Q[c][X] V_raise_a,c and, for a != b, out[X][b][a] the same with the ket's
+// variants and +2 (A - B)_X.  Field: out[X][a][b] = out[X][b][a] = sum_c Q[c][X] V_field,c (a diagonal
+// shell block takes its upper triangle for both halves, as V does).
+__global__ void __launch_bounds__(128) k_deriv_combine(CombineArgs C) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int na = 2 * C.la + 1, nb = 2 * C.lb + 1;
+  const int64_t plane = C.nbf * C.nbf;
+  for (int w = blockIdx.x; w < C.npairs; w += gridDim.x) {
+    const int pr = C.pair_base + w;
+    const int a = C.pair_a[pr], b = C.pair_b[pr];
+    const int64_t fa0 = C.shell_foff[a], fb0 = C.shell_foff[b];
+    const double* s = C.scratch + (int64_t)w * C.per_pair;
+    const double* Q = C.site_rot + 9 * (int64_t)C.pair_site[pr];
+    double ab[3];
+#pragma unroll
+    for (int X = 0; X < 3; ++X) ab[X] = C.shell_xyz[3 * a + X] - C.shell_xyz[3 * b + X];
+    for (int e = tid; e < na * nb; e += nth) {
+      const int ma = e / nb, mb = e % nb;
+#pragma unroll
+      for (int X = 0; X < 3; ++X) {
+        double* o = C.out + X * plane;
+        if (C.field) {
+          const int ee = (a == b && ma > mb) ? mb * nb + ma : e;
+          double v = 0.0;
+          for (int c = 0; c < 3; ++c) v = fma(Q[3 * c + X], s[C.voff[kKindField + c] + ee], v);
+          o[(fa0 + ma) * C.nbf + fb0 + mb] = v;
+          if (a != b) o[(fb0 + mb) * C.nbf + fa0 + ma] = v;
+          continue;
+        }
+        const double vmu = s[C.voff[kKindMu] + e];
+        double v = -2.0 * ab[X] * vmu;
+        for (int c = 0; c < 3; ++c) v = fma(Q[3 * c + X], s[C.voff[kKindRaiseA + c] + e], v);
+        if (C.la > 0) {
+          const int nl = 2 * C.la - 1;
+          const double* lo = C.low_a + ((int64_t)X * na + ma) * nl;
+          const double* vl = s + C.voff[kKindLowA];
+          for (int k = 0; k < nl; ++k) v = fma(-lo[k], vl[k * nb + mb], v);
+        }
+        o[(fa0 + ma) * C.nbf + fb0 + mb] = v;
+        if (a == b) continue;
+        double u = 2.0 * ab[X] * vmu;
+        for (int c = 0; c < 3; ++c) u = fma(Q[3 * c + X], s[C.voff[kKindRaiseB + c] + e], u);
+        if (C.lb > 0) {
+          const int nl = 2 * C.lb - 1;
+          const double* lo = C.low_b + ((int64_t)X * nb + mb) * nl;
+          const double* vl = s + C.voff[kKindLowB] + (int64_t)ma * nl;
+          for (int k = 0; k < nl; ++k) u = fma(-lo[k], vl[k], u);
+        }
+        o[(fb0 + mb) * C.nbf + fa0 + ma] = u;
+      }
+    }
+  }
+}
+
+int class_of(int l1, int l2) { return l1 >= l2 ? class_id(l1, l2) : class_id(l2, l1); }
+
+}  // namespace
+
+shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                                 int64_t nbf, int64_t ncenters, const double* centers, const double* charges,
+                                 double* out, bool field, cudaStream_t stream, std::string* err) {
+  if (nbf == 0) return SHGO_OK;
+  const size_t nout = (size_t)3 * (size_t)nbf * (size_t)nbf;
+  if (ncenters == 0) {
+    const cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * nout, stream);
+    if (e != cudaSuccess) {
+      *err = cudaGetErrorString(e);
+      return SHGO_ERR_CUDA;
+    }
+    return SHGO_OK;
+  }
+  const Tables& th = tables_host();
+  // per class: variants, scratch layout, coupling-block and scratch offsets
+  struct Plan {
+    DerivArgs d;
+    CombineArgs c;
+    size_t smem = 0;
+    int threads = 32;
+    int64_t r1 = 0, scr = 0;  // doubles
+  };
+  std::vector<Plan> plan(work.size());
+  int64_t r1_total = 0, scr_total = 0;
+  for (size_t ci = 0; ci < work.size(); ++ci) {
+    const ClassWork& w = work[ci];
+    Plan& P = plan[ci];
+    DerivArgs& d = P.d;
+    d.la = w.la;
+    d.lb = w.lb;
+    d.npairs = w.npairs;
+    d.pair_base = w.pair_base;
+    d.pp_base = w.pp_base;
+    std::vector<int> kinds;
+    if (field) {
+      kinds = {kKindField, kKindField + 1, kKindField + 2};
+    } else {
+      for (int k = kKindMu; k < kKindLowA; ++k) kinds.push_back(k);
+      if (w.la > 0) kinds.push_back(kKindLowA);
+      if (w.lb > 0) kinds.push_back(kKindLowB);
+    }
+    d.nkind = (int)kinds.size();
+    int64_t off = 0;
+    for (int k = 0; k < d.nkind; ++k) {
+      d.kinds[k] = kinds[k];
+      int lbra, lket;
+      deriv_shape(w.la, w.lb, kinds[k], lbra, lket);
+      d.voff[kinds[k]] = off;
+      off += (int64_t)(2 * lbra + 1) * (2 * lket + 1);
+      P.smem = std::max(P.smem, sizeof(double) * deriv_block_doubles(w.la, w.lb, kinds[k]));
+    }
+    d.per_pair = off;
+    P.threads = (w.la + 1) * (w.la + 1) * (w.lb + 1) * (w.lb + 1) >= 1024
+                    ? 128
+                    : ((w.la + 1) * (w.la + 1) * (w.lb + 1) * (w.lb + 1) >= 256 ? 64 : 32);
+    P.r1 = r1_total;
+    P.scr = scr_total;
+    r1_total += w.npp * (int64_t)n_r(w.la + w.lb + 1);
+    scr_total += (int64_t)w.npairs * off;
+  }
+  double* r1buf = nullptr;
+  double* scr = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&r1buf, sizeof(double) * (size_t)std::max<int64_t>(r1_total, 1), stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&scr, sizeof(double) * (size_t)std::max<int64_t>(scr_total, 1), stream);
+  if (e != cudaSuccess) {
+    if (r1buf) cudaFreeAsync(r1buf, stream);
+    cudaGetLastError();
+    *err = std::string("derivative buffers: ") + cudaGetErrorString(e);
+    return SHGO_ERR_OOM;
+  }
+  e = ensure_max_dynamic_smem((const void*)k_deriv_block);
+  cudaStream_t* pool = nullptr;
+  int npool = 0;
+  if (e == cudaSuccess) e = pool_streams(&pool, &npool);
+  // classes by decreasing work, dealt round-robin over the pool streams
+  std::vector<int> order(work.size());
+  for (size_t c = 0; c < work.size(); ++c) order[c] = (int)c;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    auto cost = [&](int c) {
+      const double nW = (double)(work[c].la + 1) * (work[c].la + 1) * (work[c].lb + 1) * (work[c].lb + 1);
+      return (double)work[c].npp * ((double)ncenters * n_r(work[c].la + work[c].lb + 1) + 8.0 * nW * plan[c].d.nkind);
+    };
+    return cost(x) > cost(y);
+  });
+  const int ns = (int)std::min<size_t>(order.size(), (size_t)std::max(npool, 1));
+  cudaEvent_t fork = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, stream);
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pool[i], fork, 0);
+  for (size_t k = 0; k < order.size() && e == cudaSuccess; ++k) {
+    const int ci = order[k];
+    const ClassWork& w = work[ci];
+    if (w.npairs == 0) continue;
+    cudaStream_t s = pool[k % ns];
+    Plan& P = plan[ci];
+    const int lam1 = w.la + w.lb + 1;
+    if (w.npp > 0) {
+      CouplingArgs ca;
+      ca.npp = w.npp;
+      ca.pp_base = w.pp_base;
+      ca.rbase = P.r1;
+      ca.pp_pair = db.pp_pair;
+      ca.pair_a = db.pair_a;
+      ca.shell_xyz = db.shell_xyz;
+      ca.mv.ncenters = ncenters;
+      ca.mv.nbf = nbf;
+      ca.centers = centers;
+      ca.charges = charges;
+      ca.boys_tab = dt.boys;
+      ca.rmap = dt.rmap + th.rmap_off[lam1];
+      ca.rnorm = dt.rnorm + th.rmap_off[lam1];
+      ca.site_rot = db.site_rot;
+      ca.pair_site = db.pair_site;
+      ca.ppd = db.ppd;
+      ca.rbuf = r1buf;
+      e = launch_coupling_fp64(lam1, lam1 <= 12 ? 32 : 16, ca, grid_cap_sm(w.npp, 8), s);
+      if (e != cudaSuccess) break;
+    }
+    DerivArgs& d = P.d;
+    const int lam = w.la + w.lb;
+    d.rbase = P.r1;
+    d.scratch = scr + P.scr;
+    d.pair_a = db.pair_a;
+    d.pair_b = db.pair_b;
+    d.pair_ppoff = db.pair_ppoff;
+    d.pair_site = db.pair_site;
+    d.rot_per = rot_block(db.rot_lmax);
+    d.rotd = db.rotd;
+    d.shell_poff = db.shell_poff;
+    d.shell_nprim = db.shell_nprim;
+    d.prim_exp = db.prim_exp;
+    d.pp_ij = db.pp_ij;
+    d.etab = dt.etab;
+    d.eoff = dt.eoff;
+    const int cids[3] = {class_id(w.la, w.lb), w.la > 0 ? class_of(w.la - 1, w.lb) : -1,
+                         w.lb > 0 ? class_of(w.la, w.lb - 1) : -1};
+    for (int p = 0; p < 3; ++p) {
+      if (cids[p] < 0) continue;
+      d.rowinfo[p] = dt.g_rowinfo + th.g_rowbase[cids[p]];
+      d.grp[p] = dt.g_grp + 2 * th.g_grpbase[cids[p]];
+      d.gterms[p] = dt.g_terms + th.g_termbase[cids[p]];
+    }
+    d.map0 = dt.d_map0 + th.d_map0_off[lam];
+    d.mapm = dt.d_mapm + th.d_mapm_off[lam];
+    d.raise = dt.d_raise + (size_t)th.d_xoff[lam] * 3 * kDerivSlots;
+    d.fconst = dt.d_field + (size_t)th.d_xoff[lam] * 3 * kDerivSlots;
+    d.ppd = db.ppd;
+    d.r1buf = r1buf;
+    const dim3 grid((unsigned)grid_cap_sm(w.npairs, 16), (unsigned)d.nkind);
+    k_deriv_block<<<grid, P.threads, P.smem, s>>>(d);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+    CombineArgs& c = P.c;
+    c.la = w.la;
+    c.lb = w.lb;
+    c.npairs = w.npairs;
+    c.pair_base = w.pair_base;
+    c.field = field;
+    c.nbf = nbf;
+    for (int k = 0; k < kKinds; ++k) c.voff[k] = d.voff[k];
+    c.per_pair = d.per_pair;
+    c.scratch = d.scratch;
+    c.pair_a = db.pair_a;
+    c.pair_b = db.pair_b;
+    c.pair_site = db.pair_site;
+    c.site_rot = db.site_rot;
+    c.shell_xyz = db.shell_xyz;
+    c.shell_foff = db.shell_foff;
+    c.low_a = w.la > 0 ? dt.d_low + th.d_low_off[w.la] : nullptr;
+    c.low_b = w.lb > 0 ? dt.d_low + th.d_low_off[w.lb] : nullptr;
+    c.out = out;
+    k_deriv_combine<<<grid_cap_sm(w.npairs, 16), 64, 0, s>>>(c);
+    e = cudaGetLastError();
+  }
+  for (int i = 0; i < ns && fork; ++i) {
+    cudaEvent_t join;
+    if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) break;
+    cudaEventRecord(join, pool[i]);
+    cudaStreamWaitEvent(stream, join, 0);
+    cudaEventDestroy(join);
+  }
+  if (fork) cudaEventDestroy(fork);
+  cudaFreeAsync(scr, stream);
+  cudaFreeAsync(r1buf, stream);
+  if (e != cudaSuccess) {
+    *err = std::string("derivative launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
+  }
+  return SHGO_OK;
+}
+
+}  // namespace shgo

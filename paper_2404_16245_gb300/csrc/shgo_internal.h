@@ -14,7 +14,8 @@ namespace shgo {
 
 constexpr int kLmax = SHGO_LMAX;          // largest shell l
 constexpr int kLamMax = 2 * kLmax;         // largest la + lb
-constexpr int kHarmMax = kLamMax;          // largest l of S_lm(C - P)
+constexpr int kLamDer = kLamMax + 1;       // largest Lambda of a coupling block (la + lb + 1: derivatives)
+constexpr int kHarmMax = kLamDer;          // largest l of S_lm(C - P)
 
 // Boys grid: T_g = g * h for g = 0..kBoysNg-1, h = 1/16, up to T = kBoysTsw.  Row g holds
 // exp(-T_g) followed by F_n(T_g), n = 0..kBoysNmax.  A value is the Taylor expansion about the
@@ -92,7 +93,7 @@ struct Tables {
   std::vector<int> gt_termbase; // [n classes]
   // R layout per Lambda: packed (harm index | beta index << 12 | k << 24) for entry e.
   std::vector<int> rmap;
-  std::vector<int> rmap_off;  // [kLamMax + 2]
+  std::vector<int> rmap_off;  // [kLamDer + 2]
   std::vector<double> rnorm;  // N_LM of entry e (HarmCoef::n), aligned with rmap
   // Real rotation matrices D^{l+1} from D^l (S_lm(R y) = sum_m' D^l[m][m'] S_lm'(y)): the
   // harmonic part of u_c S_{l,m'}(u) for a Cartesian component c is sum_M G(1 m(c), l m'; l+1 M)
@@ -109,11 +110,29 @@ struct Tables {
   std::vector<GTerm> c2_terms;
   std::vector<int> c2_base;  // [n classes]
   std::vector<double> c2_a;
+  // Derivative integrals (shgo_deriv.cu).  For each Lambda <= kLamMax the coupling block of Lambda + 1
+  // serves the class: d_map0 maps each entry (L, M, k) of the Lambda layout, d_mapm each entry of the
+  // Lambda - 1 layout, to the same (L, M, k) of the Lambda + 1 layout (offsets d_map0_off[Lambda],
+  // d_mapm_off[Lambda]).  With rho = G(1 m(c), L M; L+1 M') and g = G(1 m(c), L M; L-1 M') (m(x) = 1,
+  // m(y) = -1, m(z) = 0), for entry e of the Lambda layout and Cartesian component c, kDerivSlots terms
+  // each (zero-coefficient padding, R' indices in the Lambda + 1 layout):
+  //   d_raise:  r^{2k} x_c S_LM = sum rho r^{2k} S_{L+1,M'} + sum g r^{2k+2} S_{L-1,M'}
+  //   d_field:  the p-free part of d/dx_c [r^{2k} S_LM e^{-p r^2}] e^{+p r^2}
+  //             = sum 2k rho r^{2k-2} S_{L+1,M'} + sum (2k + 2L + 1) g r^{2k} S_{L-1,M'}  (the rest is
+  //             -2p times the d_raise terms)
+  // at ((d_xoff[Lambda] + e) * 3 + c) * kDerivSlots.  d_low: for l = 1..kLmax, the lowering
+  // d/dx_c S_lm = (2l + 1) sum_M' G(1 m(c), l m; l-1 M') S_{l-1,M'} as a dense [c][m][M'] array at
+  // d_low_off[l].
+  std::vector<int> d_map0, d_map0_off, d_mapm, d_mapm_off, d_xoff;
+  std::vector<GTerm> d_raise, d_field;
+  std::vector<double> d_low;
+  std::vector<int> d_low_off;
   // Four-centre electron repulsion: r^{2k} S_LM(r) e^{-p r^2} = sum_{n<=k} eps_{k,n}(L) p^{-(k+n)}
   // Laplacian^n [S_LM(r) e^{-p r^2}], with eps_{k,n}(L) at eri_eps[(L (kC2K + 1) + k)(kC2K + 1) + n].
   std::vector<double> eri_eps;
 };
 constexpr int kC2K = kLamMax / 2;  // largest k of the two-centre radial factors
+constexpr int kDerivSlots = 4;     // terms per entry and component of Tables::d_raise / d_field
 const Tables& tables_host();
 
 // Index of the (l -> l+1, M) list of the rotation recursion: lists for l = 0.. are stored one after
@@ -168,6 +187,12 @@ struct DeviceTables {
   float2* exp_ff = nullptr;   // exp(-g/16) as (hi, lo) FP32 pairs
   float2* rnorm_ff = nullptr; // rnorm as (hi, lo) FP32 pairs
   int* f32_items = nullptr;   // FP32-bulk work items, aligned with rmap (rmap_off)
+  // derivative tables (Tables::d_*)
+  int* d_map0 = nullptr;
+  int* d_mapm = nullptr;
+  GTerm* d_raise = nullptr;
+  GTerm* d_field = nullptr;
+  double* d_low = nullptr;
 };
 shgo_status device_tables(int device, const DeviceTables** out, std::string* err);
 
@@ -442,6 +467,16 @@ shgo_status launch_class_timed(const DeviceBasis& db, const DeviceTables& dt, co
 shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                        int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
                        bool gradient, cudaStream_t stream, std::string* err);
+
+// Derivative integrals of a single basis, computed in FP64 (shgo_deriv.cu).  field = false: out[X] (X = x, y, z,
+// nbf x nbf each) receives dV_ab/d(centre of a)_X; field = true: sum_C Z_C dV_ab/dC_X (symmetric).
+shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
+                                 int64_t nbf, int64_t ncenters, const double* centers, const double* charges,
+                                 double* out, bool field, cudaStream_t stream, std::string* err);
+// The per-device pool of non-blocking streams on which the classes of one call run concurrently.
+cudaError_t pool_streams(cudaStream_t** out, int* n);
+// Blocks for n units of work, at most per_sm per SM.
+int grid_cap_sm(int64_t n, int per_sm);
 
 // Overlap blocks of every shell pair into out (one molecule or a batch, per mv).
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,

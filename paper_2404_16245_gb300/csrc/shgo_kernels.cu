@@ -742,6 +742,11 @@ shgo_status device_tables(int device, const DeviceTables** out, std::string* err
   if (e == cudaSuccess) e = upload(&d.exp_ff, exp_table_pairs());
   if (e == cudaSuccess) e = upload(&d.rnorm_ff, pairs_of(t.rnorm));
   if (e == cudaSuccess) e = upload(&d.f32_items, coupling_f32_items(t.rmap_off));
+  if (e == cudaSuccess) e = upload(&d.d_map0, t.d_map0);
+  if (e == cudaSuccess) e = upload(&d.d_mapm, t.d_mapm);
+  if (e == cudaSuccess) e = upload(&d.d_raise, t.d_raise);
+  if (e == cudaSuccess) e = upload(&d.d_field, t.d_field);
+  if (e == cudaSuccess) e = upload(&d.d_low, t.d_low);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boys, &boys_const_host(), sizeof(BoysConst));
   if (e == cudaSuccess) e = coupling_fp64_setup();
@@ -820,6 +825,16 @@ cudaError_t stream_pool(cudaStream_t** out) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+cudaError_t pool_streams(cudaStream_t** out, int* n) {
+  *n = kPoolStreams;
+  return stream_pool(out);
+}
+
+int grid_cap_sm(int64_t n, int per_sm) { return grid_cap(n, per_sm); }
+
+namespace {
 // Dynamic shared-memory limits, once per device.
 void set_kernel_attributes() {
   int dev = 0;

@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstring>
 #include <mutex>
+#include <stdexcept>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -191,6 +192,79 @@ void boys_grid_row(ld T, int nmax, ld* F, ld* ex) {
   for (int n = nmax - 1; n >= 0; --n) F[n] = (2 * T * F[n + 1] + *ex) / (ld)(2 * n + 1);
 }
 
+// Index of (L, M, k) in the packed R layout of Lambda (entries ordered by L, then M, then k).
+int r_index(int lam, int L, int M, int k) {
+  int e = 0;
+  for (int l = 0; l < L; ++l) e += (2 * l + 1) * (kmax_of(lam, l) + 1);
+  return e + (M + L) * (kmax_of(lam, L) + 1) + k;
+}
+
+// Tables::d_* (derivative integrals): index maps between R layouts, the x_c-raising and the
+// derivative of the one-centre integrand per R entry, and the lowering d/dx_c S_lm.
+void build_deriv_tables(Tables& t) {
+  const int mc[3] = {1, -1, 0};
+  t.d_map0_off.assign(kLamMax + 2, 0);
+  t.d_mapm_off.assign(kLamMax + 2, 0);
+  t.d_xoff.assign(kLamMax + 2, 0);
+  t.d_map0.clear();
+  t.d_mapm.clear();
+  for (int lam = 0; lam <= kLamMax; ++lam) {
+    t.d_map0_off[lam] = (int)t.d_map0.size();
+    t.d_mapm_off[lam] = (int)t.d_mapm.size();
+    t.d_xoff[lam + 1] = t.d_xoff[lam] + n_r(lam);
+    for (int L = 0; L <= lam; ++L)
+      for (int M = -L; M <= L; ++M)
+        for (int k = 0; k <= kmax_of(lam, L); ++k) t.d_map0.push_back(r_index(lam + 1, L, M, k));
+    if (lam >= 1)
+      for (int L = 0; L <= lam - 1; ++L)
+        for (int M = -L; M <= L; ++M)
+          for (int k = 0; k <= kmax_of(lam - 1, L); ++k) t.d_mapm.push_back(r_index(lam + 1, L, M, k));
+  }
+  t.d_map0_off[kLamMax + 1] = (int)t.d_map0.size();
+  t.d_mapm_off[kLamMax + 1] = (int)t.d_mapm.size();
+  const size_t nx = (size_t)t.d_xoff[kLamMax + 1] * 3 * kDerivSlots;
+  t.d_raise.assign(nx, GTerm{0.0, 0, 0});
+  t.d_field.assign(nx, GTerm{0.0, 0, 0});
+  for (int lam = 0; lam <= kLamMax; ++lam) {
+    int e = 0;
+    for (int L = 0; L <= lam; ++L)
+      for (int M = -L; M <= L; ++M)
+        for (int k = 0; k <= kmax_of(lam, L); ++k, ++e)
+          for (int c = 0; c < 3; ++c) {
+            GTerm* rs = &t.d_raise[((size_t)(t.d_xoff[lam] + e) * 3 + c) * kDerivSlots];
+            GTerm* fs = &t.d_field[((size_t)(t.d_xoff[lam] + e) * 3 + c) * kDerivSlots];
+            int nr = 0, nf = 0;
+            auto put = [](GTerm* slots, int& n, double coef, int idx) {
+              if (n >= kDerivSlots) throw std::logic_error("derivative table: more terms than slots");
+              slots[n++] = GTerm{coef, idx, 0};
+            };
+            for (int Mp = -(L + 1); Mp <= L + 1; ++Mp) {
+              const double rho = gaunt_real(1, mc[c], L, M, L + 1, Mp);
+              if (std::fabs(rho) <= 1e-15) continue;
+              put(rs, nr, rho, r_index(lam + 1, L + 1, Mp, k));
+              if (k >= 1) put(fs, nf, 2.0 * k * rho, r_index(lam + 1, L + 1, Mp, k - 1));
+            }
+            for (int Mp = -(L - 1); L >= 1 && Mp <= L - 1; ++Mp) {
+              const double g = gaunt_real(1, mc[c], L, M, L - 1, Mp);
+              if (std::fabs(g) <= 1e-15) continue;
+              put(rs, nr, g, r_index(lam + 1, L - 1, Mp, k + 1));
+              put(fs, nf, (double)(2 * k + 2 * L + 1) * g, r_index(lam + 1, L - 1, Mp, k));
+            }
+          }
+  }
+  t.d_low_off.assign(kLmax + 2, 0);
+  t.d_low.clear();
+  for (int l = 0; l <= kLmax; ++l) {
+    t.d_low_off[l] = (int)t.d_low.size();
+    if (l == 0) continue;
+    for (int c = 0; c < 3; ++c)
+      for (int m = -l; m <= l; ++m)
+        for (int Mp = -(l - 1); Mp <= l - 1; ++Mp)
+          t.d_low.push_back((double)(2 * l + 1) * gaunt_real(1, mc[c], l, m, l - 1, Mp));
+  }
+  t.d_low_off[kLmax + 1] = (int)t.d_low.size();
+}
+
 void build_tables(Tables& t) {
   // Boys grid
   t.boys.assign((size_t)kBoysNg * kBoysStride, 0.0);
@@ -217,10 +291,10 @@ void build_tables(Tables& t) {
             t.etab[base + nu + (la - l1)] = translation_real(la, ma, l1, m1, nu);
         }
   // Packed R layout per Lambda: harm index | beta index << 12 | k << 24
-  t.rmap_off.assign(kLamMax + 2, 0);
-  for (int lam = 0; lam <= kLamMax; ++lam) t.rmap_off[lam + 1] = t.rmap_off[lam] + n_r(lam);
-  t.rmap.assign(t.rmap_off[kLamMax + 1], 0);
-  for (int lam = 0; lam <= kLamMax; ++lam) {
+  t.rmap_off.assign(kLamDer + 2, 0);
+  for (int lam = 0; lam <= kLamDer; ++lam) t.rmap_off[lam + 1] = t.rmap_off[lam] + n_r(lam);
+  t.rmap.assign(t.rmap_off[kLamDer + 1], 0);
+  for (int lam = 0; lam <= kLamDer; ++lam) {
     int e = t.rmap_off[lam], boff = 0;
     for (int L = 0; L <= lam; ++L) {
       const int km = kmax_of(lam, L);
@@ -231,6 +305,7 @@ void build_tables(Tables& t) {
   }
   t.rnorm.resize(t.rmap.size());
   for (size_t e = 0; e < t.rmap.size(); ++e) t.rnorm[e] = harm_coef_host().n[t.rmap[e] & 0xfff];
+  build_deriv_tables(t);
   // Rotation recursion lists: Cartesian component c = 0, 1, 2 (x, y, z) is S_{1, m(c)} with
   // m(x) = 1, m(y) = -1, m(z) = 0.
   t.rot_ptr.clear();

@@ -88,6 +88,15 @@ def _load() -> ctypes.CDLL:
     lib.shgo_esp.restype = ctypes.c_int
     lib.shgo_esp_gradient.argtypes = lib.shgo_esp.argtypes
     lib.shgo_esp_gradient.restype = ctypes.c_int
+    lib.shgo_nuclear_attraction_deriv.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_nuclear_attraction_deriv.restype = ctypes.c_int
+    lib.shgo_nuclear_field.argtypes = lib.shgo_nuclear_attraction_deriv.argtypes
+    lib.shgo_nuclear_field.restype = ctypes.c_int
+    lib.shgo_host_deriv_transform.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, f64p, f64p, f64p]
+    lib.shgo_host_deriv_transform.restype = ctypes.c_int
+    lib.shgo_host_deriv_lowering.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, f64p]
+    lib.shgo_host_deriv_lowering.restype = ctypes.c_int
     lib.shgo_overlap.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_overlap.restype = ctypes.c_int
     lib.shgo_coulomb_2c.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -379,6 +388,87 @@ def esp_gradient(basis, density, points, out=None, stream=None):
         out = torch.empty((max(n, 1), 3), dtype=torch.float64, device=points.device)
     shgo_esp_gradient(basis.handle, density.data_ptr(), n, points.data_ptr() if n else 0, out.data_ptr(), stream)
     return out[:n]
+
+
+def shgo_nuclear_attraction_deriv(basis, n_centers, centers_ptr, charges_ptr, out_ptr, stream=None):
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    _check(_lib.shgo_nuclear_attraction_deriv(ctypes.c_void_p(basis), ctypes.byref(c),
+                                              ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0),
+                                              ctypes.c_void_p(int(out_ptr) if out_ptr else 0), _stream_handle(stream)))
+
+
+def shgo_nuclear_field(basis, n_centers, centers_ptr, charges_ptr, out_ptr, stream=None):
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    _check(_lib.shgo_nuclear_field(ctypes.c_void_p(basis), ctypes.byref(c),
+                                   ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0),
+                                   ctypes.c_void_p(int(out_ptr) if out_ptr else 0), _stream_handle(stream)))
+
+
+def _deriv_args(basis, centers, charges, out):
+    import torch
+    if not (centers.is_cuda and charges.is_cuda):
+        raise ValueError("centers and charges must be CUDA tensors")
+    if centers.dtype != torch.float64 or charges.dtype != torch.float64:
+        raise ValueError("centers and charges must be float64")
+    centers = centers.contiguous()
+    charges = charges.contiguous()
+    shape = (3, basis.nbf, basis.nbf)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=centers.device)
+    if not out.is_contiguous() or out.dtype != torch.float64 or tuple(out.shape) != shape:
+        raise ValueError(f"out must be a contiguous float64 {list(shape)} tensor")
+    n = centers.shape[0] if centers.numel() else 0
+    return centers, charges, out, n
+
+
+def nuclear_attraction_deriv(basis: Basis, centers, charges, out=None, stream=None):
+    """dV/d(bra centre): [3, nbf, nbf] FP64 device tensor, out[X][a][b] = d V_ab / d A_X with A the centre of
+    a's shell (b's held fixed); the derivative by b's centre is out[X][b][a]."""
+    centers, charges, out, n = _deriv_args(basis, centers, charges, out)
+    shgo_nuclear_attraction_deriv(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
+                                  out.data_ptr(), stream)
+    return out
+
+
+def nuclear_field(basis: Basis, centers, charges, out=None, stream=None):
+    """Field integrals sum_C Z_C dV/dC_X: [3, nbf, nbf] FP64 device tensor (symmetric in a, b)."""
+    centers, charges, out, n = _deriv_args(basis, centers, charges, out)
+    shgo_nuclear_field(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
+                       out.data_ptr(), stream)
+    return out
+
+
+def field_matrices(basis: Basis, centers, stream=None):
+    """Per-nucleus field-integral matrices: [n, 3, nbf, nbf], entry C = d/dC_X <a|1/|r - C||b> (unit charge),
+    one shgo_nuclear_field call per nucleus."""
+    import torch
+    centers = centers.contiguous()
+    n = centers.shape[0] if centers.numel() else 0
+    out = torch.empty((n, 3, basis.nbf, basis.nbf), dtype=torch.float64, device=centers.device)
+    one = torch.ones(1, dtype=torch.float64, device=centers.device)
+    for k in range(n):
+        nuclear_field(basis, centers[k:k + 1], one, out=out[k], stream=stream)
+    return out
+
+
+def host_deriv_transform(lam: int, comp: int, p: float, r1):
+    """The derivative steps on one coupling block of order lam + 1 (host copy of the device tables): returns
+    (raised, field) in the layout of order lam, raised = the block of x_c times the one-centre integrand,
+    field = the block of d_c of it (exponent p)."""
+    r1 = np.ascontiguousarray(r1, dtype=np.float64)
+    n = (lam + 1) * (lam + 2) * (lam + 3) // 6
+    raised = np.zeros(n)
+    field = np.zeros(n)
+    _check(_lib.shgo_host_deriv_transform(int(lam), int(comp), float(p), _ptr(r1, ctypes.c_double),
+                                          _ptr(raised, ctypes.c_double), _ptr(field, ctypes.c_double)))
+    return raised, field
+
+
+def host_deriv_lowering(l: int, comp: int, m: int) -> np.ndarray:
+    """Coefficients of d_c S_lm = sum_M' w[M' + l - 1] S_{l-1,M'} (host copy of the device table)."""
+    w = np.zeros(max(2 * l - 1, 1))
+    _check(_lib.shgo_host_deriv_lowering(int(l), int(comp), int(m), _ptr(w, ctypes.c_double)))
+    return w[:2 * l - 1]
 
 
 def shgo_overlap(basis, out_ptr, stream=None):

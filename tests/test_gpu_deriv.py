@@ -1,0 +1,135 @@
+"""Derivative integrals against the oracle: dV/d(basis-function centre) and the field integrals of the nuclei.
+
+The oracle differentiates Cartesian Gaussians directly (raised and lowered exponents, McMurchie-Davidson);
+the library differentiates the Gaussian product and raises the one-centre integral of Eq. 12 by one order
+(Eq. 3's l +- 1).  Bar per element: |got - ref| <= 1e-11 |ref| + 1e-13 max|ref| over the component's matrix
+(derivative elements mix terms of opposite sign whose size is set by the largest elements, so the absolute
+part scales with the matrix)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_16245_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def shgo():
+    from paper_2404_16245_gb300 import shgo as mod
+    return mod
+
+
+def check(got, ref, what):
+    for X in range(3):
+        scale = max(float(np.max(np.abs(ref[X]))), 1e-300)
+        excess = np.abs(got[X] - ref[X]) - (1e-11 * np.abs(ref[X]) + 1e-13 * scale)
+        if np.any(excess > 0):
+            i = np.unravel_index(np.argmax(excess), excess.shape)
+            raise AssertionError(f"{what}[{X}]: {int(np.sum(excess > 0))} out of tolerance; worst at {i}: "
+                                 f"got {got[X][i]!r} ref {ref[X][i]!r} (scale {scale:.3e})")
+
+
+def run(shgo, basis, C, Z, field=False):
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    fn = shgo.nuclear_field if field else shgo.nuclear_attraction_deriv
+    out = fn(B, Cd, Zd).cpu().numpy()
+    B.close()
+    return out
+
+
+def every_class_basis(seed, max_prim=2):
+    ls = list(range(9)) * 2
+    rng = np.random.default_rng(seed)
+    sites = rng.uniform(0, 2.5, (3, 3))
+    exps = np.exp(rng.uniform(np.log(0.2), np.log(8.0), len(ls) * max_prim))
+    return W.make_basis(ls, [max_prim] * len(ls), exps, rng.uniform(0.2, 1, len(ls) * max_prim),
+                        [sites[i % 3] for i in range(len(ls))]), sites
+
+
+def test_deriv_small_contracted_basis(shgo):
+    basis = W.random_basis(61, 12, 4, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0, n_sites=5)
+    C, Z = W.random_nuclei(62, 7, box=3.0)
+    C[0] = np.asarray(basis["xyz"]).reshape(-1, 3)[0]  # a nucleus on a basis centre
+    got = run(shgo, basis, C, Z)
+    check(got, oracle.nuclear_deriv(basis, C, Z, threads=THREADS, precision="ld"), "dV/dA")
+
+
+def test_deriv_every_class_up_to_l8(shgo):
+    basis, sites = every_class_basis(63)
+    rng = np.random.default_rng(64)
+    C = np.vstack([rng.uniform(-1.0, 3.5, (4, 3)), sites[1:2]])
+    Z = rng.uniform(0.5, 8.0, len(C))
+    got = run(shgo, basis, C, Z)
+    check(got, oracle.nuclear_deriv(basis, C, Z, threads=THREADS, precision="ld"), "dV/dA (l <= 8)")
+
+
+def test_field_every_class_up_to_l8(shgo):
+    basis, sites = every_class_basis(65)
+    rng = np.random.default_rng(66)
+    C = np.vstack([rng.uniform(-1.0, 3.5, (4, 3)), sites[2:3]])
+    Z = rng.uniform(0.5, 8.0, len(C))
+    got = run(shgo, basis, C, Z, field=True)
+    check(got, oracle.nuclear_field(basis, C, Z, threads=THREADS, precision="ld"), "field (l <= 8)")
+    for X in range(3):
+        assert np.array_equal(got[X], got[X].T)
+
+
+def test_field_small_contracted_basis_and_per_nucleus(shgo):
+    basis = W.random_basis(67, 10, 5, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=40.0, n_sites=4)
+    C, Z = W.random_nuclei(68, 5, box=3.0)
+    got = run(shgo, basis, C, Z, field=True)
+    check(got, oracle.nuclear_field(basis, C, Z, threads=THREADS, precision="ld"), "field")
+    B = shgo.Basis(basis)
+    per = shgo.field_matrices(B, torch.tensor(C, device="cuda")).cpu().numpy()
+    B.close()
+    for k in range(len(Z)):
+        check(per[k], oracle.nuclear_field(basis, C[k:k + 1], np.ones(1), threads=THREADS, precision="ld"),
+              f"field of nucleus {k}")
+    total = np.einsum("k,kxab->xab", Z, per)
+    assert np.max(np.abs(total - got)) <= 1e-12 * np.max(np.abs(got))
+
+
+def test_translational_invariance_on_the_device(shgo):
+    # moving the basis and the nuclei together leaves V unchanged: D + D^T + field = 0
+    basis = W.random_basis(69, 14, 6, max_prim=2, box=4.0, exp_lo=0.1, exp_hi=20.0, n_sites=5)
+    C, Z = W.random_nuclei(70, 9, box=4.0)
+    D = run(shgo, basis, C, Z)
+    F = run(shgo, basis, C, Z, field=True)
+    for X in range(3):
+        assert np.max(np.abs(D[X] + D[X].T + F[X])) <= 1e-12 * np.max(np.abs(D[X]))
+
+
+def test_deriv_degenerate_inputs(shgo):
+    basis = W.random_basis(71, 4, 2, max_prim=2, box=2.0)
+    B = shgo.Basis(basis)
+    none = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    out = torch.full((3, B.nbf, B.nbf), float("nan"), dtype=torch.float64, device="cuda")
+    shgo.nuclear_attraction_deriv(B, none, torch.zeros(0, dtype=torch.float64, device="cuda"), out=out)
+    assert torch.count_nonzero(out).item() == 0
+    shgo.nuclear_field(B, none, torch.zeros(0, dtype=torch.float64, device="cuda"), out=out)
+    assert torch.count_nonzero(out).item() == 0
+    B.close()
+    # one s shell pair on one centre with the nucleus there: stationary by symmetry
+    s = W.make_basis([0, 0], [1, 1], [0.8, 2.0], [1.0, 1.0], [np.zeros(3), np.zeros(3)])
+    got = run(shgo, s, np.zeros((1, 3)), np.ones(1))
+    assert np.max(np.abs(got)) <= 1e-14
+
+
+def test_deriv_repeatable(shgo):
+    # fixed summation order: two calls give the same bits
+    basis = W.random_basis(72, 10, 5, max_prim=2, box=3.0, n_sites=4)
+    C, Z = W.random_nuclei(73, 6, box=3.0)
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    a = shgo.nuclear_attraction_deriv(B, Cd, Zd).cpu().numpy()
+    b = shgo.nuclear_attraction_deriv(B, Cd, Zd).cpu().numpy()
+    B.close()
+    assert np.array_equal(a, b)

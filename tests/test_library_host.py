@@ -110,7 +110,7 @@ def test_every_entry_point_rejects_null_handles_without_gpu_work():
     lib.shgo_mlp_free(N)
 
 
-@pytest.mark.parametrize("l", range(0, 17))
+@pytest.mark.parametrize("l", range(0, 18))
 def test_host_harmonic_recursion_matches_scipy(l):
     rng = np.random.default_rng(l)
     pts = rng.normal(size=(30, 3))
@@ -435,3 +435,67 @@ def test_option_flags_are_validated_on_the_host():
     assert st == 1 and "batch" in shgo._lib.shgo_last_error().decode()
     with pytest.raises(shgo.ShgoError):
         shgo.shgo_sparse_layout(0)
+
+
+def _r_layout(lam):
+    return [(L, M, k) for L in range(lam + 1) for M in range(-L, L + 1) for k in range((lam - L) // 2 + 1)]
+
+
+def _one_centre_values(lam, x):
+    # r^{2k} S_LM(x) for every entry of the layout of order lam (scipy's harmonics)
+    r2 = float(np.dot(x, x))
+    S = {L: RM.solid_harmonics_scipy(L, x[None, :])[0] for L in range(lam + 1)}
+    return np.array([r2 ** k * S[L][M + L] for (L, M, k) in _r_layout(lam)])
+
+
+@pytest.mark.parametrize("lam", [0, 1, 4, 9, 16])
+def test_deriv_transform_raise_and_field(lam):
+    # the tables behind the derivative integrals, applied to the integrand itself at a point: raising must
+    # give x_c r^{2k} S_LM, the field step d/dx_c [r^{2k} S_LM e^{-p r^2}] e^{p r^2} (fourth-order differences)
+    rng = np.random.default_rng(100 + lam)
+    p = 0.7
+    for _ in range(3):
+        x = rng.uniform(-1.2, 1.2, 3)
+        r1 = _one_centre_values(lam + 1, x)
+        base = _one_centre_values(lam, x)
+        lay = _r_layout(lam)
+        for c in range(3):
+            raised, field = shgo.host_deriv_transform(lam, c, p, r1)
+            assert np.allclose(raised, x[c] * base, rtol=1e-12, atol=1e-12 * np.max(np.abs(base)))
+            h = 1e-4
+
+            def f(t):
+                y = x.copy()
+                y[c] += t
+                return _one_centre_values(lam, y) * np.exp(-p * float(np.dot(y, y)))
+
+            fd = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h) * np.exp(p * float(np.dot(x, x)))
+            scale = np.max(np.abs(fd))
+            assert np.max(np.abs(field - fd)) <= 1e-8 * scale, (lam, c, lay[int(np.argmax(np.abs(field - fd)))])
+
+
+@pytest.mark.parametrize("l", [1, 2, 5, 8])
+def test_deriv_lowering_is_the_gradient_of_the_harmonic(l):
+    rng = np.random.default_rng(200 + l)
+    x = rng.normal(size=3)
+    Sl1 = RM.solid_harmonics_scipy(l - 1, x[None, :])[0]
+    h = 1e-5
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        S = lambda y: RM.solid_harmonics_scipy(l, y[None, :])[0]  # noqa: E731
+        fd = (8 * (S(x + e) - S(x - e)) - (S(x + 2 * e) - S(x - 2 * e))) / (12 * h)
+        for m in range(-l, l + 1):
+            w = shgo.host_deriv_lowering(l, c, m)
+            assert abs(float(w @ Sl1) - fd[m + l]) <= 1e-8 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_deriv_entry_points_reject_bad_arguments():
+    import ctypes
+    c = shgo.shgo_centers(0, None)
+    for fn in (shgo._lib.shgo_nuclear_attraction_deriv, shgo._lib.shgo_nuclear_field):
+        assert fn(None, ctypes.byref(c), None, None, None) == 1  # SHGO_ERR_INVALID_ARG
+    with pytest.raises(shgo.ShgoError):
+        shgo.host_deriv_transform(17, 0, 1.0, np.zeros(2000))
+    with pytest.raises(shgo.ShgoError):
+        shgo.host_deriv_lowering(0, 0, 0)
