@@ -636,6 +636,69 @@ def run_esp(args) -> int:
     return 0
 
 
+def run_deriv(args) -> int:
+    """Derivative integrals of the benchmark molecule (32 atoms, one uncontracted shell per l = 0..6 per atom):
+    one step = dV/d(basis-function centres) for all nbf^2 elements and three components (the ket's derivative
+    is the transposed element), then separately the field integrals sum_C Z_C dV/dC.  V itself is timed in
+    the same run for the ratio.  L2 flushed (256 MiB write outside the events) before every step."""
+    import torch
+
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    b, C, Z = W.config2()
+    B = shgo.Basis(b)
+    Cd, Zd = torch.tensor(C, device=dev), torch.tensor(Z, device=dev)
+    V = torch.empty((B.nbf, B.nbf), dtype=torch.float64, device=dev)
+    D = torch.empty((3, B.nbf, B.nbf), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)
+    steps = max(1, min(args.steps, 200))
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+
+    peak = measure_fma_peak("fp64", stream)["tflops"]
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms_v = timed(lambda: shgo.nuclear_attraction(B, Cd, Zd, out=V, stream=stream))
+    ms_d = timed(lambda: shgo.nuclear_attraction_deriv(B, Cd, Zd, out=D, stream=stream))
+    ms_f = timed(lambda: shgo.nuclear_field(B, Cd, Zd, out=D, stream=stream))
+    clocks = sampler.stop()
+    fd = shgo.shgo_basis_deriv_flops(B.handle, len(Z), False)
+    ff = shgo.shgo_basis_deriv_flops(B.handle, len(Z), True)
+    triples = float(B.npairs) * len(Z)
+    ach_d = float(fd.sum()) / (ms_d / 1e3) / 1e12
+    ach_f = float(ff.sum()) / (ms_f / 1e3) / 1e12
+    line = {"metric": "derivative shell-triples/s", "value": triples / (ms_d / 1e3), "unit": "shell-triples/s",
+            "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms_d, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dV/dA, dV/dB of the high-l benchmark basis: {len(b['l'])} shells, {B.nbf} "
+                                   f"functions, {len(Z)} nuclei", "shell_pairs": B.npairs,
+                       "l2": "flushed between steps (256 MiB write, outside step events)"},
+            "v_ms": ms_v, "deriv_over_v": ms_d / ms_v,
+            "field": {"ms_per_step": ms_f, "shell_triples_per_s": triples / (ms_f / 1e3), "over_v": ms_f / ms_v,
+                      "model_tflop": float(ff.sum()) / 1e12, "achieved_tflops": ach_f, "frac": ach_f / peak},
+            "roofline": {"bound": "fp64", "kernel": "whole derivative call (coupling at la + lb + 1, variant passes, "
+                                                    "combine)", "achieved": ach_d, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach_d / peak, "traffic": None, "model_tflop": [float(fd[0]) / 1e12, float(fd[1]) / 1e12],
+                         "peak_source": "shgo_measure_fma_rate in this run (of measured)"},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    B.close()
+    return 0
+
+
 def _cluster(seed: int, n_atoms: int):
     """Screening workload: atoms uniform at 0.1 atoms/bohr^3, Z ~ U{1..9}, 4s3p2d1f on every atom
     with 1..6 primitives, exponents log-uniform [0.05, 5000]."""
@@ -1172,7 +1235,8 @@ def run_peaks(args) -> int:
 
 def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
     """Small fixed case for ncu captures: one warm and one measured V of the benchmark workload
-    (highl) or of the first molecule of the batched workload (batched)."""
+    (highl) or of the first molecule of the batched workload (batched), or of the benchmark workload's
+    derivative integrals (deriv) or field integrals (field)."""
     import torch
 
     from paper_2404_16245_gb300 import shgo
@@ -1185,7 +1249,12 @@ def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
     Cd = torch.tensor(C, device="cuda")
     Zd = torch.tensor(Z, device="cuda")
     for _ in range(2):
-        V = shgo.nuclear_attraction(B, Cd, Zd)
+        if case == "deriv":
+            V = shgo.nuclear_attraction_deriv(B, Cd, Zd)
+        elif case == "field":
+            V = shgo.nuclear_field(B, Cd, Zd)
+        else:
+            V = shgo.nuclear_attraction(B, Cd, Zd)
     torch.cuda.synchronize()
     print("profile case ok", tuple(V.shape))
     B.close()
@@ -1194,7 +1263,7 @@ def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", nargs="?", const="highl", choices=["highl", "batched"],
+    ap.add_argument("--profile-case", nargs="?", const="highl", choices=["highl", "batched", "deriv", "field"],
                     help="one warm + one measured call, for ncu (the benchmark molecule or one batched molecule)")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
@@ -1202,7 +1271,8 @@ def main():
                     help="triples per (la, lb) class also checked against the double oracle")
     ap.add_argument("--sweep-ext", type=int, default=20,
                     help="triples per (la, lb) class also checked against the extended-precision oracle")
-    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri", "peaks"],
+    ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri", "peaks",
+                                                          "deriv"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
     ap.add_argument("--points", type=int, default=100000, help="points of the potential workload")
@@ -1243,6 +1313,8 @@ def main():
         return run_screened(args)
     if args.workload == "esp":
         return run_esp(args)
+    if args.workload == "deriv":
+        return run_deriv(args)
     if args.workload == "coulomb2c":
         return run_coulomb2c(args)
     if args.workload == "eri":

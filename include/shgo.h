@@ -146,6 +146,11 @@ shgo_status shgo_nuclear_attraction_timed(const shgo_basis* basis, const shgo_ce
  * triples (primitive pairs x nuclei). */
 shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double* flops, double* triples);
 
+/* The same algorithmic FP64 model for shgo_nuclear_attraction_deriv (field = 0) or shgo_nuclear_field
+ * (field = 1) of a single basis with n_centers nuclei: flops[0] the coupling kernel at la + lb + 1,
+ * flops[1] the variant pair passes (raising, Gaunt coupling, translation, rotation) and the combine. */
+shgo_status shgo_basis_deriv_flops(const shgo_basis* basis, int64_t n_centers, int32_t field, double* flops);
+
 /* Number of kernel launches one shgo_nuclear_attraction call on this basis makes (n > 0). */
 int64_t shgo_basis_launches(const shgo_basis* basis);
 

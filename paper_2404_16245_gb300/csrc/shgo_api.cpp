@@ -626,6 +626,52 @@ shgo_status ensure_live_counts(const shgo_basis* cb, std::string* err) {
   return st;
 }
 
+// Algorithmic FP64 operations of the coupling kernel of order lam per primitive triple: geometry 9; |d|^2, T,
+// 1/|d|, |d| and the unit vector 11; Boys: Horner over kBoysK Taylor terms (5 per term), exp 1, downward
+// recursion 3 per order; Z |d|^n F_n 2 Lambda + 1; (p |d|)^j / j! 2 per j; the beta running sums 2 per entry
+// beyond the first of each L; the unit-vector harmonic recursion 6 l + 5 for level l + 1; the nucleus sum
+// 2 per R entry.
+double coupling_per_triple(int lam) {
+  const double nB = n_beta(lam), nR = n_r(lam);
+  double s_lm = 0.0;
+  for (int l = 1; l < lam; ++l) s_lm += 6.0 * l + 5.0;
+  const double boys = 5.0 * kBoysK + 1 + 3.0 * lam;
+  return 9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
+}
+
+// The Gaunt coupling of one primitive pair into a (lbra, lket) block: 2 per nonzero coefficient of the class
+// stored as (max, min).
+double gaunt_flops(const Tables& t, int lbra, int lket) {
+  return 2.0 * t.g_nnz[class_id(std::max(lbra, lket), std::min(lbra, lket))];
+}
+
+// Per shell pair: the translation of a (lbra, lket) block along the pair axis (diagonal in m) and its
+// rotation back to the molecular frame.
+double block_flops(int lbra, int lket) {
+  const int nWa = (lbra + 1) * (lbra + 1);
+  const double na = 2 * lbra + 1, nb = 2 * lket + 1;
+  double zt = 0, vt = 0;
+  for (int mb = -lket; mb <= lket; ++mb) zt += 2.0 * (lket - std::abs(mb) + 1) * nWa;
+  for (int ma = -lbra; ma <= lbra; ++ma) vt += 2.0 * (lbra - std::abs(ma) + 1) * nb;
+  return zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb;
+}
+
+// One pass of the pair kernel over a (lbra, lket) block: per primitive pair the Gaunt coupling and 4 per W
+// entry (the primitive factor and the accumulation); per shell pair the translation and rotation.
+double pair_pass_flops(const Tables& t, int lbra, int lket, double live_pp, double live_pairs) {
+  const double nW = (double)(lbra + 1) * (lbra + 1) * (lket + 1) * (lket + 1);
+  return (gaunt_flops(t, lbra, lket) + 4.0 * nW) * live_pp + block_flops(lbra, lket) * live_pairs;
+}
+
+// Nonzero terms of the raising (which = 0) or the p-free field table (which = 1) of order lam, all components.
+double deriv_table_nnz(const Tables& t, int lam, int which) {
+  const std::vector<GTerm>& v = which == 0 ? t.d_raise : t.d_field;
+  double n = 0;
+  const size_t b = (size_t)t.d_xoff[lam] * 3 * kDerivSlots, e = (size_t)t.d_xoff[lam + 1] * 3 * kDerivSlots;
+  for (size_t i = b; i < e; ++i) n += v[i].coef != 0.0 ? 1.0 : 0.0;
+  return n;
+}
+
 void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* out) {
   const Tables& t = tables_host();
   const ClassWork& w = basis->work[wi];
@@ -636,27 +682,9 @@ void class_model(const shgo_basis* basis, size_t wi, int64_t n_centers, double* 
   const double live_pp = (double)basis->live_pp[wi], live_pairs = (double)basis->live_pairs[wi];
   const double pp_cent = basis->batch ? basis->live_cent[wi] : live_pp * (double)n_centers;
   const int la = w.la, lb = w.lb, lam = la + lb;
-  const double nB = n_beta(lam), nR = n_r(lam);
-  // per primitive triple: geometry 9; |d|^2, T, 1/|d|, |d| and the unit vector 11; Boys: Horner over
-  // kBoysK Taylor terms (5 per term), exp 1, downward recursion 3 per order; Z |d|^n F_n 2 Lambda + 1;
-  // (p |d|)^j / j! 2 per j; the beta running sums 2 per entry beyond the first of each L; the
-  // unit-vector harmonic recursion 6 l + 5 for level l + 1; the nucleus sum 2 per R entry
-  double s_lm = 0.0;
-  for (int l = 1; l < lam; ++l) s_lm += 6.0 * l + 5.0;
-  const double boys = 5.0 * kBoysK + 1 + 3.0 * lam;
-  const double per_triple =
-      9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
-  const double f0 = per_triple * pp_cent + 2.0 * nR * live_pp;
-  // per primitive pair: coupling
-  const int nWa = (la + 1) * (la + 1), nWb = (lb + 1) * (lb + 1), nW = nWa * nWb;
-  double f1 = (2.0 * t.g_nnz[class_id(la, lb)] + 4.0 * nW) * live_pp;
-  // per shell pair: the translation along the pair axis (diagonal in m) and the rotation of the
-  // block back to the molecular frame (the rotation matrices themselves are built once per basis)
+  const double f0 = coupling_per_triple(lam) * pp_cent + 2.0 * n_r(lam) * live_pp;
+  const double f1 = pair_pass_flops(t, la, lb, live_pp, live_pairs);
   const double na = 2 * la + 1, nb = 2 * lb + 1;
-  double zt = 0, vt = 0;
-  for (int mb = -lb; mb <= lb; ++mb) zt += 2.0 * (lb - std::abs(mb) + 1) * nWa;
-  for (int ma = -la; ma <= la; ++ma) vt += 2.0 * (la - std::abs(ma) + 1) * nb;
-  f1 += (zt + vt + 2.0 * na * nb * nb + 2.0 * na * na * nb) * live_pairs;
   out[0] = pair_cent;
   out[1] = 0;
   out[2] = f0;
@@ -1108,6 +1136,41 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
     flops[1] += c[3];
     triples[0] += c[0];
     triples[1] += c[4];
+  }
+  return SHGO_OK;
+}
+
+shgo_status shgo_basis_deriv_flops(const shgo_basis* basis, int64_t n_centers, int32_t field, double* flops) {
+  if (!basis || !flops || n_centers < 0 || basis->batch) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  {
+    std::string err;
+    const shgo_status st = ensure_live_counts(basis, &err);
+    if (st != SHGO_OK) return fail(st, err);
+  }
+  const Tables& t = tables_host();
+  flops[0] = flops[1] = 0;
+  for (size_t wi = 0; wi < basis->work.size(); ++wi) {
+    const ClassWork& w = basis->work[wi];
+    const int la = w.la, lb = w.lb, lam = la + lb;
+    const double live_pp = (double)basis->live_pp[wi], live_pairs = (double)basis->live_pairs[wi];
+    flops[0] += coupling_per_triple(lam + 1) * live_pp * (double)n_centers + 2.0 * n_r(lam + 1) * live_pp;
+    const double na = 2 * la + 1, nb = 2 * lb + 1;
+    if (field) {
+      // three differentiated blocks (raising, p-free terms, one combining FMA per entry), then Q^T per entry
+      const double tr = 2.0 * (deriv_table_nnz(t, lam, 0) + deriv_table_nnz(t, lam, 1)) + 2.0 * 3 * n_r(lam);
+      flops[1] += tr * live_pp + 3.0 * pair_pass_flops(t, la, lb, live_pp, live_pairs) + 18.0 * na * nb * w.npairs;
+      continue;
+    }
+    // per primitive pair: the raising of the three axes; the Gaunt coupling of the three raised blocks and of
+    // the unraised one (the pair-axis offsets of both centres on z); per W entry and centre 4 for x and y and
+    // 6 for z.  Per shell pair: translation and rotation of the six raised blocks; then the lowered classes.
+    const double nW = (double)(la + 1) * (la + 1) * (lb + 1) * (lb + 1);
+    flops[1] += (2.0 * deriv_table_nnz(t, lam, 0) + 4.0 * gaunt_flops(t, la, lb) + 2.0 * 14.0 * nW) * live_pp +
+                6.0 * block_flops(la, lb) * live_pairs;
+    if (la > 0) flops[1] += pair_pass_flops(t, la - 1, lb, live_pp, live_pairs);
+    if (lb > 0) flops[1] += pair_pass_flops(t, la, lb - 1, live_pp, live_pairs);
+    // combine: per element and component 6 (the frame rotation) + 2 (2l - 1) (lowered), for both orientations
+    flops[1] += 3.0 * na * nb * w.npairs * (2.0 * 6.0 + 2.0 * (2 * la - 1) + 2.0 * (2 * lb - 1));
   }
   return SHGO_OK;
 }

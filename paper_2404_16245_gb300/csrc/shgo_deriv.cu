@@ -8,12 +8,13 @@
 // 2 alpha (r - A)_X exp(...), and r - A = (r - P) + (beta / p)(B - A), so
 //   d/dA_X [a b] = -(d_X S_la)(r - A) [...]  -  2 mu (A - B)_X a b  +  2 alpha (r - P)_X a b.
 // Term 1 is a V block of the lowered class (la - 1, lb), combined with
-// d_X S_la,ma = (2 la + 1) sum_M G(1 m(X), la ma; la - 1 M) S_{la-1,M}.  Term 2 is V with every primitive pair
-// weighted by mu.  Term 3 multiplies the one-centre integrand of Eq. 12 by a Cartesian component of r - P,
-// which couples S_LM to L + 1 and (with r^2) to L - 1 as the product S_1 S_L of Eq. 3:
+// d_X S_la,ma = (2 la + 1) sum_M G(1 m(X), la ma; la - 1 M) S_{la-1,M}.  Terms 2 and 3 together are
+// 2 alpha (r - A)_X a b.  In the pair frame (z along B - A) r - A = (r - P) + |P - A| z, so component c of
+// them multiplies the one-centre integrand of Eq. 12 by 2 alpha (x_c + |P - A| delta_cz); x_c couples S_LM to
+// L + 1 and (with r^2) to L - 1 as the product S_1 S_L of Eq. 3:
 //   r^{2k} x_c S_LM = sum G(1 m(c), L M; L+1 M') r^{2k} S_{L+1,M'} + sum G(1 m(c), L M; L-1 M') r^{2k+2} S_{L-1,M'},
 // so it reads the one-centre integrals R'[L, M, k] up to Lambda + 1 = la + lb + 1.  B is the same with beta,
-// the opposite sign of term 2 and the lowered class (la, lb - 1).  The field integrals move the nucleus: the
+// r - B = (r - P) - |P - B| z and the lowered class (la, lb - 1).  The field integrals move the nucleus: the
 // integral of f(r - P) / |r - C| has d/dC_X equal to the integral of (d_X f)(r - P) / |r - C|, and
 // d_c [r^{2k} S_LM e^{-p r^2}] is again a sum of R' terms of order Lambda + 1.
 //
@@ -21,10 +22,11 @@
 // component X is sum_c Q[c][X] (component c), Q the frame rotation, applied to the rotated blocks.
 //
 // Launches per class, on the pool streams: the FP64 coupling kernel at Lambda + 1 (one block per primitive
-// pair), k_deriv_block (one block per shell pair and variant, blockIdx.y: the mu-weighted block, the blocks
-// raised along c weighted by 2 alpha or 2 beta, the lowered classes, or the field blocks, each rotated to the
-// molecular frame into a scratch array) and k_deriv_combine, which adds a shell pair's variants in a fixed
-// order into the output (no atomics: the result does not depend on the schedule).
+// pair), k_deriv_block (one block per shell pair and variant, blockIdx.y: the blocks raised along pair-frame
+// axis c, weighted by 2 alpha and by 2 beta in one pass over the Gaunt program where shared memory allows, the
+// lowered classes, or the field blocks, each rotated to the molecular frame into a scratch array) and
+// k_deriv_combine, which adds a shell pair's blocks in a fixed order into the output (no atomics: the result
+// does not depend on the schedule).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,37 +40,43 @@ namespace shgo {
 
 namespace {
 
-// Variants of k_deriv_block.
-constexpr int kKindMu = 0;      // V with primitive-pair weight mu
-constexpr int kKindRaiseA = 1;  // .. 3: (r - P)_c raised, weight 2 alpha
-constexpr int kKindRaiseB = 4;  // .. 6: (r - P)_c raised, weight 2 beta
-constexpr int kKindLowA = 7;    // class (la - 1, lb)
-constexpr int kKindLowB = 8;    // class (la, lb - 1)
-constexpr int kKindField = 9;   // .. 11: d_c of the one-centre integrand
-constexpr int kKinds = 12;
+// Variants of k_deriv_block (blockIdx.y selects one from DerivArgs::kinds).
+constexpr int kKindAB = 0;      // .. 2: raised along axis c, weights 2 alpha and 2 beta (two accumulators)
+constexpr int kKindA = 3;       // .. 5: the same, 2 alpha only
+constexpr int kKindB = 6;       // .. 8: the same, 2 beta only
+constexpr int kKindLowA = 9;    // class (la - 1, lb)
+constexpr int kKindLowB = 10;   // class (la, lb - 1)
+constexpr int kKindField = 11;  // .. 13: d_c of the one-centre integrand
+// Blocks of a shell pair's scratch, each (2 la + 1) x (2 lb + 1): A's raised blocks (3 pair-frame axes), B's,
+// the lowered classes' terms for A and for B (3 molecular axes each), the field (3 pair-frame axes).
+constexpr int kSlotA = 0, kSlotB = 3, kSlotLowA = 6, kSlotLowB = 9, kSlotField = 12, kSlots = 15;
 
 __host__ __device__ inline void deriv_shape(int la, int lb, int kind, int& lbra, int& lket) {
   lbra = kind == kKindLowA ? la - 1 : la;
   lket = kind == kKindLowB ? lb - 1 : lb;
 }
+__host__ __device__ inline bool kind_raised(int kind) { return kind < kKindLowA; }
+__host__ __device__ inline int kind_comp(int kind) { return kind >= kKindField ? kind - kKindField : kind % 3; }
 
-// Shared memory of one k_deriv_block variant (doubles, see the carve-up in the kernel).
+// Shared memory of one k_deriv_block variant (doubles, the carve-up in the kernel).
 __host__ __device__ inline size_t deriv_block_doubles(int la, int lb, int kind) {
   int lbra, lket;
   deriv_shape(la, lb, kind, lbra, lket);
   const int lhi = lbra > lket ? lbra : lket, llo = lbra > lket ? lket : lbra;
   const int na = 2 * lbra + 1, nb = 2 * lket + 1;
-  return (size_t)(lhi + 1) * (lhi + 1) * w_stride(llo) + na * na + nb * nb + (lbra + 1) * na + (lket + 1) * nb +
-         (size_t)(lbra + 1) * (lbra + 1) * nb + 2 * na * nb + (lhi + 1) * (llo + 1) + n_r(la + lb + 1) +
-         n_r(lbra + lket) + 8 + 16;
+  const int nacc = kind < kKindA ? 2 : 1;
+  const bool zoff = kind_raised(kind) && kind_comp(kind) == 2;
+  return (size_t)nacc * (lhi + 1) * (lhi + 1) * w_stride(llo) + na * na + nb * nb + (lbra + 1) * na +
+         (lket + 1) * nb + (size_t)(lbra + 1) * (lbra + 1) * nb + 2 * na * nb + 2 * (lhi + 1) * (llo + 1) +
+         n_r(la + lb + 1) + n_r(lbra + lket) + (zoff ? n_r(lbra + lket) : 0) + 16 + 16;
 }
 
 struct DerivArgs {
   int la = 0, lb = 0, npairs = 0, pair_base = 0;
   int64_t pp_base = 0, rbase = 0;  // the class's first primitive pair; its coupling blocks at r1buf + rbase
   int nkind = 0;
-  int kinds[9] = {};
-  int64_t voff[kKinds] = {};  // offset of each variant's block in a shell pair's scratch (doubles)
+  int kinds[8] = {};
+  int64_t soff[kSlots] = {};  // offset of each block in a shell pair's scratch (doubles)
   int64_t per_pair = 0;       // scratch doubles per shell pair
   double* scratch = nullptr;  // the class's scratch
   const int* pair_a = nullptr;
@@ -90,11 +98,52 @@ struct DerivArgs {
   const int* mapm = nullptr;       // Lambda - 1 layout -> Lambda + 1 layout
   const GTerm* raise = nullptr;    // Tables::d_raise of this Lambda
   const GTerm* fconst = nullptr;   // Tables::d_field of this Lambda
+  const double* low_a = nullptr;   // Tables::d_low of la (nullptr for la = 0)
+  const double* low_b = nullptr;   // of lb
   const PPData* ppd = nullptr;
   const double* r1buf = nullptr;
 };
 
-__global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
+// Gaunt coupling of one primitive pair into W0 (and W1): rows of one warp form one group (equal trip counts,
+// coalesced term loads).  acc = sum G Rv[.]; with ZOFF also acz = sum G Rz[.] (the unraised block), and the
+// row adds fab0 (acc + s0 acz) to W0 and, with TWO, fab1 (acc + s1 acz) to W1.
+template <bool ZOFF, bool TWO>
+__device__ __forceinline__ void gaunt_pass(int nrp, const int* __restrict__ rowinfo, const int* __restrict__ grp,
+                                           const GTerm* __restrict__ gterms, const double* Rv, const double* Rz,
+                                           const double* fab0, const double* fab1, int lcols, double s0, double s1,
+                                           double* W0, double* W1) {
+  for (int r = threadIdx.x; r < nrp; r += blockDim.x) {
+    const int info = rowinfo[r];
+    const int gi = r >> 5, K = grp[2 * gi + 1];
+    const GTerm* tp = gterms + grp[2 * gi] + (r & 31);
+    double acc = 0.0, acc1 = 0.0, acz = 0.0, acz1 = 0.0;
+    int j = 0;
+    for (; j + 1 < K; j += 2) {
+      const GTerm g0 = tp[32 * j], g1 = tp[32 * j + 32];
+      acc = fma(g0.coef, Rv[g0.ridx], acc);
+      acc1 = fma(g1.coef, Rv[g1.ridx], acc1);
+      if (ZOFF) {
+        acz = fma(g0.coef, Rz[g0.ridx], acz);
+        acz1 = fma(g1.coef, Rz[g1.ridx], acz1);
+      }
+    }
+    if (j < K) {
+      const GTerm g0 = tp[32 * j];
+      acc = fma(g0.coef, Rv[g0.ridx], acc);
+      if (ZOFF) acz = fma(g0.coef, Rz[g0.ridx], acz);
+    }
+    acc += acc1;
+    acz += acz1;
+    if (info >= 0) {
+      const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
+      const int f = l1 * lcols + l2;
+      W0[e] = fma(fab0[f], ZOFF ? fma(s0, acz, acc) : acc, W0[e]);
+      if (TWO) W1[e] = fma(fab1[f], ZOFF ? fma(s1, acz, acc) : acc, W1[e]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128, 8) k_deriv_block(DerivArgs A) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int kind = A.kinds[blockIdx.y];
@@ -107,10 +156,17 @@ __global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
   const int* __restrict__ rowinfo = A.rowinfo[prog];
   const int* __restrict__ grp = A.grp[prog];
   const GTerm* __restrict__ gterms = A.gterms[prog];
-  const bool raised = kind >= kKindRaiseA && kind < kKindLowA;
-  const bool field = kind >= kKindField;
-  const int comp = field ? kind - kKindField : (kind >= kKindRaiseB ? kind - kKindRaiseB : kind - kKindRaiseA);
-  const int* __restrict__ rmap = (kind == kKindLowA || kind == kKindLowB) ? A.mapm : A.map0;
+  const bool raised = kind_raised(kind), field = kind >= kKindField;
+  const bool lowered = kind == kKindLowA || kind == kKindLowB;
+  const int NA = 2 * A.la + 1, NB = 2 * A.lb + 1;  // the class's block
+  const int comp = kind_comp(kind);
+  const bool zoff = raised && comp == 2;  // the pair-axis offsets |P - A|, |P - B| enter on z
+  const int nacc = kind < kKindA ? 2 : 1;
+  // slots written: the A (or only) block, then the B block
+  const int slot0 = kind < kKindB ? kSlotA + comp
+                                  : (kind < kKindLowA ? kSlotB + comp
+                                                      : (kind == kKindLowA ? kSlotLowA
+                                                                           : (kind == kKindLowB ? kSlotLowB : kSlotField + comp)));
   const int nR1 = n_r(A.la + A.lb + 1), nRv = n_r(lbra + lket);
   const int nWh = (lhi + 1) * (lhi + 1), nWl = (llo + 1) * (llo + 1), nW = nWh * nWl;
   const int ws = w_stride(llo), nWs = nWh * ws, nrp = (nW + 31) & ~31;
@@ -118,18 +174,20 @@ __global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
   const int na = 2 * lbra + 1, nb = 2 * lket + 1;
   const int lm = lbra > lket ? lbra : lket;
   const int nDb = lbra != lket ? nb * nb : 0;
-  double* W = smem;                          // program layout [hi (l1 m1)][lo (l2 m2)], row stride ws
-  double* Dm = W + nWs;                      // D^{lbra}(Q^T), then D^{lket}(Q^T) when they differ
+  const int nfab = (lhi + 1) * (llo + 1);
+  double* W = smem;                          // nacc arrays [hi (l1 m1)][lo (l2 m2)], row stride ws
+  double* Dm = W + nacc * nWs;               // D^{lbra}(Q^T), then D^{lket}(Q^T) when they differ
   double* tA = Dm + na * na + nb * nb;       // [l1][ma]
   double* tB = tA + (lbra + 1) * na;         // [l2][mb]
   double* Zb = tB + (lket + 1) * nb;         // [bra (l1 m1)][mb]
   double* Vp = Zb + nWa * nb;                // [ma][mb]
   double* Yb = Vp + na * nb;                 // [ma][mb]
-  double* fab = Yb + na * nb;                // [hi l][lo l]
-  double* R1 = fab + (lhi + 1) * (llo + 1);  // coupling block of Lambda + 1 of one primitive pair
+  double* fab = Yb + na * nb;                // two arrays [hi l][lo l]: the weights of W0 and W1
+  double* R1 = fab + 2 * nfab;               // coupling block of Lambda + 1 of one primitive pair
   double* Rv = R1 + nR1;                     // the variant's block in the layout its program reads
-  double* scal = Rv + nRv;                   // prefactor, beta/p, alpha/p, weight, p
-  double* dpow = scal + 8;                   // |b - a|^k
+  double* Rz = Rv + nRv;                     // zoff: the unraised block
+  double* scal = Rz + (zoff ? nRv : 0);      // prefactor, beta/p, alpha/p, 2 alpha, 2 beta, p, |P - A|, |P - B|
+  double* dpow = scal + 16;                  // |b - a|^k
   for (int w = blockIdx.x; w < A.npairs; w += gridDim.x) {
     const int pr = A.pair_base + w;
     const int a = A.pair_a[pr], b = A.pair_b[pr];
@@ -145,7 +203,7 @@ __global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
     }
     for (int e = tid; e < na * na; e += nth) Dm[e] = rd[1 + rot_doff(lbra) + e];
     for (int e = tid; e < nDb; e += nth) Dm[na * na + e] = rd[1 + rot_doff(lket) + e];
-    for (int e = tid; e < nWs; e += nth) W[e] = 0.0;
+    for (int e = tid; e < nacc * nWs; e += nth) W[e] = 0.0;
     __syncthreads();
     // translation along the pair axis (Eqs. 7-8, only nu = 0 survives), as in the V pair kernel
     for (int e = tid; e < (lbra + 1) * na; e += nth) {
@@ -165,7 +223,7 @@ __global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
     const int64_t q0 = A.pair_ppoff[pr];
     bool live = false;  // uniform over the block
     for (int ij = 0; ij < npa * npb; ++ij) {
-      __syncthreads();  // the previous primitive pair is done with R1, Rv, fab and scal
+      __syncthreads();  // the previous primitive pair is done with R1, Rv, Rz, fab and scal
       if (tid == 0) {
         const PPData pd = A.ppd[q0 + ij];
         const int pij = A.pp_ij[q0 + ij];
@@ -173,28 +231,31 @@ __global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
         scal[0] = pd.pref;
         scal[1] = pd.ra;
         scal[2] = pd.rb;
-        scal[3] = kind == kKindMu ? al * be * pd.rp
-                                  : (kind >= kKindRaiseA && kind < kKindRaiseB ? 2.0 * al
-                                                                               : (kind >= kKindRaiseB && kind < kKindLowA ? 2.0 * be : 1.0));
-        scal[4] = pd.p;
+        scal[3] = 2.0 * al;
+        scal[4] = 2.0 * be;
+        scal[5] = pd.p;
+        scal[6] = pd.ra * rd[0];   // |P - A| = (beta / p) |B - A|
+        scal[7] = -pd.rb * rd[0];  // P - B along the axis: -(alpha / p) |B - A|
       }
       __syncthreads();
       if (scal[0] == 0.0) continue;  // skipped by the coupling kernel too (uniform over the block)
       live = true;
       const double* R = A.r1buf + A.rbase + (q0 + ij - A.pp_base) * (int64_t)nR1;
       for (int e = tid; e < nR1; e += nth) R1[e] = R[e];
-      if (tid < (lhi + 1) * (llo + 1)) {
+      if (tid < nfab) {
         const int l1 = tid / (llo + 1), l2 = tid % (llo + 1);
         const int lb_i = swap ? l2 : l1, lk_i = swap ? l1 : l2;  // the bra's and the ket's l of the row
-        double v = scal[0] * scal[3];
+        double v = scal[0];
         const double ra = scal[1], rb = scal[2];
         for (int k = 0; k < lbra - lb_i; ++k) v *= ra;
         for (int k = 0; k < lket - lk_i; ++k) v *= rb;
-        fab[tid] = v;
+        // weights: 2 alpha (A, AB), 2 beta (B; the second array of AB), 1 (lowered, field)
+        fab[tid] = raised ? v * (kind >= kKindB ? scal[4] : scal[3]) : v;
+        fab[nfab + tid] = v * scal[4];
       }
       __syncthreads();
       if (raised || field) {
-        const double m2p = -2.0 * scal[4];
+        const double m2p = -2.0 * scal[5];
         for (int e = tid; e < nRv; e += nth) {
           const GTerm* tr = A.raise + ((size_t)e * 3 + comp) * kDerivSlots;
           double s = 0.0;
@@ -208,74 +269,87 @@ __global__ void __launch_bounds__(128) k_deriv_block(DerivArgs A) {
             s = fma(m2p, s, f);
           }
           Rv[e] = s;
+          if (zoff) Rz[e] = R1[A.map0[e]];
         }
       } else {
-        for (int e = tid; e < nRv; e += nth) Rv[e] = R1[rmap[e]];
+        for (int e = tid; e < nRv; e += nth) Rv[e] = R1[A.mapm[e]];
       }
       __syncthreads();
-      // Gaunt coupling: rows of one warp form one group (equal trip counts, coalesced term loads)
-      for (int r = tid; r < nrp; r += nth) {
-        const int info = rowinfo[r];
-        const int gi = r >> 5, K = grp[2 * gi + 1];
-        const GTerm* tp = gterms + grp[2 * gi] + (r & 31);
-        double acc0 = 0.0, acc1 = 0.0;
-        int j = 0;
-        for (; j + 1 < K; j += 2) {
-          const GTerm g0 = tp[32 * j], g1 = tp[32 * j + 32];
-          acc0 = fma(g0.coef, Rv[g0.ridx], acc0);
-          acc1 = fma(g1.coef, Rv[g1.ridx], acc1);
-        }
-        if (j < K) {
-          const GTerm g0 = tp[32 * j];
-          acc0 = fma(g0.coef, Rv[g0.ridx], acc0);
-        }
-        if (info >= 0) {
-          const int e = info & 0xffff, l1 = (info >> 16) & 15, l2 = (info >> 20) & 15;
-          W[e] = fma(fab[l1 * (llo + 1) + l2], acc0 + acc1, W[e]);
-        }
+      const double s0 = kind >= kKindB ? scal[7] : scal[6];
+      if (zoff) {
+        if (nacc == 2)
+          gaunt_pass<true, true>(nrp, rowinfo, grp, gterms, Rv, Rz, fab, fab + nfab, llo + 1, s0, scal[7], W, W + nWs);
+        else
+          gaunt_pass<true, false>(nrp, rowinfo, grp, gterms, Rv, Rz, fab, fab, llo + 1, s0, 0.0, W, W);
+      } else if (nacc == 2) {
+        gaunt_pass<false, true>(nrp, rowinfo, grp, gterms, Rv, Rv, fab, fab + nfab, llo + 1, 0.0, 0.0, W, W + nWs);
+      } else {
+        gaunt_pass<false, false>(nrp, rowinfo, grp, gterms, Rv, Rv, fab, fab, llo + 1, 0.0, 0.0, W, W);
       }
     }
-    __syncthreads();
-    double* o = A.scratch + (int64_t)w * A.per_pair + A.voff[kind];
-    if (!live) {
-      for (int e = tid; e < na * nb; e += nth) o[e] = 0.0;
-      continue;
-    }
-    // V' = t_A W t_B in the pair frame (diagonal in m), first over the ket's l
-    for (int e = tid; e < nWa * nb; e += nth) {
-      const int q = e / nWa, i1 = e - q * nWa;
-      const int amb = (q + 1) >> 1, mb = (q & 1) ? amb : -amb;
-      double s = 0.0;
-      for (int l2 = amb; l2 <= lket; ++l2) {
-        const int i2 = l2 * l2 + l2 + mb;
-        s = fma(tB[l2 * nb + mb + lket], swap ? W[i2 * ws + i1] : W[i1 * ws + i2], s);
+    for (int t = 0; t < nacc; ++t) {
+      __syncthreads();
+      double* o = A.scratch + (int64_t)w * A.per_pair + A.soff[t == 0 ? slot0 : kSlotB + comp];
+      if (!live) {
+        for (int e = tid; e < (lowered ? 3 * NA * NB : na * nb); e += nth) o[e] = 0.0;
+        continue;
       }
-      Zb[i1 * nb + mb + lket] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < na * nb; e += nth) {
-      const int q = e / nb, mb = e - q * nb;
-      const int ama = (q + 1) >> 1, ma = (q & 1) ? ama : -ama;
-      double s = 0.0;
-      for (int l1 = ama; l1 <= lbra; ++l1) s = fma(tA[l1 * na + ma + lbra], Zb[(l1 * l1 + l1 + ma) * nb + mb], s);
-      Vp[(ma + lbra) * nb + mb] = s;
-    }
-    __syncthreads();
-    // to the molecular frame: D^{lbra} V' (D^{lket})^T
-    const double* Da = Dm;
-    const double* Db = lbra != lket ? Dm + na * na : Dm;
-    for (int e = tid; e < na * nb; e += nth) {
-      const int ma = e / nb, mb = e % nb;
-      double s = 0.0;
-      for (int k = 0; k < nb; ++k) s = fma(Vp[ma * nb + k], Db[mb * nb + k], s);
-      Yb[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < na * nb; e += nth) {
-      const int ma = e / nb, mb = e % nb;
-      double s = 0.0;
-      for (int k = 0; k < na; ++k) s = fma(Da[ma * na + k], Yb[k * nb + mb], s);
-      o[e] = s;
+      const double* Wt = W + t * nWs;
+      // V' = t_A W t_B in the pair frame (diagonal in m), first over the ket's l
+      for (int e = tid; e < nWa * nb; e += nth) {
+        const int q = e / nWa, i1 = e - q * nWa;
+        const int amb = (q + 1) >> 1, mb = (q & 1) ? amb : -amb;
+        double s = 0.0;
+        for (int l2 = amb; l2 <= lket; ++l2) {
+          const int i2 = l2 * l2 + l2 + mb;
+          s = fma(tB[l2 * nb + mb + lket], swap ? Wt[i2 * ws + i1] : Wt[i1 * ws + i2], s);
+        }
+        Zb[i1 * nb + mb + lket] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < na * nb; e += nth) {
+        const int q = e / nb, mb = e - q * nb;
+        const int ama = (q + 1) >> 1, ma = (q & 1) ? ama : -ama;
+        double s = 0.0;
+        for (int l1 = ama; l1 <= lbra; ++l1) s = fma(tA[l1 * na + ma + lbra], Zb[(l1 * l1 + l1 + ma) * nb + mb], s);
+        Vp[(ma + lbra) * nb + mb] = s;
+      }
+      __syncthreads();
+      // to the molecular frame: D^{lbra} V' (D^{lket})^T
+      const double* Da = Dm;
+      const double* Db = lbra != lket ? Dm + na * na : Dm;
+      for (int e = tid; e < na * nb; e += nth) {
+        const int ma = e / nb, mb = e % nb;
+        double s = 0.0;
+        for (int k = 0; k < nb; ++k) s = fma(Vp[ma * nb + k], Db[mb * nb + k], s);
+        Yb[e] = s;
+      }
+      __syncthreads();
+      double* fin = lowered ? Zb : o;  // a lowered block stays in shared memory for the lowering below
+      for (int e = tid; e < na * nb; e += nth) {
+        const int ma = e / nb, mb = e % nb;
+        double s = 0.0;
+        for (int k = 0; k < na; ++k) s = fma(Da[ma * na + k], Yb[k * nb + mb], s);
+        fin[e] = s;
+      }
+      if (lowered) {
+        // the lowered class's term of each molecular axis X: -(d_X S_la)-weighted rows (A) or columns (B)
+        __syncthreads();
+        for (int e = tid; e < 3 * NA * NB; e += nth) {
+          const int X = e / (NA * NB), r = e - X * NA * NB, ma = r / NB, mb = r - ma * NB;
+          double v = 0.0;
+          if (kind == kKindLowA) {
+            const int nl = 2 * A.la - 1;
+            const double* lo = A.low_a + ((int64_t)X * NA + ma) * nl;
+            for (int k = 0; k < nl; ++k) v = fma(-lo[k], Zb[k * NB + mb], v);
+          } else {
+            const int nl = 2 * A.lb - 1;
+            const double* lo = A.low_b + ((int64_t)X * NB + mb) * nl;
+            for (int k = 0; k < nl; ++k) v = fma(-lo[k], Zb[ma * nl + k], v);
+          }
+          o[e] = v;
+        }
+      }
     }
   }
 }
@@ -284,77 +358,74 @@ struct CombineArgs {
   int la = 0, lb = 0, npairs = 0, pair_base = 0;
   bool field = false;
   int64_t nbf = 0;
-  int64_t voff[kKinds] = {};
+  int64_t soff[kSlots] = {};
   int64_t per_pair = 0;
   const double* scratch = nullptr;
   const int* pair_a = nullptr;
   const int* pair_b = nullptr;
   const int* pair_site = nullptr;
   const double* site_rot = nullptr;
-  const double* shell_xyz = nullptr;
   const int64_t* shell_foff = nullptr;
-  const double* low_a = nullptr;  // Tables::d_low of la (nullptr for la = 0)
-  const double* low_b = nullptr;  // of lb
-  double* out = nullptr;          // [3][nbf][nbf]
+  double* out = nullptr;  // [3][nbf][nbf]
 };
 
-// One block per shell pair: the derivative (or field) blocks of the pair from its variants, both
-// orientations written.  Derivative: out[X][a][b] = -sum_M' low(la)[X][ma][M'] V_low_a[M'][mb]
-// - 2 (A - B)_X V_mu + sum_c Q[c][X] V_raise_a,c and, for a != b, out[X][b][a] the same with the ket's
-// variants and +2 (A - B)_X.  Field: out[X][a][b] = out[X][b][a] = sum_c Q[c][X] V_field,c (a diagonal
-// shell block takes its upper triangle for both halves, as V does).
+// One block per shell pair, one thread per element: the pair's derivative (or field) blocks from its scratch
+// blocks, all three components, both orientations written.  Derivative: out[X][a][b] = sum_c Q[c][X] V_A,c +
+// L_A,X and, for a != b, out[X][b][a] = sum_c Q[c][X] V_B,c + L_B,X (L the lowered classes' terms).  Field:
+// out[X][a][b] = out[X][b][a] = sum_c Q[c][X] V_F,c (a diagonal shell block takes its upper triangle for both
+// halves, as V does).  Every thread's loads are independent of one another.
 __global__ void __launch_bounds__(128) k_deriv_combine(CombineArgs C) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int na = 2 * C.la + 1, nb = 2 * C.lb + 1;
   const int64_t plane = C.nbf * C.nbf;
+  double* __restrict__ out = C.out;
   for (int w = blockIdx.x; w < C.npairs; w += gridDim.x) {
     const int pr = C.pair_base + w;
     const int a = C.pair_a[pr], b = C.pair_b[pr];
     const int64_t fa0 = C.shell_foff[a], fb0 = C.shell_foff[b];
-    const double* s = C.scratch + (int64_t)w * C.per_pair;
-    const double* Q = C.site_rot + 9 * (int64_t)C.pair_site[pr];
-    double ab[3];
+    const double* __restrict__ s = C.scratch + (int64_t)w * C.per_pair;
+    const double* __restrict__ Q = C.site_rot + 9 * (int64_t)C.pair_site[pr];
+    double q[9];
 #pragma unroll
-    for (int X = 0; X < 3; ++X) ab[X] = C.shell_xyz[3 * a + X] - C.shell_xyz[3 * b + X];
+    for (int k = 0; k < 9; ++k) q[k] = __ldg(Q + k);
     for (int e = tid; e < na * nb; e += nth) {
       const int ma = e / nb, mb = e % nb;
+      const int64_t iab = (fa0 + ma) * C.nbf + fb0 + mb, iba = (fb0 + mb) * C.nbf + fa0 + ma;
+      if (C.field) {
+        const int ee = (a == b && ma > mb) ? mb * nb + ma : e;
+        double v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = s[C.soff[kSlotField + c] + ee];
+#pragma unroll
+        for (int X = 0; X < 3; ++X) {
+          const double f = fma(q[6 + X], v[2], fma(q[3 + X], v[1], q[X] * v[0]));
+          out[X * plane + iab] = f;
+          if (a != b) out[X * plane + iba] = f;
+        }
+        continue;
+      }
+      const bool two = a != b;
+      double va[3], vb[3], la[3], lb[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        va[c] = s[C.soff[kSlotA + c] + e];
+        la[c] = C.la > 0 ? s[C.soff[kSlotLowA] + c * na * nb + e] : 0.0;
+        vb[c] = two ? s[C.soff[kSlotB + c] + e] : 0.0;
+        lb[c] = two && C.lb > 0 ? s[C.soff[kSlotLowB] + c * na * nb + e] : 0.0;
+      }
 #pragma unroll
       for (int X = 0; X < 3; ++X) {
-        double* o = C.out + X * plane;
-        if (C.field) {
-          const int ee = (a == b && ma > mb) ? mb * nb + ma : e;
-          double v = 0.0;
-          for (int c = 0; c < 3; ++c) v = fma(Q[3 * c + X], s[C.voff[kKindField + c] + ee], v);
-          o[(fa0 + ma) * C.nbf + fb0 + mb] = v;
-          if (a != b) o[(fb0 + mb) * C.nbf + fa0 + ma] = v;
-          continue;
-        }
-        const double vmu = s[C.voff[kKindMu] + e];
-        double v = -2.0 * ab[X] * vmu;
-        for (int c = 0; c < 3; ++c) v = fma(Q[3 * c + X], s[C.voff[kKindRaiseA + c] + e], v);
-        if (C.la > 0) {
-          const int nl = 2 * C.la - 1;
-          const double* lo = C.low_a + ((int64_t)X * na + ma) * nl;
-          const double* vl = s + C.voff[kKindLowA];
-          for (int k = 0; k < nl; ++k) v = fma(-lo[k], vl[k * nb + mb], v);
-        }
-        o[(fa0 + ma) * C.nbf + fb0 + mb] = v;
-        if (a == b) continue;
-        double u = 2.0 * ab[X] * vmu;
-        for (int c = 0; c < 3; ++c) u = fma(Q[3 * c + X], s[C.voff[kKindRaiseB + c] + e], u);
-        if (C.lb > 0) {
-          const int nl = 2 * C.lb - 1;
-          const double* lo = C.low_b + ((int64_t)X * nb + mb) * nl;
-          const double* vl = s + C.voff[kKindLowB] + (int64_t)ma * nl;
-          for (int k = 0; k < nl; ++k) u = fma(-lo[k], vl[k], u);
-        }
-        o[(fb0 + mb) * C.nbf + fa0 + ma] = u;
+        out[X * plane + iab] = fma(q[6 + X], va[2], fma(q[3 + X], va[1], fma(q[X], va[0], la[X])));
+        if (two) out[X * plane + iba] = fma(q[6 + X], vb[2], fma(q[3 + X], vb[1], fma(q[X], vb[0], lb[X])));
       }
     }
   }
 }
 
 int class_of(int l1, int l2) { return l1 >= l2 ? class_id(l1, l2) : class_id(l2, l1); }
+
+// Largest shared memory of a variant that raises for both centres in one pass: two blocks fit on an SM.
+constexpr size_t kDualMaxBytes = 113 * 1024;
 
 }  // namespace
 
@@ -391,23 +462,43 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     d.npairs = w.npairs;
     d.pair_base = w.pair_base;
     d.pp_base = w.pp_base;
+    // variants: the three axes raised for both centres in one pass when two such blocks fit on an SM,
+    // otherwise one pass per centre; the lowered classes; or the three field blocks
     std::vector<int> kinds;
     if (field) {
       kinds = {kKindField, kKindField + 1, kKindField + 2};
     } else {
-      for (int k = kKindMu; k < kKindLowA; ++k) kinds.push_back(k);
+      const bool dual = sizeof(double) * deriv_block_doubles(w.la, w.lb, kKindAB + 2) <= kDualMaxBytes;
+      for (int c = 0; c < 3; ++c) {
+        if (dual) {
+          kinds.push_back(kKindAB + c);
+        } else {
+          kinds.push_back(kKindA + c);
+          kinds.push_back(kKindB + c);
+        }
+      }
       if (w.la > 0) kinds.push_back(kKindLowA);
       if (w.lb > 0) kinds.push_back(kKindLowB);
     }
     d.nkind = (int)kinds.size();
-    int64_t off = 0;
     for (int k = 0; k < d.nkind; ++k) {
       d.kinds[k] = kinds[k];
-      int lbra, lket;
-      deriv_shape(w.la, w.lb, kinds[k], lbra, lket);
-      d.voff[kinds[k]] = off;
-      off += (int64_t)(2 * lbra + 1) * (2 * lket + 1);
       P.smem = std::max(P.smem, sizeof(double) * deriv_block_doubles(w.la, w.lb, kinds[k]));
+    }
+    // scratch blocks of a shell pair
+    const int64_t nab = (int64_t)(2 * w.la + 1) * (2 * w.lb + 1);
+    int64_t off = 0;
+    auto place = [&](int slot, int64_t n) {
+      d.soff[slot] = off;
+      off += n;
+    };
+    if (field) {
+      for (int c = 0; c < 3; ++c) place(kSlotField + c, nab);
+    } else {
+      for (int c = 0; c < 3; ++c) place(kSlotA + c, nab);
+      for (int c = 0; c < 3; ++c) place(kSlotB + c, nab);
+      if (w.la > 0) place(kSlotLowA, 3 * nab);
+      if (w.lb > 0) place(kSlotLowB, 3 * nab);
     }
     d.per_pair = off;
     P.threads = (w.la + 1) * (w.la + 1) * (w.lb + 1) * (w.lb + 1) >= 1024
@@ -504,6 +595,8 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     d.mapm = dt.d_mapm + th.d_mapm_off[lam];
     d.raise = dt.d_raise + (size_t)th.d_xoff[lam] * 3 * kDerivSlots;
     d.fconst = dt.d_field + (size_t)th.d_xoff[lam] * 3 * kDerivSlots;
+    d.low_a = w.la > 0 ? dt.d_low + th.d_low_off[w.la] : nullptr;
+    d.low_b = w.lb > 0 ? dt.d_low + th.d_low_off[w.lb] : nullptr;
     d.ppd = db.ppd;
     d.r1buf = r1buf;
     const dim3 grid((unsigned)grid_cap_sm(w.npairs, 16), (unsigned)d.nkind);
@@ -517,19 +610,16 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     c.pair_base = w.pair_base;
     c.field = field;
     c.nbf = nbf;
-    for (int k = 0; k < kKinds; ++k) c.voff[k] = d.voff[k];
+    for (int k = 0; k < kSlots; ++k) c.soff[k] = d.soff[k];
     c.per_pair = d.per_pair;
     c.scratch = d.scratch;
     c.pair_a = db.pair_a;
     c.pair_b = db.pair_b;
     c.pair_site = db.pair_site;
     c.site_rot = db.site_rot;
-    c.shell_xyz = db.shell_xyz;
     c.shell_foff = db.shell_foff;
-    c.low_a = w.la > 0 ? dt.d_low + th.d_low_off[w.la] : nullptr;
-    c.low_b = w.lb > 0 ? dt.d_low + th.d_low_off[w.lb] : nullptr;
     c.out = out;
-    k_deriv_combine<<<grid_cap_sm(w.npairs, 16), 64, 0, s>>>(c);
+    k_deriv_combine<<<grid_cap_sm(w.npairs, 16), 128, 0, s>>>(c);
     e = cudaGetLastError();
   }
   for (int i = 0; i < ns && fork; ++i) {

@@ -107,6 +107,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_eri_jk.restype = ctypes.c_int
     lib.shgo_basis_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, f64p, f64p]
     lib.shgo_basis_flops.restype = ctypes.c_int
+    lib.shgo_basis_deriv_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, f64p]
+    lib.shgo_basis_deriv_flops.restype = ctypes.c_int
     lib.shgo_sparse_layout.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]
     lib.shgo_sparse_layout.restype = ctypes.c_int
@@ -203,6 +205,14 @@ def shgo_basis_flops(basis, n_centers: int):
     _check(_lib.shgo_basis_flops(ctypes.c_void_p(basis), int(n_centers), _ptr(f, ctypes.c_double),
                                  _ptr(t, ctypes.c_double)))
     return f, t
+
+
+def shgo_basis_deriv_flops(basis, n_centers: int, field: bool = False):
+    """Algorithmic FP64 operations of one derivative (or field) call: (coupling, pair passes + combine)."""
+    f = np.zeros(2)
+    _check(_lib.shgo_basis_deriv_flops(ctypes.c_void_p(basis), int(n_centers), int(bool(field)),
+                                       _ptr(f, ctypes.c_double)))
+    return f
 
 
 def shgo_basis_set_time_limit(basis, seconds: float) -> None:
