@@ -369,17 +369,18 @@ struct CombineArgs {
   double* out = nullptr;  // [3][nbf][nbf]
 };
 
-// One block per shell pair, one thread per element: the pair's derivative (or field) blocks from its scratch
-// blocks, all three components, both orientations written.  Derivative: out[X][a][b] = sum_c Q[c][X] V_A,c +
-// L_A,X and, for a != b, out[X][b][a] = sum_c Q[c][X] V_B,c + L_B,X (L the lowered classes' terms).  Field:
-// out[X][a][b] = out[X][b][a] = sum_c Q[c][X] V_F,c (a diagonal shell block takes its upper triangle for both
-// halves, as V does).  Every thread's loads are independent of one another.
-__global__ void __launch_bounds__(128) k_deriv_combine(CombineArgs C) {
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int na = 2 * C.la + 1, nb = 2 * C.lb + 1;
+// One thread per element of every shell pair of the class (pair-major): the pair's derivative (or field)
+// elements from its scratch blocks, all three components, both orientations written.  Derivative:
+// out[X][a][b] = sum_c Q[c][X] V_A,c + L_A,X and, for a != b, out[X][b][a] = sum_c Q[c][X] V_B,c + L_B,X (L the
+// lowered classes' terms).  Field: out[X][a][b] = out[X][b][a] = sum_c Q[c][X] V_F,c (a diagonal shell block
+// takes its upper triangle for both halves, as V does).  Every thread's loads are independent of one another.
+__global__ void __launch_bounds__(256) k_deriv_combine(CombineArgs C) {
+  const int na = 2 * C.la + 1, nb = 2 * C.lb + 1, nab = na * nb;
   const int64_t plane = C.nbf * C.nbf;
+  const int64_t total = (int64_t)C.npairs * nab;
   double* __restrict__ out = C.out;
-  for (int w = blockIdx.x; w < C.npairs; w += gridDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int w = (int)(i / nab), e = (int)(i - (int64_t)w * nab);
     const int pr = C.pair_base + w;
     const int a = C.pair_a[pr], b = C.pair_b[pr];
     const int64_t fa0 = C.shell_foff[a], fb0 = C.shell_foff[b];
@@ -388,36 +389,34 @@ __global__ void __launch_bounds__(128) k_deriv_combine(CombineArgs C) {
     double q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) q[k] = __ldg(Q + k);
-    for (int e = tid; e < na * nb; e += nth) {
-      const int ma = e / nb, mb = e % nb;
-      const int64_t iab = (fa0 + ma) * C.nbf + fb0 + mb, iba = (fb0 + mb) * C.nbf + fa0 + ma;
-      if (C.field) {
-        const int ee = (a == b && ma > mb) ? mb * nb + ma : e;
-        double v[3];
+    const int ma = e / nb, mb = e % nb;
+    const int64_t iab = (fa0 + ma) * C.nbf + fb0 + mb, iba = (fb0 + mb) * C.nbf + fa0 + ma;
+    if (C.field) {
+      const int ee = (a == b && ma > mb) ? mb * nb + ma : e;
+      double v[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[c] = s[C.soff[kSlotField + c] + ee];
-#pragma unroll
-        for (int X = 0; X < 3; ++X) {
-          const double f = fma(q[6 + X], v[2], fma(q[3 + X], v[1], q[X] * v[0]));
-          out[X * plane + iab] = f;
-          if (a != b) out[X * plane + iba] = f;
-        }
-        continue;
-      }
-      const bool two = a != b;
-      double va[3], vb[3], la[3], lb[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        va[c] = s[C.soff[kSlotA + c] + e];
-        la[c] = C.la > 0 ? s[C.soff[kSlotLowA] + c * na * nb + e] : 0.0;
-        vb[c] = two ? s[C.soff[kSlotB + c] + e] : 0.0;
-        lb[c] = two && C.lb > 0 ? s[C.soff[kSlotLowB] + c * na * nb + e] : 0.0;
-      }
+      for (int c = 0; c < 3; ++c) v[c] = s[C.soff[kSlotField + c] + ee];
 #pragma unroll
       for (int X = 0; X < 3; ++X) {
-        out[X * plane + iab] = fma(q[6 + X], va[2], fma(q[3 + X], va[1], fma(q[X], va[0], la[X])));
-        if (two) out[X * plane + iba] = fma(q[6 + X], vb[2], fma(q[3 + X], vb[1], fma(q[X], vb[0], lb[X])));
+        const double f = fma(q[6 + X], v[2], fma(q[3 + X], v[1], q[X] * v[0]));
+        out[X * plane + iab] = f;
+        if (a != b) out[X * plane + iba] = f;
       }
+      continue;
+    }
+    const bool two = a != b;
+    double va[3], vb[3], la[3], lb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      va[c] = s[C.soff[kSlotA + c] + e];
+      la[c] = C.la > 0 ? s[C.soff[kSlotLowA] + c * nab + e] : 0.0;
+      vb[c] = two ? s[C.soff[kSlotB + c] + e] : 0.0;
+      lb[c] = two && C.lb > 0 ? s[C.soff[kSlotLowB] + c * nab + e] : 0.0;
+    }
+#pragma unroll
+    for (int X = 0; X < 3; ++X) {
+      out[X * plane + iab] = fma(q[6 + X], va[2], fma(q[3 + X], va[1], fma(q[X], va[0], la[X])));
+      if (two) out[X * plane + iba] = fma(q[6 + X], vb[2], fma(q[3 + X], vb[1], fma(q[X], vb[0], lb[X])));
     }
   }
 }
@@ -619,7 +618,7 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     c.site_rot = db.site_rot;
     c.shell_foff = db.shell_foff;
     c.out = out;
-    k_deriv_combine<<<grid_cap_sm(w.npairs, 16), 128, 0, s>>>(c);
+    k_deriv_combine<<<grid_cap_sm(((int64_t)w.npairs * (2 * w.la + 1) * (2 * w.lb + 1) + 255) / 256, 8), 256, 0, s>>>(c);
     e = cudaGetLastError();
   }
   for (int i = 0; i < ns && fork; ++i) {
