@@ -133,3 +133,26 @@ def test_deriv_repeatable(shgo):
     b = shgo.nuclear_attraction_deriv(B, Cd, Zd).cpu().numpy()
     B.close()
     assert np.array_equal(a, b)
+
+
+def test_deriv_is_fp64_whatever_the_basis_precision(shgo):
+    # the derivative path runs the FP64 coupling kernel for every basis: an FP32-bulk basis gives the same bits
+    basis = W.random_basis(74, 8, 4, max_prim=2, box=3.0, n_sites=3)
+    C, Z = W.random_nuclei(75, 5, box=3.0)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    B64 = shgo.Basis(basis)
+    B32 = shgo.Basis(basis, precision=shgo.SHGO_PREC_FP32_BULK)
+    for fn in (shgo.nuclear_attraction_deriv, shgo.nuclear_field):
+        assert np.array_equal(fn(B64, Cd, Zd).cpu().numpy(), fn(B32, Cd, Zd).cpu().numpy())
+    B64.close()
+    B32.close()
+
+
+def test_deriv_rejects_a_batch(shgo):
+    mols = [(W.random_basis(76 + k, 3, 2, max_prim=2, box=2.0), 2) for k in range(2)]
+    bt = shgo.Batch(mols)
+    import ctypes
+    c = shgo.shgo_centers(0, None)
+    for fn in (shgo._lib.shgo_nuclear_attraction_deriv, shgo._lib.shgo_nuclear_field):
+        assert fn(ctypes.c_void_p(bt.handle), ctypes.byref(c), None, None, None) == 1  # SHGO_ERR_INVALID_ARG
+    bt.close()
