@@ -676,6 +676,11 @@ def run_deriv(args) -> int:
     ms_v = timed(lambda: shgo.nuclear_attraction(B, Cd, Zd, out=V, stream=stream))
     ms_d = timed(lambda: shgo.nuclear_attraction_deriv(B, Cd, Zd, out=D, stream=stream))
     ms_f = timed(lambda: shgo.nuclear_field(B, Cd, Zd, out=D, stream=stream))
+    rng = np.random.default_rng(7100)
+    p = rng.normal(size=(B.nbf, B.nbf))
+    P = torch.tensor((p + p.T) / 2, device=dev)
+    G = torch.empty((B.n_shells, 3), dtype=torch.float64, device=dev)
+    ms_g = timed(lambda: shgo.nuclear_attraction_gradient(B, P, Cd, Zd, out=G, stream=stream))
     clocks = sampler.stop()
     fd = shgo.shgo_basis_deriv_flops(B.handle, len(Z), False)
     ff = shgo.shgo_basis_deriv_flops(B.handle, len(Z), True)
@@ -689,6 +694,8 @@ def run_deriv(args) -> int:
                                    f"functions, {len(Z)} nuclei", "shell_pairs": B.npairs,
                        "l2": "flushed between steps (256 MiB write, outside step events)"},
             "v_ms": ms_v, "deriv_over_v": ms_d / ms_v,
+            "gradient": {"ms_per_step": ms_g, "over_v": ms_g / ms_v,
+                         "what": "sum_ab (P_ab + P_ba) dV_ab/dA per shell for a seeded symmetric density, no matrix written"},
             "field": {"ms_per_step": ms_f, "shell_triples_per_s": triples / (ms_f / 1e3), "over_v": ms_f / ms_v,
                       "model_tflop": float(ff.sum()) / 1e12, "achieved_tflops": ach_f, "frac": ach_f / peak},
             "roofline": {"bound": "fp64", "kernel": "whole derivative call (coupling at la + lb + 1, variant passes, "

@@ -283,6 +283,20 @@ shgo_status shgo_esp_gradient(const shgo_basis* basis, const double* density, co
 shgo_status shgo_nuclear_attraction_deriv(const shgo_basis* basis, const shgo_centers* centers,
                                           const double* charges, double* out, void* stream);
 
+/* Gradient of E = sum_{a,b} P_ab V_ab with respect to the centre of every shell (the nuclear-attraction part of
+ * the basis-function force), without forming the derivative matrices:
+ *   grad[s][X] = sum_{a in s} sum_b (P_ab + P_ba) dV_ab/dA_X,   A the centre of shell s,
+ * i.e. dE/dA_X when only shell s moves; the shells on one atom add up to that atom's basis-function term.  The
+ * nuclei's own term is dE/dC_X = Z_C times shgo_esp_gradient at C for the same (symmetric) density, and
+ * translational invariance gives sum_s grad[s] + sum_C dE/dC = 0.  The same pipeline as
+ * shgo_nuclear_attraction_deriv; each shell pair's elements are weighted by P and summed on the device (one
+ * warp per pair, a fixed order), then each shell adds its pairs in pair order: the result does not depend on
+ * the schedule.  density: device, nbf x nbf row-major (any matrix).  grad: device [n_shells][3], overwritten.
+ * Same arguments, restrictions and errors as shgo_nuclear_attraction_deriv (no nbf^2 output is allocated). */
+shgo_status shgo_nuclear_attraction_gradient(const shgo_basis* basis, const double* density,
+                                             const shgo_centers* centers, const double* charges, double* grad,
+                                             void* stream);
+
 /* Field integrals of the nuclei (derivative of V by the nucleus positions, summed):
  *   out[X][a][b] = sum_C Z_C d/dC_X < phi_a | 1/|r - C| | phi_b >   (symmetric in a, b).
  * The matrix of one nucleus C (the Hellmann-Feynman force integrals) is the call with that nucleus alone

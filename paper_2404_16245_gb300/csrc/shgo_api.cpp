@@ -92,6 +92,10 @@ struct shgo_basis {
   int64_t sparse_nblocks = 0, sparse_ndoubles = 0;
   std::vector<int64_t> h_blk_off;
   int64_t* d_blk_off = nullptr;
+  // density-contracted gradient: per shell its (pair, side) entries, CSR, built on the first such call
+  int64_t* d_shell_off = nullptr;
+  int64_t* d_shell_list = nullptr;
+  std::mutex grad_mu;
 };
 
 namespace {
@@ -856,6 +860,72 @@ shgo_status deriv_call(const shgo_basis* basis, const shgo_centers* centers, con
 shgo_status shgo_nuclear_attraction_deriv(const shgo_basis* basis, const shgo_centers* centers,
                                           const double* charges, double* out, void* stream) {
   return deriv_call(basis, centers, charges, out, stream, false);
+}
+
+shgo_status shgo_nuclear_attraction_gradient(const shgo_basis* basis, const double* density,
+                                             const shgo_centers* centers, const double* charges, double* grad,
+                                             void* stream) {
+  g_last_error.clear();
+  if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "the gradient takes a single basis, not a batch");
+  if (!centers || centers->n < 0) return fail(SHGO_ERR_INVALID_ARG, "centers is NULL or negative count");
+  if (centers->n > 0 && (!centers->xyz || !charges)) return fail(SHGO_ERR_INVALID_ARG, "NULL centers/charges");
+  if (basis->n_shells > 0 && (!grad || !density)) return fail(SHGO_ERR_INVALID_ARG, "grad or density is NULL");
+  if (basis->n_shells == 0) return SHGO_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != basis->device) cudaSetDevice(basis->device);
+  shgo_basis* mb = const_cast<shgo_basis*>(basis);
+  std::string err;
+  shgo_status st = SHGO_OK;
+  {
+    // each shell's (pair, side) entries in pair order, once per basis
+    std::lock_guard<std::mutex> lk(mb->grad_mu);
+    if (!mb->d_shell_off) {
+      const int ns = basis->n_shells;
+      const int64_t np = basis->npairs;
+      std::vector<int64_t> off(ns + 1, 0), list;
+      for (int64_t q = 0; q < np; ++q) {
+        off[basis->h_pair_a[q] + 1] += 1;
+        if (basis->h_pair_b[q] != basis->h_pair_a[q]) off[basis->h_pair_b[q] + 1] += 1;
+      }
+      for (int i = 0; i < ns; ++i) off[i + 1] += off[i];
+      list.resize(off[ns]);
+      std::vector<int64_t> pos(off.begin(), off.end() - 1);
+      for (int64_t q = 0; q < np; ++q) {
+        list[pos[basis->h_pair_a[q]]++] = 2 * q;
+        if (basis->h_pair_b[q] != basis->h_pair_a[q]) list[pos[basis->h_pair_b[q]]++] = 2 * q + 1;
+      }
+      int64_t *doff = nullptr, *dlist = nullptr;
+      cudaError_t e = pool_alloc(basis->device, (void**)&doff, sizeof(int64_t) * off.size());
+      if (e == cudaSuccess) e = pool_alloc(basis->device, (void**)&dlist, sizeof(int64_t) * std::max<size_t>(list.size(), 1));
+      if (e == cudaSuccess) e = cudaMemcpy(doff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && !list.empty())
+        e = cudaMemcpy(dlist, list.data(), sizeof(int64_t) * list.size(), cudaMemcpyHostToDevice);
+      if (doff) mb->allocations.push_back(doff);
+      if (dlist) mb->allocations.push_back(dlist);
+      if (e != cudaSuccess) {
+        st = e == cudaErrorMemoryAllocation ? SHGO_ERR_OOM : SHGO_ERR_CUDA;
+        err = std::string("gradient lists: ") + cudaGetErrorString(e);
+      } else {
+        mb->d_shell_off = doff;
+        mb->d_shell_list = dlist;
+      }
+    }
+  }
+  if (st == SHGO_OK) {
+    DerivContraction c;
+    c.P = density;
+    c.n_shells = basis->n_shells;
+    c.shell_off = mb->d_shell_off;
+    c.shell_list = mb->d_shell_list;
+    c.grad = grad;
+    st = launch_nuclear_deriv(basis->d, *basis->tabs, basis->work, basis->nbf, centers->n, centers->xyz, charges,
+                              nullptr, false, (cudaStream_t)stream, &err, &c);
+  }
+  if (prev != basis->device) cudaSetDevice(prev);
+  if (st != SHGO_OK) return fail(st, err);
+  return SHGO_OK;
 }
 
 shgo_status shgo_nuclear_field(const shgo_basis* basis, const shgo_centers* centers, const double* charges,

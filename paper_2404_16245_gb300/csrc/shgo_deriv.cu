@@ -421,6 +421,108 @@ __global__ void __launch_bounds__(256) k_deriv_combine(CombineArgs C) {
   }
 }
 
+// Contraction of a class's derivative blocks with a density P: a group of lanes per shell pair writes
+// partial[pr][0..2] = sum_{a, b} (P_ab + P_ba) dV_ab/dA_X over the pair's elements (the bra shell's centre) and,
+// for two different shells, partial[pr][3..5] the same with dV_ab/dB_X (the ket shell's).  The element values
+// are those k_deriv_combine writes; each lane sums its elements in index order and the group adds its lanes in
+// a fixed butterfly, so the result does not depend on the schedule.
+struct ContractArgs {
+  int la = 0, lb = 0, npairs = 0, pair_base = 0;
+  int64_t nbf = 0;
+  int64_t soff[kSlots] = {};
+  int64_t per_pair = 0;
+  const double* scratch = nullptr;
+  const int* pair_a = nullptr;
+  const int* pair_b = nullptr;
+  const int* pair_site = nullptr;
+  const double* site_rot = nullptr;
+  const int64_t* shell_foff = nullptr;
+  const double* P = nullptr;  // nbf x nbf
+  double* partial = nullptr;  // [npairs of the basis][6]
+};
+
+template <int G>
+__global__ void __launch_bounds__(128) k_deriv_contract(ContractArgs C) {
+  // G lanes per shell pair (a power of two up to 32, from the pair's element count); a warp takes 32 / G
+  // consecutive pairs per round and keeps every lane in the round for the shuffles
+  const int lane = threadIdx.x & 31, sub = lane / G, lg = lane % G;
+  const int na = 2 * C.la + 1, nb = 2 * C.lb + 1, nab = na * nb;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int64_t w0 = wid * (32 / G); w0 < C.npairs; w0 += warps * (32 / G)) {
+    const int64_t w = w0 + sub;
+    const bool active = w < C.npairs;
+    const int pr = C.pair_base + (int)(active ? w : w0);
+    const int a = C.pair_a[pr], b = C.pair_b[pr];
+    const bool two = a != b;
+    const int64_t fa0 = C.shell_foff[a], fb0 = C.shell_foff[b];
+    const double* __restrict__ s = C.scratch + (int64_t)w * C.per_pair;
+    const double* __restrict__ Q = C.site_rot + 9 * (int64_t)C.pair_site[pr];
+    double q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) q[k] = __ldg(Q + k);
+    double ga[3] = {0.0, 0.0, 0.0}, gb[3] = {0.0, 0.0, 0.0};
+    for (int e = lg; active && e < nab; e += G) {
+      const int ma = e / nb, mb = e % nb;
+      const int64_t iab = (fa0 + ma) * C.nbf + fb0 + mb, iba = (fb0 + mb) * C.nbf + fa0 + ma;
+      const double pw = __ldg(C.P + iab) + __ldg(C.P + iba);
+      double va[3], vb[3], la[3], lb[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        va[c] = s[C.soff[kSlotA + c] + e];
+        la[c] = C.la > 0 ? s[C.soff[kSlotLowA] + c * nab + e] : 0.0;
+        vb[c] = two ? s[C.soff[kSlotB + c] + e] : 0.0;
+        lb[c] = two && C.lb > 0 ? s[C.soff[kSlotLowB] + c * nab + e] : 0.0;
+      }
+#pragma unroll
+      for (int X = 0; X < 3; ++X) {
+        ga[X] = fma(pw, fma(q[6 + X], va[2], fma(q[3 + X], va[1], fma(q[X], va[0], la[X]))), ga[X]);
+        gb[X] = fma(pw, fma(q[6 + X], vb[2], fma(q[3 + X], vb[1], fma(q[X], vb[0], lb[X]))), gb[X]);
+      }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int X = 0; X < 3; ++X) {
+        ga[X] += __shfl_xor_sync(0xffffffffu, ga[X], off);
+        gb[X] += __shfl_xor_sync(0xffffffffu, gb[X], off);
+      }
+    if (active && lg == 0) {
+      double* o = C.partial + 6 * (int64_t)pr;
+#pragma unroll
+      for (int X = 0; X < 3; ++X) {
+        o[X] = ga[X];
+        o[3 + X] = two ? gb[X] : 0.0;
+      }
+    }
+  }
+}
+
+// grad[s][X] = the partials of the shell's pairs (entries pr * 2 + side of its list, in pair order) added up: one
+// warp per shell, lane i taking entries i, i + 32, ... in order, then a fixed butterfly across the lanes.
+__global__ void __launch_bounds__(128) k_shell_gradient(int n_shells, const int64_t* __restrict__ off,
+                                                        const int64_t* __restrict__ list,
+                                                        const double* __restrict__ partial, double* __restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t sh = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sh < n_shells; sh += warps) {
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = off[sh] + lane; j < off[sh + 1]; j += 32) {
+      const int64_t e = list[j];
+      const double* p = partial + 6 * (e >> 1) + 3 * (e & 1);
+#pragma unroll
+      for (int X = 0; X < 3; ++X) g[X] += p[X];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int X = 0; X < 3; ++X) g[X] += __shfl_xor_sync(0xffffffffu, g[X], o);
+    if (lane == 0)
+#pragma unroll
+      for (int X = 0; X < 3; ++X) grad[3 * sh + X] = g[X];
+  }
+}
+
 int class_of(int l1, int l2) { return l1 >= l2 ? class_id(l1, l2) : class_id(l2, l1); }
 
 // Largest shared memory of a variant that raises for both centres in one pass: two blocks fit on an SM.
@@ -430,9 +532,11 @@ constexpr size_t kDualMaxBytes = 113 * 1024;
 
 shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                                  int64_t nbf, int64_t ncenters, const double* centers, const double* charges,
-                                 double* out, bool field, cudaStream_t stream, std::string* err) {
+                                 double* out, bool field, cudaStream_t stream, std::string* err,
+                                 const DerivContraction* contract) {
   if (nbf == 0) return SHGO_OK;
-  const size_t nout = (size_t)3 * (size_t)nbf * (size_t)nbf;
+  const size_t nout = contract ? (size_t)3 * (size_t)contract->n_shells : (size_t)3 * (size_t)nbf * (size_t)nbf;
+  if (contract) out = contract->grad;
   if (ncenters == 0) {
     const cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * nout, stream);
     if (e != cudaSuccess) {
@@ -508,12 +612,18 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     r1_total += w.npp * (int64_t)n_r(w.la + w.lb + 1);
     scr_total += (int64_t)w.npairs * off;
   }
+  int64_t npairs_all = 0;
+  for (const ClassWork& w : work) npairs_all = std::max<int64_t>(npairs_all, (int64_t)w.pair_base + w.npairs);
   double* r1buf = nullptr;
   double* scr = nullptr;
+  double* partial = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&r1buf, sizeof(double) * (size_t)std::max<int64_t>(r1_total, 1), stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&scr, sizeof(double) * (size_t)std::max<int64_t>(scr_total, 1), stream);
+  if (e == cudaSuccess && contract)
+    e = cudaMallocAsync((void**)&partial, sizeof(double) * 6 * (size_t)std::max<int64_t>(npairs_all, 1), stream);
   if (e != cudaSuccess) {
     if (r1buf) cudaFreeAsync(r1buf, stream);
+    if (scr) cudaFreeAsync(scr, stream);
     cudaGetLastError();
     *err = std::string("derivative buffers: ") + cudaGetErrorString(e);
     return SHGO_ERR_OOM;
@@ -602,6 +712,38 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     k_deriv_block<<<grid, P.threads, P.smem, s>>>(d);
     e = cudaGetLastError();
     if (e != cudaSuccess) break;
+    if (contract) {
+      ContractArgs g;
+      g.la = w.la;
+      g.lb = w.lb;
+      g.npairs = w.npairs;
+      g.pair_base = w.pair_base;
+      g.nbf = nbf;
+      for (int k = 0; k < kSlots; ++k) g.soff[k] = d.soff[k];
+      g.per_pair = d.per_pair;
+      g.scratch = d.scratch;
+      g.pair_a = db.pair_a;
+      g.pair_b = db.pair_b;
+      g.pair_site = db.pair_site;
+      g.site_rot = db.site_rot;
+      g.shell_foff = db.shell_foff;
+      g.P = contract->P;
+      g.partial = partial;
+      const int nab = (2 * w.la + 1) * (2 * w.lb + 1);
+      int G = 1;
+      while (G < 32 && G < nab) G *= 2;
+      const int grid = grid_cap_sm(((int64_t)w.npairs * G + 127) / 128, 16);
+      switch (G) {
+        case 1: k_deriv_contract<1><<<grid, 128, 0, s>>>(g); break;
+        case 2: k_deriv_contract<2><<<grid, 128, 0, s>>>(g); break;
+        case 4: k_deriv_contract<4><<<grid, 128, 0, s>>>(g); break;
+        case 8: k_deriv_contract<8><<<grid, 128, 0, s>>>(g); break;
+        case 16: k_deriv_contract<16><<<grid, 128, 0, s>>>(g); break;
+        default: k_deriv_contract<32><<<grid, 128, 0, s>>>(g); break;
+      }
+      e = cudaGetLastError();
+      continue;
+    }
     CombineArgs& c = P.c;
     c.la = w.la;
     c.lb = w.lb;
@@ -629,6 +771,12 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
     cudaEventDestroy(join);
   }
   if (fork) cudaEventDestroy(fork);
+  if (e == cudaSuccess && contract) {
+    k_shell_gradient<<<grid_cap_sm(((int64_t)contract->n_shells + 3) / 4, 16), 128, 0, stream>>>(
+        contract->n_shells, contract->shell_off, contract->shell_list, partial, contract->grad);
+    e = cudaGetLastError();
+  }
+  if (partial) cudaFreeAsync(partial, stream);
   cudaFreeAsync(scr, stream);
   cudaFreeAsync(r1buf, stream);
   if (e != cudaSuccess) {

@@ -468,11 +468,24 @@ shgo_status launch_esp(const DeviceBasis& db, const DeviceTables& dt, const std:
                        int64_t nbf, const double* D, int64_t npoints, const double* points, double* phi, double* gbuf,
                        bool gradient, cudaStream_t stream, std::string* err);
 
+// Contraction of the centre derivatives with a density (shgo_nuclear_attraction_gradient): P (device,
+// nbf x nbf), the shells' lists of (pair, side) entries pr * 2 + side in pair order (side 1: the pair's ket
+// shell), CSR over shells, and grad (device, [n_shells][3]).
+struct DerivContraction {
+  const double* P = nullptr;
+  int n_shells = 0;
+  const int64_t* shell_off = nullptr;
+  const int64_t* shell_list = nullptr;
+  double* grad = nullptr;
+};
+
 // Derivative integrals of a single basis, computed in FP64 (shgo_deriv.cu).  field = false: out[X] (X = x, y, z,
-// nbf x nbf each) receives dV_ab/d(centre of a)_X; field = true: sum_C Z_C dV_ab/dC_X (symmetric).
+// nbf x nbf each) receives dV_ab/d(centre of a)_X; field = true: sum_C Z_C dV_ab/dC_X (symmetric).  With
+// contract (field = false), no matrix is written: contract->grad receives the density-contracted gradient.
 shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                                  int64_t nbf, int64_t ncenters, const double* centers, const double* charges,
-                                 double* out, bool field, cudaStream_t stream, std::string* err);
+                                 double* out, bool field, cudaStream_t stream, std::string* err,
+                                 const DerivContraction* contract = nullptr);
 // The per-device pool of non-blocking streams on which the classes of one call run concurrently.
 cudaError_t pool_streams(cudaStream_t** out, int* n);
 // Blocks for n units of work, at most per_sm per SM.

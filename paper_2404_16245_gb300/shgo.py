@@ -91,6 +91,9 @@ def _load() -> ctypes.CDLL:
     lib.shgo_nuclear_attraction_deriv.argtypes = [ctypes.c_void_p, ctypes.POINTER(shgo_centers), ctypes.c_void_p,
                                                   ctypes.c_void_p, ctypes.c_void_p]
     lib.shgo_nuclear_attraction_deriv.restype = ctypes.c_int
+    lib.shgo_nuclear_attraction_gradient.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(shgo_centers),
+                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.shgo_nuclear_attraction_gradient.restype = ctypes.c_int
     lib.shgo_nuclear_field.argtypes = lib.shgo_nuclear_attraction_deriv.argtypes
     lib.shgo_nuclear_field.restype = ctypes.c_int
     lib.shgo_host_deriv_transform.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, f64p, f64p, f64p]
@@ -296,6 +299,7 @@ class Basis:
                                         basis["xyz"], precision, device, flags)
         self.nbf = shgo_basis_nbf(self.handle)
         self.npairs = shgo_basis_npairs(self.handle)
+        self.n_shells = len(basis["l"])
         self.sparse = bool(flags & SHGO_FLAG_BLOCK_SPARSE)
         if self.sparse:
             self.nblocks, self.ndoubles, self.offset = shgo_sparse_layout(self.handle)
@@ -446,6 +450,37 @@ def nuclear_field(basis: Basis, centers, charges, out=None, stream=None):
     shgo_nuclear_field(basis.handle, n, centers.data_ptr() if n else 0, charges.data_ptr() if n else 0,
                        out.data_ptr(), stream)
     return out
+
+
+def shgo_nuclear_attraction_gradient(basis, density_ptr, n_centers, centers_ptr, charges_ptr, grad_ptr, stream=None):
+    c = shgo_centers(int(n_centers), ctypes.c_void_p(int(centers_ptr) if centers_ptr else 0))
+    _check(_lib.shgo_nuclear_attraction_gradient(ctypes.c_void_p(basis), ctypes.c_void_p(int(density_ptr) or 0),
+                                                 ctypes.byref(c),
+                                                 ctypes.c_void_p(int(charges_ptr) if charges_ptr else 0),
+                                                 ctypes.c_void_p(int(grad_ptr) if grad_ptr else 0),
+                                                 _stream_handle(stream)))
+
+
+def nuclear_attraction_gradient(basis: Basis, density, centers, charges, out=None, stream=None):
+    """grad[s][X] = sum_{a in s} sum_b (P_ab + P_ba) dV_ab/dA_X (A the centre of shell s): [n_shells, 3] FP64
+    device tensor; density [nbf, nbf], centers [n, 3], charges [n] are CUDA float64 tensors."""
+    import torch
+    if not (centers.is_cuda and charges.is_cuda):
+        raise ValueError("centers and charges must be CUDA tensors")
+    if centers.dtype != torch.float64 or charges.dtype != torch.float64:
+        raise ValueError("centers and charges must be float64")
+    centers = centers.contiguous()
+    charges = charges.contiguous()
+    n = centers.shape[0] if centers.numel() else 0
+    density = density.contiguous()
+    if tuple(density.shape) != (basis.nbf, basis.nbf) or density.dtype != torch.float64 or not density.is_cuda:
+        raise ValueError("density must be a CUDA float64 [nbf, nbf] tensor")
+    ns = basis.n_shells
+    if out is None:
+        out = torch.empty((max(ns, 1), 3), dtype=torch.float64, device=centers.device)
+    shgo_nuclear_attraction_gradient(basis.handle, density.data_ptr(), n, centers.data_ptr() if n else 0,
+                                     charges.data_ptr() if n else 0, out.data_ptr(), stream)
+    return out[:ns]
 
 
 def field_matrices(basis: Basis, centers, stream=None):

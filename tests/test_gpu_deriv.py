@@ -156,3 +156,71 @@ def test_deriv_rejects_a_batch(shgo):
     for fn in (shgo._lib.shgo_nuclear_attraction_deriv, shgo._lib.shgo_nuclear_field):
         assert fn(ctypes.c_void_p(bt.handle), ctypes.byref(c), None, None, None) == 1  # SHGO_ERR_INVALID_ARG
     bt.close()
+
+
+def _shell_of_function(basis):
+    l = np.asarray(basis["l"])
+    return np.repeat(np.arange(len(l)), 2 * l + 1)
+
+
+def test_gradient_contracts_the_oracle_derivative(shgo):
+    # grad[s] = sum_{a in s} sum_b (P_ab + P_ba) dV_ab/dA against the oracle's derivative contracted on the host;
+    # bar per component: 1e-11 of the contraction's absolute sum
+    basis = W.random_basis(78, 12, 5, max_prim=3, box=3.0, exp_lo=0.1, exp_hi=30.0, n_sites=5)
+    C, Z = W.random_nuclei(79, 6, box=3.0)
+    n = W.nbf(basis)
+    rng = np.random.default_rng(80)
+    P = rng.normal(size=(n, n))  # not symmetric: the contraction takes P_ab + P_ba
+    B = shgo.Basis(basis)
+    g = shgo.nuclear_attraction_gradient(B, torch.tensor(P, device="cuda"), torch.tensor(C, device="cuda"),
+                                         torch.tensor(Z, device="cuda")).cpu().numpy()
+    B.close()
+    D = oracle.nuclear_deriv(basis, C, Z, threads=THREADS, precision="ld")
+    W2 = P + P.T
+    sh = _shell_of_function(basis)
+    for s in range(len(basis["l"])):
+        rows = sh == s
+        for X in range(3):
+            terms = W2[rows, :] * D[X][rows, :]
+            assert abs(g[s, X] - terms.sum()) <= 1e-11 * np.abs(terms).sum() + 1e-13, (s, X)
+
+
+def test_gradient_and_nuclear_forces_sum_to_zero(shgo):
+    # E = sum P_ab V_ab is unchanged when basis and nuclei move together: sum_s grad[s] + sum_C Z_C grad phi(C) = 0
+    basis = W.random_basis(81, 14, 6, max_prim=2, box=4.0, exp_lo=0.1, exp_hi=20.0, n_sites=5)
+    C, Z = W.random_nuclei(82, 8, box=4.0)
+    n = W.nbf(basis)
+    rng = np.random.default_rng(83)
+    p = rng.normal(size=(n, n))
+    P = (p + p.T) / 2
+    B = shgo.Basis(basis)
+    Pd, Cd, Zd = (torch.tensor(x, device="cuda") for x in (P, C, Z))
+    g = shgo.nuclear_attraction_gradient(B, Pd, Cd, Zd).cpu().numpy()
+    ge = shgo.esp_gradient(B, Pd, Cd).cpu().numpy()
+    D = shgo.nuclear_attraction_deriv(B, Cd, Zd).cpu().numpy()
+    B.close()
+    total = g.sum(axis=0) + (Z[:, None] * ge).sum(axis=0)
+    scale = np.abs(g).sum() + np.abs(Z[:, None] * ge).sum()
+    assert np.max(np.abs(total)) <= 1e-11 * scale
+    # the same as contracting the library's own derivative matrices
+    sh = _shell_of_function(basis)
+    for s in range(len(basis["l"])):
+        rows = sh == s
+        for X in range(3):
+            terms = (2 * P)[rows, :] * D[X][rows, :]
+            assert abs(g[s, X] - terms.sum()) <= 1e-12 * np.abs(terms).sum() + 1e-14
+
+
+def test_gradient_repeatable_and_degenerate(shgo):
+    basis = W.random_basis(84, 10, 4, max_prim=2, box=3.0, n_sites=4)
+    C, Z = W.random_nuclei(85, 5, box=3.0)
+    n = W.nbf(basis)
+    P = torch.tensor(np.random.default_rng(86).normal(size=(n, n)), device="cuda")
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    a = shgo.nuclear_attraction_gradient(B, P, Cd, Zd).cpu().numpy()
+    b = shgo.nuclear_attraction_gradient(B, P, Cd, Zd).cpu().numpy()
+    assert np.array_equal(a, b)
+    z = shgo.nuclear_attraction_gradient(B, P, Cd[:0], Zd[:0]).cpu().numpy()
+    assert np.count_nonzero(z) == 0
+    B.close()

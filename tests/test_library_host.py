@@ -495,6 +495,7 @@ def test_deriv_entry_points_reject_bad_arguments():
     c = shgo.shgo_centers(0, None)
     for fn in (shgo._lib.shgo_nuclear_attraction_deriv, shgo._lib.shgo_nuclear_field):
         assert fn(None, ctypes.byref(c), None, None, None) == 1  # SHGO_ERR_INVALID_ARG
+    assert shgo._lib.shgo_nuclear_attraction_gradient(None, None, ctypes.byref(c), None, None, None) == 1
     with pytest.raises(shgo.ShgoError):
         shgo.host_deriv_transform(17, 0, 1.0, np.zeros(2000))
     with pytest.raises(shgo.ShgoError):
