@@ -1245,11 +1245,26 @@ def run_peaks(args) -> int:
 def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
     """Small fixed case for ncu captures: one warm and one measured V of the benchmark workload
     (highl) or of the first molecule of the batched workload (batched), or of the benchmark workload's
-    derivative integrals (deriv) or field integrals (field)."""
+    derivative integrals (deriv) or field integrals (field); or 16 replicas of the benchmark molecule in one
+    batch with each class's two kernels timed one after another, twice (replicas16)."""
     import torch
 
     from paper_2404_16245_gb300 import shgo
     from paper_2404_16245_gb300 import workloads as W
+    if case == "replicas16":
+        # 16 replicas of the benchmark molecule in one batch, each class's kernels timed one after another
+        rb = [W.config2(replica=100 + k) for k in range(16)]
+        batch = shgo.Batch([(bb, len(ZZ)) for bb, _, ZZ in rb])
+        Cb = torch.tensor(np.concatenate([CC for _, CC, _ in rb]), device="cuda")
+        Zb = torch.tensor(np.concatenate([ZZ for _, _, ZZ in rb]), device="cuda")
+        outb = torch.empty(batch.out_size, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            shgo.shgo_nuclear_attraction_class_timed(batch.handle, Cb.shape[0], Cb.data_ptr(), Zb.data_ptr(),
+                                                     outb.data_ptr(), None)
+        torch.cuda.synchronize()
+        print("profile case ok", batch.out_size)
+        batch.close()
+        return 0
     if case == "batched":
         b, C, Z = W.config3_molecule(np.random.Generator(np.random.PCG64(3000)))
     else:
@@ -1272,7 +1287,7 @@ def run_profile_case(precision: str = "fp64", case: str = "highl") -> int:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", nargs="?", const="highl", choices=["highl", "batched", "deriv", "field"],
+    ap.add_argument("--profile-case", nargs="?", const="highl", choices=["highl", "batched", "deriv", "field", "replicas16"],
                     help="one warm + one measured call, for ncu (the benchmark molecule or one batched molecule)")
     ap.add_argument("--precision-sweep", type=int, default=0, metavar="N",
                     help="per-class FP32-bulk / FP32-plain / FP64 error study on N random triples")
