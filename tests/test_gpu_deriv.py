@@ -224,3 +224,27 @@ def test_gradient_repeatable_and_degenerate(shgo):
     z = shgo.nuclear_attraction_gradient(B, P, Cd[:0], Zd[:0]).cpu().numpy()
     assert np.count_nonzero(z) == 0
     B.close()
+
+
+def test_deriv_field_and_gradient_at_benchmark_size(shgo):
+    # the benchmark molecule in full (1568 functions, 32 nuclei), in the launch configuration the bench times
+    basis, C, Z = W.config2()
+    B = shgo.Basis(basis)
+    Cd, Zd = torch.tensor(C, device="cuda"), torch.tensor(Z, device="cuda")
+    D = shgo.nuclear_attraction_deriv(B, Cd, Zd).cpu().numpy()
+    F = shgo.nuclear_field(B, Cd, Zd).cpu().numpy()
+    n = B.nbf
+    rng = np.random.default_rng(87)
+    p = rng.normal(size=(n, n))
+    P = (p + p.T) / 2
+    g = shgo.nuclear_attraction_gradient(B, torch.tensor(P, device="cuda"), Cd, Zd).cpu().numpy()
+    B.close()
+    Dref = oracle.nuclear_deriv(basis, C, Z, threads=THREADS)
+    check(D, Dref, "dV/dA, benchmark molecule")
+    check(F, oracle.nuclear_field(basis, C, Z, threads=THREADS), "field, benchmark molecule")
+    sh = _shell_of_function(basis)
+    for s in range(len(basis["l"])):
+        rows = sh == s
+        for X in range(3):
+            terms = (2 * P)[rows, :] * Dref[X][rows, :]
+            assert abs(g[s, X] - terms.sum()) <= 1e-11 * np.abs(terms).sum() + 1e-13, (s, X)
