@@ -708,6 +708,54 @@ def run_deriv(args) -> int:
     return 0
 
 
+def run_shard(args, ws: int, rank: int, local: int) -> int:
+    """One benchmark molecule's V split over the ranks (shgo_basis_create_shard: each rank takes its share of
+    every class's shell pairs by primitive-pair count and writes its disjoint blocks; no collective, the host
+    would gather).  value = the whole V's shell triples / the slowest rank's time per V: strong scaling.
+    L2 flushed between steps."""
+    import torch
+
+    import torch.distributed as dist
+
+    from paper_2404_16245_gb300 import shgo
+    from paper_2404_16245_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    b, C, Z = W.config2()
+    B = shgo.Basis(b, shard=(rank, ws))
+    Cd, Zd = torch.tensor(C, device=dev), torch.tensor(Z, device=dev)
+    out = torch.zeros((B.nbf, B.nbf), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)
+    triples = float(len(b["l"]) * (len(b["l"]) + 1) // 2) * len(Z)
+    for _ in range(max(3, args.warmup)):
+        shgo.nuclear_attraction(B, Cd, Zd, out=out, stream=stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        shgo.nuclear_attraction(B, Cd, Zd, out=out, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in evs), ws, dev) / args.steps
+    if rank == 0:
+        print(json.dumps({"metric": "SHGO nuclear-attraction shell-triples/s, one V split over ranks",
+                          "value": triples / (ms / 1e3), "unit": "shell-triples/s", "n_gpus": ws, "steps": args.steps,
+                          "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "high-l FP64 benchmark molecule, shell pairs split over the ranks",
+                                     "shell_pairs_this_rank": B.npairs, "parallelism": f"pair shards x{ws}",
+                                     "l2": "flushed between steps (256 MiB write, outside step events)"}}),
+              flush=True)
+    B.close()
+    return 0
+
+
 def _cluster(seed: int, n_atoms: int):
     """Screening workload: atoms uniform at 0.1 atoms/bohr^3, Z ~ U{1..9}, 4s3p2d1f on every atom
     with 1..6 primitives, exponents log-uniform [0.05, 5000]."""
@@ -1296,7 +1344,7 @@ def main():
     ap.add_argument("--sweep-ext", type=int, default=20,
                     help="triples per (la, lb) class also checked against the extended-precision oracle")
     ap.add_argument("--workload", default="highl", choices=["highl", "batched", "screened", "esp", "coulomb2c", "eri", "peaks",
-                                                          "deriv"],
+                                                          "deriv", "shard"],
                     help="highl = the 32-atom l <= 6 molecule (default); batched = many contracted molecules")
     ap.add_argument("--molecules", type=int, default=64, help="molecules of the batched workload")
     ap.add_argument("--points", type=int, default=100000, help="points of the potential workload")
@@ -1354,6 +1402,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, ws, rank)
+        if args.workload == "shard":
+            return run_shard(args, ws, rank, local)
         return run_shgo(args, ws, rank, local)
     finally:
         if ws > 1:

@@ -91,6 +91,22 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
                               const double* coefs, const double* shell_xyz, const shgo_options* opt,
                               shgo_basis** out);
 
+/* One shard of a basis split over shard_count devices (one process or thread per device): the same basis,
+ * keeping only the shell pairs of shard shard_index.  Inside each (la, lb) class the pairs, in the library's
+ * pair order, are cut by their cumulative primitive-pair count (a pair's cost is its primitive-pair count
+ * times the nuclei), so every shard gets about 1/shard_count of every class.  Calls on a shard compute only
+ * its pairs: shgo_nuclear_attraction (and the overlap, two-centre Coulomb, derivative and field calls)
+ * write only the shard's blocks of out, both triangles, and leave the other blocks untouched, so the shards'
+ * outputs, each into a zeroed matrix, add up to the whole matrix (the blocks are disjoint: no collective,
+ * the host gathers); the potential, its gradient and the contracted gradient return the shard's share of
+ * the sum.  Four-centre integrals reject a shard (SHGO_ERR_INVALID_ARG).  shard_count = 1 is
+ * shgo_basis_create.  Errors: those of shgo_basis_create; SHGO_ERR_INVALID_ARG for an index outside
+ * 0..shard_count-1. */
+shgo_status shgo_basis_create_shard(int32_t n_shells, const int32_t* l, const int32_t* n_prim,
+                                    const double* exponents, const double* coefs, const double* shell_xyz,
+                                    const shgo_options* opt, int32_t shard_index, int32_t shard_count,
+                                    shgo_basis** out);
+
 /* Primitive-pair bound.  With |S_lm(r)| <= |r|^l and the potential of a non-negative radial density peaking
  * at its centre, every element of one primitive pair's block is at most
  *   |c_i c_j| K_AB 4 pi int_0^inf (r + |PA|)^la (r + |PB|)^lb e^{-p r^2} r dr    per unit of total charge.
@@ -422,6 +438,12 @@ shgo_status shgo_host_boys(int32_t nmax, double T, double* F);
  * c = comp (0, 1, 2 = x, y, z).  lam <= 2 * SHGO_LMAX. */
 shgo_status shgo_host_deriv_transform(int32_t lam, int32_t comp, double p, const double* r1, double* raised,
                                       double* field);
+
+/* The shard of every shell pair of a single basis split over shard_count shards (shgo_basis_create_shard),
+ * in the library's pair order (shgo_pair_shells), on the host.  *npairs: in, the room in shard; out, the
+ * number of pairs (shard is written only when the room suffices; shard may be NULL to ask for the count). */
+shgo_status shgo_host_shard_of_pairs(int32_t n_shells, const int32_t* l, const int32_t* n_prim, int32_t shard_count,
+                                     int64_t* npairs, int32_t* shard);
 
 /* Lowering coefficients: d/dx_c S_lm(r) = sum_M' w[M' + l - 1] S_{l-1,M'}(r), 1 <= l <= SHGO_LMAX;
  * w receives 2l - 1 values. */

@@ -92,6 +92,8 @@ struct shgo_basis {
   int64_t sparse_nblocks = 0, sparse_ndoubles = 0;
   std::vector<int64_t> h_blk_off;
   int64_t* d_blk_off = nullptr;
+  // one shard of a basis split over devices (shgo_basis_create_shard)
+  int shard_index = 0, shard_count = 1;
   // density-contracted gradient: per shell its (pair, side) entries, CSR, built on the first such call
   int64_t* d_shell_off = nullptr;
   int64_t* d_shell_list = nullptr;
@@ -211,14 +213,37 @@ const char* shgo_last_error(void) { return g_last_error.c_str(); }
 
 namespace {
 
+// Shard of every shell pair when one basis's pairs are split over `count` shards (one per device): inside each
+// class the pairs, in the library's pair order, are cut by their cumulative primitive-pair count (the cost of a
+// pair of one class is its primitive-pair count times the nuclei, the same for all of them), pair q going to
+// shard floor(count (start_q + npp_q / 2) / npp_class).  Every shard gets about 1/count of every class, so the
+// shards' costs and their mixes of classes match.
+void shard_of_pairs(const std::vector<ClassWork>& work, const std::vector<int64_t>& ppoff, int count,
+                    std::vector<int>& shard) {
+  shard.assign(ppoff.empty() ? 0 : ppoff.size() - 1, 0);
+  for (const ClassWork& w : work) {
+    const double tot = (double)w.npp;
+    for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q) {
+      const double mid = (double)(ppoff[q] - w.pp_base) + 0.5 * (double)(ppoff[q + 1] - ppoff[q]);
+      int k = tot > 0 ? (int)((double)count * mid / tot) : 0;
+      shard[q] = std::min(std::max(k, 0), count - 1);
+    }
+  }
+}
+
 // Shells of n_mol molecules (consecutive runs of mol_nshells shells; n_mol = 0 means one molecule
 // whose nuclei are given per call), validated, normalised and turned into class-sorted pair lists.
+// shard_count > 1 (single bases only): keep the pairs of shard shard_index (shard_of_pairs).
 shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_prim, const double* exponents,
                         const double* coefs, const double* shell_xyz, const shgo_options* opt, int32_t n_mol,
-                        const int32_t* mol_nshells, const int64_t* mol_ncenters, shgo_basis** out) {
+                        const int32_t* mol_nshells, const int64_t* mol_ncenters, shgo_basis** out,
+                        int32_t shard_index = 0, int32_t shard_count = 1) {
   g_last_error.clear();
   if (!out) return fail(SHGO_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  if (shard_count < 1 || shard_index < 0 || shard_index >= shard_count)
+    return fail(SHGO_ERR_INVALID_ARG, "shard index outside 0..shard_count-1");
+  if (shard_count > 1 && n_mol > 0) return fail(SHGO_ERR_INVALID_ARG, "a batch is split by molecules, not shards");
   if (n_shells < 0) return fail(SHGO_ERR_INVALID_ARG, "n_shells < 0");
   if (n_shells > 0 && (!l || !n_prim || !exponents || !coefs || !shell_xyz))
     return fail(SHGO_ERR_INVALID_ARG, "NULL basis array");
@@ -406,6 +431,52 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
         b->class_pp_cent.push_back(ppc);
       }
     }
+  if (shard_count > 1) {
+    // keep this shard's pairs (and their primitive pairs), renumbered in the same order
+    std::vector<int64_t> off_all(ppoff.begin(), ppoff.end());
+    off_all.push_back(ppcount);
+    std::vector<int> shard;
+    shard_of_pairs(b->work, off_all, shard_count, shard);
+    std::vector<int> pa2, pb2, pm2, ppp2, ppi2;
+    std::vector<int64_t> ppoff2;
+    std::vector<ClassWork> work2;
+    std::vector<double> pc2, ppc2;
+    for (size_t wi = 0; wi < b->work.size(); ++wi) {
+      const ClassWork& w = b->work[wi];
+      ClassWork v{w.la, w.lb, 0, (int)pa2.size(), 0, (int64_t)ppp2.size()};
+      for (int q = w.pair_base; q < w.pair_base + w.npairs; ++q) {
+        if (shard[q] != shard_index) continue;
+        const int nq = (int)pa2.size();
+        pa2.push_back(pa[q]);
+        pb2.push_back(pb[q]);
+        pm2.push_back(pmol[q]);
+        ppoff2.push_back((int64_t)ppp2.size());
+        for (int64_t x = off_all[q]; x < off_all[q + 1]; ++x) {
+          ppp2.push_back(nq);
+          ppi2.push_back(pp_ij[x]);
+        }
+        ++v.npairs;
+      }
+      v.npp = (int64_t)ppp2.size() - v.pp_base;
+      if (v.npairs > 0) {
+        work2.push_back(v);
+        pc2.push_back(0.0);
+        ppc2.push_back(0.0);
+      }
+    }
+    pa.swap(pa2);
+    pb.swap(pb2);
+    pmol.swap(pm2);
+    ppoff.swap(ppoff2);
+    pp_pair.swap(ppp2);
+    pp_ij.swap(ppi2);
+    ppcount = (int64_t)pp_pair.size();
+    b->work.swap(work2);
+    b->class_pair_cent.swap(pc2);
+    b->class_pp_cent.swap(ppc2);
+    b->shard_index = shard_index;
+    b->shard_count = shard_count;
+  }
   b->npairs = (int64_t)pa.size();
   b->h_pair_a = pa;
   b->h_pair_b = pb;
@@ -720,6 +791,53 @@ shgo_status shgo_basis_create(int32_t n_shells, const int32_t* l, const int32_t*
   return build_basis(n_shells, l, n_prim, exponents, coefs, shell_xyz, opt, 0, nullptr, nullptr, out);
 }
 
+shgo_status shgo_basis_create_shard(int32_t n_shells, const int32_t* l, const int32_t* n_prim,
+                                    const double* exponents, const double* coefs, const double* shell_xyz,
+                                    const shgo_options* opt, int32_t shard_index, int32_t shard_count,
+                                    shgo_basis** out) {
+  return build_basis(n_shells, l, n_prim, exponents, coefs, shell_xyz, opt, 0, nullptr, nullptr, out, shard_index,
+                     shard_count);
+}
+
+shgo_status shgo_host_shard_of_pairs(int32_t n_shells, const int32_t* l, const int32_t* n_prim, int32_t shard_count,
+                                     int64_t* npairs, int32_t* shard) {
+  g_last_error.clear();
+  if (n_shells < 0 || shard_count < 1 || !npairs || (n_shells > 0 && (!l || !n_prim)))
+    return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  for (int s = 0; s < n_shells; ++s)
+    if (l[s] < 0 || l[s] > kLmax || n_prim[s] < 1 || n_prim[s] > 64) return fail(SHGO_ERR_INVALID_ARG, "bad shell");
+  // the library's pair order for one molecule (class by class, la >= lb, then shell index) and its
+  // primitive-pair offsets
+  std::vector<std::vector<int>> by_l(kLmax + 1);
+  for (int s = 0; s < n_shells; ++s) by_l[l[s]].push_back(s);
+  std::vector<ClassWork> work;
+  std::vector<int64_t> ppoff;
+  int64_t pp = 0;
+  for (int la = 0; la <= kLmax; ++la)
+    for (int lb = 0; lb <= la; ++lb) {
+      ClassWork w{la, lb, 0, (int)ppoff.size(), 0, pp};
+      const auto& A = by_l[la];
+      const auto& B = by_l[lb];
+      for (size_t x = 0; x < A.size(); ++x)
+        for (size_t y = 0; y < ((la == lb) ? x + 1 : B.size()); ++y) {
+          ppoff.push_back(pp);
+          pp += (int64_t)n_prim[A[x]] * n_prim[B[y]];
+          ++w.npairs;
+        }
+      w.npp = pp - w.pp_base;
+      if (w.npairs > 0) work.push_back(w);
+    }
+  const int64_t np = (int64_t)ppoff.size();
+  ppoff.push_back(pp);
+  if (shard && *npairs >= np) {
+    std::vector<int> sh;
+    shard_of_pairs(work, ppoff, shard_count, sh);
+    for (int64_t q = 0; q < np; ++q) shard[q] = sh[q];
+  }
+  *npairs = np;
+  return SHGO_OK;
+}
+
 shgo_status shgo_batch_create(int32_t n_mol, const int32_t* mol_nshells, const int64_t* mol_ncenters, int32_t n_shells,
                               const int32_t* l, const int32_t* n_prim, const double* exponents, const double* coefs,
                               const double* shell_xyz, const shgo_options* opt, shgo_basis** out) {
@@ -993,6 +1111,7 @@ shgo_status shgo_coulomb_2c(const shgo_basis* basis, double* out, void* stream) 
 shgo_status shgo_eri(const shgo_basis* basis, double* out, void* stream) {
   g_last_error.clear();
   if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->shard_count > 1) return fail(SHGO_ERR_INVALID_ARG, "four-centre integrals need every shell pair, not a shard");
   if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "electron-repulsion integrals take a single basis, not a batch");
   if (basis->nbf > 40000) return fail(SHGO_ERR_INVALID_ARG, "nbf^4 output too large");
   for (const ClassWork& w : basis->work)
@@ -1012,6 +1131,7 @@ shgo_status shgo_eri(const shgo_basis* basis, double* out, void* stream) {
 shgo_status shgo_eri_jk(const shgo_basis* basis, const double* density, double* J, double* K, void* stream) {
   g_last_error.clear();
   if (!basis) return fail(SHGO_ERR_INVALID_ARG, "basis is NULL");
+  if (basis->shard_count > 1) return fail(SHGO_ERR_INVALID_ARG, "four-centre integrals need every shell pair, not a shard");
   if (basis->batch) return fail(SHGO_ERR_INVALID_ARG, "electron-repulsion integrals take a single basis, not a batch");
   for (const ClassWork& w : basis->work)
     if (w.la > kEriLmax) return fail(SHGO_ERR_UNSUPPORTED_L, "electron-repulsion integrals support l <= 4");

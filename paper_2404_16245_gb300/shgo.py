@@ -51,6 +51,12 @@ def _load() -> ctypes.CDLL:
     lib.shgo_basis_create.argtypes = [ctypes.c_int32, i32p, i32p, f64p, f64p, f64p, ctypes.POINTER(shgo_options),
                                       ctypes.POINTER(ctypes.c_void_p)]
     lib.shgo_basis_create.restype = ctypes.c_int
+    lib.shgo_basis_create_shard.argtypes = [ctypes.c_int32, i32p, i32p, f64p, f64p, f64p, ctypes.POINTER(shgo_options),
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]
+    lib.shgo_basis_create_shard.restype = ctypes.c_int
+    lib.shgo_host_shard_of_pairs.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                             i32p]
+    lib.shgo_host_shard_of_pairs.restype = ctypes.c_int
     lib.shgo_basis_nbf.argtypes = [ctypes.c_void_p]
     lib.shgo_basis_nbf.restype = ctypes.c_int64
     lib.shgo_basis_npairs.argtypes = [ctypes.c_void_p]
@@ -167,8 +173,9 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 # ------------------------------------------------------------------ C-ABI names
 def shgo_basis_create(n_shells, l, n_prim, exponents, coefs, shell_xyz, precision=SHGO_PREC_FP64, device=-1,
-                      flags=0):
-    """Returns an opaque handle (int).  Host arrays are copied by the library."""
+                      flags=0, shard=None):
+    """Returns an opaque handle (int).  Host arrays are copied by the library.  shard = (index, count) builds
+    that shard of the basis (shgo_basis_create_shard)."""
     l = np.ascontiguousarray(l, dtype=np.int32)
     n_prim = np.ascontiguousarray(n_prim, dtype=np.int32)
     exponents = np.ascontiguousarray(exponents, dtype=np.float64)
@@ -176,10 +183,26 @@ def shgo_basis_create(n_shells, l, n_prim, exponents, coefs, shell_xyz, precisio
     shell_xyz = np.ascontiguousarray(shell_xyz, dtype=np.float64).reshape(-1)
     opt = shgo_options(int(precision), int(device), int(flags))
     handle = ctypes.c_void_p()
-    _check(_lib.shgo_basis_create(int(n_shells), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32),
-                                  _ptr(exponents, ctypes.c_double), _ptr(coefs, ctypes.c_double),
-                                  _ptr(shell_xyz, ctypes.c_double), ctypes.byref(opt), ctypes.byref(handle)))
+    args = (int(n_shells), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32), _ptr(exponents, ctypes.c_double),
+            _ptr(coefs, ctypes.c_double), _ptr(shell_xyz, ctypes.c_double), ctypes.byref(opt))
+    if shard is None:
+        _check(_lib.shgo_basis_create(*args, ctypes.byref(handle)))
+    else:
+        _check(_lib.shgo_basis_create_shard(*args, int(shard[0]), int(shard[1]), ctypes.byref(handle)))
     return handle.value
+
+
+def host_shard_of_pairs(l, n_prim, shard_count: int) -> np.ndarray:
+    """Shard of every shell pair (library pair order) when one basis is split over shard_count devices."""
+    l = np.ascontiguousarray(l, dtype=np.int32)
+    n_prim = np.ascontiguousarray(n_prim, dtype=np.int32)
+    n = ctypes.c_int64(0)
+    _check(_lib.shgo_host_shard_of_pairs(len(l), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32),
+                                         int(shard_count), ctypes.byref(n), None))
+    out = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(_lib.shgo_host_shard_of_pairs(len(l), _ptr(l, ctypes.c_int32), _ptr(n_prim, ctypes.c_int32),
+                                         int(shard_count), ctypes.byref(n), _ptr(out, ctypes.c_int32)))
+    return out[:n.value]
 
 
 def shgo_nuclear_attraction(basis, n_centers, centers_ptr, charges_ptr, out_ptr, stream=None):
@@ -294,9 +317,10 @@ def shgo_sparse_layout(basis):
 class Basis:
     """Owns a shgo_basis handle built from a basis dict (see workloads.py)."""
 
-    def __init__(self, basis: dict, precision: int = SHGO_PREC_FP64, device: int = -1, flags: int = 0):
+    def __init__(self, basis: dict, precision: int = SHGO_PREC_FP64, device: int = -1, flags: int = 0,
+                 shard=None):
         self.handle = shgo_basis_create(len(basis["l"]), basis["l"], basis["nprim"], basis["exps"], basis["coefs"],
-                                        basis["xyz"], precision, device, flags)
+                                        basis["xyz"], precision, device, flags, shard)
         self.nbf = shgo_basis_nbf(self.handle)
         self.npairs = shgo_basis_npairs(self.handle)
         self.n_shells = len(basis["l"])
