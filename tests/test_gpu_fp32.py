@@ -103,3 +103,61 @@ def test_fp32_bulk_edge_cases_against_oracle(shgo, capsys):
         print(f"\nedge cases: FP32-bulk vs oracle block error max {eb.max():.2e} median {np.median(eb):.2e}")
     assert np.all(np.isfinite(bulk))
     assert eb.max() < 1e-10
+
+
+def block_errors_vs_oracle(basis, got, ref, Z):
+    """Per shell-pair block against the oracle: (max abs error, block max) of the blocks above the library's
+    elementwise bound (n_prim_a n_prim_b x 1e-20 x sum |Z|); a block below it, which the library skips, must
+    match to that bound."""
+    off = np.concatenate([[0], np.cumsum(2 * basis["l"] + 1)])
+    nprim = np.asarray(basis["nprim"])
+    zsum = float(np.sum(np.abs(Z)))
+    errs, scales = [], []
+    for a in range(len(basis["l"])):
+        for b in range(a + 1):
+            r = ref[off[a]:off[a + 1], off[b]:off[b + 1]]
+            g = got[off[a]:off[a + 1], off[b]:off[b + 1]]
+            bound = nprim[a] * nprim[b] * 1e-20 * zsum
+            scale = np.max(np.abs(r))
+            if scale <= bound:
+                assert np.max(np.abs(g - r)) <= bound, (a, b)
+                continue
+            errs.append(np.max(np.abs(g - r)))
+            scales.append(scale)
+    return np.array(errs), np.array(scales)
+
+
+def check_vs_oracle(name, e, sc, capsys):
+    # blocks: |error| <= 1e-8 x block max + 1e-13, the relative measure of reading C9 (target 1e-7) on the blocks
+    # above 1e-6 of the largest.  Against the oracle the bar is 1e-8 rather than the 1e-10 held against the FP64
+    # path: at l = 6 the double oracle's own block error reaches ~1e-10 (the two GPU paths agree to ~3e-12)
+    big = sc >= 1e-6 * sc.max()
+    rel = e[big] / sc[big]
+    with capsys.disabled():
+        print(f"\n{name}: FP32-bulk vs oracle, {len(e)} blocks above the bound: block error max {rel.max():.2e} "
+              f"median {np.median(rel):.2e} over the {int(big.sum())} blocks above 1e-6 of the largest; "
+              f"max abs error {e.max():.2e}")
+    assert np.all(e <= 1e-8 * sc + 1e-13)
+    assert rel.max() <= 1e-8
+
+
+@pytest.mark.parametrize("name,factory", [("config1", W.config1), ("config2", W.config2)])
+def test_fp32_bulk_against_the_oracle_in_full(shgo, name, factory, capsys):
+    # FP32-bulk checked directly against the oracle (not through the FP64 GPU path)
+    basis, C, Z = factory()
+    bulk = run(shgo, basis, C, Z, shgo.SHGO_PREC_FP32_BULK)
+    ref = oracle.nuclear_attraction(basis, C, Z, threads=os.cpu_count() or 1)
+    check_vs_oracle(name, *block_errors_vs_oracle(basis, bulk, ref, Z), capsys)
+
+
+def test_fp32_bulk_every_class_to_l8_against_the_oracle(shgo, capsys):
+    ls = list(range(9)) * 2
+    rng = np.random.default_rng(97)
+    sites = rng.uniform(0, 2.5, (3, 3))
+    exps = np.exp(rng.uniform(np.log(0.1), np.log(30.0), len(ls) * 2))
+    basis = W.make_basis(ls, [2] * len(ls), exps, rng.uniform(0.2, 1, len(ls) * 2), [sites[i % 3] for i in range(len(ls))])
+    C = np.vstack([rng.uniform(-1.0, 3.5, (9, 3)), sites[:1]])
+    Z = rng.uniform(0.5, 9.0, len(C))
+    bulk = run(shgo, basis, C, Z, shgo.SHGO_PREC_FP32_BULK)
+    ref = oracle.nuclear_attraction(basis, C, Z, threads=os.cpu_count() or 1, precision="ld")
+    check_vs_oracle("every class to (8, 8)", *block_errors_vs_oracle(basis, bulk, ref, Z), capsys)
