@@ -1484,15 +1484,54 @@ size_t coulomb2c_smem(int la, int lb) {
   return sizeof(double) * ((size_t)nf * nf + nf + 64 * (size_t)nf + 64 + 64 + 1 + 8);
 }
 
+// Launches `launch(w, s)` for every non-empty class of `work`, the classes (which write disjoint blocks) spread
+// over the pool streams, the costliest first (cost: an estimate of the class's work), after the work already
+// queued on `stream`, which then waits for all of them.
+template <typename Cost, typename Launch>
+cudaError_t classes_concurrent(const std::vector<ClassWork>& work, cudaStream_t stream, Cost&& cost, Launch&& launch) {
+  cudaStream_t* pool = nullptr;
+  cudaError_t e = stream_pool(&pool);
+  std::vector<int> order;
+  for (size_t c = 0; c < work.size(); ++c)
+    if (work[c].npairs > 0) order.push_back((int)c);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(work[x]) > cost(work[y]); });
+  const int ns = (int)std::min<size_t>(order.size(), (size_t)kPoolStreams);
+  cudaEvent_t fork = nullptr;
+  if (e == cudaSuccess && ns > 0) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && fork) e = cudaEventRecord(fork, stream);
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(pool[i], fork, 0);
+  for (size_t k = 0; k < order.size() && e == cudaSuccess; ++k) {
+    launch(work[order[k]], pool[k % ns]);
+    e = cudaGetLastError();
+  }
+  for (int i = 0; i < ns && fork; ++i) {
+    cudaEvent_t join;
+    if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) break;
+    cudaEventRecord(join, pool[i]);
+    cudaStreamWaitEvent(stream, join, 0);
+    cudaEventDestroy(join);
+  }
+  if (fork) cudaEventDestroy(fork);
+  return e;
+}
+
 shgo_status launch_coulomb2c(const DeviceBasis& db, const DeviceTables& dt, const Tables& th,
                              const std::vector<ClassWork>& work, const MolView& mv, double* out, cudaStream_t stream,
                              std::string* err) {
-  for (const ClassWork& w : work) {
-    if (w.npairs == 0) continue;
-    k_coulomb2c<<<grid_cap(w.npairs, 16), 64, coulomb2c_smem(w.la, w.lb), stream>>>(
-        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.shell_nprim,
-        db.shell_foff, db.prim_exp, db.prim_coef, dt.boys, dt.c2_ptr + th.c2_base[class_id(w.la, w.lb)],
-        dt.c2_terms, dt.c2_a, mv, out);
+  const cudaError_t e = classes_concurrent(
+      work, stream,
+      [](const ClassWork& w) {
+        return (double)w.npp * (w.la + w.lb + 1) + (double)w.npairs * (2 * w.la + 1) * (2 * w.lb + 1);
+      },
+      [&](const ClassWork& w, cudaStream_t s) {
+        k_coulomb2c<<<grid_cap(w.npairs, 16), 64, coulomb2c_smem(w.la, w.lb), s>>>(
+            w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.shell_xyz, db.shell_poff, db.shell_nprim,
+            db.shell_foff, db.prim_exp, db.prim_coef, dt.boys, dt.c2_ptr + th.c2_base[class_id(w.la, w.lb)],
+            dt.c2_terms, dt.c2_a, mv, out);
+      });
+  if (e != cudaSuccess) {
+    *err = std::string("two-centre launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
   }
   return launch_error(err);
 }
@@ -2043,12 +2082,17 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err) {
   ensure_max_dynamic_smem((const void*)k_overlap_block);
-  for (const ClassWork& w : work) {
-    if (w.npairs == 0) continue;
-    k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), stream>>>(
-        w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site, rot_block(db.rot_lmax),
-        db.rotd,
-        db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
+  const cudaError_t e = classes_concurrent(
+      work, stream,
+      [](const ClassWork& w) { return (double)w.npp + (double)w.npairs * (2 * w.la + 1) * (2 * w.lb + 1); },
+      [&](const ClassWork& w, cudaStream_t s) {
+        k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), s>>>(
+            w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site,
+            rot_block(db.rot_lmax), db.rotd, db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
+      });
+  if (e != cudaSuccess) {
+    *err = std::string("overlap launch: ") + cudaGetErrorString(e);
+    return SHGO_ERR_CUDA;
   }
   return launch_error(err);
 }
