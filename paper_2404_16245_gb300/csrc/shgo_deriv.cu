@@ -26,7 +26,9 @@
 // axis c, weighted by 2 alpha and by 2 beta in one pass over the Gaunt program where shared memory allows, the
 // lowered classes, or the field blocks, each rotated to the molecular frame into a scratch array) and
 // k_deriv_combine, which adds a shell pair's blocks in a fixed order into the output (no atomics: the result
-// does not depend on the schedule).
+// does not depend on the schedule).  The density-contracted gradient replaces the combine by k_deriv_contract
+// (each pair's elements weighted by the density and summed per pair) and k_shell_gradient (per shell, its
+// pairs' sums in pair order).
 #include <cuda_runtime.h>
 
 #include <algorithm>
