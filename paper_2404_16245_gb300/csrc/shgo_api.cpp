@@ -293,6 +293,7 @@ shgo_status build_basis(int32_t n_shells, const int32_t* l, const int32_t* n_pri
   b->n_shells = n_shells;
   b->d.precision = opt ? opt->precision : SHGO_PREC_FP64;
   b->d.prim_bound = (flags & SHGO_FLAG_NO_PRIM_BOUND) ? 0 : 1;
+  b->d.coupling_one_warp = 1;
   b->sparse = (flags & SHGO_FLAG_BLOCK_SPARSE) != 0;
   b->batch = batch;
   const int nm = batch ? n_mol : 1;

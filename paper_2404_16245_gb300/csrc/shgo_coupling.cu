@@ -15,7 +15,9 @@
 // two shared tables S[h][c] and B[b][c].  Then thread t owns R' entries e = t, t + 64, ...: their
 // sums over the chunk's nuclei read both table rows with 16-byte loads at fixed offsets.  Row
 // stride NCH + 2 doubles keeps those loads free of bank conflicts.  Two warps per block double
-// the warps an SM holds for the same shared memory.
+// the warps an SM holds for the same shared memory.  At small Lambda (few harmonic columns and R'
+// entries for the second warp) one warp does both halves (NW = 1); every entry is formed by the same
+// operations either way.
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -28,8 +30,9 @@ namespace shgo {
 
 namespace {
 
-template <int NCH, int LAM>
-__global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
+template <int NCH, int LAM, int NW>
+__global__ void __launch_bounds__(32 * NW) k_coupling_fp64(CouplingArgs A) {
+  constexpr int NT = 32 * NW;
   using Sh = CouplingShape<LAM, NCH>;
   constexpr int nS = Sh::nS, nR = Sh::nR, CS = Sh::CS;
   extern __shared__ __align__(16) double smem[];
@@ -54,7 +57,7 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) Q[k] = A.site_rot[9 * A.pair_site[pr] + k];
     __syncthreads();  // the previous primitive pair is done with racc and scl
-    for (int e = tid; e < nR; e += 64) racc[e] = 0.0;
+    for (int e = tid; e < nR; e += NT) racc[e] = 0.0;
     int64_t cbeg, ncen;
     mol_centers(A.mv, pr, cbeg, ncen);
     for (int64_t c0 = 0; c0 < ncen; c0 += NCH) {
@@ -66,13 +69,18 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
           pair_frame_offset(Q, Ax, Ay, Az, pd.shift, A.centers + 3 * c, dx, dy, dz);
           z = A.charges[c];
         }
-        point_tables<LAM, CS>(wid, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
+        if (NW == 2) {
+          point_tables<LAM, CS>(wid, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
+        } else {  // one warp takes both halves of the tables
+          point_tables<LAM, CS>(0, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
+          point_tables<LAM, CS>(1, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
+        }
       }
       __syncthreads();
       // a partial last chunk sums only its occupied columns (rounded up to a pair; empty columns
       // carry Z = 0 and so add exact zeros)
       const int nv2 = ncen - c0 >= NCH ? NCH / 2 : (int)((ncen - c0 + 1) >> 1);
-      for (int e = tid; e < nR; e += 64) {
+      for (int e = tid; e < nR; e += NT) {
         const int code = __ldg(A.rmap + e);
         const double2* S = reinterpret_cast<const double2*>(Stab + (code & 0xfff) * CS);
         const double2* B = reinterpret_cast<const double2*>(Btab + ((code >> 12) & 0xfff) * CS);
@@ -103,7 +111,7 @@ __global__ void __launch_bounds__(64) k_coupling_fp64(CouplingArgs A) {
     }
     __syncthreads();
     double* out = A.rbuf + A.rbase + w * (int64_t)nR;
-    for (int e = tid; e < nR; e += 64) out[e] = racc[e] * (scl[(__ldg(A.rmap + e) >> 24) & 0xff] * __ldg(A.rnorm + e));
+    for (int e = tid; e < nR; e += NT) out[e] = racc[e] * (scl[(__ldg(A.rmap + e) >> 24) & 0xff] * __ldg(A.rnorm + e));
     });
 }
 
@@ -378,10 +386,10 @@ constexpr EspKernel esp_kernel_at(int lam, std::integer_sequence<int, L...>) {
   return k;
 }
 
-template <int NCH, int... L>
+template <int NCH, int NW, int... L>
 constexpr CouplingKernel kernel_at(int lam, std::integer_sequence<int, L...>) {
   CouplingKernel k = nullptr;
-  ((lam == L ? (k = &k_coupling_fp64<NCH, L>, 0) : 0), ...);
+  ((lam == L ? (k = &k_coupling_fp64<NCH, L, NW>, 0) : 0), ...);
   return k;
 }
 
@@ -396,9 +404,18 @@ using Lams = std::make_integer_sequence<int, kLamMax + 1>;
 // the coupling kernel also runs at Lambda = la + lb + 1 (derivative integrals)
 using LamsDer = std::make_integer_sequence<int, kLamDer + 1>;
 
-CouplingKernel coupling_kernel(int lam, int nch) {
+// Small Lambda: one warp per block does both halves of the nucleus tables (the second warp of the two-warp
+// form has little of its own there: a few harmonic columns and a few R' entries).
+constexpr int kOneWarpLamMax = 8;
+using LamsOneWarp = std::make_integer_sequence<int, kOneWarpLamMax + 1>;
+int coupling_warps(int lam, bool one_warp_ok) { return one_warp_ok && lam <= kOneWarpLamMax ? 1 : 2; }
+
+CouplingKernel coupling_kernel(int lam, int nch, int nw) {
   if (lam < 0 || lam > kLamDer) return nullptr;
-  return nch == 16 ? kernel_at<16>(lam, LamsDer{}) : kernel_at<32>(lam, LamsDer{});
+  if (nw == 1)
+    return lam > kOneWarpLamMax ? nullptr
+                                : (nch == 16 ? kernel_at<16, 1>(lam, LamsOneWarp{}) : kernel_at<32, 1>(lam, LamsOneWarp{}));
+  return nch == 16 ? kernel_at<16, 2>(lam, LamsDer{}) : kernel_at<32, 2>(lam, LamsDer{});
 }
 
 }  // namespace
@@ -428,10 +445,12 @@ cudaError_t coupling_fp64_setup() {
   cudaError_t e = cudaMemcpyToSymbol(k_harm, &harm_coef_host(), sizeof(HarmCoef));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_boys, &boys_const_host(), sizeof(BoysConst));
   for (int lam = 0; lam <= kLamDer && e == cudaSuccess; ++lam)
-    for (int nch : {16, 32}) {
-      e = set_max_dynamic_smem((const void*)coupling_kernel(lam, nch));
-      if (e != cudaSuccess) break;
-    }
+    for (int nch : {16, 32})
+      for (int nw : {1, 2}) {
+        const CouplingKernel k = coupling_kernel(lam, nch, nw);
+        if (k) e = set_max_dynamic_smem((const void*)k);
+        if (e != cudaSuccess) break;
+      }
   for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam) {
     e = set_max_dynamic_smem((const void*)esp_kernel_at(lam, Lams{}));
     if (e == cudaSuccess)
@@ -441,9 +460,12 @@ cudaError_t coupling_fp64_setup() {
 }
 
 cudaError_t launch_coupling_fp64(int lam, int nch, const CouplingArgs& args, int grid, cudaStream_t stream) {
-  const CouplingKernel k = coupling_kernel(lam, nch);
+  const int nw = coupling_warps(lam, args.one_warp_ok != 0);
+  const CouplingKernel k = coupling_kernel(lam, nch, nw);
   if (!k) return cudaErrorInvalidValue;
-  k<<<grid, 64, coupling_fp64_smem(lam, nch), stream>>>(args);
+  // one-warp blocks: twice the blocks for the same warps per SM
+  if (nw == 1) grid = (int)std::min<int64_t>(2 * (int64_t)grid, std::max<int64_t>(args.npp, 1));
+  k<<<grid, 32 * nw, coupling_fp64_smem(lam, nch), stream>>>(args);
   return cudaGetLastError();
 }
 

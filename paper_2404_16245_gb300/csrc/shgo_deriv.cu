@@ -675,6 +675,7 @@ shgo_status launch_nuclear_deriv(const DeviceBasis& db, const DeviceTables& dt, 
       ca.pair_site = db.pair_site;
       ca.ppd = db.ppd;
       ca.rbuf = r1buf;
+      ca.one_warp_ok = db.coupling_one_warp;
       e = launch_coupling_fp64(lam1, lam1 <= 12 ? 32 : 16, ca, grid_cap_sm(w.npp, 8), s);
       if (e != cudaSuccess) break;
     }

@@ -381,6 +381,7 @@ struct DeviceBasis {
   int64_t rbuf_len = 0;
   int precision = SHGO_PREC_FP64;  // a shgo_precision value
   int prim_bound = 1;              // 1: primitive pairs below the elementwise bound are skipped
+  int coupling_one_warp = 0;       // 1: the FP64 coupling kernel runs one warp per block at small Lambda
   // Bounded coupling buffer: region > 0 means rbuf holds one region of `region` doubles per pool
   // stream and each class runs in chunks of whole shell pairs that fit its stream's region;
   // h_ppoff (host, npairs + 1) gives the primitive-pair offsets used to cut the chunks.
@@ -517,6 +518,7 @@ struct CouplingArgs {
   const float2* exp_ff = nullptr;
   const int* items = nullptr;         // work items of this Lambda (coupling_f32_items)
   const float2* rnorm_ff = nullptr;   // rnorm of this Lambda as (hi, lo) pairs
+  int one_warp_ok = 0;                // FP64: small Lambda may run one warp per block (DeviceBasis::coupling_one_warp)
 };
 // Arguments of the electrostatic-potential kernel for one class (shgo_coupling.cu).
 struct EspArgs {

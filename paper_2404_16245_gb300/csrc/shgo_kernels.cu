@@ -915,6 +915,7 @@ struct Launcher {
     a.pair_site = db.pair_site;
     a.ppd = db.ppd;
     a.rbuf = db.rbuf;
+    a.one_warp_ok = db.coupling_one_warp;
     if (db.precision != SHGO_PREC_FP64) {
       a.boys_ff = dt.boys_ff;
       a.exp_ff = dt.exp_ff;
