@@ -18,13 +18,14 @@
 // 2005, on pair inputs).  The Boys values come from the FP64 grid (split into pairs) by the same
 // Taylor step and recursions as the FP64 path, run on pairs.
 //
-// Block = two warps on one primitive pair, lane i of both owning nucleus i of a chunk of 32: warp 0
-// evaluates the radial factors and the harmonic columns m < MS, warp 1 the columns m >= MS.  Tables
-// S[h][c] and B[b][c] (rows of 34 pairs or 36 floats: 16-byte multiples, rows 4 banks apart) feed the
-// sums, where a thread takes the R' entries (L, M, k) and (L, M, k + 1) together (one S row, two B
-// rows) or a lone (L, M, k).
+// Block = four warps on one primitive pair (two at Lambda <= 8), lane i of each owning nucleus i of a chunk
+// of 32: warp 0 evaluates Phi for the nuclei with T < 40, warp 1 for those with T >= 40, and the harmonic
+// columns and then the radial rows are split over the warps by a cost model.  Tables S[h][c] and B[b][c]
+// (rows of 34 pairs or 36 floats: 16-byte multiples, rows 4 banks apart) feed the sums, where a thread
+// takes the R' entries (L, M, k) and (L, M, k + 1) together (one S row, two B rows) or a lone (L, M, k).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -36,7 +37,6 @@ namespace shgo {
 namespace {
 
 constexpr int kNch = 32;        // nuclei per chunk
-constexpr int kThreads = 128;   // threads per block: four warps
 constexpr int kExpN = 2048;     // exp(-g/16) table: T < 128 (beyond, exp(-T) T^{n/2} is below 1e-30 of Phi_n)
 constexpr double kTwoPiF = 6.283185307179586476925286766559;
 
@@ -244,6 +244,32 @@ __host__ __device__ constexpr int col_bound(int lam, int w, bool fp) {
         }
       }
   return bb[w];
+}
+// The same splits for two warps (small Lambda): warp 0 Phi for T < 40 and the columns below the bound,
+// warp 1 Phi for T >= 40 and the rest; the radial rows halved.
+__host__ __device__ constexpr int col_bound2(int lam, int w, bool fp) {
+  if (w <= 0) return 0;
+  if (w >= 2) return lam + 1;
+  const int small = fp ? 300 + 37 * lam : 30 + 4 * lam;
+  const int large = fp ? 180 + 31 * lam : 20 + 4 * lam;
+  int best = 1 << 30, bb = 0;
+  for (int b1 = 0; b1 <= lam + 1; ++b1) {
+    const int c0 = small + col_cost(lam, 0, b1, fp), c1 = large + col_cost(lam, b1, lam + 1, fp);
+    const int mx = c0 > c1 ? c0 : c1;
+    if (mx < best) {
+      best = mx;
+      bb = b1;
+    }
+  }
+  return bb;
+}
+__host__ __device__ constexpr int row_bound2(int lam, int w) {
+  if (w <= 0) return 0;
+  if (w >= 2) return lam + 1;
+  const int total = n_beta(lam);
+  int L = 0, acc = 0;
+  while (L <= lam && 2 * (acc + kmax_of(lam, L) + 1) <= total + 1) acc += kmax_of(lam, L++) + 1;
+  return L;
 }
 __host__ __device__ constexpr int row_bound(int lam, int w) {
   if (w <= 0) return 0;
@@ -500,8 +526,9 @@ __device__ __forceinline__ void sum_single(const float* S_, const float* B_, int
   }
 }
 
-template <int LAM, bool FF>
-__global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
+template <int LAM, bool FF, int NW>
+__global__ void __launch_bounds__(32 * NW) k_coupling_f32(CouplingArgs A) {
+  constexpr int NT = 32 * NW;  // four warps, or two at small Lambda (the same operations per entry)
   using Sh = F32Shape<LAM, FF>;
   using V = std::conditional_t<FF, ff, float>;
   constexpr int nS = Sh::nS, nB = Sh::nB, nR = Sh::nR, RS = Sh::RS;
@@ -516,8 +543,10 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
   float2* racc2 = geo + 14;                                     // [nR] (FF)
   float* racc1 = reinterpret_cast<float*>(geo + 14);            // [nR] (plain)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int cb1 = col_bound(LAM, 1, FF), cb2 = col_bound(LAM, 2, FF), cb3 = col_bound(LAM, 3, FF);
-  constexpr int rb1 = row_bound(LAM, 1), rb2 = row_bound(LAM, 2), rb3 = row_bound(LAM, 3);
+  constexpr int cb1 = NW == 4 ? col_bound(LAM, 1, FF) : col_bound2(LAM, 1, FF);
+  constexpr int cb2 = NW == 4 ? col_bound(LAM, 2, FF) : LAM + 1, cb3 = NW == 4 ? col_bound(LAM, 3, FF) : LAM + 1;
+  constexpr int rb1 = NW == 4 ? row_bound(LAM, 1) : row_bound2(LAM, 1);
+  constexpr int rb2 = NW == 4 ? row_bound(LAM, 2) : LAM + 1, rb3 = NW == 4 ? row_bound(LAM, 3) : LAM + 1;
   const int a0 = wid == 0 ? 0 : (wid == 1 ? cb1 : (wid == 2 ? cb2 : cb3));
   const int a1 = wid == 0 ? cb1 : (wid == 1 ? cb2 : (wid == 2 ? cb3 : LAM + 1));
   const int L0 = wid == 0 ? 0 : (wid == 1 ? rb1 : (wid == 2 ? rb2 : rb3));
@@ -540,7 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
     } else if (tid == 13) {
       geo[13] = to_pair<FF>(pd.p);
     }
-    for (int e = tid; e < nR; e += kThreads) {
+    for (int e = tid; e < nR; e += NT) {
       if constexpr (FF)
         racc2[e] = make_float2(0.f, 0.f);
       else
@@ -592,12 +621,12 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
       // Z = 0 radial sums)
       const int nv = ncen - c0 >= kNch ? kNch : (int)(ncen - c0);
       const int nit = (nv + Sh::PER - 1) / Sh::PER;
-      for (int i = tid; i < Sh::nPair; i += kThreads) {
+      for (int i = tid; i < Sh::nPair; i += NT) {
         const int e0 = __ldg(A.items + i);
         const int code = __ldg(A.rmap + e0);
         sum_pair<FF, RS>(Stab + (code & 0xfff) * RS, Btab + ((code >> 12) & 0xfff) * RS, nit, racc2, racc1, e0);
       }
-      for (int i = Sh::nPair + tid; i < Sh::nPair + Sh::nSingle; i += kThreads) {
+      for (int i = Sh::nPair + tid; i < Sh::nPair + Sh::nSingle; i += NT) {
         const int e0 = __ldg(A.items + i);
         const int code = __ldg(A.rmap + e0);
         sum_single<FF>(Stab + (code & 0xfff) * RS, Btab + ((code >> 12) & 0xfff) * RS, nit, racc2, racc1, e0);
@@ -616,7 +645,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
       sclL[lane] = s;
     }
     __syncthreads();
-    for (int b = tid; b < nB; b += kThreads) {
+    for (int b = tid; b < nB; b += NT) {
       int L = 0, bo = 0;
       while (bo + kmax_of(LAM, L) + 1 <= b) bo += kmax_of(LAM, L++) + 1;
       sclb[b] = sclk[b - bo] * sclL[L];
@@ -624,7 +653,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
     __syncthreads();
     // out = R' N_LM (pair product) x scale (FP64)
     double* out = A.rbuf + A.rbase + w * (int64_t)nR;
-    for (int e = tid; e < nR; e += kThreads) {
+    for (int e = tid; e < nR; e += NT) {
       const int code = __ldg(A.rmap + e);
       double v;
       if constexpr (FF) {
@@ -640,12 +669,17 @@ __global__ void __launch_bounds__(kThreads) k_coupling_f32(CouplingArgs A) {
 
 using Kernel = void (*)(CouplingArgs);
 
-template <bool FF, int... L>
+template <bool FF, int NW, int... L>
 constexpr Kernel kernel_at(int lam, std::integer_sequence<int, L...>) {
   Kernel k = nullptr;
-  ((lam == L ? (k = &k_coupling_f32<L, FF>, 0) : 0), ...);
+  ((lam == L ? (k = &k_coupling_f32<L, FF, NW>, 0) : 0), ...);
   return k;
 }
+
+// Two warps per block up to Lambda = 8 (measured: the batched workload 6 % faster, the high-l molecule 1.5 %),
+// for the bases that allow the smaller blocks (CouplingArgs::one_warp_ok).
+constexpr int kTwoWarpLamMax = 8;
+int f32_warps(int lam, bool small_ok) { return small_ok && lam <= kTwoWarpLamMax ? 2 : 4; }
 
 template <bool FF, int... L>
 constexpr size_t smem_at(int lam, std::integer_sequence<int, L...>) {
@@ -712,8 +746,10 @@ cudaError_t coupling_f32_setup() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(f_inv_int, ii, sizeof(ii));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(f_half_sqrt_pi, &hsp, sizeof(hsp));
   for (int lam = 0; lam <= kLamMax && e == cudaSuccess; ++lam) {
-    e = set_max_dynamic_smem((const void*)kernel_at<true>(lam, Lams{}));
-    if (e == cudaSuccess) e = set_max_dynamic_smem((const void*)kernel_at<false>(lam, Lams{}));
+    e = set_max_dynamic_smem((const void*)kernel_at<true, 4>(lam, Lams{}));
+    if (e == cudaSuccess) e = set_max_dynamic_smem((const void*)kernel_at<false, 4>(lam, Lams{}));
+    if (e == cudaSuccess) e = set_max_dynamic_smem((const void*)kernel_at<true, 2>(lam, Lams{}));
+    if (e == cudaSuccess) e = set_max_dynamic_smem((const void*)kernel_at<false, 2>(lam, Lams{}));
   }
   return e;
 }
@@ -721,8 +757,12 @@ cudaError_t coupling_f32_setup() {
 cudaError_t launch_coupling_f32(int lam, bool compensated, const CouplingArgs& args, int grid, cudaStream_t stream) {
   if (lam < 0 || lam > kLamMax || !args.boys_ff || !args.exp_ff || !args.items || !args.rnorm_ff)
     return cudaErrorInvalidValue;
-  const Kernel k = compensated ? kernel_at<true>(lam, Lams{}) : kernel_at<false>(lam, Lams{});
-  k<<<grid, kThreads, coupling_f32_smem(lam, compensated), stream>>>(args);
+  const int nw = f32_warps(lam, args.one_warp_ok != 0);
+  const Kernel k = nw == 2 ? (compensated ? kernel_at<true, 2>(lam, Lams{}) : kernel_at<false, 2>(lam, Lams{}))
+                           : (compensated ? kernel_at<true, 4>(lam, Lams{}) : kernel_at<false, 4>(lam, Lams{}));
+  // two-warp blocks: twice the blocks
+  if (nw == 2) grid = (int)std::min<int64_t>(2 * (int64_t)grid, std::max<int64_t>(args.npp, 1));
+  k<<<grid, 32 * nw, coupling_f32_smem(lam, compensated), stream>>>(args);
   return cudaGetLastError();
 }
 

@@ -518,7 +518,8 @@ struct CouplingArgs {
   const float2* exp_ff = nullptr;
   const int* items = nullptr;         // work items of this Lambda (coupling_f32_items)
   const float2* rnorm_ff = nullptr;   // rnorm of this Lambda as (hi, lo) pairs
-  int one_warp_ok = 0;                // FP64: small Lambda may run one warp per block (DeviceBasis::coupling_one_warp)
+  int one_warp_ok = 0;                // small Lambda may run smaller blocks (DeviceBasis::coupling_one_warp): one
+                                      // warp (FP64) or two (FP32-bulk)
 };
 // Arguments of the electrostatic-potential kernel for one class (shgo_coupling.cu).
 struct EspArgs {
