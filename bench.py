@@ -42,9 +42,9 @@ FP64_DFMA_PER_CLK = 304
 # DRAM traffic of the coupling phase of one V of this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 28 coupling launches of one call, from an ncu capture of the current
 # kernel), or None while no capture of the current kernel exists.
-COUPLING_DRAM_BYTES_PER_V = 8.27e6
+COUPLING_DRAM_BYTES_PER_V = 8.25e6
 COUPLING_DRAM_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum summed over the 28 k_coupling_fp64 launches of "
-                      "one V (8.27 MB read, 0 B written: the coupling blocks stay in L2), "
+                      "one V (8.25 MB read, 0 B written: the coupling blocks stay in L2), "
                       "profiles/k_coupling_fp64_traffic_highl_fp64.md")
 
 
