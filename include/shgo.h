@@ -167,6 +167,12 @@ shgo_status shgo_basis_flops(const shgo_basis* basis, int64_t n_centers, double*
  * flops[1] the variant pair passes (raising, Gaunt coupling, translation, rotation) and the combine. */
 shgo_status shgo_basis_deriv_flops(const shgo_basis* basis, int64_t n_centers, int32_t field, double* flops);
 
+/* The same algorithmic FP64 model for shgo_esp (gradient = 0) or shgo_esp_gradient (gradient = 1) of a
+ * single basis at n_points points: flops[0] the adjoint pass over the density (the pair kernel's count),
+ * flops[1] the per-point pass (per live primitive pair and point: the point tables and the grouped sums).
+ * SHGO_ERR_INVALID_ARG for a batch or a negative count. */
+shgo_status shgo_basis_esp_flops(const shgo_basis* basis, int64_t n_points, int32_t gradient, double* flops);
+
 /* Number of kernel launches one shgo_nuclear_attraction call on this basis makes (n > 0). */
 int64_t shgo_basis_launches(const shgo_basis* basis);
 

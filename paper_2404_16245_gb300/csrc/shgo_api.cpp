@@ -715,6 +715,28 @@ double coupling_per_triple(int lam) {
   return 9 + 11 + boys + (2.0 * lam + 1) + 2.0 * (lam / 2) + 2.0 * (nB - (lam + 1)) + s_lm + 2.0 * nR;
 }
 
+// Per (primitive pair, point) of the potential's point pass: the coupling kernel's per-nucleus tables and
+// the sum grouped by radial row, one multiply-add per R' entry and one per radial row.
+double esp_per_point(int lam) { return coupling_per_triple(lam) - 2.0 * n_r(lam) + 2.0 * (n_r(lam) + n_beta(lam)); }
+
+// Per (primitive pair, point) of the gradient's point pass: the frame offset (20), Boys values to order
+// lam + 1, T^k/k!, the radial rows B and -2p T^k/k! F (4 per row), the solid-harmonic polynomials with their
+// gradients (26 per column recursion step, 3 per first step, 22 per step of the diagonal chain, 5 for r^2),
+// the sums (per R' entry two products and four multiply-adds: a form grouped by harmonic row needs fewer
+// operations but ran slower, having less independent work per thread), the offset term (6) and the rotation
+// back to the molecular frame (18).
+double esp_grad_per_point(int lam) {
+  double harm = 5.0;
+  for (int am = 0; am <= lam; ++am) {
+    const double cols = am == 0 ? 1.0 : 2.0;
+    if (am + 1 <= lam) harm += 3.0 * cols;
+    harm += 26.0 * cols * std::max(0, lam - am - 1);
+    if (am >= 1 && am < lam) harm += 22.0;
+  }
+  const double boys = 5.0 * kBoysK + 1 + 3.0 * (lam + 1);
+  return 20.0 + boys + (lam / 2) + 4.0 * n_beta(lam) + harm + 10.0 * n_r(lam) + 24.0;
+}
+
 // The Gaunt coupling of one primitive pair into a (lbra, lket) block: 2 per nonzero coefficient of the class
 // stored as (max, min).
 double gaunt_flops(const Tables& t, int lbra, int lket) {
@@ -1362,6 +1384,26 @@ shgo_status shgo_basis_deriv_flops(const shgo_basis* basis, int64_t n_centers, i
     if (lb > 0) flops[1] += pair_pass_flops(t, la, lb - 1, live_pp, live_pairs);
     // combine: per element and component 6 (the frame rotation) + 2 (2l - 1) (lowered), for both orientations
     flops[1] += 3.0 * na * nb * w.npairs * (2.0 * 6.0 + 2.0 * (2 * la - 1) + 2.0 * (2 * lb - 1));
+  }
+  return SHGO_OK;
+}
+
+shgo_status shgo_basis_esp_flops(const shgo_basis* basis, int64_t n_points, int32_t gradient, double* flops) {
+  if (!basis || !flops || n_points < 0 || basis->batch) return fail(SHGO_ERR_INVALID_ARG, "bad arguments");
+  {
+    std::string err;
+    const shgo_status st = ensure_live_counts(basis, &err);
+    if (st != SHGO_OK) return fail(st, err);
+  }
+  const Tables& t = tables_host();
+  flops[0] = flops[1] = 0;
+  for (size_t wi = 0; wi < basis->work.size(); ++wi) {
+    const ClassWork& w = basis->work[wi];
+    const int lam = w.la + w.lb;
+    const double live_pp = (double)basis->live_pp[wi], live_pairs = (double)basis->live_pairs[wi];
+    // the adjoint pass is the pair kernel's operation count read backwards, plus the R' scale
+    flops[0] += pair_pass_flops(t, w.la, w.lb, live_pp, live_pairs) + 2.0 * n_r(lam) * live_pp;
+    flops[1] += (gradient ? esp_grad_per_point(lam) : esp_per_point(lam)) * live_pp * (double)n_points;
   }
   return SHGO_OK;
 }

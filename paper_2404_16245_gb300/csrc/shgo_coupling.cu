@@ -115,11 +115,66 @@ __global__ void __launch_bounds__(32 * NW) k_coupling_fp64(CouplingArgs A) {
     });
 }
 
+// R' entries of Lambda are ordered by L, then M, then k (k <= (Lambda - L)/2); the harmonic row of (L, M) is
+// L^2 + L + M and the radial row of (L, k) is the number of (L', k') with L' < L plus k.
+// First radial group (in (L, k) order) of the second warp: the groups before it hold at least half the entries.
+__host__ __device__ constexpr int esp_group_split(int lam) {
+  const int half = cn_r(lam) / 2;
+  int g = 0, cum = 0;
+  for (int L = 0; L <= lam; ++L)
+    for (int k = 0; k <= (lam - L) / 2; ++k, ++g) {
+      if (cum >= half) return g;
+      cum += 2 * L + 1;
+    }
+  return g;
+}
+
+// Per point: sum_e G'[e] S[h(e)] B[b(e)] grouped by the radial row, sum_{L,k} B_Lk (sum_M G'_{LMk} S_LM): one
+// multiply-add per entry and one per radial row, instead of a product and a multiply-add per entry.  Radial
+// groups g in [g0, g1); the walk from group 0 to g0 stops by L = Lambda + 1 (g0 <= number of radial rows).
+// Loops run over runtime bounds: a fully unrolled form was slower (its code overflowed the instruction cache).
+template <int LAM, int CS>
+__device__ __forceinline__ double esp_point_sum(int g0, int g1, const double* __restrict__ gam,
+                                                const double* __restrict__ S, const double* __restrict__ B) {
+  int L = 0, rb = 0, bb = 0;
+  while (bb + (LAM - L) / 2 + 1 <= g0) {
+    rb += (2 * L + 1) * ((LAM - L) / 2 + 1);
+    bb += (LAM - L) / 2 + 1;
+    ++L;
+  }
+  int k = g0 - bb, nk = (LAM - L) / 2 + 1;
+  double s0 = 0.0, s1 = 0.0;
+  for (int g = g0; g < g1; ++g) {
+    const double* gp = gam + rb + k;  // G'_{L,M,k}, M = -L..L, stride nk
+    const double* sp = S + L * L * CS;
+    const int n = 2 * L + 1;
+    double t0 = 0.0, t1 = 0.0;
+    int j = 0;
+    for (; j + 1 < n; j += 2) {
+      t0 = fma(gp[j * nk], sp[j * CS], t0);
+      t1 = fma(gp[(j + 1) * nk], sp[(j + 1) * CS], t1);
+    }
+    t0 = fma(gp[j * nk], sp[j * CS], t0);  // n is odd
+    if (g & 1)
+      s1 = fma(t0 + t1, B[(bb + k) * CS], s1);
+    else
+      s0 = fma(t0 + t1, B[(bb + k) * CS], s0);
+    if (++k == nk) {
+      rb += (2 * L + 1) * nk;
+      bb += nk;
+      ++L;
+      k = 0;
+      nk = (LAM - L) / 2 + 1;
+    }
+  }
+  return s0 + s1;
+}
+
 // Electrostatic potential (adjoint of the coupling): for a chunk of NCH points and a range of primitive
 // pairs of one class, phi(C) += sum_e G'[e] U_{L(e)M(e)}(d/|d|) |d|^L beta_{L,k}/k! (d = C - P, unit
 // charge), G' being the density-weighted adjoint block of the primitive pair (k_esp_adjoint).  Block
 // (chunk, split): the splits divide the class's primitive pairs; each block adds its partial sums to
-// phi once per point.
+// phi once per point.  Point sums: warp 0 takes the radial groups before esp_group_split, warp 1 the rest.
 template <int NCH, int LAM>
 __global__ void __launch_bounds__(64) k_esp_fp64(EspArgs A) {
   using Sh = CouplingShape<LAM, NCH>;
@@ -136,8 +191,7 @@ __global__ void __launch_bounds__(64) k_esp_fp64(EspArgs A) {
   const int64_t c = (int64_t)chunk * NCH + lane;
   const bool valid = lane < NCH && c < A.npoints;
   double acc = 0.0;
-  // R' entries split between the warps for the point sums
-  const int e0 = wid == 0 ? 0 : nR / 2, e1 = wid == 0 ? nR / 2 : nR;
+  constexpr int GS = esp_group_split(LAM);
   for (int64_t w = w0; w < w1; ++w) {
     const int64_t q = A.pp_base + w;
     const PPData pd = A.ppd[q];
@@ -159,20 +213,8 @@ __global__ void __launch_bounds__(64) k_esp_fp64(EspArgs A) {
       point_tables<LAM, CS>(wid, lane, pd.p, dx, dy, dz, z, A.boys_tab, Stab, Btab);
     }
     __syncthreads();
-    if (lane < NCH) {
-      double s0 = 0.0, s1 = 0.0;
-      int e = e0;
-      for (; e + 1 < e1; e += 2) {
-        const int c0 = __ldg(A.rmap + e), c1 = __ldg(A.rmap + e + 1);
-        s0 = fma(gam[e] * Stab[(c0 & 0xfff) * CS + lane], Btab[((c0 >> 12) & 0xfff) * CS + lane], s0);
-        s1 = fma(gam[e + 1] * Stab[(c1 & 0xfff) * CS + lane], Btab[((c1 >> 12) & 0xfff) * CS + lane], s1);
-      }
-      if (e < e1) {
-        const int c0 = __ldg(A.rmap + e);
-        s0 = fma(gam[e] * Stab[(c0 & 0xfff) * CS + lane], Btab[((c0 >> 12) & 0xfff) * CS + lane], s0);
-      }
-      acc += s0 + s1;
-    }
+    if (lane < NCH)
+      acc += esp_point_sum<LAM, CS>(wid == 0 ? 0 : GS, wid == 0 ? GS : Sh::nB, gam, Stab + lane, Btab + lane);
   }
   __syncthreads();
   if (wid == 1 && lane < NCH) part[lane] = acc;

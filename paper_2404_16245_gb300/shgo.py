@@ -118,6 +118,8 @@ def _load() -> ctypes.CDLL:
     lib.shgo_basis_flops.restype = ctypes.c_int
     lib.shgo_basis_deriv_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, f64p]
     lib.shgo_basis_deriv_flops.restype = ctypes.c_int
+    lib.shgo_basis_esp_flops.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, f64p]
+    lib.shgo_basis_esp_flops.restype = ctypes.c_int
     lib.shgo_sparse_layout.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]
     lib.shgo_sparse_layout.restype = ctypes.c_int
@@ -238,6 +240,14 @@ def shgo_basis_deriv_flops(basis, n_centers: int, field: bool = False):
     f = np.zeros(2)
     _check(_lib.shgo_basis_deriv_flops(ctypes.c_void_p(basis), int(n_centers), int(bool(field)),
                                        _ptr(f, ctypes.c_double)))
+    return f
+
+
+def shgo_basis_esp_flops(basis, n_points: int, gradient: bool = False):
+    """Algorithmic FP64 operations of one potential (or gradient) call: (adjoint pass, per-point pass)."""
+    f = np.zeros(2)
+    _check(_lib.shgo_basis_esp_flops(ctypes.c_void_p(basis), int(n_points), int(bool(gradient)),
+                                     _ptr(f, ctypes.c_double)))
     return f
 
 
