@@ -691,7 +691,7 @@ def run_overlap(args) -> int:
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"overlap of the high-l benchmark basis: {len(b['l'])} shells, {B.nbf} functions",
                        "shell_pairs": B.npairs, "l2": "flushed between steps (256 MiB write, outside step events)"},
-            "roofline": {"bound": "hbm", "kernel": "k_overlap_block", "achieved": achieved, "peak": hbm,
+            "roofline": {"bound": "hbm", "kernel": "k_overlap", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                          "note": "bytes of the matrix written (both triangles) per step; the inputs are a few KB",
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}}

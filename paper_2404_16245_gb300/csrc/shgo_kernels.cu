@@ -586,38 +586,69 @@ __global__ void __launch_bounds__(128) k_esp_adjoint(int la, int lb, int npairs,
 // so S'[ma][mb] = delta_{ma mb} sum_{l1 >= |ma|} t_A(l1, ma) t_B(l1, ma) w(l1) with
 // w(l1) = sum_ij c~_i c~_j K_ij (beta/p)^{la-l1} (alpha/p)^{lb-l1} 4 pi (pi/2)^{1/2} (2 l1 - 1)!!/(2p)^{l1+3/2};
 // the block is rotated back with D^{la} S' (D^{lb})^T.
-__host__ __device__ inline size_t overlap_smem(int la, int lb) {
-  const int lm = la > lb ? la : lb, na = 2 * la + 1, nb = 2 * lb + 1;
-  return sizeof(double) * ((size_t)na * na + nb * nb + (la + 1) * na + (lb + 1) * nb + na * nb + 2 * (lm + 1) + 32);
+//
+// One launch covers every class: the shell pairs of all classes form one list of work items, class c holding
+// items [first[c], first[c + 1]) (its shell pairs pair_base[c] onwards).  One warp per shell pair, four per
+// block, each with its own slice of shared memory and no block-wide barrier: the work per pair is a few
+// hundred operations behind a short chain of loads, so what counts is how many pairs are in flight.
+constexpr int kOverlapMaxClasses = 64;
+struct OverlapClasses {
+  int n;
+  int first[kOverlapMaxClasses + 1];
+  int pair_base[kOverlapMaxClasses];
+  unsigned char la[kOverlapMaxClasses], lb[kOverlapMaxClasses];
+};
+constexpr int kOverlapWarps = 4;
+
+// Shared doubles of one warp for angular momenta up to lm: D^{la} and D^{lb}, t_A and t_B, w(l1), |b - a|^k,
+// d(m) and X = D^{la} diag(d).
+__host__ __device__ inline int overlap_warp_doubles(int lm) {
+  const int n = 2 * lm + 1;
+  return 3 * n * n + 2 * (lm + 1) * n + 2 * (lm + 1) + n + 1;
 }
 
-__global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs, int pair_base,
-                                                      const int* __restrict__ pair_a, const int* __restrict__ pair_b,
-                                                      const int64_t* __restrict__ pair_ppoff,
-                                                      const int* __restrict__ pair_site, int64_t rot_per,
-                                                      const double* __restrict__ rotd,
-                                                      const int* __restrict__ shell_nprim,
-                                                      const int64_t* __restrict__ shell_foff,
-                                                      const double* __restrict__ etab, const int* __restrict__ eoff,
-                                                      const PPData* __restrict__ ppd, MolView mv,
-                                                      double* __restrict__ out) {
+__global__ void __launch_bounds__(32 * kOverlapWarps) k_overlap(OverlapClasses cls, int lm_max,
+                                                                const int* __restrict__ pair_a,
+                                                                const int* __restrict__ pair_b,
+                                                                const int64_t* __restrict__ pair_ppoff,
+                                                                const int* __restrict__ pair_site, int64_t rot_per,
+                                                                const double* __restrict__ rotd,
+                                                                const int* __restrict__ shell_nprim,
+                                                                const int64_t* __restrict__ shell_foff,
+                                                                const double* __restrict__ etab,
+                                                                const int* __restrict__ eoff,
+                                                                const PPData* __restrict__ ppd, MolView mv,
+                                                                double* __restrict__ out) {
   extern __shared__ double smem[];
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int na = 2 * la + 1, nb = 2 * lb + 1;
-  const int lm = la > lb ? la : lb, ln = la < lb ? la : lb;
-  const int nDb = la != lb ? nb * nb : 0;
-  double* Dm = smem;  // D^{la}(Q^T), then D^{lb}(Q^T) when lb != la
-  double* tA = Dm + na * na + nb * nb;
-  double* tB = tA + (la + 1) * na;
-  double* Vs = tB + (lb + 1) * nb;
-  double* wl = Vs + na * nb;   // w(l1)
-  double* dpow = wl + lm + 1;  // |b - a|^k
-  for (int w = blockIdx.x; w < npairs; w += gridDim.x) {
-    const int pr = pair_base + w;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* wsm = smem + wib * overlap_warp_doubles(lm_max);
+  const int total = cls.first[cls.n];
+  for (int item = blockIdx.x * kOverlapWarps + wib; item < total; item += gridDim.x * kOverlapWarps) {
+    int c = 0, hi = cls.n - 1;  // class of the item (uniform over the warp)
+    while (c < hi) {
+      const int mid = (c + hi + 1) >> 1;
+      if (cls.first[mid] <= item)
+        c = mid;
+      else
+        hi = mid - 1;
+    }
+    const int la = cls.la[c], lb = cls.lb[c];
+    const int pr = cls.pair_base[c] + (item - cls.first[c]);
+    const int na = 2 * la + 1, nb = 2 * lb + 1;
+    const int lm = la > lb ? la : lb, ln = la < lb ? la : lb;
+    const int nDb = la != lb ? nb * nb : 0;
+    double* Dm = wsm;  // D^{la}(Q^T), then D^{lb}(Q^T) when lb != la
+    double* tA = Dm + na * na + nb * nb;
+    double* tB = tA + (la + 1) * na;
+    double* wl = tB + (lb + 1) * nb;  // w(l1)
+    double* dpow = wl + lm + 1;       // |b - a|^k
+    double* dm = dpow + lm + 1;       // d(m), m = -ln..ln
+    double* X = dm + 2 * lm + 1;      // [ma][m] = D^{la}[ma][m] d(m)
+    const int nm = 2 * ln + 1;
     const int a = pair_a[pr], b = pair_b[pr];
     const double* rd = rotd + (int64_t)pair_site[pr] * rot_per;
-    __syncthreads();
-    if (tid == 0) {
+    __syncwarp();  // the warp's previous pair is done with its tables
+    if (lane == 0) {
       const double dist = rd[0];
       double v = 1.0;
       for (int k = 0; k <= lm; ++k) {
@@ -625,16 +656,16 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
         v *= dist;
       }
     }
-    for (int e = tid; e < na * na; e += nth) Dm[e] = rd[1 + rot_doff(la) + e];
-    for (int e = tid; e < nDb; e += nth) Dm[na * na + e] = rd[1 + rot_doff(lb) + e];
-    // radial sums over primitive pairs, one l1 per thread
-    if (tid <= ln) {
-      const int l1 = tid;
+    for (int e = lane; e < na * na; e += 32) Dm[e] = rd[1 + rot_doff(la) + e];
+    for (int e = lane; e < nDb; e += 32) Dm[na * na + e] = rd[1 + rot_doff(lb) + e];
+    // radial sums over primitive pairs, one l1 per lane
+    if (lane <= ln) {
+      const int l1 = lane;
       double dfact = 1.0;
       for (int k = 2 * l1 - 1; k > 1; k -= 2) dfact *= k;
       // 4 pi (pi/2)^{1/2} / 2^{l1 + 3/2} (2 l1 - 1)!!
-      double c = 4.0 * 3.14159265358979323846 * 1.2533141373155002512 * dfact * 0.35355339059327376220;
-      for (int k = 0; k < l1; ++k) c *= 0.5;
+      double cf = 4.0 * 3.14159265358979323846 * 1.2533141373155002512 * dfact * 0.35355339059327376220;
+      for (int k = 0; k < l1; ++k) cf *= 0.5;
       const int64_t q0 = pair_ppoff[pr];
       const int npp = shell_nprim[a] * shell_nprim[b];
       double acc = 0.0;
@@ -647,44 +678,49 @@ __global__ void __launch_bounds__(64) k_overlap_block(int la, int lb, int npairs
         for (int k = 0; k < lb - l1; ++k) v *= pd.rb;
         acc += v;
       }
-      wl[l1] = c * acc;
+      wl[l1] = cf * acc;
     }
-    __syncthreads();
-    for (int e = tid; e < (la + 1) * na; e += nth) {
+    __syncwarp();
+    for (int e = lane; e < (la + 1) * na; e += 32) {
       const int l1 = e / na, ma = e % na - la, lr = la - l1;
       tA[e] = l1 >= (ma < 0 ? -ma : ma) ? etab[eoff[la] + translation_offset_dev(la, ma, l1, ma) + lr] * dpow[lr] : 0.0;
     }
-    for (int e = tid; e < (lb + 1) * nb; e += nth) {
+    for (int e = lane; e < (lb + 1) * nb; e += 32) {
       const int l2 = e / nb, mb = e % nb - lb, lr = lb - l2;
       tB[e] = l2 >= (mb < 0 ? -mb : mb)
                   ? etab[eoff[lb] + translation_offset_dev(lb, mb, l2, mb) + lr] * ((lr & 1) ? -dpow[lr] : dpow[lr])
                   : 0.0;
     }
-    __syncthreads();
-    // S = D^{la} S' (D^{lb})^T with S' diagonal in m (|m| <= min(la, lb))
+    __syncwarp();
+    // S' = diag(d), d(m) = sum_{l1 >= |m|} t_A(l1, m) t_B(l1, m) w(l1) for |m| <= min(la, lb), once per pair
+    if (lane < nm) {
+      const int m = lane - ln, am = m < 0 ? -m : m;
+      double d = 0.0;
+      for (int l1 = am; l1 <= ln; ++l1) d = fma(tA[l1 * na + m + la] * tB[l1 * nb + m + lb], wl[l1], d);
+      dm[lane] = d;
+    }
+    __syncwarp();
     const double* Da = Dm;
     const double* Db = la != lb ? Dm + na * na : Dm;
-    for (int e = tid; e < na * nb; e += nth) {
-      const int ma = e / nb, mb = e % nb;
-      double s = 0.0;
-      for (int m = -ln; m <= ln; ++m) {
-        const int am = m < 0 ? -m : m;
-        double d = 0.0;
-        for (int l1 = am; l1 <= ln; ++l1) d = fma(tA[l1 * na + m + la] * tB[l1 * nb + m + lb], wl[l1], d);
-        s = fma(Da[ma * na + m + la] * Db[mb * nb + m + lb], d, s);
-      }
-      Vs[e] = s;
+    for (int e = lane; e < na * nm; e += 32) {
+      const int r = e / nm, j = e - r * nm;
+      X[e] = Da[r * na + j - ln + la] * dm[j];
     }
-    __syncthreads();
+    __syncwarp();
+    // S = X (D^{lb})^T; a diagonal block (a == b) takes the entry below its diagonal from the products of the
+    // entry above it, so it is exactly symmetric
     const int64_t fa0 = shell_foff[a], fb0 = shell_foff[b];
     int64_t obase, ld;
     mol_output(mv, pr, obase, ld);
     double* o = out + obase;
-    for (int e = tid; e < na * nb; e += nth) {
+    for (int e = lane; e < na * nb; e += 32) {
       const int ma = e / nb, mb = e % nb;
-      const double v = (a == b && ma > mb) ? Vs[mb * nb + ma] : Vs[e];
-      o[(fa0 + ma) * ld + fb0 + mb] = v;
-      if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = v;
+      const bool lower = a == b && ma > mb;
+      const int r = lower ? mb : ma, q = lower ? ma : mb;
+      double s = 0.0;
+      for (int j = 0; j < nm; ++j) s = fma(X[r * nm + j], Db[q * nb + j - ln + lb], s);
+      o[(fa0 + ma) * ld + fb0 + mb] = s;
+      if (a != b) o[(fb0 + mb) * ld + fa0 + ma] = s;
     }
   }
 }
@@ -2082,15 +2118,29 @@ shgo_status launch_eri(const DeviceBasis& db, const DeviceTables& dt, const Tabl
 
 shgo_status launch_overlap(const DeviceBasis& db, const DeviceTables& dt, const std::vector<ClassWork>& work,
                            const MolView& mv, double* out, cudaStream_t stream, std::string* err) {
-  ensure_max_dynamic_smem((const void*)k_overlap_block);
-  const cudaError_t e = classes_concurrent(
-      work, stream,
-      [](const ClassWork& w) { return (double)w.npp + (double)w.npairs * (2 * w.la + 1) * (2 * w.lb + 1); },
-      [&](const ClassWork& w, cudaStream_t s) {
-        k_overlap_block<<<grid_cap(w.npairs, 16), 64, overlap_smem(w.la, w.lb), s>>>(
-            w.la, w.lb, w.npairs, w.pair_base, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site,
-            rot_block(db.rot_lmax), db.rotd, db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
-      });
+  OverlapClasses cls{};
+  int total = 0, lm_max = 0;
+  for (const ClassWork& w : work) {
+    if (w.npairs == 0) continue;
+    if (cls.n == kOverlapMaxClasses) {
+      *err = "overlap: more classes than one launch holds";
+      return SHGO_ERR_INVALID_ARG;
+    }
+    cls.first[cls.n] = total;
+    cls.pair_base[cls.n] = w.pair_base;
+    cls.la[cls.n] = (unsigned char)w.la;
+    cls.lb[cls.n] = (unsigned char)w.lb;
+    ++cls.n;
+    total += w.npairs;
+    lm_max = std::max(lm_max, std::max(w.la, w.lb));
+  }
+  cls.first[cls.n] = total;
+  if (total == 0) return SHGO_OK;
+  const size_t sm = sizeof(double) * (size_t)kOverlapWarps * overlap_warp_doubles(lm_max);
+  k_overlap<<<grid_cap((total + kOverlapWarps - 1) / kOverlapWarps, 12), 32 * kOverlapWarps, sm, stream>>>(
+      cls, lm_max, db.pair_a, db.pair_b, db.pair_ppoff, db.pair_site, rot_block(db.rot_lmax), db.rotd,
+      db.shell_nprim, db.shell_foff, dt.etab, dt.eoff, db.ppd, mv, out);
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *err = std::string("overlap launch: ") + cudaGetErrorString(e);
     return SHGO_ERR_CUDA;

@@ -87,3 +87,19 @@ def test_batched_overlap_matches_single(shgo):
     for m, (b, _, _) in enumerate(mols):
         parity.check(batch.block(Sh, m), ref_S(b), what=f"overlap molecule {m}")
     batch.close()
+
+
+def test_repeat_is_bitwise_and_empty_classes_skip(shgo):
+    # one launch over every class: two calls give the same bits; a basis with s and g shells only (classes
+    # (0, 0), (4, 0), (4, 4)) covers the classes that hold no pairs being left out of the launch
+    basis, _, _ = W.config2()
+    B = shgo.Basis(basis)
+    s1 = shgo.overlap(B).cpu().numpy()
+    s2 = shgo.overlap(B).cpu().numpy()
+    B.close()
+    assert np.array_equal(s1, s2)
+    rng = np.random.default_rng(12)
+    ls = [0, 4, 0, 4, 4]
+    b2 = W.make_basis(ls, [2] * len(ls), np.exp(rng.uniform(np.log(0.3), np.log(5.0), 2 * len(ls))),
+                      rng.uniform(0.2, 1, 2 * len(ls)), list(rng.uniform(0, 3.0, (len(ls), 3))))
+    parity.check(gpu_S(shgo, b2), ref_S(b2), what="overlap s and g shells")
