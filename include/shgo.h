@@ -217,8 +217,8 @@ shgo_status shgo_basis_sync(const shgo_basis* basis);
  * SHGO_ERR_INVALID_ARG before any device work, and shgo_last_error() gives the sizes.
  *
  * The first call on a device does a one-time set-up (finds the array's device address with
- * cudaGetSymbolAddress and copies the tables into it, synchronously); make that first call
- * before any stream capture.  Later calls copy the shell image from pageable host memory on
+ * cudaGetSymbolAddress and copies the tables into it, synchronously).  Later calls copy the shell
+ * image from pageable host memory on
  * `stream`, which orders the copy after earlier work on that stream.  Every call reuses the same
  * array, which keeps the previous call's contents; nothing in it needs to start at zero.  Calls
  * whose device work overlaps (different streams or host threads on one device) race on the array.
