@@ -636,7 +636,7 @@ def run_esp(args) -> int:
             "config": {"workload": f"potential of a density of the 32-atom l <= 6 basis at {args.points} points",
                        "shell_pairs": npairs, "shell_pair_points_per_s": npairs * args.points / (ms / 1e3),
                        "l2": "flushed between steps (256 MiB write, outside step events)"},
-            "roofline": {"bound": "fp64", "kernel": "whole potential call (k_esp_fp64 per class after k_esp_adjoint)",
+            "roofline": {"bound": "alu", "kernel": "whole potential call (k_esp_fp64 per class after k_esp_adjoint)",
                          "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                          "model_tflop": [float(fp[0]) / 1e12, float(fp[1]) / 1e12],
                          "peak_source": "shgo_measure_fma_rate in this run (of measured)"},
@@ -756,7 +756,7 @@ def run_deriv(args) -> int:
                          "what": "sum_ab (P_ab + P_ba) dV_ab/dA per shell for a seeded symmetric density, no matrix written"},
             "field": {"ms_per_step": ms_f, "shell_triples_per_s": triples / (ms_f / 1e3), "over_v": ms_f / ms_v,
                       "model_tflop": float(ff.sum()) / 1e12, "achieved_tflops": ach_f, "frac": ach_f / peak},
-            "roofline": {"bound": "fp64", "kernel": "whole derivative call (coupling at la + lb + 1, variant passes, "
+            "roofline": {"bound": "alu", "kernel": "whole derivative call (coupling at la + lb + 1, variant passes, "
                                                     "combine)", "achieved": ach_d, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach_d / peak, "traffic": None, "model_tflop": [float(fd[0]) / 1e12, float(fd[1]) / 1e12],
                          "peak_source": "shgo_measure_fma_rate in this run (of measured)"},
